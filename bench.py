@@ -1,0 +1,394 @@
+"""Benchmark of the differentiable MLS-MPM hot path (forward + reverse rollouts) on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+
+One timed step = one whole rollout of the workload (every simulation step: controller, bin/sort,
+P2G, grid, G2P) plus its full reverse pass (segment recompute from checkpoints, adjoint scatter,
+grid adjoint, adjoint gather, controller adjoint), with the inputs resident in HBM.  The default
+workload is the 2D soft walker: 128^2 grid, ~31k particles, 1000 steps, checkpoint every 64 steps,
+loss = mean final x_0.  Prints one JSON line (rank 0).
+
+--impl reference times the FP64 CPU oracle (the reference arm of this method) on a bounded
+sample of the same workload.  With N > 1 (torchrun), every rank runs an independent replica
+(scenes are independent; no collective on the data path) and the value is the sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "particle-steps/s fwd and fwd+bwd at oracle tolerance; rollout p50/p99 latency"
+UNIT = "particle-steps/s"
+
+# Algorithmic bytes per particle of each timed kernel kind (FP32 state records: 2D x2 F4 v2 C4 =
+# 48 B, 3D 96 B; group id 4 B).  Grid-node bytes are not counted (they are a few bytes per particle
+# at these densities), so `achieved` is a lower bound.
+ALGO_BYTES = {
+    # kind: (2D, 3D)
+    "adj_gather": (48 + 48 + 48 + 4, 96 + 96 + 96 + 4),  # state n + adjoint n+1 in, adjoint n out, group
+    "p2g_adj": (48 + 48 + 4, 96 + 96 + 4),               # state n + adjoint n+1 in, group
+    "p2g": (48 + 4, 96 + 4),                             # state in, group
+    "g2p": (24 + 48, 48 + 96),                           # x, F in; state out
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="walker_2d")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name, rank=0):
+    from paper_1810_01054_gb300 import scenes as S
+    seeds = {"walker_square_2d": 0, "walker_2d": 1, "soft_body_3d": 2, "box_cluster_3d": 3}
+    spec = S.CONFIGS[name](seeds[name] + 1000 * rank)
+    return spec
+
+
+def ckpt_of(spec):
+    return spec.ckpt_interval if spec.ckpt_interval else 0
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """Samples SM clock and throttle reasons with nvidia-smi while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- helpers
+def kernel_source_hash():
+    h = hashlib.sha1()
+    for f in ("mpm_kernels.cu", "mpm_device.cuh"):
+        with open(os.path.join(ROOT, "paper_1810_01054_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def measured_traffic(kernel, workload_name, n_particles):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, scaled to this workload's
+    particle count; None if no capture matches the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path))
+        e = rec.get(workload_name, {}).get(kernel)
+        if not e or e.get("kernel_hash") != kernel_source_hash():
+            return None
+        return e["dram_bytes_per_particle"] * n_particles
+    except (ValueError, KeyError, OSError):
+        return None
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            p = json.load(open(path))
+            return float(p["hbm_gbs"]), "measured"
+        except (ValueError, KeyError):
+            pass
+    return 6800.0, "fallback"
+
+
+def cpu_baseline(spec, budget_s=15.0):
+    """The FP64 oracle, as it stands, on one host core: forward + reverse over the first steps of
+    the workload, as many as fit in about `budget_s` seconds."""
+    from oracle import oracle as O
+    sc = O.Scene(spec)
+    t0 = time.time()
+    tr = sc.rollout(2)
+    seed = np.zeros((sc.N, sc.dim))
+    seed[:, 0] = 1.0 / sc.N
+    sc.backward(tr, (seed, None, None, None))
+    per = max(time.time() - t0, 1e-3) / 2
+    n = int(max(1, min(spec.n_steps, budget_s / per)))
+    t0 = time.time()
+    tr = sc.rollout(n)
+    sc.backward(tr, (seed, None, None, None))
+    dt = time.time() - t0
+    return {"value": sc.N * n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"FP64 oracle forward+reverse of the first {n} of {spec.n_steps} steps of {spec.name} "
+                      f"({sc.N} particles), single thread, {dt:.1f} s"}
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    spec = workload(args.workload)
+    sc = O.Scene(spec)
+    seed = np.zeros((sc.N, sc.dim))
+    seed[:, 0] = 1.0 / sc.N
+    # bounded sample per step: enough simulation steps for ~2 s of CPU work
+    t0 = time.time()
+    tr = sc.rollout(2)
+    sc.backward(tr, (seed, None, None, None))
+    per = max(time.time() - t0, 1e-3) / 2
+    n = int(max(1, min(spec.n_steps, 2.0 / per)))
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.time()
+        tr = sc.rollout(n)
+        sc.backward(tr, (seed, None, None, None))
+        if i >= args.warmup:
+            times.append(time.time() - t0)
+    tot = sum(times)
+    value = sc.N * n * len(times) / tot
+    sample = (f"FP64 oracle forward+reverse of the first {n} of {spec.n_steps} steps of {spec.name} "
+              f"({sc.N} particles) per step, single thread")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": spec.name, "particles": sc.N, "sim_steps_per_step": n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1810_01054_gb300 import mpm
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    spec = workload(args.workload, rank)
+    T, k = spec.n_steps, ckpt_of(spec)
+    N, d = spec.n_particles, spec.dim
+    ctx = mpm.Context(local_rank, stream=stream)
+    scene = mpm.Scene(ctx, spec)
+    # inputs resident in HBM
+    x0 = torch.tensor(spec.x0, dtype=torch.float32, device=dev)
+    v0 = torch.tensor(spec.v0, dtype=torch.float32, device=dev)
+    C0 = torch.tensor(spec.C0, dtype=torch.float32, device=dev)
+    F0 = torch.tensor(spec.F0, dtype=torch.float32, device=dev)
+    seed = torch.zeros((N, d), dtype=torch.float32, device=dev)
+    seed[:, 0] = 1.0 / N
+    outs = [torch.empty((N, d), device=dev), torch.empty((N, d), device=dev), torch.empty((N, d, d), device=dev),
+            torch.empty((N, d, d), device=dev), torch.empty((max(scene.n_params, 1),), device=dev)]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def one_step(backward=True):
+        scene.set_state(x0, v0, C0, F0, step=0)
+        scene.rollout(T, k)
+        if backward:
+            scene.backward(seed, out=outs)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        one_step()
+    barrier()
+
+    # -- timed region: K whole fwd+bwd rollouts, L2 flushed before each (flush not timed)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ctx.profile_start([mpm.K_ADJ_GATHER, mpm.K_P2G_ADJ, mpm.K_P2G, mpm.K_G2P], max_launches=args.steps * 4 * T + 64)
+    n_launch0 = mpm.launch_count()
+    with ClockSampler(local_rank) as clk:
+        barrier()
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            one_step()
+            ev[i][1].record(stream)
+        barrier()
+    n_launch = mpm.launch_count() - n_launch0 - 0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    prof = {nm: ctx.profile_read(kk) for nm, kk in
+            (("adj_gather", mpm.K_ADJ_GATHER), ("p2g_adj", mpm.K_P2G_ADJ), ("p2g", mpm.K_P2G), ("g2p", mpm.K_G2P))}
+    tot_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([tot_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = world * N * T * args.steps / (tot_ms / 1e3)
+
+    # -- forward-only throughput (same rollouts without the reverse pass)
+    fwd_ms = []
+    for i in range(max(2, args.steps // 2)):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        one_step(backward=False)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        fwd_ms.append(a.elapsed_time(b))
+    value_fwd = world * N * T / (statistics.median(fwd_ms) / 1e3)
+
+    # -- e2e through the public API with pinned host buffers (H2D inputs, D2H gradients)
+    e2e = None
+    if not args.no_e2e:
+        hx = torch.tensor(spec.x0, dtype=torch.float32).pin_memory()
+        hv = torch.tensor(spec.v0, dtype=torch.float32).pin_memory()
+        hC = torch.tensor(spec.C0, dtype=torch.float32).pin_memory()
+        hF = torch.tensor(spec.F0, dtype=torch.float32).pin_memory()
+        hseed = seed.cpu().pin_memory()
+        houts = [torch.empty(o.shape).pin_memory() for o in outs]
+        h2d = sum(t.numel() * 4 for t in (hx, hv, hC, hF, hseed))
+        d2h = sum(t.numel() * 4 for t in houts[:4]) + 4 * scene.n_params
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            scene.set_state(hx, hv, hC, hF, step=0)
+            scene.rollout(T, k)
+            scene.backward(hseed, out=houts)
+        barrier()
+        e2e_s = time.perf_counter() - t0
+        e2e = {"value": world * N * T * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    # -- the plain single-scene form (global atomics, dense grid) on the same workload
+    plain = None
+    if not args.no_plain and rank == 0:
+        ps = mpm.Scene(ctx, spec, impl=mpm.IMPL_PLAIN)
+        for _ in range(2):
+            ps.set_state(x0, v0, C0, F0, step=0)
+            ps.rollout(T, k)
+            ps.backward(seed, out=outs)
+        torch.cuda.synchronize(dev)
+        pm = []
+        for _ in range(2):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ps.set_state(x0, v0, C0, F0, step=0)
+            ps.rollout(T, k)
+            ps.backward(seed, out=outs)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            pm.append(a.elapsed_time(b))
+        plain = {"value": N * T / (min(pm) / 1e3), "unit": UNIT, "form": "plain single-scene (float atomics)"}
+        ps.close()
+
+    if rank != 0:
+        return
+    # roofline of the dominant kernel (largest summed time in the timed region)
+    dom = max(prof, key=lambda kk: prof[kk][1])
+    cnt, ms = prof[dom]
+    hbm, src = peaks()
+    bpp = ALGO_BYTES[dom][0 if d == 2 else 1]
+    launch_ms = ms / max(cnt, 1)
+    achieved = bpp * N / (launch_ms / 1e3) / 1e9
+    traffic = measured_traffic(dom, spec.name, N)
+    share = {kk: round(v[1] / tot_ms, 4) for kk, v in prof.items()}
+    clocks = clk.summary()
+    cpu = None if args.no_cpu_baseline else cpu_baseline(spec)
+    lat = sorted(step_ms)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": spec.name, "particles": N, "grid": "x".join(map(str, spec.n_grid)), "sim_steps": T,
+                   "ckpt_interval": k, "pass": "forward+reverse rollout", "loss": "mean final x_0",
+                   "l2": "flushed before every timed step (256 MB write, untimed)",
+                   "parallelism": f"replicas x{world}"},
+        "value_fwd": value_fwd,
+        "rollout_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": traffic, "peak_source": src,
+                     "algo_bytes_per_particle": bpp, "launches": cnt, "avg_launch_us": 1e3 * launch_ms},
+        "kernel_share_of_step": share,
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch, "clocks": clocks, "plain_form": plain,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

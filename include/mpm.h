@@ -1,0 +1,185 @@
+/*
+ * mpm.h - C ABI of libgbmpm: the differentiable MLS-MPM time step of ChainQueen
+ * (Hu et al., arXiv 1810.01054) on hand-written sm_103a CUDA kernels.
+ *
+ * One explicit step n -> n+1 (Section III, Eqs. 3-10):
+ *   P2G    m_i = sum_p N_ip m_p,  p_i = sum_p N_ip [m_p v_p + G_p (x_i - x_p)],
+ *          G_p = -(4/dx^2) dt V_p^0 P_p F_p^T + m_p C_p,  P_p = P(F_p) + F_p sigma_a
+ *   grid   v_i = p_i / m_i, then gravity and the boundary condition (sticky or slip, Supplement S5)
+ *   G2P    v_p = sum_i N_ip v_i,  C_p = (4/dx^2) sum_i N_ip v_i (x_i - x_p)^T,
+ *          F_p <- (I + dt C_p) F_p,  x_p <- x_p + dt v_p
+ * with N the quadratic B-spline, P(F) the compressible neo-Hookean stress and sigma_a the
+ * actuation stress a_g(t) Diag(dir_g) of the particle's group g.  The reverse pass implements
+ * Supplement S2-S5, (A)-(L), chained over a whole rollout (Section III, "memo").
+ *
+ * Conventions for every entry point:
+ *  - Every function returns mpm_status (0 = OK, < 0 = error); nothing throws or aborts across
+ *    the ABI.  Work is enqueued on the context's stream; device-side errors (a stencil leaving
+ *    the grid, det F <= 0, a tile over capacity) are recorded in the scene's status word, first
+ *    error wins, and reported by the next synchronising call (mpm_sync, mpm_get_state,
+ *    mpm_backward).  A scene with a recorded error keeps it until mpm_set_state.
+ *  - Arrays are row-major and FP32: positions and velocities [N][dim], C and F [N][dim][dim],
+ *    particle order as given at creation (results come back in the same order).
+ *  - mem_space 0 = host pointers, 1 = device pointers (e.g. torch tensors' data_ptr()).  Inputs
+ *    are copied; the caller keeps ownership of everything it passes in and of every output buffer.
+ *  - Node i of the grid sits at i*dx, i in [0, n) per axis.  A particle whose quadratic stencil
+ *    would leave [0, n) is an error, never clamped.
+ */
+#ifndef GBMPM_MPM_H_
+#define GBMPM_MPM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MPM_OK = 0,
+  MPM_ERR_ARG = -1,      /* invalid argument or descriptor */
+  MPM_ERR_OOM = -2,      /* device allocation failed or memory budget too small */
+  MPM_ERR_DOMAIN = -3,   /* a particle's stencil left the grid */
+  MPM_ERR_INVERTED = -4, /* det F <= 0 (neo-Hookean undefined) */
+  MPM_ERR_TIMEOUT = -5,  /* a bounded device wait ran out */
+  MPM_ERR_CUDA = -6,     /* a CUDA call failed */
+  MPM_ERR_STATE = -7,    /* call out of order (e.g. backward without a rollout) */
+  MPM_ERR_DENSITY = -8   /* more particles in one 4^3 / 8^2 cell tile than the kernels stage (4096) */
+} mpm_status;
+
+typedef struct mpm_ctx mpm_ctx;
+typedef struct mpm_scene mpm_scene;
+typedef struct mpm_batch mpm_batch;
+
+/* Creates a context on CUDA device `device`, enqueuing on `cuda_stream` (a cudaStream_t; NULL
+ * creates a private non-blocking stream). */
+mpm_status mpm_ctx_create(mpm_ctx** out, int device, void* cuda_stream);
+mpm_status mpm_ctx_destroy(mpm_ctx* ctx);
+/* Waits for the context's stream; returns the first CUDA error seen. */
+mpm_status mpm_sync(mpm_ctx* ctx);
+const char* mpm_status_str(mpm_status s);
+
+/* Controller families (Section V-B uses a = tanh(W z + b); these are its forms here):
+ *  MPM_CTRL_SIN   a_g(t) = A_g sin(2 pi f t)                               params [G]
+ *  MPM_CTRL_BASIS a_g(t) = sum_j W_gj b_j(t), b = [sin 2pi f t, cos 2pi f t, sin 4pi f t, cos 4pi f t]
+ *                                                                          params [G][4]
+ *  MPM_CTRL_MLP   z = centroid_g(x) - centroid_all(x) for every group (G*dim inputs),
+ *                 a = scale * tanh(W3 tanh(W2 tanh(W1 z + b1) + b2) + b3)  params W1[H][G*dim], b1[H],
+ *                                                                          W2[H][H], b2[H], W3[G][H], b3[G]
+ * with t = n * dt at the start of step n. */
+enum { MPM_CTRL_SIN = 0, MPM_CTRL_BASIS = 1, MPM_CTRL_MLP = 2 };
+enum { MPM_BC_STICKY = 0, MPM_BC_SLIP = 1 };
+enum { MPM_IMPL_TILED = 0, MPM_IMPL_PLAIN = 1 };
+
+typedef struct {
+  int dim;             /* 2 or 3 */
+  int n_grid[3];       /* nodes per axis (only the first dim used), each >= 5 */
+  float dx, dt;        /* cell size, time step; dt <= dx sqrt(rho/E) is required (Section VI) */
+  float gravity[3];
+  float E, nu;         /* Young's modulus > 0, Poisson ratio in (-1, 0.5) */
+  float p_mass, p_vol; /* m_p and V_p^0 of every particle (> 0) */
+  int bc_type;         /* MPM_BC_STICKY: v* = 0 on band nodes; MPM_BC_SLIP: S5 projection, friction c */
+  int bc_width;        /* band = nodes with an axis index < bc_width or >= n - bc_width */
+  float friction_c;    /* Coulomb coefficient c of S5 (slip only) */
+  int n_particles;     /* 0 <= N < 2^26 */
+  const float* x0;     /* [N][dim] */
+  const float* v0;     /* [N][dim], NULL = 0 */
+  const float* C0;     /* [N][dim][dim], NULL = 0 */
+  const float* F0;     /* [N][dim][dim], NULL = identity */
+  const int32_t* group;/* [N] actuation group of every particle, -1 = none; NULL = all -1 */
+  int n_groups;        /* 0 <= G <= 64 */
+  const float* act_dir;/* [G][dim] actuation direction: sigma_a = a_g Diag(dir_g) */
+  int ctrl_type;       /* MPM_CTRL_* */
+  int ctrl_hidden;     /* MLP width H <= 128 (MLP only); G*dim <= 192 */
+  float ctrl_freq;     /* f of the sinusoid forms */
+  float ctrl_scale;    /* output scale of the MLP */
+  int n_ctrl_params;   /* must equal the family's parameter count above */
+  const float* ctrl_params;
+  int impl;            /* MPM_IMPL_TILED (sorted, deterministic) or MPM_IMPL_PLAIN (atomics baseline) */
+  int mem_space;       /* where every pointer of this descriptor lives */
+} mpm_scene_desc;
+
+/* Creates a scene (Section III state: x, v, C, F per particle; grid per desc) at step 0.  Copies
+ * every input; the library owns the scene's device buffers until mpm_scene_destroy. */
+mpm_status mpm_scene_create(mpm_ctx* ctx, const mpm_scene_desc* desc, mpm_scene** out);
+mpm_status mpm_scene_destroy(mpm_scene* scene);
+
+/* Advances the current state by n_steps steps (Eqs. 3-10 with the controller's actuation),
+ * asynchronously on the context stream.  Keeps no history. */
+mpm_status mpm_step(mpm_scene* scene, int n_steps);
+
+/* Rollout for differentiation (Section III "memo"): n_steps steps from the current state,
+ * asynchronously; the checkpoint buffers are kept for the next rollout of the same shape.
+ * storing the state every ckpt_interval steps (0 = choose from mem_budget_bytes: every step if
+ * all states fit, else about sqrt(n_steps)); the states in between are recomputed by
+ * mpm_backward.  Fails with MPM_ERR_OOM if even the chosen interval exceeds the budget
+ * (mem_budget_bytes = 0 means no limit). */
+mpm_status mpm_rollout(mpm_scene* scene, int n_steps, int ckpt_interval, size_t mem_budget_bytes);
+
+/* Reverse pass of the last rollout (Supplement S2-S5 at every step, chained to the first state
+ * and to the controller parameters used at every step).  Seeds are dL/d(final x, v, C, F)
+ * (NULL = 0); outputs are dL/d(initial x, v, C, F) and dL/d(controller params) (NULL = not
+ * wanted).  Synchronises; returns the scene's first device error. */
+mpm_status mpm_backward(mpm_scene* scene, const float* gx_T, const float* gv_T, const float* gC_T,
+                        const float* gF_T, float* gx0, float* gv0, float* gC0, float* gF0,
+                        float* g_ctrl_params, int mem_space);
+
+/* Copies the state out (step -1 = current, else a checkpointed step of the last rollout).
+ * Synchronises; returns the scene's first device error. */
+mpm_status mpm_get_state(mpm_scene* scene, int step, float* x, float* v, float* C, float* F, int mem_space);
+/* Replaces the current state (NULL C = 0, NULL F = I, NULL v = 0) and clears the error status;
+ * optionally sets the step counter (step >= 0) that drives the controller's time.  Asynchronous:
+ * non-finite inputs are reported (MPM_ERR_ARG) by the next synchronising call. */
+mpm_status mpm_set_state(mpm_scene* scene, const float* x, const float* v, const float* C, const float* F,
+                         int step, int mem_space);
+/* Replaces the controller parameters (n must equal the scene's parameter count). */
+mpm_status mpm_set_ctrl_params(mpm_scene* scene, const float* params, int n, int mem_space);
+/* Grid of the last forward step: mass m_i [nodes] and velocity v*_i [nodes][dim] after the
+ * boundary condition (nodes never touched by a particle hold stale values for the tiled form). */
+mpm_status mpm_get_grid(mpm_scene* scene, float* m, float* v, int mem_space);
+/* Sizes: particles, groups, controller parameters, current step; bytes of one stored state. */
+mpm_status mpm_scene_info(const mpm_scene* scene, int* n_particles, int* n_groups, int* n_ctrl_params,
+                          int* step, size_t* state_bytes);
+
+/* Batched execution: scenes of one dimension advanced together by the same persistent launches
+ * (one scene table, per-scene offsets).  A batch holds references to scenes it does not own.
+ *  mpm_batch_create   empty batch of dimension dim on ctx, admitting scenes while their device
+ *                     memory fits mem_budget (0 = no limit)
+ *  mpm_batch_admit    adds a scene that will run n_steps more steps (and, with want_grad, its
+ *                     reverse pass, seeded by loss = mean of final x_0); *slot = -1 if full
+ *  mpm_batch_tick     advances every admitted scene by up to max_steps steps
+ *  mpm_batch_poll     *done = 1 when the slot's work is finished (results stay in the scene)
+ *  mpm_batch_release  frees a finished slot for the next admission */
+mpm_status mpm_batch_create(mpm_ctx* ctx, int dim, size_t mem_budget, mpm_batch** out);
+mpm_status mpm_batch_destroy(mpm_batch* batch);
+mpm_status mpm_batch_admit(mpm_batch* batch, mpm_scene* scene, int n_steps, int want_grad, int* slot);
+mpm_status mpm_batch_tick(mpm_batch* batch, int max_steps);
+mpm_status mpm_batch_poll(mpm_batch* batch, int slot, int* done);
+mpm_status mpm_batch_release(mpm_batch* batch, int slot);
+
+/* Instrumentation.  Kernel kinds for timing: */
+enum {
+  MPM_K_SORT = 0,       /* bin keys, tile histogram, scan, scatter */
+  MPM_K_P2G = 1,        /* tiled P2G (forward) */
+  MPM_K_GRID = 2,       /* grid normalisation, gravity, boundary */
+  MPM_K_G2P = 3,        /* tiled G2P + F, x update */
+  MPM_K_P2G_ADJ = 4,    /* P2G recompute fused with the adjoint scatter (A)-(C) */
+  MPM_K_GRID_ADJ = 5,   /* grid recompute with (L), (D), (E) */
+  MPM_K_ADJ_GATHER = 6, /* adjoint gather (F)-(K), (J) */
+  MPM_K_CTRL = 7,       /* controller forward/backward and group reductions */
+  MPM_K_PLAIN = 8,      /* the plain (atomic) form's step or reverse step */
+  MPM_K_COUNT = 9
+};
+/* Starts timing every launch of the kinds in `mask` (bit k = kind k) with CUDA events on the
+ * context stream, for at most max_launches launches; restarts the tally. */
+mpm_status mpm_profile_start(mpm_ctx* ctx, unsigned mask, int max_launches);
+/* Synchronises and returns the number of timed launches of `kind` and their summed duration. */
+mpm_status mpm_profile_read(mpm_ctx* ctx, int kind, int* count, double* total_ms);
+/* Total number of kernels this library has launched in the process (all contexts). */
+mpm_status mpm_launch_count(long long* count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBMPM_MPM_H_ */

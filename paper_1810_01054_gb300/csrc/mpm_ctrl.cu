@@ -1,0 +1,330 @@
+// Actuation controllers and their adjoints (Section V-B: a = tanh(W z + b) generating the
+// actuation of every group at every step), plus the deterministic per-group reductions they
+// need: group centroids of x (controller input) and per-group sums of dL/da (Supplement S4 (K)).
+//
+// Reductions are two-level with a fixed order at both levels (lanes own groups, warps combine in
+// warp order, rows combine in row order), so they are bitwise reproducible.
+#include "mpm_internal.h"
+
+namespace gbmpm {
+
+constexpr float kTwoPi = 6.283185307179586f;
+constexpr int RED_WARPS = 8;
+constexpr int RED_WR = 256;                       // particles per warp
+constexpr int RED_ROW = RED_WARPS * RED_WR;       // particles per partial row
+constexpr int RED_STRIDE = MAX_GROUPS * 3 + 3;    // floats per row: [64 groups][3] + body[3]
+
+int reduction_rows(int N) { return (N + RED_ROW - 1) / RED_ROW; }
+
+// mode 0: values = x (dim channels) and body sum; mode 1: values = sig_contrib (1 channel)
+template <int CH>
+__global__ void __launch_bounds__(256) k_group_rows(const ScenePar* __restrict__ dsp, float* __restrict__ rows,
+                                                    int mode) {
+  const ScenePar& sp = *dsp;
+  __shared__ float wacc[RED_WARPS][MAX_GROUPS][CH];
+  __shared__ float wbody[RED_WARPS][CH];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int start = blockIdx.x * RED_ROW + w * RED_WR;
+  float lo[CH], hi[CH], body[CH];
+#pragma unroll
+  for (int c = 0; c < CH; ++c) lo[c] = hi[c] = body[c] = 0.0f;
+  for (int k = 0; k < RED_WR; k += 32) {
+    const int p = start + k + lane;
+    int g = -1;
+    float val[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) val[c] = 0.0f;
+    if (p < sp.N) {
+      g = sp.group ? sp.group[p] : -1;
+      if (g >= sp.G) g = -1;
+      if (mode == 0) {
+        const float4 q = sp.planes[p];
+        const float xv[3] = {q.x, q.y, q.z};
+#pragma unroll
+        for (int c = 0; c < CH; ++c) val[c] = xv[c];
+      } else {
+        val[0] = sp.sig_contrib[p];
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < CH; ++c) body[c] += val[c];
+    for (int j = 0; j < 32; ++j) {
+      const int gj = __shfl_sync(0xffffffffu, g, j);
+      float vj[CH];
+#pragma unroll
+      for (int c = 0; c < CH; ++c) vj[c] = __shfl_sync(0xffffffffu, val[c], j);
+      if (gj >= 0 && (gj & 31) == lane) {
+        if (gj >> 5) {
+#pragma unroll
+          for (int c = 0; c < CH; ++c) hi[c] += vj[c];
+        } else {
+#pragma unroll
+          for (int c = 0; c < CH; ++c) lo[c] += vj[c];
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    wacc[w][lane][c] = lo[c];
+    wacc[w][lane + 32][c] = hi[c];
+    float b = body[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
+    if (lane == 0) wbody[w][c] = b;
+  }
+  __syncthreads();
+  float* row = rows + size_t(blockIdx.x) * RED_STRIDE;
+  for (int i = threadIdx.x; i < MAX_GROUPS * CH; i += blockDim.x) {
+    const int g = i / CH, c = i - g * CH;
+    float s = 0.0f;
+    for (int ww = 0; ww < RED_WARPS; ++ww) s += wacc[ww][g][c];
+    row[g * 3 + c] = s;
+  }
+  if (threadIdx.x < CH) {
+    float s = 0.0f;
+    for (int ww = 0; ww < RED_WARPS; ++ww) s += wbody[ww][threadIdx.x];
+    row[MAX_GROUPS * 3 + threadIdx.x] = s;
+  }
+}
+
+// Sum rows in a fixed order into out[g*3+c] (groups) and out[192+c] (body); 1024-thread CTA.
+__device__ void reduce_rows(const float* __restrict__ rows, int n_rows, int G, int CH, float* out) {
+  __shared__ float part[1024];
+  const int O = MAX_GROUPS * 3 + 3;  // outputs, some unused
+  const int S = blockDim.x / O;      // splits per output (5 with 1024 threads)
+  const int o = threadIdx.x % O, s = threadIdx.x / O;
+  float acc = 0.0f;
+  const bool used = s < S && ((o < MAX_GROUPS * 3 && (o / 3) < G && (o % 3) < CH) || (o >= MAX_GROUPS * 3 && (o - MAX_GROUPS * 3) < CH));
+  if (used)
+    for (int r = s; r < n_rows; r += S) acc += rows[size_t(r) * RED_STRIDE + o];
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x < O) {
+    float t = 0.0f;
+    for (int k = 0; k < S; ++k) t += part[k * O + threadIdx.x];
+    out[threadIdx.x] = t;
+  }
+  __syncthreads();
+}
+
+// ----------------------------------------------------------------------------- forward
+// Writes sp.act[g] for step n = *sp_step (then advances the scene's step counter).
+__global__ void __launch_bounds__(1024) k_ctrl_forward(const ScenePar* __restrict__ dsp, CtrlPar c, const float* rows,
+                                                       int n_rows, int* step_ctr, int advance) {
+  const ScenePar& sp = *dsp;
+  __shared__ float red[MAX_GROUPS * 3 + 3];
+  __shared__ float z[MAX_GROUPS * 3], h1[MAX_HIDDEN], h2[MAX_HIDDEN];
+  const int n = *step_ctr;
+  const float t = float(n) * sp.dt;
+  const int G = c.G, tid = threadIdx.x;
+  if (c.type == 0) {
+    if (tid < G) sp.act[tid] = c.params[tid] * sinf(kTwoPi * c.freq * t);
+  } else if (c.type == 1) {
+    if (tid < G) {
+      const float w = kTwoPi * c.freq * t;
+      const float bs[4] = {sinf(w), cosf(w), sinf(2.0f * w), cosf(2.0f * w)};
+      float a = 0.0f;
+      for (int j = 0; j < 4; ++j) a += c.params[tid * 4 + j] * bs[j];
+      sp.act[tid] = a;
+    }
+  } else {
+    const int dim = c.dim, Z = G * dim, H = c.hidden;
+    reduce_rows(rows, n_rows, G, dim, red);
+    if (tid < Z) {
+      const int g = tid / dim, a = tid - g * dim;
+      const float cg = red[g * 3 + a] * c.inv_count[g];
+      const float cb = red[MAX_GROUPS * 3 + a] * c.inv_n;
+      z[tid] = cg - cb;
+      c.centroid[tid] = cg;
+      if (tid < dim) c.centroid[Z + tid] = cb;
+    }
+    __syncthreads();
+    const float* W1 = c.params;
+    const float* b1 = W1 + H * Z;
+    const float* W2 = b1 + H;
+    const float* b2 = W2 + H * H;
+    const float* W3 = b2 + H;
+    const float* b3 = W3 + G * H;
+    if (tid < H) {
+      float u = b1[tid];
+      for (int j = 0; j < Z; ++j) u += W1[tid * Z + j] * z[j];
+      h1[tid] = tanhf(u);
+    }
+    __syncthreads();
+    if (tid < H) {
+      float u = b2[tid];
+      for (int j = 0; j < H; ++j) u += W2[tid * H + j] * h1[j];
+      h2[tid] = tanhf(u);
+    }
+    __syncthreads();
+    if (tid < G) {
+      float u = b3[tid];
+      for (int j = 0; j < H; ++j) u += W3[tid * H + j] * h2[j];
+      sp.act[tid] = c.scale * tanhf(u);
+    }
+  }
+  __syncthreads();
+  if (tid == 0 && advance) *step_ctr = n + 1;
+}
+
+// ----------------------------------------------------------------------------- backward
+// dL/da_g = sum over the group of the (K) contributions; accumulate dL/dparams for step n;
+// for the MLP also dL/dz, turned into per-group coefficients for the x adjoint.
+__global__ void __launch_bounds__(1024) k_ctrl_backward(const ScenePar* __restrict__ dsp, CtrlPar c,
+                                                        const float* rows, int n_rows, int* step_ctr) {
+  const ScenePar& sp = *dsp;
+  __shared__ float red[MAX_GROUPS * 3 + 3];
+  __shared__ float ga[MAX_GROUPS], z[MAX_GROUPS * 3], h1[MAX_HIDDEN], h2[MAX_HIDDEN], o3[MAX_GROUPS];
+  __shared__ float gu3[MAX_GROUPS], gu2[MAX_HIDDEN], gu1[MAX_HIDDEN];
+  const int n = *step_ctr;
+  const float t = float(n) * sp.dt;
+  const int G = c.G, tid = threadIdx.x;
+  reduce_rows(rows, n_rows, G, 1, red);
+  if (tid < G) {
+    ga[tid] = red[tid * 3];
+    sp.act_grad[tid] = ga[tid];
+  }
+  __syncthreads();
+  if (c.type == 0) {
+    if (tid < G) c.gparams[tid] += ga[tid] * sinf(kTwoPi * c.freq * t);
+  } else if (c.type == 1) {
+    if (tid < G * 4) {
+      const int g = tid / 4, j = tid - 4 * g;
+      const float w = kTwoPi * c.freq * t;
+      const float bs[4] = {sinf(w), cosf(w), sinf(2.0f * w), cosf(2.0f * w)};
+      c.gparams[tid] += ga[g] * bs[j];
+    }
+  } else {
+    const int dim = c.dim, Z = G * dim, H = c.hidden;
+    const float* W1 = c.params;
+    const float* b1 = W1 + H * Z;
+    const float* W2 = b1 + H;
+    const float* b2 = W2 + H * H;
+    const float* W3 = b2 + H;
+    const float* b3 = W3 + G * H;
+    float* gW1 = c.gparams;
+    float* gb1 = gW1 + H * Z;
+    float* gW2 = gb1 + H;
+    float* gb2 = gW2 + H * H;
+    float* gW3 = gb2 + H;
+    float* gb3 = gW3 + G * H;
+    // forward replay from the centroids of this step (written by k_ctrl_forward)
+    if (tid < Z) z[tid] = c.centroid[tid] - c.centroid[Z + tid % dim];
+    __syncthreads();
+    if (tid < H) {
+      float u = b1[tid];
+      for (int j = 0; j < Z; ++j) u += W1[tid * Z + j] * z[j];
+      h1[tid] = tanhf(u);
+    }
+    __syncthreads();
+    if (tid < H) {
+      float u = b2[tid];
+      for (int j = 0; j < H; ++j) u += W2[tid * H + j] * h1[j];
+      h2[tid] = tanhf(u);
+    }
+    __syncthreads();
+    if (tid < G) {
+      float u = b3[tid];
+      for (int j = 0; j < H; ++j) u += W3[tid * H + j] * h2[j];
+      o3[tid] = tanhf(u);
+      gu3[tid] = ga[tid] * c.scale * (1.0f - o3[tid] * o3[tid]);
+      gb3[tid] += gu3[tid];
+    }
+    __syncthreads();
+    for (int i = tid; i < G * H; i += blockDim.x) gW3[i] += gu3[i / H] * h2[i % H];
+    if (tid < H) {
+      float s = 0.0f;
+      for (int g = 0; g < G; ++g) s += gu3[g] * W3[g * H + tid];
+      gu2[tid] = s * (1.0f - h2[tid] * h2[tid]);
+      gb2[tid] += gu2[tid];
+    }
+    __syncthreads();
+    for (int i = tid; i < H * H; i += blockDim.x) gW2[i] += gu2[i / H] * h1[i % H];
+    if (tid < H) {
+      float s = 0.0f;
+      for (int i = 0; i < H; ++i) s += gu2[i] * W2[i * H + tid];
+      gu1[tid] = s * (1.0f - h1[tid] * h1[tid]);
+      gb1[tid] += gu1[tid];
+    }
+    __syncthreads();
+    for (int i = tid; i < H * Z; i += blockDim.x) gW1[i] += gu1[i / Z] * z[i % Z];
+    if (tid < Z) {
+      float s = 0.0f;
+      for (int i = 0; i < H; ++i) s += gu1[i] * W1[i * Z + tid];
+      c.gz[tid] = s;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) *step_ctr = n - 1;
+}
+
+// x adjoint of the MLP input: z_g = c_g - c_body, c_g = mean of x over g, c_body = mean over all.
+template <int D>
+__global__ void k_ctrl_scatter_x(const ScenePar* __restrict__ dsp, CtrlPar c) {
+  const ScenePar& sp = *dsp;
+  __shared__ float coef[MAX_GROUPS * 3], body[3];
+  const int G = c.G;
+  for (int i = threadIdx.x; i < G * D; i += blockDim.x) coef[i] = c.gz[i] * c.inv_count[i / D];
+  if (threadIdx.x < D) {
+    float s = 0.0f;
+    for (int g = 0; g < G; ++g) s += c.gz[g * D + threadIdx.x];
+    body[threadIdx.x] = -s * c.inv_n;
+  }
+  __syncthreads();
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= sp.N) return;
+  const int g = sp.group ? sp.group[p] : -1;
+  float4 q = sp.adj_out[p];
+  float add[3] = {body[0], body[1], D == 3 ? body[D == 3 ? 2 : 0] : 0.0f};
+  if (g >= 0 && g < G) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) add[a] += coef[g * D + a];
+  }
+  q.x += add[0];
+  q.y += add[1];
+  if (D == 3) q.z += add[2];
+  sp.adj_out[p] = q;
+}
+
+// Controller forward for one step: (MLP: centroid rows first), then act; advances *step_ctr.
+cudaError_t ctrl_step_forward(const ScenePar& sp, const ScenePar* dsp, const CtrlPar& c, int* step_ctr, int advance,
+                              cudaStream_t s) {
+  if (c.G == 0) {
+    if (advance) {
+      k_ctrl_forward<<<1, 32, 0, s>>>(dsp, c, nullptr, 0, step_ctr, advance);
+      count_launches(1);
+    }
+    return cudaGetLastError();
+  }
+  int rows = 0;
+  if (c.type == 2) {
+    rows = reduction_rows(sp.N);
+    if (sp.dim == 2)
+      k_group_rows<2><<<rows, 256, 0, s>>>(dsp, c.partials, 0);
+    else
+      k_group_rows<3><<<rows, 256, 0, s>>>(dsp, c.partials, 0);
+  }
+  k_ctrl_forward<<<1, 1024, 0, s>>>(dsp, c, c.partials, rows, step_ctr, advance);
+  count_launches(c.type == 2 ? 2 : 1);
+  return cudaGetLastError();
+}
+
+// Controller backward for one reverse step: group sums of (K), parameter adjoint, and (MLP) the
+// centroid adjoint added to dL/dx of state n.  Decrements *step_ctr.
+cudaError_t ctrl_step_backward(const ScenePar& sp, const ScenePar* dsp, const CtrlPar& c, int* step_ctr,
+                               cudaStream_t s) {
+  int rows = reduction_rows(sp.N);
+  if (c.G > 0 && rows > 0) k_group_rows<1><<<rows, 256, 0, s>>>(dsp, c.partials, 1);
+  k_ctrl_backward<<<1, 1024, 0, s>>>(dsp, c, c.partials, c.G > 0 ? rows : 0, step_ctr);
+  count_launches(1 + ((c.G > 0 && rows > 0) ? 1 : 0) + ((c.type == 2 && c.G > 0 && sp.N > 0) ? 1 : 0));
+  if (c.type == 2 && c.G > 0 && sp.N > 0) {
+    if (sp.dim == 2)
+      k_ctrl_scatter_x<2><<<(sp.N + 255) / 256, 256, 0, s>>>(dsp, c);
+    else
+      k_ctrl_scatter_x<3><<<(sp.N + 255) / 256, 256, 0, s>>>(dsp, c);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace gbmpm

@@ -1,0 +1,387 @@
+// Device-side math of the differentiable MLS-MPM step (ChainQueen, arXiv 1810.01054), FP32.
+//
+// Per-particle pieces used by every kernel of the library: the quadratic B-spline stencil and
+// its gradient, the neo-Hookean stress and its Hessian product (Section III and Supplement S4
+// (H)), the MLS momentum matrix G of Eq. 4, the boundary projection of Supplement S5 (L) and its
+// adjoint.  Layout helpers for the SoA float4 state planes live here too.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gbmpm {
+
+// --------------------------------------------------------------------------- configuration
+// Tiles: a CTA owns a block of B^D cells ("tile"); particles are binned by the cell of their
+// stencil base, and a tile's particles touch the (B+2)^D node block starting at the tile origin.
+template <int D>
+struct Cfg;
+template <>
+struct Cfg<2> {
+  static constexpr int B = 8;             // tile edge in cells
+  static constexpr int CELLS = 64;        // cells per tile
+  static constexpr int BN = 10;           // node-block edge (B + 2)
+  static constexpr int BLOCK_NODES = 100; // nodes per block
+  static constexpr int S = 12;            // floats per particle state: x(2) F(4) v(2) C(4)
+  static constexpr int PLANES = 3;        // float4 planes per particle
+  static constexpr int XF_PLANES = 2;     // planes holding x and F (what G2P reads)
+  static constexpr int STENCIL = 9;
+};
+template <>
+struct Cfg<3> {
+  static constexpr int B = 4;
+  static constexpr int CELLS = 64;
+  static constexpr int BN = 6;
+  static constexpr int BLOCK_NODES = 216;
+  static constexpr int S = 24;            // x(3) F(9) v(3) C(9)
+  static constexpr int PLANES = 6;
+  static constexpr int XF_PLANES = 3;
+  static constexpr int STENCIL = 27;
+};
+
+// Status codes written to the per-scene device status word (first error wins).
+enum : int {
+  ST_OK = 0,
+  ST_DOMAIN = -3,    // a stencil left the grid
+  ST_INVERTED = -4,  // det F <= 0
+  ST_TIMEOUT = -5,   // a bounded device wait ran out
+  ST_DENSITY = -8,   // more particles in one tile than the tile kernels stage
+};
+
+__device__ __forceinline__ void set_status(int* st, int code) {
+  if (st) atomicCAS(st, 0, code);
+}
+
+// --------------------------------------------------------------------------- particle record
+// One particle's state in the order x, F, v, C (row-major matrices).  The four-float planes of
+// the state arrays are consecutive chunks of this record, so the first XF_PLANES planes hold
+// exactly the inputs of G2P (x and F).
+template <int D>
+struct Part {
+  float x[D];
+  float F[D][D];
+  float v[D];
+  float C[D][D];
+};
+
+template <int D>
+__device__ __forceinline__ void unpack(const float* r, Part<D>& q) {
+  int o = 0;
+#pragma unroll
+  for (int a = 0; a < D; ++a) q.x[a] = r[o++];
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int b = 0; b < D; ++b) q.F[a][b] = r[o++];
+#pragma unroll
+  for (int a = 0; a < D; ++a) q.v[a] = r[o++];
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int b = 0; b < D; ++b) q.C[a][b] = r[o++];
+}
+
+template <int D>
+__device__ __forceinline__ void pack(const Part<D>& q, float* r) {
+  int o = 0;
+#pragma unroll
+  for (int a = 0; a < D; ++a) r[o++] = q.x[a];
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int b = 0; b < D; ++b) r[o++] = q.F[a][b];
+#pragma unroll
+  for (int a = 0; a < D; ++a) r[o++] = q.v[a];
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int b = 0; b < D; ++b) r[o++] = q.C[a][b];
+}
+
+// Load the first `np` planes of particle p (plane j of the array starts at planes + j*npad).
+template <int D, int NP>
+__device__ __forceinline__ void load_planes(const float4* __restrict__ planes, int npad, int p, float* r) {
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    float4 q = __ldg(planes + size_t(j) * npad + p);
+    r[4 * j + 0] = q.x;
+    r[4 * j + 1] = q.y;
+    r[4 * j + 2] = q.z;
+    r[4 * j + 3] = q.w;
+  }
+}
+
+template <int D, int NP>
+__device__ __forceinline__ void store_planes(float4* __restrict__ planes, int npad, int p, const float* r) {
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    planes[size_t(j) * npad + p] = make_float4(r[4 * j + 0], r[4 * j + 1], r[4 * j + 2], r[4 * j + 3]);
+  }
+}
+
+// --------------------------------------------------------------------------- small matrices
+template <int D>
+__device__ __forceinline__ float det(const float (&F)[D][D]) {
+  if constexpr (D == 2) {
+    return F[0][0] * F[1][1] - F[0][1] * F[1][0];
+  } else {
+    return F[0][0] * (F[1][1] * F[2][2] - F[1][2] * F[2][1]) - F[0][1] * (F[1][0] * F[2][2] - F[1][2] * F[2][0]) +
+           F[0][2] * (F[1][0] * F[2][1] - F[1][1] * F[2][0]);
+  }
+}
+
+// F^{-T} from the cofactor matrix: (F^{-T})_{ij} = cof(F)_{ij} / det F.
+template <int D>
+__device__ __forceinline__ void inv_transpose(const float (&F)[D][D], float J, float (&A)[D][D]) {
+  float rJ = 1.0f / J;
+  if constexpr (D == 2) {
+    A[0][0] = F[1][1] * rJ;
+    A[0][1] = -F[1][0] * rJ;
+    A[1][0] = -F[0][1] * rJ;
+    A[1][1] = F[0][0] * rJ;
+  } else {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+        A[i][j] = (F[i1][j1] * F[i2][j2] - F[i1][j2] * F[i2][j1]) * rJ;
+      }
+  }
+}
+
+// --------------------------------------------------------------------------- stencil
+// Quadratic B-spline: per axis base = floor(x/dx - 0.5), f = x/dx - base in [0.5, 1.5); node
+// base+k has weight w_k(f) and dw_k = d w_k / d x_p.
+template <int D>
+struct Sten {
+  int base[D];
+  float f[D];
+  float w[D][3];
+  float dw[D][3];
+};
+
+template <int D>
+__device__ __forceinline__ bool stencil_base(const float* x, float inv_dx, const int* n, int* base, float* f) {
+  bool ok = true;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    float xs = x[a] * inv_dx;
+    float b = floorf(xs - 0.5f);
+    ok = ok && (b >= 0.0f) && (b <= float(n[a] - 3));
+    base[a] = ok ? int(b) : 0;
+    f[a] = xs - b;
+  }
+  return ok;
+}
+
+__device__ __forceinline__ void bspline(float f, float inv_dx, float* w, float* dw) {
+  float t0 = 1.5f - f, t1 = f - 1.0f, t2 = f - 0.5f;
+  w[0] = 0.5f * t0 * t0;
+  w[1] = 0.75f - t1 * t1;
+  w[2] = 0.5f * t2 * t2;
+  dw[0] = -t0 * inv_dx;
+  dw[1] = -2.0f * t1 * inv_dx;
+  dw[2] = t2 * inv_dx;
+}
+
+template <int D>
+__device__ __forceinline__ bool make_stencil(const float* x, float inv_dx, const int* n, Sten<D>& s) {
+  bool ok = stencil_base<D>(x, inv_dx, n, s.base, s.f);
+#pragma unroll
+  for (int a = 0; a < D; ++a) bspline(s.f[a], inv_dx, s.w[a], s.dw[a]);
+  return ok;
+}
+
+// --------------------------------------------------------------------------- constitutive
+struct Material {
+  float mu, la;
+};
+
+// P = mu (F - F^{-T}) + lambda ln J F^{-T} + F sigma_a, sigma_a = a Diag(dir).
+// Returns J (caller checks J > 0 before trusting P).
+template <int D>
+__device__ __forceinline__ float stress(const float (&F)[D][D], Material m, const float* sig_diag, float (&P)[D][D],
+                                        float (&A)[D][D]) {
+  float J = det<D>(F);
+  float Js = J > 0.0f ? J : 1.0f;
+  inv_transpose<D>(F, Js, A);
+  float lJ = logf(Js);
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) P[i][j] = m.mu * (F[i][j] - A[i][j]) + m.la * lJ * A[i][j] + F[i][j] * sig_diag[j];
+  return J;
+}
+
+// G = -(4/dx^2) dt V0 P F^T + m C  (Eq. 4)
+template <int D>
+__device__ __forceinline__ void mls_G(const float (&P)[D][D], const float (&F)[D][D], const float (&C)[D][D], float kG,
+                                      float mass, float (&G)[D][D]) {
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      float s = 0.0f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) s += P[i][k] * F[j][k];
+      G[i][j] = kG * s + mass * C[i][j];
+    }
+}
+
+// mu Pbar + (mu - lambda ln J) F^{-T} Pbar^T F^{-T} + lambda (F^{-T}:Pbar) F^{-T}
+template <int D>
+__device__ __forceinline__ void nh_hessian_apply(const float (&A)[D][D], float J, Material m, const float (&Pb)[D][D],
+                                                 float (&R)[D][D]) {
+  float lJ = logf(J > 0.0f ? J : 1.0f);
+  float AP = 0.0f;
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) AP += A[i][j] * Pb[i][j];
+  float T[D][D];  // A Pb^T
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      float s = 0.0f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) s += A[i][k] * Pb[j][k];
+      T[i][j] = s;
+    }
+  float c = m.mu - m.la * lJ;
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      float s = 0.0f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) s += T[i][k] * A[k][j];
+      R[i][j] = m.mu * Pb[i][j] + c * s + m.la * AP * A[i][j];
+    }
+}
+
+// --------------------------------------------------------------------------- boundary (S5)
+struct BCPar {
+  int type;   // 0 sticky, 1 slip with friction c
+  int width;  // band width in nodes
+  float c;
+};
+
+constexpr float kBCEps = 1e-20f;
+
+template <int D>
+__device__ __forceinline__ bool in_band(const int* idx, const int* n, int b) {
+  bool r = false;
+#pragma unroll
+  for (int a = 0; a < D; ++a) r = r || idx[a] < b || idx[a] >= n[a] - b;
+  return r;
+}
+
+// One wall: v <- l_t* v_t / l_t + max(l_n, 0) n, l_t* = max(l_t + c min(l_n, 0), 0).
+template <int D>
+__device__ __forceinline__ void project(float* v, int axis, float sgn, float c) {
+  float ln = v[axis] * sgn;
+  float vt[D];
+  float lt2 = 0.0f;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    vt[a] = v[a] - (a == axis ? ln * sgn : 0.0f);
+    lt2 += vt[a] * vt[a];
+  }
+  float lt = sqrtf(lt2 + kBCEps);
+  float R = lt + c * fminf(ln, 0.0f);
+  float lts = fmaxf(R, 0.0f);
+  float s = lts / lt;
+#pragma unroll
+  for (int a = 0; a < D; ++a) v[a] = s * vt[a] + (a == axis ? fmaxf(ln, 0.0f) * sgn : 0.0f);
+}
+
+// Adjoint of `project` at input v (forward value recomputed here), g in/out.
+template <int D>
+__device__ __forceinline__ void project_adj(const float* v, int axis, float sgn, float c, float* g) {
+  float ln = v[axis] * sgn;
+  float vt[D];
+  float lt2 = 0.0f;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    vt[a] = v[a] - (a == axis ? ln * sgn : 0.0f);
+    lt2 += vt[a] * vt[a];
+  }
+  float lt = sqrtf(lt2 + kBCEps);
+  float R = lt + c * fminf(ln, 0.0f);
+  float lts = fmaxf(R, 0.0f);
+  float rlt = 1.0f / lt;
+  float g_lts = 0.0f, s = 0.0f, gn = g[axis] * sgn;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    g_lts += g[a] * vt[a] * rlt;
+    s += vt[a] * g[a] * lts;  // v_t . vhat_bar with vhat_bar = g l_t*
+  }
+  float HR = R >= 0.0f ? 1.0f : 0.0f;
+  float g_lt = -s * rlt * rlt + g_lts * HR;
+  float gvt[D];
+  float vtn = 0.0f;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    gvt[a] = (g_lt * vt[a] + g[a] * lts) * rlt;
+    vtn += (a == axis ? gvt[a] * sgn : 0.0f);
+  }
+  float g_ln = -vtn + g_lts * HR * c * (ln <= 0.0f ? 1.0f : 0.0f) + (ln >= 0.0f ? 1.0f : 0.0f) * gn;
+#pragma unroll
+  for (int a = 0; a < D; ++a) g[a] = gvt[a] + (a == axis ? g_ln * sgn : 0.0f);
+}
+
+// Boundary condition on the node velocity (gravity already added).  Walls of a slip node are
+// applied in sequence: axis 0, 1, 2, low side before high side.
+template <int D>
+__device__ __forceinline__ void bc_apply(const int* idx, const int* n, BCPar bc, float* v) {
+  if (!in_band<D>(idx, n, bc.width)) return;
+  if (bc.type == 0) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) v[a] = 0.0f;
+    return;
+  }
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    if (idx[a] < bc.width) project<D>(v, a, 1.0f, bc.c);
+    if (idx[a] >= n[a] - bc.width) project<D>(v, a, -1.0f, bc.c);
+  }
+}
+
+// Adjoint of bc_apply: g holds dL/dv* on entry and dL/dv_g on exit; vg = velocity before BC.
+template <int D>
+__device__ __forceinline__ void bc_adjoint(const int* idx, const int* n, BCPar bc, const float* vg, float* g) {
+  if (!in_band<D>(idx, n, bc.width)) return;
+  if (bc.type == 0) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) g[a] = 0.0f;
+    return;
+  }
+  // replay the wall sequence to get every wall's input, then walk it backwards
+  float vin[2 * D][D];
+  int axis[2 * D];
+  float sg[2 * D];
+  int nw = 0;
+  float v[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) v[a] = vg[a];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      bool hit = side == 0 ? idx[a] < bc.width : idx[a] >= n[a] - bc.width;
+      if (hit) {
+#pragma unroll
+        for (int b = 0; b < D; ++b) vin[nw][b] = v[b];
+        axis[nw] = a;
+        sg[nw] = side == 0 ? 1.0f : -1.0f;
+        project<D>(v, a, sg[nw], bc.c);
+        ++nw;
+      }
+    }
+  }
+  for (int w = nw - 1; w >= 0; --w) project_adj<D>(vin[w], axis[w], sg[w], bc.c, g);
+}
+
+}  // namespace gbmpm

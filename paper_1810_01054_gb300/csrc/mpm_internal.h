@@ -1,0 +1,129 @@
+// Internal structures shared by the kernel and C-ABI translation units of libgbmpm.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "mpm_device.cuh"
+
+namespace gbmpm {
+
+// Kernels launched by this library (process-wide tally, read by mpm_launch_count).
+void count_launches(int n);
+long long launch_total();
+
+constexpr uint32_t KEY_INVALID = 0xffffffffu;
+constexpr int SORT_CAP = 4096;  // most particles one tile may hold (tile kernels stage its list)
+constexpr int MAX_GROUPS = 64;  // actuation groups per scene
+constexpr int MAX_HIDDEN = 128; // controller MLP width
+
+// Per-scene parameters and device pointers, as the kernels see them (one entry per scene of
+// a launch).  Particle state stays in the caller's particle order for the scene's lifetime.
+struct ScenePar {
+  int dim;
+  int n[3];
+  float dx, inv_dx, dt;
+  float gravity[3];
+  Material mat;
+  float mass, vol;
+  BCPar bc;
+  int N, npad;      // particles, plane stride (N rounded up)
+  int G;            // actuation groups
+  int nt[3];        // tiles per axis
+  int n_tiles;      // product of nt
+  int tile_base;    // first batch-global tile id of this scene
+  int pbase;        // first batch-global particle slot of this scene
+  int step;         // global step index of the state being advanced (t_n = step*dt)
+  float4* planes;   // state planes [PLANES][npad] read by the step
+  float4* planes_out;  // where G2P writes state n+1 (== planes for an in-place step)
+  const float4* adj_in;   // adjoint planes of state n+1 (reverse step)
+  float4* adj_out;        // adjoint planes of state n  (reverse step)
+  uint32_t* key;          // [N] tile << 6 | cell-in-tile, KEY_INVALID if the stencil left the grid
+  float4* grid;           // [nodes] (v*, m) after the boundary condition
+  float4* grid_b;         // [nodes] reverse: (pbar, mbar)
+  const int32_t* group;   // [N]
+  const float* act_dir;   // [G][dim]
+  float* act;             // [G] actuation of the current step
+  float* act_grad;        // [G] dL/da of the current reverse step
+  float* sig_contrib;     // [N] per-particle part of dL/da (S4 (K))
+  int* status;            // first-error status word
+};
+
+// One batch of scenes of equal dimension that advance together.
+struct BatchDev {
+  ScenePar* scenes;     // device [n_scenes]
+  int n_scenes;
+  int* scene_pbase;     // device [n_scenes + 1] prefix of particle counts
+  int* tile_scene;      // device [total_tiles] owning scene of every batch tile
+  int total_particles;
+  int total_tiles;
+  uint32_t* tile_count; // [total_tiles], zero between steps
+  uint32_t* tile_fill;  // [total_tiles], zero between steps
+  uint32_t* tile_start; // [total_tiles + 1]
+  int* tile_slot;       // [total_tiles] active-slot of the tile or -1
+  int* active;          // [total_tiles] batch tile id of every active slot
+  int* n_active;        // [1]
+  uint32_t* block_sums; // scan scratch
+  uint32_t* sorted;     // [total_particles] scene-local particle ids, tile-major, canonical
+  float4* partial;      // [total_tiles * BLOCK_NODES] node blocks of P2G
+  float4* partial_b;    // [total_tiles * BLOCK_NODES] node blocks of the adjoint scatter
+  int max_ctas;         // persistent-grid size for the tile kernels
+  int p2g_block;        // threads per CTA of the tile kernels (autotuned)
+};
+
+// ---------------------------------------------------------------------------- launchers
+// Tiled (sorted, deterministic) form.
+template <int D>
+cudaError_t launch_keys(const BatchDev& b, cudaStream_t s);
+template <int D>
+cudaError_t launch_sort(const BatchDev& b, cudaStream_t s);
+template <int D>
+cudaError_t launch_p2g(const BatchDev& b, bool with_adjoint, cudaStream_t s);
+template <int D>
+cudaError_t launch_grid(const BatchDev& b, bool with_adjoint, cudaStream_t s);
+template <int D>
+cudaError_t launch_g2p(const BatchDev& b, cudaStream_t s);
+template <int D>
+cudaError_t launch_adj_gather(const BatchDev& b, cudaStream_t s);
+
+// Plain form (one scene, global atomics, dense grid): the baseline the tiled form is measured against.
+template <int D>
+cudaError_t launch_plain_step(const ScenePar* dev_scene, const ScenePar& host_scene, cudaStream_t s);
+template <int D>
+cudaError_t launch_plain_adjoint(const ScenePar* dev_scene, const ScenePar& host_scene, cudaStream_t s);
+
+// Controllers.  ctrl_* describe one scene's controller.
+struct CtrlPar {
+  int type;        // 0 sinusoid amplitude, 1 sinusoid basis, 2 MLP on group centroids
+  int G, dim, hidden;
+  float freq, scale;
+  const float* params;   // device
+  float* gparams;        // device, accumulated by the reverse pass
+  const float* inv_count;  // device [G] 1/|g| (0 for empty groups)
+  float inv_n;            // 1/N
+  float* centroid;        // device [G*dim + dim] scratch: group centroids then body centroid
+  float* gz;              // device [G*dim] scratch: dL/dz of the MLP input
+  float* partials;        // device scratch for the deterministic group reductions
+  int n_partials;         // number of reduction partial rows available
+};
+
+int reduction_rows(int N);                  // partial rows of the group reductions
+constexpr int RED_ROW_FLOATS = MAX_GROUPS * 3 + 3;  // floats per partial row
+// Controller forward for the step *step_ctr (advancing it when `advance`), and the reverse of
+// the step *step_ctr (decrementing it afterwards).
+cudaError_t ctrl_step_forward(const ScenePar& sp, const ScenePar* dsp, const CtrlPar& c, int* step_ctr, int advance,
+                              cudaStream_t s);
+cudaError_t ctrl_step_backward(const ScenePar& sp, const ScenePar* dsp, const CtrlPar& c, int* step_ctr,
+                               cudaStream_t s);
+
+// *p = v on the stream (kernel argument, so no host buffer outlives the call).
+cudaError_t launch_set_int(int* p, int v, cudaStream_t s);
+
+// Layout conversions between row-major [N][d], [N][d][d] arrays and the state planes.
+cudaError_t launch_pack(int dim, int N, int npad, const float* x, const float* v, const float* C, const float* F,
+                        float4* planes, int* status, cudaStream_t s);
+cudaError_t launch_unpack(int dim, int N, int npad, const float4* planes, float* x, float* v, float* C, float* F,
+                          cudaStream_t s);
+
+}  // namespace gbmpm

@@ -1,0 +1,1340 @@
+// sm_103a kernels of the differentiable MLS-MPM step (ChainQueen, arXiv 1810.01054).
+//
+// Forward step (Section III, Eqs. 3-10), tiled form:
+//   k_hist / scan / k_scatter : bin particles by the tile of their stencil base cell
+//   k_p2g                     : per tile, canonical (cell, id) order, per-particle stress and
+//                               MLS matrix G (Eq. 4), per-cell register accumulation of the
+//                               3^d stencil (Eqs. 3, 5), fixed-order reduction into the tile's
+//                               (B+2)^d node block -- no atomics on floating point anywhere
+//   k_grid                    : sums the <= 2^d node blocks covering each node in a fixed order,
+//                               Eq. 6, gravity, boundary (S5)
+//   k_g2p                     : per tile, node block staged in shared memory, Eqs. 7-10 and the
+//                               next step's bin key
+// Reverse step (Supplement S2-S5): k_p2g also scatters (C) from (A), (B) in the same pass; k_grid
+// applies (L), (D), (E); k_adj_gather evaluates (F)-(K), (J).
+//
+// Every floating-point sum has a fixed order, so results are bitwise reproducible run to run and
+// independent of which other scenes share the launch.
+#include <atomic>
+#include <cstdio>
+
+#include "mpm_internal.h"
+
+namespace gbmpm {
+
+static std::atomic<long long> g_launches{0};
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launch_total() { return g_launches.load(std::memory_order_relaxed); }
+
+// ============================================================================ helpers
+__device__ __forceinline__ int find_scene(const int* __restrict__ pbase, int n_scenes, int gp) {
+  int lo = 0, hi = n_scenes - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (__ldg(pbase + mid) <= gp)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int D>
+__device__ __forceinline__ int lin3(const int* c, const int* n) {
+  int l = 0;
+#pragma unroll
+  for (int a = 0; a < D; ++a) l = l * n[a] + c[a];
+  return l;
+}
+
+template <int D>
+__device__ __forceinline__ void unlin(int l, const int* n, int* c) {
+#pragma unroll
+  for (int a = D - 1; a >= 0; --a) {
+    c[a] = l % n[a];
+    l /= n[a];
+  }
+}
+
+template <int D>
+__device__ __forceinline__ int cell_lin(const int* c) {
+  constexpr int B = Cfg<D>::B;
+  int l = 0;
+#pragma unroll
+  for (int a = 0; a < D; ++a) l = l * B + c[a];
+  return l;
+}
+
+// Bin key of a particle at x: (scene-local tile << 6) | cell within the tile.
+template <int D>
+__device__ __forceinline__ uint32_t bin_key(const float* x, const ScenePar& sp) {
+  constexpr int B = Cfg<D>::B;
+  int base[D];
+  float f[D];
+  if (!stencil_base<D>(x, sp.inv_dx, sp.n, base, f)) {
+    set_status(sp.status, ST_DOMAIN);
+    return KEY_INVALID;
+  }
+  int t[D], c[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    t[a] = base[a] / B;
+    c[a] = base[a] - t[a] * B;
+  }
+  return (uint32_t(lin3<D>(t, sp.nt)) << 6) | uint32_t(cell_lin<D>(c));
+}
+
+// Actuation stress diagonal of particle id: sigma_a = a_g Diag(dir_g) (Section III).
+template <int D>
+__device__ __forceinline__ void actuation(const ScenePar& sp, int id, float* sig) {
+  int g = sp.group ? __ldg(sp.group + id) : -1;
+  float a = (g >= 0 && g < sp.G) ? __ldg(sp.act + g) : 0.0f;
+#pragma unroll
+  for (int k = 0; k < D; ++k) sig[k] = (g >= 0 && g < sp.G) ? a * __ldg(sp.act_dir + g * D + k) : 0.0f;
+}
+
+// Per-particle quantities of P2G: stress with actuation and G of Eq. 4.  Returns J.
+template <int D>
+__device__ __forceinline__ float particle_G(const Part<D>& q, const ScenePar& sp, int id, float (&P)[D][D],
+                                            float (&A)[D][D], float (&G)[D][D], float* sig) {
+  actuation<D>(sp, id, sig);
+  float J = stress<D>(q.F, sp.mat, sig, P, A);
+  float kG = -4.0f * sp.inv_dx * sp.inv_dx * sp.dt * sp.vol;
+  mls_G<D>(P, q.F, q.C, kG, sp.mass, G);
+  return J;
+}
+
+// ============================================================================ keys / sort
+template <int D>
+__global__ void k_keys(BatchDev b) {
+  int gp = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gp >= b.total_particles) return;
+  const ScenePar& sp = b.scenes[find_scene(b.scene_pbase, b.n_scenes, gp)];
+  int p = gp - sp.pbase;
+  float4 q = sp.planes[p];
+  float x[3] = {q.x, q.y, q.z};
+  sp.key[p] = bin_key<D>(x, sp);
+}
+
+template <int D>
+__global__ void k_hist(BatchDev b) {
+  int gp = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gp >= b.total_particles) return;
+  const ScenePar& sp = b.scenes[find_scene(b.scene_pbase, b.n_scenes, gp)];
+  uint32_t k = sp.key[gp - sp.pbase];
+  if (k != KEY_INVALID) atomicAdd(b.tile_count + sp.tile_base + (k >> 6), 1u);
+}
+
+template <int D>
+__global__ void k_scatter(BatchDev b) {
+  int gp = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gp >= b.total_particles) return;
+  const ScenePar& sp = b.scenes[find_scene(b.scene_pbase, b.n_scenes, gp)];
+  int p = gp - sp.pbase;
+  uint32_t k = sp.key[p];
+  if (k == KEY_INVALID) return;
+  uint32_t t = sp.tile_base + (k >> 6);
+  uint32_t pos = b.tile_start[t] + atomicAdd(b.tile_fill + t, 1u);
+  b.sorted[pos] = uint32_t(p);
+}
+
+// Exclusive block scan of (sum, count) pairs over blockDim.x <= 1024 threads.
+__device__ __forceinline__ void block_scan2(uint32_t& a, uint32_t& c, uint32_t& tot_a, uint32_t& tot_c) {
+  __shared__ uint32_t wa[32], wc[32];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  uint32_t ia = a, ic = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t ta = __shfl_up_sync(0xffffffffu, ia, o), tc = __shfl_up_sync(0xffffffffu, ic, o);
+    if (lane >= o) {
+      ia += ta;
+      ic += tc;
+    }
+  }
+  if (lane == 31) {
+    wa[w] = ia;
+    wc[w] = ic;
+  }
+  __syncthreads();
+  if (w == 0) {
+    uint32_t xa = lane < nw ? wa[lane] : 0u, xc = lane < nw ? wc[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t ta = __shfl_up_sync(0xffffffffu, xa, o), tc = __shfl_up_sync(0xffffffffu, xc, o);
+      if (lane >= o) {
+        xa += ta;
+        xc += tc;
+      }
+    }
+    wa[lane] = xa;
+    wc[lane] = xc;
+  }
+  __syncthreads();
+  uint32_t pa = w > 0 ? wa[w - 1] : 0u, pc = w > 0 ? wc[w - 1] : 0u;
+  tot_a = wa[nw - 1];
+  tot_c = wc[nw - 1];
+  a = pa + ia - a;
+  c = pc + ic - c;
+  __syncthreads();
+}
+
+constexpr int SCAN_THREADS = 1024;
+constexpr int SCAN_PER_THREAD = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_PER_THREAD;
+
+// Phase 1 of the tile scan: per-block totals of particle counts and of active tiles.
+__global__ void k_scan_reduce(BatchDev b) {
+  int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_PER_THREAD;
+  uint32_t s = 0, c = 0;
+#pragma unroll
+  for (int i = 0; i < SCAN_PER_THREAD; ++i) {
+    int t = base + i;
+    if (t < b.total_tiles) {
+      uint32_t v = b.tile_count[t];
+      s += v;
+      c += v > 0;
+    }
+  }
+  uint32_t ta, tc;
+  block_scan2(s, c, ta, tc);
+  if (threadIdx.x == 0) {
+    b.block_sums[2 * blockIdx.x] = ta;
+    b.block_sums[2 * blockIdx.x + 1] = tc;
+  }
+}
+
+// Phase 2: exclusive scan of the block totals (one CTA).
+__global__ void k_scan_top(BatchDev b, int n_blocks) {
+  uint32_t carry_s = 0, carry_c = 0;
+  for (int base = 0; base < n_blocks; base += blockDim.x) {
+    int i = base + threadIdx.x;
+    uint32_t s = i < n_blocks ? b.block_sums[2 * i] : 0u, c = i < n_blocks ? b.block_sums[2 * i + 1] : 0u;
+    uint32_t ts, tc;
+    block_scan2(s, c, ts, tc);
+    if (i < n_blocks) {
+      b.block_sums[2 * i] = s + carry_s;
+      b.block_sums[2 * i + 1] = c + carry_c;
+    }
+    carry_s += ts;
+    carry_c += tc;
+    __syncthreads();
+  }
+}
+
+// Phase 3 (or the whole scan for one block): tile_start, tile_slot, active list, n_active;
+// resets the per-step counters for the next step.
+__global__ void k_scan_down(BatchDev b, int single) {
+  int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_PER_THREAD;
+  uint32_t cnt[SCAN_PER_THREAD];
+  uint32_t s = 0, c = 0;
+#pragma unroll
+  for (int i = 0; i < SCAN_PER_THREAD; ++i) {
+    int t = base + i;
+    cnt[i] = t < b.total_tiles ? b.tile_count[t] : 0u;
+    s += cnt[i];
+    c += cnt[i] > 0;
+  }
+  uint32_t ts, tc;
+  block_scan2(s, c, ts, tc);
+  uint32_t off_s = single ? 0u : b.block_sums[2 * blockIdx.x];
+  uint32_t off_c = single ? 0u : b.block_sums[2 * blockIdx.x + 1];
+  s += off_s;
+  c += off_c;
+#pragma unroll
+  for (int i = 0; i < SCAN_PER_THREAD; ++i) {
+    int t = base + i;
+    if (t < b.total_tiles) {
+      b.tile_start[t] = s;
+      if (cnt[i] > 0) {
+        b.tile_slot[t] = int(c);
+        b.active[c] = t;
+        ++c;
+      } else {
+        b.tile_slot[t] = -1;
+      }
+      s += cnt[i];
+      b.tile_count[t] = 0u;
+      b.tile_fill[t] = 0u;
+    }
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) {
+    b.tile_start[b.total_tiles] = s;
+    *b.n_active = int(c);
+  }
+}
+
+// ============================================================================ P2G (tiled)
+template <int D, bool ADJ>
+struct P2GCfg {
+  static constexpr int RF = 2 * D + D * D;                 // f, a, M
+  static constexpr int RA = ADJ ? D + D * D : 0;           // a', M'
+  static constexpr int RW = ((RF + RA) % 2 == 0) ? RF + RA + 1 : RF + RA;  // odd stride: no bank conflicts
+  static constexpr int CHF = D + 1;                        // momentum + mass
+  static constexpr int CHA = ADJ ? D : 0;                  // vbar*
+  static constexpr int CH = CHF + CHA;
+  static constexpr int NK = D == 2 ? 3 : 9;                // stencil nodes per (cell, kx) thread
+  static constexpr int THREADS = 256;
+  static constexpr int CHUNK = 256;
+  static constexpr size_t REC_BYTES = size_t(CHUNK) * RW * 4;
+  static constexpr size_t ACC_BYTES = size_t(Cfg<D>::CELLS) * Cfg<D>::STENCIL * CH * 4;
+  static constexpr size_t IDS_BYTES = size_t(SORT_CAP) * 4;
+  static constexpr size_t U_BYTES = (REC_BYTES > ACC_BYTES ? REC_BYTES : ACC_BYTES) > IDS_BYTES
+                                        ? (REC_BYTES > ACC_BYTES ? REC_BYTES : ACC_BYTES)
+                                        : IDS_BYTES;
+  static constexpr size_t SMEM = IDS_BYTES + U_BYTES;
+};
+
+template <int D, bool ADJ>
+__global__ void __launch_bounds__(256) k_p2g(BatchDev b) {
+  using K = P2GCfg<D, ADJ>;
+  constexpr int B = Cfg<D>::B, CELLS = Cfg<D>::CELLS, NB = Cfg<D>::BLOCK_NODES, BN = Cfg<D>::BN;
+  constexpr int ST = Cfg<D>::STENCIL;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint32_t* ids = reinterpret_cast<uint32_t*>(smem_raw);
+  float* U = reinterpret_cast<float*>(smem_raw + K::IDS_BYTES);
+  __shared__ int cstart[CELLS + 1], cfill[CELLS];
+  const int tid = threadIdx.x;
+  const int n_active = *b.n_active;
+
+  for (int slot = blockIdx.x; slot < n_active; slot += gridDim.x) {
+    const int gt = b.active[slot];
+    const ScenePar& sp = b.scenes[b.tile_scene[gt]];
+    const uint32_t st = b.tile_start[gt];
+    const int cnt = int(b.tile_start[gt + 1] - st);
+    if (cnt > SORT_CAP) {
+      if (tid == 0) set_status(sp.status, ST_DENSITY);
+      continue;  // uniform across the CTA
+    }
+    // ---- phase A: canonical order (cell, then particle id) ------------------------------
+    uint32_t* raw = reinterpret_cast<uint32_t*>(U);
+    if (tid < CELLS) {
+      cfill[tid] = 0;
+    }
+    __syncthreads();
+    for (int i = tid; i < cnt; i += blockDim.x) {
+      uint32_t id = b.sorted[st + i];
+      uint32_t c = sp.key[id] & 63u;
+      raw[i] = (c << 26) | id;
+      atomicAdd(&cfill[c], 1);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      int acc = 0;
+      for (int c = 0; c < CELLS; ++c) {
+        cstart[c] = acc;
+        acc += cfill[c];
+      }
+      cstart[CELLS] = acc;
+    }
+    __syncthreads();
+    if (tid < CELLS) cfill[tid] = 0;
+    __syncthreads();
+    for (int i = tid; i < cnt; i += blockDim.x) {
+      uint32_t r = raw[i];
+      uint32_t c = r >> 26;
+      int pos = cstart[c] + atomicAdd(&cfill[c], 1);
+      ids[pos] = r & 0x3ffffffu;
+    }
+    __syncthreads();
+    if (tid < CELLS) {  // insertion sort of each cell's ids (a few entries per cell)
+      int s0 = cstart[tid], s1 = cstart[tid + 1];
+      for (int i = s0 + 1; i < s1; ++i) {
+        uint32_t v = ids[i];
+        int j = i - 1;
+        while (j >= s0 && ids[j] > v) {
+          ids[j + 1] = ids[j];
+          --j;
+        }
+        ids[j + 1] = v;
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < cnt; i += blockDim.x) b.sorted[st + i] = ids[i];
+
+    // ---- phases B, C: per-particle records, per-(cell, kx) register accumulation --------
+    const int my_cell = tid / 3, my_kx = tid - 3 * (tid / 3);
+    const bool acc_thread = tid < 3 * CELLS;
+    const int cs = acc_thread ? cstart[my_cell] : 0, ce = acc_thread ? cstart[my_cell + 1] : 0;
+    float acc[K::NK][K::CH];
+#pragma unroll
+    for (int k = 0; k < K::NK; ++k)
+#pragma unroll
+      for (int c = 0; c < K::CH; ++c) acc[k][c] = 0.0f;
+    const float dx = sp.dx, dt = sp.dt;
+    const float Dx4 = 4.0f * sp.inv_dx;  // (4/dx^2) * dx
+    for (int c0 = 0; c0 < cnt; c0 += K::CHUNK) {
+      __syncthreads();  // previous chunk fully consumed (and phase A finished)
+      const int e = c0 + tid;
+      if (tid < K::CHUNK && e < cnt) {
+        const int id = int(ids[e]);
+        float r[Cfg<D>::S];
+        load_planes<D, Cfg<D>::PLANES>(sp.planes, sp.npad, id, r);
+        Part<D> q;
+        unpack<D>(r, q);
+        int base[D];
+        float f[D];
+        stencil_base<D>(q.x, sp.inv_dx, sp.n, base, f);
+        float P[D][D], A[D][D], G[D][D], sig[D];
+        float J = particle_G<D>(q, sp, id, P, A, G, sig);
+        if (!(J > 0.0f)) set_status(sp.status, ST_INVERTED);
+        float* rec = U + size_t(tid) * K::RW;
+        int o = 0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) rec[o++] = f[a];
+        // a = m v - dx G f ; M = dx G  (G (x_i - x_p) = dx G (k - f))
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          float s = 0.0f;
+#pragma unroll
+          for (int c = 0; c < D; ++c) s += G[a][c] * f[c];
+          rec[o++] = sp.mass * q.v[a] - dx * s;
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+          for (int c = 0; c < D; ++c) rec[o++] = dx * G[a][c];
+        if constexpr (ADJ) {
+          // (A) vbar' = gv1 + dt gx1 ; (B) Cbar' = gC1 + dt gF1 F^T ; record for (C):
+          // vbar'_p + (4/dx^2) Cbar' (x_i - x_p) = [vbar' - (4/dx) Cbar' f] + (4/dx) Cbar' k
+          float ra[Cfg<D>::S];
+          load_planes<D, Cfg<D>::PLANES>(sp.adj_in, sp.npad, id, ra);
+          Part<D> g1;
+          unpack<D>(ra, g1);
+          float vb[D], Cb[D][D];
+#pragma unroll
+          for (int a = 0; a < D; ++a) vb[a] = g1.v[a] + dt * g1.x[a];
+#pragma unroll
+          for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+              float s = 0.0f;
+#pragma unroll
+              for (int k = 0; k < D; ++k) s += g1.F[a][k] * q.F[c][k];
+              Cb[a][c] = g1.C[a][c] + dt * s;
+            }
+#pragma unroll
+          for (int a = 0; a < D; ++a) {
+            float s = 0.0f;
+#pragma unroll
+            for (int c = 0; c < D; ++c) s += Cb[a][c] * f[c];
+            rec[o++] = vb[a] - Dx4 * s;
+          }
+#pragma unroll
+          for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int c = 0; c < D; ++c) rec[o++] = Dx4 * Cb[a][c];
+        }
+      }
+      __syncthreads();
+      if (acc_thread) {
+        const int lo = cs > c0 ? cs : c0;
+        const int hi = ce < c0 + K::CHUNK ? ce : c0 + K::CHUNK;
+        const float mass = sp.mass;
+        for (int ei = lo; ei < hi; ++ei) {
+          const float* rec = U + size_t(ei - c0) * K::RW;
+          float w[D][3], dwd[3];
+#pragma unroll
+          for (int a = 0; a < D; ++a) bspline(rec[a], 1.0f, w[a], dwd);
+          const float wx = w[0][my_kx];
+          // base value at (kx, 0, 0): a + M[:,0] kx
+          float u[D], ua[D];
+#pragma unroll
+          for (int a = 0; a < D; ++a) u[a] = rec[D + a] + rec[2 * D + a * D + 0] * float(my_kx);
+          if constexpr (ADJ) {
+#pragma unroll
+            for (int a = 0; a < D; ++a) ua[a] = rec[K::RF + a] + rec[K::RF + D + a * D + 0] * float(my_kx);
+          }
+          if constexpr (D == 2) {
+#pragma unroll
+            for (int ky = 0; ky < 3; ++ky) {
+              const float N = wx * w[1][ky];
+#pragma unroll
+              for (int a = 0; a < D; ++a) acc[ky][a] += N * (u[a] + rec[2 * D + a * D + 1] * float(ky));
+              acc[ky][D] += N * mass;
+              if constexpr (ADJ) {
+#pragma unroll
+                for (int a = 0; a < D; ++a)
+                  acc[ky][K::CHF + a] += N * (ua[a] + rec[K::RF + D + a * D + 1] * float(ky));
+              }
+            }
+          } else {
+#pragma unroll
+            for (int ky = 0; ky < 3; ++ky) {
+              const float wxy = wx * w[1][ky];
+              float u2[D], ua2[D];
+#pragma unroll
+              for (int a = 0; a < D; ++a) u2[a] = u[a] + rec[2 * D + a * D + 1] * float(ky);
+              if constexpr (ADJ) {
+#pragma unroll
+                for (int a = 0; a < D; ++a) ua2[a] = ua[a] + rec[K::RF + D + a * D + 1] * float(ky);
+              }
+#pragma unroll
+              for (int kz = 0; kz < 3; ++kz) {
+                const float N = wxy * w[2][kz];
+                const int k = ky * 3 + kz;
+#pragma unroll
+                for (int a = 0; a < D; ++a) acc[k][a] += N * (u2[a] + rec[2 * D + a * D + 2] * float(kz));
+                acc[k][D] += N * mass;
+                if constexpr (ADJ) {
+#pragma unroll
+                  for (int a = 0; a < D; ++a)
+                    acc[k][K::CHF + a] += N * (ua2[a] + rec[K::RF + D + a * D + 2] * float(kz));
+                }
+              }
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();  // records done; U becomes the per-cell stencil accumulator array
+    if (acc_thread) {
+      float* ca = U + size_t(my_cell) * ST * K::CH;
+#pragma unroll
+      for (int k = 0; k < K::NK; ++k)
+#pragma unroll
+        for (int c = 0; c < K::CH; ++c) ca[(my_kx * K::NK + k) * K::CH + c] = acc[k][c];
+    }
+    __syncthreads();
+    // ---- phase D: node block = fixed-order sum over the cells whose stencil covers it -----
+    if (tid < NB) {
+      int nl[D];
+      {
+        int l = tid;
+#pragma unroll
+        for (int a = D - 1; a >= 0; --a) {
+          nl[a] = l % BN;
+          l /= BN;
+        }
+      }
+      float s[K::CH];
+#pragma unroll
+      for (int c = 0; c < K::CH; ++c) s[c] = 0.0f;
+#pragma unroll
+      for (int kx = 0; kx < 3; ++kx) {
+        const int cx = nl[0] - kx;
+        if (cx < 0 || cx >= B) continue;
+#pragma unroll
+        for (int ky = 0; ky < 3; ++ky) {
+          const int cy = nl[1] - ky;
+          if (cy < 0 || cy >= B) continue;
+          if constexpr (D == 2) {
+            const int cell = cx * B + cy;
+            const float* ca = U + (size_t(cell) * ST + kx * 3 + ky) * K::CH;
+#pragma unroll
+            for (int c = 0; c < K::CH; ++c) s[c] += ca[c];
+          } else {
+#pragma unroll
+            for (int kz = 0; kz < 3; ++kz) {
+              const int cz = nl[2] - kz;
+              if (cz < 0 || cz >= B) continue;
+              const int cell = (cx * B + cy) * B + cz;
+              const float* ca = U + (size_t(cell) * ST + kx * 9 + ky * 3 + kz) * K::CH;
+#pragma unroll
+              for (int c = 0; c < K::CH; ++c) s[c] += ca[c];
+            }
+          }
+        }
+      }
+      float4 o;
+      if constexpr (D == 2)
+        o = make_float4(s[0], s[1], s[2], 0.0f);
+      else
+        o = make_float4(s[0], s[1], s[2], s[3]);
+      b.partial[size_t(slot) * NB + tid] = o;
+      if constexpr (ADJ) {
+        float4 oa;
+        if constexpr (D == 2)
+          oa = make_float4(s[K::CHF], s[K::CHF + 1], 0.0f, 0.0f);
+        else
+          oa = make_float4(s[K::CHF], s[K::CHF + 1], s[K::CHF + 2], 0.0f);
+        b.partial_b[size_t(slot) * NB + tid] = oa;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ============================================================================ grid
+// One thread per node of a tile's B^D node tile; 4 node tiles per 256-thread CTA.
+template <int D, bool ADJ>
+__global__ void __launch_bounds__(256) k_grid(BatchDev b) {
+  constexpr int B = Cfg<D>::B, NB = Cfg<D>::BLOCK_NODES, BN = Cfg<D>::BN;
+  const int gt = blockIdx.x * 4 + (threadIdx.x >> 6);
+  if (gt >= b.total_tiles) return;
+  const ScenePar& sp = b.scenes[b.tile_scene[gt]];
+  int t[D], il[D], node[D];
+  unlin<D>(gt - sp.tile_base, sp.nt, t);
+  {
+    const int bn[3] = {B, B, B};
+    unlin<D>(threadIdx.x & 63, bn, il);
+  }
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    node[a] = t[a] * B + il[a];
+    if (node[a] >= sp.n[a]) return;
+  }
+  float s[4] = {0.0f, 0.0f, 0.0f, 0.0f}, sb[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  bool any = false;
+#pragma unroll
+  for (int e = 0; e < (1 << D); ++e) {  // source tile t - e, fixed order
+    int src[D], loc[D];
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const int ea = (e >> (D - 1 - a)) & 1;
+      src[a] = t[a] - ea;
+      loc[a] = il[a] + ea * B;
+      ok = ok && src[a] >= 0 && loc[a] < BN;
+    }
+    if (!ok) continue;
+    const int slot = b.tile_slot[sp.tile_base + lin3<D>(src, sp.nt)];
+    if (slot < 0) continue;
+    any = true;
+    int l = 0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) l = l * BN + loc[a];
+    const float4 v = b.partial[size_t(slot) * NB + l];
+    s[0] += v.x;
+    s[1] += v.y;
+    s[2] += v.z;
+    s[3] += v.w;
+    if constexpr (ADJ) {
+      const float4 g = b.partial_b[size_t(slot) * NB + l];
+      sb[0] += g.x;
+      sb[1] += g.y;
+      sb[2] += g.z;
+    }
+  }
+  if (!any) return;
+  const float m = D == 2 ? s[2] : s[3];
+  float vraw[D], v[D];
+  if (m > 0.0f) {
+    const float rm = 1.0f / m;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      vraw[a] = s[a] * rm;
+      v[a] = vraw[a] + sp.dt * sp.gravity[a];
+    }
+    bc_apply<D>(node, sp.n, sp.bc, v);
+  } else {
+#pragma unroll
+    for (int a = 0; a < D; ++a) v[a] = vraw[a] = 0.0f;
+  }
+  const int nl = lin3<D>(node, sp.n);
+  if constexpr (D == 2)
+    sp.grid[nl] = make_float4(v[0], v[1], m, 0.0f);
+  else
+    sp.grid[nl] = make_float4(v[0], v[1], v[2], m);
+  if constexpr (ADJ) {
+    // (L) boundary adjoint on vbar*, gravity passes through, (D) pbar = vbar/m, (E) mbar.
+    float g[D], pb[D], mb = 0.0f;
+    if (m > 0.0f) {
+      float vg[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        g[a] = sb[a];
+        vg[a] = vraw[a] + sp.dt * sp.gravity[a];
+      }
+      bc_adjoint<D>(node, sp.n, sp.bc, vg, g);
+      const float rm = 1.0f / m;
+      float dot = 0.0f;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        pb[a] = g[a] * rm;
+        dot += vraw[a] * g[a];
+      }
+      mb = -dot * rm;
+    } else {
+#pragma unroll
+      for (int a = 0; a < D; ++a) pb[a] = 0.0f;
+    }
+    if constexpr (D == 2)
+      sp.grid_b[nl] = make_float4(pb[0], pb[1], mb, 0.0f);
+    else
+      sp.grid_b[nl] = make_float4(pb[0], pb[1], pb[2], mb);
+  }
+}
+
+// ============================================================================ G2P core
+// Gathers v* over the stencil (Eqs. 7, 8) and updates F and x (Eqs. 9, 10).
+template <int D, class Fetch>
+__device__ __forceinline__ void g2p_core(Part<D>& q, const float* f, const float (&w)[D][3], float dt, float inv_dx,
+                                         Fetch fetch) {
+  float vn[D], Cn[D][D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    vn[a] = 0.0f;
+#pragma unroll
+    for (int c = 0; c < D; ++c) Cn[a][c] = 0.0f;
+  }
+#pragma unroll
+  for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+    for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+      for (int kz = 0; kz < (D == 3 ? 3 : 1); ++kz) {
+        float N = w[0][kx] * w[1][ky];
+        if constexpr (D == 3) N *= w[D == 3 ? 2 : 0][kz];
+        const float4 g = fetch(kx, ky, kz);
+        const float vv[3] = {g.x, g.y, g.z};
+        const float dk[3] = {float(kx) - f[0], float(ky) - f[1], D == 3 ? float(kz) - f[D == 3 ? 2 : 0] : 0.0f};
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          const float Nv = N * vv[a];
+          vn[a] += Nv;
+#pragma unroll
+          for (int c = 0; c < D; ++c) Cn[a][c] += Nv * dk[c];
+        }
+      }
+  const float s = 4.0f * inv_dx;  // (4/dx^2) * dx, since x_i - x_p = dx (k - f)
+  float Fo[D][D];
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      Cn[a][c] *= s;
+      Fo[a][c] = q.F[a][c];
+    }
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      float acc = Fo[a][c];
+#pragma unroll
+      for (int k = 0; k < D; ++k) acc += dt * Cn[a][k] * Fo[k][c];
+      q.F[a][c] = acc;
+      q.C[a][c] = Cn[a][c];
+    }
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    q.v[a] = vn[a];
+    q.x[a] += dt * vn[a];
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_g2p(BatchDev b) {
+  constexpr int B = Cfg<D>::B, NB = Cfg<D>::BLOCK_NODES, BN = Cfg<D>::BN;
+  __shared__ float4 sv[NB];
+  const int tid = threadIdx.x;
+  const int n_active = *b.n_active;
+  for (int slot = blockIdx.x; slot < n_active; slot += gridDim.x) {
+    const int gt = b.active[slot];
+    const ScenePar& sp = b.scenes[b.tile_scene[gt]];
+    int t[D];
+    unlin<D>(gt - sp.tile_base, sp.nt, t);
+    for (int i = tid; i < NB; i += blockDim.x) {
+      int l = i, nd[D];
+      bool ok = true;
+#pragma unroll
+      for (int a = D - 1; a >= 0; --a) {
+        nd[a] = t[a] * B + l % BN;
+        l /= BN;
+        ok = ok && nd[a] < sp.n[a];
+      }
+      sv[i] = ok ? sp.grid[lin3<D>(nd, sp.n)] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    const uint32_t st = b.tile_start[gt];
+    const int cnt = int(b.tile_start[gt + 1] - st);
+    for (int e = tid; e < cnt; e += blockDim.x) {
+      const int id = int(b.sorted[st + e]);
+      float r[Cfg<D>::S];
+      load_planes<D, Cfg<D>::XF_PLANES>(sp.planes, sp.npad, id, r);
+      Part<D> q;
+      unpack<D>(r, q);
+      int base[D];
+      float f[D], w[D][3], dw[3];
+      stencil_base<D>(q.x, sp.inv_dx, sp.n, base, f);
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        bspline(f[a], sp.inv_dx, w[a], dw);
+        base[a] -= t[a] * B;  // local stencil origin inside the node block
+      }
+      g2p_core<D>(q, f, w, sp.dt, sp.inv_dx, [&](int kx, int ky, int kz) {
+        int l = (base[0] + kx) * BN + base[1] + ky;
+        if constexpr (D == 3) l = l * BN + base[2] + kz;
+        return sv[l];
+      });
+      pack<D>(q, r);
+      store_planes<D, Cfg<D>::PLANES>(sp.planes_out, sp.npad, id, r);
+      sp.key[id] = bin_key<D>(q.x, sp);
+    }
+    __syncthreads();
+  }
+}
+
+// ============================================================================ adjoint gather
+// Supplement S4: (F) vbar, (I) Cbar, (G) Pbar, (H) Fbar, (J) xbar, (K) sigma-bar -> dL/da.
+// `fetch(kx,ky,kz, v, pb)` returns (v*, m) in v and (pbar, mbar) in pb.
+template <int D, class Fetch>
+__device__ __forceinline__ float adj_core(const Part<D>& q, const Part<D>& g1, const float* f, const float (&w)[D][3],
+                                          const float (&dw)[D][3], const ScenePar& sp, int id, Fetch fetch,
+                                          Part<D>& g0) {
+  const float dt = sp.dt, dx = sp.dx, mass = sp.mass;
+  const float Dinv = 4.0f * sp.inv_dx * sp.inv_dx;
+  const float kG = -Dinv * dt * sp.vol;
+  float P[D][D], A[D][D], G[D][D], sig[D];
+  const float J = particle_G<D>(q, sp, id, P, A, G, sig);
+  float vb[D], Cb[D][D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) vb[a] = g1.v[a] + dt * g1.x[a];
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      float s = 0.0f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) s += g1.F[a][k] * q.F[c][k];
+      Cb[a][c] = g1.C[a][c] + dt * s;
+    }
+  float Gbar[D][D], Cn[D][D], gxs[D], sv[D], spb[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    gxs[a] = sv[a] = spb[a] = 0.0f;
+#pragma unroll
+    for (int c = 0; c < D; ++c) Gbar[a][c] = Cn[a][c] = 0.0f;
+  }
+  float mv[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) mv[a] = mass * q.v[a];
+#pragma unroll
+  for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+    for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+      for (int kz = 0; kz < (D == 3 ? 3 : 1); ++kz) {
+        const int k[3] = {kx, ky, kz};
+        float N = 1.0f, dN[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) N *= w[a][k[a]];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          float g = dw[a][k[a]];
+#pragma unroll
+          for (int c = 0; c < D; ++c)
+            if (c != a) g *= w[c][k[c]];
+          dN[a] = g;
+        }
+        float4 v4, p4;
+        fetch(kx, ky, kz, v4, p4);
+        const float vs[3] = {v4.x, v4.y, v4.z};
+        const float pb[3] = {p4.x, p4.y, p4.z};
+        const float mb = D == 2 ? p4.z : p4.w;
+        float dk[D], dp[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          dk[a] = float(k[a]) - f[a];
+          dp[a] = dk[a] * dx;
+        }
+        // s_i = vbar'.v* + Dinv v*^T Cbar' d + pbar.(m v + G d) + m mbar
+        float si = mass * mb;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          float Cd = 0.0f, Gd = 0.0f;
+#pragma unroll
+          for (int c = 0; c < D; ++c) {
+            Cd += Cb[a][c] * dp[c];
+            Gd += G[a][c] * dp[c];
+          }
+          si += vs[a] * (vb[a] + Dinv * Cd) + pb[a] * (mv[a] + Gd);
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          gxs[a] += dN[a] * si;
+          sv[a] += N * vs[a];
+          spb[a] += N * pb[a];
+#pragma unroll
+          for (int c = 0; c < D; ++c) {
+            Gbar[a][c] += N * pb[a] * dp[c];
+            Cn[a][c] += N * vs[a] * dk[c];
+          }
+        }
+      }
+  // (J): gx = gx' + sum dN s_i - Dinv Cbar'^T sum N v* - G^T sum N pbar
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    float t = 0.0f;
+#pragma unroll
+    for (int c = 0; c < D; ++c) t += Dinv * Cb[c][a] * sv[c] + G[c][a] * spb[c];
+    g0.x[a] = g1.x[a] + gxs[a] - t;
+    g0.v[a] = mass * spb[a];  // (F)
+  }
+  const float sC = 4.0f * sp.inv_dx;
+  float Pb[D][D];
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      Cn[a][c] *= sC;
+      g0.C[a][c] = mass * Gbar[a][c];  // (I)
+      float s = 0.0f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) s += Gbar[a][k] * q.F[k][c];
+      Pb[a][c] = kG * s;  // (G)
+    }
+  float H[D][D];
+  nh_hessian_apply<D>(A, J, sp.mat, Pb, H);
+  // (H) Fbar = (I + dt C^{n+1})^T Fbar' + H[Pbar] + Pbar sigma^T + kG Gbar^T P
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      float s = g1.F[a][c];
+      float t = 0.0f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        s += dt * Cn[k][a] * g1.F[k][c];
+        t += Gbar[k][a] * P[k][c];
+      }
+      g0.F[a][c] = s + H[a][c] + Pb[a][c] * sig[c] + kG * t;
+    }
+  // (K) sigma-bar = F^T Pbar, contracted with the group's direction
+  int g = sp.group ? __ldg(sp.group + id) : -1;
+  float contrib = 0.0f;
+  if (g >= 0 && g < sp.G) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      float s = 0.0f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) s += q.F[k][a] * Pb[k][a];
+      contrib += __ldg(sp.act_dir + g * D + a) * s;
+    }
+  }
+  return contrib;
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_adj_gather(BatchDev b) {
+  constexpr int B = Cfg<D>::B, NB = Cfg<D>::BLOCK_NODES, BN = Cfg<D>::BN;
+  __shared__ float4 sv[NB], sb[NB];
+  const int tid = threadIdx.x;
+  const int n_active = *b.n_active;
+  for (int slot = blockIdx.x; slot < n_active; slot += gridDim.x) {
+    const int gt = b.active[slot];
+    const ScenePar& sp = b.scenes[b.tile_scene[gt]];
+    int t[D];
+    unlin<D>(gt - sp.tile_base, sp.nt, t);
+    for (int i = tid; i < NB; i += blockDim.x) {
+      int l = i, nd[D];
+      bool ok = true;
+#pragma unroll
+      for (int a = D - 1; a >= 0; --a) {
+        nd[a] = t[a] * B + l % BN;
+        l /= BN;
+        ok = ok && nd[a] < sp.n[a];
+      }
+      const int nl = ok ? lin3<D>(nd, sp.n) : 0;
+      sv[i] = ok ? sp.grid[nl] : make_float4(0.f, 0.f, 0.f, 0.f);
+      sb[i] = ok ? sp.grid_b[nl] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    const uint32_t st = b.tile_start[gt];
+    const int cnt = int(b.tile_start[gt + 1] - st);
+    for (int e = tid; e < cnt; e += blockDim.x) {
+      const int id = int(b.sorted[st + e]);
+      float r[Cfg<D>::S];
+      load_planes<D, Cfg<D>::PLANES>(sp.planes, sp.npad, id, r);
+      Part<D> q, g1, g0;
+      unpack<D>(r, q);
+      load_planes<D, Cfg<D>::PLANES>(sp.adj_in, sp.npad, id, r);
+      unpack<D>(r, g1);
+      int base[D];
+      float f[D], w[D][3], dw[D][3];
+      stencil_base<D>(q.x, sp.inv_dx, sp.n, base, f);
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        bspline(f[a], sp.inv_dx, w[a], dw[a]);
+        base[a] -= t[a] * B;
+      }
+      const float c = adj_core<D>(q, g1, f, w, dw, sp, id, [&](int kx, int ky, int kz, float4& v, float4& p) {
+        int l = (base[0] + kx) * BN + base[1] + ky;
+        if constexpr (D == 3) l = l * BN + base[2] + kz;
+        v = sv[l];
+        p = sb[l];
+      }, g0);
+      pack<D>(g0, r);
+      store_planes<D, Cfg<D>::PLANES>(sp.adj_out, sp.npad, id, r);
+      sp.sig_contrib[id] = c;
+    }
+    __syncthreads();
+  }
+}
+
+// ============================================================================ launchers (tiled)
+template <int D>
+cudaError_t launch_keys(const BatchDev& b, cudaStream_t s) {
+  if (b.total_particles == 0) return cudaSuccess;
+  k_keys<D><<<(b.total_particles + 255) / 256, 256, 0, s>>>(b);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t launch_sort(const BatchDev& b, cudaStream_t s) {
+  if (b.total_particles > 0) k_hist<D><<<(b.total_particles + 255) / 256, 256, 0, s>>>(b);
+  const int nblk = (b.total_tiles + SCAN_TILE - 1) / SCAN_TILE;
+  if (nblk <= 1) {
+    k_scan_down<<<1, SCAN_THREADS, 0, s>>>(b, 1);
+  } else {
+    k_scan_reduce<<<nblk, SCAN_THREADS, 0, s>>>(b);
+    k_scan_top<<<1, SCAN_THREADS, 0, s>>>(b, nblk);
+    k_scan_down<<<nblk, SCAN_THREADS, 0, s>>>(b, 0);
+  }
+  if (b.total_particles > 0) k_scatter<D><<<(b.total_particles + 255) / 256, 256, 0, s>>>(b);
+  count_launches((b.total_particles > 0 ? 2 : 0) + (nblk <= 1 ? 1 : 3));
+  return cudaGetLastError();
+}
+
+template <int D, bool ADJ>
+static cudaError_t p2g_impl(const BatchDev& b, cudaStream_t s) {
+  using K = P2GCfg<D, ADJ>;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_p2g<D, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(K::SMEM));
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  int grid = b.max_ctas < b.total_tiles ? b.max_ctas : b.total_tiles;
+  if (grid < 1) grid = 1;
+  k_p2g<D, ADJ><<<grid, K::THREADS, K::SMEM, s>>>(b);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t launch_p2g(const BatchDev& b, bool with_adjoint, cudaStream_t s) {
+  return with_adjoint ? p2g_impl<D, true>(b, s) : p2g_impl<D, false>(b, s);
+}
+
+template <int D>
+cudaError_t launch_grid(const BatchDev& b, bool with_adjoint, cudaStream_t s) {
+  const int grid = (b.total_tiles + 3) / 4;
+  if (grid == 0) return cudaSuccess;
+  if (with_adjoint)
+    k_grid<D, true><<<grid, 256, 0, s>>>(b);
+  else
+    k_grid<D, false><<<grid, 256, 0, s>>>(b);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t launch_g2p(const BatchDev& b, cudaStream_t s) {
+  int grid = b.max_ctas < b.total_tiles ? b.max_ctas : b.total_tiles;
+  if (grid < 1) grid = 1;
+  k_g2p<D><<<grid, 256, 0, s>>>(b);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t launch_adj_gather(const BatchDev& b, cudaStream_t s) {
+  int grid = b.max_ctas < b.total_tiles ? b.max_ctas : b.total_tiles;
+  if (grid < 1) grid = 1;
+  k_adj_gather<D><<<grid, 256, 0, s>>>(b);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_keys<2>(const BatchDev&, cudaStream_t);
+template cudaError_t launch_keys<3>(const BatchDev&, cudaStream_t);
+template cudaError_t launch_sort<2>(const BatchDev&, cudaStream_t);
+template cudaError_t launch_sort<3>(const BatchDev&, cudaStream_t);
+template cudaError_t launch_p2g<2>(const BatchDev&, bool, cudaStream_t);
+template cudaError_t launch_p2g<3>(const BatchDev&, bool, cudaStream_t);
+template cudaError_t launch_grid<2>(const BatchDev&, bool, cudaStream_t);
+template cudaError_t launch_grid<3>(const BatchDev&, bool, cudaStream_t);
+template cudaError_t launch_g2p<2>(const BatchDev&, cudaStream_t);
+template cudaError_t launch_g2p<3>(const BatchDev&, cudaStream_t);
+template cudaError_t launch_adj_gather<2>(const BatchDev&, cudaStream_t);
+template cudaError_t launch_adj_gather<3>(const BatchDev&, cudaStream_t);
+
+// ============================================================================ plain form
+// One scene; P2G and the adjoint scatter add into a zeroed dense grid with global float atomics;
+// the grid kernels visit every node.  Same per-particle math as the tiled form.
+template <int D, bool ADJ>
+__global__ void k_plain_scatter(const ScenePar* __restrict__ dsp) {
+  const ScenePar& sp = *dsp;
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= sp.N) return;
+  float r[Cfg<D>::S];
+  load_planes<D, Cfg<D>::PLANES>(sp.planes, sp.npad, id, r);
+  Part<D> q;
+  unpack<D>(r, q);
+  Sten<D> stn;
+  if (!make_stencil<D>(q.x, sp.inv_dx, sp.n, stn)) {
+    set_status(sp.status, ST_DOMAIN);
+    return;
+  }
+  float P[D][D], A[D][D], G[D][D], sig[D];
+  const float J = particle_G<D>(q, sp, id, P, A, G, sig);
+  if (!(J > 0.0f)) set_status(sp.status, ST_INVERTED);
+  float vb[D], Cb[D][D];
+  if constexpr (ADJ) {
+    Part<D> g1;
+    load_planes<D, Cfg<D>::PLANES>(sp.adj_in, sp.npad, id, r);
+    unpack<D>(r, g1);
+#pragma unroll
+    for (int a = 0; a < D; ++a) vb[a] = g1.v[a] + sp.dt * g1.x[a];
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        float s = 0.0f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) s += g1.F[a][k] * q.F[c][k];
+        Cb[a][c] = g1.C[a][c] + sp.dt * s;
+      }
+  }
+  const float Dinv = 4.0f * sp.inv_dx * sp.inv_dx;
+#pragma unroll
+  for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+    for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+      for (int kz = 0; kz < (D == 3 ? 3 : 1); ++kz) {
+        const int k[3] = {kx, ky, kz};
+        float N = 1.0f;
+        int nd[D];
+        float dp[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          N *= stn.w[a][k[a]];
+          nd[a] = stn.base[a] + k[a];
+          dp[a] = (float(k[a]) - stn.f[a]) * sp.dx;
+        }
+        const int nl = lin3<D>(nd, sp.n);
+        float* gp = reinterpret_cast<float*>(sp.grid + nl);
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          float s = sp.mass * q.v[a];
+#pragma unroll
+          for (int c = 0; c < D; ++c) s += G[a][c] * dp[c];
+          atomicAdd(gp + a, N * s);
+        }
+        atomicAdd(gp + (D == 2 ? 2 : 3), N * sp.mass);
+        if constexpr (ADJ) {
+          float* gb = reinterpret_cast<float*>(sp.grid_b + nl);
+#pragma unroll
+          for (int a = 0; a < D; ++a) {
+            float s = vb[a];
+#pragma unroll
+            for (int c = 0; c < D; ++c) s += Dinv * Cb[a][c] * dp[c];
+            atomicAdd(gb + a, N * s);
+          }
+        }
+      }
+}
+
+template <int D, bool ADJ>
+__global__ void k_plain_grid(const ScenePar* __restrict__ dsp, int n_nodes) {
+  const ScenePar& sp = *dsp;
+  const int nl = blockIdx.x * blockDim.x + threadIdx.x;
+  if (nl >= n_nodes) return;
+  int node[D];
+  unlin<D>(nl, sp.n, node);
+  const float4 s4 = sp.grid[nl];
+  const float s[4] = {s4.x, s4.y, s4.z, s4.w};
+  const float m = D == 2 ? s[2] : s[3];
+  float vraw[D], v[D];
+  if (m > 0.0f) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      vraw[a] = s[a] / m;
+      v[a] = vraw[a] + sp.dt * sp.gravity[a];
+    }
+    bc_apply<D>(node, sp.n, sp.bc, v);
+  } else {
+#pragma unroll
+    for (int a = 0; a < D; ++a) v[a] = vraw[a] = 0.0f;
+  }
+  if constexpr (D == 2)
+    sp.grid[nl] = make_float4(v[0], v[1], m, 0.0f);
+  else
+    sp.grid[nl] = make_float4(v[0], v[1], v[2], m);
+  if constexpr (ADJ) {
+    const float4 b4 = sp.grid_b[nl];
+    float g[D] = {};
+    float pb[D], mb = 0.0f;
+    g[0] = b4.x;
+    g[1] = b4.y;
+    if constexpr (D == 3) g[D == 3 ? 2 : 0] = b4.z;
+    if (m > 0.0f) {
+      float vg[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) vg[a] = vraw[a] + sp.dt * sp.gravity[a];
+      bc_adjoint<D>(node, sp.n, sp.bc, vg, g);
+      float dot = 0.0f;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        pb[a] = g[a] / m;
+        dot += vraw[a] * g[a];
+      }
+      mb = -dot / m;
+    } else {
+#pragma unroll
+      for (int a = 0; a < D; ++a) pb[a] = 0.0f;
+    }
+    if constexpr (D == 2)
+      sp.grid_b[nl] = make_float4(pb[0], pb[1], mb, 0.0f);
+    else
+      sp.grid_b[nl] = make_float4(pb[0], pb[1], pb[2], mb);
+  }
+}
+
+template <int D>
+__global__ void k_plain_g2p(const ScenePar* __restrict__ dsp) {
+  const ScenePar& sp = *dsp;
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= sp.N) return;
+  float r[Cfg<D>::S];
+  load_planes<D, Cfg<D>::XF_PLANES>(sp.planes, sp.npad, id, r);
+  Part<D> q;
+  unpack<D>(r, q);
+  Sten<D> stn;
+  if (!make_stencil<D>(q.x, sp.inv_dx, sp.n, stn)) return;  // status already set by the scatter
+  g2p_core<D>(q, stn.f, stn.w, sp.dt, sp.inv_dx, [&](int kx, int ky, int kz) {
+    int nd[D];
+    nd[0] = stn.base[0] + kx;
+    nd[1] = stn.base[1] + ky;
+    if constexpr (D == 3) nd[D == 3 ? 2 : 0] = stn.base[D == 3 ? 2 : 0] + kz;
+    return sp.grid[lin3<D>(nd, sp.n)];
+  });
+  pack<D>(q, r);
+  store_planes<D, Cfg<D>::PLANES>(sp.planes_out, sp.npad, id, r);
+}
+
+template <int D>
+__global__ void k_plain_gather(const ScenePar* __restrict__ dsp) {
+  const ScenePar& sp = *dsp;
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= sp.N) return;
+  float r[Cfg<D>::S];
+  load_planes<D, Cfg<D>::PLANES>(sp.planes, sp.npad, id, r);
+  Part<D> q, g1, g0;
+  unpack<D>(r, q);
+  load_planes<D, Cfg<D>::PLANES>(sp.adj_in, sp.npad, id, r);
+  unpack<D>(r, g1);
+  Sten<D> stn;
+  if (!make_stencil<D>(q.x, sp.inv_dx, sp.n, stn)) return;
+  const float c = adj_core<D>(q, g1, stn.f, stn.w, stn.dw, sp, id, [&](int kx, int ky, int kz, float4& v, float4& p) {
+    int nd[D];
+    nd[0] = stn.base[0] + kx;
+    nd[1] = stn.base[1] + ky;
+    if constexpr (D == 3) nd[D == 3 ? 2 : 0] = stn.base[D == 3 ? 2 : 0] + kz;
+    const int nl = lin3<D>(nd, sp.n);
+    v = sp.grid[nl];
+    p = sp.grid_b[nl];
+  }, g0);
+  pack<D>(g0, r);
+  store_planes<D, Cfg<D>::PLANES>(sp.adj_out, sp.npad, id, r);
+  sp.sig_contrib[id] = c;
+}
+
+static int host_nodes(const ScenePar& sp) {
+  int c = 1;
+  for (int a = 0; a < sp.dim; ++a) c *= sp.n[a];
+  return c;
+}
+
+template <int D>
+cudaError_t launch_plain_step(const ScenePar* dsp, const ScenePar& sp, cudaStream_t s) {
+  const int nn = host_nodes(sp);
+  cudaError_t e = cudaMemsetAsync(sp.grid, 0, sizeof(float4) * size_t(nn), s);
+  if (e != cudaSuccess) return e;
+  if (sp.N > 0) k_plain_scatter<D, false><<<(sp.N + 255) / 256, 256, 0, s>>>(dsp);
+  k_plain_grid<D, false><<<(nn + 255) / 256, 256, 0, s>>>(dsp, nn);
+  if (sp.N > 0) k_plain_g2p<D><<<(sp.N + 255) / 256, 256, 0, s>>>(dsp);
+  count_launches(sp.N > 0 ? 3 : 1);
+  return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t launch_plain_adjoint(const ScenePar* dsp, const ScenePar& sp, cudaStream_t s) {
+  const int nn = host_nodes(sp);
+  cudaError_t e = cudaMemsetAsync(sp.grid, 0, sizeof(float4) * size_t(nn), s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(sp.grid_b, 0, sizeof(float4) * size_t(nn), s);
+  if (e != cudaSuccess) return e;
+  if (sp.N > 0) k_plain_scatter<D, true><<<(sp.N + 255) / 256, 256, 0, s>>>(dsp);
+  k_plain_grid<D, true><<<(nn + 255) / 256, 256, 0, s>>>(dsp, nn);
+  if (sp.N > 0) k_plain_gather<D><<<(sp.N + 255) / 256, 256, 0, s>>>(dsp);
+  count_launches(sp.N > 0 ? 3 : 1);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_plain_step<2>(const ScenePar*, const ScenePar&, cudaStream_t);
+template cudaError_t launch_plain_step<3>(const ScenePar*, const ScenePar&, cudaStream_t);
+template cudaError_t launch_plain_adjoint<2>(const ScenePar*, const ScenePar&, cudaStream_t);
+template cudaError_t launch_plain_adjoint<3>(const ScenePar*, const ScenePar&, cudaStream_t);
+
+// ============================================================================ pack / unpack
+__global__ void k_pack(int dim, int N, int npad, const float* x, const float* v, const float* C, const float* F,
+                       float4* planes, int* status) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npad) return;
+  const int S = dim == 2 ? 12 : 24, d2 = dim * dim;
+  float r[24];
+  if (p < N) {
+    int o = 0;
+    for (int a = 0; a < dim; ++a) r[o++] = x[size_t(p) * dim + a];
+    for (int a = 0; a < d2; ++a) r[o++] = F ? F[size_t(p) * d2 + a] : ((a % (dim + 1)) == 0 ? 1.0f : 0.0f);
+    for (int a = 0; a < dim; ++a) r[o++] = v ? v[size_t(p) * dim + a] : 0.0f;
+    for (int a = 0; a < d2; ++a) r[o++] = C ? C[size_t(p) * d2 + a] : 0.0f;
+    for (int a = 0; a < S; ++a)
+      if (!(r[a] == r[a]) || fabsf(r[a]) > 3.0e38f) set_status(status, -1);
+  } else {
+    for (int a = 0; a < S; ++a) r[a] = 0.0f;
+  }
+  for (int j = 0; j < S / 4; ++j) planes[size_t(j) * npad + p] = make_float4(r[4 * j], r[4 * j + 1], r[4 * j + 2], r[4 * j + 3]);
+}
+
+__global__ void k_unpack(int dim, int N, int npad, const float4* planes, float* x, float* v, float* C, float* F) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  const int S = dim == 2 ? 12 : 24, d2 = dim * dim;
+  float r[24];
+  for (int j = 0; j < S / 4; ++j) {
+    float4 q = planes[size_t(j) * npad + p];
+    r[4 * j] = q.x;
+    r[4 * j + 1] = q.y;
+    r[4 * j + 2] = q.z;
+    r[4 * j + 3] = q.w;
+  }
+  int o = 0;
+  for (int a = 0; a < dim; ++a, ++o)
+    if (x) x[size_t(p) * dim + a] = r[o];
+  for (int a = 0; a < d2; ++a, ++o)
+    if (F) F[size_t(p) * d2 + a] = r[o];
+  for (int a = 0; a < dim; ++a, ++o)
+    if (v) v[size_t(p) * dim + a] = r[o];
+  for (int a = 0; a < d2; ++a, ++o)
+    if (C) C[size_t(p) * d2 + a] = r[o];
+}
+
+__global__ void k_set_int(int* p, int v) { *p = v; }
+
+cudaError_t launch_set_int(int* p, int v, cudaStream_t s) {
+  k_set_int<<<1, 1, 0, s>>>(p, v);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack(int dim, int N, int npad, const float* x, const float* v, const float* C, const float* F,
+                        float4* planes, int* status, cudaStream_t s) {
+  if (npad == 0) return cudaSuccess;
+  k_pack<<<(npad + 255) / 256, 256, 0, s>>>(dim, N, npad, x, v, C, F, planes, status);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack(int dim, int N, int npad, const float4* planes, float* x, float* v, float* C, float* F,
+                          cudaStream_t s) {
+  if (N == 0) return cudaSuccess;
+  k_unpack<<<(N + 255) / 256, 256, 0, s>>>(dim, N, npad, planes, x, v, C, F);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace gbmpm

@@ -1,0 +1,347 @@
+"""Thin ctypes binding of libgbmpm (include/mpm.h): argument marshalling only.
+
+Every step of the simulation and of its reverse pass runs in the library's CUDA kernels.  The
+library must have been built (``python -m paper_1810_01054_gb300.build``); importing this module
+without it, or calling it without a CUDA device, raises -- there is no CPU fallback.
+
+Arrays cross the boundary as FP32, row-major: x, v [N, d]; C, F [N, d, d].  numpy arrays use
+host pointers (mem_space 0); torch CUDA tensors use device pointers (mem_space 1).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libgbmpm.so")
+
+MPM_OK = 0
+STATUS = {0: "ok", -1: "invalid argument", -2: "out of device memory or budget", -3: "stencil left the grid",
+          -4: "det F <= 0", -5: "bounded device wait expired", -6: "CUDA error", -7: "call out of order",
+          -8: "too many particles in one tile"}
+IMPL_TILED, IMPL_PLAIN = 0, 1
+
+
+class MPMError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: status {status} ({STATUS.get(status, 'unknown')})")
+        self.status = status
+
+
+class SceneDesc(C.Structure):
+    _fields_ = [
+        ("dim", C.c_int),
+        ("n_grid", C.c_int * 3),
+        ("dx", C.c_float),
+        ("dt", C.c_float),
+        ("gravity", C.c_float * 3),
+        ("E", C.c_float),
+        ("nu", C.c_float),
+        ("p_mass", C.c_float),
+        ("p_vol", C.c_float),
+        ("bc_type", C.c_int),
+        ("bc_width", C.c_int),
+        ("friction_c", C.c_float),
+        ("n_particles", C.c_int),
+        ("x0", C.c_void_p),
+        ("v0", C.c_void_p),
+        ("C0", C.c_void_p),
+        ("F0", C.c_void_p),
+        ("group", C.c_void_p),
+        ("n_groups", C.c_int),
+        ("act_dir", C.c_void_p),
+        ("ctrl_type", C.c_int),
+        ("ctrl_hidden", C.c_int),
+        ("ctrl_freq", C.c_float),
+        ("ctrl_scale", C.c_float),
+        ("n_ctrl_params", C.c_int),
+        ("ctrl_params", C.c_void_p),
+        ("impl", C.c_int),
+        ("mem_space", C.c_int),
+    ]
+
+
+_lib = None
+_lock = threading.Lock()
+
+_SIGS = {
+    "mpm_ctx_create": [C.POINTER(C.c_void_p), C.c_int, C.c_void_p],
+    "mpm_ctx_destroy": [C.c_void_p],
+    "mpm_sync": [C.c_void_p],
+    "mpm_status_str": [C.c_int],
+    "mpm_scene_create": [C.c_void_p, C.POINTER(SceneDesc), C.POINTER(C.c_void_p)],
+    "mpm_scene_destroy": [C.c_void_p],
+    "mpm_step": [C.c_void_p, C.c_int],
+    "mpm_rollout": [C.c_void_p, C.c_int, C.c_int, C.c_size_t],
+    "mpm_backward": [C.c_void_p] + [C.c_void_p] * 9 + [C.c_int],
+    "mpm_get_state": [C.c_void_p, C.c_int] + [C.c_void_p] * 4 + [C.c_int],
+    "mpm_set_state": [C.c_void_p] + [C.c_void_p] * 4 + [C.c_int, C.c_int],
+    "mpm_set_ctrl_params": [C.c_void_p, C.c_void_p, C.c_int, C.c_int],
+    "mpm_get_grid": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int],
+    "mpm_scene_info": [C.c_void_p] + [C.POINTER(C.c_int)] * 4 + [C.POINTER(C.c_size_t)],
+    "mpm_batch_create": [C.c_void_p, C.c_int, C.c_size_t, C.POINTER(C.c_void_p)],
+    "mpm_batch_destroy": [C.c_void_p],
+    "mpm_batch_admit": [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int)],
+    "mpm_batch_tick": [C.c_void_p, C.c_int],
+    "mpm_batch_poll": [C.c_void_p, C.c_int, C.POINTER(C.c_int)],
+    "mpm_batch_release": [C.c_void_p, C.c_int],
+    "mpm_profile_start": [C.c_void_p, C.c_uint, C.c_int],
+    "mpm_profile_read": [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)],
+    "mpm_launch_count": [C.POINTER(C.c_longlong)],
+}
+
+K_SORT, K_P2G, K_GRID, K_G2P, K_P2G_ADJ, K_GRID_ADJ, K_ADJ_GATHER, K_CTRL, K_PLAIN = range(9)
+KERNEL_NAMES = ["sort", "p2g", "grid", "g2p", "p2g_adj", "grid_adj", "adj_gather", "ctrl", "plain"]
+
+
+def launch_count() -> int:
+    n = C.c_longlong()
+    _check(lib().mpm_launch_count(C.byref(n)), "mpm_launch_count")
+    return int(n.value)
+
+
+def lib():
+    """Loads libgbmpm.so (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_1810_01054_gb300.build`")
+            L = C.CDLL(LIB_PATH)
+            for name, args in _SIGS.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = C.c_char_p if name == "mpm_status_str" else C.c_int
+            _lib = L
+    return _lib
+
+
+def _check(status: int, what: str):
+    if status != MPM_OK:
+        raise MPMError(status, what)
+
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if _is_torch(a):
+        return C.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _f32(a, shape):
+    if a is None:
+        return None
+    if _is_torch(a):
+        import torch
+        t = a.detach().to(dtype=torch.float32).contiguous()
+        if tuple(t.shape) != tuple(shape):
+            t = t.reshape(shape)
+        return t
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32).reshape(shape))
+
+
+class Context:
+    """A CUDA device plus the stream every call of its scenes enqueues on.  ``stream`` may be a
+    torch.cuda.Stream (or raw cudaStream_t int); None creates a private stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        raw = None
+        if stream is not None:
+            raw = C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+        h = C.c_void_p()
+        _check(lib().mpm_ctx_create(C.byref(h), int(device), raw), "mpm_ctx_create")
+        self.handle = h
+        self.device = device
+
+    def sync(self):
+        _check(lib().mpm_sync(self.handle), "mpm_sync")
+
+    def profile_start(self, kinds, max_launches: int = 1 << 16):
+        mask = 0
+        for k in kinds:
+            mask |= 1 << int(k)
+        _check(lib().mpm_profile_start(self.handle, mask, int(max_launches)), "mpm_profile_start")
+
+    def profile_read(self, kind):
+        n, t = C.c_int(), C.c_double()
+        _check(lib().mpm_profile_read(self.handle, int(kind), C.byref(n), C.byref(t)), "mpm_profile_read")
+        return n.value, t.value
+
+    def close(self):
+        if self.handle:
+            lib().mpm_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Scene:
+    """One simulation (state, grid, controller) living on the GPU."""
+
+    def __init__(self, ctx: Context, spec, impl: int = IMPL_TILED, params=None):
+        d = int(spec.dim)
+        self.ctx, self.dim = ctx, d
+        self.spec = spec
+        N = int(np.asarray(spec.x0).shape[0]) if not _is_torch(spec.x0) else int(spec.x0.shape[0])
+        self.N = N
+        G = int(np.asarray(spec.act_dir).shape[0])
+        keep = []
+        dev = _is_torch(spec.x0) and spec.x0.is_cuda
+
+        def arr(a, shape):
+            t = _f32(a, shape)
+            keep.append(t)
+            return t
+
+        desc = SceneDesc()
+        desc.dim = d
+        ng = list(spec.n_grid) + [1] * (3 - len(spec.n_grid))
+        for a in range(3):
+            desc.n_grid[a] = int(ng[a])
+        desc.dx, desc.dt = float(spec.dx), float(spec.dt)
+        g = list(spec.gravity) + [0.0] * (3 - len(spec.gravity))
+        for a in range(3):
+            desc.gravity[a] = float(g[a])
+        desc.E, desc.nu = float(spec.E), float(spec.nu)
+        desc.p_mass, desc.p_vol = float(spec.p_mass), float(spec.p_vol)
+        desc.bc_type, desc.bc_width, desc.friction_c = int(spec.bc_type), int(spec.bc_width), float(spec.friction_c)
+        desc.n_particles = N
+        desc.x0 = _ptr(arr(spec.x0, (N, d)))
+        desc.v0 = _ptr(arr(spec.v0, (N, d))) if spec.v0 is not None else None
+        desc.C0 = _ptr(arr(spec.C0, (N, d, d))) if spec.C0 is not None else None
+        desc.F0 = _ptr(arr(spec.F0, (N, d, d))) if spec.F0 is not None else None
+        if dev:
+            import torch
+            grp = torch.as_tensor(spec.group, dtype=torch.int32, device=spec.x0.device).contiguous()
+            params_t = torch.as_tensor(spec.ctrl_params if params is None else params, dtype=torch.float32,
+                                       device=spec.x0.device).contiguous()
+            dirs = torch.as_tensor(spec.act_dir, dtype=torch.float32, device=spec.x0.device).contiguous()
+        else:
+            grp = np.ascontiguousarray(np.asarray(spec.group, dtype=np.int32))
+            params_t = np.ascontiguousarray(np.asarray(spec.ctrl_params if params is None else params,
+                                                       dtype=np.float32).ravel())
+            dirs = np.ascontiguousarray(np.asarray(spec.act_dir, dtype=np.float32).reshape(G, d) if G else
+                                        np.zeros((1, d), np.float32))
+        keep += [grp, params_t, dirs]
+        desc.group = _ptr(grp)
+        desc.n_groups = G
+        desc.act_dir = _ptr(dirs)
+        desc.ctrl_type, desc.ctrl_hidden = int(spec.ctrl_type), int(spec.ctrl_hidden)
+        desc.ctrl_freq, desc.ctrl_scale = float(spec.ctrl_freq), float(spec.ctrl_scale)
+        self.n_params = int(params_t.numel() if _is_torch(params_t) else params_t.size)
+        desc.n_ctrl_params = self.n_params
+        desc.ctrl_params = _ptr(params_t)
+        desc.impl = int(impl)
+        desc.mem_space = 1 if dev else 0
+        h = C.c_void_p()
+        _check(lib().mpm_scene_create(ctx.handle, C.byref(desc), C.byref(h)), "mpm_scene_create")
+        self.handle = h
+        self.G = G
+        self.impl = impl
+
+    # ------------------------------------------------------------------ forward
+    def step(self, n: int = 1):
+        _check(lib().mpm_step(self.handle, int(n)), "mpm_step")
+
+    def rollout(self, n_steps: int, ckpt_interval: int = 0, mem_budget: int = 0):
+        _check(lib().mpm_rollout(self.handle, int(n_steps), int(ckpt_interval), C.c_size_t(int(mem_budget))),
+               "mpm_rollout")
+
+    def sync(self):
+        self.ctx.sync()
+
+    # ------------------------------------------------------------------ state
+    def get_state(self, step: int = -1, out=None):
+        """Returns (x, v, C, F) as numpy arrays (or fills the given torch CUDA tensors)."""
+        N, d = self.N, self.dim
+        if out is not None:
+            x, v, Cm, F = out
+            _check(lib().mpm_get_state(self.handle, int(step), _ptr(x), _ptr(v), _ptr(Cm), _ptr(F), 1),
+                   "mpm_get_state")
+            return out
+        x, v = np.empty((N, d), np.float32), np.empty((N, d), np.float32)
+        Cm, F = np.empty((N, d, d), np.float32), np.empty((N, d, d), np.float32)
+        _check(lib().mpm_get_state(self.handle, int(step), _ptr(x), _ptr(v), _ptr(Cm), _ptr(F), 0), "mpm_get_state")
+        return x, v, Cm, F
+
+    def set_state(self, x, v=None, Cm=None, F=None, step: int = -1):
+        N, d = self.N, self.dim
+        dev = _is_torch(x) and x.is_cuda
+        arrs = [_f32(x, (N, d)), _f32(v, (N, d)), _f32(Cm, (N, d, d)), _f32(F, (N, d, d))]
+        _check(lib().mpm_set_state(self.handle, *[_ptr(a) for a in arrs], int(step), 1 if dev else 0),
+               "mpm_set_state")
+
+    def set_params(self, params):
+        dev = _is_torch(params) and params.is_cuda
+        p = _f32(params, (self.n_params,))
+        _check(lib().mpm_set_ctrl_params(self.handle, _ptr(p), self.n_params, 1 if dev else 0), "mpm_set_ctrl_params")
+
+    def get_grid(self):
+        n = int(np.prod(list(self.spec.n_grid)))
+        m = np.empty(n, np.float32)
+        v = np.empty((n, self.dim), np.float32)
+        _check(lib().mpm_get_grid(self.handle, _ptr(m), _ptr(v), 0), "mpm_get_grid")
+        return m, v
+
+    def info(self):
+        a, b, c, s = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        sb = C.c_size_t()
+        _check(lib().mpm_scene_info(self.handle, C.byref(a), C.byref(b), C.byref(c), C.byref(s), C.byref(sb)),
+               "mpm_scene_info")
+        return dict(n_particles=a.value, n_groups=b.value, n_ctrl_params=c.value, step=s.value,
+                    state_bytes=sb.value)
+
+    # ------------------------------------------------------------------ reverse
+    def backward(self, gx=None, gv=None, gC=None, gF=None, out=None):
+        """Reverse pass of the last rollout.  Seeds are dL/d(final state) (None = 0).  Returns
+        (gx0, gv0, gC0, gF0, g_params) as numpy arrays, or fills ``out`` (torch CUDA tensors, the
+        same five in that order) and returns it."""
+        N, d = self.N, self.dim
+        seeds = [_f32(gx, (N, d)), _f32(gv, (N, d)), _f32(gC, (N, d, d)), _f32(gF, (N, d, d))]
+        if out is not None:
+            on_dev = bool(out[0].is_cuda)
+            for sd in seeds:
+                if sd is not None and (not _is_torch(sd) or bool(sd.is_cuda) != on_dev):
+                    raise ValueError("seeds and outputs must live in the same memory space")
+            _check(lib().mpm_backward(self.handle, *[_ptr(a) for a in seeds], *[_ptr(a) for a in out],
+                                      1 if on_dev else 0), "mpm_backward")
+            return out
+        if any(_is_torch(sd) for sd in seeds if sd is not None):
+            seeds = [None if sd is None else sd.detach().cpu().numpy() for sd in seeds]
+        gx0, gv0 = np.empty((N, d), np.float32), np.empty((N, d), np.float32)
+        gC0, gF0 = np.empty((N, d, d), np.float32), np.empty((N, d, d), np.float32)
+        gp = np.empty(max(self.n_params, 1), np.float32)
+        _check(lib().mpm_backward(self.handle, *[_ptr(a) for a in seeds], _ptr(gx0), _ptr(gv0), _ptr(gC0), _ptr(gF0),
+                                  _ptr(gp), 0), "mpm_backward")
+        return gx0, gv0, gC0, gF0, gp[: self.n_params]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().mpm_scene_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def header_symbols(header_path: str):
+    """Names of the functions declared in include/mpm.h."""
+    import re
+    text = open(header_path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mpm_[a-z_]+)\s*\(", text)))

@@ -1,0 +1,211 @@
+"""GPU path (libgbmpm through its C ABI) against the FP64 oracle on the same seeded inputs.
+
+Forward: one step on small 2D/3D scenes (sticky, slip, friction, every controller form, several
+tiles, a ragged tail of particles), 10-step re-synced windows over the whole 100-step 64^2 square
+workload, and one full-size step of each larger workload.  Reverse: full-horizon gradients of
+the 64^2 square workload, gradients of every controller form, and one full-size reverse step.
+Both kernel forms (tiled/sorted and plain/atomic) are checked.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1810_01054_gb300 import scenes as S
+from tests.parity_utils import (FWD_TOL, assert_grad_close, assert_state_close, mean_x0_seed, oracle_step_from,
+                                rel_l2)
+
+pytestmark = pytest.mark.gpu
+
+IMPLS = [0, 1]  # tiled, plain
+
+
+@pytest.fixture(scope="module")
+def M():
+    from paper_1810_01054_gb300 import mpm
+    mpm.lib()
+    return mpm
+
+
+@pytest.fixture(scope="module")
+def ctx(M):
+    c = M.Context(0)
+    yield c
+    c.close()
+
+
+def small_scenes():
+    return {
+        "2d_sticky": S.blob(2, 32, 300, 1, v_scale=0.5, c_scale=2.0, f_scale=0.05, radius_cells=5.0,
+                            center=(0.5, 6.5 / 32), bc_width=3, amp=2.0),
+        "3d_sticky": S.blob(3, 24, 700, 2, v_scale=0.5, c_scale=2.0, f_scale=0.05, radius_cells=4.0,
+                            center=(0.5, 5.0 / 24, 0.45), bc_width=3, amp=2.0),
+        "2d_slip_friction": S.blob(2, 32, 257, 3, v_scale=0.8, bc_type=S.BC_SLIP, friction_c=0.4, bc_width=3,
+                                   radius_cells=4.0, center=(0.4, 4.8 / 32), amp=1.0),
+        "3d_slip": S.blob(3, 24, 333, 4, v_scale=0.8, bc_type=S.BC_SLIP, friction_c=0.0, bc_width=3,
+                          radius_cells=3.5, center=(0.5, 4.5 / 24, 5.0 / 24), amp=1.0),
+        "2d_basis": S.blob(2, 32, 200, 5, ctrl_type=S.CTRL_BASIS, n_groups=4, freq=4.0, radius_cells=4.0,
+                           v_scale=0.3),
+        "3d_mlp": S.blob(3, 16, 400, 6, ctrl_type=S.CTRL_MLP, n_groups=4, hidden=16, scale=5.0, radius_cells=3.5,
+                         v_scale=0.3),
+    }
+
+
+@pytest.mark.parametrize("impl", IMPLS, ids=["tiled", "plain"])
+@pytest.mark.parametrize("name", list(small_scenes().keys()))
+def test_one_step_forward(M, ctx, name, impl):
+    spec = small_scenes()[name]
+    gpu = M.Scene(ctx, spec, impl=impl)
+    st0 = O.Scene(spec).initial_state()
+    # start at step 3 so the sinusoid controllers are non-zero
+    gpu.set_state(*st0, step=3)
+    gpu.step(1)
+    got = gpu.get_state()
+    ref = oracle_step_from(spec, st0, 3)
+    assert_state_close(got, ref)
+
+
+@pytest.mark.parametrize("impl", IMPLS, ids=["tiled", "plain"])
+def test_walker_square_windows(M, ctx, impl):
+    """64^2 grid, 1024 particles, 100 steps: every 10-step window re-synced to the oracle."""
+    spec = S.walker_square_2d(0)
+    osc = O.Scene(spec)
+    xs, vs, Cs, Fs, acts = osc.rollout(100)
+    gpu = M.Scene(ctx, spec, impl=impl)
+    for w in range(10):
+        n0 = 10 * w
+        gpu.set_state(xs[n0], vs[n0], Cs[n0], Fs[n0], step=n0)
+        gpu.step(10)
+        x, v, Cm, F = gpu.get_state()
+        n1 = n0 + 10
+        assert_state_close((x, v), (xs[n1], vs[n1]), names=("x", "v"))
+
+
+@pytest.mark.parametrize("impl", IMPLS, ids=["tiled", "plain"])
+def test_walker_square_full_horizon_gradient(M, ctx, impl):
+    """dL/dv0 and dL/dA over the full 100 steps, L = mean final x_0, against the oracle."""
+    spec = S.walker_square_2d(0)
+    osc = O.Scene(spec)
+    traj = osc.rollout(100)
+    seed = mean_x0_seed(osc.N, 2)
+    ogx, ogv, ogC, ogF, ogp = osc.backward(traj, (seed, None, None, None))
+    gpu = M.Scene(ctx, spec, impl=impl)
+    gpu.rollout(100, 10)
+    x, v, _, _ = gpu.get_state()
+    assert rel_l2(x, traj[0][100]) < 1e-3
+    gx, gv, gC, gF, gp = gpu.backward(seed)
+    assert_grad_close(gv, ogv, "dL/dv0")
+    assert_grad_close(gp, ogp, "dL/dA")
+    assert_grad_close(gx, ogx, "dL/dx0")
+    assert_grad_close(gF, ogF, "dL/dF0")
+
+
+@pytest.mark.parametrize("name", ["2d_basis", "3d_mlp", "2d_slip_friction", "3d_sticky"])
+def test_controller_and_state_gradients(M, ctx, name):
+    spec = small_scenes()[name]
+    T = 25
+    osc = O.Scene(spec)
+    traj = osc.rollout(T)
+    rng = np.random.default_rng(7)
+    wx = rng.normal(size=traj[0][T].shape) / osc.N
+    wv = rng.normal(size=traj[1][T].shape) / osc.N
+    ogx, ogv, ogC, ogF, ogp = osc.backward(traj, (wx, wv, None, None))
+    gpu = M.Scene(ctx, spec)
+    gpu.rollout(T, 4)
+    gx, gv, gC, gF, gp = gpu.backward(wx, wv)
+    for nm, a, b in (("x0", gx, ogx), ("v0", gv, ogv), ("C0", gC, ogC), ("F0", gF, ogF), ("params", gp, ogp)):
+        assert_grad_close(a, b, f"{name} dL/d{nm}")
+
+
+def test_tiled_is_bitwise_deterministic_and_checkpoint_invariant(M, ctx):
+    """The tiled form sums in a fixed order everywhere: two runs agree bit for bit, and the
+    recomputed states of any checkpoint interval equal the stored ones, so gradients too."""
+    spec = S.walker_square_2d(0)
+    seed = mean_x0_seed(spec.n_particles, 2)
+    outs = []
+    for k in (1, 7, 64, 100, 7):
+        gpu = M.Scene(ctx, spec)
+        gpu.rollout(100, k)
+        outs.append(gpu.backward(seed))
+        gpu.close()
+    for o in outs[1:]:
+        for a, b in zip(o, outs[0]):
+            assert np.array_equal(a, b)
+
+
+def test_plain_and_tiled_agree(M, ctx):
+    spec = S.walker_square_2d(0)
+    res = []
+    for impl in IMPLS:
+        gpu = M.Scene(ctx, spec, impl=impl)
+        gpu.step(50)
+        res.append(gpu.get_state())
+    assert_state_close(res[0], res[1], tol=1e-5)
+
+
+def test_domain_and_inversion_errors(M, ctx):
+    spec = S.blob(2, 16, 20, 0)
+    spec.x0[0] = [2.6 / 16, 0.5]
+    spec.v0[0] = [-400.0, 0.0]  # leaves the grid within one step
+    spec = spec.copy(bc_width=0)
+    g = M.Scene(ctx, spec)
+    g.step(2)
+    with pytest.raises(M.MPMError) as e:
+        g.get_state()
+    assert e.value.status == -3
+    spec2 = S.blob(2, 16, 20, 0)
+    spec2.F0[3] = np.diag([1.0, -0.5])
+    g2 = M.Scene(ctx, spec2)
+    g2.step(1)
+    with pytest.raises(M.MPMError) as e:
+        g2.get_state()
+    assert e.value.status == -4
+    # set_state clears the error
+    g2.set_state(*O.Scene(S.blob(2, 16, 20, 0)).initial_state())
+    g2.step(1)
+    g2.get_state()
+
+
+def test_empty_scene(M, ctx):
+    spec = S.blob(2, 16, 1, 0)
+    spec = spec.copy(x0=np.zeros((0, 2)), v0=np.zeros((0, 2)), C0=np.zeros((0, 2, 2)), F0=np.zeros((0, 2, 2)),
+                     group=np.zeros(0, np.int32))
+    g = M.Scene(ctx, spec)
+    g.rollout(3, 1)
+    out = g.backward(np.zeros((0, 2)))
+    assert out[0].shape == (0, 2)
+
+
+# ----------------------------------------------------------------------------- full sizes
+FULL = {
+    "walker_2d": lambda: S.walker_2d(1),
+    "soft_body_3d": lambda: S.soft_body_3d(2),
+    "box_cluster_3d": lambda: S.box_cluster_3d(3),
+}
+
+
+@pytest.mark.parametrize("name", list(FULL))
+def test_full_size_one_step_forward_and_reverse(M, ctx, name):
+    """At the full workload sizes, in the launch configuration the benchmark times: one forward
+    step and one reverse step against the oracle (a step touches every particle and node)."""
+    spec = FULL[name]()
+    osc = O.Scene(spec)
+    st0 = osc.initial_state()
+    step0 = 5
+    gpu = M.Scene(ctx, spec)
+    gpu.set_state(*st0, step=step0)
+    gpu.step(1)
+    ref = oracle_step_from(spec, st0, step0)
+    assert_state_close(gpu.get_state(), ref)
+    # one reverse step: L = <w, x_1> + <u, v_1>
+    rng = np.random.default_rng(3)
+    wx = rng.normal(size=st0[0].shape) / osc.N
+    wv = rng.normal(size=st0[1].shape) / osc.N
+    gpu.set_state(*st0, step=step0)
+    gpu.rollout(1)
+    act = osc.controller(step0, st0[0])
+    (ogx, ogv, ogC, ogF), ogact = osc.step_adjoint(act, st0, (wx, wv, np.zeros_like(st0[2]), np.zeros_like(st0[3])))
+    gx, gv, gC, gF, gp = gpu.backward(wx, wv)
+    ogp, ogx_ctrl = osc.controller_adjoint(step0, st0[0], ogact)
+    for nm, a, b in (("x", gx, ogx + ogx_ctrl), ("v", gv, ogv), ("C", gC, ogC), ("F", gF, ogF)):
+        assert_grad_close(a, b, f"{name} one-step dL/d{nm}")
+    assert_grad_close(gp, ogp, f"{name} one-step dL/dparams")
