@@ -314,6 +314,7 @@ const char* mpm_status_str(mpm_status s) {
     case MPM_ERR_CUDA: return "CUDA error";
     case MPM_ERR_STATE: return "call out of order";
     case MPM_ERR_DENSITY: return "too many particles in one tile";
+    case MPM_ERR_INTERNAL: return "internal consistency check failed";
   }
   return "unknown status";
 }
@@ -737,6 +738,12 @@ mpm_status mpm_backward(mpm_scene* s, const float* gxT, const float* gvT, const 
     const int L = std::min(k, T - sg * k);
     const int c0 = seg_c0[sg];
     if (L > 1) {
+      // bin keys of the checkpoint the recompute starts from
+      if (s->impl != MPM_IMPL_PLAIN) {
+        BatchDev bb = s->b;
+        bb.scenes = table + c0;
+        CK(s->dim == 2 ? launch_keys<2>(bb, st) : launch_keys<3>(bb, st));
+      }
       CKS(set_counter(s, s->d_step, s->roll_start + sg * k));
       for (int j = 0; j + 1 < L; ++j) CKS(forward_step(s, table + c0 + j, confs[c0 + j], s->d_step));
     }

@@ -46,6 +46,7 @@ enum : int {
   ST_INVERTED = -4,  // det F <= 0
   ST_TIMEOUT = -5,   // a bounded device wait ran out
   ST_DENSITY = -8,   // more particles in one tile than the tile kernels stage
+  ST_BINNING = -9,   // a particle's bin key disagrees with its position (access skipped)
 };
 
 __device__ __forceinline__ void set_status(int* st, int code) {

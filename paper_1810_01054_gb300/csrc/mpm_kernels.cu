@@ -266,7 +266,7 @@ __global__ void k_scan_down(BatchDev b, int single) {
 // ============================================================================ P2G (tiled)
 template <int D, bool ADJ>
 struct P2GCfg {
-  static constexpr int RF = 2 * D + D * D;                 // f, a, M
+  static constexpr int RF = 2 * D + D * D + 1;             // f, a, M, mass
   static constexpr int RA = ADJ ? D + D * D : 0;           // a', M'
   static constexpr int RW = ((RF + RA) % 2 == 0) ? RF + RA + 1 : RF + RA;  // odd stride: no bank conflicts
   static constexpr int CHF = D + 1;                        // momentum + mass
@@ -374,9 +374,25 @@ __global__ void __launch_bounds__(256) k_p2g(BatchDev b) {
         int base[D];
         float f[D];
         stencil_base<D>(q.x, sp.inv_dx, sp.n, base, f);
+        // the particle must sit in the cell its key names; otherwise contribute nothing
+        float wm = sp.mass;
+        {
+          int t[D], c[D];
+          unlin<D>(gt - sp.tile_base, sp.nt, t);
+          const int bn[3] = {B, B, B};
+          unlin<D>(int(sp.key[id] & 63u), bn, c);
+          bool ok = true;
+#pragma unroll
+          for (int a = 0; a < D; ++a) ok = ok && base[a] == t[a] * B + c[a];
+          if (!ok) {
+            set_status(sp.status, ST_BINNING);
+            wm = 0.0f;
+          }
+        }
         float P[D][D], A[D][D], G[D][D], sig[D];
         float J = particle_G<D>(q, sp, id, P, A, G, sig);
         if (!(J > 0.0f)) set_status(sp.status, ST_INVERTED);
+        const float keep = wm > 0.0f ? 1.0f : 0.0f;
         float* rec = U + size_t(tid) * K::RW;
         int o = 0;
 #pragma unroll
@@ -387,12 +403,13 @@ __global__ void __launch_bounds__(256) k_p2g(BatchDev b) {
           float s = 0.0f;
 #pragma unroll
           for (int c = 0; c < D; ++c) s += G[a][c] * f[c];
-          rec[o++] = sp.mass * q.v[a] - dx * s;
+          rec[o++] = keep * (sp.mass * q.v[a] - dx * s);
         }
 #pragma unroll
         for (int a = 0; a < D; ++a)
 #pragma unroll
-          for (int c = 0; c < D; ++c) rec[o++] = dx * G[a][c];
+          for (int c = 0; c < D; ++c) rec[o++] = keep * dx * G[a][c];
+        rec[o++] = wm;
         if constexpr (ADJ) {
           // (A) vbar' = gv1 + dt gx1 ; (B) Cbar' = gC1 + dt gF1 F^T ; record for (C):
           // vbar'_p + (4/dx^2) Cbar' (x_i - x_p) = [vbar' - (4/dx) Cbar' f] + (4/dx) Cbar' k
@@ -417,21 +434,21 @@ __global__ void __launch_bounds__(256) k_p2g(BatchDev b) {
             float s = 0.0f;
 #pragma unroll
             for (int c = 0; c < D; ++c) s += Cb[a][c] * f[c];
-            rec[o++] = vb[a] - Dx4 * s;
+            rec[o++] = keep * (vb[a] - Dx4 * s);
           }
 #pragma unroll
           for (int a = 0; a < D; ++a)
 #pragma unroll
-            for (int c = 0; c < D; ++c) rec[o++] = Dx4 * Cb[a][c];
+            for (int c = 0; c < D; ++c) rec[o++] = keep * Dx4 * Cb[a][c];
         }
       }
       __syncthreads();
       if (acc_thread) {
         const int lo = cs > c0 ? cs : c0;
         const int hi = ce < c0 + K::CHUNK ? ce : c0 + K::CHUNK;
-        const float mass = sp.mass;
         for (int ei = lo; ei < hi; ++ei) {
           const float* rec = U + size_t(ei - c0) * K::RW;
+          const float mass = rec[K::RF - 1];
           float w[D][3], dwd[3];
 #pragma unroll
           for (int a = 0; a < D; ++a) bspline(rec[a], 1.0f, w[a], dwd);
@@ -746,10 +763,16 @@ __global__ void __launch_bounds__(256) k_g2p(BatchDev b) {
       int base[D];
       float f[D], w[D][3], dw[3];
       stencil_base<D>(q.x, sp.inv_dx, sp.n, base, f);
+      bool inside = true;
 #pragma unroll
       for (int a = 0; a < D; ++a) {
         bspline(f[a], sp.inv_dx, w[a], dw);
         base[a] -= t[a] * B;  // local stencil origin inside the node block
+        inside = inside && base[a] >= 0 && base[a] < B;
+      }
+      if (!inside) {  // bin key disagrees with the position: never index outside the block
+        set_status(sp.status, ST_BINNING);
+        continue;
       }
       g2p_core<D>(q, f, w, sp.dt, sp.inv_dx, [&](int kx, int ky, int kz) {
         int l = (base[0] + kx) * BN + base[1] + ky;
@@ -942,10 +965,16 @@ __global__ void __launch_bounds__(256) k_adj_gather(BatchDev b) {
       int base[D];
       float f[D], w[D][3], dw[D][3];
       stencil_base<D>(q.x, sp.inv_dx, sp.n, base, f);
+      bool inside = true;
 #pragma unroll
       for (int a = 0; a < D; ++a) {
         bspline(f[a], sp.inv_dx, w[a], dw[a]);
         base[a] -= t[a] * B;
+        inside = inside && base[a] >= 0 && base[a] < B;
+      }
+      if (!inside) {
+        set_status(sp.status, ST_BINNING);
+        continue;
       }
       const float c = adj_core<D>(q, g1, f, w, dw, sp, id, [&](int kx, int ky, int kz, float4& v, float4& p) {
         int l = (base[0] + kx) * BN + base[1] + ky;

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libgbmpm.so")
 MPM_OK = 0
 STATUS = {0: "ok", -1: "invalid argument", -2: "out of device memory or budget", -3: "stencil left the grid",
           -4: "det F <= 0", -5: "bounded device wait expired", -6: "CUDA error", -7: "call out of order",
-          -8: "too many particles in one tile"}
+          -8: "too many particles in one tile", -9: "internal consistency check failed"}
 IMPL_TILED, IMPL_PLAIN = 0, 1
 
 
