@@ -180,6 +180,51 @@ mpm_status mpm_profile_read(mpm_ctx* ctx, int kind, int* count, double* total_ms
 /* Total number of kernels this library has launched in the process (all contexts). */
 mpm_status mpm_launch_count(long long* count);
 
+/* Allocation-free forward step (no counterpart in the paper; an addition for callers that must
+ * not allocate device memory: a control loop with a hard latency budget, where cudaMalloc may
+ * block and synchronise the device, or a process whose device memory is owned entirely by
+ * another allocator).
+ *
+ * One step of the plain form (Eqs. 3-10 with gravity and the boundary condition) from the
+ * caller's state arrays to the caller's output arrays, all device pointers, row-major FP32 as
+ * everywhere in this header; act[g] is the actuation a_g of this step.  The only scratch, the
+ * dense node grid, lives in a fixed array of 2^18 float4 nodes (4 MiB: 512^2 in 2D, 64^3 in 3D)
+ * that every GPU loading this library holds until the process exits; larger grids are rejected
+ * with MPM_ERR_ARG.  No cudaMalloc, cudaFree or allocating library call is made.
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ *    that device current; make that first call before any stream capture.
+ *  - Every call shares the array and clears the part it uses before use; calls whose work
+ *    overlaps on the GPU (e.g. on two streams) race on it.
+ *  - device < 0 keeps the current device; status (device int, may be NULL) receives the first
+ *    device-side error as in the rest of this header.
+ * Asynchronous on cuda_stream (a cudaStream_t, NULL = the legacy default stream). */
+typedef struct {
+  int device;
+  int dim;
+  int n_grid[3];
+  float dx, dt;
+  float gravity[3];
+  float E, nu;
+  float p_mass, p_vol;
+  int bc_type, bc_width;
+  float friction_c;
+  int n_particles;
+  const float* x;        /* [N][dim] */
+  const float* v;        /* [N][dim], NULL = 0 */
+  const float* C;        /* [N][dim][dim], NULL = 0 */
+  const float* F;        /* [N][dim][dim], NULL = identity */
+  const int32_t* group;  /* [N], NULL = all -1 */
+  int n_groups;
+  const float* act_dir;  /* [G][dim] */
+  const float* act;      /* [G] */
+  float* x_out;
+  float* v_out;
+  float* C_out;
+  float* F_out;
+  int* status;
+} mpm_noalloc_step;
+mpm_status mpm_step_noalloc(const mpm_noalloc_step* args, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

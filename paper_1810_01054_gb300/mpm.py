@@ -64,6 +64,39 @@ class SceneDesc(C.Structure):
     ]
 
 
+class NoAllocStep(C.Structure):
+    """Mirror of mpm_noalloc_step (include/mpm.h)."""
+    _fields_ = [
+        ("device", C.c_int),
+        ("dim", C.c_int),
+        ("n_grid", C.c_int * 3),
+        ("dx", C.c_float),
+        ("dt", C.c_float),
+        ("gravity", C.c_float * 3),
+        ("E", C.c_float),
+        ("nu", C.c_float),
+        ("p_mass", C.c_float),
+        ("p_vol", C.c_float),
+        ("bc_type", C.c_int),
+        ("bc_width", C.c_int),
+        ("friction_c", C.c_float),
+        ("n_particles", C.c_int),
+        ("x", C.c_void_p),
+        ("v", C.c_void_p),
+        ("C", C.c_void_p),
+        ("F", C.c_void_p),
+        ("group", C.c_void_p),
+        ("n_groups", C.c_int),
+        ("act_dir", C.c_void_p),
+        ("act", C.c_void_p),
+        ("x_out", C.c_void_p),
+        ("v_out", C.c_void_p),
+        ("C_out", C.c_void_p),
+        ("F_out", C.c_void_p),
+        ("status", C.c_void_p),
+    ]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -91,6 +124,7 @@ _SIGS = {
     "mpm_profile_start": [C.c_void_p, C.c_uint, C.c_int],
     "mpm_profile_read": [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)],
     "mpm_launch_count": [C.POINTER(C.c_longlong)],
+    "mpm_step_noalloc": [C.POINTER(NoAllocStep), C.c_void_p],
 }
 
 K_SORT, K_P2G, K_GRID, K_G2P, K_P2G_ADJ, K_GRID_ADJ, K_ADJ_GATHER, K_CTRL, K_PLAIN = range(9)
