@@ -44,7 +44,8 @@ typedef enum {
   MPM_ERR_TIMEOUT = -5,  /* a bounded device wait ran out */
   MPM_ERR_CUDA = -6,     /* a CUDA call failed */
   MPM_ERR_STATE = -7,    /* call out of order (e.g. backward without a rollout) */
-  MPM_ERR_DENSITY = -8,  /* more particles in one 4^3 / 8^2 cell tile than the kernels stage (4096) */
+  MPM_ERR_DENSITY = -8,  /* more particles in one cell tile than the tile kernels stage: 2048 in a
+                            4x4 tile (2D), 4096 in a 4x4x4 tile (3D) */
   MPM_ERR_INTERNAL = -9  /* a kernel's own consistency check failed (a particle binned to the wrong
                             tile); the offending access was skipped */
 } mpm_status;

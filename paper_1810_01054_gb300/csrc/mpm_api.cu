@@ -1,16 +1,23 @@
 // C ABI of libgbmpm (include/mpm.h): contexts, scenes, stepping, checkpointed rollouts and the
 // rollout-level reverse pass (Section III "memo"; Supplement S2-S5 per step).
 //
+// Every step of a phase (plain stepping, rollout, segment recompute, reverse pass) is the same
+// launch sequence: a selection kernel first copies the scene record of step n (which buffers to
+// read and write) from a device table indexed by the scene's device-resident step counter, then
+// the step's kernels run on that record.  The sequences are captured once as CUDA graphs (one
+// step and GRAPH_STEPS steps per phase) and replayed.
+//
 // Checkpointing: a rollout of T steps stores the state every k steps.  The stored states are
 // written by the step itself (G2P writes out of place at segment boundaries), so storing costs no
 // extra copy.  The reverse pass walks the segments from last to first, recomputes the states of
 // a segment out of place from its checkpoint, then runs the reverse steps of that segment.
-// Memory: ceil(T/k) + (k - 1) + 2 states.  k = 1 keeps every state (the paper's memo) and
+// Memory: ceil(T/k) + (k - 1) + 2 states; k = 1 keeps every state (the paper's memo) and
 // recomputes nothing.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -19,40 +26,61 @@
 
 using namespace gbmpm;
 
+namespace {
+constexpr int GRAPH_STEPS = 8;  // steps per replayed graph
+enum Phase { PH_STEP = 0, PH_ROLL = 1, PH_RCM = 2, PH_REV = 3, PH_PREP = 4, PH_COUNT = 5 };
+std::mutex g_config_mutex;
+bool g_configured[64] = {};
+}  // namespace
+
 struct mpm_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  cudaStream_t capture = nullptr;  // private stream graphs are captured on
   int sm_count = 1;
-  // launch timing (mpm_profile_*): event pairs around launches of the selected kinds
+  // launch timing (mpm_profile_*): event pairs around launches of the selected kinds; while a
+  // mask is set, steps are launched directly (not from graphs) so every launch can be bracketed
   unsigned prof_mask = 0;
   std::vector<cudaEvent_t> prof_ev;
   std::vector<int> prof_kind;
   int prof_used = 0;
 };
 
+struct Graph {
+  cudaGraphExec_t exec = nullptr;
+  long long kernels = 0;
+};
+
 struct mpm_scene {
   mpm_ctx* ctx = nullptr;
   int dim = 0, N = 0, npad = 0, G = 0, nparams = 0, impl = 0, n_nodes = 0;
   size_t state_bytes = 0;
-  ScenePar hp{};             // host template of the device scene record
+  ScenePar hp{};             // host template of the scene record
   CtrlPar ctrl{};
-  BatchDev b{};              // private batch of one scene (tiled form)
+  BatchDev b{};              // private batch of one scene; b.scenes = cur
   std::vector<void*> allocs; // everything allocated at creation
   float4* state = nullptr;   // current state planes
   float4* adj[2] = {nullptr, nullptr};
   int* d_step = nullptr;     // forward step counter (controller time)
   int* d_bstep = nullptr;    // reverse step counter
   int* d_status = nullptr;
+  ScenePar* cur = nullptr;   // device: the record of the running step
+  SelectPar* dsel = nullptr; // device: one selection per phase
+  SelectPar hsel[PH_COUNT]{};
   int step = 0;              // host mirror of the current step
-  // device scene records, one cached table per purpose (uploaded only when its content changes):
-  // table 0 = in-place forward on `state`, 1 = rollout, 2 = reverse pass
-  ScenePar* dconf = nullptr;  // == tables[0].dev
+  // device record tables, one per phase family (uploaded only when their content changes)
   struct Table {
     ScenePar* dev = nullptr;
     int cap = 0;
     std::vector<ScenePar> host;
-  } tables[3];
+  } tables[3];               // 0 = in-place step, 1 = rollout, 2 = recompute + reverse
+  struct Map {
+    int* dev = nullptr;
+    int cap = 0;
+    std::vector<int> host;
+  } maps[3];                 // record index per step: rollout, recompute, reverse
+  Graph graphs[PH_COUNT][2]; // [phase][single step, GRAPH_STEPS steps]
   // rollout record
   bool have_rollout = false;
   int roll_T = 0, roll_k = 0, roll_start = 0, roll_nseg = 0;
@@ -78,20 +106,19 @@ mpm_status cuda_fail(cudaError_t e) {
     if (e_ != cudaSuccess) return cuda_fail(e_); \
   } while (0)
 
-#define CKS(expr)                   \
-  do {                              \
-    mpm_status s_ = (expr);         \
-    if (s_ != MPM_OK) return s_;    \
+#define CKS(expr)                \
+  do {                           \
+    mpm_status s_ = (expr);      \
+    if (s_ != MPM_OK) return s_; \
   } while (0)
 
 template <class T>
-mpm_status dalloc(mpm_scene* s, T** p, size_t count, std::vector<void*>& list) {
+mpm_status dalloc(T** p, size_t count, std::vector<void*>& list) {
   void* q = nullptr;
   size_t bytes = std::max<size_t>(count * sizeof(T), 16);
   CK(cudaMalloc(&q, bytes));
   list.push_back(q);
   *p = reinterpret_cast<T*>(q);
-  (void)s;
   return MPM_OK;
 }
 
@@ -120,7 +147,7 @@ mpm_status stage(mpm_scene* s, const void* src, size_t bytes, int mem_space, siz
     return MPM_OK;
   }
   char* dst = reinterpret_cast<char*>(s->scratch) + offset;
-  CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s->ctx->stream));
+  if (bytes) CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s->ctx->stream));
   *out = dst;
   return MPM_OK;
 }
@@ -136,142 +163,235 @@ mpm_status ensure_scratch(mpm_scene* s, size_t bytes) {
   return MPM_OK;
 }
 
-
-// Upload a table of scene records unless the device already holds exactly this table
-// (synchronously: work enqueued afterwards reads it, and work in flight may read the old one).
-mpm_status upload_conf(mpm_scene* s, int which, const std::vector<ScenePar>& confs, ScenePar** dev) {
-  auto& t = s->tables[which];
-  const bool same = t.host.size() == confs.size() &&
-                    std::memcmp(t.host.data(), confs.data(), sizeof(ScenePar) * confs.size()) == 0;
-  if (!same) {
-    CK(cudaStreamSynchronize(s->ctx->stream));
-    if (int(confs.size()) > t.cap) {
-      if (t.dev) cudaFree(t.dev);
-      t.dev = nullptr;
-      t.cap = 0;
-      CK(cudaMalloc(&t.dev, sizeof(ScenePar) * confs.size()));
-      t.cap = int(confs.size());
-    }
-    CK(cudaMemcpy(t.dev, confs.data(), sizeof(ScenePar) * confs.size(), cudaMemcpyHostToDevice));
-    t.host = confs;
-  }
-  if (dev) *dev = t.dev;
-  if (which == 0) s->dconf = t.dev;
+// The selection of every phase points at tables and maps through device SelectPar records, so
+// graphs captured once stay valid when tables or maps are re-uploaded or grown.
+mpm_status upload_sel(mpm_scene* s) {
+  CK(cudaStreamSynchronize(s->ctx->stream));
+  CK(cudaMemcpy(s->dsel, s->hsel, sizeof(s->hsel), cudaMemcpyHostToDevice));
   return MPM_OK;
 }
 
-ScenePar conf_fwd(const mpm_scene* s, float4* in, float4* out) {
+// Upload a table of scene records unless the device already holds exactly this table.
+mpm_status upload_table(mpm_scene* s, int which, const std::vector<ScenePar>& confs) {
+  auto& t = s->tables[which];
+  const bool same = t.host.size() == confs.size() &&
+                    std::memcmp(t.host.data(), confs.data(), sizeof(ScenePar) * confs.size()) == 0;
+  if (same) return MPM_OK;
+  CK(cudaStreamSynchronize(s->ctx->stream));
+  bool moved = false;
+  if (int(confs.size()) > t.cap) {
+    if (t.dev) cudaFree(t.dev);
+    t.dev = nullptr;
+    t.cap = 0;
+    CK(cudaMalloc(&t.dev, sizeof(ScenePar) * confs.size()));
+    t.cap = int(confs.size());
+    moved = true;
+  }
+  CK(cudaMemcpy(t.dev, confs.data(), sizeof(ScenePar) * confs.size(), cudaMemcpyHostToDevice));
+  t.host = confs;
+  if (moved) {
+    for (int ph = 0; ph < PH_COUNT; ++ph) {
+      const int tw = ph == PH_STEP ? 0 : ph == PH_ROLL ? 1 : 2;
+      if (tw == which) s->hsel[ph].table = t.dev;
+    }
+    CKS(upload_sel(s));
+  }
+  return MPM_OK;
+}
+
+mpm_status upload_map(mpm_scene* s, int which, const std::vector<int>& m, int base) {
+  auto& mp = s->maps[which];
+  const bool same = mp.host == m;
+  const int phs[3][2] = {{PH_ROLL, -1}, {PH_RCM, PH_PREP}, {PH_REV, -1}};
+  bool sel_changed = false;
+  for (int ph : phs[which])
+    if (ph >= 0 && s->hsel[ph].base != base) {
+      s->hsel[ph].base = base;
+      sel_changed = true;
+    }
+  if (!same) {
+    CK(cudaStreamSynchronize(s->ctx->stream));
+    if (int(m.size()) > mp.cap) {
+      if (mp.dev) cudaFree(mp.dev);
+      mp.dev = nullptr;
+      mp.cap = 0;
+      CK(cudaMalloc(&mp.dev, sizeof(int) * std::max<size_t>(m.size(), 1)));
+      mp.cap = int(m.size());
+      for (int ph : phs[which])
+        if (ph >= 0) s->hsel[ph].map = mp.dev;
+      sel_changed = true;
+    }
+    if (!m.empty()) CK(cudaMemcpy(mp.dev, m.data(), sizeof(int) * m.size(), cudaMemcpyHostToDevice));
+    mp.host = m;
+  }
+  if (sel_changed) CKS(upload_sel(s));
+  return MPM_OK;
+}
+
+ScenePar rec_fwd(const mpm_scene* s, float4* in, float4* out) {
   ScenePar p = s->hp;
   p.planes = in;
   p.planes_out = out;
+  p.step_ctr = s->d_step;
   return p;
 }
 
-ScenePar conf_bwd(const mpm_scene* s, float4* st, const float4* ain, float4* aout) {
+ScenePar rec_rev(const mpm_scene* s, float4* st, const float4* ain, float4* aout) {
   ScenePar p = s->hp;
   p.planes = st;
   p.planes_out = st;
   p.adj_in = ain;
   p.adj_out = aout;
+  p.step_ctr = s->d_bstep;
   return p;
-}
-
-mpm_status set_counter(mpm_scene* s, int* dctr, int value) {
-  CK(launch_set_int(dctr, value, s->ctx->stream));
-  return MPM_OK;
 }
 
 // Event pair around one launch of kind k (no-op unless k is being timed).
 struct ProfScope {
   mpm_ctx* c;
+  cudaStream_t st;
   int slot = -1;
-  ProfScope(mpm_ctx* ctx, int kind) : c(ctx) {
+  ProfScope(mpm_ctx* ctx, cudaStream_t stream, int kind) : c(ctx), st(stream) {
     if (!(c->prof_mask & (1u << kind))) return;
     if (2 * (c->prof_used + 1) > int(c->prof_ev.size())) return;
     slot = c->prof_used++;
     c->prof_kind[slot] = kind;
-    cudaEventRecord(c->prof_ev[2 * slot], c->stream);
+    cudaEventRecord(c->prof_ev[2 * slot], st);
   }
   ~ProfScope() {
-    if (slot >= 0) cudaEventRecord(c->prof_ev[2 * slot + 1], c->stream);
+    if (slot >= 0) cudaEventRecord(c->prof_ev[2 * slot + 1], st);
   }
 };
 
-// One forward step with device record `dsp` (host copy `hsp`).
-mpm_status forward_step(mpm_scene* s, const ScenePar* dsp, const ScenePar& hsp, int* ctr) {
-  cudaStream_t st = s->ctx->stream;
+// ---------------------------------------------------------------------------- step sequences
+// Forward step of phase ph (PH_STEP, PH_ROLL, PH_RCM) on stream st.
+mpm_status enqueue_forward(mpm_scene* s, int ph, cudaStream_t st) {
   mpm_ctx* c = s->ctx;
+  CK(launch_select(s->dsel + ph, 1, s->cur, st));
   {
-    ProfScope p(c, MPM_K_CTRL);
-    CK(ctrl_step_forward(hsp, dsp, s->ctrl, ctr, 1, st));
+    ProfScope p(c, st, MPM_K_CTRL);
+    CK(ctrl_step_forward(s->hp, s->cur, s->ctrl, st));
   }
   if (s->impl == MPM_IMPL_PLAIN) {
-    ProfScope p(c, MPM_K_PLAIN);
-    CK(s->dim == 2 ? launch_plain_step<2>(dsp, hsp, st) : launch_plain_step<3>(dsp, hsp, st));
+    ProfScope p(c, st, MPM_K_PLAIN);
+    CK(s->dim == 2 ? launch_plain_step<2>(s->cur, s->hp, st) : launch_plain_step<3>(s->cur, s->hp, st));
     return MPM_OK;
   }
-  BatchDev bb = s->b;
-  bb.scenes = const_cast<ScenePar*>(dsp);
   const bool two = s->dim == 2;
   {
-    ProfScope p(c, MPM_K_SORT);
-    CK(two ? launch_sort<2>(bb, st) : launch_sort<3>(bb, st));
+    ProfScope p(c, st, MPM_K_SORT);
+    CK(two ? launch_sort<2>(s->b, st) : launch_sort<3>(s->b, st));
   }
   {
-    ProfScope p(c, MPM_K_P2G);
-    CK(two ? launch_p2g<2>(bb, false, st) : launch_p2g<3>(bb, false, st));
+    ProfScope p(c, st, MPM_K_P2G);
+    CK(two ? launch_p2g<2>(s->b, false, st) : launch_p2g<3>(s->b, false, st));
   }
   {
-    ProfScope p(c, MPM_K_GRID);
-    CK(two ? launch_grid<2>(bb, false, st) : launch_grid<3>(bb, false, st));
-  }
-  {
-    ProfScope p(c, MPM_K_G2P);
-    CK(two ? launch_g2p<2>(bb, st) : launch_g2p<3>(bb, st));
+    ProfScope p(c, st, MPM_K_G2P);
+    CK(two ? launch_g2p<2>(s->b, st) : launch_g2p<3>(s->b, st));
   }
   return MPM_OK;
 }
 
-// One reverse step on record `dsp` (state n, adjoint n+1 in, adjoint n out).
-mpm_status reverse_step(mpm_scene* s, const ScenePar* dsp, const ScenePar& hsp) {
-  cudaStream_t st = s->ctx->stream;
+// Reverse step (state n, adjoint n+1 in, adjoint n out), n = *d_bstep.
+mpm_status enqueue_reverse(mpm_scene* s, cudaStream_t st) {
   mpm_ctx* c = s->ctx;
-  BatchDev bb = s->b;
-  bb.scenes = const_cast<ScenePar*>(dsp);
   const bool two = s->dim == 2;
+  CK(launch_select(s->dsel + PH_REV, 1, s->cur, st));
   if (s->impl != MPM_IMPL_PLAIN) {
-    ProfScope p(c, MPM_K_SORT);
-    CK(two ? launch_keys<2>(bb, st) : launch_keys<3>(bb, st));
+    ProfScope p(c, st, MPM_K_SORT);
+    CK(two ? launch_keys<2>(s->b, st) : launch_keys<3>(s->b, st));
   }
   {
-    ProfScope p(c, MPM_K_CTRL);
-    CK(ctrl_step_forward(hsp, dsp, s->ctrl, s->d_bstep, 0, st));
+    ProfScope p(c, st, MPM_K_CTRL);
+    CK(ctrl_step_forward(s->hp, s->cur, s->ctrl, st));
   }
   if (s->impl == MPM_IMPL_PLAIN) {
-    ProfScope p(c, MPM_K_PLAIN);
-    CK(two ? launch_plain_adjoint<2>(dsp, hsp, st) : launch_plain_adjoint<3>(dsp, hsp, st));
+    ProfScope p(c, st, MPM_K_PLAIN);
+    CK(two ? launch_plain_adjoint<2>(s->cur, s->hp, s->b.gpartial, st)
+           : launch_plain_adjoint<3>(s->cur, s->hp, s->b.gpartial, st));
   } else {
     {
-      ProfScope p(c, MPM_K_SORT);
-      CK(two ? launch_sort<2>(bb, st) : launch_sort<3>(bb, st));
+      ProfScope p(c, st, MPM_K_SORT);
+      CK(two ? launch_sort<2>(s->b, st) : launch_sort<3>(s->b, st));
     }
     {
-      ProfScope p(c, MPM_K_P2G_ADJ);
-      CK(two ? launch_p2g<2>(bb, true, st) : launch_p2g<3>(bb, true, st));
+      ProfScope p(c, st, MPM_K_P2G_ADJ);
+      CK(two ? launch_p2g<2>(s->b, true, st) : launch_p2g<3>(s->b, true, st));
     }
     {
-      ProfScope p(c, MPM_K_GRID_ADJ);
-      CK(two ? launch_grid<2>(bb, true, st) : launch_grid<3>(bb, true, st));
-    }
-    {
-      ProfScope p(c, MPM_K_ADJ_GATHER);
-      CK(two ? launch_adj_gather<2>(bb, st) : launch_adj_gather<3>(bb, st));
+      ProfScope p(c, st, MPM_K_ADJ_GATHER);
+      CK(two ? launch_adj_gather<2>(s->b, st) : launch_adj_gather<3>(s->b, st));
     }
   }
   {
-    ProfScope p(c, MPM_K_CTRL);
-    CK(ctrl_step_backward(hsp, dsp, s->ctrl, s->d_bstep, st));
+    ProfScope p(c, st, MPM_K_CTRL);
+    CK(ctrl_step_backward(s->hp, s->cur, s->ctrl, st));
   }
+  return MPM_OK;
+}
+
+// Bin keys and tile histogram of the state the selection of phase ph names (tiled form only).
+mpm_status enqueue_keys(mpm_scene* s, int ph, cudaStream_t st) {
+  if (s->impl == MPM_IMPL_PLAIN) return MPM_OK;
+  CK(launch_select(s->dsel + ph, 1, s->cur, st));
+  CK(s->dim == 2 ? launch_keys<2>(s->b, st) : launch_keys<3>(s->b, st));
+  return MPM_OK;
+}
+
+mpm_status enqueue_phase(mpm_scene* s, int ph, cudaStream_t st) {
+  if (ph == PH_REV) return enqueue_reverse(s, st);
+  if (ph == PH_PREP) return enqueue_keys(s, PH_PREP, st);
+  return enqueue_forward(s, ph, st);
+}
+
+mpm_status capture(mpm_scene* s, int ph, int steps, Graph* g) {
+  mpm_ctx* c = s->ctx;
+  long long tally = 0;
+  CK(cudaStreamBeginCapture(c->capture, cudaStreamCaptureModeThreadLocal));
+  capture_tally(&tally);
+  mpm_status st = MPM_OK;
+  for (int i = 0; i < steps && st == MPM_OK; ++i) st = enqueue_phase(s, ph, c->capture);
+  capture_tally(nullptr);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->capture, &graph);
+  if (st != MPM_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  CK(e);
+  e = cudaGraphInstantiate(&g->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  CK(e);
+  g->kernels = tally;
+  return MPM_OK;
+}
+
+// Runs `count` steps of phase ph on the context stream: graph replays, or direct launches while
+// launch timing is on.
+mpm_status run_phase(mpm_scene* s, int ph, int count) {
+  mpm_ctx* c = s->ctx;
+  if (count <= 0) return MPM_OK;
+  if (c->prof_mask) {
+    for (int i = 0; i < count; ++i) CKS(enqueue_phase(s, ph, c->stream));
+    return MPM_OK;
+  }
+  const int big = count / GRAPH_STEPS, small = count % GRAPH_STEPS;
+  if (big > 0 && !s->graphs[ph][1].exec) CKS(capture(s, ph, GRAPH_STEPS, &s->graphs[ph][1]));
+  if (small > 0 && !s->graphs[ph][0].exec) CKS(capture(s, ph, 1, &s->graphs[ph][0]));
+  for (int i = 0; i < big; ++i) {
+    CK(cudaGraphLaunch(s->graphs[ph][1].exec, c->stream));
+    count_launches(int(s->graphs[ph][1].kernels));
+  }
+  for (int i = 0; i < small; ++i) {
+    CK(cudaGraphLaunch(s->graphs[ph][0].exec, c->stream));
+    count_launches(int(s->graphs[ph][0].kernels));
+  }
+  return MPM_OK;
+}
+
+mpm_status set_counter(mpm_scene* s, int* dctr, int value) {
+  CK(launch_set_int(dctr, value, s->ctx->stream));
   return MPM_OK;
 }
 
@@ -280,14 +400,6 @@ mpm_status read_status(mpm_scene* s) {
   CK(cudaStreamSynchronize(s->ctx->stream));
   CK(cudaMemcpy(&v, s->d_status, sizeof(int), cudaMemcpyDeviceToHost));
   return mpm_status(v);
-}
-
-mpm_status refresh_keys(mpm_scene* s) {
-  if (s->impl == MPM_IMPL_PLAIN) return MPM_OK;
-  BatchDev bb = s->b;
-  bb.scenes = s->dconf;
-  CK(s->dim == 2 ? launch_keys<2>(bb, s->ctx->stream) : launch_keys<3>(bb, s->ctx->stream));
-  return MPM_OK;
 }
 
 void free_rollout(mpm_scene* s) {
@@ -324,16 +436,29 @@ mpm_status mpm_ctx_create(mpm_ctx** out, int device, void* cuda_stream) {
   *out = nullptr;
   int ndev = 0;
   CK(cudaGetDeviceCount(&ndev));
-  if (device < 0 || device >= ndev) return MPM_ERR_ARG;
+  if (device < 0 || device >= ndev || device >= 64) return MPM_ERR_ARG;
   CK(cudaSetDevice(device));
+  {
+    std::lock_guard<std::mutex> lock(g_config_mutex);
+    if (!g_configured[device]) {
+      CK(configure_kernels());
+      g_configured[device] = true;
+    }
+  }
   mpm_ctx* c = new (std::nothrow) mpm_ctx();
   if (!c) return MPM_ERR_OOM;
   c->device = device;
+  cudaError_t e = cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_fail(e);
+  }
   if (cuda_stream) {
     c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
   } else {
-    cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
+      cudaStreamDestroy(c->capture);
       delete c;
       return cuda_fail(e);
     }
@@ -348,6 +473,7 @@ mpm_status mpm_ctx_destroy(mpm_ctx* c) {
   if (!c) return MPM_ERR_ARG;
   cudaStreamSynchronize(c->stream);
   for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+  cudaStreamDestroy(c->capture);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
   return MPM_OK;
@@ -364,9 +490,14 @@ mpm_status mpm_scene_destroy(mpm_scene* s) {
   if (!s) return MPM_ERR_ARG;
   cudaStreamSynchronize(s->ctx->stream);
   free_rollout(s);
+  for (auto& row : s->graphs)
+    for (auto& g : row)
+      if (g.exec) cudaGraphExecDestroy(g.exec);
   for (void* p : s->allocs) cudaFree(p);
   for (auto& t : s->tables)
     if (t.dev) cudaFree(t.dev);
+  for (auto& m : s->maps)
+    if (m.dev) cudaFree(m.dev);
   if (s->scratch) cudaFree(s->scratch);
   delete s;
   return MPM_OK;
@@ -437,18 +568,20 @@ mpm_status mpm_scene_create(mpm_ctx* c, const mpm_scene_desc* d, mpm_scene** out
   p.N = s->N;
   p.npad = s->npad;
   p.G = s->G;
-  p.tile_base = 0;
-  p.pbase = 0;
 
   auto fail = [&](mpm_status st) {
     mpm_scene_destroy(s);
     return st;
   };
   mpm_status st = MPM_OK;
-#define ALLOC(ptr, n)                                       \
-  do {                                                      \
-    st = dalloc(s, &(ptr), size_t(n), s->allocs);           \
-    if (st != MPM_OK) return fail(st);                      \
+#define ALLOC(ptr, n)                              \
+  do {                                             \
+    st = dalloc(&(ptr), size_t(n), s->allocs);     \
+    if (st != MPM_OK) return fail(st);             \
+  } while (0)
+#define TRY(expr)                                  \
+  do {                                             \
+    if ((st = (expr)) != MPM_OK) return fail(st);  \
   } while (0)
   ALLOC(s->state, size_t(PL) * s->npad);
   ALLOC(s->adj[0], size_t(PL) * s->npad);
@@ -468,6 +601,8 @@ mpm_status mpm_scene_create(mpm_ctx* c, const mpm_scene_desc* d, mpm_scene** out
   ALLOC(s->d_step, 1);
   ALLOC(s->d_bstep, 1);
   ALLOC(s->d_status, 1);
+  ALLOC(s->cur, 1);
+  ALLOC(s->dsel, PH_COUNT);
   p.planes = p.planes_out = s->state;
   p.key = key;
   p.grid = grid;
@@ -478,6 +613,7 @@ mpm_status mpm_scene_create(mpm_ctx* c, const mpm_scene_desc* d, mpm_scene** out
   p.act_grad = act_grad;
   p.sig_contrib = sig;
   p.status = s->d_status;
+  p.step_ctr = s->d_step;
   // controller
   CtrlPar& cp = s->ctrl;
   cp.type = d->ctrl_type;
@@ -502,8 +638,9 @@ mpm_status mpm_scene_create(mpm_ctx* c, const mpm_scene_desc* d, mpm_scene** out
   cp.gz = gz;
   cp.partials = partials;
   cp.n_partials = rows;
-  // batch of one
+  // batch of one scene
   BatchDev& b = s->b;
+  b.scenes = s->cur;
   b.n_scenes = 1;
   b.total_particles = s->N;
   b.total_tiles = p.n_tiles;
@@ -518,79 +655,88 @@ mpm_status mpm_scene_create(mpm_ctx* c, const mpm_scene_desc* d, mpm_scene** out
   ALLOC(b.tile_slot, p.n_tiles);
   ALLOC(b.active, p.n_tiles);
   ALLOC(b.n_active, 1);
-  ALLOC(b.block_sums, 2 * ((p.n_tiles + 8191) / 8192) + 2);
+  ALLOC(b.block_sums, 2 * ((p.n_tiles + 2047) / 2048) + 2);
   ALLOC(b.sorted, s->npad);
   if (s->impl == MPM_IMPL_TILED) {
     ALLOC(b.partial, size_t(p.n_tiles) * NB);
     ALLOC(b.partial_b, size_t(p.n_tiles) * NB);
   }
-#undef ALLOC
+  const int plain_rows = (s->N + 255) / 256;
+  ALLOC(b.gpartial, size_t(std::max(std::max(p.n_tiles, plain_rows), 1)) * MAX_GROUPS);
+  cp.gpart = b.gpartial;
+  cp.active = s->impl == MPM_IMPL_TILED ? b.active : nullptr;
+  cp.n_active = b.n_active;
+  cp.plain_rows = plain_rows;
   b.scene_pbase = pbase;
   b.tile_scene = tile_scene;
   b.max_ctas = c->sm_count * 4;
   b.p2g_block = 256;
   cudaStream_t stream = c->stream;
-  // zero-initialised counters and scene tables
-  if ((st = cuda_fail(cudaMemsetAsync(b.tile_count, 0, sizeof(uint32_t) * p.n_tiles, stream))) != MPM_OK) return fail(st);
-  if ((st = cuda_fail(cudaMemsetAsync(b.tile_fill, 0, sizeof(uint32_t) * p.n_tiles, stream))) != MPM_OK) return fail(st);
-  if ((st = cuda_fail(cudaMemsetAsync(tile_scene, 0, sizeof(int) * p.n_tiles, stream))) != MPM_OK) return fail(st);
-  if ((st = cuda_fail(cudaMemsetAsync(s->d_status, 0, sizeof(int), stream))) != MPM_OK) return fail(st);
-  if ((st = cuda_fail(cudaMemsetAsync(s->d_step, 0, sizeof(int), stream))) != MPM_OK) return fail(st);
-  if ((st = cuda_fail(cudaMemsetAsync(grid, 0, sizeof(float4) * s->n_nodes, stream))) != MPM_OK) return fail(st);
-  if ((st = cuda_fail(cudaMemsetAsync(grid_b, 0, sizeof(float4) * s->n_nodes, stream))) != MPM_OK) return fail(st);
-  if ((st = cuda_fail(cudaMemsetAsync(group, 0xff, sizeof(int32_t) * s->npad, stream))) != MPM_OK) return fail(st);
-  if ((st = cuda_fail(cudaMemsetAsync(sig, 0, sizeof(float) * s->npad, stream))) != MPM_OK) return fail(st);
+  TRY(cuda_fail(cudaMemsetAsync(b.tile_count, 0, sizeof(uint32_t) * p.n_tiles, stream)));
+  TRY(cuda_fail(cudaMemsetAsync(b.tile_fill, 0, sizeof(uint32_t) * p.n_tiles, stream)));
+  TRY(cuda_fail(cudaMemsetAsync(tile_scene, 0, sizeof(int) * p.n_tiles, stream)));
+  TRY(cuda_fail(cudaMemsetAsync(s->d_status, 0, sizeof(int), stream)));
+  TRY(cuda_fail(cudaMemsetAsync(s->d_step, 0, sizeof(int), stream)));
+  TRY(cuda_fail(cudaMemsetAsync(s->d_bstep, 0, sizeof(int), stream)));
+  TRY(cuda_fail(cudaMemsetAsync(grid, 0, sizeof(float4) * s->n_nodes, stream)));
+  TRY(cuda_fail(cudaMemsetAsync(grid_b, 0, sizeof(float4) * s->n_nodes, stream)));
+  TRY(cuda_fail(cudaMemsetAsync(group, 0xff, sizeof(int32_t) * s->npad, stream)));
+  TRY(cuda_fail(cudaMemsetAsync(sig, 0, sizeof(float) * s->npad, stream)));
   {
     int hb[2] = {0, s->N};
-    if ((st = cuda_fail(cudaMemcpy(pbase, hb, sizeof(hb), cudaMemcpyHostToDevice))) != MPM_OK) return fail(st);
+    TRY(cuda_fail(cudaMemcpy(pbase, hb, sizeof(hb), cudaMemcpyHostToDevice)));
   }
   // inputs
   const size_t xb = sizeof(float) * size_t(s->N) * dim, mb = xb * dim;
-  if ((st = ensure_scratch(s, 2 * xb + 2 * mb + sizeof(int32_t) * s->N + 64 * 4)) != MPM_OK) return fail(st);
+  TRY(ensure_scratch(s, 2 * xb + 2 * mb + sizeof(int32_t) * s->N + 256));
   const void *x0, *v0, *C0, *F0, *grp;
-  if ((st = stage(s, d->x0, xb, d->mem_space, 0, &x0)) != MPM_OK) return fail(st);
-  if ((st = stage(s, d->v0, xb, d->mem_space, xb, &v0)) != MPM_OK) return fail(st);
-  if ((st = stage(s, d->C0, mb, d->mem_space, 2 * xb, &C0)) != MPM_OK) return fail(st);
-  if ((st = stage(s, d->F0, mb, d->mem_space, 2 * xb + mb, &F0)) != MPM_OK) return fail(st);
-  if ((st = stage(s, d->group, sizeof(int32_t) * s->N, d->mem_space, 2 * xb + 2 * mb, &grp)) != MPM_OK) return fail(st);
-  if ((st = cuda_fail(launch_pack(dim, s->N, s->npad, (const float*)x0, (const float*)v0, (const float*)C0,
-                                  (const float*)F0, s->state, s->d_status, stream))) != MPM_OK)
-    return fail(st);
-  if (grp && s->N > 0) {
-    if ((st = cuda_fail(cudaMemcpyAsync(group, grp, sizeof(int32_t) * s->N, cudaMemcpyDeviceToDevice, stream))) != MPM_OK)
-      return fail(st);
-  }
-  if ((st = cuda_fail(cudaStreamSynchronize(stream))) != MPM_OK) return fail(st);
+  TRY(stage(s, d->x0, xb, d->mem_space, 0, &x0));
+  TRY(stage(s, d->v0, xb, d->mem_space, xb, &v0));
+  TRY(stage(s, d->C0, mb, d->mem_space, 2 * xb, &C0));
+  TRY(stage(s, d->F0, mb, d->mem_space, 2 * xb + mb, &F0));
+  TRY(stage(s, d->group, sizeof(int32_t) * s->N, d->mem_space, 2 * xb + 2 * mb, &grp));
+  TRY(cuda_fail(launch_pack(dim, s->N, s->npad, (const float*)x0, (const float*)v0, (const float*)C0,
+                            (const float*)F0, s->state, s->d_status, stream)));
+  if (grp && s->N > 0)
+    TRY(cuda_fail(cudaMemcpyAsync(group, grp, sizeof(int32_t) * s->N, cudaMemcpyDeviceToDevice, stream)));
+  TRY(cuda_fail(cudaStreamSynchronize(stream)));
   // small per-group arrays go through the host so group sizes can be counted there
   std::vector<float> hdir(std::max(1, s->G * dim), 0.f), hparams(std::max(1, np), 0.f), hinv(std::max(1, s->G), 0.f);
   std::vector<int32_t> hgroup(s->N, -1);
   {
     cudaMemcpyKind k = d->mem_space == 1 ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
-    if (s->G > 0 && (st = cuda_fail(cudaMemcpy(hdir.data(), d->act_dir, sizeof(float) * s->G * dim, k))) != MPM_OK)
-      return fail(st);
-    if (np > 0 && (st = cuda_fail(cudaMemcpy(hparams.data(), d->ctrl_params, sizeof(float) * np, k))) != MPM_OK)
-      return fail(st);
-    if (d->group && s->N > 0 &&
-        (st = cuda_fail(cudaMemcpy(hgroup.data(), d->group, sizeof(int32_t) * s->N, k))) != MPM_OK)
-      return fail(st);
+    if (s->G > 0) TRY(cuda_fail(cudaMemcpy(hdir.data(), d->act_dir, sizeof(float) * s->G * dim, k)));
+    if (np > 0) TRY(cuda_fail(cudaMemcpy(hparams.data(), d->ctrl_params, sizeof(float) * np, k)));
+    if (d->group && s->N > 0) TRY(cuda_fail(cudaMemcpy(hgroup.data(), d->group, sizeof(int32_t) * s->N, k)));
   }
   std::vector<int> count(std::max(1, s->G), 0);
   for (int i = 0; i < s->N; ++i)
     if (hgroup[i] >= 0 && hgroup[i] < s->G) count[hgroup[i]]++;
   for (int g = 0; g < s->G; ++g) hinv[g] = count[g] > 0 ? 1.0f / float(count[g]) : 0.0f;
-  if ((st = cuda_fail(cudaMemcpy(act_dir, hdir.data(), sizeof(float) * hdir.size(), cudaMemcpyHostToDevice))) != MPM_OK)
-    return fail(st);
-  if ((st = cuda_fail(cudaMemcpy(params, hparams.data(), sizeof(float) * hparams.size(), cudaMemcpyHostToDevice))) != MPM_OK)
-    return fail(st);
-  if ((st = cuda_fail(cudaMemcpy(inv_count, hinv.data(), sizeof(float) * hinv.size(), cudaMemcpyHostToDevice))) != MPM_OK)
-    return fail(st);
-  std::vector<ScenePar> confs(1, conf_fwd(s, s->state, s->state));
-  if ((st = upload_conf(s, 0, confs, nullptr)) != MPM_OK) return fail(st);
-  if ((st = refresh_keys(s)) != MPM_OK) return fail(st);
-  int v = 0;
-  if ((st = cuda_fail(cudaStreamSynchronize(stream))) != MPM_OK) return fail(st);
-  if ((st = cuda_fail(cudaMemcpy(&v, s->d_status, sizeof(int), cudaMemcpyDeviceToHost))) != MPM_OK) return fail(st);
-  if (v != 0) return fail(mpm_status(v));
+  TRY(cuda_fail(cudaMemcpy(act_dir, hdir.data(), sizeof(float) * hdir.size(), cudaMemcpyHostToDevice)));
+  TRY(cuda_fail(cudaMemcpy(params, hparams.data(), sizeof(float) * hparams.size(), cudaMemcpyHostToDevice)));
+  TRY(cuda_fail(cudaMemcpy(inv_count, hinv.data(), sizeof(float) * hinv.size(), cudaMemcpyHostToDevice)));
+  // selections: PH_STEP uses record 0 of table 0 with the forward counter; the others are filled
+  // in by mpm_rollout / mpm_backward
+  std::vector<ScenePar> t0(1, rec_fwd(s, s->state, s->state));
+  for (int ph = 0; ph < PH_COUNT; ++ph) {
+    SelectPar& q = s->hsel[ph];
+    std::memset(&q, 0, sizeof(q));
+    q.ctr = ph == PH_REV ? s->d_bstep : s->d_step;
+    q.ctrl_type = d->ctrl_type;
+    q.G = s->G;
+    q.freq = d->ctrl_freq;
+    q.dt = d->dt;
+    q.params = params;
+    q.act = act;
+  }
+  TRY(upload_table(s, 0, t0));
+  s->hsel[PH_STEP].table = s->tables[0].dev;
+  TRY(upload_sel(s));
+  TRY(enqueue_keys(s, PH_STEP, stream));
+  TRY(read_status(s));
+#undef ALLOC
+#undef TRY
   *out = s;
   return MPM_OK;
 }
@@ -609,7 +755,7 @@ mpm_status mpm_scene_info(const mpm_scene* s, int* n_particles, int* n_groups, i
 mpm_status mpm_step(mpm_scene* s, int n_steps) {
   if (!s || n_steps < 0) return MPM_ERR_ARG;
   s->have_rollout = false;
-  for (int i = 0; i < n_steps; ++i) CKS(forward_step(s, s->dconf, s->hp, s->d_step));
+  CKS(run_phase(s, PH_STEP, n_steps));
   s->step += n_steps;
   CK(cudaGetLastError());
   return MPM_OK;
@@ -619,13 +765,7 @@ mpm_status mpm_rollout(mpm_scene* s, int T, int k, size_t budget) {
   if (!s || T < 1 || k < 0) return MPM_ERR_ARG;
   s->have_rollout = false;
   const size_t S = s->state_bytes;
-  if (k == 0) {
-    if (budget == 0 || size_t(T) * S <= budget) {
-      k = 1;
-    } else {
-      k = int(std::ceil(std::sqrt(double(T))));
-    }
-  }
+  if (k == 0) k = (budget == 0 || size_t(T) * S <= budget) ? 1 : int(std::ceil(std::sqrt(double(T))));
   k = std::min(k, T);
   const int nseg = (T + k - 1) / k;
   const size_t need = (size_t(nseg) + size_t(k - 1)) * S;
@@ -634,7 +774,7 @@ mpm_status mpm_rollout(mpm_scene* s, int T, int k, size_t budget) {
     free_rollout(s);  // buffers of another shape
     s->ckpt.assign(nseg, nullptr);
     for (int i = 0; i < nseg; ++i) {
-      mpm_status st = dalloc(s, &s->ckpt[i], S / sizeof(float4), s->roll_allocs);
+      mpm_status st = dalloc(&s->ckpt[i], S / sizeof(float4), s->roll_allocs);
       if (st != MPM_OK) {
         free_rollout(s);
         return st;
@@ -642,7 +782,7 @@ mpm_status mpm_rollout(mpm_scene* s, int T, int k, size_t budget) {
     }
     s->seg.assign(std::max(0, k - 1), nullptr);
     for (int i = 0; i < k - 1; ++i) {
-      mpm_status st = dalloc(s, &s->seg[i], S / sizeof(float4), s->roll_allocs);
+      mpm_status st = dalloc(&s->seg[i], S / sizeof(float4), s->roll_allocs);
       if (st != MPM_OK) {
         free_rollout(s);
         return st;
@@ -651,32 +791,37 @@ mpm_status mpm_rollout(mpm_scene* s, int T, int k, size_t budget) {
   }
   // records: [0] state->state, [1 + 2j] state->ckpt[j], [2 + 2j] ckpt[j]->state, then (k = 1)
   // ckpt[n] -> ckpt[n+1]; every stored state is written by the step that produces it.
-  std::vector<ScenePar> confs;
-  confs.push_back(conf_fwd(s, s->state, s->state));
+  std::vector<ScenePar> recs;
+  recs.push_back(rec_fwd(s, s->state, s->state));
   for (int j = 0; j < nseg; ++j) {
-    confs.push_back(conf_fwd(s, s->state, s->ckpt[j]));
-    confs.push_back(conf_fwd(s, s->ckpt[j], s->state));
+    recs.push_back(rec_fwd(s, s->state, s->ckpt[j]));
+    recs.push_back(rec_fwd(s, s->ckpt[j], s->state));
   }
-  std::vector<int> cidx(T);
+  std::vector<int> map(T);
   for (int n = 0; n < T; ++n) {
     const bool from_ck = (n % k) == 0;
     const bool to_ck = ((n + 1) % k) == 0 && (n + 1) / k < nseg;
     if (from_ck && to_ck) {
-      cidx[n] = int(confs.size());
-      confs.push_back(conf_fwd(s, s->ckpt[n / k], s->ckpt[(n + 1) / k]));
+      map[n] = int(recs.size());
+      recs.push_back(rec_fwd(s, s->ckpt[n / k], s->ckpt[(n + 1) / k]));
     } else if (from_ck) {
-      cidx[n] = 2 + 2 * (n / k);
+      map[n] = 2 + 2 * (n / k);
     } else if (to_ck) {
-      cidx[n] = 1 + 2 * ((n + 1) / k);
+      map[n] = 1 + 2 * ((n + 1) / k);
     } else {
-      cidx[n] = 0;
+      map[n] = 0;
     }
   }
-  ScenePar* table = nullptr;
-  CKS(upload_conf(s, 1, confs, &table));
+  CKS(upload_table(s, 1, recs));
+  if (s->hsel[PH_ROLL].table != s->tables[1].dev) {
+    s->hsel[PH_ROLL].table = s->tables[1].dev;
+    CKS(upload_sel(s));
+  }
+  CKS(upload_map(s, 0, map, s->step));
   cudaStream_t st = s->ctx->stream;
   CK(cudaMemcpyAsync(s->ckpt[0], s->state, S, cudaMemcpyDeviceToDevice, st));
-  for (int n = 0; n < T; ++n) CKS(forward_step(s, table + cidx[n], confs[cidx[n]], s->d_step));
+  CKS(set_counter(s, s->d_step, s->step));
+  CKS(run_phase(s, PH_ROLL, T));
   s->roll_T = T;
   s->roll_k = k;
   s->roll_nseg = nseg;
@@ -692,90 +837,89 @@ mpm_status mpm_backward(mpm_scene* s, const float* gxT, const float* gvT, const 
   if (!s || (mem_space != 0 && mem_space != 1)) return MPM_ERR_ARG;
   if (!s->have_rollout) return MPM_ERR_STATE;
   cudaStream_t st = s->ctx->stream;
-  const int dim = s->dim, N = s->N, T = s->roll_T, k = s->roll_k, nseg = s->roll_nseg;
+  const int dim = s->dim, N = s->N, T = s->roll_T, k = s->roll_k, nseg = s->roll_nseg, n0 = s->roll_start;
   const size_t xb = sizeof(float) * size_t(N) * dim, mb = xb * dim;
-  CKS(ensure_scratch(s, 2 * xb + 2 * mb + 64));
+  CKS(ensure_scratch(s, 2 * xb + 2 * mb + 256));
   const void *a, *bv, *c, *f;
   CKS(stage(s, gxT, xb, mem_space, 0, &a));
   CKS(stage(s, gvT, xb, mem_space, xb, &bv));
   CKS(stage(s, gCT, mb, mem_space, 2 * xb, &c));
   CKS(stage(s, gFT, mb, mem_space, 2 * xb + mb, &f));
-  // seed: F seed defaults to 0 (not identity) for adjoints
-  CK(cudaMemsetAsync(s->adj[0], 0, s->state_bytes, st));
-  {
-    // pack with F = 0 when absent: pack writes identity for a NULL F, so pass zeros explicitly
-    if (!f && N > 0) {
-      CK(cudaMemsetAsync(reinterpret_cast<char*>(s->scratch) + 2 * xb + mb, 0, mb, st));
-      f = reinterpret_cast<char*>(s->scratch) + 2 * xb + mb;
-    }
-    const float* xs = a ? (const float*)a : nullptr;
-    if (!xs && N > 0) {
-      CK(cudaMemsetAsync(s->scratch, 0, xb, st));
-      xs = (const float*)s->scratch;
-    }
-    CK(launch_pack(dim, N, s->npad, xs, (const float*)bv, (const float*)c, (const float*)f, s->adj[0], s->d_status,
-                   st));
+  // adjoint of the final state; a missing F seed is 0 (the packer's default is the identity)
+  char* sc = reinterpret_cast<char*>(s->scratch);
+  if (!f && N > 0) {
+    CK(cudaMemsetAsync(sc + 2 * xb + mb, 0, mb, st));
+    f = sc + 2 * xb + mb;
   }
+  if (!a && N > 0) {
+    CK(cudaMemsetAsync(sc, 0, xb, st));
+    a = sc;
+  }
+  CK(launch_pack(dim, N, s->npad, (const float*)a, (const float*)bv, (const float*)c, (const float*)f, s->adj[0],
+                 s->d_status, st));
   CK(cudaMemsetAsync(s->ctrl.gparams, 0, sizeof(float) * std::max(1, s->nparams), st));
-  // records for every segment: recompute F_{s,j} then reverse B_{s,n,parity}
-  std::vector<ScenePar> confs;
-  std::vector<int> seg_c0(nseg);
+  // table 2: per segment the recompute records F_{sg,j} (state j -> j+1) and the reverse records
+  // B_{sg,n,parity} (state n, adjoint buffers by parity); maps by global step
+  std::vector<ScenePar> recs;
+  std::vector<int> rcm(T, 0), rev(T, 0);
   for (int sg = 0; sg < nseg; ++sg) {
     const int L = std::min(k, T - sg * k);
-    seg_c0[sg] = int(confs.size());
     auto segp = [&](int j) { return j == 0 ? s->ckpt[sg] : s->seg[j - 1]; };
-    for (int j = 0; j + 1 < L; ++j) confs.push_back(conf_fwd(s, segp(j), segp(j + 1)));
+    for (int j = 0; j + 1 < L; ++j) {
+      rcm[sg * k + j] = int(recs.size());
+      recs.push_back(rec_fwd(s, segp(j), segp(j + 1)));
+    }
     for (int n = 0; n < L; ++n) {
-      confs.push_back(conf_bwd(s, segp(n), s->adj[0], s->adj[1]));
-      confs.push_back(conf_bwd(s, segp(n), s->adj[1], s->adj[0]));
+      const int gstep = sg * k + n;
+      const int parity = (T - 1 - gstep) & 1;  // reverse step T-1 reads adj[0]
+      rev[gstep] = int(recs.size()) + parity;
+      recs.push_back(rec_rev(s, segp(n), s->adj[0], s->adj[1]));
+      recs.push_back(rec_rev(s, segp(n), s->adj[1], s->adj[0]));
     }
   }
-  ScenePar* table = nullptr;
-  CKS(upload_conf(s, 2, confs, &table));
-  CKS(set_counter(s, s->d_bstep, s->roll_start + T - 1));
-  int cur = 0;
+  CKS(upload_table(s, 2, recs));
+  bool sel_dirty = false;
+  for (int ph : {PH_RCM, PH_REV, PH_PREP})
+    if (s->hsel[ph].table != s->tables[2].dev) {
+      s->hsel[ph].table = s->tables[2].dev;
+      sel_dirty = true;
+    }
+  if (sel_dirty) CKS(upload_sel(s));
+  CKS(upload_map(s, 1, rcm, n0));
+  CKS(upload_map(s, 2, rev, n0));
+  CKS(set_counter(s, s->d_bstep, n0 + T - 1));
   for (int sg = nseg - 1; sg >= 0; --sg) {
     const int L = std::min(k, T - sg * k);
-    const int c0 = seg_c0[sg];
     if (L > 1) {
-      // bin keys of the checkpoint the recompute starts from
-      if (s->impl != MPM_IMPL_PLAIN) {
-        BatchDev bb = s->b;
-        bb.scenes = table + c0;
-        CK(s->dim == 2 ? launch_keys<2>(bb, st) : launch_keys<3>(bb, st));
-      }
-      CKS(set_counter(s, s->d_step, s->roll_start + sg * k));
-      for (int j = 0; j + 1 < L; ++j) CKS(forward_step(s, table + c0 + j, confs[c0 + j], s->d_step));
+      CKS(set_counter(s, s->d_step, n0 + sg * k));
+      CKS(run_phase(s, PH_PREP, 1));  // bin keys of the checkpoint the recompute starts from
+      CKS(run_phase(s, PH_RCM, L - 1));
     }
-    for (int n = L - 1; n >= 0; --n) {
-      const int ci = c0 + (L - 1) + 2 * n + cur;
-      CKS(reverse_step(s, table + ci, confs[ci]));
-      cur ^= 1;
-    }
+    CKS(run_phase(s, PH_REV, L));
   }
   // outputs
-  const float4* res = s->adj[cur];
+  const float4* res = s->adj[T & 1];
   if (mem_space == 1) {
     CK(launch_unpack(dim, N, s->npad, res, gx0, gv0, gC0, gF0, st));
     if (gctrl && s->nparams > 0)
       CK(cudaMemcpyAsync(gctrl, s->ctrl.gparams, sizeof(float) * s->nparams, cudaMemcpyDeviceToDevice, st));
   } else {
-    CKS(ensure_scratch(s, 2 * xb + 2 * mb + 64));
-    char* sc = reinterpret_cast<char*>(s->scratch);
     float* dx_ = (float*)sc;
     float* dv_ = (float*)(sc + xb);
     float* dC_ = (float*)(sc + 2 * xb);
     float* dF_ = (float*)(sc + 2 * xb + mb);
     CK(launch_unpack(dim, N, s->npad, res, dx_, dv_, dC_, dF_, st));
-    if (gx0) CK(cudaMemcpyAsync(gx0, dx_, xb, cudaMemcpyDeviceToHost, st));
-    if (gv0) CK(cudaMemcpyAsync(gv0, dv_, xb, cudaMemcpyDeviceToHost, st));
-    if (gC0) CK(cudaMemcpyAsync(gC0, dC_, mb, cudaMemcpyDeviceToHost, st));
-    if (gF0) CK(cudaMemcpyAsync(gF0, dF_, mb, cudaMemcpyDeviceToHost, st));
+    if (gx0 && xb) CK(cudaMemcpyAsync(gx0, dx_, xb, cudaMemcpyDeviceToHost, st));
+    if (gv0 && xb) CK(cudaMemcpyAsync(gv0, dv_, xb, cudaMemcpyDeviceToHost, st));
+    if (gC0 && mb) CK(cudaMemcpyAsync(gC0, dC_, mb, cudaMemcpyDeviceToHost, st));
+    if (gF0 && mb) CK(cudaMemcpyAsync(gF0, dF_, mb, cudaMemcpyDeviceToHost, st));
     if (gctrl && s->nparams > 0)
       CK(cudaMemcpyAsync(gctrl, s->ctrl.gparams, sizeof(float) * s->nparams, cudaMemcpyDeviceToHost, st));
   }
-  // the keys now describe state 0 of the rollout; restore those of the current state
-  CKS(refresh_keys(s));
+  // the bin keys now describe state 0 of the rollout: restore those of the current state and the
+  // forward counter
+  CKS(set_counter(s, s->d_step, s->step));
+  CKS(enqueue_keys(s, PH_STEP, st));
   return read_status(s);
 }
 
@@ -794,14 +938,14 @@ mpm_status mpm_get_state(mpm_scene* s, int step, float* x, float* v, float* C, f
   if (mem_space == 1) {
     CK(launch_unpack(dim, N, s->npad, src, x, v, C, F, st));
   } else {
-    CKS(ensure_scratch(s, 2 * xb + 2 * mb + 64));
+    CKS(ensure_scratch(s, 2 * xb + 2 * mb + 256));
     char* sc = reinterpret_cast<char*>(s->scratch);
     CK(launch_unpack(dim, N, s->npad, src, (float*)sc, (float*)(sc + xb), (float*)(sc + 2 * xb),
                      (float*)(sc + 2 * xb + mb), st));
-    if (x) CK(cudaMemcpyAsync(x, sc, xb, cudaMemcpyDeviceToHost, st));
-    if (v) CK(cudaMemcpyAsync(v, sc + xb, xb, cudaMemcpyDeviceToHost, st));
-    if (C) CK(cudaMemcpyAsync(C, sc + 2 * xb, mb, cudaMemcpyDeviceToHost, st));
-    if (F) CK(cudaMemcpyAsync(F, sc + 2 * xb + mb, mb, cudaMemcpyDeviceToHost, st));
+    if (x && xb) CK(cudaMemcpyAsync(x, sc, xb, cudaMemcpyDeviceToHost, st));
+    if (v && xb) CK(cudaMemcpyAsync(v, sc + xb, xb, cudaMemcpyDeviceToHost, st));
+    if (C && mb) CK(cudaMemcpyAsync(C, sc + 2 * xb, mb, cudaMemcpyDeviceToHost, st));
+    if (F && mb) CK(cudaMemcpyAsync(F, sc + 2 * xb + mb, mb, cudaMemcpyDeviceToHost, st));
   }
   return read_status(s);
 }
@@ -813,7 +957,7 @@ mpm_status mpm_set_state(mpm_scene* s, const float* x, const float* v, const flo
   cudaStream_t st = s->ctx->stream;
   const int dim = s->dim, N = s->N;
   const size_t xb = sizeof(float) * size_t(N) * dim, mb = xb * dim;
-  CKS(ensure_scratch(s, 2 * xb + 2 * mb + 64));
+  CKS(ensure_scratch(s, 2 * xb + 2 * mb + 256));
   const void *a, *b, *c, *f;
   CKS(stage(s, x, xb, mem_space, 0, &a));
   CKS(stage(s, v, xb, mem_space, xb, &b));
@@ -822,11 +966,9 @@ mpm_status mpm_set_state(mpm_scene* s, const float* x, const float* v, const flo
   CK(cudaMemsetAsync(s->d_status, 0, sizeof(int), st));
   CK(launch_pack(dim, N, s->npad, (const float*)a, (const float*)b, (const float*)c, (const float*)f, s->state,
                  s->d_status, st));
-  if (step >= 0) {
-    CKS(set_counter(s, s->d_step, step));
-    s->step = step;
-  }
-  CKS(refresh_keys(s));
+  if (step >= 0) s->step = step;
+  CKS(set_counter(s, s->d_step, s->step));
+  CKS(enqueue_keys(s, PH_STEP, st));
   CK(cudaGetLastError());
   return MPM_OK;
 }

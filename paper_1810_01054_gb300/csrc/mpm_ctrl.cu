@@ -16,7 +16,7 @@ constexpr int RED_STRIDE = MAX_GROUPS * 3 + 3;    // floats per row: [64 groups]
 
 int reduction_rows(int N) { return (N + RED_ROW - 1) / RED_ROW; }
 
-// mode 0: values = x (dim channels) and body sum; mode 1: values = sig_contrib (1 channel)
+// Group sums of x (dim channels) and the body sum, for the MLP controller's centroids.
 template <int CH>
 __global__ void __launch_bounds__(256) k_group_rows(const ScenePar* __restrict__ dsp, float* __restrict__ rows,
                                                     int mode) {
@@ -109,83 +109,102 @@ __device__ void reduce_rows(const float* __restrict__ rows, int n_rows, int G, i
 }
 
 // ----------------------------------------------------------------------------- forward
-// Writes sp.act[g] for step n = *sp_step (then advances the scene's step counter).
+// MLP controller of step n = *step_ctr (the sinusoid forms are evaluated by the record
+// selection): group centroids from the partial rows, then the three tanh layers -> sp.act.
 __global__ void __launch_bounds__(1024) k_ctrl_forward(const ScenePar* __restrict__ dsp, CtrlPar c, const float* rows,
-                                                       int n_rows, int* step_ctr, int advance) {
+                                                       int n_rows) {
   const ScenePar& sp = *dsp;
   __shared__ float red[MAX_GROUPS * 3 + 3];
   __shared__ float z[MAX_GROUPS * 3], h1[MAX_HIDDEN], h2[MAX_HIDDEN];
-  const int n = *step_ctr;
-  const float t = float(n) * sp.dt;
   const int G = c.G, tid = threadIdx.x;
-  if (c.type == 0) {
-    if (tid < G) sp.act[tid] = c.params[tid] * sinf(kTwoPi * c.freq * t);
-  } else if (c.type == 1) {
-    if (tid < G) {
-      const float w = kTwoPi * c.freq * t;
-      const float bs[4] = {sinf(w), cosf(w), sinf(2.0f * w), cosf(2.0f * w)};
-      float a = 0.0f;
-      for (int j = 0; j < 4; ++j) a += c.params[tid * 4 + j] * bs[j];
-      sp.act[tid] = a;
-    }
-  } else {
-    const int dim = c.dim, Z = G * dim, H = c.hidden;
-    reduce_rows(rows, n_rows, G, dim, red);
-    if (tid < Z) {
-      const int g = tid / dim, a = tid - g * dim;
-      const float cg = red[g * 3 + a] * c.inv_count[g];
-      const float cb = red[MAX_GROUPS * 3 + a] * c.inv_n;
-      z[tid] = cg - cb;
-      c.centroid[tid] = cg;
-      if (tid < dim) c.centroid[Z + tid] = cb;
-    }
-    __syncthreads();
-    const float* W1 = c.params;
-    const float* b1 = W1 + H * Z;
-    const float* W2 = b1 + H;
-    const float* b2 = W2 + H * H;
-    const float* W3 = b2 + H;
-    const float* b3 = W3 + G * H;
-    if (tid < H) {
-      float u = b1[tid];
-      for (int j = 0; j < Z; ++j) u += W1[tid * Z + j] * z[j];
-      h1[tid] = tanhf(u);
-    }
-    __syncthreads();
-    if (tid < H) {
-      float u = b2[tid];
-      for (int j = 0; j < H; ++j) u += W2[tid * H + j] * h1[j];
-      h2[tid] = tanhf(u);
-    }
-    __syncthreads();
-    if (tid < G) {
-      float u = b3[tid];
-      for (int j = 0; j < H; ++j) u += W3[tid * H + j] * h2[j];
-      sp.act[tid] = c.scale * tanhf(u);
-    }
+  const int dim = c.dim, Z = G * dim, H = c.hidden;
+  reduce_rows(rows, n_rows, G, dim, red);
+  if (tid < Z) {
+    const int g = tid / dim, a = tid - g * dim;
+    const float cg = red[g * 3 + a] * c.inv_count[g];
+    const float cb = red[MAX_GROUPS * 3 + a] * c.inv_n;
+    z[tid] = cg - cb;
+    c.centroid[tid] = cg;
+    if (tid < dim) c.centroid[Z + tid] = cb;
   }
   __syncthreads();
-  if (tid == 0 && advance) *step_ctr = n + 1;
+  const float* W1 = c.params;
+  const float* b1 = W1 + H * Z;
+  const float* W2 = b1 + H;
+  const float* b2 = W2 + H * H;
+  const float* W3 = b2 + H;
+  const float* b3 = W3 + G * H;
+  if (tid < H) {
+    float u = b1[tid];
+    for (int j = 0; j < Z; ++j) u += W1[tid * Z + j] * z[j];
+    h1[tid] = tanhf(u);
+  }
+  __syncthreads();
+  if (tid < H) {
+    float u = b2[tid];
+    for (int j = 0; j < H; ++j) u += W2[tid * H + j] * h1[j];
+    h2[tid] = tanhf(u);
+  }
+  __syncthreads();
+  if (tid < G) {
+    float u = b3[tid];
+    for (int j = 0; j < H; ++j) u += W3[tid * H + j] * h2[j];
+    sp.act[tid] = c.scale * tanhf(u);
+  }
 }
 
 // ----------------------------------------------------------------------------- backward
 // dL/da_g = sum over the group of the (K) contributions; accumulate dL/dparams for step n;
 // for the MLP also dL/dz, turned into per-group coefficients for the x adjoint.
-__global__ void __launch_bounds__(1024) k_ctrl_backward(const ScenePar* __restrict__ dsp, CtrlPar c,
-                                                        const float* rows, int n_rows, int* step_ctr) {
+__global__ void __launch_bounds__(1024) k_ctrl_backward(const ScenePar* __restrict__ dsp, CtrlPar c) {
   const ScenePar& sp = *dsp;
   __shared__ float red[MAX_GROUPS * 3 + 3];
   __shared__ float ga[MAX_GROUPS], z[MAX_GROUPS * 3], h1[MAX_HIDDEN], h2[MAX_HIDDEN], o3[MAX_GROUPS];
   __shared__ float gu3[MAX_GROUPS], gu2[MAX_HIDDEN], gu1[MAX_HIDDEN];
+  int* step_ctr = sp.step_ctr;
   const int n = *step_ctr;
   const float t = float(n) * sp.dt;
   const int G = c.G, tid = threadIdx.x;
-  reduce_rows(rows, n_rows, G, 1, red);
-  if (tid < G) {
-    ga[tid] = red[tid * 3];
-    sp.act_grad[tid] = ga[tid];
+  // dL/da_g = sum of the per-tile (per-block) partials of this scene, rows in order, 16 fixed
+  // interleaved splits per group combined in split order
+  {
+    __shared__ float part[16][MAX_GROUPS];
+    __shared__ int range[2];
+    if (tid == 0) {
+      int lo = 0, hi = c.plain_rows;
+      if (c.active) {
+        const int na = *c.n_active, t0 = sp.tile_base, t1 = sp.tile_base + sp.n_tiles;
+        int a = 0, b = na;  // first slot with active[slot] >= t0
+        while (a < b) {
+          const int m = (a + b) >> 1;
+          if (c.active[m] < t0) a = m + 1; else b = m;
+        }
+        lo = a;
+        b = na;  // first slot with active[slot] >= t1
+        while (a < b) {
+          const int m = (a + b) >> 1;
+          if (c.active[m] < t1) a = m + 1; else b = m;
+        }
+        hi = a;
+      }
+      range[0] = lo;
+      range[1] = hi;
+    }
+    __syncthreads();
+    const int g = tid & (MAX_GROUPS - 1), split = tid >> 6;
+    float acc = 0.0f;
+    if (g < G)
+      for (int r = range[0] + split; r < range[1]; r += 16) acc += c.gpart[size_t(r) * MAX_GROUPS + g];
+    part[split][g] = acc;
+    __syncthreads();
+    if (tid < G) {
+      float t = 0.0f;
+      for (int k = 0; k < 16; ++k) t += part[k][tid];
+      ga[tid] = t;
+      sp.act_grad[tid] = t;
+    }
+    __syncthreads();
   }
-  __syncthreads();
   if (c.type == 0) {
     if (tid < G) c.gparams[tid] += ga[tid] * sinf(kTwoPi * c.freq * t);
   } else if (c.type == 1) {
@@ -287,43 +306,32 @@ __global__ void k_ctrl_scatter_x(const ScenePar* __restrict__ dsp, CtrlPar c) {
   sp.adj_out[p] = q;
 }
 
-// Controller forward for one step: (MLP: centroid rows first), then act; advances *step_ctr.
-cudaError_t ctrl_step_forward(const ScenePar& sp, const ScenePar* dsp, const CtrlPar& c, int* step_ctr, int advance,
-                              cudaStream_t s) {
-  if (c.G == 0) {
-    if (advance) {
-      k_ctrl_forward<<<1, 32, 0, s>>>(dsp, c, nullptr, 0, step_ctr, advance);
-      count_launches(1);
-    }
-    return cudaGetLastError();
-  }
-  int rows = 0;
-  if (c.type == 2) {
-    rows = reduction_rows(sp.N);
+// Controller forward for one step: the MLP form only (group centroid rows, then the network).
+cudaError_t ctrl_step_forward(const ScenePar& sp, const ScenePar* dsp, const CtrlPar& c, cudaStream_t s) {
+  if (c.type != 2 || c.G == 0) return cudaSuccess;
+  const int rows = reduction_rows(sp.N);
+  if (rows > 0) {
     if (sp.dim == 2)
       k_group_rows<2><<<rows, 256, 0, s>>>(dsp, c.partials, 0);
     else
       k_group_rows<3><<<rows, 256, 0, s>>>(dsp, c.partials, 0);
   }
-  k_ctrl_forward<<<1, 1024, 0, s>>>(dsp, c, c.partials, rows, step_ctr, advance);
-  count_launches(c.type == 2 ? 2 : 1);
+  k_ctrl_forward<<<1, 1024, 0, s>>>(dsp, c, c.partials, rows);
+  count_launches(rows > 0 ? 2 : 1);
   return cudaGetLastError();
 }
 
 // Controller backward for one reverse step: group sums of (K), parameter adjoint, and (MLP) the
-// centroid adjoint added to dL/dx of state n.  Decrements *step_ctr.
-cudaError_t ctrl_step_backward(const ScenePar& sp, const ScenePar* dsp, const CtrlPar& c, int* step_ctr,
-                               cudaStream_t s) {
-  int rows = reduction_rows(sp.N);
-  if (c.G > 0 && rows > 0) k_group_rows<1><<<rows, 256, 0, s>>>(dsp, c.partials, 1);
-  k_ctrl_backward<<<1, 1024, 0, s>>>(dsp, c, c.partials, c.G > 0 ? rows : 0, step_ctr);
-  count_launches(1 + ((c.G > 0 && rows > 0) ? 1 : 0) + ((c.type == 2 && c.G > 0 && sp.N > 0) ? 1 : 0));
+// centroid adjoint added to dL/dx of state n.  Rewinds the scene's step counter.
+cudaError_t ctrl_step_backward(const ScenePar& sp, const ScenePar* dsp, const CtrlPar& c, cudaStream_t s) {
+  k_ctrl_backward<<<1, 1024, 0, s>>>(dsp, c);
   if (c.type == 2 && c.G > 0 && sp.N > 0) {
     if (sp.dim == 2)
       k_ctrl_scatter_x<2><<<(sp.N + 255) / 256, 256, 0, s>>>(dsp, c);
     else
       k_ctrl_scatter_x<3><<<(sp.N + 255) / 256, 256, 0, s>>>(dsp, c);
   }
+  count_launches(1 + ((c.type == 2 && c.G > 0 && sp.N > 0) ? 1 : 0));
   return cudaGetLastError();
 }
 

@@ -18,10 +18,11 @@ template <int D>
 struct Cfg;
 template <>
 struct Cfg<2> {
-  static constexpr int B = 8;             // tile edge in cells
-  static constexpr int CELLS = 64;        // cells per tile
-  static constexpr int BN = 10;           // node-block edge (B + 2)
-  static constexpr int BLOCK_NODES = 100; // nodes per block
+  static constexpr int B = 4;             // tile edge in cells
+  static constexpr int CELLS = 16;        // cells per tile
+  static constexpr int BN = 6;            // node-block edge (B + 2)
+  static constexpr int BLOCK_NODES = 36;  // nodes per block
+  static constexpr int SORT_CAP = 2048;   // most particles one tile may hold
   static constexpr int S = 12;            // floats per particle state: x(2) F(4) v(2) C(4)
   static constexpr int PLANES = 3;        // float4 planes per particle
   static constexpr int XF_PLANES = 2;     // planes holding x and F (what G2P reads)
@@ -33,6 +34,7 @@ struct Cfg<3> {
   static constexpr int CELLS = 64;
   static constexpr int BN = 6;
   static constexpr int BLOCK_NODES = 216;
+  static constexpr int SORT_CAP = 4096;
   static constexpr int S = 24;            // x(3) F(9) v(3) C(9)
   static constexpr int PLANES = 6;
   static constexpr int XF_PLANES = 3;

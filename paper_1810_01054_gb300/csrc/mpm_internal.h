@@ -9,12 +9,14 @@
 
 namespace gbmpm {
 
-// Kernels launched by this library (process-wide tally, read by mpm_launch_count).
+// Kernels launched by this library (process-wide tally, read by mpm_launch_count).  While a
+// thread captures a CUDA graph its launches go to the capture's tally instead; the graph's kernels
+// are counted each time it is launched.
 void count_launches(int n);
 long long launch_total();
+void capture_tally(long long* tally);  // non-null: this thread is capturing
 
 constexpr uint32_t KEY_INVALID = 0xffffffffu;
-constexpr int SORT_CAP = 4096;  // most particles one tile may hold (tile kernels stage its list)
 constexpr int MAX_GROUPS = 64;  // actuation groups per scene
 constexpr int MAX_HIDDEN = 128; // controller MLP width
 
@@ -48,6 +50,20 @@ struct ScenePar {
   float* act_grad;        // [G] dL/da of the current reverse step
   float* sig_contrib;     // [N] per-particle part of dL/da (S4 (K))
   int* status;            // first-error status word
+  int* step_ctr;          // step counter the step advances (G2P) or rewinds (controller adjoint)
+};
+
+// Where a scene's record for the current step comes from (see k_select).
+struct SelectPar {
+  const ScenePar* table;  // the scene's record table for the running phase
+  const int* map;         // record index of step n at map[n - base]; NULL = record 0
+  int base;
+  const int* ctr;         // step counter n
+  int tile_base, pbase;   // batch offsets of the scene
+  int ctrl_type, G;       // sinusoid controllers are evaluated by the selection
+  float freq, dt;
+  const float* params;
+  float* act;
 };
 
 // One batch of scenes of equal dimension that advance together.
@@ -68,11 +84,14 @@ struct BatchDev {
   uint32_t* sorted;     // [total_particles] scene-local particle ids, tile-major, canonical
   float4* partial;      // [total_tiles * BLOCK_NODES] node blocks of P2G
   float4* partial_b;    // [total_tiles * BLOCK_NODES] node blocks of the adjoint scatter
+  float* gpartial;      // [total_tiles * MAX_GROUPS] per active tile group sums of dL/da
   int max_ctas;         // persistent-grid size for the tile kernels
   int p2g_block;        // threads per CTA of the tile kernels (autotuned)
 };
 
 // ---------------------------------------------------------------------------- launchers
+// Sets the kernels' launch attributes (large dynamic shared memory); once per process/device.
+cudaError_t configure_kernels();
 // Tiled (sorted, deterministic) form.
 template <int D>
 cudaError_t launch_keys(const BatchDev& b, cudaStream_t s);
@@ -80,10 +99,11 @@ template <int D>
 cudaError_t launch_sort(const BatchDev& b, cudaStream_t s);
 template <int D>
 cudaError_t launch_p2g(const BatchDev& b, bool with_adjoint, cudaStream_t s);
-template <int D>
-cudaError_t launch_grid(const BatchDev& b, bool with_adjoint, cudaStream_t s);
+// G2P (Eqs. 7-10) including the grid update of its node block (Eq. 6, gravity, boundary).
 template <int D>
 cudaError_t launch_g2p(const BatchDev& b, cudaStream_t s);
+// Adjoint gather (S4 (F)-(K), (J)) including the grid adjoint of its node block (S3, S5) and
+// the per-tile group sums of dL/da into gpartial.
 template <int D>
 cudaError_t launch_adj_gather(const BatchDev& b, cudaStream_t s);
 
@@ -91,7 +111,7 @@ cudaError_t launch_adj_gather(const BatchDev& b, cudaStream_t s);
 template <int D>
 cudaError_t launch_plain_step(const ScenePar* dev_scene, const ScenePar& host_scene, cudaStream_t s);
 template <int D>
-cudaError_t launch_plain_adjoint(const ScenePar* dev_scene, const ScenePar& host_scene, cudaStream_t s);
+cudaError_t launch_plain_adjoint(const ScenePar* dev_scene, const ScenePar& host_scene, float* gpart, cudaStream_t s);
 
 // Controllers.  ctrl_* describe one scene's controller.
 struct CtrlPar {
@@ -106,17 +126,23 @@ struct CtrlPar {
   float* gz;              // device [G*dim] scratch: dL/dz of the MLP input
   float* partials;        // device scratch for the deterministic group reductions
   int n_partials;         // number of reduction partial rows available
+  // rows of per-tile (tiled form) or per-block (plain form) group sums of dL/da, MAX_GROUPS each:
+  // the tiled rows of the scene are the active slots whose tile lies in the scene's tile range
+  const float* gpart;
+  const int* active;      // tiled form: batch active tile list (NULL: plain form)
+  const int* n_active;
+  int plain_rows;
 };
 
 int reduction_rows(int N);                  // partial rows of the group reductions
 constexpr int RED_ROW_FLOATS = MAX_GROUPS * 3 + 3;  // floats per partial row
-// Controller forward for the step *step_ctr (advancing it when `advance`), and the reverse of
-// the step *step_ctr (decrementing it afterwards).
-cudaError_t ctrl_step_forward(const ScenePar& sp, const ScenePar* dsp, const CtrlPar& c, int* step_ctr, int advance,
-                              cudaStream_t s);
-cudaError_t ctrl_step_backward(const ScenePar& sp, const ScenePar* dsp, const CtrlPar& c, int* step_ctr,
-                               cudaStream_t s);
+// Controller forward (MLP form; the sinusoid forms are evaluated by k_select) and the reverse of
+// the step *sp.step_ctr, which it then decrements.
+cudaError_t ctrl_step_forward(const ScenePar& sp, const ScenePar* dsp, const CtrlPar& c, cudaStream_t s);
+cudaError_t ctrl_step_backward(const ScenePar& sp, const ScenePar* dsp, const CtrlPar& c, cudaStream_t s);
 
+// Copies every scene's record for the current step into cur[] (one block per scene).
+cudaError_t launch_select(const SelectPar* sel, int n_scenes, ScenePar* cur, cudaStream_t s);
 // *p = v on the stream (kernel argument, so no host buffer outlives the call).
 cudaError_t launch_set_int(int* p, int v, cudaStream_t s);
 

@@ -23,7 +23,14 @@
 namespace gbmpm {
 
 static std::atomic<long long> g_launches{0};
-void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+static thread_local long long* t_capture = nullptr;
+void capture_tally(long long* tally) { t_capture = tally; }
+void count_launches(int n) {
+  if (t_capture)
+    *t_capture += n;
+  else
+    g_launches.fetch_add(n, std::memory_order_relaxed);
+}
 long long launch_total() { return g_launches.load(std::memory_order_relaxed); }
 
 // ============================================================================ helpers
@@ -37,6 +44,19 @@ __device__ __forceinline__ int find_scene(const int* __restrict__ pbase, int n_s
       hi = mid - 1;
   }
   return lo;
+}
+
+// ctr[t] += 1 for every active lane's t (t < 0: nothing); returns the old value plus the lane's rank
+// among the lanes with the same t -- one atomic per distinct t in the warp.
+__device__ __forceinline__ uint32_t warp_aggregated_inc(uint32_t* ctr, int t) {
+  const unsigned mask = __activemask();
+  const unsigned peers = __match_any_sync(mask, t);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  uint32_t base = 0;
+  if (lane == leader && t >= 0) base = atomicAdd(ctr + t, uint32_t(__popc(peers)));
+  base = __shfl_sync(peers, base, leader);
+  return base + uint32_t(__popc(peers & ((1u << lane) - 1u)));
 }
 
 template <int D>
@@ -105,6 +125,7 @@ __device__ __forceinline__ float particle_G(const Part<D>& q, const ScenePar& sp
 }
 
 // ============================================================================ keys / sort
+// Bin keys of the state being read, and the tile histogram (tile_count must be zero on entry).
 template <int D>
 __global__ void k_keys(BatchDev b) {
   int gp = blockIdx.x * blockDim.x + threadIdx.x;
@@ -113,16 +134,9 @@ __global__ void k_keys(BatchDev b) {
   int p = gp - sp.pbase;
   float4 q = sp.planes[p];
   float x[3] = {q.x, q.y, q.z};
-  sp.key[p] = bin_key<D>(x, sp);
-}
-
-template <int D>
-__global__ void k_hist(BatchDev b) {
-  int gp = blockIdx.x * blockDim.x + threadIdx.x;
-  if (gp >= b.total_particles) return;
-  const ScenePar& sp = b.scenes[find_scene(b.scene_pbase, b.n_scenes, gp)];
-  uint32_t k = sp.key[gp - sp.pbase];
-  if (k != KEY_INVALID) atomicAdd(b.tile_count + sp.tile_base + (k >> 6), 1u);
+  const uint32_t k = bin_key<D>(x, sp);
+  sp.key[p] = k;
+  warp_aggregated_inc(b.tile_count, k != KEY_INVALID ? int(sp.tile_base + (k >> 6)) : -1);
 }
 
 template <int D>
@@ -131,11 +145,11 @@ __global__ void k_scatter(BatchDev b) {
   if (gp >= b.total_particles) return;
   const ScenePar& sp = b.scenes[find_scene(b.scene_pbase, b.n_scenes, gp)];
   int p = gp - sp.pbase;
-  uint32_t k = sp.key[p];
-  if (k == KEY_INVALID) return;
-  uint32_t t = sp.tile_base + (k >> 6);
-  uint32_t pos = b.tile_start[t] + atomicAdd(b.tile_fill + t, 1u);
-  b.sorted[pos] = uint32_t(p);
+  const uint32_t k = sp.key[p];
+  const int t = k != KEY_INVALID ? int(sp.tile_base + (k >> 6)) : -1;
+  const uint32_t rank = warp_aggregated_inc(b.tile_fill, t);
+  if (t < 0) return;
+  b.sorted[b.tile_start[t] + rank] = ((k & 63u) << 26) | uint32_t(p);  // cell in tile, particle id
 }
 
 // Exclusive block scan of (sum, count) pairs over blockDim.x <= 1024 threads.
@@ -179,7 +193,7 @@ __device__ __forceinline__ void block_scan2(uint32_t& a, uint32_t& c, uint32_t& 
 }
 
 constexpr int SCAN_THREADS = 1024;
-constexpr int SCAN_PER_THREAD = 8;
+constexpr int SCAN_PER_THREAD = 2;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_PER_THREAD;
 
 // Phase 1 of the tile scan: per-block totals of particle counts and of active tiles.
@@ -264,6 +278,13 @@ __global__ void k_scan_down(BatchDev b, int single) {
 }
 
 // ============================================================================ P2G (tiled)
+// Phase A  canonical order of the tile's particles: by cell, then by particle id (counting sort
+//          over the tile's cells, insertion sort inside each cell) -- fixes every later sum order.
+// Phase B  one record per particle (fraction f, momentum part a, MLS matrix M = dx G, mass; plus
+//          the adjoint-scatter record (C) in the reverse pass), all staged in shared memory.
+// Phase C  work item = (cell, part): 2D one stencil node, 3D one x-slab of 9 nodes; a thread
+//          accumulates its item over the cell's particles in registers (fixed particle order).
+// Phase D  node block = fixed-order sum of the cell stencils covering each node -> global.
 template <int D, bool ADJ>
 struct P2GCfg {
   static constexpr int RF = 2 * D + D * D + 1;             // f, a, M, mass
@@ -272,20 +293,24 @@ struct P2GCfg {
   static constexpr int CHF = D + 1;                        // momentum + mass
   static constexpr int CHA = ADJ ? D : 0;                  // vbar*
   static constexpr int CH = CHF + CHA;
-  static constexpr int NK = D == 2 ? 3 : 9;                // stencil nodes per (cell, kx) thread
+  static constexpr int PARTS = D == 2 ? 9 : 3;             // work items per cell
+  static constexpr int NK = D == 2 ? 1 : 9;                // stencil nodes per work item
   static constexpr int THREADS = 256;
-  static constexpr int CHUNK = 256;
-  static constexpr size_t REC_BYTES = size_t(CHUNK) * RW * 4;
+  static constexpr int ITEMS = Cfg<D>::CELLS * PARTS;      // 2D 144, 3D 192
+  static constexpr int REC_CAP = D == 2 ? 1024 : 512;      // records staged at once
+  static constexpr int CAP = Cfg<D>::SORT_CAP;
+  static constexpr size_t REC_BYTES = size_t(REC_CAP) * RW * 4;
   static constexpr size_t ACC_BYTES = size_t(Cfg<D>::CELLS) * Cfg<D>::STENCIL * CH * 4;
-  static constexpr size_t IDS_BYTES = size_t(SORT_CAP) * 4;
-  static constexpr size_t U_BYTES = (REC_BYTES > ACC_BYTES ? REC_BYTES : ACC_BYTES) > IDS_BYTES
-                                        ? (REC_BYTES > ACC_BYTES ? REC_BYTES : ACC_BYTES)
-                                        : IDS_BYTES;
+  static constexpr size_t IDS_BYTES = size_t(CAP) * 4;
+  static constexpr size_t U1 = REC_BYTES > ACC_BYTES ? REC_BYTES : ACC_BYTES;
+  static constexpr size_t U_BYTES = U1 > IDS_BYTES ? U1 : IDS_BYTES;
   static constexpr size_t SMEM = IDS_BYTES + U_BYTES;
+  static_assert(ITEMS <= THREADS, "one work item per thread");
+  static_assert(Cfg<D>::BLOCK_NODES <= THREADS, "one node per thread in phase D");
 };
 
 template <int D, bool ADJ>
-__global__ void __launch_bounds__(256) k_p2g(BatchDev b) {
+__global__ void __launch_bounds__(256, ADJ ? 2 : 3) k_p2g(BatchDev b) {
   using K = P2GCfg<D, ADJ>;
   constexpr int B = Cfg<D>::B, CELLS = Cfg<D>::CELLS, NB = Cfg<D>::BLOCK_NODES, BN = Cfg<D>::BN;
   constexpr int ST = Cfg<D>::STENCIL;
@@ -301,60 +326,16 @@ __global__ void __launch_bounds__(256) k_p2g(BatchDev b) {
     const ScenePar& sp = b.scenes[b.tile_scene[gt]];
     const uint32_t st = b.tile_start[gt];
     const int cnt = int(b.tile_start[gt + 1] - st);
-    if (cnt > SORT_CAP) {
+    if (cnt > K::CAP) {
       if (tid == 0) set_status(sp.status, ST_DENSITY);
       continue;  // uniform across the CTA
     }
-    // ---- phase A: canonical order (cell, then particle id) ------------------------------
-    uint32_t* raw = reinterpret_cast<uint32_t*>(U);
-    if (tid < CELLS) {
-      cfill[tid] = 0;
-    }
-    __syncthreads();
-    for (int i = tid; i < cnt; i += blockDim.x) {
-      uint32_t id = b.sorted[st + i];
-      uint32_t c = sp.key[id] & 63u;
-      raw[i] = (c << 26) | id;
-      atomicAdd(&cfill[c], 1);
-    }
-    __syncthreads();
-    if (tid == 0) {
-      int acc = 0;
-      for (int c = 0; c < CELLS; ++c) {
-        cstart[c] = acc;
-        acc += cfill[c];
-      }
-      cstart[CELLS] = acc;
-    }
-    __syncthreads();
-    if (tid < CELLS) cfill[tid] = 0;
-    __syncthreads();
-    for (int i = tid; i < cnt; i += blockDim.x) {
-      uint32_t r = raw[i];
-      uint32_t c = r >> 26;
-      int pos = cstart[c] + atomicAdd(&cfill[c], 1);
-      ids[pos] = r & 0x3ffffffu;
-    }
-    __syncthreads();
-    if (tid < CELLS) {  // insertion sort of each cell's ids (a few entries per cell)
-      int s0 = cstart[tid], s1 = cstart[tid + 1];
-      for (int i = s0 + 1; i < s1; ++i) {
-        uint32_t v = ids[i];
-        int j = i - 1;
-        while (j >= s0 && ids[j] > v) {
-          ids[j + 1] = ids[j];
-          --j;
-        }
-        ids[j + 1] = v;
-      }
-    }
-    __syncthreads();
-    for (int i = tid; i < cnt; i += blockDim.x) b.sorted[st + i] = ids[i];
-
-    // ---- phases B, C: per-particle records, per-(cell, kx) register accumulation --------
-    const int my_cell = tid / 3, my_kx = tid - 3 * (tid / 3);
-    const bool acc_thread = tid < 3 * CELLS;
-    const int cs = acc_thread ? cstart[my_cell] : 0, ce = acc_thread ? cstart[my_cell + 1] : 0;
+    int t[D];
+    unlin<D>(gt - sp.tile_base, sp.nt, t);
+    const bool item_thread = tid < K::ITEMS;
+    const int my_cell = tid / K::PARTS, my_part = tid - K::PARTS * (tid / K::PARTS);
+    const int ikx = D == 2 ? my_part / 3 : my_part;  // stencil x offset of the item
+    const int iky = D == 2 ? my_part % 3 : 0;        // 2D: stencil y offset of the item
     float acc[K::NK][K::CH];
 #pragma unroll
     for (int k = 0; k < K::NK; ++k)
@@ -362,154 +343,258 @@ __global__ void __launch_bounds__(256) k_p2g(BatchDev b) {
       for (int c = 0; c < K::CH; ++c) acc[k][c] = 0.0f;
     const float dx = sp.dx, dt = sp.dt;
     const float Dx4 = 4.0f * sp.inv_dx;  // (4/dx^2) * dx
-    for (int c0 = 0; c0 < cnt; c0 += K::CHUNK) {
-      __syncthreads();  // previous chunk fully consumed (and phase A finished)
-      const int e = c0 + tid;
-      if (tid < K::CHUNK && e < cnt) {
-        const int id = int(ids[e]);
-        float r[Cfg<D>::S];
-        load_planes<D, Cfg<D>::PLANES>(sp.planes, sp.npad, id, r);
-        Part<D> q;
-        unpack<D>(r, q);
-        int base[D];
-        float f[D];
-        stencil_base<D>(q.x, sp.inv_dx, sp.n, base, f);
-        // the particle must sit in the cell its key names; otherwise contribute nothing
-        float wm = sp.mass;
-        {
-          int t[D], c[D];
-          unlin<D>(gt - sp.tile_base, sp.nt, t);
-          const int bn[3] = {B, B, B};
-          unlin<D>(int(sp.key[id] & 63u), bn, c);
-          bool ok = true;
+
+    // Phase B for one particle: record of particle `id` (state in r[]) at staging row `row`.
+    auto make_record = [&](int id, float* r, int row) {
+      Part<D> q;
+      unpack<D>(r, q);
+      int base[D];
+      float f[D];
+      stencil_base<D>(q.x, sp.inv_dx, sp.n, base, f);
+      // the particle must sit in the cell its key names; otherwise it contributes nothing
+      float wm = sp.mass;
+      {
+        int c[D];
+        const int bn[3] = {B, B, B};
+        unlin<D>(int(sp.key[id] & 63u), bn, c);
+        bool ok = true;
 #pragma unroll
-          for (int a = 0; a < D; ++a) ok = ok && base[a] == t[a] * B + c[a];
-          if (!ok) {
-            set_status(sp.status, ST_BINNING);
-            wm = 0.0f;
-          }
+        for (int a = 0; a < D; ++a) ok = ok && base[a] == t[a] * B + c[a];
+        if (!ok) {
+          set_status(sp.status, ST_BINNING);
+          wm = 0.0f;
         }
-        float P[D][D], A[D][D], G[D][D], sig[D];
-        float J = particle_G<D>(q, sp, id, P, A, G, sig);
-        if (!(J > 0.0f)) set_status(sp.status, ST_INVERTED);
-        const float keep = wm > 0.0f ? 1.0f : 0.0f;
-        float* rec = U + size_t(tid) * K::RW;
-        int o = 0;
+      }
+      float P[D][D], A[D][D], G[D][D], sig[D];
+      const float J = particle_G<D>(q, sp, id, P, A, G, sig);
+      if (!(J > 0.0f)) set_status(sp.status, ST_INVERTED);
+      const float keep = wm > 0.0f ? 1.0f : 0.0f;
+      float* rec = U + size_t(row) * K::RW;
+      int o = 0;
 #pragma unroll
-        for (int a = 0; a < D; ++a) rec[o++] = f[a];
-        // a = m v - dx G f ; M = dx G  (G (x_i - x_p) = dx G (k - f))
+      for (int a = 0; a < D; ++a) rec[o++] = f[a];
+      // a = m v - dx G f ; M = dx G, since G (x_i - x_p) = dx G (k - f)
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        float s = 0.0f;
+#pragma unroll
+        for (int c = 0; c < D; ++c) s += G[a][c] * f[c];
+        rec[o++] = keep * (sp.mass * q.v[a] - dx * s);
+      }
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int c = 0; c < D; ++c) rec[o++] = keep * dx * G[a][c];
+      rec[o++] = wm;
+      if constexpr (ADJ) {
+        // (A) vbar' = gv1 + dt gx1 ; (B) Cbar' = gC1 + dt gF1 F^T ; record of (C):
+        // vbar' + (4/dx^2) Cbar' (x_i - x_p) = [vbar' - (4/dx) Cbar' f] + (4/dx) Cbar' k
+        float ra[Cfg<D>::S];
+        load_planes<D, Cfg<D>::PLANES>(sp.adj_in, sp.npad, id, ra);
+        Part<D> g1;
+        unpack<D>(ra, g1);
+        float vb[D], Cb[D][D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) vb[a] = g1.v[a] + dt * g1.x[a];
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+          for (int c = 0; c < D; ++c) {
+            float s = 0.0f;
+#pragma unroll
+            for (int k = 0; k < D; ++k) s += g1.F[a][k] * q.F[c][k];
+            Cb[a][c] = g1.C[a][c] + dt * s;
+          }
 #pragma unroll
         for (int a = 0; a < D; ++a) {
           float s = 0.0f;
 #pragma unroll
-          for (int c = 0; c < D; ++c) s += G[a][c] * f[c];
-          rec[o++] = keep * (sp.mass * q.v[a] - dx * s);
+          for (int c = 0; c < D; ++c) s += Cb[a][c] * f[c];
+          rec[o++] = keep * (vb[a] - Dx4 * s);
         }
 #pragma unroll
         for (int a = 0; a < D; ++a)
 #pragma unroll
-          for (int c = 0; c < D; ++c) rec[o++] = keep * dx * G[a][c];
-        rec[o++] = wm;
-        if constexpr (ADJ) {
-          // (A) vbar' = gv1 + dt gx1 ; (B) Cbar' = gC1 + dt gF1 F^T ; record for (C):
-          // vbar'_p + (4/dx^2) Cbar' (x_i - x_p) = [vbar' - (4/dx) Cbar' f] + (4/dx) Cbar' k
-          float ra[Cfg<D>::S];
-          load_planes<D, Cfg<D>::PLANES>(sp.adj_in, sp.npad, id, ra);
-          Part<D> g1;
-          unpack<D>(ra, g1);
-          float vb[D], Cb[D][D];
-#pragma unroll
-          for (int a = 0; a < D; ++a) vb[a] = g1.v[a] + dt * g1.x[a];
-#pragma unroll
-          for (int a = 0; a < D; ++a)
-#pragma unroll
-            for (int c = 0; c < D; ++c) {
-              float s = 0.0f;
-#pragma unroll
-              for (int k = 0; k < D; ++k) s += g1.F[a][k] * q.F[c][k];
-              Cb[a][c] = g1.C[a][c] + dt * s;
-            }
-#pragma unroll
-          for (int a = 0; a < D; ++a) {
-            float s = 0.0f;
-#pragma unroll
-            for (int c = 0; c < D; ++c) s += Cb[a][c] * f[c];
-            rec[o++] = keep * (vb[a] - Dx4 * s);
-          }
-#pragma unroll
-          for (int a = 0; a < D; ++a)
-#pragma unroll
-            for (int c = 0; c < D; ++c) rec[o++] = keep * Dx4 * Cb[a][c];
-        }
+          for (int c = 0; c < D; ++c) rec[o++] = keep * Dx4 * Cb[a][c];
       }
-      __syncthreads();
-      if (acc_thread) {
-        const int lo = cs > c0 ? cs : c0;
-        const int hi = ce < c0 + K::CHUNK ? ce : c0 + K::CHUNK;
-        for (int ei = lo; ei < hi; ++ei) {
-          const float* rec = U + size_t(ei - c0) * K::RW;
-          const float mass = rec[K::RF - 1];
-          float w[D][3], dwd[3];
+    };
+
+    // Phase C over staged rows [lo, hi) (row = canonical position - c0): this thread's work item
+    // accumulates its stencil nodes over the cell's particles in canonical order.
+    auto accumulate = [&](int lo, int hi, int c0) {
+      for (int ei = lo; ei < hi; ++ei) {
+        const float* rec = U + size_t(ei - c0) * K::RW;
+        const float mass = rec[K::RF - 1];
+        float w[D][3], dwd[3];
 #pragma unroll
-          for (int a = 0; a < D; ++a) bspline(rec[a], 1.0f, w[a], dwd);
-          const float wx = w[0][my_kx];
-          // base value at (kx, 0, 0): a + M[:,0] kx
+        for (int a = 0; a < D; ++a) bspline(rec[a], 1.0f, w[a], dwd);
+        const float* av = rec + D;      // a
+        const float* Mv = rec + 2 * D;  // M, row-major
+        if constexpr (D == 2) {
+          const float N = w[0][ikx] * w[1][iky];
+#pragma unroll
+          for (int a = 0; a < D; ++a) acc[0][a] += N * (av[a] + Mv[a * D] * float(ikx) + Mv[a * D + 1] * float(iky));
+          acc[0][D] += N * mass;
+          if constexpr (ADJ) {
+            const float* aa = rec + K::RF;
+            const float* Ma = aa + D;
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+              acc[0][K::CHF + a] += N * (aa[a] + Ma[a * D] * float(ikx) + Ma[a * D + 1] * float(iky));
+          }
+        } else {
+          const float wx = w[0][ikx];
           float u[D], ua[D];
 #pragma unroll
-          for (int a = 0; a < D; ++a) u[a] = rec[D + a] + rec[2 * D + a * D + 0] * float(my_kx);
+          for (int a = 0; a < D; ++a) u[a] = av[a] + Mv[a * D] * float(ikx);
           if constexpr (ADJ) {
 #pragma unroll
-            for (int a = 0; a < D; ++a) ua[a] = rec[K::RF + a] + rec[K::RF + D + a * D + 0] * float(my_kx);
+            for (int a = 0; a < D; ++a) ua[a] = rec[K::RF + a] + rec[K::RF + D + a * D] * float(ikx);
           }
-          if constexpr (D == 2) {
 #pragma unroll
-            for (int ky = 0; ky < 3; ++ky) {
-              const float N = wx * w[1][ky];
+          for (int ky = 0; ky < 3; ++ky) {
+            const float wxy = wx * w[1][ky];
+            float u2[D], ua2[D];
 #pragma unroll
-              for (int a = 0; a < D; ++a) acc[ky][a] += N * (u[a] + rec[2 * D + a * D + 1] * float(ky));
-              acc[ky][D] += N * mass;
+            for (int a = 0; a < D; ++a) u2[a] = u[a] + Mv[a * D + 1] * float(ky);
+            if constexpr (ADJ) {
+#pragma unroll
+              for (int a = 0; a < D; ++a) ua2[a] = ua[a] + rec[K::RF + D + a * D + 1] * float(ky);
+            }
+#pragma unroll
+            for (int kz = 0; kz < 3; ++kz) {
+              const float N = wxy * w[D == 3 ? 2 : 0][kz];
+              const int k = ky * 3 + kz;
+#pragma unroll
+              for (int a = 0; a < D; ++a) acc[k][a] += N * (u2[a] + Mv[a * D + D - 1] * float(kz));
+              acc[k][D] += N * mass;
               if constexpr (ADJ) {
 #pragma unroll
                 for (int a = 0; a < D; ++a)
-                  acc[ky][K::CHF + a] += N * (ua[a] + rec[K::RF + D + a * D + 1] * float(ky));
-              }
-            }
-          } else {
-#pragma unroll
-            for (int ky = 0; ky < 3; ++ky) {
-              const float wxy = wx * w[1][ky];
-              float u2[D], ua2[D];
-#pragma unroll
-              for (int a = 0; a < D; ++a) u2[a] = u[a] + rec[2 * D + a * D + 1] * float(ky);
-              if constexpr (ADJ) {
-#pragma unroll
-                for (int a = 0; a < D; ++a) ua2[a] = ua[a] + rec[K::RF + D + a * D + 1] * float(ky);
-              }
-#pragma unroll
-              for (int kz = 0; kz < 3; ++kz) {
-                const float N = wxy * w[2][kz];
-                const int k = ky * 3 + kz;
-#pragma unroll
-                for (int a = 0; a < D; ++a) acc[k][a] += N * (u2[a] + rec[2 * D + a * D + 2] * float(kz));
-                acc[k][D] += N * mass;
-                if constexpr (ADJ) {
-#pragma unroll
-                  for (int a = 0; a < D; ++a)
-                    acc[k][K::CHF + a] += N * (ua2[a] + rec[K::RF + D + a * D + 2] * float(kz));
-                }
+                  acc[k][K::CHF + a] += N * (ua2[a] + rec[K::RF + D + a * D + D - 1] * float(kz));
               }
             }
           }
         }
       }
+    };
+
+    // scan of the per-cell counts in cfill into cstart (one warp; CELLS <= 64)
+    auto scan_cells = [&]() {
+      if (tid < 32) {
+        const int lane = tid;
+        int v0 = lane < CELLS ? cfill[lane] : 0, v1 = lane + 32 < CELLS ? cfill[lane + 32] : 0;
+        int i0 = v0, i1 = v1;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int a0 = __shfl_up_sync(0xffffffffu, i0, o), a1 = __shfl_up_sync(0xffffffffu, i1, o);
+          if (lane >= o) {
+            i0 += a0;
+            i1 += a1;
+          }
+        }
+        const int tot0 = __shfl_sync(0xffffffffu, i0, 31);
+        if (lane < CELLS) cstart[lane] = i0 - v0;
+        if (lane + 32 < CELLS) cstart[lane + 32] = tot0 + i1 - v1;
+        if (lane == 31) cstart[CELLS] = tot0 + (CELLS > 32 ? i1 : 0);
+      }
+    };
+
+    if (cnt <= 2 * K::THREADS && cnt <= K::REC_CAP) {
+      // ---- fast path: every thread owns raw entries tid and tid + THREADS of the tile list.
+      // Its first particle's state is requested at once and arrives while the tile is being
+      // bucketed; its canonical position is the cell start plus the number of smaller ids in its
+      // cell (order: cell, then particle id), and its record is written straight there.
+      if (tid < CELLS) cfill[tid] = 0;
+      const uint32_t r0 = tid < cnt ? b.sorted[st + tid] : 0xffffffffu;
+      const uint32_t r1 = tid + K::THREADS < cnt ? b.sorted[st + tid + K::THREADS] : 0xffffffffu;
+      float pre[Cfg<D>::S];
+      if (r0 != 0xffffffffu) load_planes<D, Cfg<D>::PLANES>(sp.planes, sp.npad, int(r0 & 0x3ffffffu), pre);
+      __syncthreads();
+      if (r0 != 0xffffffffu) atomicAdd(&cfill[r0 >> 26], 1);
+      if (r1 != 0xffffffffu) atomicAdd(&cfill[r1 >> 26], 1);
+      __syncthreads();
+      scan_cells();
+      __syncthreads();
+      if (tid < CELLS) cfill[tid] = 0;
+      __syncthreads();
+      if (r0 != 0xffffffffu) ids[cstart[r0 >> 26] + atomicAdd(&cfill[r0 >> 26], 1)] = r0 & 0x3ffffffu;
+      if (r1 != 0xffffffffu) ids[cstart[r1 >> 26] + atomicAdd(&cfill[r1 >> 26], 1)] = r1 & 0x3ffffffu;
+      __syncthreads();
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const uint32_t rr = h == 0 ? r0 : r1;
+        if (rr == 0xffffffffu) continue;
+        const uint32_t id = rr & 0x3ffffffu, c = rr >> 26;
+        int pos = cstart[c];
+        for (int j = cstart[c]; j < cstart[c + 1]; ++j) pos += ids[j] < id;
+        b.sorted[st + pos] = id;  // canonical order for the gathers of this step
+        if (h == 0) {
+          make_record(int(id), pre, pos);
+        } else {
+          float r[Cfg<D>::S];
+          load_planes<D, Cfg<D>::PLANES>(sp.planes, sp.npad, int(id), r);
+          make_record(int(id), r, pos);
+        }
+      }
+      __syncthreads();
+      if (item_thread) accumulate(cstart[my_cell], cstart[my_cell + 1], 0);
+    } else {
+      // ---- general path: bucket, insertion-sort each cell's ids, stage records in chunks
+      uint32_t* raw = reinterpret_cast<uint32_t*>(U);
+      if (tid < CELLS) cfill[tid] = 0;
+      __syncthreads();
+      for (int i = tid; i < cnt; i += blockDim.x) {
+        const uint32_t r = b.sorted[st + i];  // (cell << 26) | id, written by the scatter
+        raw[i] = r;
+        atomicAdd(&cfill[r >> 26], 1);
+      }
+      __syncthreads();
+      scan_cells();
+      __syncthreads();
+      if (tid < CELLS) cfill[tid] = 0;
+      __syncthreads();
+      for (int i = tid; i < cnt; i += blockDim.x) {
+        const uint32_t r = raw[i];
+        const uint32_t c = r >> 26;
+        ids[cstart[c] + atomicAdd(&cfill[c], 1)] = r & 0x3ffffffu;
+      }
+      __syncthreads();
+      if (tid < CELLS) {  // insertion sort of each cell's ids
+        const int s0 = cstart[tid], s1 = cstart[tid + 1];
+        for (int i = s0 + 1; i < s1; ++i) {
+          const uint32_t v = ids[i];
+          int j = i - 1;
+          while (j >= s0 && ids[j] > v) {
+            ids[j + 1] = ids[j];
+            --j;
+          }
+          ids[j + 1] = v;
+        }
+      }
+      __syncthreads();
+      for (int i = tid; i < cnt; i += blockDim.x) b.sorted[st + i] = ids[i];
+      const int cs = item_thread ? cstart[my_cell] : 0, ce = item_thread ? cstart[my_cell + 1] : 0;
+      for (int c0 = 0; c0 < cnt; c0 += K::REC_CAP) {
+        __syncthreads();  // previous records consumed (and phase A's scratch released)
+        const int c1 = cnt < c0 + K::REC_CAP ? cnt : c0 + K::REC_CAP;
+        for (int e = c0 + tid; e < c1; e += K::THREADS) {
+          const int id = int(ids[e]);
+          float r[Cfg<D>::S];
+          load_planes<D, Cfg<D>::PLANES>(sp.planes, sp.npad, id, r);
+          make_record(id, r, e - c0);
+        }
+        __syncthreads();
+        if (item_thread) accumulate(cs > c0 ? cs : c0, ce < c1 ? ce : c1, c0);
+      }
     }
     __syncthreads();  // records done; U becomes the per-cell stencil accumulator array
-    if (acc_thread) {
+    if (item_thread) {
       float* ca = U + size_t(my_cell) * ST * K::CH;
 #pragma unroll
       for (int k = 0; k < K::NK; ++k)
 #pragma unroll
-        for (int c = 0; c < K::CH; ++c) ca[(my_kx * K::NK + k) * K::CH + c] = acc[k][c];
+        for (int c = 0; c < K::CH; ++c) ca[(my_part * K::NK + k) * K::CH + c] = acc[k][c];
     }
     __syncthreads();
     // ---- phase D: node block = fixed-order sum over the cells whose stencil covers it -----
@@ -572,103 +657,158 @@ __global__ void __launch_bounds__(256) k_p2g(BatchDev b) {
 }
 
 // ============================================================================ grid
-// One thread per node of a tile's B^D node tile; 4 node tiles per 256-thread CTA.
+// The grid update of Eq. 6 with gravity and the boundary condition, evaluated by every CTA that
+// gathers from a node block: node i of tile t's (B+2)^D block sums, in a fixed order, the P2G node
+// blocks of the <= 2^D tiles whose blocks contain it.  With ADJ the adjoint-scatter blocks give
+// vbar*, and (L), (D), (E) give pbar and mbar.  Nodes a tile owns (its B^D corner) are also
+// written to the dense grid for inspection.
 template <int D, bool ADJ>
-__global__ void __launch_bounds__(256) k_grid(BatchDev b) {
+__device__ __forceinline__ void build_node_block(const BatchDev& b, const ScenePar& sp, const int* t, float4* sv,
+                                                 float4* sb) {
   constexpr int B = Cfg<D>::B, NB = Cfg<D>::BLOCK_NODES, BN = Cfg<D>::BN;
-  const int gt = blockIdx.x * 4 + (threadIdx.x >> 6);
-  if (gt >= b.total_tiles) return;
-  const ScenePar& sp = b.scenes[b.tile_scene[gt]];
-  int t[D], il[D], node[D];
-  unlin<D>(gt - sp.tile_base, sp.nt, t);
-  {
-    const int bn[3] = {B, B, B};
-    unlin<D>(threadIdx.x & 63, bn, il);
-  }
-#pragma unroll
-  for (int a = 0; a < D; ++a) {
-    node[a] = t[a] * B + il[a];
-    if (node[a] >= sp.n[a]) return;
-  }
-  float s[4] = {0.0f, 0.0f, 0.0f, 0.0f}, sb[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-  bool any = false;
-#pragma unroll
-  for (int e = 0; e < (1 << D); ++e) {  // source tile t - e, fixed order
-    int src[D], loc[D];
+  constexpr int NN = D == 2 ? 9 : 27;  // tiles t + o, o in {-1, 0, 1}^D
+  __shared__ int nslot[NN];
+  if (threadIdx.x < NN) {
+    int o[3] = {int(threadIdx.x) / (D == 2 ? 3 : 9) - 1, (int(threadIdx.x) / (D == 2 ? 1 : 3)) % 3 - 1,
+                int(threadIdx.x) % 3 - 1};
+    int u[D];
     bool ok = true;
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-      const int ea = (e >> (D - 1 - a)) & 1;
-      src[a] = t[a] - ea;
-      loc[a] = il[a] + ea * B;
-      ok = ok && src[a] >= 0 && loc[a] < BN;
+      u[a] = t[a] + o[a];
+      ok = ok && u[a] >= 0 && u[a] < sp.nt[a];
     }
-    if (!ok) continue;
-    const int slot = b.tile_slot[sp.tile_base + lin3<D>(src, sp.nt)];
-    if (slot < 0) continue;
-    any = true;
-    int l = 0;
-#pragma unroll
-    for (int a = 0; a < D; ++a) l = l * BN + loc[a];
-    const float4 v = b.partial[size_t(slot) * NB + l];
-    s[0] += v.x;
-    s[1] += v.y;
-    s[2] += v.z;
-    s[3] += v.w;
-    if constexpr (ADJ) {
-      const float4 g = b.partial_b[size_t(slot) * NB + l];
-      sb[0] += g.x;
-      sb[1] += g.y;
-      sb[2] += g.z;
-    }
+    nslot[threadIdx.x] = ok ? b.tile_slot[sp.tile_base + lin3<D>(u, sp.nt)] : -1;
   }
-  if (!any) return;
-  const float m = D == 2 ? s[2] : s[3];
-  float vraw[D], v[D];
-  if (m > 0.0f) {
-    const float rm = 1.0f / m;
+  __syncthreads();
+  for (int i = threadIdx.x; i < NB; i += blockDim.x) {
+    int nl[D], nd[D], r[D], qo[D];
+    bool in_grid = true, owned = true;
+    {
+      int l = i;
+#pragma unroll
+      for (int a = D - 1; a >= 0; --a) {
+        nl[a] = l % BN;
+        l /= BN;
+      }
+    }
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-      vraw[a] = s[a] * rm;
-      v[a] = vraw[a] + sp.dt * sp.gravity[a];
+      nd[a] = t[a] * B + nl[a];
+      in_grid = in_grid && nd[a] < sp.n[a];
+      owned = owned && nl[a] < B;
+      qo[a] = nl[a] / B;  // the node's tile is t + qo
+      r[a] = nl[a] - qo[a] * B;
     }
-    bc_apply<D>(node, sp.n, sp.bc, v);
-  } else {
+    if (!in_grid) {
+      sv[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if constexpr (ADJ) sb[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      continue;
+    }
+    // sources: tiles t + qo - e with e in {0,1}^D and r + e*B inside the block; independent loads
+    float4 pv[1 << D], pa[1 << D];
 #pragma unroll
-    for (int a = 0; a < D; ++a) v[a] = vraw[a] = 0.0f;
-  }
-  const int nl = lin3<D>(node, sp.n);
-  if constexpr (D == 2)
-    sp.grid[nl] = make_float4(v[0], v[1], m, 0.0f);
-  else
-    sp.grid[nl] = make_float4(v[0], v[1], v[2], m);
-  if constexpr (ADJ) {
-    // (L) boundary adjoint on vbar*, gravity passes through, (D) pbar = vbar/m, (E) mbar.
-    float g[D], pb[D], mb = 0.0f;
+    for (int e = 0; e < (1 << D); ++e) {
+      int so = 0, l = 0;
+      bool ok = true;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const int ea = (e >> (D - 1 - a)) & 1;
+        const int loc = r[a] + ea * B;
+        ok = ok && loc < BN;
+        so = so * 3 + (qo[a] - ea + 1);
+        l = l * BN + loc;
+      }
+      const int slot = ok ? nslot[so] : -1;
+      pv[e] = slot >= 0 ? b.partial[size_t(slot) * NB + l] : make_float4(0.f, 0.f, 0.f, 0.f);
+      if constexpr (ADJ) pa[e] = slot >= 0 ? b.partial_b[size_t(slot) * NB + l] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    float s[4] = {0.0f, 0.0f, 0.0f, 0.0f}, sa[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int e = 0; e < (1 << D); ++e) {  // fixed order
+      s[0] += pv[e].x;
+      s[1] += pv[e].y;
+      s[2] += pv[e].z;
+      s[3] += pv[e].w;
+      if constexpr (ADJ) {
+        sa[0] += pa[e].x;
+        sa[1] += pa[e].y;
+        sa[2] += pa[e].z;
+      }
+    }
+    const float m = s[D];
+    float vraw[D], v[D];
     if (m > 0.0f) {
-      float vg[D];
-#pragma unroll
-      for (int a = 0; a < D; ++a) {
-        g[a] = sb[a];
-        vg[a] = vraw[a] + sp.dt * sp.gravity[a];
-      }
-      bc_adjoint<D>(node, sp.n, sp.bc, vg, g);
       const float rm = 1.0f / m;
-      float dot = 0.0f;
 #pragma unroll
       for (int a = 0; a < D; ++a) {
-        pb[a] = g[a] * rm;
-        dot += vraw[a] * g[a];
+        vraw[a] = s[a] * rm;
+        v[a] = vraw[a] + sp.dt * sp.gravity[a];
       }
-      mb = -dot * rm;
+      bc_apply<D>(nd, sp.n, sp.bc, v);
     } else {
 #pragma unroll
-      for (int a = 0; a < D; ++a) pb[a] = 0.0f;
+      for (int a = 0; a < D; ++a) v[a] = vraw[a] = 0.0f;
     }
+    float4 o;
     if constexpr (D == 2)
-      sp.grid_b[nl] = make_float4(pb[0], pb[1], mb, 0.0f);
+      o = make_float4(v[0], v[1], m, 0.0f);
     else
-      sp.grid_b[nl] = make_float4(pb[0], pb[1], pb[2], mb);
+      o = make_float4(v[0], v[1], v[2], m);
+    sv[i] = o;
+    if (owned) sp.grid[lin3<D>(nd, sp.n)] = o;
+    if constexpr (ADJ) {
+      float g[D], pb[D], mb = 0.0f;
+      if (m > 0.0f) {
+        float vg[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          g[a] = sa[a];
+          vg[a] = vraw[a] + sp.dt * sp.gravity[a];
+        }
+        bc_adjoint<D>(nd, sp.n, sp.bc, vg, g);  // (L); gravity passes the adjoint through
+        const float rm = 1.0f / m;
+        float dot = 0.0f;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          pb[a] = g[a] * rm;        // (D)
+          dot += vraw[a] * g[a];
+        }
+        mb = -dot * rm;             // (E)
+      } else {
+#pragma unroll
+        for (int a = 0; a < D; ++a) pb[a] = 0.0f;
+      }
+      float4 ob;
+      if constexpr (D == 2)
+        ob = make_float4(pb[0], pb[1], mb, 0.0f);
+      else
+        ob = make_float4(pb[0], pb[1], pb[2], mb);
+      sb[i] = ob;
+      if (owned) sp.grid_b[lin3<D>(nd, sp.n)] = ob;
+    }
+  }
+}
+
+// Deterministic per-warp group sums: lanes hold (group g, value c); the sum of every group present
+// in the warp is formed by a fixed butterfly and added to the register of the lane that owns the
+// group (lane g % 32, slot g / 32).  All 32 lanes must call it.
+__device__ __forceinline__ void warp_group_add(int g, float c, float& lo, float& hi) {
+  const int lane = threadIdx.x & 31;
+  unsigned todo = __ballot_sync(0xffffffffu, g >= 0);
+  while (todo) {
+    const int leader = __ffs(todo) - 1;
+    const int gs = __shfl_sync(0xffffffffu, g, leader);
+    float v = g == gs ? c : 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == (gs & 31)) {
+      if (gs >> 5)
+        hi += v;
+      else
+        lo += v;
+    }
+    todo &= ~__ballot_sync(0xffffffffu, g == gs);
   }
 }
 
@@ -735,29 +875,27 @@ __global__ void __launch_bounds__(256) k_g2p(BatchDev b) {
   __shared__ float4 sv[NB];
   const int tid = threadIdx.x;
   const int n_active = *b.n_active;
+  if (blockIdx.x == 0)  // this step's counters move on (every reader of them ran before)
+    for (int s = tid; s < b.n_scenes; s += blockDim.x)
+      if (b.scenes[s].step_ctr) *b.scenes[s].step_ctr += 1;
   for (int slot = blockIdx.x; slot < n_active; slot += gridDim.x) {
     const int gt = b.active[slot];
     const ScenePar& sp = b.scenes[b.tile_scene[gt]];
     int t[D];
     unlin<D>(gt - sp.tile_base, sp.nt, t);
-    for (int i = tid; i < NB; i += blockDim.x) {
-      int l = i, nd[D];
-      bool ok = true;
-#pragma unroll
-      for (int a = D - 1; a >= 0; --a) {
-        nd[a] = t[a] * B + l % BN;
-        l /= BN;
-        ok = ok && nd[a] < sp.n[a];
-      }
-      sv[i] = ok ? sp.grid[lin3<D>(nd, sp.n)] : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    __syncthreads();
     const uint32_t st = b.tile_start[gt];
     const int cnt = int(b.tile_start[gt + 1] - st);
+    // the first particle's state is requested before the node block is built, so the two overlap
+    float r[Cfg<D>::S];
+    int id = tid < cnt ? int(b.sorted[st + tid]) : 0;
+    if (tid < cnt) load_planes<D, Cfg<D>::XF_PLANES>(sp.planes, sp.npad, id, r);
+    build_node_block<D, false>(b, sp, t, sv, nullptr);
+    __syncthreads();
     for (int e = tid; e < cnt; e += blockDim.x) {
-      const int id = int(b.sorted[st + e]);
-      float r[Cfg<D>::S];
-      load_planes<D, Cfg<D>::XF_PLANES>(sp.planes, sp.npad, id, r);
+      if (e != tid) {
+        id = int(b.sorted[st + e]);
+        load_planes<D, Cfg<D>::XF_PLANES>(sp.planes, sp.npad, id, r);
+      }
       Part<D> q;
       unpack<D>(r, q);
       int base[D];
@@ -779,9 +917,12 @@ __global__ void __launch_bounds__(256) k_g2p(BatchDev b) {
         if constexpr (D == 3) l = l * BN + base[2] + kz;
         return sv[l];
       });
-      pack<D>(q, r);
-      store_planes<D, Cfg<D>::PLANES>(sp.planes_out, sp.npad, id, r);
-      sp.key[id] = bin_key<D>(q.x, sp);
+      float ro[Cfg<D>::S];
+      pack<D>(q, ro);
+      store_planes<D, Cfg<D>::PLANES>(sp.planes_out, sp.npad, id, ro);
+      const uint32_t nk = bin_key<D>(q.x, sp);  // bin of state n+1 and its histogram
+      sp.key[id] = nk;
+      warp_aggregated_inc(b.tile_count, nk != KEY_INVALID ? int(sp.tile_base + (nk >> 6)) : -1);
     }
     __syncthreads();
   }
@@ -797,8 +938,11 @@ __device__ __forceinline__ float adj_core(const Part<D>& q, const Part<D>& g1, c
   const float dt = sp.dt, dx = sp.dx, mass = sp.mass;
   const float Dinv = 4.0f * sp.inv_dx * sp.inv_dx;
   const float kG = -Dinv * dt * sp.vol;
-  float P[D][D], A[D][D], G[D][D], sig[D];
-  const float J = particle_G<D>(q, sp, id, P, A, G, sig);
+  float G[D][D], sig[D];
+  {
+    float P[D][D], A[D][D];  // recomputed after the stencil loop: not kept live across it
+    particle_G<D>(q, sp, id, P, A, G, sig);
+  }
   float vb[D], Cb[D][D];
 #pragma unroll
   for (int a = 0; a < D; ++a) vb[a] = g1.v[a] + dt * g1.x[a];
@@ -821,35 +965,40 @@ __device__ __forceinline__ float adj_core(const Part<D>& q, const Part<D>& g1, c
   float mv[D];
 #pragma unroll
   for (int a = 0; a < D; ++a) mv[a] = mass * q.v[a];
-#pragma unroll
-  for (int kx = 0; kx < 3; ++kx)
+#pragma unroll 1
+  for (int kx = 0; kx < 3; ++kx) {
+    // weights of this x-slab as scalars (a loop index must not index the weight arrays)
+    const float wx = kx == 0 ? w[0][0] : (kx == 1 ? w[0][1] : w[0][2]);
+    const float dwx = kx == 0 ? dw[0][0] : (kx == 1 ? dw[0][1] : dw[0][2]);
+    const float dkx = float(kx) - f[0];
 #pragma unroll
     for (int ky = 0; ky < 3; ++ky)
 #pragma unroll
       for (int kz = 0; kz < (D == 3 ? 3 : 1); ++kz) {
-        const int k[3] = {kx, ky, kz};
-        float N = 1.0f, dN[D];
-#pragma unroll
-        for (int a = 0; a < D; ++a) N *= w[a][k[a]];
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-          float g = dw[a][k[a]];
-#pragma unroll
-          for (int c = 0; c < D; ++c)
-            if (c != a) g *= w[c][k[c]];
-          dN[a] = g;
+        float wyz = w[1][ky], N, dN[D], dk[D];
+        if constexpr (D == 3) {
+          const float wz = w[D == 3 ? 2 : 0][kz];
+          wyz *= wz;
+          N = wx * wyz;
+          dN[0] = dwx * wyz;
+          dN[1] = wx * dw[1][ky] * wz;
+          dN[D == 3 ? 2 : 0] = wx * w[1][ky] * dw[D == 3 ? 2 : 0][kz];
+          dk[D == 3 ? 2 : 0] = float(kz) - f[D == 3 ? 2 : 0];
+        } else {
+          N = wx * wyz;
+          dN[0] = dwx * wyz;
+          dN[1] = wx * dw[1][ky];
         }
+        dk[0] = dkx;
+        dk[1] = float(ky) - f[1];
         float4 v4, p4;
         fetch(kx, ky, kz, v4, p4);
         const float vs[3] = {v4.x, v4.y, v4.z};
         const float pb[3] = {p4.x, p4.y, p4.z};
         const float mb = D == 2 ? p4.z : p4.w;
-        float dk[D], dp[D];
+        float dp[D];
 #pragma unroll
-        for (int a = 0; a < D; ++a) {
-          dk[a] = float(k[a]) - f[a];
-          dp[a] = dk[a] * dx;
-        }
+        for (int a = 0; a < D; ++a) dp[a] = dk[a] * dx;
         // s_i = vbar'.v* + Dinv v*^T Cbar' d + pbar.(m v + G d) + m mbar
         float si = mass * mb;
 #pragma unroll
@@ -874,6 +1023,7 @@ __device__ __forceinline__ float adj_core(const Part<D>& q, const Part<D>& g1, c
           }
         }
       }
+  }
   // (J): gx = gx' + sum dN s_i - Dinv Cbar'^T sum N v* - G^T sum N pbar
 #pragma unroll
   for (int a = 0; a < D; ++a) {
@@ -896,6 +1046,8 @@ __device__ __forceinline__ float adj_core(const Part<D>& q, const Part<D>& g1, c
       for (int k = 0; k < D; ++k) s += Gbar[a][k] * q.F[k][c];
       Pb[a][c] = kG * s;  // (G)
     }
+  float P[D][D], A[D][D];
+  const float J = stress<D>(q.F, sp.mat, sig, P, A);
   float H[D][D];
   nh_hessian_apply<D>(A, J, sp.mat, Pb, H);
   // (H) Fbar = (I + dt C^{n+1})^T Fbar' + H[Pbar] + Pbar sigma^T + kG Gbar^T P
@@ -928,63 +1080,70 @@ __device__ __forceinline__ float adj_core(const Part<D>& q, const Part<D>& g1, c
 }
 
 template <int D>
-__global__ void __launch_bounds__(256) k_adj_gather(BatchDev b) {
+__global__ void __launch_bounds__(256, 2) k_adj_gather(BatchDev b) {
   constexpr int B = Cfg<D>::B, NB = Cfg<D>::BLOCK_NODES, BN = Cfg<D>::BN;
   __shared__ float4 sv[NB], sb[NB];
-  const int tid = threadIdx.x;
+  __shared__ float wpart[8][MAX_GROUPS];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n_active = *b.n_active;
   for (int slot = blockIdx.x; slot < n_active; slot += gridDim.x) {
     const int gt = b.active[slot];
     const ScenePar& sp = b.scenes[b.tile_scene[gt]];
     int t[D];
     unlin<D>(gt - sp.tile_base, sp.nt, t);
-    for (int i = tid; i < NB; i += blockDim.x) {
-      int l = i, nd[D];
-      bool ok = true;
-#pragma unroll
-      for (int a = D - 1; a >= 0; --a) {
-        nd[a] = t[a] * B + l % BN;
-        l /= BN;
-        ok = ok && nd[a] < sp.n[a];
-      }
-      const int nl = ok ? lin3<D>(nd, sp.n) : 0;
-      sv[i] = ok ? sp.grid[nl] : make_float4(0.f, 0.f, 0.f, 0.f);
-      sb[i] = ok ? sp.grid_b[nl] : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    __syncthreads();
     const uint32_t st = b.tile_start[gt];
     const int cnt = int(b.tile_start[gt + 1] - st);
-    for (int e = tid; e < cnt; e += blockDim.x) {
-      const int id = int(b.sorted[st + e]);
-      float r[Cfg<D>::S];
-      load_planes<D, Cfg<D>::PLANES>(sp.planes, sp.npad, id, r);
-      Part<D> q, g1, g0;
-      unpack<D>(r, q);
-      load_planes<D, Cfg<D>::PLANES>(sp.adj_in, sp.npad, id, r);
-      unpack<D>(r, g1);
-      int base[D];
-      float f[D], w[D][3], dw[D][3];
-      stencil_base<D>(q.x, sp.inv_dx, sp.n, base, f);
-      bool inside = true;
+    // the first particle's state is requested before the node block is built, so the two overlap
+    float r[Cfg<D>::S];
+    if (tid < cnt) load_planes<D, Cfg<D>::PLANES>(sp.planes, sp.npad, int(b.sorted[st + tid]), r);
+    build_node_block<D, true>(b, sp, t, sv, sb);
+    __syncthreads();
+    float lo = 0.0f, hi = 0.0f;  // per-warp group sums of (K), lane-owned
+    for (int e0 = 0; e0 < cnt; e0 += blockDim.x) {
+      const int e = e0 + tid;
+      int g = -1;
+      float contrib = 0.0f;
+      if (e < cnt) {
+        const int id = int(b.sorted[st + e]);
+        if (e0 > 0) load_planes<D, Cfg<D>::PLANES>(sp.planes, sp.npad, id, r);
+        Part<D> q, g1, g0;
+        unpack<D>(r, q);
+        load_planes<D, Cfg<D>::PLANES>(sp.adj_in, sp.npad, id, r);
+        unpack<D>(r, g1);
+        int base[D];
+        float f[D], w[D][3], dw[D][3];
+        stencil_base<D>(q.x, sp.inv_dx, sp.n, base, f);
+        bool inside = true;
 #pragma unroll
-      for (int a = 0; a < D; ++a) {
-        bspline(f[a], sp.inv_dx, w[a], dw[a]);
-        base[a] -= t[a] * B;
-        inside = inside && base[a] >= 0 && base[a] < B;
+        for (int a = 0; a < D; ++a) {
+          bspline(f[a], sp.inv_dx, w[a], dw[a]);
+          base[a] -= t[a] * B;
+          inside = inside && base[a] >= 0 && base[a] < B;
+        }
+        if (inside) {
+          contrib = adj_core<D>(q, g1, f, w, dw, sp, id, [&](int kx, int ky, int kz, float4& v, float4& p) {
+            int l = (base[0] + kx) * BN + base[1] + ky;
+            if constexpr (D == 3) l = l * BN + base[2] + kz;
+            v = sv[l];
+            p = sb[l];
+          }, g0);
+          pack<D>(g0, r);
+          store_planes<D, Cfg<D>::PLANES>(sp.adj_out, sp.npad, id, r);
+          g = sp.group ? __ldg(sp.group + id) : -1;
+          if (g >= sp.G) g = -1;
+        } else {
+          set_status(sp.status, ST_BINNING);
+        }
       }
-      if (!inside) {
-        set_status(sp.status, ST_BINNING);
-        continue;
-      }
-      const float c = adj_core<D>(q, g1, f, w, dw, sp, id, [&](int kx, int ky, int kz, float4& v, float4& p) {
-        int l = (base[0] + kx) * BN + base[1] + ky;
-        if constexpr (D == 3) l = l * BN + base[2] + kz;
-        v = sv[l];
-        p = sb[l];
-      }, g0);
-      pack<D>(g0, r);
-      store_planes<D, Cfg<D>::PLANES>(sp.adj_out, sp.npad, id, r);
-      sp.sig_contrib[id] = c;
+      warp_group_add(g, contrib, lo, hi);
+    }
+    wpart[warp][lane] = lo;
+    wpart[warp][lane + 32] = hi;
+    __syncthreads();
+    if (tid < MAX_GROUPS) {
+      float s = 0.0f;
+      for (int w = 0; w < int(blockDim.x >> 5); ++w) s += wpart[w][tid];
+      b.gpartial[size_t(slot) * MAX_GROUPS + tid] = s;
     }
     __syncthreads();
   }
@@ -993,6 +1152,8 @@ __global__ void __launch_bounds__(256) k_adj_gather(BatchDev b) {
 // ============================================================================ launchers (tiled)
 template <int D>
 cudaError_t launch_keys(const BatchDev& b, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(b.tile_count, 0, sizeof(uint32_t) * size_t(b.total_tiles), s);
+  if (e != cudaSuccess) return e;
   if (b.total_particles == 0) return cudaSuccess;
   k_keys<D><<<(b.total_particles + 255) / 256, 256, 0, s>>>(b);
   count_launches(1);
@@ -1001,7 +1162,6 @@ cudaError_t launch_keys(const BatchDev& b, cudaStream_t s) {
 
 template <int D>
 cudaError_t launch_sort(const BatchDev& b, cudaStream_t s) {
-  if (b.total_particles > 0) k_hist<D><<<(b.total_particles + 255) / 256, 256, 0, s>>>(b);
   const int nblk = (b.total_tiles + SCAN_TILE - 1) / SCAN_TILE;
   if (nblk <= 1) {
     k_scan_down<<<1, SCAN_THREADS, 0, s>>>(b, 1);
@@ -1011,19 +1171,27 @@ cudaError_t launch_sort(const BatchDev& b, cudaStream_t s) {
     k_scan_down<<<nblk, SCAN_THREADS, 0, s>>>(b, 0);
   }
   if (b.total_particles > 0) k_scatter<D><<<(b.total_particles + 255) / 256, 256, 0, s>>>(b);
-  count_launches((b.total_particles > 0 ? 2 : 0) + (nblk <= 1 ? 1 : 3));
+  count_launches((b.total_particles > 0 ? 1 : 0) + (nblk <= 1 ? 1 : 3));
   return cudaGetLastError();
+}
+
+template <int D, bool ADJ>
+static cudaError_t p2g_configure() {
+  using K = P2GCfg<D, ADJ>;
+  return cudaFuncSetAttribute(k_p2g<D, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(K::SMEM));
+}
+
+cudaError_t configure_kernels() {
+  cudaError_t e;
+  if ((e = p2g_configure<2, false>()) != cudaSuccess) return e;
+  if ((e = p2g_configure<2, true>()) != cudaSuccess) return e;
+  if ((e = p2g_configure<3, false>()) != cudaSuccess) return e;
+  return p2g_configure<3, true>();
 }
 
 template <int D, bool ADJ>
 static cudaError_t p2g_impl(const BatchDev& b, cudaStream_t s) {
   using K = P2GCfg<D, ADJ>;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_p2g<D, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(K::SMEM));
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
   int grid = b.max_ctas < b.total_tiles ? b.max_ctas : b.total_tiles;
   if (grid < 1) grid = 1;
   k_p2g<D, ADJ><<<grid, K::THREADS, K::SMEM, s>>>(b);
@@ -1034,18 +1202,6 @@ static cudaError_t p2g_impl(const BatchDev& b, cudaStream_t s) {
 template <int D>
 cudaError_t launch_p2g(const BatchDev& b, bool with_adjoint, cudaStream_t s) {
   return with_adjoint ? p2g_impl<D, true>(b, s) : p2g_impl<D, false>(b, s);
-}
-
-template <int D>
-cudaError_t launch_grid(const BatchDev& b, bool with_adjoint, cudaStream_t s) {
-  const int grid = (b.total_tiles + 3) / 4;
-  if (grid == 0) return cudaSuccess;
-  if (with_adjoint)
-    k_grid<D, true><<<grid, 256, 0, s>>>(b);
-  else
-    k_grid<D, false><<<grid, 256, 0, s>>>(b);
-  count_launches(1);
-  return cudaGetLastError();
 }
 
 template <int D>
@@ -1072,8 +1228,6 @@ template cudaError_t launch_sort<2>(const BatchDev&, cudaStream_t);
 template cudaError_t launch_sort<3>(const BatchDev&, cudaStream_t);
 template cudaError_t launch_p2g<2>(const BatchDev&, bool, cudaStream_t);
 template cudaError_t launch_p2g<3>(const BatchDev&, bool, cudaStream_t);
-template cudaError_t launch_grid<2>(const BatchDev&, bool, cudaStream_t);
-template cudaError_t launch_grid<3>(const BatchDev&, bool, cudaStream_t);
 template cudaError_t launch_g2p<2>(const BatchDev&, cudaStream_t);
 template cudaError_t launch_g2p<3>(const BatchDev&, cudaStream_t);
 template cudaError_t launch_adj_gather<2>(const BatchDev&, cudaStream_t);
@@ -1216,6 +1370,7 @@ template <int D>
 __global__ void k_plain_g2p(const ScenePar* __restrict__ dsp) {
   const ScenePar& sp = *dsp;
   const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id == 0 && sp.step_ctr) *sp.step_ctr += 1;
   if (id >= sp.N) return;
   float r[Cfg<D>::S];
   load_planes<D, Cfg<D>::XF_PLANES>(sp.planes, sp.npad, id, r);
@@ -1261,6 +1416,30 @@ __global__ void k_plain_gather(const ScenePar* __restrict__ dsp) {
   sp.sig_contrib[id] = c;
 }
 
+// Per-block (256 particles) group sums of the (K) contributions of the plain form.
+__global__ void k_plain_group_partials(const ScenePar* __restrict__ dsp, float* __restrict__ gpart) {
+  const ScenePar& sp = *dsp;
+  __shared__ float wpart[8][MAX_GROUPS];
+  const int id = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int g = -1;
+  float c = 0.0f;
+  if (id < sp.N) {
+    g = sp.group ? sp.group[id] : -1;
+    if (g >= sp.G) g = -1;
+    c = sp.sig_contrib[id];
+  }
+  float lo = 0.0f, hi = 0.0f;
+  warp_group_add(g, c, lo, hi);
+  wpart[warp][lane] = lo;
+  wpart[warp][lane + 32] = hi;
+  __syncthreads();
+  if (threadIdx.x < MAX_GROUPS) {
+    float s = 0.0f;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) s += wpart[w][threadIdx.x];
+    gpart[size_t(blockIdx.x) * MAX_GROUPS + threadIdx.x] = s;
+  }
+}
+
 static int host_nodes(const ScenePar& sp) {
   int c = 1;
   for (int a = 0; a < sp.dim; ++a) c *= sp.n[a];
@@ -1274,13 +1453,13 @@ cudaError_t launch_plain_step(const ScenePar* dsp, const ScenePar& sp, cudaStrea
   if (e != cudaSuccess) return e;
   if (sp.N > 0) k_plain_scatter<D, false><<<(sp.N + 255) / 256, 256, 0, s>>>(dsp);
   k_plain_grid<D, false><<<(nn + 255) / 256, 256, 0, s>>>(dsp, nn);
-  if (sp.N > 0) k_plain_g2p<D><<<(sp.N + 255) / 256, 256, 0, s>>>(dsp);
-  count_launches(sp.N > 0 ? 3 : 1);
+  k_plain_g2p<D><<<(sp.N + 255) / 256 + (sp.N == 0), 256, 0, s>>>(dsp);
+  count_launches(sp.N > 0 ? 3 : 2);
   return cudaGetLastError();
 }
 
 template <int D>
-cudaError_t launch_plain_adjoint(const ScenePar* dsp, const ScenePar& sp, cudaStream_t s) {
+cudaError_t launch_plain_adjoint(const ScenePar* dsp, const ScenePar& sp, float* gpart, cudaStream_t s) {
   const int nn = host_nodes(sp);
   cudaError_t e = cudaMemsetAsync(sp.grid, 0, sizeof(float4) * size_t(nn), s);
   if (e != cudaSuccess) return e;
@@ -1289,14 +1468,15 @@ cudaError_t launch_plain_adjoint(const ScenePar* dsp, const ScenePar& sp, cudaSt
   if (sp.N > 0) k_plain_scatter<D, true><<<(sp.N + 255) / 256, 256, 0, s>>>(dsp);
   k_plain_grid<D, true><<<(nn + 255) / 256, 256, 0, s>>>(dsp, nn);
   if (sp.N > 0) k_plain_gather<D><<<(sp.N + 255) / 256, 256, 0, s>>>(dsp);
-  count_launches(sp.N > 0 ? 3 : 1);
+  if (sp.N > 0) k_plain_group_partials<<<(sp.N + 255) / 256, 256, 0, s>>>(dsp, gpart);
+  count_launches(sp.N > 0 ? 4 : 1);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_plain_step<2>(const ScenePar*, const ScenePar&, cudaStream_t);
 template cudaError_t launch_plain_step<3>(const ScenePar*, const ScenePar&, cudaStream_t);
-template cudaError_t launch_plain_adjoint<2>(const ScenePar*, const ScenePar&, cudaStream_t);
-template cudaError_t launch_plain_adjoint<3>(const ScenePar*, const ScenePar&, cudaStream_t);
+template cudaError_t launch_plain_adjoint<2>(const ScenePar*, const ScenePar&, float*, cudaStream_t);
+template cudaError_t launch_plain_adjoint<3>(const ScenePar*, const ScenePar&, float*, cudaStream_t);
 
 // ============================================================================ pack / unpack
 __global__ void k_pack(int dim, int N, int npad, const float* x, const float* v, const float* C, const float* F,
@@ -1340,6 +1520,41 @@ __global__ void k_unpack(int dim, int N, int npad, const float4* planes, float* 
     if (v) v[size_t(p) * dim + a] = r[o];
   for (int a = 0; a < d2; ++a, ++o)
     if (C) C[size_t(p) * d2 + a] = r[o];
+}
+
+// Device-side choice of this step's scene records: scene s of the launch uses
+// table[map[*ctr - base]] (map NULL: table[0]), with the batch offsets patched in; the
+// sinusoid controllers' actuation a_g(t_n) is evaluated here too.  Every step of a rollout is
+// then the same launch sequence, which CUDA graphs replay.
+__global__ void k_select(const SelectPar* __restrict__ sel, ScenePar* __restrict__ cur) {
+  const SelectPar& q = sel[blockIdx.x];
+  const int n = *q.ctr;
+  const int idx = q.map ? q.map[n - q.base] : 0;
+  const int* src = reinterpret_cast<const int*>(q.table + idx);
+  int* dst = reinterpret_cast<int*>(cur + blockIdx.x);
+  constexpr int W = int(sizeof(ScenePar) / sizeof(int));
+  for (int i = threadIdx.x; i < W; i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    cur[blockIdx.x].tile_base = q.tile_base;
+    cur[blockIdx.x].pbase = q.pbase;
+  }
+  const float tt = float(n) * q.dt;
+  const int g = threadIdx.x;
+  if (g < q.G && q.ctrl_type == 0) {
+    q.act[g] = q.params[g] * sinf(6.283185307179586f * q.freq * tt);
+  } else if (g < q.G && q.ctrl_type == 1) {
+    const float w = 6.283185307179586f * q.freq * tt;
+    q.act[g] = q.params[g * 4] * sinf(w) + q.params[g * 4 + 1] * cosf(w) + q.params[g * 4 + 2] * sinf(2.0f * w) +
+               q.params[g * 4 + 3] * cosf(2.0f * w);
+  }
+}
+
+cudaError_t launch_select(const SelectPar* sel, int n_scenes, ScenePar* cur, cudaStream_t s) {
+  if (n_scenes <= 0) return cudaSuccess;
+  k_select<<<n_scenes, 64, 0, s>>>(sel, cur);
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 __global__ void k_set_int(int* p, int v) { *p = v; }

@@ -189,7 +189,10 @@ class Context:
     def __init__(self, device: int = 0, stream=None):
         raw = None
         if stream is not None:
-            raw = C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+            handle = int(getattr(stream, "cuda_stream", stream))
+            # handle 0 is the legacy default stream, which the C ABI spells cudaStreamLegacy (0x1);
+            # a NULL stream would make the library create a private one
+            raw = C.c_void_p(handle if handle != 0 else 1)
         h = C.c_void_p()
         _check(lib().mpm_ctx_create(C.byref(h), int(device), raw), "mpm_ctx_create")
         self.handle = h
