@@ -127,6 +127,11 @@ mpm_status mpm_backward(mpm_scene* scene, const float* gx_T, const float* gv_T, 
                         const float* gF_T, float* gx0, float* gv0, float* gC0, float* gF0,
                         float* g_ctrl_params, int mem_space);
 
+/* Result of the last finished reverse pass (mpm_backward, or a batched gradient request): dL/d
+ * of the rollout's first x, v, C, F and of the controller parameters (NULL = not wanted).
+ * Synchronises; MPM_ERR_STATE if no reverse pass has finished since the last rollout. */
+mpm_status mpm_get_gradients(mpm_scene* scene, float* gx0, float* gv0, float* gC0, float* gF0, float* g_ctrl_params,
+                             int mem_space);
 /* Copies the state out (step -1 = current, else a checkpointed step of the last rollout).
  * Synchronises; returns the scene's first device error. */
 mpm_status mpm_get_state(mpm_scene* scene, int step, float* x, float* v, float* C, float* F, int mem_space);

@@ -23,74 +23,14 @@
 
 #include "../../include/mpm.h"
 #include "mpm_internal.h"
+#include "mpm_scene.h"
 
 using namespace gbmpm;
 
 namespace {
-constexpr int GRAPH_STEPS = 8;  // steps per replayed graph
-enum Phase { PH_STEP = 0, PH_ROLL = 1, PH_RCM = 2, PH_REV = 3, PH_PREP = 4, PH_COUNT = 5 };
 std::mutex g_config_mutex;
 bool g_configured[64] = {};
 }  // namespace
-
-struct mpm_ctx {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  cudaStream_t capture = nullptr;  // private stream graphs are captured on
-  int sm_count = 1;
-  // launch timing (mpm_profile_*): event pairs around launches of the selected kinds; while a
-  // mask is set, steps are launched directly (not from graphs) so every launch can be bracketed
-  unsigned prof_mask = 0;
-  std::vector<cudaEvent_t> prof_ev;
-  std::vector<int> prof_kind;
-  int prof_used = 0;
-};
-
-struct Graph {
-  cudaGraphExec_t exec = nullptr;
-  long long kernels = 0;
-};
-
-struct mpm_scene {
-  mpm_ctx* ctx = nullptr;
-  int dim = 0, N = 0, npad = 0, G = 0, nparams = 0, impl = 0, n_nodes = 0;
-  size_t state_bytes = 0;
-  ScenePar hp{};             // host template of the scene record
-  CtrlPar ctrl{};
-  BatchDev b{};              // private batch of one scene; b.scenes = cur
-  std::vector<void*> allocs; // everything allocated at creation
-  float4* state = nullptr;   // current state planes
-  float4* adj[2] = {nullptr, nullptr};
-  int* d_step = nullptr;     // forward step counter (controller time)
-  int* d_bstep = nullptr;    // reverse step counter
-  int* d_status = nullptr;
-  ScenePar* cur = nullptr;   // device: the record of the running step
-  SelectPar* dsel = nullptr; // device: one selection per phase
-  SelectPar hsel[PH_COUNT]{};
-  int step = 0;              // host mirror of the current step
-  // device record tables, one per phase family (uploaded only when their content changes)
-  struct Table {
-    ScenePar* dev = nullptr;
-    int cap = 0;
-    std::vector<ScenePar> host;
-  } tables[3];               // 0 = in-place step, 1 = rollout, 2 = recompute + reverse
-  struct Map {
-    int* dev = nullptr;
-    int cap = 0;
-    std::vector<int> host;
-  } maps[3];                 // record index per step: rollout, recompute, reverse
-  Graph graphs[PH_COUNT][2]; // [phase][single step, GRAPH_STEPS steps]
-  // rollout record
-  bool have_rollout = false;
-  int roll_T = 0, roll_k = 0, roll_start = 0, roll_nseg = 0;
-  std::vector<float4*> ckpt;
-  std::vector<float4*> seg;  // k - 1 recompute buffers
-  std::vector<void*> roll_allocs;
-  // staging scratch
-  void* scratch = nullptr;
-  size_t scratch_bytes = 0;
-};
 
 namespace {
 
@@ -390,6 +330,20 @@ mpm_status run_phase(mpm_scene* s, int ph, int count) {
   return MPM_OK;
 }
 
+
+void free_rollout(mpm_scene* s) {
+  if (!s->roll_allocs.empty()) cudaStreamSynchronize(s->ctx->stream);
+  for (void* p : s->roll_allocs) cudaFree(p);
+  s->roll_allocs.clear();
+  s->ckpt.clear();
+  s->seg.clear();
+  s->have_rollout = false;
+}
+
+}  // namespace
+
+namespace gbmpm {
+
 mpm_status set_counter(mpm_scene* s, int* dctr, int value) {
   CK(launch_set_int(dctr, value, s->ctx->stream));
   return MPM_OK;
@@ -402,16 +356,179 @@ mpm_status read_status(mpm_scene* s) {
   return mpm_status(v);
 }
 
-void free_rollout(mpm_scene* s) {
-  if (!s->roll_allocs.empty()) cudaStreamSynchronize(s->ctx->stream);
-  for (void* p : s->roll_allocs) cudaFree(p);
-  s->roll_allocs.clear();
-  s->ckpt.clear();
-  s->seg.clear();
+
+// Rollout set-up: checkpoint buffers (kept when the shape repeats), the record table and the
+// per-step record map, the forward counter, and checkpoint 0 = the current state.
+mpm_status prepare_rollout(mpm_scene* s, int T, int k, size_t budget) {
   s->have_rollout = false;
+  s->have_grad = false;
+  const size_t S = s->state_bytes;
+  if (k == 0) k = (budget == 0 || size_t(T) * S <= budget) ? 1 : int(std::ceil(std::sqrt(double(T))));
+  k = std::min(k, T);
+  const int nseg = (T + k - 1) / k;
+  const size_t need = (size_t(nseg) + size_t(k - 1)) * S;
+  if (budget != 0 && need > budget) return MPM_ERR_OOM;
+  if (int(s->ckpt.size()) != nseg || int(s->seg.size()) != k - 1) {
+    free_rollout(s);  // buffers of another shape
+    s->ckpt.assign(nseg, nullptr);
+    for (int i = 0; i < nseg; ++i) {
+      mpm_status st = dalloc(&s->ckpt[i], S / sizeof(float4), s->roll_allocs);
+      if (st != MPM_OK) {
+        free_rollout(s);
+        return st;
+      }
+    }
+    s->seg.assign(std::max(0, k - 1), nullptr);
+    for (int i = 0; i < k - 1; ++i) {
+      mpm_status st = dalloc(&s->seg[i], S / sizeof(float4), s->roll_allocs);
+      if (st != MPM_OK) {
+        free_rollout(s);
+        return st;
+      }
+    }
+  }
+  // records: [0] state->state, [1 + 2j] state->ckpt[j], [2 + 2j] ckpt[j]->state, then (k = 1)
+  // ckpt[n] -> ckpt[n+1]; every stored state is written by the step that produces it.
+  std::vector<ScenePar> recs;
+  recs.push_back(rec_fwd(s, s->state, s->state));
+  for (int j = 0; j < nseg; ++j) {
+    recs.push_back(rec_fwd(s, s->state, s->ckpt[j]));
+    recs.push_back(rec_fwd(s, s->ckpt[j], s->state));
+  }
+  std::vector<int> map(T);
+  for (int n = 0; n < T; ++n) {
+    const bool from_ck = (n % k) == 0;
+    const bool to_ck = ((n + 1) % k) == 0 && (n + 1) / k < nseg;
+    if (from_ck && to_ck) {
+      map[n] = int(recs.size());
+      recs.push_back(rec_fwd(s, s->ckpt[n / k], s->ckpt[(n + 1) / k]));
+    } else if (from_ck) {
+      map[n] = 2 + 2 * (n / k);
+    } else if (to_ck) {
+      map[n] = 1 + 2 * ((n + 1) / k);
+    } else {
+      map[n] = 0;
+    }
+  }
+  CKS(upload_table(s, 1, recs));
+  if (s->hsel[PH_ROLL].table != s->tables[1].dev) {
+    s->hsel[PH_ROLL].table = s->tables[1].dev;
+    CKS(upload_sel(s));
+  }
+  CKS(upload_map(s, 0, map, s->step));
+  CK(cudaMemcpyAsync(s->ckpt[0], s->state, S, cudaMemcpyDeviceToDevice, s->ctx->stream));
+  CKS(set_counter(s, s->d_step, s->step));
+  s->roll_T = T;
+  s->roll_k = k;
+  s->roll_nseg = nseg;
+  s->roll_start = s->step;
+  return MPM_OK;
 }
 
-}  // namespace
+// Reverse-pass set-up: adjoint of the final state from the seeds, controller adjoint zeroed, the
+// record table of every segment's recompute and reverse steps, their maps, the reverse counter.
+mpm_status prepare_backward(mpm_scene* s, const float* gxT, const float* gvT, const float* gCT, const float* gFT,
+                            int mem_space) {
+  cudaStream_t st = s->ctx->stream;
+  const int dim = s->dim, N = s->N, T = s->roll_T, k = s->roll_k, nseg = s->roll_nseg, n0 = s->roll_start;
+  const size_t xb = sizeof(float) * size_t(N) * dim, mb = xb * dim;
+  CKS(ensure_scratch(s, 2 * xb + 2 * mb + 256));
+  const void *a, *bv, *c, *f;
+  CKS(stage(s, gxT, xb, mem_space, 0, &a));
+  CKS(stage(s, gvT, xb, mem_space, xb, &bv));
+  CKS(stage(s, gCT, mb, mem_space, 2 * xb, &c));
+  CKS(stage(s, gFT, mb, mem_space, 2 * xb + mb, &f));
+  // adjoint of the final state; a missing F seed is 0 (the packer's default is the identity)
+  char* sc = reinterpret_cast<char*>(s->scratch);
+  if (!f && N > 0) {
+    CK(cudaMemsetAsync(sc + 2 * xb + mb, 0, mb, st));
+    f = sc + 2 * xb + mb;
+  }
+  if (!a && N > 0) {
+    CK(cudaMemsetAsync(sc, 0, xb, st));
+    a = sc;
+  }
+  CK(launch_pack(dim, N, s->npad, (const float*)a, (const float*)bv, (const float*)c, (const float*)f, s->adj[0],
+                 s->d_status, st));
+  CK(cudaMemsetAsync(s->ctrl.gparams, 0, sizeof(float) * std::max(1, s->nparams), st));
+  // table 2: per segment the recompute records F_{sg,j} (state j -> j+1) and the reverse records
+  // B_{sg,n,parity} (state n, adjoint buffers by parity); maps by global step
+  std::vector<ScenePar> recs;
+  std::vector<int> rcm(T, 0), rev(T, 0);
+  for (int sg = 0; sg < nseg; ++sg) {
+    const int L = std::min(k, T - sg * k);
+    auto segp = [&](int j) { return j == 0 ? s->ckpt[sg] : s->seg[j - 1]; };
+    for (int j = 0; j + 1 < L; ++j) {
+      rcm[sg * k + j] = int(recs.size());
+      recs.push_back(rec_fwd(s, segp(j), segp(j + 1)));
+    }
+    for (int n = 0; n < L; ++n) {
+      const int gstep = sg * k + n;
+      const int parity = (T - 1 - gstep) & 1;  // reverse step T-1 reads adj[0]
+      rev[gstep] = int(recs.size()) + parity;
+      recs.push_back(rec_rev(s, segp(n), s->adj[0], s->adj[1]));
+      recs.push_back(rec_rev(s, segp(n), s->adj[1], s->adj[0]));
+    }
+  }
+  CKS(upload_table(s, 2, recs));
+  bool sel_dirty = false;
+  for (int ph : {PH_RCM, PH_REV, PH_PREP})
+    if (s->hsel[ph].table != s->tables[2].dev) {
+      s->hsel[ph].table = s->tables[2].dev;
+      sel_dirty = true;
+    }
+  if (sel_dirty) CKS(upload_sel(s));
+  CKS(upload_map(s, 1, rcm, n0));
+  CKS(upload_map(s, 2, rev, n0));
+  CKS(set_counter(s, s->d_bstep, n0 + T - 1));
+  s->have_grad = false;
+  return MPM_OK;
+}
+
+// dL/dx_T = e_0 / N: the seed of the loss "mean final x_0" used by batched gradient requests.
+mpm_status seed_mean_x0(mpm_scene* s) {
+  const int N = s->N, dim = s->dim;
+  std::vector<float> h(size_t(N) * dim, 0.0f);
+  for (int p = 0; p < N; ++p) h[size_t(p) * dim] = 1.0f / float(N);
+  return prepare_backward(s, N > 0 ? h.data() : nullptr, nullptr, nullptr, nullptr, 0);
+}
+
+// Reads the result of the finished reverse pass (adjoint of the rollout's first state and of the
+// controller parameters) and restores the bin keys and forward counter of the current state.
+mpm_status finish_backward(mpm_scene* s, float* gx0, float* gv0, float* gC0, float* gF0, float* gctrl,
+                           int mem_space) {
+  cudaStream_t st = s->ctx->stream;
+  const int dim = s->dim, N = s->N;
+  const size_t xb = sizeof(float) * size_t(N) * dim, mb = xb * dim;
+  CKS(ensure_scratch(s, 2 * xb + 2 * mb + 256));
+  char* sc = reinterpret_cast<char*>(s->scratch);
+  const float4* res = s->adj[s->roll_T & 1];
+  if (mem_space == 1) {
+    CK(launch_unpack(dim, N, s->npad, res, gx0, gv0, gC0, gF0, st));
+    if (gctrl && s->nparams > 0)
+      CK(cudaMemcpyAsync(gctrl, s->ctrl.gparams, sizeof(float) * s->nparams, cudaMemcpyDeviceToDevice, st));
+  } else {
+    float* dx_ = (float*)sc;
+    float* dv_ = (float*)(sc + xb);
+    float* dC_ = (float*)(sc + 2 * xb);
+    float* dF_ = (float*)(sc + 2 * xb + mb);
+    CK(launch_unpack(dim, N, s->npad, res, dx_, dv_, dC_, dF_, st));
+    if (gx0 && xb) CK(cudaMemcpyAsync(gx0, dx_, xb, cudaMemcpyDeviceToHost, st));
+    if (gv0 && xb) CK(cudaMemcpyAsync(gv0, dv_, xb, cudaMemcpyDeviceToHost, st));
+    if (gC0 && mb) CK(cudaMemcpyAsync(gC0, dC_, mb, cudaMemcpyDeviceToHost, st));
+    if (gF0 && mb) CK(cudaMemcpyAsync(gF0, dF_, mb, cudaMemcpyDeviceToHost, st));
+    if (gctrl && s->nparams > 0)
+      CK(cudaMemcpyAsync(gctrl, s->ctrl.gparams, sizeof(float) * s->nparams, cudaMemcpyDeviceToHost, st));
+  }
+  s->have_grad = true;
+  // the bin keys now describe state 0 of the rollout: restore those of the current state and the
+  // forward counter
+  CKS(set_counter(s, s->d_step, s->step));
+  CKS(enqueue_keys(s, PH_STEP, st));
+  return read_status(s);
+}
+
+}  // namespace gbmpm
 
 extern "C" {
 
@@ -763,69 +880,8 @@ mpm_status mpm_step(mpm_scene* s, int n_steps) {
 
 mpm_status mpm_rollout(mpm_scene* s, int T, int k, size_t budget) {
   if (!s || T < 1 || k < 0) return MPM_ERR_ARG;
-  s->have_rollout = false;
-  const size_t S = s->state_bytes;
-  if (k == 0) k = (budget == 0 || size_t(T) * S <= budget) ? 1 : int(std::ceil(std::sqrt(double(T))));
-  k = std::min(k, T);
-  const int nseg = (T + k - 1) / k;
-  const size_t need = (size_t(nseg) + size_t(k - 1)) * S;
-  if (budget != 0 && need > budget) return MPM_ERR_OOM;
-  if (int(s->ckpt.size()) != nseg || int(s->seg.size()) != k - 1) {
-    free_rollout(s);  // buffers of another shape
-    s->ckpt.assign(nseg, nullptr);
-    for (int i = 0; i < nseg; ++i) {
-      mpm_status st = dalloc(&s->ckpt[i], S / sizeof(float4), s->roll_allocs);
-      if (st != MPM_OK) {
-        free_rollout(s);
-        return st;
-      }
-    }
-    s->seg.assign(std::max(0, k - 1), nullptr);
-    for (int i = 0; i < k - 1; ++i) {
-      mpm_status st = dalloc(&s->seg[i], S / sizeof(float4), s->roll_allocs);
-      if (st != MPM_OK) {
-        free_rollout(s);
-        return st;
-      }
-    }
-  }
-  // records: [0] state->state, [1 + 2j] state->ckpt[j], [2 + 2j] ckpt[j]->state, then (k = 1)
-  // ckpt[n] -> ckpt[n+1]; every stored state is written by the step that produces it.
-  std::vector<ScenePar> recs;
-  recs.push_back(rec_fwd(s, s->state, s->state));
-  for (int j = 0; j < nseg; ++j) {
-    recs.push_back(rec_fwd(s, s->state, s->ckpt[j]));
-    recs.push_back(rec_fwd(s, s->ckpt[j], s->state));
-  }
-  std::vector<int> map(T);
-  for (int n = 0; n < T; ++n) {
-    const bool from_ck = (n % k) == 0;
-    const bool to_ck = ((n + 1) % k) == 0 && (n + 1) / k < nseg;
-    if (from_ck && to_ck) {
-      map[n] = int(recs.size());
-      recs.push_back(rec_fwd(s, s->ckpt[n / k], s->ckpt[(n + 1) / k]));
-    } else if (from_ck) {
-      map[n] = 2 + 2 * (n / k);
-    } else if (to_ck) {
-      map[n] = 1 + 2 * ((n + 1) / k);
-    } else {
-      map[n] = 0;
-    }
-  }
-  CKS(upload_table(s, 1, recs));
-  if (s->hsel[PH_ROLL].table != s->tables[1].dev) {
-    s->hsel[PH_ROLL].table = s->tables[1].dev;
-    CKS(upload_sel(s));
-  }
-  CKS(upload_map(s, 0, map, s->step));
-  cudaStream_t st = s->ctx->stream;
-  CK(cudaMemcpyAsync(s->ckpt[0], s->state, S, cudaMemcpyDeviceToDevice, st));
-  CKS(set_counter(s, s->d_step, s->step));
+  CKS(prepare_rollout(s, T, k, budget));
   CKS(run_phase(s, PH_ROLL, T));
-  s->roll_T = T;
-  s->roll_k = k;
-  s->roll_nseg = nseg;
-  s->roll_start = s->step;
   s->step += T;
   s->have_rollout = true;
   CK(cudaGetLastError());
@@ -836,58 +892,8 @@ mpm_status mpm_backward(mpm_scene* s, const float* gxT, const float* gvT, const 
                         float* gx0, float* gv0, float* gC0, float* gF0, float* gctrl, int mem_space) {
   if (!s || (mem_space != 0 && mem_space != 1)) return MPM_ERR_ARG;
   if (!s->have_rollout) return MPM_ERR_STATE;
-  cudaStream_t st = s->ctx->stream;
-  const int dim = s->dim, N = s->N, T = s->roll_T, k = s->roll_k, nseg = s->roll_nseg, n0 = s->roll_start;
-  const size_t xb = sizeof(float) * size_t(N) * dim, mb = xb * dim;
-  CKS(ensure_scratch(s, 2 * xb + 2 * mb + 256));
-  const void *a, *bv, *c, *f;
-  CKS(stage(s, gxT, xb, mem_space, 0, &a));
-  CKS(stage(s, gvT, xb, mem_space, xb, &bv));
-  CKS(stage(s, gCT, mb, mem_space, 2 * xb, &c));
-  CKS(stage(s, gFT, mb, mem_space, 2 * xb + mb, &f));
-  // adjoint of the final state; a missing F seed is 0 (the packer's default is the identity)
-  char* sc = reinterpret_cast<char*>(s->scratch);
-  if (!f && N > 0) {
-    CK(cudaMemsetAsync(sc + 2 * xb + mb, 0, mb, st));
-    f = sc + 2 * xb + mb;
-  }
-  if (!a && N > 0) {
-    CK(cudaMemsetAsync(sc, 0, xb, st));
-    a = sc;
-  }
-  CK(launch_pack(dim, N, s->npad, (const float*)a, (const float*)bv, (const float*)c, (const float*)f, s->adj[0],
-                 s->d_status, st));
-  CK(cudaMemsetAsync(s->ctrl.gparams, 0, sizeof(float) * std::max(1, s->nparams), st));
-  // table 2: per segment the recompute records F_{sg,j} (state j -> j+1) and the reverse records
-  // B_{sg,n,parity} (state n, adjoint buffers by parity); maps by global step
-  std::vector<ScenePar> recs;
-  std::vector<int> rcm(T, 0), rev(T, 0);
-  for (int sg = 0; sg < nseg; ++sg) {
-    const int L = std::min(k, T - sg * k);
-    auto segp = [&](int j) { return j == 0 ? s->ckpt[sg] : s->seg[j - 1]; };
-    for (int j = 0; j + 1 < L; ++j) {
-      rcm[sg * k + j] = int(recs.size());
-      recs.push_back(rec_fwd(s, segp(j), segp(j + 1)));
-    }
-    for (int n = 0; n < L; ++n) {
-      const int gstep = sg * k + n;
-      const int parity = (T - 1 - gstep) & 1;  // reverse step T-1 reads adj[0]
-      rev[gstep] = int(recs.size()) + parity;
-      recs.push_back(rec_rev(s, segp(n), s->adj[0], s->adj[1]));
-      recs.push_back(rec_rev(s, segp(n), s->adj[1], s->adj[0]));
-    }
-  }
-  CKS(upload_table(s, 2, recs));
-  bool sel_dirty = false;
-  for (int ph : {PH_RCM, PH_REV, PH_PREP})
-    if (s->hsel[ph].table != s->tables[2].dev) {
-      s->hsel[ph].table = s->tables[2].dev;
-      sel_dirty = true;
-    }
-  if (sel_dirty) CKS(upload_sel(s));
-  CKS(upload_map(s, 1, rcm, n0));
-  CKS(upload_map(s, 2, rev, n0));
-  CKS(set_counter(s, s->d_bstep, n0 + T - 1));
+  CKS(prepare_backward(s, gxT, gvT, gCT, gFT, mem_space));
+  const int T = s->roll_T, k = s->roll_k, nseg = s->roll_nseg, n0 = s->roll_start;
   for (int sg = nseg - 1; sg >= 0; --sg) {
     const int L = std::min(k, T - sg * k);
     if (L > 1) {
@@ -897,30 +903,14 @@ mpm_status mpm_backward(mpm_scene* s, const float* gxT, const float* gvT, const 
     }
     CKS(run_phase(s, PH_REV, L));
   }
-  // outputs
-  const float4* res = s->adj[T & 1];
-  if (mem_space == 1) {
-    CK(launch_unpack(dim, N, s->npad, res, gx0, gv0, gC0, gF0, st));
-    if (gctrl && s->nparams > 0)
-      CK(cudaMemcpyAsync(gctrl, s->ctrl.gparams, sizeof(float) * s->nparams, cudaMemcpyDeviceToDevice, st));
-  } else {
-    float* dx_ = (float*)sc;
-    float* dv_ = (float*)(sc + xb);
-    float* dC_ = (float*)(sc + 2 * xb);
-    float* dF_ = (float*)(sc + 2 * xb + mb);
-    CK(launch_unpack(dim, N, s->npad, res, dx_, dv_, dC_, dF_, st));
-    if (gx0 && xb) CK(cudaMemcpyAsync(gx0, dx_, xb, cudaMemcpyDeviceToHost, st));
-    if (gv0 && xb) CK(cudaMemcpyAsync(gv0, dv_, xb, cudaMemcpyDeviceToHost, st));
-    if (gC0 && mb) CK(cudaMemcpyAsync(gC0, dC_, mb, cudaMemcpyDeviceToHost, st));
-    if (gF0 && mb) CK(cudaMemcpyAsync(gF0, dF_, mb, cudaMemcpyDeviceToHost, st));
-    if (gctrl && s->nparams > 0)
-      CK(cudaMemcpyAsync(gctrl, s->ctrl.gparams, sizeof(float) * s->nparams, cudaMemcpyDeviceToHost, st));
-  }
-  // the bin keys now describe state 0 of the rollout: restore those of the current state and the
-  // forward counter
-  CKS(set_counter(s, s->d_step, s->step));
-  CKS(enqueue_keys(s, PH_STEP, st));
-  return read_status(s);
+  return finish_backward(s, gx0, gv0, gC0, gF0, gctrl, mem_space);
+}
+
+mpm_status mpm_get_gradients(mpm_scene* s, float* gx0, float* gv0, float* gC0, float* gF0, float* gctrl,
+                             int mem_space) {
+  if (!s || (mem_space != 0 && mem_space != 1)) return MPM_ERR_ARG;
+  if (!s->have_grad) return MPM_ERR_STATE;
+  return finish_backward(s, gx0, gv0, gC0, gF0, gctrl, mem_space);
 }
 
 mpm_status mpm_get_state(mpm_scene* s, int step, float* x, float* v, float* C, float* F, int mem_space) {

@@ -156,8 +156,7 @@ __global__ void __launch_bounds__(1024) k_ctrl_forward(const ScenePar* __restric
 // ----------------------------------------------------------------------------- backward
 // dL/da_g = sum over the group of the (K) contributions; accumulate dL/dparams for step n;
 // for the MLP also dL/dz, turned into per-group coefficients for the x adjoint.
-__global__ void __launch_bounds__(1024) k_ctrl_backward(const ScenePar* __restrict__ dsp, CtrlPar c) {
-  const ScenePar& sp = *dsp;
+__device__ void ctrl_backward_body(const ScenePar& sp, const CtrlPar& c) {
   __shared__ float red[MAX_GROUPS * 3 + 3];
   __shared__ float ga[MAX_GROUPS], z[MAX_GROUPS * 3], h1[MAX_HIDDEN], h2[MAX_HIDDEN], o3[MAX_GROUPS];
   __shared__ float gu3[MAX_GROUPS], gu2[MAX_HIDDEN], gu1[MAX_HIDDEN];
@@ -278,6 +277,16 @@ __global__ void __launch_bounds__(1024) k_ctrl_backward(const ScenePar* __restri
   if (tid == 0) *step_ctr = n - 1;
 }
 
+__global__ void __launch_bounds__(1024) k_ctrl_backward(const ScenePar* __restrict__ dsp, CtrlPar c) {
+  ctrl_backward_body(*dsp, c);
+}
+
+// One block per scene of a batch: scene i uses cur[i] and cs[i].
+__global__ void __launch_bounds__(1024) k_ctrl_backward_multi(const ScenePar* __restrict__ cur,
+                                                              const CtrlPar* __restrict__ cs) {
+  ctrl_backward_body(cur[blockIdx.x], cs[blockIdx.x]);
+}
+
 // x adjoint of the MLP input: z_g = c_g - c_body, c_g = mean of x over g, c_body = mean over all.
 template <int D>
 __global__ void k_ctrl_scatter_x(const ScenePar* __restrict__ dsp, CtrlPar c) {
@@ -318,6 +327,25 @@ cudaError_t ctrl_step_forward(const ScenePar& sp, const ScenePar* dsp, const Ctr
   }
   k_ctrl_forward<<<1, 1024, 0, s>>>(dsp, c, c.partials, rows);
   count_launches(rows > 0 ? 2 : 1);
+  return cudaGetLastError();
+}
+
+// Reverse of the controllers of n scenes (records cur[i], controllers cs[i], both on the device);
+// the MLP scenes' centroid adjoint is added to their dL/dx separately (ctrl_scatter_x).
+cudaError_t ctrl_backward_batched(const ScenePar* cur, const CtrlPar* cs, int n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_ctrl_backward_multi<<<n, 1024, 0, s>>>(cur, cs);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t ctrl_scatter_x(const ScenePar& sp, const ScenePar* dsp, const CtrlPar& c, cudaStream_t s) {
+  if (c.type != 2 || c.G == 0 || sp.N == 0) return cudaSuccess;
+  if (sp.dim == 2)
+    k_ctrl_scatter_x<2><<<(sp.N + 255) / 256, 256, 0, s>>>(dsp, c);
+  else
+    k_ctrl_scatter_x<3><<<(sp.N + 255) / 256, 256, 0, s>>>(dsp, c);
+  count_launches(1);
   return cudaGetLastError();
 }
 

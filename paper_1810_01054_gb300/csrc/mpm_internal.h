@@ -140,6 +140,9 @@ constexpr int RED_ROW_FLOATS = MAX_GROUPS * 3 + 3;  // floats per partial row
 // the step *sp.step_ctr, which it then decrements.
 cudaError_t ctrl_step_forward(const ScenePar& sp, const ScenePar* dsp, const CtrlPar& c, cudaStream_t s);
 cudaError_t ctrl_step_backward(const ScenePar& sp, const ScenePar* dsp, const CtrlPar& c, cudaStream_t s);
+// Batched form: one block per scene; records and controllers are device arrays of n entries.
+cudaError_t ctrl_backward_batched(const ScenePar* cur, const CtrlPar* cs, int n, cudaStream_t s);
+cudaError_t ctrl_scatter_x(const ScenePar& sp, const ScenePar* dsp, const CtrlPar& c, cudaStream_t s);
 
 // Copies every scene's record for the current step into cur[] (one block per scene).
 cudaError_t launch_select(const SelectPar* sel, int n_scenes, ScenePar* cur, cudaStream_t s);

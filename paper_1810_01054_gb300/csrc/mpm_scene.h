@@ -1,0 +1,94 @@
+// Internal definitions of the C ABI objects (contexts, scenes) shared by the API and the batch
+// scheduler translation units.
+#pragma once
+
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "../../include/mpm.h"
+#include "mpm_internal.h"
+
+namespace gbmpm {
+constexpr int GRAPH_STEPS = 8;  // steps per replayed graph
+enum Phase { PH_STEP = 0, PH_ROLL = 1, PH_RCM = 2, PH_REV = 3, PH_PREP = 4, PH_COUNT = 5 };
+}  // namespace gbmpm
+
+using gbmpm::BatchDev;
+using gbmpm::CtrlPar;
+using gbmpm::ScenePar;
+using gbmpm::SelectPar;
+
+struct mpm_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaStream_t capture = nullptr;  // private stream graphs are captured on
+  int sm_count = 1;
+  // launch timing (mpm_profile_*): event pairs around launches of the selected kinds; while a
+  // mask is set, steps are launched directly (not from graphs) so every launch can be bracketed
+  unsigned prof_mask = 0;
+  std::vector<cudaEvent_t> prof_ev;
+  std::vector<int> prof_kind;
+  int prof_used = 0;
+};
+
+struct Graph {
+  cudaGraphExec_t exec = nullptr;
+  long long kernels = 0;
+};
+
+struct mpm_scene {
+  mpm_ctx* ctx = nullptr;
+  int dim = 0, N = 0, npad = 0, G = 0, nparams = 0, impl = 0, n_nodes = 0;
+  size_t state_bytes = 0;
+  ScenePar hp{};             // host template of the scene record
+  CtrlPar ctrl{};
+  BatchDev b{};              // private batch of one scene; b.scenes = cur
+  std::vector<void*> allocs; // everything allocated at creation
+  float4* state = nullptr;   // current state planes
+  float4* adj[2] = {nullptr, nullptr};
+  int* d_step = nullptr;     // forward step counter (controller time)
+  int* d_bstep = nullptr;    // reverse step counter
+  int* d_status = nullptr;
+  ScenePar* cur = nullptr;   // device: the record of the running step
+  SelectPar* dsel = nullptr; // device: one selection per phase
+  SelectPar hsel[gbmpm::PH_COUNT]{};
+  int step = 0;              // host mirror of the current step
+  // device record tables, one per phase family (uploaded only when their content changes)
+  struct Table {
+    ScenePar* dev = nullptr;
+    int cap = 0;
+    std::vector<ScenePar> host;
+  } tables[3];               // 0 = in-place step, 1 = rollout, 2 = recompute + reverse
+  struct Map {
+    int* dev = nullptr;
+    int cap = 0;
+    std::vector<int> host;
+  } maps[3];                 // record index per step: rollout, recompute, reverse
+  Graph graphs[gbmpm::PH_COUNT][2]; // [phase][single step, GRAPH_STEPS steps]
+  // rollout record
+  bool have_rollout = false;
+  bool have_grad = false;    // adjoint buffers hold a finished reverse pass
+  int roll_T = 0, roll_k = 0, roll_start = 0, roll_nseg = 0;
+  std::vector<float4*> ckpt;
+  std::vector<float4*> seg;  // k - 1 recompute buffers
+  std::vector<void*> roll_allocs;
+  // staging scratch
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+};
+
+
+namespace gbmpm {
+// Helpers the batch scheduler shares with the single-scene entry points (mpm_api.cu).
+mpm_status prepare_rollout(mpm_scene* s, int T, int k, size_t budget);
+mpm_status prepare_backward(mpm_scene* s, const float* gxT, const float* gvT, const float* gCT, const float* gFT,
+                            int mem_space);
+mpm_status seed_mean_x0(mpm_scene* s);
+mpm_status finish_backward(mpm_scene* s, float* gx0, float* gv0, float* gC0, float* gF0, float* gctrl,
+                           int mem_space);
+mpm_status set_counter(mpm_scene* s, int* dctr, int value);
+mpm_status read_status(mpm_scene* s);
+mpm_status scene_sync_status(mpm_scene* s);
+}  // namespace gbmpm

@@ -111,6 +111,7 @@ _SIGS = {
     "mpm_rollout": [C.c_void_p, C.c_int, C.c_int, C.c_size_t],
     "mpm_backward": [C.c_void_p] + [C.c_void_p] * 9 + [C.c_int],
     "mpm_get_state": [C.c_void_p, C.c_int] + [C.c_void_p] * 4 + [C.c_int],
+    "mpm_get_gradients": [C.c_void_p] + [C.c_void_p] * 5 + [C.c_int],
     "mpm_set_state": [C.c_void_p] + [C.c_void_p] * 4 + [C.c_int, C.c_int],
     "mpm_set_ctrl_params": [C.c_void_p, C.c_void_p, C.c_int, C.c_int],
     "mpm_get_grid": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int],
@@ -364,9 +365,65 @@ class Scene:
                                   _ptr(gp), 0), "mpm_backward")
         return gx0, gv0, gC0, gF0, gp[: self.n_params]
 
+    def gradients(self, out=None):
+        """Result of the last finished reverse pass (mpm_backward or a batched gradient request):
+        (gx0, gv0, gC0, gF0, g_params) as numpy arrays, or filled into ``out`` (torch tensors)."""
+        N, d = self.N, self.dim
+        if out is not None:
+            on_dev = bool(out[0].is_cuda)
+            _check(lib().mpm_get_gradients(self.handle, *[_ptr(a) for a in out], 1 if on_dev else 0),
+                   "mpm_get_gradients")
+            return out
+        gx0, gv0 = np.empty((N, d), np.float32), np.empty((N, d), np.float32)
+        gC0, gF0 = np.empty((N, d, d), np.float32), np.empty((N, d, d), np.float32)
+        gp = np.empty(max(self.n_params, 1), np.float32)
+        _check(lib().mpm_get_gradients(self.handle, _ptr(gx0), _ptr(gv0), _ptr(gC0), _ptr(gF0), _ptr(gp), 0),
+               "mpm_get_gradients")
+        return gx0, gv0, gC0, gF0, gp[: self.n_params]
+
     def close(self):
         if getattr(self, "handle", None):
             lib().mpm_scene_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Scenes of one dimension advanced together by the same launches (mpm_batch_*).  A request is
+    a rollout of n_steps and, with want_grad, its reverse pass seeded by loss = mean final x_0;
+    results stay in the scene (Scene.get_state, Scene.gradients)."""
+
+    def __init__(self, ctx: Context, dim: int, mem_budget: int = 0):
+        h = C.c_void_p()
+        _check(lib().mpm_batch_create(ctx.handle, int(dim), C.c_size_t(int(mem_budget)), C.byref(h)),
+               "mpm_batch_create")
+        self.handle, self.ctx, self.dim = h, ctx, dim
+
+    def admit(self, scene: "Scene", n_steps: int, want_grad: bool) -> int:
+        slot = C.c_int(-1)
+        _check(lib().mpm_batch_admit(self.handle, scene.handle, int(n_steps), int(bool(want_grad)), C.byref(slot)),
+               "mpm_batch_admit")
+        return slot.value
+
+    def tick(self, max_steps: int = 1):
+        _check(lib().mpm_batch_tick(self.handle, int(max_steps)), "mpm_batch_tick")
+
+    def poll(self, slot: int) -> bool:
+        done = C.c_int(0)
+        _check(lib().mpm_batch_poll(self.handle, int(slot), C.byref(done)), "mpm_batch_poll")
+        return bool(done.value)
+
+    def release(self, slot: int):
+        _check(lib().mpm_batch_release(self.handle, int(slot)), "mpm_batch_release")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().mpm_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -1,0 +1,165 @@
+"""Batched launches, the serving loop and the rollout autograd.Function (GPU).
+
+A scene's results must be the same bits alone and inside any batch mix (tiles never span scenes
+and every sum has a fixed order); requests served with continuous batching must return exactly
+what they return alone; torch autograd through the rollout Function must equal the library's own
+reverse pass and the FP64 oracle's gradient within the stated tolerance.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1810_01054_gb300 import scenes as S
+from tests.parity_utils import assert_grad_close, mean_x0_seed
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    from paper_1810_01054_gb300 import mpm
+    mpm.lib()
+    return mpm
+
+
+@pytest.fixture(scope="module")
+def ctx(M):
+    c = M.Context(0)
+    yield c
+    c.close()
+
+
+def _k_of(T):
+    return 1 if T <= 16 else int(math.ceil(math.sqrt(T)))
+
+
+def _alone(M, ctx, spec, T, want_grad):
+    sc = M.Scene(ctx, spec)
+    sc.rollout(T, _k_of(T))
+    st = sc.get_state()
+    g = sc.backward(mean_x0_seed(sc.N, sc.dim)) if want_grad else None
+    sc.close()
+    return st, g
+
+
+def _mix_2d():
+    return [
+        (S.blob(2, 32, 300, 1, v_scale=0.3, radius_cells=5.0, center=(0.5, 7.0 / 32), bc_width=3, amp=2.0), 23, True),
+        (S.walker_square_2d(0), 40, True),
+        (S.blob(2, 48, 500, 2, ctrl_type=S.CTRL_BASIS, n_groups=4, freq=4.0, radius_cells=6.0, v_scale=0.2), 17, False),
+        (S.blob(2, 24, 64, 3, bc_type=S.BC_SLIP, friction_c=0.3, radius_cells=3.0, center=(0.4, 4.5 / 24)), 30, True),
+    ]
+
+
+def _mix_3d():
+    return [
+        (S.blob(3, 16, 400, 4, radius_cells=3.5, v_scale=0.3, amp=2.0), 12, True),
+        (S.blob(3, 24, 900, 5, radius_cells=4.0, v_scale=0.3, ctrl_type=S.CTRL_MLP, n_groups=4, hidden=8,
+                scale=3.0), 20, True),
+        (S.blob(3, 20, 250, 6, radius_cells=3.0, v_scale=0.3), 9, False),
+    ]
+
+
+@pytest.mark.parametrize("mix", [_mix_2d, _mix_3d], ids=["2d", "3d"])
+def test_batch_results_equal_alone_bitwise(M, ctx, mix):
+    reqs = mix()
+    alone = [_alone(M, ctx, spec, T, g) for spec, T, g in reqs]
+    batch = M.Batch(ctx, reqs[0][0].dim)
+    scenes, slots = [], []
+    for spec, T, g in reqs:
+        sc = M.Scene(ctx, spec)
+        scenes.append(sc)
+        slots.append(batch.admit(sc, T, g))
+    assert all(s >= 0 for s in slots)
+    for _ in range(10000):
+        batch.tick(4)
+        if all(batch.poll(s) for s in slots):
+            break
+    assert all(batch.poll(s) for s in slots)
+    for (spec, T, g), sc, (st, grads) in zip(reqs, scenes, alone):
+        got = sc.get_state()
+        for a, b in zip(got, st):
+            assert np.array_equal(a, b)
+        if g:
+            gg = sc.gradients()
+            for a, b in zip(gg, grads):
+                assert np.array_equal(a, b)
+    for s in slots:
+        batch.release(s)
+    batch.close()
+
+
+def test_serving_mix_equals_alone_and_reports_latency(M, ctx):
+    from paper_1810_01054_gb300.serve import Server
+    reqs = [(spec, T, g) for spec, T, g in _mix_2d()[:3]] + [(spec, T, g) for spec, T, g in _mix_3d()[:2]]
+    alone = [_alone(M, ctx, spec, T, g) for spec, T, g in reqs]
+    srv = Server(device=0, mem_fraction=0.2, tick_steps=3)
+    ids = []
+    for i, (spec, T, g) in enumerate(reqs):
+        ids.append(srv.submit(spec, g, n_steps=T, arrival=0.002 * i))  # staggered arrivals
+    srv.run()
+    for rid, (spec, T, g), (st, grads) in zip(ids, reqs, alone):
+        r = srv.results[rid]
+        for a, b in zip((r["x"], r["v"], r["C"], r["F"]), st):
+            assert np.array_equal(a, b)
+        if g:
+            for a, b in zip(r["grads"], grads):
+                assert np.array_equal(a, b)
+    p50, p99 = srv.latency_percentiles()
+    assert 0 < p50 <= p99
+    srv.close()
+
+
+def test_admission_waits_for_memory(M, ctx):
+    """A batch whose budget holds one request admits the second only after the first leaves."""
+    spec = S.blob(2, 32, 200, 9, radius_cells=4.0)
+    a, b = M.Scene(ctx, spec), M.Scene(ctx, spec)
+    info = a.info()
+    T = 25
+    k = _k_of(T)
+    need = ((T + k - 1) // k + k - 1) * info["state_bytes"]
+    batch = M.Batch(ctx, 2, mem_budget=need + need // 2)
+    s0 = batch.admit(a, T, True)
+    assert s0 >= 0
+    assert batch.admit(b, T, True) == -1
+    while not batch.poll(s0):
+        batch.tick(8)
+    batch.release(s0)
+    s1 = batch.admit(b, T, True)
+    assert s1 >= 0
+    while not batch.poll(s1):
+        batch.tick(8)
+    for x, y in zip(a.gradients(), b.gradients()):
+        assert np.array_equal(x, y)
+    batch.close()
+
+
+def test_autograd_function_matches_library_and_oracle(M, ctx):
+    torch = pytest.importorskip("torch")
+    from paper_1810_01054_gb300.rollout import rollout
+    dev = torch.device("cuda", 0)
+    spec = S.walker_square_2d(0, n_steps=40)
+    T = 40
+    sc = M.Scene(ctx, spec)
+    t = lambda a: torch.tensor(np.asarray(a), dtype=torch.float32, device=dev, requires_grad=True)
+    x0, v0, C0, F0 = t(spec.x0), t(spec.v0), t(spec.C0), t(spec.F0)
+    params = t(spec.ctrl_params)
+    xT, vT, CT, FT = rollout(sc, T, x0, v0, C0, F0, params, ckpt_interval=8)
+    loss = xT[:, 0].mean()
+    loss.backward()
+    torch.cuda.synchronize()
+    # the library's own reverse pass on the same rollout
+    sc2 = M.Scene(ctx, spec)
+    sc2.rollout(T, 8)
+    gx, gv, gC, gF, gp = sc2.backward(mean_x0_seed(sc2.N, 2))
+    assert np.array_equal(v0.grad.cpu().numpy(), gv)
+    assert np.array_equal(params.grad.cpu().numpy(), gp)
+    # and the oracle
+    osc = O.Scene(spec)
+    traj = osc.rollout(T)
+    ogx, ogv, ogC, ogF, ogp = osc.backward(traj, (mean_x0_seed(osc.N, 2), None, None, None))
+    assert_grad_close(v0.grad.cpu().numpy(), ogv, "autograd dL/dv0")
+    assert_grad_close(params.grad.cpu().numpy(), ogp, "autograd dL/dA")
+    assert_grad_close(F0.grad.cpu().numpy(), ogF, "autograd dL/dF0")
