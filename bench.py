@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--ncu", type=int, default=0, metavar="SIM_STEPS",
                     help="profiling mode: one short rollout of SIM_STEPS steps + reverse pass, no timing")
     return ap.parse_args()
@@ -220,22 +222,29 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- multi-rank
+def whole_job_rate(local_ms, units_per_rank, world, device=None):
+    """Whole-job throughput over N independent replicas: the timed span is the maximum over
+    ranks, the units are those of every rank (weak scaling; no collective on the data path)."""
+    import torch
+    t = torch.tensor([float(local_ms)], device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    span_ms = float(t.item())
+    return world * units_per_rank / (span_ms / 1e3), span_ms
+
+
 # ----------------------------------------------------------------------------- our arm
-def run_ours(args, rank, world, local_rank):
+def measure(args, spec, rank, world, dev, stream, ctx, *, e2e=True, plain=True):
+    """Times K whole forward+reverse rollouts of `spec` (graph replays, inputs resident in HBM, L2
+    flushed before every step), then per-kernel durations in a directly-launched repeat, forward-only
+    rollouts, optionally the end-to-end host-buffer path and the plain atomic form."""
     import torch
     from paper_1810_01054_gb300 import mpm
 
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    # a dedicated stream: the library enqueues on it and every event below is recorded on it
-    stream = torch.cuda.Stream(dev)
-    torch.cuda.set_stream(stream)
-    spec = workload(args.workload, rank)
     T, k = spec.n_steps, ckpt_of(spec)
     N, d = spec.n_particles, spec.dim
-    ctx = mpm.Context(local_rank, stream=stream)
     scene = mpm.Scene(ctx, spec)
-    # inputs resident in HBM
     x0 = torch.tensor(spec.x0, dtype=torch.float32, device=dev)
     v0 = torch.tensor(spec.v0, dtype=torch.float32, device=dev)
     C0 = torch.tensor(spec.C0, dtype=torch.float32, device=dev)
@@ -246,25 +255,16 @@ def run_ours(args, rank, world, local_rank):
             torch.empty((N, d, d), device=dev), torch.empty((max(scene.n_params, 1),), device=dev)]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def one_step(backward=True):
-        scene.set_state(x0, v0, C0, F0, step=0)
-        scene.rollout(T, k)
+    def one_step(backward=True, sc=scene):
+        sc.set_state(x0, v0, C0, F0, step=0)
+        sc.rollout(T, k)
         if backward:
-            scene.backward(seed, out=outs)
+            sc.backward(seed, out=outs)
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
-
-    if args.ncu:
-        # short run for profilers: one rollout of --ncu steps (checkpoint interval kept) + reverse pass
-        T = min(T, args.ncu)
-        k = min(k, T) if k else 0
-        one_step()
-        torch.cuda.synchronize(dev)
-        print(json.dumps({"ncu_run": spec.name, "sim_steps": T, "launches": mpm.launch_count()}), flush=True)
-        return
 
     for _ in range(args.warmup):
         one_step()
@@ -273,7 +273,7 @@ def run_ours(args, rank, world, local_rank):
     # -- timed region: K whole fwd+bwd rollouts (graph replays), L2 flushed before each (untimed)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     n_launch0 = mpm.launch_count()
-    with ClockSampler(local_rank) as clk:
+    with ClockSampler(dev.index) as clk:
         barrier()
         for i in range(args.steps):
             flush.zero_()
@@ -283,17 +283,12 @@ def run_ours(args, rank, world, local_rank):
         barrier()
     n_launch = mpm.launch_count() - n_launch0
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    tot_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([tot_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = world * N * T * args.steps / (tot_ms / 1e3)
+    value, tot_ms = whole_job_rate(sum(step_ms), N * T * args.steps, world, dev)
 
     # -- per-kernel durations: CUDA events around every launch of the hot kernels, in a repeat of
     #    the timed steps launched directly (event pairs cannot bracket kernels inside a graph)
     kinds = (("adj_gather", mpm.K_ADJ_GATHER), ("p2g_adj", mpm.K_P2G_ADJ), ("p2g", mpm.K_P2G), ("g2p", mpm.K_G2P),
-             ("grid", mpm.K_GRID), ("grid_adj", mpm.K_GRID_ADJ), ("sort", mpm.K_SORT), ("ctrl", mpm.K_CTRL))
+             ("sort", mpm.K_SORT), ("ctrl", mpm.K_CTRL))
     ctx.profile_start([kk for _, kk in kinds], max_launches=args.steps * 12 * T + 64)
     pa, pb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
@@ -319,8 +314,8 @@ def run_ours(args, rank, world, local_rank):
     value_fwd = world * N * T / (statistics.median(fwd_ms) / 1e3)
 
     # -- e2e through the public API with pinned host buffers (H2D inputs, D2H gradients)
-    e2e = None
-    if not args.no_e2e:
+    e2e_rec = None
+    if e2e:
         hx = torch.tensor(spec.x0, dtype=torch.float32).pin_memory()
         hv = torch.tensor(spec.v0, dtype=torch.float32).pin_memory()
         hC = torch.tensor(spec.C0, dtype=torch.float32).pin_memory()
@@ -337,34 +332,29 @@ def run_ours(args, rank, world, local_rank):
             scene.backward(hseed, out=houts)
         barrier()
         e2e_s = time.perf_counter() - t0
-        e2e = {"value": world * N * T * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h}
+        e2e_rec = {"value": world * N * T * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                   "d2h_bytes_per_step": d2h}
 
-    # -- the plain single-scene form (global atomics, dense grid) on the same workload
-    plain = None
-    if not args.no_plain and rank == 0:
+    # -- the plain single-scene form (global float atomics, dense grid) on the same workload
+    plain_rec = None
+    if plain and rank == 0:
         ps = mpm.Scene(ctx, spec, impl=mpm.IMPL_PLAIN)
         for _ in range(2):
-            ps.set_state(x0, v0, C0, F0, step=0)
-            ps.rollout(T, k)
-            ps.backward(seed, out=outs)
+            one_step(sc=ps)
         torch.cuda.synchronize(dev)
         pm = []
         for _ in range(2):
             flush.zero_()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            ps.set_state(x0, v0, C0, F0, step=0)
-            ps.rollout(T, k)
-            ps.backward(seed, out=outs)
+            one_step(sc=ps)
             b.record(stream)
             torch.cuda.synchronize(dev)
             pm.append(a.elapsed_time(b))
-        plain = {"value": N * T / (min(pm) / 1e3), "unit": UNIT, "form": "plain single-scene (float atomics)"}
+        plain_rec = {"value": N * T / (min(pm) / 1e3), "unit": UNIT, "form": "plain single-scene (float atomics)"}
         ps.close()
+    scene.close()
 
-    if rank != 0:
-        return
     # roofline of the dominant hot kernel (largest summed time in the profiled repeat)
     dom = max(ALGO_BYTES, key=lambda kk: prof[kk][1])
     cnt, ms = prof[dom]
@@ -372,28 +362,99 @@ def run_ours(args, rank, world, local_rank):
     bpp = ALGO_BYTES[dom][0 if d == 2 else 1]
     launch_ms = ms / max(cnt, 1)
     achieved = bpp * N / (launch_ms / 1e3) / 1e9
-    traffic = measured_traffic(dom, spec.name, N)
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": measured_traffic(dom, spec.name, N), "peak_source": src, "algo_bytes_per_particle": bpp,
+            "launches": cnt, "avg_launch_us": 1e3 * launch_ms,
+            "timing": "CUDA events around every launch of the kernel in a directly-launched repeat of the timed steps"}
     share = {kk: round(v[1] / prof_total_ms, 4) for kk, v in prof.items()}
-    clocks = clk.summary()
+    return {"value": value, "tot_ms": tot_ms, "step_ms": step_ms, "value_fwd": value_fwd, "roofline": roof,
+            "share": share, "e2e": e2e_rec, "plain": plain_rec, "gpu_launches": n_launch, "clocks": clk.summary(),
+            "N": N, "T": T, "k": k}
+
+
+def measure_serving(dev, stream, n_requests=32, seed=4):
+    """Serving mix (Poisson stream of rollout/gradient requests, 2D and 3D box clusters): first the
+    saturation rate (all requests queued at once), then Poisson arrivals at 0.75x that rate;
+    latency = arrival -> result on the host."""
+    from paper_1810_01054_gb300 import scenes as S
+    from paper_1810_01054_gb300.serve import Server
+    reqs = [S.serving_request(i, seed) for i in range(n_requests)]
+    work = sum(sp.n_particles * sp.n_steps for sp, _ in reqs)
+
+    def run(arrivals):
+        srv = Server(device=dev.index, mem_fraction=0.3, tick_steps=8, stream=stream, keep_results=False)
+        for (sp, g), t in zip(reqs, arrivals):
+            srv.submit(sp, g, arrival=t)
+        t0 = time.perf_counter()
+        srv.run()
+        span = time.perf_counter() - t0
+        p50, p99 = srv.latency_percentiles()
+        srv.close()
+        return span, p50, p99
+
+    run([0.0] * 4)  # warm-up of the first few requests' code paths
+    span, _, _ = run([0.0] * n_requests)
+    rate = n_requests / span
+    rng = np.random.default_rng(seed)
+    arrivals = np.cumsum(rng.exponential(1.0 / (0.75 * rate), size=n_requests))
+    span2, p50, p99 = run(list(arrivals))
+    return {"requests": n_requests, "saturation_req_per_s": rate, "load": 0.75,
+            "p50_ms": 1e3 * p50, "p99_ms": 1e3 * p99, "aggregate_particle_steps_per_s": work / span2,
+            "mix": "seeded serving requests: dim 2/3 50/50, n in {32..128}, N log-uniform 1e3-2e5, T 50-500, "
+                   "60% with gradient (loss = mean final x_0)"}
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1810_01054_gb300 import mpm
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    # a dedicated stream: the library enqueues on it and every event below is recorded on it
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    ctx = mpm.Context(local_rank, stream=stream)
+    spec = workload(args.workload, rank)
+
+    if args.ncu:
+        # short run for profilers: one rollout of --ncu steps (checkpoint interval kept) + reverse pass
+        T = min(spec.n_steps, args.ncu)
+        sc = mpm.Scene(ctx, spec)
+        sc.rollout(T, min(ckpt_of(spec), T) if ckpt_of(spec) else 0)
+        seed = np.zeros((spec.n_particles, spec.dim), np.float32)
+        seed[:, 0] = 1.0 / spec.n_particles
+        sc.backward(seed)
+        print(json.dumps({"ncu_run": spec.name, "sim_steps": T, "launches": mpm.launch_count()}), flush=True)
+        return
+
+    r = measure(args, spec, rank, world, dev, stream, ctx, e2e=not args.no_e2e, plain=not args.no_plain)
+    large = None
+    if args.workload != "box_cluster_3d" and not args.no_large:
+        lspec = workload("box_cluster_3d", rank)
+        lr = measure(args, lspec, rank, world, dev, stream, ctx, e2e=False, plain=False)
+        large = {"workload": lspec.name, "particles": lr["N"], "sim_steps": lr["T"], "value": lr["value"],
+                 "value_fwd": lr["value_fwd"], "unit": UNIT, "ms_per_step": lr["tot_ms"] / args.steps,
+                 "roofline": lr["roofline"], "kernel_share_of_profiled_step": lr["share"]}
+    serving = None
+    if rank == 0 and not args.no_serve:
+        serving = measure_serving(dev, stream)
+    if rank != 0:
+        return
     cpu = None if args.no_cpu_baseline else cpu_baseline(spec)
-    lat = sorted(step_ms)
+    lat = sorted(r["step_ms"])
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
-        "config": {"workload": spec.name, "particles": N, "grid": "x".join(map(str, spec.n_grid)), "sim_steps": T,
-                   "ckpt_interval": k, "pass": "forward+reverse rollout", "loss": "mean final x_0",
-                   "l2": "flushed before every timed step (256 MB write, untimed)",
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["tot_ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": spec.name, "particles": r["N"], "grid": "x".join(map(str, spec.n_grid)),
+                   "sim_steps": r["T"], "ckpt_interval": r["k"], "pass": "forward+reverse rollout",
+                   "loss": "mean final x_0", "l2": "flushed before every timed step (256 MB write, untimed)",
                    "parallelism": f"replicas x{world}"},
-        "value_fwd": value_fwd,
+        "value_fwd": r["value_fwd"],
         "rollout_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": traffic, "peak_source": src,
-                     "algo_bytes_per_particle": bpp, "launches": cnt, "avg_launch_us": 1e3 * launch_ms,
-                     "timing": "CUDA events around every launch of the kernel in a directly-launched repeat of "
-                               "the timed steps"},
-        "kernel_share_of_profiled_step": share,
-        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch, "clocks": clocks, "plain_form": plain,
+        "roofline": r["roofline"], "kernel_share_of_profiled_step": r["share"],
+        "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": r["gpu_launches"], "clocks": r["clocks"],
+        "plain_form": r["plain"], "large_scene": large, "serving": serving,
     }
     print(json.dumps(line), flush=True)
 

@@ -122,6 +122,16 @@ __device__ __forceinline__ void store_planes(float4* __restrict__ planes, int np
   }
 }
 
+// --------------------------------------------------------------------------- async staging
+// 16-byte global -> shared copies that complete in the background (cp.async, L2 only), so a
+// CTA can request a tile's particle records and do other work while they arrive.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 // --------------------------------------------------------------------------- small matrices
 template <int D>
 __device__ __forceinline__ float det(const float (&F)[D][D]) {

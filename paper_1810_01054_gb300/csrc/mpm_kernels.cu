@@ -869,10 +869,19 @@ __device__ __forceinline__ void g2p_core(Part<D>& q, const float* f, const float
   }
 }
 
+// Particles of a tile staged in shared memory by asynchronous copies (first STAGE of them).
 template <int D>
-__global__ void __launch_bounds__(256) k_g2p(BatchDev b) {
+struct G2PCfg {
+  static constexpr int STAGE = 512;
+  static constexpr int NP = Cfg<D>::XF_PLANES;
+};
+
+template <int D>
+__global__ void __launch_bounds__(256, 3) k_g2p(BatchDev b) {
+  using K = G2PCfg<D>;
   constexpr int B = Cfg<D>::B, NB = Cfg<D>::BLOCK_NODES, BN = Cfg<D>::BN;
   __shared__ float4 sv[NB];
+  __shared__ float4 stage[K::NP][K::STAGE];
   const int tid = threadIdx.x;
   const int n_active = *b.n_active;
   if (blockIdx.x == 0)  // this step's counters move on (every reader of them ran before)
@@ -885,16 +894,31 @@ __global__ void __launch_bounds__(256) k_g2p(BatchDev b) {
     unlin<D>(gt - sp.tile_base, sp.nt, t);
     const uint32_t st = b.tile_start[gt];
     const int cnt = int(b.tile_start[gt + 1] - st);
-    // the first particle's state is requested before the node block is built, so the two overlap
-    float r[Cfg<D>::S];
-    int id = tid < cnt ? int(b.sorted[st + tid]) : 0;
-    if (tid < cnt) load_planes<D, Cfg<D>::XF_PLANES>(sp.planes, sp.npad, id, r);
+    const int staged = cnt < K::STAGE ? cnt : K::STAGE;
+    // request the x, F planes of the tile's particles; they arrive while the node block is built
+    for (int e = tid; e < staged; e += blockDim.x) {
+      const int id = int(b.sorted[st + e]);
+#pragma unroll
+      for (int j = 0; j < K::NP; ++j) cp_async16(&stage[j][e], sp.planes + size_t(j) * sp.npad + id);
+    }
+    cp_async_commit();
     build_node_block<D, false>(b, sp, t, sv, nullptr);
+    cp_async_wait_all();
     __syncthreads();
     for (int e = tid; e < cnt; e += blockDim.x) {
-      if (e != tid) {
-        id = int(b.sorted[st + e]);
-        load_planes<D, Cfg<D>::XF_PLANES>(sp.planes, sp.npad, id, r);
+      const int id = int(b.sorted[st + e]);
+      float r[Cfg<D>::S];
+      if (e < K::STAGE) {
+#pragma unroll
+        for (int j = 0; j < K::NP; ++j) {
+          const float4 q = stage[j][e];
+          r[4 * j] = q.x;
+          r[4 * j + 1] = q.y;
+          r[4 * j + 2] = q.z;
+          r[4 * j + 3] = q.w;
+        }
+      } else {
+        load_planes<D, K::NP>(sp.planes, sp.npad, id, r);
       }
       Part<D> q;
       unpack<D>(r, q);

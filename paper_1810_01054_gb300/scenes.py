@@ -211,7 +211,13 @@ def _box_union(rng, dim, n, dx, s, target_lo, target_hi, *, exact=None, max_trie
         occ = np.zeros((L,) * dim, dtype=bool)
         order = []
         count = 0
+        boxes = 0
         while True:
+            boxes += 1
+            if boxes > 4000:  # the region is saturated: keep what the union holds
+                if exact is not None:
+                    return np.concatenate(order)
+                break
             sides = rng.uniform(side[0], side[1], size=dim)
             lo = np.empty(dim)
             for a in range(dim):
@@ -296,7 +302,10 @@ def serving_request(req_id: int, seed: int = 4) -> tuple:
     rng = np.random.default_rng([seed, req_id])
     dim = int(rng.integers(2, 4))
     n = int(rng.choice([32, 48, 64, 96, 128]))
-    cap = 16 * (n - 10) ** dim // 2
+    # at most half the lattice points of the region the boxes are drawn in
+    s_ = 0.5 / n
+    height = 0.3 if dim == 2 else 0.2
+    cap = int(0.5 * (0.7 / s_) ** (dim - 1) * (height / s_))
     N = int(min(cap, math.exp(rng.uniform(math.log(1e3), math.log(2e5)))))
     N = max(N, 64)
     T = int(rng.integers(50, 501))
