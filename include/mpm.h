@@ -57,6 +57,8 @@ typedef struct mpm_batch mpm_batch;
 /* Creates a context on CUDA device `device`, enqueuing on `cuda_stream` (a cudaStream_t; NULL
  * creates a private non-blocking stream). */
 mpm_status mpm_ctx_create(mpm_ctx** out, int device, void* cuda_stream);
+/* Destroys the context.  Every scene and batch created on it must be destroyed first:
+ * MPM_ERR_STATE (and nothing freed) while any is alive. */
 mpm_status mpm_ctx_destroy(mpm_ctx* ctx);
 /* Waits for the context's stream; returns the first CUDA error seen. */
 mpm_status mpm_sync(mpm_ctx* ctx);

@@ -588,6 +588,7 @@ mpm_status mpm_ctx_create(mpm_ctx** out, int device, void* cuda_stream) {
 
 mpm_status mpm_ctx_destroy(mpm_ctx* c) {
   if (!c) return MPM_ERR_ARG;
+  if (c->live.load() != 0) return MPM_ERR_STATE;  // its scenes and batches still use its stream
   cudaStreamSynchronize(c->stream);
   for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
   cudaStreamDestroy(c->capture);
@@ -616,6 +617,7 @@ mpm_status mpm_scene_destroy(mpm_scene* s) {
   for (auto& m : s->maps)
     if (m.dev) cudaFree(m.dev);
   if (s->scratch) cudaFree(s->scratch);
+  s->ctx->live.fetch_sub(1);
   delete s;
   return MPM_OK;
 }
@@ -650,6 +652,7 @@ mpm_status mpm_scene_create(mpm_ctx* c, const mpm_scene_desc* d, mpm_scene** out
   mpm_scene* s = new (std::nothrow) mpm_scene();
   if (!s) return MPM_ERR_OOM;
   s->ctx = c;
+  c->live.fetch_add(1);
   s->dim = dim;
   s->N = d->n_particles;
   s->npad = std::max(64, (s->N + 63) / 64 * 64);
@@ -784,6 +787,7 @@ mpm_status mpm_scene_create(mpm_ctx* c, const mpm_scene_desc* d, mpm_scene** out
   cp.active = s->impl == MPM_IMPL_TILED ? b.active : nullptr;
   cp.n_active = b.n_active;
   cp.plain_rows = plain_rows;
+  cp.whole = 1;
   b.scene_pbase = pbase;
   b.tile_scene = tile_scene;
   b.max_ctas = c->sm_count * 4;

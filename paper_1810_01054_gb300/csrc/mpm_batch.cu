@@ -159,6 +159,7 @@ mpm_status compose(mpm_batch* B, SubBatch& sb) {
     c.gpart = sb.b.gpartial;
     c.active = sb.b.active;
     c.n_active = sb.b.n_active;
+    c.whole = sb.members.size() == 1 ? 1 : 0;  // others' tiles share the active list otherwise
     ctl.push_back(c);
     for (int t = 0; t < s->hp.n_tiles; ++t) tscene[tb + t] = int(m);
     tb += s->hp.n_tiles;
@@ -309,6 +310,7 @@ mpm_status mpm_batch_create(mpm_ctx* ctx, int dim, size_t mem_budget, mpm_batch*
   mpm_batch* B = new (std::nothrow) mpm_batch();
   if (!B) return MPM_ERR_OOM;
   B->ctx = ctx;
+  ctx->live.fetch_add(1);
   B->dim = dim;
   B->budget = mem_budget;
   *out = B;
@@ -322,6 +324,7 @@ mpm_status mpm_batch_destroy(mpm_batch* B) {
   free_sub(B->rev);
   dfree(B->partial);
   dfree(B->partial_b);
+  B->ctx->live.fetch_sub(1);
   delete B;
   return MPM_OK;
 }

@@ -20,6 +20,7 @@ int reduction_rows(int N) { return (N + RED_ROW - 1) / RED_ROW; }
 template <int CH>
 __global__ void __launch_bounds__(256) k_group_rows(const ScenePar* __restrict__ dsp, float* __restrict__ rows,
                                                     int mode) {
+  pdl_enter();
   const ScenePar& sp = *dsp;
   __shared__ float wacc[RED_WARPS][MAX_GROUPS][CH];
   __shared__ float wbody[RED_WARPS][CH];
@@ -113,6 +114,7 @@ __device__ void reduce_rows(const float* __restrict__ rows, int n_rows, int G, i
 // selection): group centroids from the partial rows, then the three tanh layers -> sp.act.
 __global__ void __launch_bounds__(1024) k_ctrl_forward(const ScenePar* __restrict__ dsp, CtrlPar c, const float* rows,
                                                        int n_rows) {
+  pdl_enter();
   const ScenePar& sp = *dsp;
   __shared__ float red[MAX_GROUPS * 3 + 3];
   __shared__ float z[MAX_GROUPS * 3], h1[MAX_HIDDEN], h2[MAX_HIDDEN];
@@ -156,8 +158,28 @@ __global__ void __launch_bounds__(1024) k_ctrl_forward(const ScenePar* __restric
 // ----------------------------------------------------------------------------- backward
 // dL/da_g = sum over the group of the (K) contributions; accumulate dL/dparams for step n;
 // for the MLP also dL/dz, turned into per-group coefficients for the x adjoint.
+// First index i in [0, n) with a[i] >= key (a ascending), found by one warp in 32-way steps: each
+// round probes 32 evenly spaced entries and keeps the interval between the last probe below key and
+// the first probe at or above it.  All 32 lanes call it and get the same result.
+__device__ __forceinline__ int first_at_least(const int* a, int n, int key) {
+  const int lane = threadIdx.x & 31;
+  int lo = 0, hi = n;  // answer in [lo, hi]
+  while (lo < hi) {
+    const int step = (hi - lo + 31) / 32;
+    const int p = lo + lane * step;
+    const bool ge = p < hi && a[p] >= key;
+    const unsigned m = __ballot_sync(0xffffffffu, ge) | __ballot_sync(0xffffffffu, p >= hi);
+    const int f = m ? __ffs(m) - 1 : 32;  // first probe at/above key (or past the end)
+    if (f == 0) return lo;
+    const int nlo = lo + (f - 1) * step + 1;
+    const int nhi = f < 32 ? lo + f * step : hi;
+    lo = nlo;
+    hi = nhi < hi ? nhi : hi;
+  }
+  return lo;
+}
+
 __device__ void ctrl_backward_body(const ScenePar& sp, const CtrlPar& c) {
-  __shared__ float red[MAX_GROUPS * 3 + 3];
   __shared__ float ga[MAX_GROUPS], z[MAX_GROUPS * 3], h1[MAX_HIDDEN], h2[MAX_HIDDEN], o3[MAX_GROUPS];
   __shared__ float gu3[MAX_GROUPS], gu2[MAX_HIDDEN], gu1[MAX_HIDDEN];
   int* step_ctr = sp.step_ctr;
@@ -169,25 +191,21 @@ __device__ void ctrl_backward_body(const ScenePar& sp, const CtrlPar& c) {
   {
     __shared__ float part[16][MAX_GROUPS];
     __shared__ int range[2];
-    if (tid == 0) {
+    if (tid < 32) {
       int lo = 0, hi = c.plain_rows;
       if (c.active) {
-        const int na = *c.n_active, t0 = sp.tile_base, t1 = sp.tile_base + sp.n_tiles;
-        int a = 0, b = na;  // first slot with active[slot] >= t0
-        while (a < b) {
-          const int m = (a + b) >> 1;
-          if (c.active[m] < t0) a = m + 1; else b = m;
+        const int na = *c.n_active;
+        if (c.whole) {
+          hi = na;
+        } else {
+          lo = first_at_least(c.active, na, sp.tile_base);
+          hi = first_at_least(c.active, na, sp.tile_base + sp.n_tiles);
         }
-        lo = a;
-        b = na;  // first slot with active[slot] >= t1
-        while (a < b) {
-          const int m = (a + b) >> 1;
-          if (c.active[m] < t1) a = m + 1; else b = m;
-        }
-        hi = a;
       }
-      range[0] = lo;
-      range[1] = hi;
+      if (tid == 0) {
+        range[0] = lo;
+        range[1] = hi;
+      }
     }
     __syncthreads();
     const int g = tid & (MAX_GROUPS - 1), split = tid >> 6;
@@ -278,18 +296,21 @@ __device__ void ctrl_backward_body(const ScenePar& sp, const CtrlPar& c) {
 }
 
 __global__ void __launch_bounds__(1024) k_ctrl_backward(const ScenePar* __restrict__ dsp, CtrlPar c) {
+  pdl_enter();
   ctrl_backward_body(*dsp, c);
 }
 
 // One block per scene of a batch: scene i uses cur[i] and cs[i].
 __global__ void __launch_bounds__(1024) k_ctrl_backward_multi(const ScenePar* __restrict__ cur,
                                                               const CtrlPar* __restrict__ cs) {
+  pdl_enter();
   ctrl_backward_body(cur[blockIdx.x], cs[blockIdx.x]);
 }
 
 // x adjoint of the MLP input: z_g = c_g - c_body, c_g = mean of x over g, c_body = mean over all.
 template <int D>
 __global__ void k_ctrl_scatter_x(const ScenePar* __restrict__ dsp, CtrlPar c) {
+  pdl_enter();
   const ScenePar& sp = *dsp;
   __shared__ float coef[MAX_GROUPS * 3], body[3];
   const int G = c.G;
@@ -321,11 +342,11 @@ cudaError_t ctrl_step_forward(const ScenePar& sp, const ScenePar* dsp, const Ctr
   const int rows = reduction_rows(sp.N);
   if (rows > 0) {
     if (sp.dim == 2)
-      k_group_rows<2><<<rows, 256, 0, s>>>(dsp, c.partials, 0);
+      launch_pdl(k_group_rows<2>, dim3(rows), dim3(256), 0, s, dsp, c.partials, 0);
     else
-      k_group_rows<3><<<rows, 256, 0, s>>>(dsp, c.partials, 0);
+      launch_pdl(k_group_rows<3>, dim3(rows), dim3(256), 0, s, dsp, c.partials, 0);
   }
-  k_ctrl_forward<<<1, 1024, 0, s>>>(dsp, c, c.partials, rows);
+  launch_pdl(k_ctrl_forward, dim3(1), dim3(1024), 0, s, dsp, c, c.partials, rows);
   count_launches(rows > 0 ? 2 : 1);
   return cudaGetLastError();
 }
@@ -334,7 +355,7 @@ cudaError_t ctrl_step_forward(const ScenePar& sp, const ScenePar* dsp, const Ctr
 // the MLP scenes' centroid adjoint is added to their dL/dx separately (ctrl_scatter_x).
 cudaError_t ctrl_backward_batched(const ScenePar* cur, const CtrlPar* cs, int n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_ctrl_backward_multi<<<n, 1024, 0, s>>>(cur, cs);
+  launch_pdl(k_ctrl_backward_multi, dim3(n), dim3(1024), 0, s, cur, cs);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -342,9 +363,9 @@ cudaError_t ctrl_backward_batched(const ScenePar* cur, const CtrlPar* cs, int n,
 cudaError_t ctrl_scatter_x(const ScenePar& sp, const ScenePar* dsp, const CtrlPar& c, cudaStream_t s) {
   if (c.type != 2 || c.G == 0 || sp.N == 0) return cudaSuccess;
   if (sp.dim == 2)
-    k_ctrl_scatter_x<2><<<(sp.N + 255) / 256, 256, 0, s>>>(dsp, c);
+    launch_pdl(k_ctrl_scatter_x<2>, dim3((sp.N + 255) / 256), dim3(256), 0, s, dsp, c);
   else
-    k_ctrl_scatter_x<3><<<(sp.N + 255) / 256, 256, 0, s>>>(dsp, c);
+    launch_pdl(k_ctrl_scatter_x<3>, dim3((sp.N + 255) / 256), dim3(256), 0, s, dsp, c);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -352,12 +373,12 @@ cudaError_t ctrl_scatter_x(const ScenePar& sp, const ScenePar* dsp, const CtrlPa
 // Controller backward for one reverse step: group sums of (K), parameter adjoint, and (MLP) the
 // centroid adjoint added to dL/dx of state n.  Rewinds the scene's step counter.
 cudaError_t ctrl_step_backward(const ScenePar& sp, const ScenePar* dsp, const CtrlPar& c, cudaStream_t s) {
-  k_ctrl_backward<<<1, 1024, 0, s>>>(dsp, c);
+  launch_pdl(k_ctrl_backward, dim3(1), dim3(1024), 0, s, dsp, c);
   if (c.type == 2 && c.G > 0 && sp.N > 0) {
     if (sp.dim == 2)
-      k_ctrl_scatter_x<2><<<(sp.N + 255) / 256, 256, 0, s>>>(dsp, c);
+      launch_pdl(k_ctrl_scatter_x<2>, dim3((sp.N + 255) / 256), dim3(256), 0, s, dsp, c);
     else
-      k_ctrl_scatter_x<3><<<(sp.N + 255) / 256, 256, 0, s>>>(dsp, c);
+      launch_pdl(k_ctrl_scatter_x<3>, dim3((sp.N + 255) / 256), dim3(256), 0, s, dsp, c);
   }
   count_launches(1 + ((c.type == 2 && c.G > 0 && sp.N > 0) ? 1 : 0));
   return cudaGetLastError();

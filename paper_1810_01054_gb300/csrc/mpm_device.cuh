@@ -132,6 +132,19 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// Programmatic dependent launch.  A kernel launched with launch_pdl may be scheduled while the
+// kernel before it on the stream is still running; pdl_wait() blocks until that kernel has
+// completed and its writes are visible.  Every CTA of such a kernel calls pdl_wait() first, before
+// any access to memory and before it can exit: the kernel then cannot complete ahead of its
+// predecessor, so completion stays ordered along the whole stream.  pdl_trigger() lets the next
+// kernel be scheduled; its CTAs then wait in pdl_wait() for this one to finish.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_enter() {
+  pdl_wait();
+  pdl_trigger();
+}
+
 // --------------------------------------------------------------------------- small matrices
 template <int D>
 __device__ __forceinline__ float det(const float (&F)[D][D]) {
@@ -371,30 +384,24 @@ __device__ __forceinline__ void bc_adjoint(const int* idx, const int* n, BCPar b
     for (int a = 0; a < D; ++a) g[a] = 0.0f;
     return;
   }
-  // replay the wall sequence to get every wall's input, then walk it backwards
+  // replay the wall sequence (wall w: axis w / 2, low side for even w) to get every wall's input,
+  // then walk it backwards; the loops are unrolled so the inputs stay in registers
   float vin[2 * D][D];
-  int axis[2 * D];
-  float sg[2 * D];
-  int nw = 0;
+  bool hit[2 * D];
   float v[D];
 #pragma unroll
   for (int a = 0; a < D; ++a) v[a] = vg[a];
 #pragma unroll
-  for (int a = 0; a < D; ++a) {
+  for (int w = 0; w < 2 * D; ++w) {
+    const int a = w >> 1;
+    hit[w] = (w & 1) ? idx[a] >= n[a] - bc.width : idx[a] < bc.width;
 #pragma unroll
-    for (int side = 0; side < 2; ++side) {
-      bool hit = side == 0 ? idx[a] < bc.width : idx[a] >= n[a] - bc.width;
-      if (hit) {
-#pragma unroll
-        for (int b = 0; b < D; ++b) vin[nw][b] = v[b];
-        axis[nw] = a;
-        sg[nw] = side == 0 ? 1.0f : -1.0f;
-        project<D>(v, a, sg[nw], bc.c);
-        ++nw;
-      }
-    }
+    for (int b = 0; b < D; ++b) vin[w][b] = v[b];
+    if (hit[w]) project<D>(v, a, (w & 1) ? -1.0f : 1.0f, bc.c);
   }
-  for (int w = nw - 1; w >= 0; --w) project_adj<D>(vin[w], axis[w], sg[w], bc.c, g);
+#pragma unroll
+  for (int w = 2 * D - 1; w >= 0; --w)
+    if (hit[w]) project_adj<D>(vin[w], w >> 1, (w & 1) ? -1.0f : 1.0f, bc.c, g);
 }
 
 }  // namespace gbmpm

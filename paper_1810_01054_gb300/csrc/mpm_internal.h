@@ -13,8 +13,26 @@ namespace gbmpm {
 // thread captures a CUDA graph its launches go to the capture's tally instead; the graph's kernels
 // are counted each time it is launched.
 void count_launches(int n);
+
 long long launch_total();
 void capture_tally(long long* tally);  // non-null: this thread is capturing
+
+// Launches kernel k with programmatic stream serialization (its CTAs may be scheduled while the
+// previous kernel on s finishes).  k must begin with pdl_enter().
+template <class... P, class... A>
+cudaError_t launch_pdl(void (*k)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, static_cast<P>(args)...);
+}
 
 constexpr uint32_t KEY_INVALID = 0xffffffffu;
 constexpr int MAX_GROUPS = 64;  // actuation groups per scene
@@ -132,6 +150,7 @@ struct CtrlPar {
   const int* active;      // tiled form: batch active tile list (NULL: plain form)
   const int* n_active;
   int plain_rows;
+  int whole;              // tiled form, scene alone in its batch: its rows are all active slots
 };
 
 int reduction_rows(int N);                  // partial rows of the group reductions

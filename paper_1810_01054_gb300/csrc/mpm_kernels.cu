@@ -128,6 +128,7 @@ __device__ __forceinline__ float particle_G(const Part<D>& q, const ScenePar& sp
 // Bin keys of the state being read, and the tile histogram (tile_count must be zero on entry).
 template <int D>
 __global__ void k_keys(BatchDev b) {
+  pdl_enter();
   int gp = blockIdx.x * blockDim.x + threadIdx.x;
   if (gp >= b.total_particles) return;
   const ScenePar& sp = b.scenes[find_scene(b.scene_pbase, b.n_scenes, gp)];
@@ -137,19 +138,6 @@ __global__ void k_keys(BatchDev b) {
   const uint32_t k = bin_key<D>(x, sp);
   sp.key[p] = k;
   warp_aggregated_inc(b.tile_count, k != KEY_INVALID ? int(sp.tile_base + (k >> 6)) : -1);
-}
-
-template <int D>
-__global__ void k_scatter(BatchDev b) {
-  int gp = blockIdx.x * blockDim.x + threadIdx.x;
-  if (gp >= b.total_particles) return;
-  const ScenePar& sp = b.scenes[find_scene(b.scene_pbase, b.n_scenes, gp)];
-  int p = gp - sp.pbase;
-  const uint32_t k = sp.key[p];
-  const int t = k != KEY_INVALID ? int(sp.tile_base + (k >> 6)) : -1;
-  const uint32_t rank = warp_aggregated_inc(b.tile_fill, t);
-  if (t < 0) return;
-  b.sorted[b.tile_start[t] + rank] = ((k & 63u) << 26) | uint32_t(p);  // cell in tile, particle id
 }
 
 // Exclusive block scan of (sum, count) pairs over blockDim.x <= 1024 threads.
@@ -195,9 +183,12 @@ __device__ __forceinline__ void block_scan2(uint32_t& a, uint32_t& c, uint32_t& 
 constexpr int SCAN_THREADS = 1024;
 constexpr int SCAN_PER_THREAD = 2;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_PER_THREAD;
+// Small batches scan the tile histogram inside the scatter kernel (k_scatter<D, true>).
+__host__ __device__ __forceinline__ bool fused_scan(const BatchDev& b) { return b.total_tiles <= SCAN_TILE; }
 
 // Phase 1 of the tile scan: per-block totals of particle counts and of active tiles.
 __global__ void k_scan_reduce(BatchDev b) {
+  pdl_enter();
   int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_PER_THREAD;
   uint32_t s = 0, c = 0;
 #pragma unroll
@@ -219,6 +210,7 @@ __global__ void k_scan_reduce(BatchDev b) {
 
 // Phase 2: exclusive scan of the block totals (one CTA).
 __global__ void k_scan_top(BatchDev b, int n_blocks) {
+  pdl_enter();
   uint32_t carry_s = 0, carry_c = 0;
   for (int base = 0; base < n_blocks; base += blockDim.x) {
     int i = base + threadIdx.x;
@@ -235,9 +227,10 @@ __global__ void k_scan_top(BatchDev b, int n_blocks) {
   }
 }
 
-// Phase 3 (or the whole scan for one block): tile_start, tile_slot, active list, n_active;
-// resets the per-step counters for the next step.
-__global__ void k_scan_down(BatchDev b, int single) {
+// Phase 3: tile_start, tile_slot, active list, n_active; resets the per-step counters for the
+// next step.
+__global__ void k_scan_down(BatchDev b) {
+  pdl_enter();
   int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_PER_THREAD;
   uint32_t cnt[SCAN_PER_THREAD];
   uint32_t s = 0, c = 0;
@@ -250,8 +243,8 @@ __global__ void k_scan_down(BatchDev b, int single) {
   }
   uint32_t ts, tc;
   block_scan2(s, c, ts, tc);
-  uint32_t off_s = single ? 0u : b.block_sums[2 * blockIdx.x];
-  uint32_t off_c = single ? 0u : b.block_sums[2 * blockIdx.x + 1];
+  uint32_t off_s = b.block_sums[2 * blockIdx.x];
+  uint32_t off_c = b.block_sums[2 * blockIdx.x + 1];
   s += off_s;
   c += off_c;
 #pragma unroll
@@ -275,6 +268,63 @@ __global__ void k_scan_down(BatchDev b, int single) {
     b.tile_start[b.total_tiles] = s;
     *b.n_active = int(c);
   }
+}
+
+// Scatter of the particles into their tiles' ranges of `sorted`.  With FUSED (total_tiles <=
+// SCAN_TILE) the tile scan is done here instead of by the scan kernels: every CTA scans the whole
+// histogram in shared memory (it is small), CTA 0 publishes tile_start, tile_slot, the active list
+// and n_active, and the per-step counters are cleared by the P2G that follows.
+template <int D, bool FUSED>
+__global__ void __launch_bounds__(256) k_scatter(BatchDev b) {
+  pdl_enter();
+  constexpr int PER = FUSED ? SCAN_TILE / 256 : 1;
+  __shared__ uint32_t sstart[FUSED ? SCAN_TILE : 1];
+  if constexpr (FUSED) {
+    const int nt = b.total_tiles, t0 = threadIdx.x * PER;
+    uint32_t cnt[PER], s = 0, c = 0;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      cnt[i] = t0 + i < nt ? b.tile_count[t0 + i] : 0u;
+      s += cnt[i];
+      c += cnt[i] > 0;
+    }
+    uint32_t ts, tc;
+    block_scan2(s, c, ts, tc);
+    const bool pub = blockIdx.x == 0;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int t = t0 + i;
+      if (t < nt) {
+        sstart[t] = s;
+        if (pub) {
+          b.tile_start[t] = s;
+          if (cnt[i] > 0) {
+            b.tile_slot[t] = int(c);
+            b.active[c] = t;
+          } else {
+            b.tile_slot[t] = -1;
+          }
+        }
+        s += cnt[i];
+        c += cnt[i] > 0;
+      }
+    }
+    if (pub && threadIdx.x == 0) {
+      b.tile_start[nt] = ts;
+      *b.n_active = int(tc);
+    }
+    __syncthreads();
+  }
+  int gp = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gp >= b.total_particles) return;
+  const ScenePar& sp = b.scenes[find_scene(b.scene_pbase, b.n_scenes, gp)];
+  int p = gp - sp.pbase;
+  const uint32_t k = sp.key[p];
+  const int t = k != KEY_INVALID ? int(sp.tile_base + (k >> 6)) : -1;
+  const uint32_t rank = warp_aggregated_inc(b.tile_fill, t);
+  if (t < 0) return;
+  const uint32_t start = FUSED ? sstart[t] : b.tile_start[t];
+  b.sorted[start + rank] = ((k & 63u) << 26) | uint32_t(p);  // cell in tile, particle id
 }
 
 // ============================================================================ P2G (tiled)
@@ -311,6 +361,7 @@ struct P2GCfg {
 
 template <int D, bool ADJ>
 __global__ void __launch_bounds__(256, ADJ ? 2 : 3) k_p2g(BatchDev b) {
+  pdl_enter();
   using K = P2GCfg<D, ADJ>;
   constexpr int B = Cfg<D>::B, CELLS = Cfg<D>::CELLS, NB = Cfg<D>::BLOCK_NODES, BN = Cfg<D>::BN;
   constexpr int ST = Cfg<D>::STENCIL;
@@ -320,6 +371,11 @@ __global__ void __launch_bounds__(256, ADJ ? 2 : 3) k_p2g(BatchDev b) {
   __shared__ int cstart[CELLS + 1], cfill[CELLS];
   const int tid = threadIdx.x;
   const int n_active = *b.n_active;
+  if (fused_scan(b))  // the scatter's scan left the per-step counters for this kernel to clear
+    for (int i = blockIdx.x * blockDim.x + tid; i < b.total_tiles; i += gridDim.x * blockDim.x) {
+      b.tile_count[i] = 0u;
+      b.tile_fill[i] = 0u;
+    }
 
   for (int slot = blockIdx.x; slot < n_active; slot += gridDim.x) {
     const int gt = b.active[slot];
@@ -430,8 +486,10 @@ __global__ void __launch_bounds__(256, ADJ ? 2 : 3) k_p2g(BatchDev b) {
         for (int a = 0; a < D; ++a) bspline(rec[a], 1.0f, w[a], dwd);
         const float* av = rec + D;      // a
         const float* Mv = rec + 2 * D;  // M, row-major
+        // the item's own offsets select weights by value: a runtime index would put w in local memory
+        const float wx = ikx == 0 ? w[0][0] : (ikx == 1 ? w[0][1] : w[0][2]);
         if constexpr (D == 2) {
-          const float N = w[0][ikx] * w[1][iky];
+          const float N = wx * (iky == 0 ? w[1][0] : (iky == 1 ? w[1][1] : w[1][2]));
 #pragma unroll
           for (int a = 0; a < D; ++a) acc[0][a] += N * (av[a] + Mv[a * D] * float(ikx) + Mv[a * D + 1] * float(iky));
           acc[0][D] += N * mass;
@@ -443,7 +501,6 @@ __global__ void __launch_bounds__(256, ADJ ? 2 : 3) k_p2g(BatchDev b) {
               acc[0][K::CHF + a] += N * (aa[a] + Ma[a * D] * float(ikx) + Ma[a * D + 1] * float(iky));
           }
         } else {
-          const float wx = w[0][ikx];
           float u[D], ua[D];
 #pragma unroll
           for (int a = 0; a < D; ++a) u[a] = av[a] + Mv[a * D] * float(ikx);
@@ -834,13 +891,15 @@ __device__ __forceinline__ void g2p_core(Part<D>& q, const float* f, const float
         if constexpr (D == 3) N *= w[D == 3 ? 2 : 0][kz];
         const float4 g = fetch(kx, ky, kz);
         const float vv[3] = {g.x, g.y, g.z};
-        const float dk[3] = {float(kx) - f[0], float(ky) - f[1], D == 3 ? float(kz) - f[D == 3 ? 2 : 0] : 0.0f};
+        const int k[3] = {kx, ky, kz};
+        // Cn accumulates sum N v k^T here (k the integer node offset); the f part is taken once below
 #pragma unroll
         for (int a = 0; a < D; ++a) {
           const float Nv = N * vv[a];
           vn[a] += Nv;
 #pragma unroll
-          for (int c = 0; c < D; ++c) Cn[a][c] += Nv * dk[c];
+          for (int c = 0; c < D; ++c)
+            if (k[c] > 0) Cn[a][c] += float(k[c]) * Nv;
         }
       }
   const float s = 4.0f * inv_dx;  // (4/dx^2) * dx, since x_i - x_p = dx (k - f)
@@ -849,7 +908,7 @@ __device__ __forceinline__ void g2p_core(Part<D>& q, const float* f, const float
   for (int a = 0; a < D; ++a)
 #pragma unroll
     for (int c = 0; c < D; ++c) {
-      Cn[a][c] *= s;
+      Cn[a][c] = s * (Cn[a][c] - f[c] * vn[a]);
       Fo[a][c] = q.F[a][c];
     }
 #pragma unroll
@@ -878,6 +937,7 @@ struct G2PCfg {
 
 template <int D>
 __global__ void __launch_bounds__(256, 3) k_g2p(BatchDev b) {
+  pdl_enter();
   using K = G2PCfg<D>;
   constexpr int B = Cfg<D>::B, NB = Cfg<D>::BLOCK_NODES, BN = Cfg<D>::BN;
   __shared__ float4 sv[NB];
@@ -967,9 +1027,11 @@ __device__ __forceinline__ float adj_core(const Part<D>& q, const Part<D>& g1, c
     float P[D][D], A[D][D];  // recomputed after the stencil loop: not kept live across it
     particle_G<D>(q, sp, id, P, A, G, sig);
   }
-  float vb[D], Cb[D][D];
-#pragma unroll
-  for (int a = 0; a < D; ++a) vb[a] = g1.v[a] + dt * g1.x[a];
+  // s_i = vbar'.v* + Dinv v*^T Cbar' d + pbar.(m v + G d) + m mbar with d = (k - f) dx is affine in
+  // the integer node offset k: alpha(k) = vbar' + Dinv Cbar' d and beta(k) = m v + G d are kept as
+  // their value at the slab/row start plus one column per axis (Ac[c] = Dinv dx Cbar'[:, c],
+  // Bc[c] = dx G[:, c]), so a node costs additions instead of two matrix-vector products
+  float Ac[D][D], Bc[D][D], al[D], be[D];
 #pragma unroll
   for (int a = 0; a < D; ++a)
 #pragma unroll
@@ -977,84 +1039,128 @@ __device__ __forceinline__ float adj_core(const Part<D>& q, const Part<D>& g1, c
       float s = 0.0f;
 #pragma unroll
       for (int k = 0; k < D; ++k) s += g1.F[a][k] * q.F[c][k];
-      Cb[a][c] = g1.C[a][c] + dt * s;
+      Ac[c][a] = Dinv * dx * (g1.C[a][c] + dt * s);  // Cbar' = C' + dt F' F^T
+      Bc[c][a] = dx * G[a][c];
     }
-  float Gbar[D][D], Cn[D][D], gxs[D], sv[D], spb[D];
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    gxs[a] = sv[a] = spb[a] = 0.0f;
+    float sa = g1.v[a] + dt * g1.x[a], sb = mass * q.v[a];  // vbar' and m v
 #pragma unroll
-    for (int c = 0; c < D; ++c) Gbar[a][c] = Cn[a][c] = 0.0f;
+    for (int c = 0; c < D; ++c) {
+      sa -= Ac[c][a] * f[c];
+      sb -= Bc[c][a] * f[c];
+    }
+    al[a] = sa;
+    be[a] = sb;
   }
-  float mv[D];
+  // accumulators: gxs = sum dN s_i; sv = sum N v*, spb = sum N pbar; Tv/Tp = the same sums weighted
+  // by the y (and z) node offset; Rv/Rp = running totals of sv/spb at each x-slab end, from which the
+  // x-offset-weighted sums follow (sum kx S_kx = 3 S - R for kx = 0, 1, 2)
+  float gxs[D], sv[D], spb[D], Tv[D][D - 1], Tp[D][D - 1], Rv[D], Rp[D];
 #pragma unroll
-  for (int a = 0; a < D; ++a) mv[a] = mass * q.v[a];
+  for (int a = 0; a < D; ++a) {
+    gxs[a] = sv[a] = spb[a] = Rv[a] = Rp[a] = 0.0f;
+#pragma unroll
+    for (int c = 0; c < D - 1; ++c) Tv[a][c] = Tp[a][c] = 0.0f;
+  }
 #pragma unroll 1
   for (int kx = 0; kx < 3; ++kx) {
     // weights of this x-slab as scalars (a loop index must not index the weight arrays)
     const float wx = kx == 0 ? w[0][0] : (kx == 1 ? w[0][1] : w[0][2]);
     const float dwx = kx == 0 ? dw[0][0] : (kx == 1 ? dw[0][1] : dw[0][2]);
-    const float dkx = float(kx) - f[0];
 #pragma unroll
-    for (int ky = 0; ky < 3; ++ky)
+    for (int ky = 0; ky < 3; ++ky) {
+      const float wxy = wx * w[1][ky], dwxy = dwx * w[1][ky], wxdy = wx * dw[1][ky];
+      float ar[D], br[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        ar[a] = ky == 0 ? al[a] : al[a] + float(ky) * Ac[1][a];
+        br[a] = ky == 0 ? be[a] : be[a] + float(ky) * Bc[1][a];
+      }
 #pragma unroll
       for (int kz = 0; kz < (D == 3 ? 3 : 1); ++kz) {
-        float wyz = w[1][ky], N, dN[D], dk[D];
+        constexpr int Z = D == 3 ? 2 : 0;
+        float N, dN[D], alpha[D], beta[D];
         if constexpr (D == 3) {
-          const float wz = w[D == 3 ? 2 : 0][kz];
-          wyz *= wz;
-          N = wx * wyz;
-          dN[0] = dwx * wyz;
-          dN[1] = wx * dw[1][ky] * wz;
-          dN[D == 3 ? 2 : 0] = wx * w[1][ky] * dw[D == 3 ? 2 : 0][kz];
-          dk[D == 3 ? 2 : 0] = float(kz) - f[D == 3 ? 2 : 0];
+          N = wxy * w[Z][kz];
+          dN[0] = dwxy * w[Z][kz];
+          dN[1] = wxdy * w[Z][kz];
+          dN[Z] = wxy * dw[Z][kz];
+#pragma unroll
+          for (int a = 0; a < D; ++a) {
+            alpha[a] = kz == 0 ? ar[a] : ar[a] + float(kz) * Ac[Z][a];
+            beta[a] = kz == 0 ? br[a] : br[a] + float(kz) * Bc[Z][a];
+          }
         } else {
-          N = wx * wyz;
-          dN[0] = dwx * wyz;
-          dN[1] = wx * dw[1][ky];
+          N = wxy;
+          dN[0] = dwxy;
+          dN[1] = wxdy;
+#pragma unroll
+          for (int a = 0; a < D; ++a) {
+            alpha[a] = ar[a];
+            beta[a] = br[a];
+          }
         }
-        dk[0] = dkx;
-        dk[1] = float(ky) - f[1];
         float4 v4, p4;
         fetch(kx, ky, kz, v4, p4);
         const float vs[3] = {v4.x, v4.y, v4.z};
         const float pb[3] = {p4.x, p4.y, p4.z};
         const float mb = D == 2 ? p4.z : p4.w;
-        float dp[D];
-#pragma unroll
-        for (int a = 0; a < D; ++a) dp[a] = dk[a] * dx;
-        // s_i = vbar'.v* + Dinv v*^T Cbar' d + pbar.(m v + G d) + m mbar
         float si = mass * mb;
 #pragma unroll
-        for (int a = 0; a < D; ++a) {
-          float Cd = 0.0f, Gd = 0.0f;
-#pragma unroll
-          for (int c = 0; c < D; ++c) {
-            Cd += Cb[a][c] * dp[c];
-            Gd += G[a][c] * dp[c];
-          }
-          si += vs[a] * (vb[a] + Dinv * Cd) + pb[a] * (mv[a] + Gd);
-        }
+        for (int a = 0; a < D; ++a) si += vs[a] * alpha[a] + pb[a] * beta[a];
 #pragma unroll
         for (int a = 0; a < D; ++a) {
           gxs[a] += dN[a] * si;
-          sv[a] += N * vs[a];
-          spb[a] += N * pb[a];
-#pragma unroll
-          for (int c = 0; c < D; ++c) {
-            Gbar[a][c] += N * pb[a] * dp[c];
-            Cn[a][c] += N * vs[a] * dk[c];
+          const float qv = N * vs[a], qp = N * pb[a];
+          sv[a] += qv;
+          spb[a] += qp;
+          if (ky > 0) {
+            Tv[a][0] += float(ky) * qv;
+            Tp[a][0] += float(ky) * qp;
+          }
+          if constexpr (D == 3) {
+            if (kz > 0) {
+              Tv[a][D - 2] += float(kz) * qv;
+              Tp[a][D - 2] += float(kz) * qp;
+            }
           }
         }
       }
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      Rv[a] += sv[a];
+      Rp[a] += spb[a];
+      al[a] += Ac[0][a];
+      be[a] += Bc[0][a];
+    }
+  }
+  // Gbar = sum N pbar d^T (= dx (sum N pbar k^T - spb f^T)), Cn = sum N v* (k - f)^T
+  float Gbar[D][D], Cn[D][D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    float tv[D], tp[D];
+    tv[0] = 3.0f * sv[a] - Rv[a];
+    tp[0] = 3.0f * spb[a] - Rp[a];
+#pragma unroll
+    for (int c = 1; c < D; ++c) {
+      tv[c] = Tv[a][c - 1];
+      tp[c] = Tp[a][c - 1];
+    }
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      Cn[a][c] = tv[c] - f[c] * sv[a];
+      Gbar[a][c] = dx * (tp[c] - f[c] * spb[a]);
+    }
   }
   // (J): gx = gx' + sum dN s_i - Dinv Cbar'^T sum N v* - G^T sum N pbar
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     float t = 0.0f;
 #pragma unroll
-    for (int c = 0; c < D; ++c) t += Dinv * Cb[c][a] * sv[c] + G[c][a] * spb[c];
-    g0.x[a] = g1.x[a] + gxs[a] - t;
+    for (int c = 0; c < D; ++c) t += Ac[a][c] * sv[c] + Bc[a][c] * spb[c];
+    g0.x[a] = g1.x[a] + gxs[a] - sp.inv_dx * t;
     g0.v[a] = mass * spb[a];  // (F)
   }
   const float sC = 4.0f * sp.inv_dx;
@@ -1104,7 +1210,15 @@ __device__ __forceinline__ float adj_core(const Part<D>& q, const Part<D>& g1, c
 }
 
 template <int D>
+struct GatherCfg {
+  static constexpr int STAGE = 512;                  // particles staged per tile
+  static constexpr int NP = 2 * Cfg<D>::PLANES;      // state planes, then adjoint planes
+  static constexpr size_t SMEM = size_t(NP) * STAGE * sizeof(float4);
+};
+
+template <int D>
 __global__ void __launch_bounds__(256, 2) k_adj_gather(BatchDev b) {
+  pdl_enter();
   constexpr int B = Cfg<D>::B, NB = Cfg<D>::BLOCK_NODES, BN = Cfg<D>::BN;
   __shared__ float4 sv[NB], sb[NB];
   __shared__ float wpart[8][MAX_GROUPS];
@@ -1179,23 +1293,25 @@ cudaError_t launch_keys(const BatchDev& b, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(b.tile_count, 0, sizeof(uint32_t) * size_t(b.total_tiles), s);
   if (e != cudaSuccess) return e;
   if (b.total_particles == 0) return cudaSuccess;
-  k_keys<D><<<(b.total_particles + 255) / 256, 256, 0, s>>>(b);
+  launch_pdl(k_keys<D>, dim3((b.total_particles + 255) / 256), dim3(256), 0, s, b);
   count_launches(1);
   return cudaGetLastError();
 }
 
 template <int D>
 cudaError_t launch_sort(const BatchDev& b, cudaStream_t s) {
-  const int nblk = (b.total_tiles + SCAN_TILE - 1) / SCAN_TILE;
-  if (nblk <= 1) {
-    k_scan_down<<<1, SCAN_THREADS, 0, s>>>(b, 1);
-  } else {
-    k_scan_reduce<<<nblk, SCAN_THREADS, 0, s>>>(b);
-    k_scan_top<<<1, SCAN_THREADS, 0, s>>>(b, nblk);
-    k_scan_down<<<nblk, SCAN_THREADS, 0, s>>>(b, 0);
+  if (fused_scan(b)) {  // scan inside the scatter; at least one CTA so the scan results are written
+    const int nblk = b.total_particles > 0 ? (b.total_particles + 255) / 256 : 1;
+    launch_pdl(k_scatter<D, true>, dim3(nblk), dim3(256), 0, s, b);
+    count_launches(1);
+    return cudaGetLastError();
   }
-  if (b.total_particles > 0) k_scatter<D><<<(b.total_particles + 255) / 256, 256, 0, s>>>(b);
-  count_launches((b.total_particles > 0 ? 1 : 0) + (nblk <= 1 ? 1 : 3));
+  const int nblk = (b.total_tiles + SCAN_TILE - 1) / SCAN_TILE;
+  launch_pdl(k_scan_reduce, dim3(nblk), dim3(SCAN_THREADS), 0, s, b);
+  launch_pdl(k_scan_top, dim3(1), dim3(SCAN_THREADS), 0, s, b, nblk);
+  launch_pdl(k_scan_down, dim3(nblk), dim3(SCAN_THREADS), 0, s, b);
+  if (b.total_particles > 0) launch_pdl(k_scatter<D, false>, dim3((b.total_particles + 255) / 256), dim3(256), 0, s, b);
+  count_launches((b.total_particles > 0 ? 1 : 0) + 3);
   return cudaGetLastError();
 }
 
@@ -1218,7 +1334,7 @@ static cudaError_t p2g_impl(const BatchDev& b, cudaStream_t s) {
   using K = P2GCfg<D, ADJ>;
   int grid = b.max_ctas < b.total_tiles ? b.max_ctas : b.total_tiles;
   if (grid < 1) grid = 1;
-  k_p2g<D, ADJ><<<grid, K::THREADS, K::SMEM, s>>>(b);
+  launch_pdl(k_p2g<D, ADJ>, dim3(grid), dim3(K::THREADS), K::SMEM, s, b);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -1232,7 +1348,7 @@ template <int D>
 cudaError_t launch_g2p(const BatchDev& b, cudaStream_t s) {
   int grid = b.max_ctas < b.total_tiles ? b.max_ctas : b.total_tiles;
   if (grid < 1) grid = 1;
-  k_g2p<D><<<grid, 256, 0, s>>>(b);
+  launch_pdl(k_g2p<D>, dim3(grid), dim3(256), 0, s, b);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -1241,7 +1357,7 @@ template <int D>
 cudaError_t launch_adj_gather(const BatchDev& b, cudaStream_t s) {
   int grid = b.max_ctas < b.total_tiles ? b.max_ctas : b.total_tiles;
   if (grid < 1) grid = 1;
-  k_adj_gather<D><<<grid, 256, 0, s>>>(b);
+  launch_pdl(k_adj_gather<D>, dim3(grid), dim3(256), 0, s, b);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -1551,6 +1667,7 @@ __global__ void k_unpack(int dim, int N, int npad, const float4* planes, float* 
 // sinusoid controllers' actuation a_g(t_n) is evaluated here too.  Every step of a rollout is
 // then the same launch sequence, which CUDA graphs replay.
 __global__ void k_select(const SelectPar* __restrict__ sel, ScenePar* __restrict__ cur) {
+  pdl_enter();
   const SelectPar& q = sel[blockIdx.x];
   const int n = *q.ctr;
   const int idx = q.map ? q.map[n - q.base] : 0;
@@ -1576,7 +1693,7 @@ __global__ void k_select(const SelectPar* __restrict__ sel, ScenePar* __restrict
 
 cudaError_t launch_select(const SelectPar* sel, int n_scenes, ScenePar* cur, cudaStream_t s) {
   if (n_scenes <= 0) return cudaSuccess;
-  k_select<<<n_scenes, 64, 0, s>>>(sel, cur);
+  launch_pdl(k_select, dim3(n_scenes), dim3(64), 0, s, sel, cur);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -2,6 +2,7 @@
 // scheduler translation units.
 #pragma once
 
+#include <atomic>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -31,6 +32,7 @@ struct mpm_ctx {
   std::vector<cudaEvent_t> prof_ev;
   std::vector<int> prof_kind;
   int prof_used = 0;
+  std::atomic<int> live{0};  // scenes and batches created on this context and not yet destroyed
 };
 
 struct Graph {

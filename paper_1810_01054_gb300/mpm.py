@@ -12,6 +12,7 @@ from __future__ import annotations
 import ctypes as C
 import os
 import threading
+import weakref
 
 import numpy as np
 
@@ -188,6 +189,8 @@ class Context:
     torch.cuda.Stream (or raw cudaStream_t int); None creates a private stream."""
 
     def __init__(self, device: int = 0, stream=None):
+        self.handle = None
+        self._children = weakref.WeakSet()  # live scenes and batches, closed before the context
         raw = None
         if stream is not None:
             handle = int(getattr(stream, "cuda_stream", stream))
@@ -213,9 +216,19 @@ class Context:
         _check(lib().mpm_profile_read(self.handle, int(kind), C.byref(n), C.byref(t)), "mpm_profile_read")
         return n.value, t.value
 
+    def _adopt(self, child):
+        self._children.add(child)
+
     def close(self):
+        """Closes the context's batches, then its scenes, then the context itself."""
         if self.handle:
-            lib().mpm_ctx_destroy(self.handle)
+            kids = list(self._children)
+            for k in kids:
+                if isinstance(k, Batch):
+                    k.close()
+            for k in kids:
+                k.close()
+            _check(lib().mpm_ctx_destroy(self.handle), "mpm_ctx_destroy")
             self.handle = None
 
     def __del__(self):
@@ -286,6 +299,7 @@ class Scene:
         h = C.c_void_p()
         _check(lib().mpm_scene_create(ctx.handle, C.byref(desc), C.byref(h)), "mpm_scene_create")
         self.handle = h
+        ctx._adopt(self)
         self.G = G
         self.impl = impl
 
@@ -403,6 +417,7 @@ class Batch:
         _check(lib().mpm_batch_create(ctx.handle, int(dim), C.c_size_t(int(mem_budget)), C.byref(h)),
                "mpm_batch_create")
         self.handle, self.ctx, self.dim = h, ctx, dim
+        ctx._adopt(self)
 
     def admit(self, scene: "Scene", n_steps: int, want_grad: bool) -> int:
         slot = C.c_int(-1)

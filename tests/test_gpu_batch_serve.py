@@ -163,3 +163,14 @@ def test_autograd_function_matches_library_and_oracle(M, ctx):
     assert_grad_close(v0.grad.cpu().numpy(), ogv, "autograd dL/dv0")
     assert_grad_close(params.grad.cpu().numpy(), ogp, "autograd dL/dA")
     assert_grad_close(F0.grad.cpu().numpy(), ogF, "autograd dL/dF0")
+
+
+def test_context_outlives_its_scenes_and_batches(M):
+    """The C context refuses to go while scenes or batches use it; the binding closes them first."""
+    c = M.Context(0)
+    sc = M.Scene(c, S.blob(2, 16, 50, 11, radius_cells=3.0))
+    b = M.Batch(c, 2)
+    assert M.lib().mpm_ctx_destroy(c.handle) == -7  # MPM_ERR_STATE: nothing freed
+    sc.step(2)
+    c.close()
+    assert sc.handle is None and b.handle is None and c.handle is None
