@@ -104,20 +104,26 @@ __device__ __forceinline__ uint32_t bin_key(const float* x, const ScenePar& sp) 
   return (uint32_t(lin3<D>(t, sp.nt)) << 6) | uint32_t(cell_lin<D>(c));
 }
 
-// Actuation stress diagonal of particle id: sigma_a = a_g Diag(dir_g) (Section III).
-template <int D>
-__device__ __forceinline__ void actuation(const ScenePar& sp, int id, float* sig) {
-  int g = sp.group ? __ldg(sp.group + id) : -1;
-  float a = (g >= 0 && g < sp.G) ? __ldg(sp.act + g) : 0.0f;
-#pragma unroll
-  for (int k = 0; k < D; ++k) sig[k] = (g >= 0 && g < sp.G) ? a * __ldg(sp.act_dir + g * D + k) : 0.0f;
+// Actuation group of particle id (-1: none).
+__device__ __forceinline__ int group_of(const ScenePar& sp, int id) {
+  const int g = sp.group ? __ldg(sp.group + id) : -1;
+  return g < sp.G ? g : -1;
 }
 
-// Per-particle quantities of P2G: stress with actuation and G of Eq. 4.  Returns J.
+// Actuation stress diagonal of a particle of group g: sigma_a = a_g Diag(dir_g) (Section III).
 template <int D>
-__device__ __forceinline__ float particle_G(const Part<D>& q, const ScenePar& sp, int id, float (&P)[D][D],
+__device__ __forceinline__ void actuation(const ScenePar& sp, int g, float* sig) {
+  float a = g >= 0 ? __ldg(sp.act + g) : 0.0f;
+#pragma unroll
+  for (int k = 0; k < D; ++k) sig[k] = g >= 0 ? a * __ldg(sp.act_dir + g * D + k) : 0.0f;
+}
+
+// Per-particle quantities of P2G for a particle of group g: stress with actuation and G of Eq. 4.
+// Returns J.
+template <int D>
+__device__ __forceinline__ float particle_G(const Part<D>& q, const ScenePar& sp, int g, float (&P)[D][D],
                                             float (&A)[D][D], float (&G)[D][D], float* sig) {
-  actuation<D>(sp, id, sig);
+  actuation<D>(sp, g, sig);
   float J = stress<D>(q.F, sp.mat, sig, P, A);
   float kG = -4.0f * sp.inv_dx * sp.inv_dx * sp.dt * sp.vol;
   mls_G<D>(P, q.F, q.C, kG, sp.mass, G);
@@ -360,7 +366,7 @@ struct P2GCfg {
 };
 
 template <int D, bool ADJ>
-__global__ void __launch_bounds__(256, ADJ ? 2 : 3) k_p2g(BatchDev b) {
+__global__ void __launch_bounds__(256, 2) k_p2g(BatchDev b) {
   pdl_enter();
   using K = P2GCfg<D, ADJ>;
   constexpr int B = Cfg<D>::B, CELLS = Cfg<D>::CELLS, NB = Cfg<D>::BLOCK_NODES, BN = Cfg<D>::BN;
@@ -400,8 +406,9 @@ __global__ void __launch_bounds__(256, ADJ ? 2 : 3) k_p2g(BatchDev b) {
     const float dx = sp.dx, dt = sp.dt;
     const float Dx4 = 4.0f * sp.inv_dx;  // (4/dx^2) * dx
 
-    // Phase B for one particle: record of particle `id` (state in r[]) at staging row `row`.
-    auto make_record = [&](int id, float* r, int row) {
+    // Phase B for one particle: record of particle `id` (state in r[], bin cell `kc` of its key,
+    // actuation group g) at staging row `row`.
+    auto make_record = [&](int id, uint32_t kc, int g, float* r, int row) {
       Part<D> q;
       unpack<D>(r, q);
       int base[D];
@@ -412,7 +419,7 @@ __global__ void __launch_bounds__(256, ADJ ? 2 : 3) k_p2g(BatchDev b) {
       {
         int c[D];
         const int bn[3] = {B, B, B};
-        unlin<D>(int(sp.key[id] & 63u), bn, c);
+        unlin<D>(int(kc), bn, c);
         bool ok = true;
 #pragma unroll
         for (int a = 0; a < D; ++a) ok = ok && base[a] == t[a] * B + c[a];
@@ -422,7 +429,7 @@ __global__ void __launch_bounds__(256, ADJ ? 2 : 3) k_p2g(BatchDev b) {
         }
       }
       float P[D][D], A[D][D], G[D][D], sig[D];
-      const float J = particle_G<D>(q, sp, id, P, A, G, sig);
+      const float J = particle_G<D>(q, sp, g, P, A, G, sig);
       if (!(J > 0.0f)) set_status(sp.status, ST_INVERTED);
       const float keep = wm > 0.0f ? 1.0f : 0.0f;
       float* rec = U + size_t(row) * K::RW;
@@ -566,7 +573,12 @@ __global__ void __launch_bounds__(256, ADJ ? 2 : 3) k_p2g(BatchDev b) {
       const uint32_t r0 = tid < cnt ? b.sorted[st + tid] : 0xffffffffu;
       const uint32_t r1 = tid + K::THREADS < cnt ? b.sorted[st + tid + K::THREADS] : 0xffffffffu;
       float pre[Cfg<D>::S];
-      if (r0 != 0xffffffffu) load_planes<D, Cfg<D>::PLANES>(sp.planes, sp.npad, int(r0 & 0x3ffffffu), pre);
+      int g0 = -1, g1 = -1;
+      if (r0 != 0xffffffffu) {
+        load_planes<D, Cfg<D>::PLANES>(sp.planes, sp.npad, int(r0 & 0x3ffffffu), pre);
+        g0 = group_of(sp, int(r0 & 0x3ffffffu));
+      }
+      if (r1 != 0xffffffffu) g1 = group_of(sp, int(r1 & 0x3ffffffu));
       __syncthreads();
       if (r0 != 0xffffffffu) atomicAdd(&cfill[r0 >> 26], 1);
       if (r1 != 0xffffffffu) atomicAdd(&cfill[r1 >> 26], 1);
@@ -587,11 +599,11 @@ __global__ void __launch_bounds__(256, ADJ ? 2 : 3) k_p2g(BatchDev b) {
         for (int j = cstart[c]; j < cstart[c + 1]; ++j) pos += ids[j] < id;
         b.sorted[st + pos] = id;  // canonical order for the gathers of this step
         if (h == 0) {
-          make_record(int(id), pre, pos);
+          make_record(int(id), c, g0, pre, pos);
         } else {
           float r[Cfg<D>::S];
           load_planes<D, Cfg<D>::PLANES>(sp.planes, sp.npad, int(id), r);
-          make_record(int(id), r, pos);
+          make_record(int(id), c, g1, r, pos);
         }
       }
       __syncthreads();
@@ -639,7 +651,7 @@ __global__ void __launch_bounds__(256, ADJ ? 2 : 3) k_p2g(BatchDev b) {
           const int id = int(ids[e]);
           float r[Cfg<D>::S];
           load_planes<D, Cfg<D>::PLANES>(sp.planes, sp.npad, id, r);
-          make_record(id, r, e - c0);
+          make_record(id, sp.key[id] & 63u, group_of(sp, id), r, e - c0);
         }
         __syncthreads();
         if (item_thread) accumulate(cs > c0 ? cs : c0, ce < c1 ? ce : c1, c0);
@@ -1017,7 +1029,7 @@ __global__ void __launch_bounds__(256, 3) k_g2p(BatchDev b) {
 // `fetch(kx,ky,kz, v, pb)` returns (v*, m) in v and (pbar, mbar) in pb.
 template <int D, class Fetch>
 __device__ __forceinline__ float adj_core(const Part<D>& q, const Part<D>& g1, const float* f, const float (&w)[D][3],
-                                          const float (&dw)[D][3], const ScenePar& sp, int id, Fetch fetch,
+                                          const float (&dw)[D][3], const ScenePar& sp, int g, Fetch fetch,
                                           Part<D>& g0) {
   const float dt = sp.dt, dx = sp.dx, mass = sp.mass;
   const float Dinv = 4.0f * sp.inv_dx * sp.inv_dx;
@@ -1025,7 +1037,7 @@ __device__ __forceinline__ float adj_core(const Part<D>& q, const Part<D>& g1, c
   float G[D][D], sig[D];
   {
     float P[D][D], A[D][D];  // recomputed after the stencil loop: not kept live across it
-    particle_G<D>(q, sp, id, P, A, G, sig);
+    particle_G<D>(q, sp, g, P, A, G, sig);
   }
   // s_i = vbar'.v* + Dinv v*^T Cbar' d + pbar.(m v + G d) + m mbar with d = (k - f) dx is affine in
   // the integer node offset k: alpha(k) = vbar' + Dinv Cbar' d and beta(k) = m v + G d are kept as
@@ -1195,9 +1207,8 @@ __device__ __forceinline__ float adj_core(const Part<D>& q, const Part<D>& g1, c
       g0.F[a][c] = s + H[a][c] + Pb[a][c] * sig[c] + kG * t;
     }
   // (K) sigma-bar = F^T Pbar, contracted with the group's direction
-  int g = sp.group ? __ldg(sp.group + id) : -1;
   float contrib = 0.0f;
-  if (g >= 0 && g < sp.G) {
+  if (g >= 0) {
 #pragma unroll
     for (int a = 0; a < D; ++a) {
       float s = 0.0f;
@@ -1208,13 +1219,6 @@ __device__ __forceinline__ float adj_core(const Part<D>& q, const Part<D>& g1, c
   }
   return contrib;
 }
-
-template <int D>
-struct GatherCfg {
-  static constexpr int STAGE = 512;                  // particles staged per tile
-  static constexpr int NP = 2 * Cfg<D>::PLANES;      // state planes, then adjoint planes
-  static constexpr size_t SMEM = size_t(NP) * STAGE * sizeof(float4);
-};
 
 template <int D>
 __global__ void __launch_bounds__(256, 2) k_adj_gather(BatchDev b) {
@@ -1232,6 +1236,7 @@ __global__ void __launch_bounds__(256, 2) k_adj_gather(BatchDev b) {
     const uint32_t st = b.tile_start[gt];
     const int cnt = int(b.tile_start[gt + 1] - st);
     // the first particle's state is requested before the node block is built, so the two overlap
+    // (requesting its adjoint too, or staging the second particle in shared memory, measured slower)
     float r[Cfg<D>::S];
     if (tid < cnt) load_planes<D, Cfg<D>::PLANES>(sp.planes, sp.npad, int(b.sorted[st + tid]), r);
     build_node_block<D, true>(b, sp, t, sv, sb);
@@ -1248,6 +1253,7 @@ __global__ void __launch_bounds__(256, 2) k_adj_gather(BatchDev b) {
         unpack<D>(r, q);
         load_planes<D, Cfg<D>::PLANES>(sp.adj_in, sp.npad, id, r);
         unpack<D>(r, g1);
+        const int gq = group_of(sp, id);
         int base[D];
         float f[D], w[D][3], dw[D][3];
         stencil_base<D>(q.x, sp.inv_dx, sp.n, base, f);
@@ -1259,7 +1265,7 @@ __global__ void __launch_bounds__(256, 2) k_adj_gather(BatchDev b) {
           inside = inside && base[a] >= 0 && base[a] < B;
         }
         if (inside) {
-          contrib = adj_core<D>(q, g1, f, w, dw, sp, id, [&](int kx, int ky, int kz, float4& v, float4& p) {
+          contrib = adj_core<D>(q, g1, f, w, dw, sp, gq, [&](int kx, int ky, int kz, float4& v, float4& p) {
             int l = (base[0] + kx) * BN + base[1] + ky;
             if constexpr (D == 3) l = l * BN + base[2] + kz;
             v = sv[l];
@@ -1267,8 +1273,7 @@ __global__ void __launch_bounds__(256, 2) k_adj_gather(BatchDev b) {
           }, g0);
           pack<D>(g0, r);
           store_planes<D, Cfg<D>::PLANES>(sp.adj_out, sp.npad, id, r);
-          g = sp.group ? __ldg(sp.group + id) : -1;
-          if (g >= sp.G) g = -1;
+          g = gq;
         } else {
           set_status(sp.status, ST_BINNING);
         }
@@ -1391,7 +1396,7 @@ __global__ void k_plain_scatter(const ScenePar* __restrict__ dsp) {
     return;
   }
   float P[D][D], A[D][D], G[D][D], sig[D];
-  const float J = particle_G<D>(q, sp, id, P, A, G, sig);
+  const float J = particle_G<D>(q, sp, group_of(sp, id), P, A, G, sig);
   if (!(J > 0.0f)) set_status(sp.status, ST_INVERTED);
   float vb[D], Cb[D][D];
   if constexpr (ADJ) {
@@ -1542,7 +1547,7 @@ __global__ void k_plain_gather(const ScenePar* __restrict__ dsp) {
   unpack<D>(r, g1);
   Sten<D> stn;
   if (!make_stencil<D>(q.x, sp.inv_dx, sp.n, stn)) return;
-  const float c = adj_core<D>(q, g1, stn.f, stn.w, stn.dw, sp, id, [&](int kx, int ky, int kz, float4& v, float4& p) {
+  const float c = adj_core<D>(q, g1, stn.f, stn.w, stn.dw, sp, group_of(sp, id), [&](int kx, int ky, int kz, float4& v, float4& p) {
     int nd[D];
     nd[0] = stn.base[0] + kx;
     nd[1] = stn.base[1] + ky;
