@@ -353,6 +353,7 @@ def measure(args, spec, rank, world, dev, stream, ctx, *, e2e=True, plain=True):
             pm.append(a.elapsed_time(b))
         plain_rec = {"value": N * T / (min(pm) / 1e3), "unit": UNIT, "form": "plain single-scene (float atomics)"}
         ps.close()
+    launch = {mpm.TILE_KERNELS[kk]: list(scene.launch(kk)) for kk in range(4)}  # [ctas/SM, threads, tuned]
     scene.close()
 
     # roofline of the dominant hot kernel (largest summed time in the profiled repeat)
@@ -369,7 +370,7 @@ def measure(args, spec, rank, world, dev, stream, ctx, *, e2e=True, plain=True):
     share = {kk: round(v[1] / prof_total_ms, 4) for kk, v in prof.items()}
     return {"value": value, "tot_ms": tot_ms, "step_ms": step_ms, "value_fwd": value_fwd, "roofline": roof,
             "share": share, "e2e": e2e_rec, "plain": plain_rec, "gpu_launches": n_launch, "clocks": clk.summary(),
-            "N": N, "T": T, "k": k}
+            "N": N, "T": T, "k": k, "launch": launch}
 
 
 def measure_serving(dev, stream, n_requests=32, seed=4):
@@ -449,7 +450,7 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": spec.name, "particles": r["N"], "grid": "x".join(map(str, spec.n_grid)),
                    "sim_steps": r["T"], "ckpt_interval": r["k"], "pass": "forward+reverse rollout",
                    "loss": "mean final x_0", "l2": "flushed before every timed step (256 MB write, untimed)",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}", "launch": r["launch"]},
         "value_fwd": r["value_fwd"],
         "rollout_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
         "roofline": r["roofline"], "kernel_share_of_profiled_step": r["share"],

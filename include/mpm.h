@@ -188,6 +188,39 @@ mpm_status mpm_profile_read(mpm_ctx* ctx, int kind, int* count, double* total_ms
 /* Total number of kernels this library has launched in the process (all contexts). */
 mpm_status mpm_launch_count(long long* count);
 
+/* Launch-shape autotuning (no counterpart in the paper, whose kernels were launched with fixed
+ * shapes on its own GPU).  The four tile kernels -- P2G, G2P, the adjoint scatter and the
+ * adjoint gather -- run as persistent grids; how many CTAs per SM each gets (and, for G2P, 128 or
+ * 256 threads per CTA) is chosen per workload.  Under MPM_TUNE_AUTO (the default) a scene looks
+ * its workload key -- dimension, log2 buckets of its particle and grid-tile counts, SM count -- up
+ * in a process-wide cache; on a miss its next steps try every candidate shape of each kernel in
+ * turn (two timed launches each, CUDA events, launched directly instead of from graphs), keep
+ * the fastest and store it in the cache.  Every tile is processed whole by one CTA, so results
+ * are bitwise the same under every shape and the trial steps are ordinary steps.  Batches use
+ * the cache entry of their composition's key when there is one, the default shape (4 CTAs of
+ * 256 threads per SM) otherwise.  MPM_TUNE_FORCE re-tunes ignoring the cache; MPM_TUNE_OFF uses
+ * the default shapes. */
+enum { MPM_TUNE_OFF = 0, MPM_TUNE_AUTO = 1, MPM_TUNE_FORCE = 2 };
+/* Tile kernels, for mpm_scene_launch and the cache arrays below (in this order). */
+enum { MPM_TK_P2G = 0, MPM_TK_G2P = 1, MPM_TK_P2G_ADJ = 2, MPM_TK_ADJ_GATHER = 3, MPM_TK_COUNT = 4 };
+mpm_status mpm_scene_set_tuning(mpm_scene* scene, int mode);
+/* Launch shape of tile kernel `kernel` for this scene; *tuned = 1 once it came from the cache or
+ * from trials, 0 while it is the default or still being tried. */
+mpm_status mpm_scene_launch(const mpm_scene* scene, int kernel, int* ctas_per_sm, int* threads, int* tuned);
+/* The process-wide cache.  shape[2k], shape[2k+1] = CTAs per SM and threads of tile kernel k.
+ *  mpm_tune_cache_lookup  *found = 1 and shape filled when the key of (dim, particles, grid
+ *                         tiles, sm_count) has an entry
+ *  mpm_tune_cache_store   sets the entry of that key (shapes are checked against the candidates)
+ *  mpm_tune_cache_save    writes every entry to a text file (one line per key)
+ *  mpm_tune_cache_load    adds the entries of such a file (MPM_ERR_ARG if it is malformed)
+ * None of them touches the GPU.  When the environment variable GBMPM_TUNE_CACHE names a file,
+ * it is loaded at the first lookup and rewritten after every tuning that finishes. */
+mpm_status mpm_tune_cache_lookup(int dim, long long particles, long long grid_tiles, int sm_count, int* shape,
+                                 int* found);
+mpm_status mpm_tune_cache_store(int dim, long long particles, long long grid_tiles, int sm_count, const int* shape);
+mpm_status mpm_tune_cache_save(const char* path);
+mpm_status mpm_tune_cache_load(const char* path);
+
 /* Allocation-free forward step (no counterpart in the paper; an addition for callers that must
  * not allocate device memory: a control loop with a hard latency budget, where cudaMalloc may
  * block and synchronise the device, or a process whose device memory is owned entirely by

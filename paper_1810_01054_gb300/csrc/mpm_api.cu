@@ -224,10 +224,12 @@ mpm_status enqueue_forward(mpm_scene* s, int ph, cudaStream_t st) {
   }
   {
     ProfScope p(c, st, MPM_K_P2G);
+    TuneScope t(s, TK_P2G, st);
     CK(two ? launch_p2g<2>(s->b, false, st) : launch_p2g<3>(s->b, false, st));
   }
   {
     ProfScope p(c, st, MPM_K_G2P);
+    TuneScope t(s, TK_G2P, st);
     CK(two ? launch_g2p<2>(s->b, st) : launch_g2p<3>(s->b, st));
   }
   return MPM_OK;
@@ -257,10 +259,12 @@ mpm_status enqueue_reverse(mpm_scene* s, cudaStream_t st) {
     }
     {
       ProfScope p(c, st, MPM_K_P2G_ADJ);
+      TuneScope t(s, TK_P2G_ADJ, st);
       CK(two ? launch_p2g<2>(s->b, true, st) : launch_p2g<3>(s->b, true, st));
     }
     {
       ProfScope p(c, st, MPM_K_ADJ_GATHER);
+      TuneScope t(s, TK_ADJ_GATHER, st);
       CK(two ? launch_adj_gather<2>(s->b, st) : launch_adj_gather<3>(s->b, st));
     }
   }
@@ -311,6 +315,9 @@ mpm_status capture(mpm_scene* s, int ph, int steps, Graph* g) {
 // launch timing is on.
 mpm_status run_phase(mpm_scene* s, int ph, int count) {
   mpm_ctx* c = s->ctx;
+  // steps that still try launch shapes run one at a time, launched directly and timed; graphs are
+  // captured only once the shapes of the phase's kernels are settled
+  for (; count > 0 && tune_wants(s, ph); --count) CKS(tune_step(s, ph));
   if (count <= 0) return MPM_OK;
   if (c->prof_mask) {
     for (int i = 0; i < count; ++i) CKS(enqueue_phase(s, ph, c->stream));
@@ -343,6 +350,18 @@ void free_rollout(mpm_scene* s) {
 }  // namespace
 
 namespace gbmpm {
+
+mpm_status enqueue_step(mpm_scene* s, int ph, cudaStream_t st) { return enqueue_phase(s, ph, st); }
+
+void invalidate_graphs(mpm_scene* s) {
+  for (auto& row : s->graphs)
+    for (auto& g : row)
+      if (g.exec) {
+        cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
+        g.kernels = 0;
+      }
+}
 
 mpm_status set_counter(mpm_scene* s, int* dctr, int value) {
   CK(launch_set_int(dctr, value, s->ctx->stream));
@@ -608,9 +627,8 @@ mpm_status mpm_scene_destroy(mpm_scene* s) {
   if (!s) return MPM_ERR_ARG;
   cudaStreamSynchronize(s->ctx->stream);
   free_rollout(s);
-  for (auto& row : s->graphs)
-    for (auto& g : row)
-      if (g.exec) cudaGraphExecDestroy(g.exec);
+  invalidate_graphs(s);
+  tune_release(s);
   for (void* p : s->allocs) cudaFree(p);
   for (auto& t : s->tables)
     if (t.dev) cudaFree(t.dev);
@@ -790,8 +808,7 @@ mpm_status mpm_scene_create(mpm_ctx* c, const mpm_scene_desc* d, mpm_scene** out
   cp.whole = 1;
   b.scene_pbase = pbase;
   b.tile_scene = tile_scene;
-  b.max_ctas = c->sm_count * 4;
-  b.p2g_block = 256;
+  default_launch(b, c->sm_count);
   cudaStream_t stream = c->stream;
   TRY(cuda_fail(cudaMemsetAsync(b.tile_count, 0, sizeof(uint32_t) * p.n_tiles, stream)));
   TRY(cuda_fail(cudaMemsetAsync(b.tile_fill, 0, sizeof(uint32_t) * p.n_tiles, stream)));
@@ -854,6 +871,7 @@ mpm_status mpm_scene_create(mpm_ctx* c, const mpm_scene_desc* d, mpm_scene** out
   TRY(upload_table(s, 0, t0));
   s->hsel[PH_STEP].table = s->tables[0].dev;
   TRY(upload_sel(s));
+  TRY(tune_init(s));
   TRY(enqueue_keys(s, PH_STEP, stream));
   TRY(read_status(s));
 #undef ALLOC

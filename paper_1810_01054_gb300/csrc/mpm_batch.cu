@@ -179,8 +179,8 @@ mpm_status compose(mpm_batch* B, SubBatch& sb) {
   sb.b.scene_pbase = sb.pbase;
   sb.b.total_particles = particles;
   sb.b.total_tiles = tiles;
-  sb.b.max_ctas = B->ctx->sm_count * 4;
-  sb.b.p2g_block = 256;
+  default_launch(sb.b, B->ctx->sm_count);
+  tune_apply_cached(sb.b, B->dim);
   sb.need_keys = true;
   return MPM_OK;
 }

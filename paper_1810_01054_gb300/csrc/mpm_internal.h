@@ -84,6 +84,16 @@ struct SelectPar {
   float* act;
 };
 
+// Tile kernels whose launch shape (CTAs per SM of the persistent grid, threads per CTA) is
+// chosen per workload by the autotuner (mpm_tune.cu).
+enum TileKernel { TK_P2G = 0, TK_G2P = 1, TK_P2G_ADJ = 2, TK_ADJ_GATHER = 3, TK_COUNT = 4 };
+struct TileLaunch {
+  int ctas_per_sm;
+  int threads;
+};
+// Launch shapes used when nothing was tuned: four CTAs per SM of 256 threads.
+constexpr TileLaunch kDefaultLaunch{4, 256};
+
 // One batch of scenes of equal dimension that advance together.
 struct BatchDev {
   ScenePar* scenes;     // device [n_scenes]
@@ -103,9 +113,15 @@ struct BatchDev {
   float4* partial;      // [total_tiles * BLOCK_NODES] node blocks of P2G
   float4* partial_b;    // [total_tiles * BLOCK_NODES] node blocks of the adjoint scatter
   float* gpartial;      // [total_tiles * MAX_GROUPS] per active tile group sums of dL/da
-  int max_ctas;         // persistent-grid size for the tile kernels
-  int p2g_block;        // threads per CTA of the tile kernels (autotuned)
+  int sm_count;                 // SMs of the device
+  TileLaunch launch[TK_COUNT];  // launch shape of each tile kernel
 };
+
+// Sets every tile kernel of b to the default launch shape.
+inline void default_launch(BatchDev& b, int sm_count) {
+  b.sm_count = sm_count;
+  for (int k = 0; k < TK_COUNT; ++k) b.launch[k] = kDefaultLaunch;
+}
 
 // ---------------------------------------------------------------------------- launchers
 // Sets the kernels' launch attributes (large dynamic shared memory); once per process/device.

@@ -947,8 +947,8 @@ struct G2PCfg {
   static constexpr int NP = Cfg<D>::XF_PLANES;
 };
 
-template <int D>
-__global__ void __launch_bounds__(256, 3) k_g2p(BatchDev b) {
+template <int D, int T>
+__global__ void __launch_bounds__(T, 768 / T) k_g2p(BatchDev b) {
   pdl_enter();
   using K = G2PCfg<D>;
   constexpr int B = Cfg<D>::B, NB = Cfg<D>::BLOCK_NODES, BN = Cfg<D>::BN;
@@ -1334,11 +1334,17 @@ cudaError_t configure_kernels() {
   return p2g_configure<3, true>();
 }
 
+// Persistent-grid size of tile kernel k: its CTAs per SM times the SMs, at most one per tile.
+static int tile_grid(const BatchDev& b, int k) {
+  const int g = b.launch[k].ctas_per_sm * b.sm_count;
+  const int grid = g < b.total_tiles ? g : b.total_tiles;
+  return grid < 1 ? 1 : grid;
+}
+
 template <int D, bool ADJ>
 static cudaError_t p2g_impl(const BatchDev& b, cudaStream_t s) {
   using K = P2GCfg<D, ADJ>;
-  int grid = b.max_ctas < b.total_tiles ? b.max_ctas : b.total_tiles;
-  if (grid < 1) grid = 1;
+  const int grid = tile_grid(b, ADJ ? TK_P2G_ADJ : TK_P2G);
   launch_pdl(k_p2g<D, ADJ>, dim3(grid), dim3(K::THREADS), K::SMEM, s, b);
   count_launches(1);
   return cudaGetLastError();
@@ -1351,17 +1357,18 @@ cudaError_t launch_p2g(const BatchDev& b, bool with_adjoint, cudaStream_t s) {
 
 template <int D>
 cudaError_t launch_g2p(const BatchDev& b, cudaStream_t s) {
-  int grid = b.max_ctas < b.total_tiles ? b.max_ctas : b.total_tiles;
-  if (grid < 1) grid = 1;
-  launch_pdl(k_g2p<D>, dim3(grid), dim3(256), 0, s, b);
+  const int grid = tile_grid(b, TK_G2P);
+  if (b.launch[TK_G2P].threads == 128)
+    launch_pdl(k_g2p<D, 128>, dim3(grid), dim3(128), 0, s, b);
+  else
+    launch_pdl(k_g2p<D, 256>, dim3(grid), dim3(256), 0, s, b);
   count_launches(1);
   return cudaGetLastError();
 }
 
 template <int D>
 cudaError_t launch_adj_gather(const BatchDev& b, cudaStream_t s) {
-  int grid = b.max_ctas < b.total_tiles ? b.max_ctas : b.total_tiles;
-  if (grid < 1) grid = 1;
+  const int grid = tile_grid(b, TK_ADJ_GATHER);
   launch_pdl(k_adj_gather<D>, dim3(grid), dim3(256), 0, s, b);
   count_launches(1);
   return cudaGetLastError();

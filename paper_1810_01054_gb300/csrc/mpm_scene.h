@@ -40,6 +40,21 @@ struct Graph {
   long long kernels = 0;
 };
 
+// Autotuner state of a scene (mpm_tune.cu): which tile kernels are still trying candidate launch
+// shapes, the candidate under trial, and the best time seen per kernel.
+struct TuneState {
+  int mode = 1;                         // MPM_TUNE_*
+  bool pending[gbmpm::TK_COUNT] = {};   // kernel still being tried
+  bool tuned[gbmpm::TK_COUNT] = {};     // shape came from the cache or from trials
+  int cand[gbmpm::TK_COUNT] = {};       // candidate under trial
+  int rep[gbmpm::TK_COUNT] = {};        // timed launches of it so far
+  int best[gbmpm::TK_COUNT] = {};
+  float cur_ms[gbmpm::TK_COUNT] = {};
+  float best_ms[gbmpm::TK_COUNT] = {};
+  bool timing = false;                  // the step being enqueued records the events below
+  cudaEvent_t ev[gbmpm::TK_COUNT][2] = {};
+};
+
 struct mpm_scene {
   mpm_ctx* ctx = nullptr;
   int dim = 0, N = 0, npad = 0, G = 0, nparams = 0, impl = 0, n_nodes = 0;
@@ -79,6 +94,7 @@ struct mpm_scene {
   // staging scratch
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
+  TuneState tune;
 };
 
 
@@ -93,4 +109,34 @@ mpm_status finish_backward(mpm_scene* s, float* gx0, float* gv0, float* gC0, flo
 mpm_status set_counter(mpm_scene* s, int* dctr, int value);
 mpm_status read_status(mpm_scene* s);
 mpm_status scene_sync_status(mpm_scene* s);
+
+// One step of phase ph enqueued on st (mpm_api.cu); graphs are not used.
+mpm_status enqueue_step(mpm_scene* s, int ph, cudaStream_t st);
+// Drops the scene's captured graphs (they are captured again with the current launch shapes).
+void invalidate_graphs(mpm_scene* s);
+
+// Autotuner (mpm_tune.cu).
+// Looks the scene's workload up in the cache, or arms trials for its tile kernels (mode AUTO/FORCE).
+mpm_status tune_init(mpm_scene* s);
+void tune_release(mpm_scene* s);
+// True while a tile kernel that phase ph launches is still being tried.
+bool tune_wants(const mpm_scene* s, int ph);
+// One directly-launched step of phase ph with the candidate shapes under trial, timed.
+mpm_status tune_step(mpm_scene* s, int ph);
+// Shapes of the cache entry of a batch's key, if there is one (defaults stay otherwise).
+void tune_apply_cached(BatchDev& b, int dim);
+// Records CUDA events around one launch of tile kernel k while its shape is being tried.
+struct TuneScope {
+  mpm_scene* s;
+  int k;
+  cudaStream_t st;
+  bool on;
+  TuneScope(mpm_scene* scene, int kernel, cudaStream_t stream)
+      : s(scene), k(kernel), st(stream), on(scene->tune.timing && scene->tune.pending[kernel]) {
+    if (on) cudaEventRecord(s->tune.ev[k][0], st);
+  }
+  ~TuneScope() {
+    if (on) cudaEventRecord(s->tune.ev[k][1], st);
+  }
+};
 }  // namespace gbmpm

@@ -127,9 +127,18 @@ _SIGS = {
     "mpm_profile_read": [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)],
     "mpm_launch_count": [C.POINTER(C.c_longlong)],
     "mpm_step_noalloc": [C.POINTER(NoAllocStep), C.c_void_p],
+    "mpm_scene_set_tuning": [C.c_void_p, C.c_int],
+    "mpm_scene_launch": [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)],
+    "mpm_tune_cache_lookup": [C.c_int, C.c_longlong, C.c_longlong, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)],
+    "mpm_tune_cache_store": [C.c_int, C.c_longlong, C.c_longlong, C.c_int, C.POINTER(C.c_int)],
+    "mpm_tune_cache_save": [C.c_char_p],
+    "mpm_tune_cache_load": [C.c_char_p],
 }
 
 K_SORT, K_P2G, K_GRID, K_G2P, K_P2G_ADJ, K_GRID_ADJ, K_ADJ_GATHER, K_CTRL, K_PLAIN = range(9)
+TUNE_OFF, TUNE_AUTO, TUNE_FORCE = 0, 1, 2
+TK_P2G, TK_G2P, TK_P2G_ADJ, TK_ADJ_GATHER = range(4)
+TILE_KERNELS = ["p2g", "g2p", "p2g_adj", "adj_gather"]
 KERNEL_NAMES = ["sort", "p2g", "grid", "g2p", "p2g_adj", "grid_adj", "adj_gather", "ctrl", "plain"]
 
 
@@ -137,6 +146,28 @@ def launch_count() -> int:
     n = C.c_longlong()
     _check(lib().mpm_launch_count(C.byref(n)), "mpm_launch_count")
     return int(n.value)
+
+
+def tune_cache_lookup(dim: int, particles: int, grid_tiles: int, sm_count: int):
+    """Launch shapes [(ctas_per_sm, threads)] * 4 of the cache entry of this workload key, or None."""
+    shape, found = (C.c_int * 8)(), C.c_int(0)
+    _check(lib().mpm_tune_cache_lookup(int(dim), int(particles), int(grid_tiles), int(sm_count), shape,
+                                       C.byref(found)), "mpm_tune_cache_lookup")
+    return [(shape[2 * k], shape[2 * k + 1]) for k in range(4)] if found.value else None
+
+
+def tune_cache_store(dim: int, particles: int, grid_tiles: int, sm_count: int, shapes):
+    flat = (C.c_int * 8)(*[int(v) for sh in shapes for v in sh])
+    _check(lib().mpm_tune_cache_store(int(dim), int(particles), int(grid_tiles), int(sm_count), flat),
+           "mpm_tune_cache_store")
+
+
+def tune_cache_save(path: str):
+    _check(lib().mpm_tune_cache_save(os.fsencode(path)), "mpm_tune_cache_save")
+
+
+def tune_cache_load(path: str):
+    _check(lib().mpm_tune_cache_load(os.fsencode(path)), "mpm_tune_cache_load")
 
 
 def lib():
@@ -306,6 +337,17 @@ class Scene:
     # ------------------------------------------------------------------ forward
     def step(self, n: int = 1):
         _check(lib().mpm_step(self.handle, int(n)), "mpm_step")
+
+    def set_tuning(self, mode: int):
+        """TUNE_OFF (default shapes), TUNE_AUTO (cache, else trials: the default) or TUNE_FORCE."""
+        _check(lib().mpm_scene_set_tuning(self.handle, int(mode)), "mpm_scene_set_tuning")
+
+    def launch(self, kernel: int):
+        """(ctas_per_sm, threads, tuned) of tile kernel TK_*."""
+        a, t, d = C.c_int(), C.c_int(), C.c_int()
+        _check(lib().mpm_scene_launch(self.handle, int(kernel), C.byref(a), C.byref(t), C.byref(d)),
+               "mpm_scene_launch")
+        return a.value, t.value, bool(d.value)
 
     def rollout(self, n_steps: int, ckpt_interval: int = 0, mem_budget: int = 0):
         _check(lib().mpm_rollout(self.handle, int(n_steps), int(ckpt_interval), C.c_size_t(int(mem_budget))),
