@@ -30,7 +30,7 @@ typedef struct {
   double dx, dt;
   double gravity[3];
   double E, nu;       // Young's modulus, Poisson ratio (Lame parameters by the textbook map)
-  double p_mass, p_vol;  // m_p and V_p^0 (uniform within a scene)
+  double p_mass, p_vol;  // m_p (unless p_m below is given) and V_p^0 (uniform within a scene)
   int bc_type;        // 0 sticky, 1 slip with Coulomb friction c (S5)
   int bc_width;       // boundary band width in nodes
   double friction_c;
@@ -42,6 +42,8 @@ typedef struct {
   int ctrl_hidden;
   double ctrl_freq;
   double ctrl_scale;
+  const double* p_E;      // [N] per-particle Young's modulus, NULL = E for every particle
+  const double* p_m;      // [N] per-particle mass, NULL = p_mass for every particle
 } oracle_scene;
 
 }  // extern "C"
@@ -115,10 +117,17 @@ M3 inverse(const M3& F, int d) {
   return R;
 }
 
-void lame(const oracle_scene* s, double* mu, double* la) {
-  *mu = s->E / (2.0 * (1.0 + s->nu));
-  *la = s->E * s->nu / ((1.0 + s->nu) * (1.0 - 2.0 * s->nu));
+// Lame parameters from (E, nu) by the textbook map; per particle when the scene carries E_p.
+// dmu/dE and dlambda/dE are the same map at E = 1.
+void lame_E(double E, double nu, double* mu, double* la) {
+  *mu = E / (2.0 * (1.0 + nu));
+  *la = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
 }
+void lame(const oracle_scene* s, double* mu, double* la) { lame_E(s->E, s->nu, mu, la); }
+void lame_of(const oracle_scene* s, int p, double* mu, double* la) {
+  lame_E(s->p_E ? s->p_E[p] : s->E, s->nu, mu, la);
+}
+double mass_of(const oracle_scene* s, int p) { return s->p_m ? s->p_m[p] : s->p_mass; }
 
 // Neo-Hookean first Piola-Kirchhoff stress P = d psi / dF = mu (F - F^{-T}) + lambda ln J F^{-T}.
 M3 neohookean_P(const M3& F, int d, double mu, double la) {
@@ -353,7 +362,7 @@ bool particle_stress(const oracle_scene* s, const double* act, int p, const doub
                      const double* C_in, ParticleP2G* q) {
   int d = s->dim;
   double mu, la;
-  lame(s, &mu, &la);
+  lame_of(s, p, &mu, &la);
   q->F = load_mat(F_in, d);
   q->J = det(q->F, d);
   if (!(q->J > 0.0)) return false;
@@ -373,7 +382,7 @@ bool particle_stress(const oracle_scene* s, const double* act, int p, const doub
   M3 PFt = matmul(P, transpose(q->F, d), d);
   M3 C = load_mat(C_in, d);
   for (int i = 0; i < d; ++i)
-    for (int j = 0; j < d; ++j) q->G.a[i][j] = k * PFt.a[i][j] + s->p_mass * C.a[i][j];
+    for (int j = 0; j < d; ++j) q->G.a[i][j] = k * PFt.a[i][j] + mass_of(s, p) * C.a[i][j];
   return true;
 }
 
@@ -407,11 +416,11 @@ int forward_grid(const oracle_scene* s, const double* act, const double* x, cons
       int lin = node_index(s, idx);
       double dpos[3];
       for (int a = 0; a < d; ++a) dpos[a] = idx[a] * s->dx - x[p * d + a];
-      g->m[lin] += N_ * s->p_mass;
+      g->m[lin] += N_ * mass_of(s, p);
       for (int a = 0; a < d; ++a) {
         double Gd = 0;
         for (int b = 0; b < d; ++b) Gd += q.G.a[a][b] * dpos[b];
-        g->p[size_t(lin) * d + a] += N_ * (s->p_mass * v[p * d + a] + Gd);
+        g->p[size_t(lin) * d + a] += N_ * (mass_of(s, p) * v[p * d + a] + Gd);
       }
     }
   }
@@ -659,14 +668,19 @@ int oracle_step(const oracle_scene* s, const double* act, const double* x, const
 // One reverse step.  Given state n and the adjoints of state n+1 (gx1, gv1, gC1, gF1: total
 // derivatives of the loss with respect to x, v, C, F of step n+1), writes the adjoints of
 // state n and gact[g] = dL/da_g(t_n).  Letters refer to the supplement.
-int oracle_step_adjoint(const oracle_scene* s, const double* act, const double* x, const double* v,
-                        const double* C, const double* F, const double* gx1, const double* gv1,
-                        const double* gC1, const double* gF1, double* gx0, double* gv0, double* gC0,
-                        double* gF0, double* gact) {
+//
+// Material gradients (optional gE, gm, per particle, this step's contribution): E_p enters only P
+// through mu_p and lambda_p, so dL/dE_p = (F - F^{-T}) : Pbar dmu/dE + ln J (F^{-T} : Pbar)
+// dlambda/dE with Pbar of (G); m_p enters only P2G (Eqs. 3, 4: m_i, and p_i through m v_p and
+// the m C_p term of G), so dL/dm_p = sum_i N_ip (mbar_i + pbar_i . (v_p + C_p (x_i - x_p))).
+int oracle_step_adjoint_mat(const oracle_scene* s, const double* act, const double* x, const double* v,
+                            const double* C, const double* F, const double* gx1, const double* gv1,
+                            const double* gC1, const double* gF1, double* gx0, double* gv0, double* gC0,
+                            double* gF0, double* gact, double* gE, double* gm_p) {
   int d = s->dim, N = s->n_particles, nn = n_nodes(s), ns = n_stencil(d);
   if (d != 2 && d != 3) return -1;
-  double mu, la;
-  lame(s, &mu, &la);
+  double dmu_dE, dla_dE;
+  lame_E(1.0, s->nu, &dmu_dE, &dla_dE);
   Grid g;
   int rc = forward_grid(s, act, x, v, C, F, &g, true);
   if (rc) return rc;
@@ -728,6 +742,11 @@ int oracle_step_adjoint(const oracle_scene* s, const double* act, const double* 
     make_stencil(s, x + p * d, &st);
     ParticleP2G q;
     particle_stress(s, act, p, F + p * d * d, C + p * d * d, &q);
+    const double mp = mass_of(s, p);
+    double mu, la;
+    lame_of(s, p, &mu, &la);
+    const M3 Cp = load_mat(C + p * d * d, d);
+    double gmass = 0.0;  // dL/dm_p of this step
     double gvp[3] = {0, 0, 0}, gxp[3] = {0, 0, 0};
     M3 Gbar = zero3();
     M3 Cn = zero3();  // C^{n+1}, recomputed for (H)
@@ -746,7 +765,15 @@ int oracle_step_adjoint(const oracle_scene* s, const double* act, const double* 
       for (int a = 0; a < d; ++a)
         for (int b = 0; b < d; ++b) Cn.a[a][b] += Dinv * N_ * vs[a] * dpos[b];
       // (F)
-      for (int a = 0; a < d; ++a) gvp[a] += N_ * s->p_mass * pb[a];
+      for (int a = 0; a < d; ++a) gvp[a] += N_ * mp * pb[a];
+      // m_p in m_i and in p_i = N (m_p v_p + m_p C_p (x_i - x_p) + stress term)
+      double pvc = 0;
+      for (int a = 0; a < d; ++a) {
+        double Cd = 0;
+        for (int b = 0; b < d; ++b) Cd += Cp.a[a][b] * dpos[b];
+        pvc += pb[a] * (v[p * d + a] + Cd);
+      }
+      gmass += N_ * (mb + pvc);
       // Gbar = sum_i N pbar_i (x_i - x_p)^T, shared by (G), (H), (I)
       for (int a = 0; a < d; ++a)
         for (int b = 0; b < d; ++b) Gbar.a[a][b] += N_ * pb[a] * dpos[b];
@@ -760,7 +787,7 @@ int oracle_step_adjoint(const oracle_scene* s, const double* act, const double* 
       for (int a = 0; a < d; ++a) {
         double Gd = 0;
         for (int b = 0; b < d; ++b) Gd += q.G.a[a][b] * dpos[b];
-        pmom += pb[a] * (s->p_mass * v[p * d + a] + Gd);
+        pmom += pb[a] * (mp * v[p * d + a] + Gd);
       }
       for (int al = 0; al < d; ++al) {
         double CtV = 0, GtP = 0;
@@ -769,13 +796,13 @@ int oracle_step_adjoint(const oracle_scene* s, const double* act, const double* 
           GtP += q.G.a[b][al] * pb[b];
         }
         gxp[al] += dN[al] * vbv + Dinv * (-N_ * CtV + dN[al] * vCd) + dN[al] * pmom - N_ * GtP +
-                   s->p_mass * mb * dN[al];
+                   mp * mb * dN[al];
       }
     }
     // (I) Cbar = m Gbar
     M3 gCp = zero3();
     for (int a = 0; a < d; ++a)
-      for (int b = 0; b < d; ++b) gCp.a[a][b] = s->p_mass * Gbar.a[a][b];
+      for (int b = 0; b < d; ++b) gCp.a[a][b] = mp * Gbar.a[a][b];
     // (G) Pbar = -Dinv dt V0 Gbar F
     M3 GF = matmul(Gbar, q.F, d);
     M3 Pbar = zero3();
@@ -788,6 +815,18 @@ int oracle_step_adjoint(const oracle_scene* s, const double* act, const double* 
     M3 gFn = load_mat(gF1 + p * d * d, d);
     M3 t1 = matmul(transpose(A, d), gFn, d);
     M3 t2 = neohookean_hessian_apply(q.F, Pbar, d, mu, la);
+    if (gE) {  // dP/dmu = F - F^{-T}, dP/dlambda = ln J F^{-T}
+      M3 FinvT = transpose(inverse(q.F, d), d);
+      double gmu = 0, gla = 0;
+      for (int a = 0; a < d; ++a)
+        for (int b = 0; b < d; ++b) {
+          gmu += (q.F.a[a][b] - FinvT.a[a][b]) * Pbar.a[a][b];
+          gla += FinvT.a[a][b] * Pbar.a[a][b];
+        }
+      gla *= std::log(q.J);
+      gE[p] = gmu * dmu_dE + gla * dla_dE;
+    }
+    if (gm_p) gm_p[p] = gmass;
     M3 t3 = matmul(Pbar, transpose(q.sig, d), d);
     M3 t4 = matmul(transpose(Gbar, d), q.P, d);
     M3 gFp = zero3();
@@ -809,6 +848,14 @@ int oracle_step_adjoint(const oracle_scene* s, const double* act, const double* 
     store_mat(gF0 + p * d * d, gFp, d);
   }
   return 0;
+}
+
+int oracle_step_adjoint(const oracle_scene* s, const double* act, const double* x, const double* v,
+                        const double* C, const double* F, const double* gx1, const double* gv1,
+                        const double* gC1, const double* gF1, double* gx0, double* gv0, double* gC0,
+                        double* gF0, double* gact) {
+  return oracle_step_adjoint_mat(s, act, x, v, C, F, gx1, gv1, gC1, gF1, gx0, gv0, gC0, gF0, gact, nullptr,
+                                 nullptr);
 }
 
 // Forward rollout storing every state (the paper's "memo" of Section III): xs [(T+1)][N][d],
@@ -836,11 +883,12 @@ int oracle_rollout(const oracle_scene* s, const double* params, int n_steps, con
 
 // Rollout-level chain rule (Section III): from seeds on the final state to the adjoints of the
 // initial state and of the controller parameters, which are used at every step.
-int oracle_backward(const oracle_scene* s, const double* params, int n_params, int n_steps,
-                    const double* xs, const double* vs, const double* Cs, const double* Fs,
-                    const double* acts, const double* gxT, const double* gvT, const double* gCT,
-                    const double* gFT, double* gx0, double* gv0, double* gC0, double* gF0,
-                    double* gparams) {
+// With gE, gm: dL/dE_p and dL/dm_p summed over every step (the material is the same at all steps).
+int oracle_backward_mat(const oracle_scene* s, const double* params, int n_params, int n_steps,
+                        const double* xs, const double* vs, const double* Cs, const double* Fs,
+                        const double* acts, const double* gxT, const double* gvT, const double* gCT,
+                        const double* gFT, double* gx0, double* gv0, double* gC0, double* gF0,
+                        double* gparams, double* gE, double* gm) {
   int d = s->dim, N = s->n_particles, G = s->n_groups;
   size_t sx = size_t(N) * d, sm = size_t(N) * d * d;
   std::vector<double> ax(sx, 0.0), av(sx, 0.0), aC(sm, 0.0), aF(sm, 0.0);
@@ -849,12 +897,17 @@ int oracle_backward(const oracle_scene* s, const double* params, int n_params, i
   if (gCT) std::memcpy(aC.data(), gCT, sizeof(double) * sm);
   if (gFT) std::memcpy(aF.data(), gFT, sizeof(double) * sm);
   for (int i = 0; i < n_params; ++i) gparams[i] = 0.0;
-  std::vector<double> bx(sx), bv(sx), bC(sm), bF(sm), gact(G > 0 ? G : 1);
+  for (int p = 0; p < N && gE; ++p) gE[p] = 0.0;
+  for (int p = 0; p < N && gm; ++p) gm[p] = 0.0;
+  std::vector<double> bx(sx), bv(sx), bC(sm), bF(sm), gact(G > 0 ? G : 1), sE(gE ? N : 0), sm_(gm ? N : 0);
   for (int n = n_steps - 1; n >= 0; --n) {
-    int rc = oracle_step_adjoint(s, acts + size_t(n) * G, xs + n * sx, vs + n * sx, Cs + n * sm, Fs + n * sm,
-                                 ax.data(), av.data(), aC.data(), aF.data(), bx.data(), bv.data(), bC.data(),
-                                 bF.data(), gact.data());
+    int rc = oracle_step_adjoint_mat(s, acts + size_t(n) * G, xs + n * sx, vs + n * sx, Cs + n * sm,
+                                     Fs + n * sm, ax.data(), av.data(), aC.data(), aF.data(), bx.data(),
+                                     bv.data(), bC.data(), bF.data(), gact.data(), gE ? sE.data() : nullptr,
+                                     gm ? sm_.data() : nullptr);
     if (rc) return rc;
+    for (int p = 0; p < N && gE; ++p) gE[p] += sE[p];
+    for (int p = 0; p < N && gm; ++p) gm[p] += sm_[p];
     rc = oracle_controller_adjoint(s, params, n, xs + n * sx, gact.data(), gparams, bx.data());
     if (rc) return rc;
     ax.swap(bx);
@@ -867,6 +920,15 @@ int oracle_backward(const oracle_scene* s, const double* params, int n_params, i
   std::memcpy(gC0, aC.data(), sizeof(double) * sm);
   std::memcpy(gF0, aF.data(), sizeof(double) * sm);
   return 0;
+}
+
+int oracle_backward(const oracle_scene* s, const double* params, int n_params, int n_steps,
+                    const double* xs, const double* vs, const double* Cs, const double* Fs,
+                    const double* acts, const double* gxT, const double* gvT, const double* gCT,
+                    const double* gFT, double* gx0, double* gv0, double* gC0, double* gF0,
+                    double* gparams) {
+  return oracle_backward_mat(s, params, n_params, n_steps, xs, vs, Cs, Fs, acts, gxT, gvT, gCT, gFT, gx0, gv0,
+                             gC0, gF0, gparams, nullptr, nullptr);
 }
 
 // Constitutive helpers exposed for the constitutive pins: P(F) and H_psi[Pbar].

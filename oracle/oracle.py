@@ -52,6 +52,8 @@ class _Scene(C.Structure):
         ("ctrl_hidden", C.c_int),
         ("ctrl_freq", C.c_double),
         ("ctrl_scale", C.c_double),
+        ("p_E", C.c_void_p),
+        ("p_m", C.c_void_p),
     ]
 
 
@@ -70,9 +72,9 @@ def lib():
     with _lock:
         if _lib is None:
             _lib = C.CDLL(build())
-            for name in ("oracle_step", "oracle_step_adjoint", "oracle_controller",
+            for name in ("oracle_step", "oracle_step_adjoint", "oracle_step_adjoint_mat", "oracle_controller",
                          "oracle_controller_adjoint", "oracle_rollout", "oracle_backward",
-                         "oracle_neohookean", "oracle_bc"):
+                         "oracle_backward_mat", "oracle_neohookean", "oracle_bc"):
                 getattr(_lib, name).restype = C.c_int
     return _lib
 
@@ -115,6 +117,11 @@ class Scene:
         s.group, s.act_dir = _p(self._group), _p(self._dir)
         s.ctrl_type, s.ctrl_hidden = int(spec.ctrl_type), int(spec.ctrl_hidden)
         s.ctrl_freq, s.ctrl_scale = float(spec.ctrl_freq), float(spec.ctrl_scale)
+        # optional per-particle Young's modulus and mass (NULL: the scene's E and p_mass)
+        E_arr, m_arr = getattr(spec, "E_arr", None), getattr(spec, "mass_arr", None)
+        self._E = None if E_arr is None else _f64(E_arr).ravel()
+        self._m = None if m_arr is None else _f64(m_arr).ravel()
+        s.p_E, s.p_m = _p(self._E), _p(self._m)
         self.struct = s
         self.params = _f64(spec.ctrl_params).ravel()
         self.n_nodes = int(np.prod(ng[:d]))
@@ -164,7 +171,8 @@ class Scene:
             return (x1, v1, C1, F1), (gm, gv)
         return x1, v1, C1, F1
 
-    def step_adjoint(self, act, state, adj1):
+    def step_adjoint(self, act, state, adj1, material=False):
+        """((gx0, gv0, gC0, gF0), gact), plus (gE, gm) of this step with material=True."""
         d, N = self.dim, self.N
         act = _f64(act) if self.G else np.zeros(1)
         x, v, Cm, F = (_f64(a) for a in state)
@@ -172,9 +180,14 @@ class Scene:
         gx0, gv0 = np.empty((N, d)), np.empty((N, d))
         gC0, gF0 = np.empty((N, d, d)), np.empty((N, d, d))
         gact = np.zeros(max(self.G, 1))
-        rc = lib().oracle_step_adjoint(self.ref, _p(act), _p(x), _p(v), _p(Cm), _p(F), _p(gx1), _p(gv1), _p(gC1),
-                                       _p(gF1), _p(gx0), _p(gv0), _p(gC0), _p(gF0), _p(gact))
+        gE = np.empty(N) if material else None
+        gm = np.empty(N) if material else None
+        rc = lib().oracle_step_adjoint_mat(self.ref, _p(act), _p(x), _p(v), _p(Cm), _p(F), _p(gx1), _p(gv1),
+                                           _p(gC1), _p(gF1), _p(gx0), _p(gv0), _p(gC0), _p(gF0), _p(gact), _p(gE),
+                                           _p(gm))
         self._check(rc, "step adjoint")
+        if material:
+            return (gx0, gv0, gC0, gF0), gact[: self.G], (gE, gm)
         return (gx0, gv0, gC0, gF0), gact[: self.G]
 
     def rollout(self, n_steps, state0=None, params=None):
@@ -190,9 +203,9 @@ class Scene:
         self._check(rc, "rollout")
         return xs, vs, Cs, Fs, acts[:n_steps, :G]
 
-    def backward(self, traj, seeds, params=None):
+    def backward(self, traj, seeds, params=None, material=False):
         """traj from rollout(); seeds = (gxT, gvT, gCT, gFT) with None for zero.
-        Returns (gx0, gv0, gC0, gF0, gparams)."""
+        Returns (gx0, gv0, gC0, gF0, gparams), plus (dL/dE_p, dL/dm_p) with material=True."""
         d, N, G = self.dim, self.N, self.G
         params = self.params if params is None else _f64(params).ravel()
         xs, vs, Cs, Fs, acts = traj
@@ -206,11 +219,15 @@ class Scene:
         gp = np.zeros(max(params.size, 1))
         if G == 0:
             acts_p = np.zeros((max(T, 1), 1))
-        rc = lib().oracle_backward(self.ref, _p(params), int(params.size), int(T), _p(_f64(xs)), _p(_f64(vs)),
-                                   _p(_f64(Cs)), _p(_f64(Fs)), _p(acts_p if G else np.zeros(1)),
-                                   _p(sd[0]), _p(sd[1]), _p(sd[2]), _p(sd[3]), _p(gx0), _p(gv0), _p(gC0),
-                                   _p(gF0), _p(gp))
+        gE = np.empty(N) if material else None
+        gm = np.empty(N) if material else None
+        rc = lib().oracle_backward_mat(self.ref, _p(params), int(params.size), int(T), _p(_f64(xs)),
+                                       _p(_f64(vs)), _p(_f64(Cs)), _p(_f64(Fs)), _p(acts_p if G else np.zeros(1)),
+                                       _p(sd[0]), _p(sd[1]), _p(sd[2]), _p(sd[3]), _p(gx0), _p(gv0), _p(gC0),
+                                       _p(gF0), _p(gp), _p(gE), _p(gm))
         self._check(rc, "backward")
+        if material:
+            return gx0, gv0, gC0, gF0, gp[: params.size], gE, gm
         return gx0, gv0, gC0, gF0, gp[: params.size]
 
 

@@ -74,6 +74,8 @@ class SceneSpec:
     ctrl_scale: float = 1.0
     n_steps: int = 1
     ckpt_interval: int = 0
+    E_arr: Optional[np.ndarray] = None     # [N] per-particle Young's modulus (None: E for all)
+    mass_arr: Optional[np.ndarray] = None  # [N] per-particle mass (None: p_mass for all)
 
     @property
     def n_particles(self) -> int:
@@ -90,6 +92,17 @@ class SceneSpec:
                 d[k] = v.copy()
         d.update(changes)
         return SceneSpec(**d)
+
+
+def with_material(spec: SceneSpec, seed: int, spread: float = 0.2) -> SceneSpec:
+    """Copy of spec with per-particle Young's modulus and mass, each the scene's value times an
+    independent factor uniform in [1 - spread, 1 + spread] (seeded).  The largest E_p must still
+    satisfy the explicit-integration limit of the scene's dt."""
+    rng = np.random.default_rng(seed)
+    N = spec.n_particles
+    E = spec.E * rng.uniform(1.0 - spread, 1.0 + spread, N)
+    m = spec.p_mass * rng.uniform(1.0 - spread, 1.0 + spread, N)
+    return spec.copy(E_arr=E, mass_arr=m, name=spec.name + "+material")
 
 
 def n_ctrl_params(ctrl_type: int, n_groups: int, dim: int, hidden: int) -> int:
