@@ -43,6 +43,9 @@ ALGO_BYTES = {
     "p2g": (48 + 4, 96 + 4),                             # state in, group
     "g2p": (24 + 48, 48 + 96),                           # x, F in; state out
 }
+# with per-particle material: E_p and m_p read by the P2G kernels and the adjoint gather, and the
+# (dL/dE_p, dL/dm_p) accumulator read and written by the adjoint gather
+MATERIAL_EXTRA = {"adj_gather": 8 + 16, "p2g_adj": 8, "p2g": 8, "g2p": 0}
 
 
 def parse():
@@ -57,9 +60,15 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-material", action="store_true")
     ap.add_argument("--ncu", type=int, default=0, metavar="SIM_STEPS",
                     help="profiling mode: one short rollout of SIM_STEPS steps + reverse pass, no timing")
     return ap.parse_args()
+
+
+def material_variant(spec):
+    from paper_1810_01054_gb300 import scenes as S
+    return S.with_material(spec, 21)
 
 
 def workload(name, rank=0):
@@ -360,7 +369,8 @@ def measure(args, spec, rank, world, dev, stream, ctx, *, e2e=True, plain=True):
     dom = max(ALGO_BYTES, key=lambda kk: prof[kk][1])
     cnt, ms = prof[dom]
     hbm, src = peaks()
-    bpp = ALGO_BYTES[dom][0 if d == 2 else 1]
+    material = spec.E_arr is not None or spec.mass_arr is not None
+    bpp = ALGO_BYTES[dom][0 if d == 2 else 1] + (MATERIAL_EXTRA[dom] if material else 0)
     launch_ms = ms / max(cnt, 1)
     achieved = bpp * N / (launch_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
@@ -436,6 +446,15 @@ def run_ours(args, rank, world, local_rank):
         large = {"workload": lspec.name, "particles": lr["N"], "sim_steps": lr["T"], "value": lr["value"],
                  "value_fwd": lr["value_fwd"], "unit": UNIT, "ms_per_step": lr["tot_ms"] / args.steps,
                  "roofline": lr["roofline"], "kernel_share_of_profiled_step": lr["share"]}
+    material = None
+    if args.workload == "walker_2d" and not args.no_material:
+        # the same workload with per-particle Young's modulus and mass and their gradients
+        mspec = material_variant(spec)
+        mr = measure(args, mspec, rank, world, dev, stream, ctx, e2e=False, plain=False)
+        material = {"workload": mspec.name, "value": mr["value"], "value_fwd": mr["value_fwd"], "unit": UNIT,
+                    "ms_per_step": mr["tot_ms"] / args.steps, "roofline": mr["roofline"],
+                    "kernel_share_of_profiled_step": mr["share"],
+                    "gradients": "dL/dx0, v0, C0, F0, controller parameters, E_p, m_p"}
     serving = None
     if rank == 0 and not args.no_serve:
         serving = measure_serving(dev, stream)
@@ -455,7 +474,7 @@ def run_ours(args, rank, world, local_rank):
         "rollout_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
         "roofline": r["roofline"], "kernel_share_of_profiled_step": r["share"],
         "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": r["gpu_launches"], "clocks": r["clocks"],
-        "plain_form": r["plain"], "large_scene": large, "serving": serving,
+        "plain_form": r["plain"], "large_scene": large, "material": material, "serving": serving,
     }
     print(json.dumps(line), flush=True)
 

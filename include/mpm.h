@@ -144,6 +144,20 @@ mpm_status mpm_set_state(mpm_scene* scene, const float* x, const float* v, const
                          int step, int mem_space);
 /* Replaces the controller parameters (n must equal the scene's parameter count). */
 mpm_status mpm_set_ctrl_params(mpm_scene* scene, const float* params, int n, int mem_space);
+/* Per-particle material (an extension: the paper's co-design and inference examples treat
+ * material parameters as optimisation variables, Sections V-A and V-C).  E [N] Young's modulus and
+ * mass [N] per particle replace the descriptor's E and p_mass (NULL keeps the scene's value for
+ * every particle; both NULL returns to the uniform scene); nu and V^0 stay per scene.  Values must
+ * be finite and positive, and dt must satisfy dt <= dx sqrt(rho_p / E_p) for every particle
+ * (rho_p = m_p / V^0), else MPM_ERR_ARG and nothing changes.  Synchronises.  Invalidates an
+ * earlier rollout (run mpm_rollout again).  While per-particle material is set, mpm_backward also
+ * accumulates dL/dE_p and dL/dm_p over every reverse step:
+ *   dL/dE_p  = sum_n (F - F^-T) : Pbar dmu/dE + ln J (F^-T : Pbar) dlambda/dE   (Pbar of S4 (G))
+ *   dL/dm_p  = sum_n sum_i N_ip (mbar_i + pbar_i . (v_p + C_p (x_i - x_p)))   (S3 (D), (E))
+ * read with mpm_get_material_gradients (MPM_ERR_STATE without material or without a finished
+ * reverse pass; outputs on the host or the device per mem_space; NULL skips one). */
+mpm_status mpm_scene_set_material(mpm_scene* scene, const float* E, const float* mass, int mem_space);
+mpm_status mpm_get_material_gradients(mpm_scene* scene, float* gE, float* gm, int mem_space);
 /* Grid of the last forward step: mass m_i [nodes] and velocity v*_i [nodes][dim] after the
  * boundary condition (nodes never touched by a particle hold stale values for the tiled form). */
 mpm_status mpm_get_grid(mpm_scene* scene, float* m, float* v, int mem_space);

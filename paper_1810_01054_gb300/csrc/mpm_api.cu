@@ -470,6 +470,7 @@ mpm_status prepare_backward(mpm_scene* s, const float* gxT, const float* gvT, co
   CK(launch_pack(dim, N, s->npad, (const float*)a, (const float*)bv, (const float*)c, (const float*)f, s->adj[0],
                  s->d_status, st));
   CK(cudaMemsetAsync(s->ctrl.gparams, 0, sizeof(float) * std::max(1, s->nparams), st));
+  if (s->hp.gmat && N > 0) CK(cudaMemsetAsync(s->hp.gmat, 0, sizeof(float2) * size_t(N), st));
   // table 2: per segment the recompute records F_{sg,j} (state j -> j+1) and the reverse records
   // B_{sg,n,parity} (state n, adjoint buffers by parity); maps by global step
   std::vector<ScenePar> recs;
@@ -635,6 +636,8 @@ mpm_status mpm_scene_destroy(mpm_scene* s) {
   for (auto& m : s->maps)
     if (m.dev) cudaFree(m.dev);
   if (s->scratch) cudaFree(s->scratch);
+  for (void* q : {s->d_pE, s->d_pmass, s->d_gmat})
+    if (q) cudaFree(q);
   s->ctx->live.fetch_sub(1);
   delete s;
   return MPM_OK;
@@ -696,8 +699,15 @@ mpm_status mpm_scene_create(mpm_ctx* c, const mpm_scene_desc* d, mpm_scene** out
   p.dx = d->dx;
   p.inv_dx = 1.0f / d->dx;
   p.dt = d->dt;
-  p.mat.mu = float(double(d->E) / (2.0 * (1.0 + double(d->nu))));
-  p.mat.la = float(double(d->E) * double(d->nu) / ((1.0 + double(d->nu)) * (1.0 - 2.0 * double(d->nu))));
+  // Lame parameters as E x (per-unit-E factors) in FP32, the same route the kernels take for a
+  // per-particle E_p, so uniform per-particle arrays reproduce the uniform scene bit for bit
+  p.mu_per_E = float(1.0 / (2.0 * (1.0 + double(d->nu))));
+  p.la_per_E = float(double(d->nu) / ((1.0 + double(d->nu)) * (1.0 - 2.0 * double(d->nu))));
+  p.mat.mu = d->E * p.mu_per_E;
+  p.mat.la = d->E * p.la_per_E;
+  p.pE = nullptr;
+  p.pmass = nullptr;
+  p.gmat = nullptr;
   p.mass = d->p_mass;
   p.vol = d->p_vol;
   p.bc.type = d->bc_type;
@@ -992,6 +1002,70 @@ mpm_status mpm_set_ctrl_params(mpm_scene* s, const float* params, int n, int mem
   CK(cudaMemcpy(const_cast<float*>(s->ctrl.params), params, sizeof(float) * n,
                 mem_space == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
   return MPM_OK;
+}
+
+mpm_status mpm_scene_set_material(mpm_scene* s, const float* E, const float* mass, int mem_space) {
+  if (!s || (mem_space != 0 && mem_space != 1)) return MPM_ERR_ARG;
+  const int N = s->N;
+  CK(cudaStreamSynchronize(s->ctx->stream));
+  // host copies for validation: E_p > 0 and m_p > 0 finite, and the explicit-integration limit
+  // dt <= dx sqrt(rho_p / E_p) (C = 1, as at scene creation) at the stiffest, lightest particle
+  std::vector<float> hE, hm;
+  cudaMemcpyKind kin = mem_space == 1 ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+  if (E && N > 0) {
+    hE.resize(N);
+    CK(cudaMemcpy(hE.data(), E, sizeof(float) * N, kin));
+  }
+  if (mass && N > 0) {
+    hm.resize(N);
+    CK(cudaMemcpy(hm.data(), mass, sizeof(float) * N, kin));
+  }
+  double worst = 0.0;  // max E_p / rho_p
+  for (int p = 0; p < N && (E || mass); ++p) {
+    const double e = E ? double(hE[p]) : double(s->hp.mat.mu / s->hp.mu_per_E);
+    const double m = mass ? double(hm[p]) : double(s->hp.mass);
+    if (!(std::isfinite(e) && e > 0.0 && std::isfinite(m) && m > 0.0)) return MPM_ERR_ARG;
+    worst = std::max(worst, e / (m / double(s->hp.vol)));
+  }
+  if ((E || mass) && double(s->hp.dt) > double(s->hp.dx) / std::sqrt(worst) * (1.0 + 1e-6)) return MPM_ERR_ARG;
+  const size_t fb = sizeof(float) * std::max(N, 1);
+  if ((E || mass) && !s->d_gmat) {
+    CK(cudaMalloc(&s->d_pE, fb));
+    CK(cudaMalloc(&s->d_pmass, fb));
+    CK(cudaMalloc(&s->d_gmat, 2 * fb));
+  }
+  if (E && N > 0) CK(cudaMemcpy(s->d_pE, hE.data(), fb, cudaMemcpyHostToDevice));
+  if (mass && N > 0) CK(cudaMemcpy(s->d_pmass, hm.data(), fb, cudaMemcpyHostToDevice));
+  s->hp.pE = E ? s->d_pE : nullptr;
+  s->hp.pmass = mass ? s->d_pmass : nullptr;
+  s->hp.gmat = (E || mass) ? reinterpret_cast<float2*>(s->d_gmat) : nullptr;
+  s->b.has_material = s->hp.gmat ? 1 : 0;
+  // records built from the old material are stale: the in-place step's table now, rollout and
+  // reverse tables at the next mpm_rollout; graphs of the plain form hold the record by value
+  s->have_rollout = false;
+  s->have_grad = false;
+  invalidate_graphs(s);
+  std::vector<ScenePar> t0(1, rec_fwd(s, s->state, s->state));
+  CKS(upload_table(s, 0, t0));
+  return MPM_OK;
+}
+
+mpm_status mpm_get_material_gradients(mpm_scene* s, float* gE, float* gm, int mem_space) {
+  if (!s || (mem_space != 0 && mem_space != 1)) return MPM_ERR_ARG;
+  if (!s->hp.gmat || !s->have_grad) return MPM_ERR_STATE;
+  CK(cudaStreamSynchronize(s->ctx->stream));
+  const int N = s->N;
+  std::vector<float> h(2 * size_t(N));
+  if (N > 0) CK(cudaMemcpy(h.data(), s->d_gmat, sizeof(float) * 2 * size_t(N), cudaMemcpyDeviceToHost));
+  std::vector<float> a(N), b(N);
+  for (int p = 0; p < N; ++p) {
+    a[p] = h[2 * size_t(p)];
+    b[p] = h[2 * size_t(p) + 1];
+  }
+  cudaMemcpyKind kk = mem_space == 1 ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+  if (gE && N > 0) CK(cudaMemcpy(gE, a.data(), sizeof(float) * N, kk));
+  if (gm && N > 0) CK(cudaMemcpy(gm, b.data(), sizeof(float) * N, kk));
+  return read_status(s);
 }
 
 mpm_status mpm_get_grid(mpm_scene* s, float* m, float* v, int mem_space) {

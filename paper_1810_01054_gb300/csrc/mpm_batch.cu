@@ -181,6 +181,8 @@ mpm_status compose(mpm_batch* B, SubBatch& sb) {
   sb.b.total_tiles = tiles;
   default_launch(sb.b, B->ctx->sm_count);
   tune_apply_cached(sb.b, B->dim);
+  sb.b.has_material = 0;
+  for (int m : sb.members) sb.b.has_material |= B->slots[m].s->hp.gmat ? 1 : 0;
   sb.need_keys = true;
   return MPM_OK;
 }

@@ -47,6 +47,13 @@ struct ScenePar {
   float gravity[3];
   Material mat;
   float mass, vol;
+  // optional per-particle Young's modulus and mass (NULL: mat and mass above for every particle);
+  // mat = E x (mu_per_E, la_per_E), the Lame parameters of E = 1 at the scene's nu.  With them
+  // the reverse step adds this step's dL/dE_p, dL/dm_p into gmat[p] = (gE, gm).
+  const float* pE;
+  const float* pmass;
+  float mu_per_E, la_per_E;
+  float2* gmat;
   BCPar bc;
   int N, npad;      // particles, plane stride (N rounded up)
   int G;            // actuation groups
@@ -113,6 +120,7 @@ struct BatchDev {
   float4* partial;      // [total_tiles * BLOCK_NODES] node blocks of P2G
   float4* partial_b;    // [total_tiles * BLOCK_NODES] node blocks of the adjoint scatter
   float* gpartial;      // [total_tiles * MAX_GROUPS] per active tile group sums of dL/da
+  int has_material;             // some scene has per-particle material (gmat): material gradients
   int sm_count;                 // SMs of the device
   TileLaunch launch[TK_COUNT];  // launch shape of each tile kernel
 };

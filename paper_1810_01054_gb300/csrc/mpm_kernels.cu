@@ -118,15 +118,32 @@ __device__ __forceinline__ void actuation(const ScenePar& sp, int g, float* sig)
   for (int k = 0; k < D; ++k) sig[k] = g >= 0 ? a * __ldg(sp.act_dir + g * D + k) : 0.0f;
 }
 
-// Per-particle quantities of P2G for a particle of group g: stress with actuation and G of Eq. 4.
-// Returns J.
+// Material of particle id: the scene's, or its own Young's modulus and mass when the scene has
+// per-particle arrays (Lame parameters E_p x the scene's per-unit-E factors).
+struct PMat {
+  Material mat;
+  float mass;
+};
+__device__ __forceinline__ PMat pmat_of(const ScenePar& sp, int id) {
+  PMat r{sp.mat, sp.mass};
+  if (sp.pE) {
+    const float E = __ldg(sp.pE + id);
+    r.mat.mu = E * sp.mu_per_E;
+    r.mat.la = E * sp.la_per_E;
+  }
+  if (sp.pmass) r.mass = __ldg(sp.pmass + id);
+  return r;
+}
+
+// Per-particle quantities of P2G for a particle of group g and material pm: stress with
+// actuation and G of Eq. 4.  Returns J.
 template <int D>
-__device__ __forceinline__ float particle_G(const Part<D>& q, const ScenePar& sp, int g, float (&P)[D][D],
-                                            float (&A)[D][D], float (&G)[D][D], float* sig) {
+__device__ __forceinline__ float particle_G(const Part<D>& q, const ScenePar& sp, int g, const PMat& pm,
+                                            float (&P)[D][D], float (&A)[D][D], float (&G)[D][D], float* sig) {
   actuation<D>(sp, g, sig);
-  float J = stress<D>(q.F, sp.mat, sig, P, A);
+  float J = stress<D>(q.F, pm.mat, sig, P, A);
   float kG = -4.0f * sp.inv_dx * sp.inv_dx * sp.dt * sp.vol;
-  mls_G<D>(P, q.F, q.C, kG, sp.mass, G);
+  mls_G<D>(P, q.F, q.C, kG, pm.mass, G);
   return J;
 }
 
@@ -414,8 +431,9 @@ __global__ void __launch_bounds__(256, 2) k_p2g(BatchDev b) {
       int base[D];
       float f[D];
       stencil_base<D>(q.x, sp.inv_dx, sp.n, base, f);
+      const PMat pm = pmat_of(sp, id);
       // the particle must sit in the cell its key names; otherwise it contributes nothing
-      float wm = sp.mass;
+      float wm = pm.mass;
       {
         int c[D];
         const int bn[3] = {B, B, B};
@@ -429,7 +447,7 @@ __global__ void __launch_bounds__(256, 2) k_p2g(BatchDev b) {
         }
       }
       float P[D][D], A[D][D], G[D][D], sig[D];
-      const float J = particle_G<D>(q, sp, g, P, A, G, sig);
+      const float J = particle_G<D>(q, sp, g, pm, P, A, G, sig);
       if (!(J > 0.0f)) set_status(sp.status, ST_INVERTED);
       const float keep = wm > 0.0f ? 1.0f : 0.0f;
       float* rec = U + size_t(row) * K::RW;
@@ -442,7 +460,7 @@ __global__ void __launch_bounds__(256, 2) k_p2g(BatchDev b) {
         float s = 0.0f;
 #pragma unroll
         for (int c = 0; c < D; ++c) s += G[a][c] * f[c];
-        rec[o++] = keep * (sp.mass * q.v[a] - dx * s);
+        rec[o++] = keep * (pm.mass * q.v[a] - dx * s);
       }
 #pragma unroll
       for (int a = 0; a < D; ++a)
@@ -1026,18 +1044,21 @@ __global__ void __launch_bounds__(T, 768 / T) k_g2p(BatchDev b) {
 
 // ============================================================================ adjoint gather
 // Supplement S4: (F) vbar, (I) Cbar, (G) Pbar, (H) Fbar, (J) xbar, (K) sigma-bar -> dL/da.
-// `fetch(kx,ky,kz, v, pb)` returns (v*, m) in v and (pbar, mbar) in pb.
-template <int D, class Fetch>
+// `fetch(kx,ky,kz, v, pb)` returns (v*, m) in v and (pbar, mbar) in pb.  With MAT and per-particle
+// material (sp.gmat) this step's dL/dE_p = (F - F^{-T}):Pbar dmu/dE + ln J (F^{-T}:Pbar) dlambda/dE
+// and dL/dm_p = sum_i N (mbar_i + pbar_i . (v_p + C_p (x_i - x_p))) are added into gmat[id].
+template <int D, bool MAT, class Fetch>
 __device__ __forceinline__ float adj_core(const Part<D>& q, const Part<D>& g1, const float* f, const float (&w)[D][3],
-                                          const float (&dw)[D][3], const ScenePar& sp, int g, Fetch fetch,
+                                          const float (&dw)[D][3], const ScenePar& sp, int id, int g, Fetch fetch,
                                           Part<D>& g0) {
-  const float dt = sp.dt, dx = sp.dx, mass = sp.mass;
+  const PMat pm = pmat_of(sp, id);
+  const float dt = sp.dt, dx = sp.dx, mass = pm.mass;
   const float Dinv = 4.0f * sp.inv_dx * sp.inv_dx;
   const float kG = -Dinv * dt * sp.vol;
   float G[D][D], sig[D];
   {
     float P[D][D], A[D][D];  // recomputed after the stencil loop: not kept live across it
-    particle_G<D>(q, sp, g, P, A, G, sig);
+    particle_G<D>(q, sp, g, pm, P, A, G, sig);
   }
   // s_i = vbar'.v* + Dinv v*^T Cbar' d + pbar.(m v + G d) + m mbar with d = (k - f) dx is affine in
   // the integer node offset k: alpha(k) = vbar' + Dinv Cbar' d and beta(k) = m v + G d are kept as
@@ -1068,7 +1089,7 @@ __device__ __forceinline__ float adj_core(const Part<D>& q, const Part<D>& g1, c
   // accumulators: gxs = sum dN s_i; sv = sum N v*, spb = sum N pbar; Tv/Tp = the same sums weighted
   // by the y (and z) node offset; Rv/Rp = running totals of sv/spb at each x-slab end, from which the
   // x-offset-weighted sums follow (sum kx S_kx = 3 S - R for kx = 0, 1, 2)
-  float gxs[D], sv[D], spb[D], Tv[D][D - 1], Tp[D][D - 1], Rv[D], Rp[D];
+  float gxs[D], sv[D], spb[D], Tv[D][D - 1], Tp[D][D - 1], Rv[D], Rp[D], smb = 0.0f;  // smb = sum N mbar
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     gxs[a] = sv[a] = spb[a] = Rv[a] = Rp[a] = 0.0f;
@@ -1119,6 +1140,7 @@ __device__ __forceinline__ float adj_core(const Part<D>& q, const Part<D>& g1, c
         const float pb[3] = {p4.x, p4.y, p4.z};
         const float mb = D == 2 ? p4.z : p4.w;
         float si = mass * mb;
+        if constexpr (MAT) smb += N * mb;
 #pragma unroll
         for (int a = 0; a < D; ++a) si += vs[a] * alpha[a] + pb[a] * beta[a];
 #pragma unroll
@@ -1189,9 +1211,27 @@ __device__ __forceinline__ float adj_core(const Part<D>& q, const Part<D>& g1, c
       Pb[a][c] = kG * s;  // (G)
     }
   float P[D][D], A[D][D];
-  const float J = stress<D>(q.F, sp.mat, sig, P, A);
+  const float J = stress<D>(q.F, pm.mat, sig, P, A);
   float H[D][D];
-  nh_hessian_apply<D>(A, J, sp.mat, Pb, H);
+  nh_hessian_apply<D>(A, J, pm.mat, Pb, H);
+  if (MAT && sp.gmat) {  // material gradients of this step (P2G is where E_p and m_p enter)
+    float gmu = 0.0f, gla = 0.0f, gm = smb;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      gm += q.v[a] * spb[a];
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        gmu += (q.F[a][c] - A[a][c]) * Pb[a][c];
+        gla += A[a][c] * Pb[a][c];
+        gm += q.C[a][c] * Gbar[a][c];
+      }
+    }
+    const float gE = gmu * sp.mu_per_E + logf(J > 0.0f ? J : 1.0f) * gla * sp.la_per_E;
+    float2 acc = sp.gmat[id];
+    acc.x += gE;
+    acc.y += gm;
+    sp.gmat[id] = acc;
+  }
   // (H) Fbar = (I + dt C^{n+1})^T Fbar' + H[Pbar] + Pbar sigma^T + kG Gbar^T P
 #pragma unroll
   for (int a = 0; a < D; ++a)
@@ -1220,7 +1260,7 @@ __device__ __forceinline__ float adj_core(const Part<D>& q, const Part<D>& g1, c
   return contrib;
 }
 
-template <int D>
+template <int D, bool MAT>
 __global__ void __launch_bounds__(256, 2) k_adj_gather(BatchDev b) {
   pdl_enter();
   constexpr int B = Cfg<D>::B, NB = Cfg<D>::BLOCK_NODES, BN = Cfg<D>::BN;
@@ -1265,7 +1305,7 @@ __global__ void __launch_bounds__(256, 2) k_adj_gather(BatchDev b) {
           inside = inside && base[a] >= 0 && base[a] < B;
         }
         if (inside) {
-          contrib = adj_core<D>(q, g1, f, w, dw, sp, gq, [&](int kx, int ky, int kz, float4& v, float4& p) {
+          contrib = adj_core<D, MAT>(q, g1, f, w, dw, sp, id, gq, [&](int kx, int ky, int kz, float4& v, float4& p) {
             int l = (base[0] + kx) * BN + base[1] + ky;
             if constexpr (D == 3) l = l * BN + base[2] + kz;
             v = sv[l];
@@ -1369,7 +1409,10 @@ cudaError_t launch_g2p(const BatchDev& b, cudaStream_t s) {
 template <int D>
 cudaError_t launch_adj_gather(const BatchDev& b, cudaStream_t s) {
   const int grid = tile_grid(b, TK_ADJ_GATHER);
-  launch_pdl(k_adj_gather<D>, dim3(grid), dim3(256), 0, s, b);
+  if (b.has_material)
+    launch_pdl(k_adj_gather<D, true>, dim3(grid), dim3(256), 0, s, b);
+  else
+    launch_pdl(k_adj_gather<D, false>, dim3(grid), dim3(256), 0, s, b);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -1403,7 +1446,8 @@ __global__ void k_plain_scatter(const ScenePar* __restrict__ dsp) {
     return;
   }
   float P[D][D], A[D][D], G[D][D], sig[D];
-  const float J = particle_G<D>(q, sp, group_of(sp, id), P, A, G, sig);
+  const PMat pm = pmat_of(sp, id);
+  const float J = particle_G<D>(q, sp, group_of(sp, id), pm, P, A, G, sig);
   if (!(J > 0.0f)) set_status(sp.status, ST_INVERTED);
   float vb[D], Cb[D][D];
   if constexpr (ADJ) {
@@ -1443,12 +1487,12 @@ __global__ void k_plain_scatter(const ScenePar* __restrict__ dsp) {
         float* gp = reinterpret_cast<float*>(sp.grid + nl);
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-          float s = sp.mass * q.v[a];
+          float s = pm.mass * q.v[a];
 #pragma unroll
           for (int c = 0; c < D; ++c) s += G[a][c] * dp[c];
           atomicAdd(gp + a, N * s);
         }
-        atomicAdd(gp + (D == 2 ? 2 : 3), N * sp.mass);
+        atomicAdd(gp + (D == 2 ? 2 : 3), N * pm.mass);
         if constexpr (ADJ) {
           float* gb = reinterpret_cast<float*>(sp.grid_b + nl);
 #pragma unroll
@@ -1554,7 +1598,7 @@ __global__ void k_plain_gather(const ScenePar* __restrict__ dsp) {
   unpack<D>(r, g1);
   Sten<D> stn;
   if (!make_stencil<D>(q.x, sp.inv_dx, sp.n, stn)) return;
-  const float c = adj_core<D>(q, g1, stn.f, stn.w, stn.dw, sp, group_of(sp, id), [&](int kx, int ky, int kz, float4& v, float4& p) {
+  const float c = adj_core<D, true>(q, g1, stn.f, stn.w, stn.dw, sp, id, group_of(sp, id), [&](int kx, int ky, int kz, float4& v, float4& p) {
     int nd[D];
     nd[0] = stn.base[0] + kx;
     nd[1] = stn.base[1] + ky;

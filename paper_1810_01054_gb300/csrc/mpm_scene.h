@@ -68,6 +68,10 @@ struct mpm_scene {
   int* d_step = nullptr;     // forward step counter (controller time)
   int* d_bstep = nullptr;    // reverse step counter
   int* d_status = nullptr;
+  // per-particle material (mpm_scene_set_material): E_p, m_p and the (gE, gm) accumulator
+  float* d_pE = nullptr;
+  float* d_pmass = nullptr;
+  float* d_gmat = nullptr;
   ScenePar* cur = nullptr;   // device: the record of the running step
   SelectPar* dsel = nullptr; // device: one selection per phase
   SelectPar hsel[gbmpm::PH_COUNT]{};

@@ -128,6 +128,8 @@ _SIGS = {
     "mpm_launch_count": [C.POINTER(C.c_longlong)],
     "mpm_step_noalloc": [C.POINTER(NoAllocStep), C.c_void_p],
     "mpm_scene_set_tuning": [C.c_void_p, C.c_int],
+    "mpm_scene_set_material": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int],
+    "mpm_get_material_gradients": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int],
     "mpm_scene_launch": [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)],
     "mpm_tune_cache_lookup": [C.c_int, C.c_longlong, C.c_longlong, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)],
     "mpm_tune_cache_store": [C.c_int, C.c_longlong, C.c_longlong, C.c_int, C.POINTER(C.c_int)],
@@ -331,6 +333,9 @@ class Scene:
         _check(lib().mpm_scene_create(ctx.handle, C.byref(desc), C.byref(h)), "mpm_scene_create")
         self.handle = h
         ctx._adopt(self)
+        E_arr, m_arr = getattr(spec, "E_arr", None), getattr(spec, "mass_arr", None)
+        if E_arr is not None or m_arr is not None:
+            self.set_material(E_arr, m_arr)
         self.G = G
         self.impl = impl
 
@@ -420,6 +425,31 @@ class Scene:
         _check(lib().mpm_backward(self.handle, *[_ptr(a) for a in seeds], _ptr(gx0), _ptr(gv0), _ptr(gC0), _ptr(gF0),
                                   _ptr(gp), 0), "mpm_backward")
         return gx0, gv0, gC0, gF0, gp[: self.n_params]
+
+    def set_material(self, E=None, mass=None):
+        """Per-particle Young's modulus and mass [N] (None keeps the scene's value); host arrays or
+        CUDA tensors.  Enables dL/dE_p, dL/dm_p in the reverse pass (material_gradients)."""
+        arrs = [a for a in (E, mass) if a is not None]
+        on_dev = bool(arrs) and _is_torch(arrs[0]) and arrs[0].is_cuda
+        conv = []
+        for a in (E, mass):
+            if a is None:
+                conv.append(None)
+            elif on_dev:
+                conv.append(a.float().contiguous())
+            else:
+                conv.append(np.ascontiguousarray(np.asarray(a, np.float32).ravel()))
+        for a in conv:
+            if a is not None and (a.numel() if _is_torch(a) else a.size) != self.N:
+                raise ValueError("per-particle material arrays need one entry per particle")
+        _check(lib().mpm_scene_set_material(self.handle, _ptr(conv[0]), _ptr(conv[1]), 1 if on_dev else 0),
+               "mpm_scene_set_material")
+
+    def material_gradients(self):
+        """(dL/dE_p, dL/dm_p) [N] of the last finished reverse pass (per-particle material only)."""
+        gE, gm = np.empty(self.N, np.float32), np.empty(self.N, np.float32)
+        _check(lib().mpm_get_material_gradients(self.handle, _ptr(gE), _ptr(gm), 0), "mpm_get_material_gradients")
+        return gE, gm
 
     def gradients(self, out=None):
         """Result of the last finished reverse pass (mpm_backward or a batched gradient request):
