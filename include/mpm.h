@@ -71,8 +71,11 @@ const char* mpm_status_str(mpm_status s);
  *  MPM_CTRL_MLP   z = centroid_g(x) - centroid_all(x) for every group (G*dim inputs),
  *                 a = scale * tanh(W3 tanh(W2 tanh(W1 z + b1) + b2) + b3)  params W1[H][G*dim], b1[H],
  *                                                                          W2[H][H], b2[H], W3[G][H], b3[G]
- * with t = n * dt at the start of step n. */
-enum { MPM_CTRL_SIN = 0, MPM_CTRL_BASIS = 1, MPM_CTRL_MLP = 2 };
+ *  MPM_CTRL_TABLE every step's actuation is a decision variable (the trajectory-optimisation
+ *                 examples, Section V-C): a_g(t_n) = U[n][g] for steps 0 <= n < L, 0 after
+ *                                                                          params U[L][G], L = ctrl_hidden
+ * with t = n * dt at the start of step n (n the scene's step counter). */
+enum { MPM_CTRL_SIN = 0, MPM_CTRL_BASIS = 1, MPM_CTRL_MLP = 2, MPM_CTRL_TABLE = 3 };
 enum { MPM_BC_STICKY = 0, MPM_BC_SLIP = 1 };
 enum { MPM_IMPL_TILED = 0, MPM_IMPL_PLAIN = 1 };
 
@@ -95,7 +98,7 @@ typedef struct {
   int n_groups;        /* 0 <= G <= 64 */
   const float* act_dir;/* [G][dim] actuation direction: sigma_a = a_g Diag(dir_g) */
   int ctrl_type;       /* MPM_CTRL_* */
-  int ctrl_hidden;     /* MLP width H <= 128 (MLP only); G*dim <= 192 */
+  int ctrl_hidden;     /* MLP width H <= 128 (MLP; G*dim <= 192); table length L >= 0 (TABLE) */
   float ctrl_freq;     /* f of the sinusoid forms */
   float ctrl_scale;    /* output scale of the MLP */
   int n_ctrl_params;   /* must equal the family's parameter count above */

@@ -455,6 +455,9 @@ int oracle_version() { return 1; }
 //           b = [sin 2pi f t, cos 2pi f t, sin 4pi f t, cos 4pi f t]   params [G][4]
 //   type 2: z = (c_g - c_body) for every group (G*d), c = unweighted centroids of x;
 //           h1 = tanh(W1 z + b1), h2 = tanh(W2 h1 + b2), a = scale * tanh(W3 h2 + b3)
+//   type 3: the actuation of every step is a decision variable (the per-step actuation of the
+//           trajectory-optimisation examples, Section V-C): a_g(t_n) = U[n][g] for 0 <= n < L,
+//           L = ctrl_hidden steps, and 0 after the table      params [L][G]
 int oracle_controller(const oracle_scene* s, const double* params, int step, const double* x, double* act) {
   int G = s->n_groups, d = s->dim, N = s->n_particles;
   double t = step * s->dt;
@@ -508,6 +511,10 @@ int oracle_controller(const oracle_scene* s, const double* params, int step, con
       for (int j = 0; j < H_; ++j) u += W3[g * H_ + j] * h2[j];
       act[g] = s->ctrl_scale * std::tanh(u);
     }
+    return 0;
+  }
+  if (s->ctrl_type == 3) {
+    for (int g = 0; g < G; ++g) act[g] = (step >= 0 && step < s->ctrl_hidden) ? params[size_t(step) * G + g] : 0.0;
     return 0;
   }
   return -1;
@@ -611,6 +618,11 @@ int oracle_controller_adjoint(const oracle_scene* s, const double* params, int s
         }
       }
     }
+    return 0;
+  }
+  if (s->ctrl_type == 3) {
+    if (step >= 0 && step < s->ctrl_hidden)
+      for (int g = 0; g < G; ++g) gparams[size_t(step) * G + g] += gact[g];
     return 0;
   }
   return -1;

@@ -73,6 +73,7 @@ int ctrl_param_count(int type, int G, int dim, int H) {
     int Z = G * dim;
     return H * Z + H + H * H + H + G * H + G;
   }
+  if (type == MPM_CTRL_TABLE) return H >= 0 ? H * G : -1;
   return -1;
 }
 
@@ -874,6 +875,7 @@ mpm_status mpm_scene_create(mpm_ctx* c, const mpm_scene_desc* d, mpm_scene** out
     q.ctrl_type = d->ctrl_type;
     q.G = s->G;
     q.freq = d->ctrl_freq;
+    q.ctrl_len = d->ctrl_hidden;
     q.dt = d->dt;
     q.params = params;
     q.act = act;

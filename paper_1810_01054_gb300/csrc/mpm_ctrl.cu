@@ -224,6 +224,8 @@ __device__ void ctrl_backward_body(const ScenePar& sp, const CtrlPar& c) {
   }
   if (c.type == 0) {
     if (tid < G) c.gparams[tid] += ga[tid] * sinf(kTwoPi * c.freq * t);
+  } else if (c.type == 3) {  // table: dL/dU[n][g] = dL/da_g(t_n)
+    if (tid < G && n >= 0 && n < c.hidden) c.gparams[size_t(n) * G + tid] += ga[tid];
   } else if (c.type == 1) {
     if (tid < G * 4) {
       const int g = tid / 4, j = tid - 4 * g;

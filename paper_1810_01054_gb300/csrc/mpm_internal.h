@@ -85,7 +85,8 @@ struct SelectPar {
   int base;
   const int* ctr;         // step counter n
   int tile_base, pbase;   // batch offsets of the scene
-  int ctrl_type, G;       // sinusoid controllers are evaluated by the selection
+  int ctrl_type, G;       // sinusoid and table controllers are evaluated by the selection
+  int ctrl_len;           // table controller: steps in the table
   float freq, dt;
   const float* params;
   float* act;
@@ -157,7 +158,7 @@ cudaError_t launch_plain_adjoint(const ScenePar* dev_scene, const ScenePar& host
 
 // Controllers.  ctrl_* describe one scene's controller.
 struct CtrlPar {
-  int type;        // 0 sinusoid amplitude, 1 sinusoid basis, 2 MLP on group centroids
+  int type;        // 0 sinusoid amplitude, 1 sinusoid basis, 2 MLP on group centroids, 3 per-step table
   int G, dim, hidden;
   float freq, scale;
   const float* params;   // device

@@ -1744,6 +1744,8 @@ __global__ void k_select(const SelectPar* __restrict__ sel, ScenePar* __restrict
     const float w = 6.283185307179586f * q.freq * tt;
     q.act[g] = q.params[g * 4] * sinf(w) + q.params[g * 4 + 1] * cosf(w) + q.params[g * 4 + 2] * sinf(2.0f * w) +
                q.params[g * 4 + 3] * cosf(2.0f * w);
+  } else if (g < q.G && q.ctrl_type == 3) {
+    q.act[g] = (n >= 0 && n < q.ctrl_len) ? q.params[size_t(n) * q.G + g] : 0.0f;
   }
 }
 

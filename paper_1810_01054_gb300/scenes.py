@@ -39,6 +39,7 @@ import numpy as np
 CTRL_SIN = 0      # a_g(t) = A_g * sin(2*pi*freq*t)
 CTRL_BASIS = 1    # a_g(t) = sum_j W_gj b_j(t), b = [sin 2pi f t, cos 2pi f t, sin 4pi f t, cos 4pi f t]
 CTRL_MLP = 2      # a = scale * tanh(W3 tanh(W2 tanh(W1 z + b1) + b2) + b3), z = group centroids - body centroid
+CTRL_TABLE = 3    # a_g(t_n) = U[n][g] for n < L (L = hidden), 0 after: every step's actuation a decision variable
 
 BC_STICKY = 0
 BC_SLIP = 1
@@ -114,6 +115,8 @@ def n_ctrl_params(ctrl_type: int, n_groups: int, dim: int, hidden: int) -> int:
     if ctrl_type == CTRL_MLP:
         zin = n_groups * dim
         return hidden * zin + hidden + hidden * hidden + hidden + n_groups * hidden + n_groups
+    if ctrl_type == CTRL_TABLE:
+        return hidden * n_groups
     raise ValueError(f"unknown controller type {ctrl_type}")
 
 

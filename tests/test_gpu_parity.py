@@ -47,6 +47,11 @@ def small_scenes():
                            v_scale=0.3),
         "3d_mlp": S.blob(3, 16, 400, 6, ctrl_type=S.CTRL_MLP, n_groups=4, hidden=16, scale=5.0, radius_cells=3.5,
                          v_scale=0.3),
+        # per-step actuation table (30 rows, longer than the 25-step rollouts below)
+        "2d_table": S.blob(2, 32, 300, 7, ctrl_type=S.CTRL_TABLE, n_groups=4, hidden=30, radius_cells=4.5,
+                           v_scale=0.3, amp=3.0),
+        "3d_table": S.blob(3, 20, 500, 8, ctrl_type=S.CTRL_TABLE, n_groups=3, hidden=30, radius_cells=3.5,
+                           v_scale=0.3, amp=3.0),
     }
 
 
@@ -99,7 +104,7 @@ def test_walker_square_full_horizon_gradient(M, ctx, impl):
     assert_grad_close(gF, ogF, "dL/dF0")
 
 
-@pytest.mark.parametrize("name", ["2d_basis", "3d_mlp", "2d_slip_friction", "3d_sticky"])
+@pytest.mark.parametrize("name", ["2d_basis", "3d_mlp", "2d_slip_friction", "3d_sticky", "2d_table", "3d_table"])
 def test_controller_and_state_gradients(M, ctx, name):
     spec = small_scenes()[name]
     T = 25
@@ -114,6 +119,8 @@ def test_controller_and_state_gradients(M, ctx, name):
     gx, gv, gC, gF, gp = gpu.backward(wx, wv)
     for nm, a, b in (("x0", gx, ogx), ("v0", gv, ogv), ("C0", gC, ogC), ("F0", gF, ogF), ("params", gp, ogp)):
         assert_grad_close(a, b, f"{name} dL/d{nm}")
+    if spec.ctrl_type == S.CTRL_TABLE:  # rows past the rollout stay exactly zero
+        assert np.all(gp.reshape(spec.ctrl_hidden, -1)[T:] == 0)
 
 
 def test_tiled_is_bitwise_deterministic_and_checkpoint_invariant(M, ctx):

@@ -284,12 +284,13 @@ def test_step_adjoint_dot_product(case):
     assert abs(lhs - rhs) <= 1e-6 * max(1.0, abs(lhs)), (lhs, rhs)
 
 
-@pytest.mark.parametrize("ctrl", [S.CTRL_SIN, S.CTRL_BASIS, S.CTRL_MLP])
+@pytest.mark.parametrize("ctrl", [S.CTRL_SIN, S.CTRL_BASIS, S.CTRL_MLP, S.CTRL_TABLE])
 def test_controller_adjoint_fd(ctrl):
     """The controller forms' reverse (parameters and, for the MLP, positions through the group
     centroids) against central differences."""
     rng = np.random.default_rng(ctrl)
-    sp = S.blob(3, 12, 40, 9, n_groups=4, ctrl_type=ctrl, hidden=6, freq=4.0, scale=3.0)
+    sp = S.blob(3, 12, 40, 9, n_groups=4, ctrl_type=ctrl, hidden=10 if ctrl == S.CTRL_TABLE else 6, freq=4.0,
+                scale=3.0)
     sc = O.Scene(sp)
     x = sc.initial_state()[0]
     step = 7
@@ -306,18 +307,18 @@ def test_controller_adjoint_fd(ctrl):
         assert np.all(gx == 0)
 
 
-@pytest.mark.parametrize("ctrl,dim", [(S.CTRL_SIN, 2), (S.CTRL_BASIS, 2), (S.CTRL_MLP, 3)])
+@pytest.mark.parametrize("ctrl,dim", [(S.CTRL_SIN, 2), (S.CTRL_BASIS, 2), (S.CTRL_MLP, 3), (S.CTRL_TABLE, 2)])
 def test_rollout_gradient_fd(ctrl, dim):
     """I7 over a rollout: the chain rule of Section III from a loss on the final state back to the
     initial v0, x0 and the controller parameters used at every step, against FP64 central FD
     (the paper's Table III B/C methodology) on a tiny scene touching the sticky floor."""
     rng = np.random.default_rng(40 + ctrl)
     n = 16 if dim == 2 else 12
-    sp = S.blob(dim, n, 24, 20 + ctrl, n_groups=3, ctrl_type=ctrl, hidden=5, freq=4.0, scale=2.0,
-                v_scale=0.3, radius_cells=2.0, center=np.full(dim, 3.8 / n), amp=2.0, bc_width=2,
-                dt=2e-3)
-    sc = O.Scene(sp)
     T = 15
+    sp = S.blob(dim, n, 24, 20 + ctrl, n_groups=3, ctrl_type=ctrl, hidden=T + 3 if ctrl == S.CTRL_TABLE else 5,
+                freq=4.0, scale=2.0, v_scale=0.3, radius_cells=2.0, center=np.full(dim, 3.8 / n), amp=2.0,
+                bc_width=2, dt=2e-3)
+    sc = O.Scene(sp)
     traj = sc.rollout(T)
     w = rng.normal(size=traj[0][T].shape)
     wv = rng.normal(size=traj[1][T].shape)
@@ -337,6 +338,30 @@ def test_rollout_gradient_fd(ctrl, dim):
     dp = rng.normal(size=sc.params.shape)
     fd = (loss(sc.rollout(T, params=sc.params + h * dp)) - loss(sc.rollout(T, params=sc.params - h * dp))) / (2 * h)
     assert abs(fd - gp @ dp) <= 1e-6 * max(1, abs(fd))
+    if ctrl == S.CTRL_TABLE:  # rows of steps the rollout never reaches have no effect
+        assert np.all(gp.reshape(T + 3, 3)[T:] == 0) and np.any(gp.reshape(T + 3, 3)[:T] != 0)
+
+
+def test_table_controller_filled_with_a_sinusoid_is_that_sinusoid():
+    """A table whose rows are the sinusoid controller's outputs reproduces its rollout exactly, and
+    the chain rule between the two forms holds: dL/dA_g = sum_n dL/dU[n][g] sin(2 pi f t_n)."""
+    T = 12
+    sin = S.blob(2, 16, 30, 31, n_groups=3, ctrl_type=S.CTRL_SIN, freq=4.0, v_scale=0.3, radius_cells=2.0,
+                 center=(0.5, 3.8 / 16), amp=3.0, bc_width=2, dt=2e-3)
+    ss = O.Scene(sin)
+    x0 = ss.initial_state()[0]
+    U = np.stack([ss.controller(n, x0) for n in range(T)])            # a_g(t_n) with A
+    basis = np.stack([ss.controller(n, x0, params=np.ones(3)) for n in range(T)])  # sin(2 pi f t_n)
+    tab = sin.copy(ctrl_type=S.CTRL_TABLE, ctrl_hidden=T, ctrl_params=U.ravel())
+    ts = O.Scene(tab)
+    ra, rb = ss.rollout(T), ts.rollout(T)
+    for a, b in zip(ra, rb):
+        assert np.array_equal(a, b)
+    rng = np.random.default_rng(3)
+    w = rng.normal(size=ra[0][T].shape)
+    gA = ss.backward(ra, (w, None, None, None))[4]
+    gU = ts.backward(rb, (w, None, None, None))[4].reshape(T, 3)
+    assert np.allclose(gA, np.sum(gU * basis, axis=0), rtol=1e-12, atol=1e-14 * np.abs(gU).max())
 
 
 def test_domain_and_inversion_errors():
