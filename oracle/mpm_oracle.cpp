@@ -443,6 +443,32 @@ int forward_grid(const oracle_scene* s, const double* act, const double* x, cons
   return 0;
 }
 
+// Input of the closed-loop controller (type 4): z = [target (d), c_g (d per group), u_g (d per
+// group)] with c_g, u_g the unweighted means of x and v over group g (0 for an empty group); the
+// group sizes go to cnt when given.
+void com_input(const oracle_scene* s, const double* params, const double* x, const double* v,
+               std::vector<double>* z, std::vector<double>* cnt_out) {
+  const int G = s->n_groups, d = s->dim, N = s->n_particles;
+  std::vector<double> cnt(G, 0.0), cx(size_t(G) * d, 0.0), cv(size_t(G) * d, 0.0);
+  for (int p = 0; p < N; ++p) {
+    const int g = s->group ? s->group[p] : -1;
+    if (g < 0 || g >= G) continue;
+    cnt[g] += 1.0;
+    for (int a = 0; a < d; ++a) {
+      cx[g * d + a] += x[p * d + a];
+      cv[g * d + a] += v[p * d + a];
+    }
+  }
+  z->assign(size_t(d) * (1 + 2 * G), 0.0);
+  for (int a = 0; a < d; ++a) (*z)[a] = params[a];
+  for (int g = 0; g < G; ++g)
+    for (int a = 0; a < d; ++a) {
+      (*z)[d + g * d + a] = cnt[g] > 0 ? cx[g * d + a] / cnt[g] : 0.0;
+      (*z)[d + G * d + g * d + a] = cnt[g] > 0 ? cv[g * d + a] / cnt[g] : 0.0;
+    }
+  if (cnt_out) *cnt_out = cnt;
+}
+
 }  // namespace
 
 extern "C" {
@@ -458,7 +484,12 @@ int oracle_version() { return 1; }
 //   type 3: the actuation of every step is a decision variable (the per-step actuation of the
 //           trajectory-optimisation examples, Section V-C): a_g(t_n) = U[n][g] for 0 <= n < L,
 //           L = ctrl_hidden steps, and 0 after the table      params [L][G]
-int oracle_controller(const oracle_scene* s, const double* params, int step, const double* x, double* act) {
+//   type 4: the closed-loop controller of Section V-B, a = scale * tanh(W z + b) with z = target
+//           position, centre of mass and velocity of every component (group):
+//           z = [target, c_1..c_G, u_1..u_G], c_g, u_g the means of x, v over group g
+//                                                  params [target (d), W [G][d(1+2G)], b [G]]
+int oracle_controller_xv(const oracle_scene* s, const double* params, int step, const double* x, const double* v,
+                         double* act) {
   int G = s->n_groups, d = s->dim, N = s->n_particles;
   double t = step * s->dt;
   if (s->ctrl_type == 0) {
@@ -517,12 +548,30 @@ int oracle_controller(const oracle_scene* s, const double* params, int step, con
     for (int g = 0; g < G; ++g) act[g] = (step >= 0 && step < s->ctrl_hidden) ? params[size_t(step) * G + g] : 0.0;
     return 0;
   }
+  if (s->ctrl_type == 4) {
+    if (!v) return -1;
+    std::vector<double> z;
+    com_input(s, params, x, v, &z, nullptr);
+    const int Z = int(z.size());
+    const double* W = params + d;
+    const double* b = W + size_t(G) * Z;
+    for (int g = 0; g < G; ++g) {
+      double u = b[g];
+      for (int j = 0; j < Z; ++j) u += W[size_t(g) * Z + j] * z[j];
+      act[g] = s->ctrl_scale * std::tanh(u);
+    }
+    return 0;
+  }
   return -1;
 }
 
+int oracle_controller(const oracle_scene* s, const double* params, int step, const double* x, double* act) {
+  return oracle_controller_xv(s, params, step, x, nullptr, act);
+}
+
 // Reverse of oracle_controller: gparams += (da/dparams)^T gact; gx += (da/dx)^T gact (type 2).
-int oracle_controller_adjoint(const oracle_scene* s, const double* params, int step, const double* x,
-                              const double* gact, double* gparams, double* gx) {
+int oracle_controller_adjoint_xv(const oracle_scene* s, const double* params, int step, const double* x,
+                                 const double* v, const double* gact, double* gparams, double* gx, double* gv) {
   int G = s->n_groups, d = s->dim, N = s->n_particles;
   double t = step * s->dt;
   if (s->ctrl_type == 0) {
@@ -625,7 +674,44 @@ int oracle_controller_adjoint(const oracle_scene* s, const double* params, int s
       for (int g = 0; g < G; ++g) gparams[size_t(step) * G + g] += gact[g];
     return 0;
   }
+  if (s->ctrl_type == 4) {
+    if (!v) return -1;
+    std::vector<double> z, cnt;
+    com_input(s, params, x, v, &z, &cnt);
+    const int Z = int(z.size());
+    const double* W = params + d;
+    const double* b = W + size_t(G) * Z;
+    double* gW = gparams + d;
+    double* gb = gW + size_t(G) * Z;
+    std::vector<double> gz(Z, 0.0);
+    for (int g = 0; g < G; ++g) {
+      double u = b[g];
+      for (int j = 0; j < Z; ++j) u += W[size_t(g) * Z + j] * z[j];
+      const double th = std::tanh(u);
+      const double gu = gact[g] * s->ctrl_scale * (1.0 - th * th);
+      gb[g] += gu;
+      for (int j = 0; j < Z; ++j) {
+        gW[size_t(g) * Z + j] += gu * z[j];
+        gz[j] += W[size_t(g) * Z + j] * gu;
+      }
+    }
+    for (int a = 0; a < d; ++a) gparams[a] += gz[a];  // the target is an input held in params
+    for (int p = 0; p < N; ++p) {
+      const int g = s->group ? s->group[p] : -1;
+      if (g < 0 || g >= G || !(cnt[g] > 0)) continue;
+      for (int a = 0; a < d; ++a) {
+        gx[p * d + a] += gz[d + g * d + a] / cnt[g];
+        if (gv) gv[p * d + a] += gz[d + G * d + g * d + a] / cnt[g];
+      }
+    }
+    return 0;
+  }
   return -1;
+}
+
+int oracle_controller_adjoint(const oracle_scene* s, const double* params, int step, const double* x,
+                              const double* gact, double* gparams, double* gx) {
+  return oracle_controller_adjoint_xv(s, params, step, x, nullptr, gact, gparams, gx, nullptr);
 }
 
 // One forward step n -> n+1 (Section III Eqs. 3-10 with gravity and boundary).  Optional
@@ -883,7 +969,7 @@ int oracle_rollout(const oracle_scene* s, const double* params, int n_steps, con
   std::memcpy(Fs, F0, sizeof(double) * sm);
   std::vector<double> act(G > 0 ? G : 1, 0.0);
   for (int n = 0; n < n_steps; ++n) {
-    int rc = oracle_controller(s, params, n, xs + n * sx, act.data());
+    int rc = oracle_controller_xv(s, params, n, xs + n * sx, vs + n * sx, act.data());
     if (rc) return rc;
     for (int g = 0; g < G; ++g) acts[size_t(n) * G + g] = act[g];
     rc = oracle_step(s, act.data(), xs + n * sx, vs + n * sx, Cs + n * sm, Fs + n * sm, xs + (n + 1) * sx,
@@ -920,7 +1006,8 @@ int oracle_backward_mat(const oracle_scene* s, const double* params, int n_param
     if (rc) return rc;
     for (int p = 0; p < N && gE; ++p) gE[p] += sE[p];
     for (int p = 0; p < N && gm; ++p) gm[p] += sm_[p];
-    rc = oracle_controller_adjoint(s, params, n, xs + n * sx, gact.data(), gparams, bx.data());
+    rc = oracle_controller_adjoint_xv(s, params, n, xs + n * sx, vs + n * sx, gact.data(), gparams, bx.data(),
+                                      bv.data());
     if (rc) return rc;
     ax.swap(bx);
     av.swap(bv);

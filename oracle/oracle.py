@@ -73,7 +73,8 @@ def lib():
         if _lib is None:
             _lib = C.CDLL(build())
             for name in ("oracle_step", "oracle_step_adjoint", "oracle_step_adjoint_mat", "oracle_controller",
-                         "oracle_controller_adjoint", "oracle_rollout", "oracle_backward",
+                         "oracle_controller_xv", "oracle_controller_adjoint", "oracle_controller_adjoint_xv",
+                         "oracle_rollout", "oracle_backward",
                          "oracle_backward_mat", "oracle_neohookean", "oracle_bc"):
                 getattr(_lib, name).restype = C.c_int
     return _lib
@@ -139,22 +140,27 @@ class Scene:
         d, N = self.dim, self.N
         return (_f64(sp.x0, (N, d)), _f64(sp.v0, (N, d)), _f64(sp.C0, (N, d, d)), _f64(sp.F0, (N, d, d)))
 
-    def controller(self, step, x, params=None):
+    def controller(self, step, x, params=None, v=None):
+        """Actuation a_g(t_step) from positions x (and velocities v, needed by the closed-loop form)."""
         params = self.params if params is None else _f64(params).ravel()
         act = np.zeros(max(self.G, 1))
         x = _f64(x)
-        self._check(lib().oracle_controller(self.ref, _p(params), int(step), _p(x), _p(act)), "controller")
+        v = None if v is None else _f64(v)
+        self._check(lib().oracle_controller_xv(self.ref, _p(params), int(step), _p(x), _p(v), _p(act)), "controller")
         return act[: self.G]
 
-    def controller_adjoint(self, step, x, gact, params=None):
+    def controller_adjoint(self, step, x, gact, params=None, v=None):
+        """(dL/dparams, dL/dx) from dL/da; with v also dL/dv (closed-loop form)."""
         params = self.params if params is None else _f64(params).ravel()
         gp = np.zeros_like(params)
         gx = np.zeros((self.N, self.dim))
+        gv = np.zeros((self.N, self.dim)) if v is not None else None
         x = _f64(x)
+        v = None if v is None else _f64(v)
         gact = _f64(gact)
-        self._check(lib().oracle_controller_adjoint(self.ref, _p(params), int(step), _p(x), _p(gact), _p(gp),
-                                                    _p(gx)), "controller adjoint")
-        return gp, gx
+        self._check(lib().oracle_controller_adjoint_xv(self.ref, _p(params), int(step), _p(x), _p(v), _p(gact),
+                                                       _p(gp), _p(gx), _p(gv)), "controller adjoint")
+        return (gp, gx) if v is None else (gp, gx, gv)
 
     def step(self, act, x, v, Cm, F, want_grid=False):
         d, N = self.dim, self.N

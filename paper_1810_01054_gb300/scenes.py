@@ -40,6 +40,7 @@ CTRL_SIN = 0      # a_g(t) = A_g * sin(2*pi*freq*t)
 CTRL_BASIS = 1    # a_g(t) = sum_j W_gj b_j(t), b = [sin 2pi f t, cos 2pi f t, sin 4pi f t, cos 4pi f t]
 CTRL_MLP = 2      # a = scale * tanh(W3 tanh(W2 tanh(W1 z + b1) + b2) + b3), z = group centroids - body centroid
 CTRL_TABLE = 3    # a_g(t_n) = U[n][g] for n < L (L = hidden), 0 after: every step's actuation a decision variable
+CTRL_COM = 4      # a = scale * tanh(W z + b), z = [target, group centres of mass, group mean velocities]
 
 BC_STICKY = 0
 BC_SLIP = 1
@@ -117,7 +118,16 @@ def n_ctrl_params(ctrl_type: int, n_groups: int, dim: int, hidden: int) -> int:
         return hidden * zin + hidden + hidden * hidden + hidden + n_groups * hidden + n_groups
     if ctrl_type == CTRL_TABLE:
         return hidden * n_groups
+    if ctrl_type == CTRL_COM:
+        return dim + n_groups * dim * (1 + 2 * n_groups) + n_groups
     raise ValueError(f"unknown controller type {ctrl_type}")
+
+
+def com_init(rng: np.random.Generator, n_groups: int, dim: int, target) -> np.ndarray:
+    """Closed-loop controller parameters: the target, W ~ N(0, 1/Z), b = 0 (Z = dim (1 + 2G))."""
+    Z = dim * (1 + 2 * n_groups)
+    W = rng.normal(size=(n_groups, Z)) / math.sqrt(Z)
+    return np.concatenate([np.asarray(target, np.float64).ravel(), W.ravel(), np.zeros(n_groups)])
 
 
 def mlp_init(rng: np.random.Generator, n_groups: int, dim: int, hidden: int) -> np.ndarray:
@@ -367,6 +377,8 @@ def blob(dim: int, n: int, n_particles: int, seed: int, *, dt: float = 1e-3, E: 
     d /= np.linalg.norm(d, axis=1, keepdims=True)
     if ctrl_type == CTRL_MLP:
         params = mlp_init(rng, G, dim, hidden)
+    elif ctrl_type == CTRL_COM:
+        params = com_init(rng, G, dim, center + rng.uniform(-0.2, 0.2, dim))
     else:
         params = amp * rng.normal(size=n_ctrl_params(ctrl_type, G, dim, hidden))
     spec = _finish(f"blob{dim}d_{n}_{n_particles}_{seed}", dim, n, dx, dt, E, s, pos, group, d,

@@ -307,7 +307,35 @@ def test_controller_adjoint_fd(ctrl):
         assert np.all(gx == 0)
 
 
-@pytest.mark.parametrize("ctrl,dim", [(S.CTRL_SIN, 2), (S.CTRL_BASIS, 2), (S.CTRL_MLP, 3), (S.CTRL_TABLE, 2)])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_closed_loop_controller_adjoint_fd(dim):
+    """The closed-loop form a = scale tanh(W z + b), z = [target, group centres of mass, group
+    velocities]: its reverse for the parameters (target included), x and v against central
+    differences; particles of no group get no x or v adjoint."""
+    rng = np.random.default_rng(50 + dim)
+    sp = S.blob(dim, 12, 40, 19, n_groups=3, ctrl_type=S.CTRL_COM, scale=3.0, v_scale=0.5)
+    sp.group[::7] = -1  # some particles in no group
+    sc = O.Scene(sp)
+    x, v = sc.initial_state()[:2]
+    step, h = 5, 1e-6
+    ga = rng.normal(size=sc.G)
+    gp, gx, gv = sc.controller_adjoint(step, x, ga, v=v)
+    a = lambda **k: sc.controller(step, k.get("x", x), params=k.get("p"), v=k.get("v", v))
+    pd = rng.normal(size=sc.params.shape)
+    fd = ga @ (a(p=sc.params + h * pd) - a(p=sc.params - h * pd)) / (2 * h)
+    assert abs(fd - gp @ pd) <= 1e-7 * max(1, abs(fd))
+    xd = rng.normal(size=x.shape)
+    fd = ga @ (a(x=x + h * xd) - a(x=x - h * xd)) / (2 * h)
+    assert abs(fd - np.sum(gx * xd)) <= 1e-7 * max(1, abs(fd))
+    vd = rng.normal(size=v.shape)
+    fd = ga @ (a(v=v + h * vd) - a(v=v - h * vd)) / (2 * h)
+    assert abs(fd - np.sum(gv * vd)) <= 1e-7 * max(1, abs(fd))
+    assert np.all(gx[::7] == 0) and np.all(gv[::7] == 0)
+    assert np.any(gv != 0)
+
+
+@pytest.mark.parametrize("ctrl,dim", [(S.CTRL_SIN, 2), (S.CTRL_BASIS, 2), (S.CTRL_MLP, 3), (S.CTRL_TABLE, 2),
+                                      (S.CTRL_COM, 2), (S.CTRL_COM, 3)])
 def test_rollout_gradient_fd(ctrl, dim):
     """I7 over a rollout: the chain rule of Section III from a loss on the final state back to the
     initial v0, x0 and the controller parameters used at every step, against FP64 central FD
