@@ -74,8 +74,14 @@ const char* mpm_status_str(mpm_status s);
  *  MPM_CTRL_TABLE every step's actuation is a decision variable (the trajectory-optimisation
  *                 examples, Section V-C): a_g(t_n) = U[n][g] for steps 0 <= n < L, 0 after
  *                                                                          params U[L][G], L = ctrl_hidden
+ *  MPM_CTRL_COM   the closed-loop controller of Section V-B: a = scale * tanh(W z + b) with
+ *                 z = [target, c_1..c_G, u_1..u_G], c_g and u_g the means of x and v over group g
+ *                 (0 for an empty group)                                  params target[dim],
+ *                                                                          W[G][dim (1 + 2G)], b[G]
+ *                 (the gradient includes dL/dtarget; the reverse pass adds dL/dx and dL/dv through
+ *                 the group means)
  * with t = n * dt at the start of step n (n the scene's step counter). */
-enum { MPM_CTRL_SIN = 0, MPM_CTRL_BASIS = 1, MPM_CTRL_MLP = 2, MPM_CTRL_TABLE = 3 };
+enum { MPM_CTRL_SIN = 0, MPM_CTRL_BASIS = 1, MPM_CTRL_MLP = 2, MPM_CTRL_TABLE = 3, MPM_CTRL_COM = 4 };
 enum { MPM_BC_STICKY = 0, MPM_BC_SLIP = 1 };
 enum { MPM_IMPL_TILED = 0, MPM_IMPL_PLAIN = 1 };
 

@@ -74,6 +74,7 @@ int ctrl_param_count(int type, int G, int dim, int H) {
     return H * Z + H + H * H + H + G * H + G;
   }
   if (type == MPM_CTRL_TABLE) return H >= 0 ? H * G : -1;
+  if (type == MPM_CTRL_COM) return dim + G * dim * (1 + 2 * G) + G;
   return -1;
 }
 
@@ -776,10 +777,12 @@ mpm_status mpm_scene_create(mpm_ctx* c, const mpm_scene_desc* d, mpm_scene** out
   ALLOC(params, std::max(1, np));
   ALLOC(gparams, std::max(1, np));
   ALLOC(inv_count, std::max(1, s->G));
-  ALLOC(centroid, MAX_GROUPS * 3 + 3);
-  ALLOC(gz, MAX_GROUPS * 3);
+  // centroid: the MLP's group and body centroids, or the closed-loop input z (3 (1 + 2G) floats);
+  // gz: dL/d(centroids), or dL/d(group means of x, then of v); partial rows: x, then v
+  ALLOC(centroid, 3 * (1 + 2 * MAX_GROUPS));
+  ALLOC(gz, MAX_GROUPS * 6);
   const int rows = std::max(1, reduction_rows(s->N));
-  ALLOC(partials, size_t(rows) * RED_ROW_FLOATS);
+  ALLOC(partials, 2 * size_t(rows) * RED_ROW_FLOATS);
   cp.params = params;
   cp.gparams = gparams;
   cp.inv_count = inv_count;

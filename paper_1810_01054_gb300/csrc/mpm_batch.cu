@@ -210,7 +210,7 @@ mpm_status forward_step(mpm_batch* B) {
   CK(launch_select(sb.dsel, n, sb.cur, st));
   for (int m = 0; m < n; ++m) {
     mpm_scene* s = B->slots[sb.members[m]].s;
-    if (s->ctrl.type == MPM_CTRL_MLP) CK(ctrl_step_forward(s->hp, sb.cur + m, s->ctrl, st));
+    if (ctrl_reads_state(s->ctrl)) CK(ctrl_step_forward(s->hp, sb.cur + m, s->ctrl, st));
   }
   if (sb.need_keys) {
     CK(launch_keys<D>(sb.b, st));
@@ -232,7 +232,7 @@ mpm_status reverse_step(mpm_batch* B) {
   CK(launch_keys<D>(sb.b, st));
   for (int m = 0; m < n; ++m) {
     mpm_scene* s = B->slots[sb.members[m]].s;
-    if (s->ctrl.type == MPM_CTRL_MLP) CK(ctrl_step_forward(s->hp, sb.cur + m, s->ctrl, st));
+    if (ctrl_reads_state(s->ctrl)) CK(ctrl_step_forward(s->hp, sb.cur + m, s->ctrl, st));
   }
   CK(launch_sort<D>(sb.b, st));
   CK(launch_p2g<D>(sb.b, true, st));
@@ -240,7 +240,7 @@ mpm_status reverse_step(mpm_batch* B) {
   CK(ctrl_backward_batched(sb.cur, sb.dctrl, n, st));  // rewinds every member's reverse counter
   for (int m = 0; m < n; ++m) {
     mpm_scene* s = B->slots[sb.members[m]].s;
-    if (s->ctrl.type == MPM_CTRL_MLP) CK(ctrl_scatter_x(s->hp, sb.cur + m, s->ctrl, st));
+    if (ctrl_reads_state(s->ctrl)) CK(ctrl_scatter_x(s->hp, sb.cur + m, s->ctrl, st));
   }
   return MPM_OK;
 }

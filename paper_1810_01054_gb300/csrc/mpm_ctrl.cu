@@ -43,6 +43,12 @@ __global__ void __launch_bounds__(256) k_group_rows(const ScenePar* __restrict__
         const float xv[3] = {q.x, q.y, q.z};
 #pragma unroll
         for (int c = 0; c < CH; ++c) val[c] = xv[c];
+      } else if (mode == 2) {  // v: floats D + D*D .. of the state, inside one plane for D = 2, 3
+        constexpr int O = CH + CH * CH;
+        const float4 q = sp.planes[size_t(O / 4) * sp.npad + p];
+        const float qv[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int c = 0; c < CH; ++c) val[c] = qv[O % 4 + c];
       } else {
         val[0] = sp.sig_contrib[p];
       }
@@ -155,6 +161,41 @@ __global__ void __launch_bounds__(1024) k_ctrl_forward(const ScenePar* __restric
   }
 }
 
+// Closed-loop controller of step n (type 4, Section V-B): z = [target, c_g, u_g] with c_g, u_g the
+// group means of x and v (partial rows of x, then of v), a = scale * tanh(W z + b) -> sp.act; z is
+// kept in c.centroid for the reverse step.
+__global__ void __launch_bounds__(1024) k_ctrl_forward_com(const ScenePar* __restrict__ dsp, CtrlPar c,
+                                                           const float* rows, int n_rows) {
+  pdl_enter();
+  const ScenePar& sp = *dsp;
+  __shared__ float rx[MAX_GROUPS * 3 + 3], rv[MAX_GROUPS * 3 + 3];
+  __shared__ float z[3 * (1 + 2 * MAX_GROUPS)];
+  const int G = c.G, dim = c.dim, tid = threadIdx.x, Z = dim * (1 + 2 * G);
+  reduce_rows(rows, n_rows, G, dim, rx);
+  reduce_rows(rows + size_t(n_rows) * (MAX_GROUPS * 3 + 3), n_rows, G, dim, rv);
+  if (tid < Z) {
+    float val;
+    if (tid < dim) {
+      val = c.params[tid];
+    } else if (tid < dim + G * dim) {
+      const int i = tid - dim;
+      val = rx[(i / dim) * 3 + i % dim] * c.inv_count[i / dim];
+    } else {
+      const int i = tid - dim - G * dim;
+      val = rv[(i / dim) * 3 + i % dim] * c.inv_count[i / dim];
+    }
+    z[tid] = val;
+    c.centroid[tid] = val;
+  }
+  __syncthreads();
+  if (tid < G) {
+    const float* W = c.params + dim + size_t(tid) * Z;
+    float u = c.params[dim + size_t(G) * Z + tid];
+    for (int j = 0; j < Z; ++j) u += W[j] * z[j];
+    sp.act[tid] = c.scale * tanhf(u);
+  }
+}
+
 // ----------------------------------------------------------------------------- backward
 // dL/da_g = sum over the group of the (K) contributions; accumulate dL/dparams for step n;
 // for the MLP also dL/dz, turned into per-group coefficients for the x adjoint.
@@ -226,6 +267,27 @@ __device__ void ctrl_backward_body(const ScenePar& sp, const CtrlPar& c) {
     if (tid < G) c.gparams[tid] += ga[tid] * sinf(kTwoPi * c.freq * t);
   } else if (c.type == 3) {  // table: dL/dU[n][g] = dL/da_g(t_n)
     if (tid < G && n >= 0 && n < c.hidden) c.gparams[size_t(n) * G + tid] += ga[tid];
+  } else if (c.type == 4) {  // closed loop: z of this step from the forward replay in c.centroid
+    const int dim = c.dim, Z = dim * (1 + 2 * G);
+    __shared__ float gu4[MAX_GROUPS];
+    if (tid < G) {
+      const float* W = c.params + dim + size_t(tid) * Z;
+      float u = c.params[dim + size_t(G) * Z + tid];
+      for (int j = 0; j < Z; ++j) u += W[j] * c.centroid[j];
+      const float th = tanhf(u);
+      gu4[tid] = ga[tid] * c.scale * (1.0f - th * th);
+      c.gparams[dim + size_t(G) * Z + tid] += gu4[tid];  // b
+    }
+    __syncthreads();
+    for (int i = tid; i < G * Z; i += blockDim.x) c.gparams[dim + i] += gu4[i / Z] * c.centroid[i % Z];  // W
+    if (tid < Z) {  // dL/dz: the target's part goes to its parameters, the group means' to gz
+      float sacc = 0.0f;
+      for (int g = 0; g < G; ++g) sacc += c.params[dim + size_t(g) * Z + tid] * gu4[g];
+      if (tid < dim)
+        c.gparams[tid] += sacc;
+      else
+        c.gz[tid - dim] = sacc;  // [c_g part (G*dim)][u_g part (G*dim)]
+    }
   } else if (c.type == 1) {
     if (tid < G * 4) {
       const int g = tid / 4, j = tid - 4 * g;
@@ -309,18 +371,23 @@ __global__ void __launch_bounds__(1024) k_ctrl_backward_multi(const ScenePar* __
   ctrl_backward_body(cur[blockIdx.x], cs[blockIdx.x]);
 }
 
-// x adjoint of the MLP input: z_g = c_g - c_body, c_g = mean of x over g, c_body = mean over all.
+// x (and, for the closed-loop form, v) adjoint of the controller input: the MLP's centroids
+// (z_g = c_g - c_body, so the body term), or the closed-loop form's group means of x and v.
 template <int D>
 __global__ void k_ctrl_scatter_x(const ScenePar* __restrict__ dsp, CtrlPar c) {
   pdl_enter();
   const ScenePar& sp = *dsp;
-  __shared__ float coef[MAX_GROUPS * 3], body[3];
+  __shared__ float coef[MAX_GROUPS * 3], coefv[MAX_GROUPS * 3], body[3];
   const int G = c.G;
-  for (int i = threadIdx.x; i < G * D; i += blockDim.x) coef[i] = c.gz[i] * c.inv_count[i / D];
+  const bool com = c.type == 4;
+  for (int i = threadIdx.x; i < G * D; i += blockDim.x) {
+    coef[i] = c.gz[i] * c.inv_count[i / D];
+    coefv[i] = com ? c.gz[G * D + i] * c.inv_count[i / D] : 0.0f;
+  }
   if (threadIdx.x < D) {
     float s = 0.0f;
     for (int g = 0; g < G; ++g) s += c.gz[g * D + threadIdx.x];
-    body[threadIdx.x] = -s * c.inv_n;
+    body[threadIdx.x] = com ? 0.0f : -s * c.inv_n;
   }
   __syncthreads();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -336,20 +403,40 @@ __global__ void k_ctrl_scatter_x(const ScenePar* __restrict__ dsp, CtrlPar c) {
   q.y += add[1];
   if (D == 3) q.z += add[2];
   sp.adj_out[p] = q;
+  if (com && g >= 0 && g < G) {  // v: floats D + D*D .. of the adjoint state, inside one plane
+    constexpr int O = D + D * D;
+    float4* pv = sp.adj_out + size_t(O / 4) * sp.npad + p;
+    float4 w = *pv;
+    float* wc = reinterpret_cast<float*>(&w);
+#pragma unroll
+    for (int a = 0; a < D; ++a) wc[O % 4 + a] += coefv[g * D + a];
+    *pv = w;
+  }
 }
 
-// Controller forward for one step: the MLP form only (group centroid rows, then the network).
+// Controller forward for one step: the forms that read the state (MLP on centroids, closed loop on
+// group means of x and v): group rows, then the controller.
 cudaError_t ctrl_step_forward(const ScenePar& sp, const ScenePar* dsp, const CtrlPar& c, cudaStream_t s) {
-  if (c.type != 2 || c.G == 0) return cudaSuccess;
+  if (!ctrl_reads_state(c)) return cudaSuccess;
   const int rows = reduction_rows(sp.N);
+  const bool com = c.type == 4;
+  int n = 0;
   if (rows > 0) {
-    if (sp.dim == 2)
+    float* vrows = c.partials + size_t(rows) * RED_STRIDE;
+    if (sp.dim == 2) {
       launch_pdl(k_group_rows<2>, dim3(rows), dim3(256), 0, s, dsp, c.partials, 0);
-    else
+      if (com) launch_pdl(k_group_rows<2>, dim3(rows), dim3(256), 0, s, dsp, vrows, 2);
+    } else {
       launch_pdl(k_group_rows<3>, dim3(rows), dim3(256), 0, s, dsp, c.partials, 0);
+      if (com) launch_pdl(k_group_rows<3>, dim3(rows), dim3(256), 0, s, dsp, vrows, 2);
+    }
+    n += com ? 2 : 1;
   }
-  launch_pdl(k_ctrl_forward, dim3(1), dim3(1024), 0, s, dsp, c, c.partials, rows);
-  count_launches(rows > 0 ? 2 : 1);
+  if (com)
+    launch_pdl(k_ctrl_forward_com, dim3(1), dim3(1024), 0, s, dsp, c, c.partials, rows);
+  else
+    launch_pdl(k_ctrl_forward, dim3(1), dim3(1024), 0, s, dsp, c, c.partials, rows);
+  count_launches(n + 1);
   return cudaGetLastError();
 }
 
@@ -363,7 +450,7 @@ cudaError_t ctrl_backward_batched(const ScenePar* cur, const CtrlPar* cs, int n,
 }
 
 cudaError_t ctrl_scatter_x(const ScenePar& sp, const ScenePar* dsp, const CtrlPar& c, cudaStream_t s) {
-  if (c.type != 2 || c.G == 0 || sp.N == 0) return cudaSuccess;
+  if (!ctrl_reads_state(c) || sp.N == 0) return cudaSuccess;
   if (sp.dim == 2)
     launch_pdl(k_ctrl_scatter_x<2>, dim3((sp.N + 255) / 256), dim3(256), 0, s, dsp, c);
   else
@@ -376,13 +463,13 @@ cudaError_t ctrl_scatter_x(const ScenePar& sp, const ScenePar* dsp, const CtrlPa
 // centroid adjoint added to dL/dx of state n.  Rewinds the scene's step counter.
 cudaError_t ctrl_step_backward(const ScenePar& sp, const ScenePar* dsp, const CtrlPar& c, cudaStream_t s) {
   launch_pdl(k_ctrl_backward, dim3(1), dim3(1024), 0, s, dsp, c);
-  if (c.type == 2 && c.G > 0 && sp.N > 0) {
+  if (ctrl_reads_state(c) && sp.N > 0) {
     if (sp.dim == 2)
       launch_pdl(k_ctrl_scatter_x<2>, dim3((sp.N + 255) / 256), dim3(256), 0, s, dsp, c);
     else
       launch_pdl(k_ctrl_scatter_x<3>, dim3((sp.N + 255) / 256), dim3(256), 0, s, dsp, c);
   }
-  count_launches(1 + ((c.type == 2 && c.G > 0 && sp.N > 0) ? 1 : 0));
+  count_launches(1 + ((ctrl_reads_state(c) && sp.N > 0) ? 1 : 0));
   return cudaGetLastError();
 }
 

@@ -178,7 +178,10 @@ struct CtrlPar {
   int whole;              // tiled form, scene alone in its batch: its rows are all active slots
 };
 
-int reduction_rows(int N);                  // partial rows of the group reductions
+// Controllers whose input is the state (MLP on centroids, closed loop on group means of x and v):
+// they need group reductions each step and add an input adjoint to dL/dx (and dL/dv).
+inline bool ctrl_reads_state(const CtrlPar& c) { return (c.type == 2 || c.type == 4) && c.G > 0; }
+int reduction_rows(int N);                  // partial rows of the group reductions (per reduced quantity)
 constexpr int RED_ROW_FLOATS = MAX_GROUPS * 3 + 3;  // floats per partial row
 // Controller forward (MLP form; the sinusoid forms are evaluated by k_select) and the reverse of
 // the step *sp.step_ctr, which it then decrements.

@@ -48,7 +48,7 @@ def assert_grad_close(gpu, ref, name, tol=GRAD_TOL, cos=GRAD_COS):
 
 def oracle_step_from(spec, state, step):
     sc = O.Scene(spec)
-    act = sc.controller(step, state[0])
+    act = sc.controller(step, state[0], v=state[1])
     return sc.step(act, *state)
 
 

@@ -52,7 +52,17 @@ def small_scenes():
                            v_scale=0.3, amp=3.0),
         "3d_table": S.blob(3, 20, 500, 8, ctrl_type=S.CTRL_TABLE, n_groups=3, hidden=30, radius_cells=3.5,
                            v_scale=0.3, amp=3.0),
+        # the closed-loop controller on group centres of mass and velocities (some particles in no group)
+        "2d_com": _ungroup(S.blob(2, 32, 300, 9, ctrl_type=S.CTRL_COM, n_groups=4, scale=5.0, radius_cells=4.5,
+                                  v_scale=0.5)),
+        "3d_com": _ungroup(S.blob(3, 20, 500, 10, ctrl_type=S.CTRL_COM, n_groups=3, scale=5.0, radius_cells=3.5,
+                                  v_scale=0.5)),
     }
+
+
+def _ungroup(spec, every=9):
+    spec.group[::every] = -1
+    return spec
 
 
 @pytest.mark.parametrize("impl", IMPLS, ids=["tiled", "plain"])
@@ -104,7 +114,8 @@ def test_walker_square_full_horizon_gradient(M, ctx, impl):
     assert_grad_close(gF, ogF, "dL/dF0")
 
 
-@pytest.mark.parametrize("name", ["2d_basis", "3d_mlp", "2d_slip_friction", "3d_sticky", "2d_table", "3d_table"])
+@pytest.mark.parametrize("name", ["2d_basis", "3d_mlp", "2d_slip_friction", "3d_sticky", "2d_table", "3d_table",
+                                  "2d_com", "3d_com"])
 def test_controller_and_state_gradients(M, ctx, name):
     spec = small_scenes()[name]
     T = 25
