@@ -44,6 +44,9 @@ typedef struct {
   double ctrl_scale;
   const double* p_E;      // [N] per-particle Young's modulus, NULL = E for every particle
   const double* p_m;      // [N] per-particle mass, NULL = p_mass for every particle
+  const int* wall_kind;   // [2 dim] per wall (axis a, low side 2a, high side 2a+1): 0 sticky,
+                          // 1 slip with friction wall_c, 2 open; NULL = bc_type on every wall
+  const double* wall_c;   // [2 dim] friction of each wall, NULL = friction_c
 } oracle_scene;
 
 }  // extern "C"
@@ -295,39 +298,52 @@ void project_adjoint(const ProjTape& t, double c, int d, const double* gout, dou
   for (int a = 0; a < d; ++a) gv[a] = g_ln * t.n[a] + g_vt[a];
 }
 
-// Boundary condition applied to a node velocity.  Sticky: zero in the band.  Slip: the walls
-// whose band contains the node are applied one after another, axis 0,1,2, low side before high
-// side; the inward normal is +e_a on the low side and -e_a on the high side.
+// Boundary condition applied to a node velocity.  Wall w = 2a + side (axis a, low side first) is
+// sticky, slip with its own friction c (S5) or open; its band holds the nodes with idx[a] < width
+// (low) or idx[a] >= n_a - width (high).  A node in the band of a sticky wall is fixed (v* = 0);
+// otherwise the slip walls whose band contains it are applied one after another, axis 0,1,2, low
+// side before high side, with inward normal +e_a (low) or -e_a (high); open walls do nothing.
+// With one kind and c for every wall this is the uniform sticky or slip boundary.
 struct BCTape {
   int n_walls;
   ProjTape walls[6];
+  double c[6];
 };
+
+int wall_kind(const oracle_scene* s, int w) { return s->wall_kind ? s->wall_kind[w] : s->bc_type; }
+double wall_c(const oracle_scene* s, int w) { return s->wall_c ? s->wall_c[w] : s->friction_c; }
+bool wall_hit(const oracle_scene* s, const int* idx, int w) {
+  const int a = w >> 1;
+  return (w & 1) ? idx[a] >= s->n_grid[a] - s->bc_width : idx[a] < s->bc_width;
+}
+bool sticky_node(const oracle_scene* s, const int* idx) {
+  for (int w = 0; w < 2 * s->dim; ++w)
+    if (wall_hit(s, idx, w) && wall_kind(s, w) == 0) return true;
+  return false;
+}
 
 void bc_forward(const oracle_scene* s, const int* idx, const double* vin, double* vout, BCTape* tape) {
   int d = s->dim;
   if (tape) tape->n_walls = 0;
-  bool band = in_band(s, idx);
-  if (!band) {
+  if (!in_band(s, idx)) {
     for (int a = 0; a < d; ++a) vout[a] = vin[a];
     return;
   }
-  if (s->bc_type == 0) {
+  if (sticky_node(s, idx)) {
     for (int a = 0; a < d; ++a) vout[a] = 0;
     return;
   }
   double v[3] = {0, 0, 0};
   for (int a = 0; a < d; ++a) v[a] = vin[a];
-  for (int a = 0; a < d; ++a) {
-    for (int side = 0; side < 2; ++side) {
-      bool hit = side == 0 ? idx[a] < s->bc_width : idx[a] >= s->n_grid[a] - s->bc_width;
-      if (!hit) continue;
-      double nrm[3] = {0, 0, 0};
-      nrm[a] = side == 0 ? 1.0 : -1.0;
-      double out[3];
-      ProjTape* t = tape ? &tape->walls[tape->n_walls++] : nullptr;
-      project_forward(v, nrm, s->friction_c, d, out, t);
-      for (int b = 0; b < d; ++b) v[b] = out[b];
-    }
+  for (int w = 0; w < 2 * d; ++w) {
+    if (!wall_hit(s, idx, w) || wall_kind(s, w) != 1) continue;
+    double nrm[3] = {0, 0, 0};
+    nrm[w >> 1] = (w & 1) ? -1.0 : 1.0;
+    double out[3];
+    if (tape) tape->c[tape->n_walls] = wall_c(s, w);
+    ProjTape* t = tape ? &tape->walls[tape->n_walls++] : nullptr;
+    project_forward(v, nrm, wall_c(s, w), d, out, t);
+    for (int b = 0; b < d; ++b) v[b] = out[b];
   }
   for (int a = 0; a < d; ++a) vout[a] = v[a];
 }
@@ -338,7 +354,7 @@ void bc_adjoint(const oracle_scene* s, const int* idx, const BCTape& tape, const
     for (int a = 0; a < d; ++a) gin[a] = gout[a];
     return;
   }
-  if (s->bc_type == 0) {
+  if (sticky_node(s, idx)) {
     for (int a = 0; a < d; ++a) gin[a] = 0;
     return;
   }
@@ -346,7 +362,7 @@ void bc_adjoint(const oracle_scene* s, const int* idx, const BCTape& tape, const
   for (int a = 0; a < d; ++a) g[a] = gout[a];
   for (int w = tape.n_walls - 1; w >= 0; --w) {
     double gi[3];
-    project_adjoint(tape.walls[w], s->friction_c, d, g, gi);
+    project_adjoint(tape.walls[w], tape.c[w], d, g, gi);
     for (int a = 0; a < d; ++a) g[a] = gi[a];
   }
   for (int a = 0; a < d; ++a) gin[a] = g[a];

@@ -54,6 +54,8 @@ class _Scene(C.Structure):
         ("ctrl_scale", C.c_double),
         ("p_E", C.c_void_p),
         ("p_m", C.c_void_p),
+        ("wall_kind", C.c_void_p),
+        ("wall_c", C.c_void_p),
     ]
 
 
@@ -123,6 +125,11 @@ class Scene:
         self._E = None if E_arr is None else _f64(E_arr).ravel()
         self._m = None if m_arr is None else _f64(m_arr).ravel()
         s.p_E, s.p_m = _p(self._E), _p(self._m)
+        # optional per-wall boundary kinds and friction (NULL: bc_type and friction_c on every wall)
+        wk, wc = getattr(spec, "wall_kind", None), getattr(spec, "wall_c", None)
+        self._wk = None if wk is None else np.ascontiguousarray(np.asarray(wk, dtype=np.int32).ravel())
+        self._wc = None if wc is None else _f64(wc).ravel()
+        s.wall_kind, s.wall_c = _p(self._wk), _p(self._wc)
         self.struct = s
         self.params = _f64(spec.ctrl_params).ravel()
         self.n_nodes = int(np.prod(ng[:d]))

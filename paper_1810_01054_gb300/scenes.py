@@ -44,6 +44,7 @@ CTRL_COM = 4      # a = scale * tanh(W z + b), z = [target, group centres of mas
 
 BC_STICKY = 0
 BC_SLIP = 1
+BC_OPEN = 2       # per-wall only: the wall constrains nothing
 
 
 @dataclasses.dataclass
@@ -78,6 +79,9 @@ class SceneSpec:
     ckpt_interval: int = 0
     E_arr: Optional[np.ndarray] = None     # [N] per-particle Young's modulus (None: E for all)
     mass_arr: Optional[np.ndarray] = None  # [N] per-particle mass (None: p_mass for all)
+    # per wall w = 2 axis + side (low side first): 0 sticky, 1 slip with friction wall_c[w], 2 open
+    wall_kind: Optional[np.ndarray] = None  # [2 dim] int32 (None: bc_type on every wall)
+    wall_c: Optional[np.ndarray] = None     # [2 dim] (None: friction_c on every wall)
 
     @property
     def n_particles(self) -> int:
