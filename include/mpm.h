@@ -82,7 +82,7 @@ const char* mpm_status_str(mpm_status s);
  *                 the group means)
  * with t = n * dt at the start of step n (n the scene's step counter). */
 enum { MPM_CTRL_SIN = 0, MPM_CTRL_BASIS = 1, MPM_CTRL_MLP = 2, MPM_CTRL_TABLE = 3, MPM_CTRL_COM = 4 };
-enum { MPM_BC_STICKY = 0, MPM_BC_SLIP = 1 };
+enum { MPM_BC_STICKY = 0, MPM_BC_SLIP = 1, MPM_BC_OPEN = 2 /* per wall only (mpm_scene_set_walls) */ };
 enum { MPM_IMPL_TILED = 0, MPM_IMPL_PLAIN = 1 };
 
 typedef struct {
@@ -167,6 +167,15 @@ mpm_status mpm_set_ctrl_params(mpm_scene* scene, const float* params, int n, int
  * reverse pass; outputs on the host or the device per mem_space; NULL skips one). */
 mpm_status mpm_scene_set_material(mpm_scene* scene, const float* E, const float* mass, int mem_space);
 mpm_status mpm_get_material_gradients(mpm_scene* scene, float* gE, float* gm, int mem_space);
+/* Per-wall boundary (Supplement S5's friction projection on selected walls).  Wall w = 2a + side
+ * (axis a, side 0 = low) gets kind[w] (MPM_BC_STICKY, MPM_BC_SLIP with Coulomb friction c[w] >= 0,
+ * or MPM_BC_OPEN) for w < 2 dim; the band depth stays bc_width.  A node in a sticky wall's band is
+ * fixed; otherwise the slip walls whose band contains it are applied in sequence (axis 0, 1, 2, low
+ * side first), each with its own c; open walls constrain nothing (a particle whose stencil then
+ * leaves the grid is MPM_ERR_DOMAIN as always).  NULL kind or c keeps the current values.
+ * Synchronises; invalidates an earlier rollout.  MPM_ERR_ARG (and nothing changes) for an unknown
+ * kind or a negative or non-finite c. */
+mpm_status mpm_scene_set_walls(mpm_scene* scene, const int* kind, const float* c);
 /* Grid of the last forward step: mass m_i [nodes] and velocity v*_i [nodes][dim] after the
  * boundary condition (nodes never touched by a particle hold stale values for the tiled form). */
 mpm_status mpm_get_grid(mpm_scene* scene, float* m, float* v, int mem_space);

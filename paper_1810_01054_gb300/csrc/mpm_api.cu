@@ -365,6 +365,17 @@ void invalidate_graphs(mpm_scene* s) {
       }
 }
 
+// After a change of the scene template (material, walls): the in-place step's record table is
+// rebuilt now, rollout and reverse tables at the next mpm_rollout; graphs of the plain form hold
+// the record by value, so they are captured again.
+mpm_status refresh_records(mpm_scene* s) {
+  s->have_rollout = false;
+  s->have_grad = false;
+  invalidate_graphs(s);
+  std::vector<ScenePar> t0(1, rec_fwd(s, s->state, s->state));
+  return upload_table(s, 0, t0);
+}
+
 mpm_status set_counter(mpm_scene* s, int* dctr, int value) {
   CK(launch_set_int(dctr, value, s->ctx->stream));
   return MPM_OK;
@@ -712,9 +723,11 @@ mpm_status mpm_scene_create(mpm_ctx* c, const mpm_scene_desc* d, mpm_scene** out
   p.gmat = nullptr;
   p.mass = d->p_mass;
   p.vol = d->p_vol;
-  p.bc.type = d->bc_type;
   p.bc.width = d->bc_width;
-  p.bc.c = d->friction_c;
+  for (int w = 0; w < 6; ++w) {  // the same kind and friction on every wall
+    p.bc.kind[w] = d->bc_type;
+    p.bc.c[w] = d->friction_c;
+  }
   p.N = s->N;
   p.npad = s->npad;
   p.G = s->G;
@@ -1045,14 +1058,22 @@ mpm_status mpm_scene_set_material(mpm_scene* s, const float* E, const float* mas
   s->hp.pmass = mass ? s->d_pmass : nullptr;
   s->hp.gmat = (E || mass) ? reinterpret_cast<float2*>(s->d_gmat) : nullptr;
   s->b.has_material = s->hp.gmat ? 1 : 0;
-  // records built from the old material are stale: the in-place step's table now, rollout and
-  // reverse tables at the next mpm_rollout; graphs of the plain form hold the record by value
-  s->have_rollout = false;
-  s->have_grad = false;
-  invalidate_graphs(s);
-  std::vector<ScenePar> t0(1, rec_fwd(s, s->state, s->state));
-  CKS(upload_table(s, 0, t0));
-  return MPM_OK;
+  return refresh_records(s);
+}
+
+mpm_status mpm_scene_set_walls(mpm_scene* s, const int* kind, const float* c) {
+  if (!s) return MPM_ERR_ARG;
+  const int nw = 2 * s->dim;
+  for (int w = 0; w < nw; ++w) {
+    if (kind && (kind[w] < MPM_BC_STICKY || kind[w] > MPM_BC_OPEN)) return MPM_ERR_ARG;
+    if (c && !(std::isfinite(c[w]) && c[w] >= 0.0f)) return MPM_ERR_ARG;
+  }
+  CK(cudaStreamSynchronize(s->ctx->stream));
+  for (int w = 0; w < nw; ++w) {
+    if (kind) s->hp.bc.kind[w] = kind[w];
+    if (c) s->hp.bc.c[w] = c[w];
+  }
+  return refresh_records(s);
 }
 
 mpm_status mpm_get_material_gradients(mpm_scene* s, float* gE, float* gm, int mem_space) {

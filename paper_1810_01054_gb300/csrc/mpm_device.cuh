@@ -288,20 +288,21 @@ __device__ __forceinline__ void nh_hessian_apply(const float (&A)[D][D], float J
 }
 
 // --------------------------------------------------------------------------- boundary (S5)
+// Boundary of the grid: a band `width` nodes deep along each of the 2 dim walls; wall w = 2a + side
+// (axis a, low side 0) is sticky (kind 0), slip with Coulomb friction c[w] (kind 1, S5) or open
+// (kind 2).
 struct BCPar {
-  int type;   // 0 sticky, 1 slip with friction c
-  int width;  // band width in nodes
-  float c;
+  int width;
+  int kind[6];
+  float c[6];
 };
 
 constexpr float kBCEps = 1e-20f;
 
-template <int D>
-__device__ __forceinline__ bool in_band(const int* idx, const int* n, int b) {
-  bool r = false;
-#pragma unroll
-  for (int a = 0; a < D; ++a) r = r || idx[a] < b || idx[a] >= n[a] - b;
-  return r;
+// Whether node idx lies in wall w's band.
+__device__ __forceinline__ bool wall_hit(const int* idx, const int* n, int width, int w) {
+  const int a = w >> 1;
+  return (w & 1) ? idx[a] >= n[a] - width : idx[a] < width;
 }
 
 // One wall: v <- l_t* v_t / l_t + max(l_n, 0) n, l_t* = max(l_t + c min(l_n, 0), 0).
@@ -358,28 +359,42 @@ __device__ __forceinline__ void project_adj(const float* v, int axis, float sgn,
   for (int a = 0; a < D; ++a) g[a] = gvt[a] + (a == axis ? g_ln * sgn : 0.0f);
 }
 
-// Boundary condition on the node velocity (gravity already added).  Walls of a slip node are
-// applied in sequence: axis 0, 1, 2, low side before high side.
+// Boundary condition on the node velocity (gravity already added).  A node in a sticky wall's
+// band is fixed; otherwise the slip walls whose band contains it are applied in sequence: axis
+// 0, 1, 2, low side before high side, each with its own friction; open walls do nothing.
 template <int D>
-__device__ __forceinline__ void bc_apply(const int* idx, const int* n, BCPar bc, float* v) {
-  if (!in_band<D>(idx, n, bc.width)) return;
-  if (bc.type == 0) {
+__device__ __forceinline__ void bc_apply(const int* idx, const int* n, const BCPar& bc, float* v) {
+  bool hit[2 * D], any = false, sticky = false;
+#pragma unroll
+  for (int w = 0; w < 2 * D; ++w) {
+    hit[w] = wall_hit(idx, n, bc.width, w);
+    any = any || hit[w];
+    sticky = sticky || (hit[w] && bc.kind[w] == 0);
+  }
+  if (!any) return;
+  if (sticky) {
 #pragma unroll
     for (int a = 0; a < D; ++a) v[a] = 0.0f;
     return;
   }
 #pragma unroll
-  for (int a = 0; a < D; ++a) {
-    if (idx[a] < bc.width) project<D>(v, a, 1.0f, bc.c);
-    if (idx[a] >= n[a] - bc.width) project<D>(v, a, -1.0f, bc.c);
-  }
+  for (int w = 0; w < 2 * D; ++w)
+    if (hit[w] && bc.kind[w] == 1) project<D>(v, w >> 1, (w & 1) ? -1.0f : 1.0f, bc.c[w]);
 }
 
 // Adjoint of bc_apply: g holds dL/dv* on entry and dL/dv_g on exit; vg = velocity before BC.
 template <int D>
-__device__ __forceinline__ void bc_adjoint(const int* idx, const int* n, BCPar bc, const float* vg, float* g) {
-  if (!in_band<D>(idx, n, bc.width)) return;
-  if (bc.type == 0) {
+__device__ __forceinline__ void bc_adjoint(const int* idx, const int* n, const BCPar& bc, const float* vg,
+                                           float* g) {
+  bool hit[2 * D], any = false, sticky = false;
+#pragma unroll
+  for (int w = 0; w < 2 * D; ++w) {
+    hit[w] = wall_hit(idx, n, bc.width, w) && bc.kind[w] != 2;
+    any = any || hit[w];
+    sticky = sticky || (hit[w] && bc.kind[w] == 0);
+  }
+  if (!any) return;
+  if (sticky) {
 #pragma unroll
     for (int a = 0; a < D; ++a) g[a] = 0.0f;
     return;
@@ -387,21 +402,18 @@ __device__ __forceinline__ void bc_adjoint(const int* idx, const int* n, BCPar b
   // replay the wall sequence (wall w: axis w / 2, low side for even w) to get every wall's input,
   // then walk it backwards; the loops are unrolled so the inputs stay in registers
   float vin[2 * D][D];
-  bool hit[2 * D];
   float v[D];
 #pragma unroll
   for (int a = 0; a < D; ++a) v[a] = vg[a];
 #pragma unroll
   for (int w = 0; w < 2 * D; ++w) {
-    const int a = w >> 1;
-    hit[w] = (w & 1) ? idx[a] >= n[a] - bc.width : idx[a] < bc.width;
 #pragma unroll
     for (int b = 0; b < D; ++b) vin[w][b] = v[b];
-    if (hit[w]) project<D>(v, a, (w & 1) ? -1.0f : 1.0f, bc.c);
+    if (hit[w]) project<D>(v, w >> 1, (w & 1) ? -1.0f : 1.0f, bc.c[w]);
   }
 #pragma unroll
   for (int w = 2 * D - 1; w >= 0; --w)
-    if (hit[w]) project_adj<D>(vin[w], w >> 1, (w & 1) ? -1.0f : 1.0f, bc.c, g);
+    if (hit[w]) project_adj<D>(vin[w], w >> 1, (w & 1) ? -1.0f : 1.0f, bc.c[w], g);
 }
 
 }  // namespace gbmpm

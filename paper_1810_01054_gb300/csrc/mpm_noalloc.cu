@@ -252,9 +252,11 @@ extern "C" mpm_status mpm_step_noalloc(const mpm_noalloc_step* a, void* cuda_str
   p.mat.la = float(double(a->E) * double(a->nu) / ((1.0 + double(a->nu)) * (1.0 - 2.0 * double(a->nu))));
   p.mass = a->p_mass;
   p.vol = a->p_vol;
-  p.bc.type = a->bc_type;
   p.bc.width = a->bc_width;
-  p.bc.c = a->friction_c;
+  for (int w = 0; w < 6; ++w) {  // the same kind and friction on every wall
+    p.bc.kind[w] = a->bc_type;
+    p.bc.c[w] = a->friction_c;
+  }
   p.N = a->n_particles;
   p.G = a->n_groups;
   p.n_nodes = int(nodes);

@@ -118,6 +118,8 @@ mpm_status scene_sync_status(mpm_scene* s);
 mpm_status enqueue_step(mpm_scene* s, int ph, cudaStream_t st);
 // Drops the scene's captured graphs (they are captured again with the current launch shapes).
 void invalidate_graphs(mpm_scene* s);
+// Records rebuilt after the scene template changed (mpm_scene_set_material / _set_walls).
+mpm_status refresh_records(mpm_scene* s);
 
 // Autotuner (mpm_tune.cu).
 // Looks the scene's workload up in the cache, or arms trials for its tile kernels (mode AUTO/FORCE).

@@ -129,6 +129,7 @@ _SIGS = {
     "mpm_step_noalloc": [C.POINTER(NoAllocStep), C.c_void_p],
     "mpm_scene_set_tuning": [C.c_void_p, C.c_int],
     "mpm_scene_set_material": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int],
+    "mpm_scene_set_walls": [C.c_void_p, C.c_void_p, C.c_void_p],
     "mpm_get_material_gradients": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int],
     "mpm_scene_launch": [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)],
     "mpm_tune_cache_lookup": [C.c_int, C.c_longlong, C.c_longlong, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)],
@@ -336,6 +337,9 @@ class Scene:
         E_arr, m_arr = getattr(spec, "E_arr", None), getattr(spec, "mass_arr", None)
         if E_arr is not None or m_arr is not None:
             self.set_material(E_arr, m_arr)
+        wk, wc = getattr(spec, "wall_kind", None), getattr(spec, "wall_c", None)
+        if wk is not None or wc is not None:
+            self.set_walls(wk, wc)
         self.G = G
         self.impl = impl
 
@@ -444,6 +448,17 @@ class Scene:
                 raise ValueError("per-particle material arrays need one entry per particle")
         _check(lib().mpm_scene_set_material(self.handle, _ptr(conv[0]), _ptr(conv[1]), 1 if on_dev else 0),
                "mpm_scene_set_material")
+
+    def set_walls(self, kind=None, c=None):
+        """Per-wall boundary: kind[2 dim] (BC_STICKY / BC_SLIP / BC_OPEN), friction c[2 dim];
+        wall w = 2 axis + side, low side first.  None keeps the current values."""
+        nw = 2 * self.dim
+        k = None if kind is None else np.ascontiguousarray(np.asarray(kind, np.int32).ravel())
+        cc = None if c is None else np.ascontiguousarray(np.asarray(c, np.float32).ravel())
+        for a in (k, cc):
+            if a is not None and a.size != nw:
+                raise ValueError(f"per-wall arrays need {nw} entries")
+        _check(lib().mpm_scene_set_walls(self.handle, _ptr(k), _ptr(cc)), "mpm_scene_set_walls")
 
     def material_gradients(self):
         """(dL/dE_p, dL/dm_p) [N] of the last finished reverse pass (per-particle material only)."""
