@@ -4,7 +4,8 @@
 // A trial step is an ordinary simulation step: the tile kernels process every tile whole inside
 // one CTA, so neither the number of CTAs nor (for G2P, whose outputs are per particle) the CTA
 // size changes a single bit of the results.  The adjoint gather's group sums are formed per warp
-// and then per CTA, so its CTA size would change their rounding; it is not a candidate there.
+// and then per CTA, so its CTA size would change their rounding: it is fixed per dimension and
+// only its CTAs per SM are tuned.
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -128,7 +129,8 @@ mpm_status save_locked(const char* path) {
   const std::string tmp = std::string(path) + ".tmp";
   FILE* f = std::fopen(tmp.c_str(), "w");
   if (!f) return MPM_ERR_ARG;
-  std::fprintf(f, "gbmpm-tune 1 (dim log2_particles log2_tiles sms then ctas_per_sm threads of p2g g2p p2g_adj adj_gather)\n");
+  std::fprintf(f, "gbmpm-tune 1 (dim log2_particles log2_tiles sms, then ctas_per_sm threads of p2g g2p p2g_adj "
+                 "adj_gather; threads are chosen for g2p only)\n");
   for (auto& kv : g_cache) {
     std::fprintf(f, "%d %d %d %d", std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
                  std::get<3>(kv.first));
@@ -279,7 +281,7 @@ mpm_status mpm_scene_set_tuning(mpm_scene* s, int mode) {
 mpm_status mpm_scene_launch(const mpm_scene* s, int kernel, int* ctas_per_sm, int* threads, int* tuned) {
   if (!s || kernel < 0 || kernel >= TK_COUNT) return MPM_ERR_ARG;
   if (ctas_per_sm) *ctas_per_sm = s->b.launch[kernel].ctas_per_sm;
-  if (threads) *threads = kernel == TK_G2P ? s->b.launch[kernel].threads : 256;
+  if (threads) *threads = kernel == TK_G2P ? s->b.launch[kernel].threads : (kernel == TK_ADJ_GATHER && s->dim == 3 ? 128 : 256);
   if (tuned) *tuned = s->tune.tuned[kernel] ? 1 : 0;
   return MPM_OK;
 }
