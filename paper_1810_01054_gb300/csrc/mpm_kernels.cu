@@ -206,7 +206,8 @@ __device__ __forceinline__ void block_scan2(uint32_t& a, uint32_t& c, uint32_t& 
 constexpr int SCAN_THREADS = 1024;
 constexpr int SCAN_PER_THREAD = 2;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_PER_THREAD;
-// Small batches scan the tile histogram inside the scatter kernel (k_scatter<D, true>).
+// Small batches scan the tile histogram inside the scatter kernel (k_scatter<D, true>); the P2G
+// that follows every scatter clears the counters.
 __host__ __device__ __forceinline__ bool fused_scan(const BatchDev& b) { return b.total_tiles <= SCAN_TILE; }
 
 // Phase 1 of the tile scan: per-block totals of particle counts and of active tiles.
@@ -296,7 +297,7 @@ __global__ void k_scan_down(BatchDev b) {
 // Scatter of the particles into their tiles' ranges of `sorted`.  With FUSED (total_tiles <=
 // SCAN_TILE) the tile scan is done here instead of by the scan kernels: every CTA scans the whole
 // histogram in shared memory (it is small), CTA 0 publishes tile_start, tile_slot, the active list
-// and n_active, and the per-step counters are cleared by the P2G that follows.
+// and n_active; the P2G that follows clears the per-step counters.
 template <int D, bool FUSED>
 __global__ void __launch_bounds__(256) k_scatter(BatchDev b) {
   pdl_enter();
@@ -394,11 +395,13 @@ __global__ void __launch_bounds__(256, 2) k_p2g(BatchDev b) {
   __shared__ int cstart[CELLS + 1], cfill[CELLS];
   const int tid = threadIdx.x;
   const int n_active = *b.n_active;
-  if (fused_scan(b))  // the scatter's scan left the per-step counters for this kernel to clear
-    for (int i = blockIdx.x * blockDim.x + tid; i < b.total_tiles; i += gridDim.x * blockDim.x) {
-      b.tile_count[i] = 0u;
-      b.tile_fill[i] = 0u;
-    }
+  // the per-step counters are cleared here whichever scan ran (the fused one leaves them set, the
+  // separate one leaves the scatter's fill counts): every step then starts from zero, also when a
+  // batch's composition moves it between the two scans
+  for (int i = blockIdx.x * blockDim.x + tid; i < b.total_tiles; i += gridDim.x * blockDim.x) {
+    b.tile_count[i] = 0u;
+    b.tile_fill[i] = 0u;
+  }
 
   for (int slot = blockIdx.x; slot < n_active; slot += gridDim.x) {
     const int gt = b.active[slot];

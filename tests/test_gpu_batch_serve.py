@@ -174,3 +174,25 @@ def test_context_outlives_its_scenes_and_batches(M):
     sc.step(2)
     c.close()
     assert sc.handle is None and b.handle is None and c.handle is None
+
+
+def test_batch_crossing_the_fused_scan_threshold_equals_alone(M, ctx):
+    """Tile counts above and below 2048 take different scans (separate, or inside the scatter);
+    a batch whose composition moves between them as requests finish must still give every scene
+    exactly its alone result.  Two 128^2 scenes (1024 tiles each) plus a 48^2 one (144 tiles)
+    that finishes first: 2192 tiles, then 2048."""
+    reqs = [(S.blob(2, 128, 300, 61, v_scale=0.3, radius_cells=6.0, amp=2.0), 14, True),
+            (S.blob(2, 128, 250, 62, v_scale=0.3, radius_cells=5.0, amp=2.0), 30, True),
+            (S.blob(2, 48, 120, 63, v_scale=0.3, radius_cells=4.0, amp=2.0), 5, True)]
+    alone = [_alone(M, ctx, spec, T, g) for spec, T, g in reqs]
+    batch = M.Batch(ctx, 2)
+    scenes = [M.Scene(ctx, spec) for spec, _, _ in reqs]
+    slots = [batch.admit(sc, T, g) for sc, (_, T, g) in zip(scenes, reqs)]
+    for _ in range(1000):
+        batch.tick(2)
+        if all(batch.poll(s) for s in slots):
+            break
+    for sc, (st, grads) in zip(scenes, alone):
+        for a, b in zip(sc.get_state() + sc.gradients(), st + grads):
+            assert np.array_equal(a, b)
+    batch.close()
