@@ -191,7 +191,11 @@ mpm_status mpm_scene_info(const mpm_scene* scene, int* n_particles, int* n_group
  *                     reverse pass, seeded by loss = mean of final x_0); *slot = -1 if full
  *  mpm_batch_tick     advances every admitted scene by up to max_steps steps
  *  mpm_batch_poll     *done = 1 when the slot's work is finished (results stay in the scene)
- *  mpm_batch_release  frees a finished slot for the next admission */
+ *  mpm_batch_release  frees a finished slot for the next admission
+ * From admission until its slot is released (or the batch destroyed) a scene is driven by the
+ * batch: calls that would change it (step, rollout, backward, set_state, set_ctrl_params,
+ * set_material, set_walls, set_tuning, destroy) return MPM_ERR_STATE; reading its results is
+ * allowed once mpm_batch_poll reports the slot done. */
 mpm_status mpm_batch_create(mpm_ctx* ctx, int dim, size_t mem_budget, mpm_batch** out);
 mpm_status mpm_batch_destroy(mpm_batch* batch);
 mpm_status mpm_batch_admit(mpm_batch* batch, mpm_scene* scene, int n_steps, int want_grad, int* slot);

@@ -639,6 +639,7 @@ mpm_status mpm_sync(mpm_ctx* c) {
 
 mpm_status mpm_scene_destroy(mpm_scene* s) {
   if (!s) return MPM_ERR_ARG;
+  if (s->batch_refs > 0) return MPM_ERR_STATE;  // a batch still holds it
   cudaStreamSynchronize(s->ctx->stream);
   free_rollout(s);
   invalidate_graphs(s);
@@ -921,6 +922,7 @@ mpm_status mpm_scene_info(const mpm_scene* s, int* n_particles, int* n_groups, i
 
 mpm_status mpm_step(mpm_scene* s, int n_steps) {
   if (!s || n_steps < 0) return MPM_ERR_ARG;
+  if (s->batch_refs > 0) return MPM_ERR_STATE;
   s->have_rollout = false;
   CKS(run_phase(s, PH_STEP, n_steps));
   s->step += n_steps;
@@ -930,6 +932,7 @@ mpm_status mpm_step(mpm_scene* s, int n_steps) {
 
 mpm_status mpm_rollout(mpm_scene* s, int T, int k, size_t budget) {
   if (!s || T < 1 || k < 0) return MPM_ERR_ARG;
+  if (s->batch_refs > 0) return MPM_ERR_STATE;
   CKS(prepare_rollout(s, T, k, budget));
   CKS(run_phase(s, PH_ROLL, T));
   s->step += T;
@@ -941,6 +944,7 @@ mpm_status mpm_rollout(mpm_scene* s, int T, int k, size_t budget) {
 mpm_status mpm_backward(mpm_scene* s, const float* gxT, const float* gvT, const float* gCT, const float* gFT,
                         float* gx0, float* gv0, float* gC0, float* gF0, float* gctrl, int mem_space) {
   if (!s || (mem_space != 0 && mem_space != 1)) return MPM_ERR_ARG;
+  if (s->batch_refs > 0) return MPM_ERR_STATE;
   if (!s->have_rollout) return MPM_ERR_STATE;
   CKS(prepare_backward(s, gxT, gvT, gCT, gFT, mem_space));
   const int T = s->roll_T, k = s->roll_k, nseg = s->roll_nseg, n0 = s->roll_start;
@@ -993,6 +997,7 @@ mpm_status mpm_get_state(mpm_scene* s, int step, float* x, float* v, float* C, f
 mpm_status mpm_set_state(mpm_scene* s, const float* x, const float* v, const float* C, const float* F, int step,
                          int mem_space) {
   if (!s || (mem_space != 0 && mem_space != 1) || (s->N > 0 && !x)) return MPM_ERR_ARG;
+  if (s->batch_refs > 0) return MPM_ERR_STATE;
   s->have_rollout = false;
   cudaStream_t st = s->ctx->stream;
   const int dim = s->dim, N = s->N;
@@ -1015,6 +1020,7 @@ mpm_status mpm_set_state(mpm_scene* s, const float* x, const float* v, const flo
 
 mpm_status mpm_set_ctrl_params(mpm_scene* s, const float* params, int n, int mem_space) {
   if (!s || n != s->nparams || (n > 0 && !params)) return MPM_ERR_ARG;
+  if (s->batch_refs > 0) return MPM_ERR_STATE;
   if (n == 0) return MPM_OK;
   CK(cudaStreamSynchronize(s->ctx->stream));
   CK(cudaMemcpy(const_cast<float*>(s->ctrl.params), params, sizeof(float) * n,
@@ -1024,6 +1030,7 @@ mpm_status mpm_set_ctrl_params(mpm_scene* s, const float* params, int n, int mem
 
 mpm_status mpm_scene_set_material(mpm_scene* s, const float* E, const float* mass, int mem_space) {
   if (!s || (mem_space != 0 && mem_space != 1)) return MPM_ERR_ARG;
+  if (s->batch_refs > 0) return MPM_ERR_STATE;
   const int N = s->N;
   CK(cudaStreamSynchronize(s->ctx->stream));
   // host copies for validation: E_p > 0 and m_p > 0 finite, and the explicit-integration limit
@@ -1063,6 +1070,7 @@ mpm_status mpm_scene_set_material(mpm_scene* s, const float* E, const float* mas
 
 mpm_status mpm_scene_set_walls(mpm_scene* s, const int* kind, const float* c) {
   if (!s) return MPM_ERR_ARG;
+  if (s->batch_refs > 0) return MPM_ERR_STATE;
   const int nw = 2 * s->dim;
   for (int w = 0; w < nw; ++w) {
     if (kind && (kind[w] < MPM_BC_STICKY || kind[w] > MPM_BC_OPEN)) return MPM_ERR_ARG;

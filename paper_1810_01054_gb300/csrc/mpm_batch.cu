@@ -322,6 +322,8 @@ mpm_status mpm_batch_create(mpm_ctx* ctx, int dim, size_t mem_budget, mpm_batch*
 mpm_status mpm_batch_destroy(mpm_batch* B) {
   if (!B) return MPM_ERR_ARG;
   cudaStreamSynchronize(B->ctx->stream);
+  for (Slot& sl : B->slots)  // the scenes of unreleased slots are the caller's again
+    if (sl.state != S_FREE && sl.s) sl.s->batch_refs -= 1;
   free_sub(B->fwd);
   free_sub(B->rev);
   dfree(B->partial);
@@ -361,6 +363,7 @@ mpm_status mpm_batch_admit(mpm_batch* B, mpm_scene* s, int n_steps, int want_gra
   sl.mem = need;
   B->used += need;
   B->dirty = true;
+  s->batch_refs += 1;
   *slot = idx;
   return MPM_OK;
 }
@@ -398,6 +401,7 @@ mpm_status mpm_batch_release(mpm_batch* B, int slot) {
   Slot& sl = B->slots[slot];
   if (sl.state != S_DONE) return MPM_ERR_STATE;
   B->used -= sl.mem;
+  sl.s->batch_refs -= 1;
   sl = Slot();
   B->dirty = true;
   return MPM_OK;

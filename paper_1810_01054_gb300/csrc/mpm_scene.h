@@ -99,6 +99,7 @@ struct mpm_scene {
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
   TuneState tune;
+  int batch_refs = 0;  // batch slots holding the scene (admitted, not yet released)
 };
 
 

@@ -272,6 +272,7 @@ extern "C" {
 
 mpm_status mpm_scene_set_tuning(mpm_scene* s, int mode) {
   if (!s || mode < MPM_TUNE_OFF || mode > MPM_TUNE_FORCE) return MPM_ERR_ARG;
+  if (s->batch_refs > 0) return MPM_ERR_STATE;
   CK(cudaStreamSynchronize(s->ctx->stream));
   s->tune.mode = mode;
   invalidate_graphs(s);  // graphs hold the launch shapes they were captured with

@@ -483,8 +483,9 @@ class Scene:
         return gx0, gv0, gC0, gF0, gp[: self.n_params]
 
     def close(self):
+        """Frees the scene (MPMError while a batch still holds it: release or close the batch)."""
         if getattr(self, "handle", None):
-            lib().mpm_scene_destroy(self.handle)
+            _check(lib().mpm_scene_destroy(self.handle), "mpm_scene_destroy")
             self.handle = None
 
     def __del__(self):

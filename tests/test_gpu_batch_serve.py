@@ -196,3 +196,25 @@ def test_batch_crossing_the_fused_scan_threshold_equals_alone(M, ctx):
         for a, b in zip(sc.get_state() + sc.gradients(), st + grads):
             assert np.array_equal(a, b)
     batch.close()
+
+
+def test_scene_is_driven_by_its_batch_until_released(M, ctx):
+    spec = S.blob(2, 32, 200, 71, radius_cells=4.0)
+    sc = M.Scene(ctx, spec)
+    batch = M.Batch(ctx, 2)
+    slot = batch.admit(sc, 6, True)
+    for call in (lambda: sc.step(1), lambda: sc.rollout(3), lambda: sc.set_state(*[np.asarray(a) for a in
+                 (spec.x0, spec.v0, spec.C0, spec.F0)]), lambda: sc.set_walls(kind=[0, 0, 0, 0]),
+                 lambda: sc.set_tuning(M.TUNE_OFF), sc.close):
+        with pytest.raises(M.MPMError):
+            call()
+    while not batch.poll(slot):
+        batch.tick(4)
+    g = sc.gradients()  # results can be read once the slot is done
+    assert np.all(np.isfinite(g[1]))
+    with pytest.raises(M.MPMError):
+        sc.step(1)  # still held until released
+    batch.release(slot)
+    sc.step(1)
+    sc.close()
+    batch.close()
