@@ -302,7 +302,7 @@ template <int D, bool FUSED>
 __global__ void __launch_bounds__(256) k_scatter(BatchDev b) {
   pdl_enter();
   constexpr int PER = FUSED ? SCAN_TILE / 256 : 1;
-  __shared__ uint32_t sstart[FUSED ? SCAN_TILE : 1];
+  __shared__ uint32_t sstart[FUSED ? SCAN_TILE + 1 : 1];
   if constexpr (FUSED) {
     const int nt = b.total_tiles, t0 = threadIdx.x * PER;
     uint32_t cnt[PER], s = 0, c = 0;
@@ -333,9 +333,12 @@ __global__ void __launch_bounds__(256) k_scatter(BatchDev b) {
         c += cnt[i] > 0;
       }
     }
-    if (pub && threadIdx.x == 0) {
-      b.tile_start[nt] = ts;
-      *b.n_active = int(tc);
+    if (threadIdx.x == 0) {
+      sstart[nt] = ts;
+      if (pub) {
+        b.tile_start[nt] = ts;
+        *b.n_active = int(tc);
+      }
     }
     __syncthreads();
   }
@@ -348,6 +351,11 @@ __global__ void __launch_bounds__(256) k_scatter(BatchDev b) {
   const uint32_t rank = warp_aggregated_inc(b.tile_fill, t);
   if (t < 0) return;
   const uint32_t start = FUSED ? sstart[t] : b.tile_start[t];
+  const uint32_t end = FUSED ? sstart[t + 1] : b.tile_start[t + 1];
+  if (start + rank >= end) {  // a key the histogram did not count: record it, write nothing
+    set_status(sp.status, ST_BINNING);
+    return;
+  }
   b.sorted[start + rank] = ((k & 63u) << 26) | uint32_t(p);  // cell in tile, particle id
 }
 
@@ -408,8 +416,12 @@ __global__ void __launch_bounds__(256, 2) k_p2g(BatchDev b) {
     const ScenePar& sp = b.scenes[b.tile_scene[gt]];
     const uint32_t st = b.tile_start[gt];
     const int cnt = int(b.tile_start[gt + 1] - st);
-    if (cnt > K::CAP) {
+    if (cnt > K::CAP) {  // the step fails (status); the tile adds nothing to the grid
       if (tid == 0) set_status(sp.status, ST_DENSITY);
+      for (int i = tid; i < NB; i += blockDim.x) {
+        b.partial[size_t(slot) * NB + i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if constexpr (ADJ) b.partial_b[size_t(slot) * NB + i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
       continue;  // uniform across the CTA
     }
     int t[D];
@@ -987,10 +999,18 @@ __global__ void __launch_bounds__(T, 768 / T) k_g2p(BatchDev b) {
     unlin<D>(gt - sp.tile_base, sp.nt, t);
     const uint32_t st = b.tile_start[gt];
     const int cnt = int(b.tile_start[gt + 1] - st);
+    // a tile over P2G's capacity was skipped there (the step reports it): its list still holds
+    // the scatter's cell-tagged entries, so it is skipped here too
+    if (cnt > Cfg<D>::SORT_CAP) {  // uniform across the CTA
+      // its particles are not advanced: their keys go invalid so the next step's histogram and
+      // scatter (which count keys) stay consistent; the step has already reported the error
+      for (int e = tid; e < cnt; e += blockDim.x) sp.key[b.sorted[st + e] & 0x3ffffffu] = KEY_INVALID;
+      continue;
+    }
     const int staged = cnt < K::STAGE ? cnt : K::STAGE;
     // request the x, F planes of the tile's particles; they arrive while the node block is built
     for (int e = tid; e < staged; e += blockDim.x) {
-      const int id = int(b.sorted[st + e]);
+      const int id = int(b.sorted[st + e] & 0x3ffffffu);
 #pragma unroll
       for (int j = 0; j < K::NP; ++j) cp_async16(&stage[j][e], sp.planes + size_t(j) * sp.npad + id);
     }
@@ -999,7 +1019,7 @@ __global__ void __launch_bounds__(T, 768 / T) k_g2p(BatchDev b) {
     cp_async_wait_all();
     __syncthreads();
     for (int e = tid; e < cnt; e += blockDim.x) {
-      const int id = int(b.sorted[st + e]);
+      const int id = int(b.sorted[st + e] & 0x3ffffffu);
       float r[Cfg<D>::S];
       if (e < K::STAGE) {
 #pragma unroll
@@ -1027,6 +1047,7 @@ __global__ void __launch_bounds__(T, 768 / T) k_g2p(BatchDev b) {
       }
       if (!inside) {  // bin key disagrees with the position: never index outside the block
         set_status(sp.status, ST_BINNING);
+        sp.key[id] = KEY_INVALID;  // not advanced, not counted: the next scatter stays in bounds
         continue;
       }
       g2p_core<D>(q, f, w, sp.dt, sp.inv_dx, [&](int kx, int ky, int kz) {
@@ -1284,10 +1305,14 @@ __global__ void __launch_bounds__(kAdjThreads<D>, 512 / kAdjThreads<D>) k_adj_ga
     unlin<D>(gt - sp.tile_base, sp.nt, t);
     const uint32_t st = b.tile_start[gt];
     const int cnt = int(b.tile_start[gt + 1] - st);
+    if (cnt > Cfg<D>::SORT_CAP) {  // skipped by the adjoint scatter (the step reports it)
+      if (tid < MAX_GROUPS) b.gpartial[size_t(slot) * MAX_GROUPS + tid] = 0.0f;
+      continue;  // uniform across the CTA
+    }
     // the first particle's state is requested before the node block is built, so the two overlap
     // (requesting its adjoint too, or staging the second particle in shared memory, measured slower)
     float r[Cfg<D>::S];
-    if (tid < cnt) load_planes<D, Cfg<D>::PLANES>(sp.planes, sp.npad, int(b.sorted[st + tid]), r);
+    if (tid < cnt) load_planes<D, Cfg<D>::PLANES>(sp.planes, sp.npad, int(b.sorted[st + tid] & 0x3ffffffu), r);
     build_node_block<D, true>(b, sp, t, sv, sb);
     __syncthreads();
     float lo = 0.0f, hi = 0.0f;  // per-warp group sums of (K), lane-owned
@@ -1296,7 +1321,7 @@ __global__ void __launch_bounds__(kAdjThreads<D>, 512 / kAdjThreads<D>) k_adj_ga
       int g = -1;
       float contrib = 0.0f;
       if (e < cnt) {
-        const int id = int(b.sorted[st + e]);
+        const int id = int(b.sorted[st + e] & 0x3ffffffu);
         if (e0 > 0) load_planes<D, Cfg<D>::PLANES>(sp.planes, sp.npad, id, r);
         Part<D> q, g1, g0;
         unpack<D>(r, q);
