@@ -190,7 +190,12 @@ mpm_status mpm_scene_info(const mpm_scene* scene, int* n_particles, int* n_group
  *  mpm_batch_admit    adds a scene that will run n_steps more steps (and, with want_grad, its
  *                     reverse pass, seeded by loss = mean of final x_0); *slot = -1 if full
  *  mpm_batch_tick     advances every admitted scene by up to max_steps steps
- *  mpm_batch_poll     *done = 1 when the slot's work is finished (results stay in the scene)
+ *  mpm_batch_poll     *done = 1 when the slot's work is finished (results stay in the scene);
+ *                     a request that stopped on a device error (a particle left the grid, a
+ *                     tile over capacity) is finished too: *done = 1 and the return value is
+ *                     that error, which the scene's own calls also report.  Only that slot
+ *                     stops; the other scenes of the batch go on unaffected.  MPM_ERR_ARG for
+ *                     a free or out-of-range slot (then *done is left unchanged)
  *  mpm_batch_release  frees a finished slot for the next admission
  * From admission until its slot is released (or the batch destroyed) a scene is driven by the
  * batch: calls that would change it (step, rollout, backward, set_state, set_ctrl_params,

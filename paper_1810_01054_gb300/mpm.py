@@ -517,9 +517,19 @@ class Batch:
         _check(lib().mpm_batch_tick(self.handle, int(max_steps)), "mpm_batch_tick")
 
     def poll(self, slot: int) -> bool:
+        """True once the slot's request is finished, successfully or not (see status)."""
+        return self._poll(slot)[0]
+
+    def status(self, slot: int) -> int:
+        """MPM_OK, or the error a finished request stopped with (e.g. a particle left the grid)."""
+        return self._poll(slot)[1]
+
+    def _poll(self, slot: int):
         done = C.c_int(0)
-        _check(lib().mpm_batch_poll(self.handle, int(slot), C.byref(done)), "mpm_batch_poll")
-        return bool(done.value)
+        st = lib().mpm_batch_poll(self.handle, int(slot), C.byref(done))
+        if st != MPM_OK and not done.value:
+            raise MPMError(st, "mpm_batch_poll")
+        return bool(done.value), int(st)
 
     def release(self, slot: int):
         _check(lib().mpm_batch_release(self.handle, int(slot)), "mpm_batch_release")

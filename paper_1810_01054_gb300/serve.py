@@ -10,7 +10,9 @@ host from arrival to the moment the result (final state, and gradients when aske
     server = Server(device=0)
     rid = server.submit(spec, want_grad=True)          # or submit(..., arrival=t)
     server.run()                                       # until every request is done
-    server.results[rid]  -> dict(x, v, C, F, grads, latency_s)
+    server.results[rid]  -> dict(status, x, v, C, F, grads, latency_s); a request that failed on
+                            the device (status < 0, e.g. a particle left the grid) carries
+                            status and error instead of a state, and the others are unaffected
     server.latency_percentiles()                       -> (p50, p99) in seconds
 """
 from __future__ import annotations
@@ -100,19 +102,24 @@ class Server:
             batch = self.batches[req.dim]
             if not batch.poll(req.slot):
                 continue
-            x, v, Cm, F = req.scene.get_state()
-            res = {"x": x, "v": v, "C": Cm, "F": F}
-            if req.want_grad:
-                res["grads"] = req.scene.gradients()
+            status = batch.status(req.slot)
+            if status == mpm.MPM_OK:
+                x, v, Cm, F = req.scene.get_state()
+                res = {"status": status, "x": x, "v": v, "C": Cm, "F": F}
+                if req.want_grad:
+                    res["grads"] = req.scene.gradients()
+            else:  # the request failed on the device (e.g. a particle left the grid); others go on
+                res = {"status": status, "error": mpm.STATUS.get(status, "unknown")}
             req.done = self.now()
             res["latency_s"] = req.done - req.arrival
             res["queued_s"] = req.admitted - req.arrival
-            self.particle_steps += req.scene.N * req.n_steps
+            if status == mpm.MPM_OK:
+                self.particle_steps += req.scene.N * req.n_steps
             batch.release(req.slot)
             req.scene.close()
             req.scene = None
             del self.active[key]
-            self.results[req.rid] = res if self.keep_results else {"latency_s": res["latency_s"]}
+            self.results[req.rid] = res if self.keep_results else {"status": status, "latency_s": res["latency_s"]}
 
     def step(self):
         """One scheduling round: admit arrived requests, advance every batch, collect results."""

@@ -218,3 +218,40 @@ def test_scene_is_driven_by_its_batch_until_released(M, ctx):
     sc.step(1)
     sc.close()
     batch.close()
+
+
+def test_a_failing_scene_does_not_disturb_its_batch(M, ctx):
+    """One scene of a batch throws a particle out of the grid: its status reports it, and the
+    other scenes still get their alone results bit for bit."""
+    good = [(S.blob(2, 32, 300, 91, v_scale=0.3, radius_cells=5.0, amp=2.0), 20),
+            (S.blob(2, 48, 400, 92, v_scale=0.3, radius_cells=6.0, amp=2.0), 12)]
+    bad = S.blob(2, 32, 200, 93, radius_cells=4.0).copy(bc_width=0)
+    bad.x0[0] = [2.6 / 32, 0.5]
+    bad.v0[0] = [-800.0, 0.0]  # leaves the grid in the first step
+    alone = [_alone(M, ctx, spec, T, True) for spec, T in good]
+    batch = M.Batch(ctx, 2)
+    scenes = [M.Scene(ctx, spec) for spec, _ in good] + [M.Scene(ctx, bad)]
+    slots = [batch.admit(sc, T, True) for sc, T in zip(scenes, [20, 12, 15])]
+    for _ in range(1000):
+        batch.tick(4)
+        if all(batch.poll(s) for s in slots):
+            break
+    assert [batch.status(s) for s in slots] == [0, 0, -3]
+    for sc, (st, grads) in zip(scenes[:2], alone):
+        for a, b in zip(sc.get_state() + sc.gradients(), st + grads):
+            assert np.array_equal(a, b)
+    with pytest.raises(M.MPMError) as e:
+        scenes[2].get_state()
+    assert e.value.status == -3
+    batch.close()
+    # the serving loop reports the failed request and serves the others
+    from paper_1810_01054_gb300.serve import Server
+    srv = Server(device=0, mem_fraction=0.2, tick_steps=4)
+    ids = [srv.submit(spec, True, n_steps=T) for spec, T in good] + [srv.submit(bad, True, n_steps=15)]
+    srv.run()
+    assert srv.results[ids[2]]["status"] == -3
+    for rid, (st, grads) in zip(ids[:2], alone):
+        r = srv.results[rid]
+        for a, b in zip((r["x"], r["v"], r["C"], r["F"]) + tuple(r["grads"]), st + grads):
+            assert np.array_equal(a, b)
+    srv.close()
