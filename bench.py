@@ -61,6 +61,10 @@ def parse():
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-material", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--ncu-fp64", action="store_true",
+                    help="short run for profilers: the FP64 form on a 200k-particle 3D cluster (64^3 grid), "
+                         "2 steps and their reverse pass")
     ap.add_argument("--ncu", type=int, default=0, metavar="SIM_STEPS",
                     help="profiling mode: one short rollout of SIM_STEPS steps + reverse pass, no timing")
     return ap.parse_args()
@@ -415,6 +419,121 @@ def measure_serving(dev, stream, n_requests=32, seed=4):
                    "60% with gradient (loss = mean final x_0)"}
 
 
+# FP64 roofline: GB300 SMs issue 2 FP64 thread-ops per clock (the nominal 1.25 TFLOP/s FP64 rate:
+# 152 SMs x 2 DFMA x 2 flops x 2.07 GHz); no measured FP64 peak exists for this machine.
+F64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP64 arithmetic of the per-particle adjoint kernel (S4 (F)-(K), (J)), DADD + DMUL + 2 DFMA thread
+# instructions per particle from the ncu counters of the 3D capture (profiles/k64_fp64_box_cluster_3d.md)
+F64_ADJ_FLOPS_3D = 3700.0
+
+
+def table_of(spec, T):
+    """The sinusoid actuation a_g(t_n) = A_g sin(2 pi f t_n) of a CTRL_SIN workload as a per-step
+    table (the FP64 form's actuation input)."""
+    t = np.arange(T) * spec.dt
+    return np.asarray(spec.ctrl_params)[None, :] * np.sin(2 * np.pi * spec.ctrl_freq * t)[:, None]
+
+
+def measure_fp64(args, dev, stream):
+    """Double-precision plain form (the float64 accuracy case of Section VI): throughput of a
+    1000-step forward+reverse rollout of the colliding-discs scene with the oracle timed beside it,
+    the accuracy study (GPU adjoint vs GPU central differences), and the FP64-pipe roofline of the
+    per-particle adjoint kernel on the 1M-particle 3D cluster (8 steps, sinusoid as a table)."""
+    import torch
+    from oracle import oracle as O
+    from paper_1810_01054_gb300 import mpm
+    from paper_1810_01054_gb300 import scenes as S
+
+    ctx = mpm.Context(dev.index, stream=stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    spec = S.billiards_2d()
+    T, N = spec.n_steps, spec.n_particles
+    a = S.billiards_ball_a(spec)
+    w = np.zeros_like(spec.x0)
+    w[~a, 0] = 1.0 / (~a).sum()  # loss: x centroid of ball B at step T
+    sc = mpm.Scene64(ctx, spec)
+    for _ in range(args.warmup):
+        sc.rollout(T)
+        sc.backward(w)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    torch.cuda.synchronize(dev)
+    for e in ev:
+        flush.zero_()
+        e[0].record(stream)
+        sc.rollout(T)
+        e[1].record(stream)
+        sc.backward(w)
+        e[2].record(stream)
+    torch.cuda.synchronize(dev)
+    fwd = [e[0].elapsed_time(e[1]) for e in ev]
+    tot = [e[0].elapsed_time(e[2]) for e in ev]
+    # accuracy: dL/d(vx of ball A) by the adjoint and by FP64 central differences (h = 1e-6)
+    acc = {}
+    for TT in (1, 10, 100, 1000):
+        sc.set_state(spec.x0, spec.v0, spec.C0, spec.F0)
+        sc.rollout(TT)
+        g = float(sc.backward(w)[1][a, 0].sum())
+        L = []
+        for sgn in (1, -1):
+            v0 = spec.v0.copy()
+            v0[a, 0] += sgn * 1e-6
+            sc.set_state(spec.x0, v0, spec.C0, spec.F0)
+            sc.rollout(TT)
+            L.append(float(np.sum(w * sc.get_state()[0])))
+        fd = (L[0] - L[1]) / 2e-6
+        acc[str(TT)] = {"adjoint": g, "fd": fd, "rel_err": abs(g - fd) / abs(fd) if g != 0.0 else None}
+    sc.close()
+    # the oracle on the same scene (bounded sample: 100 steps forward + reverse, one thread)
+    osc = O.Scene(spec)
+    t0 = time.time()
+    tr = osc.rollout(100)
+    osc.backward(tr, (w, None, None, None))
+    odt = time.time() - t0
+    # FP64-pipe roofline of the per-particle adjoint on the 1M-particle 3D cluster
+    lspec = S.box_cluster_3d()
+    LT, LN = 8, lspec.n_particles
+    lsc = mpm.Scene64(ctx, lspec, act=table_of(lspec, LT))
+    lw = np.zeros_like(lspec.x0)
+    lw[:, 0] = 1.0 / LN
+    lsc.rollout(LT)
+    lsc.backward(lw)
+    kinds = (("adjoint", mpm.K_F64_ADJ), ("p2g_adj", mpm.K_F64_P2G_ADJ), ("p2g", mpm.K_F64_P2G),
+             ("g2p", mpm.K_F64_G2P), ("grid", mpm.K_F64_GRID))
+    ctx.profile_start([k for _, k in kinds], max_launches=8 * LT + 16)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.zero_()
+    e0.record(stream)
+    lsc.rollout(LT)
+    lsc.backward(lw)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    lms = e0.elapsed_time(e1)
+    per = {nm: ctx.profile_read(k) for nm, k in kinds}
+    lsc.close()
+    ctx.close()
+    n_adj, t_adj = per["adjoint"]
+    adj_s = t_adj / max(n_adj, 1) / 1e3
+    achieved = F64_ADJ_FLOPS_3D * LN / adj_s / 1e12
+    return {
+        "workload": spec.name, "particles": N, "sim_steps": T, "dtype": "f64",
+        "pass": "forward+reverse rollout, every state kept; device events around the rollout and reverse calls",
+        "value": N * T / (np.median(tot) / 1e3), "value_fwd": N * T / (np.median(fwd) / 1e3), "unit": UNIT,
+        "ms_per_rollout_and_reverse": float(np.median(tot)),
+        "accuracy": {"loss": "x centroid of ball B at step T", "wrt": "x velocity of every ball-A particle",
+                     "fd": "central, h = 1e-6, GPU FP64", "by_steps": acc,
+                     "paper_rel_err": {"100": 2.39e-8, "1000": 2.83e-8}},
+        "oracle": {"value": N * 100 / odt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"FP64 oracle forward+reverse of 100 steps of {spec.name}, single thread, {odt:.2f} s"},
+        "large": {"workload": lspec.name, "particles": LN, "sim_steps": LT, "value": LN * LT / (lms / 1e3),
+                  "unit": UNIT, "ms": lms,
+                  "kernel_avg_us": {nm: 1e3 * t / max(n, 1) for nm, (n, t) in per.items()},
+                  "roofline": {"bound": "alu", "kernel": "k64_adjoint<3>", "achieved": achieved,
+                               "peak": F64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / F64_PEAK_TFLOPS,
+                               "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz",
+                               "flops_per_particle": F64_ADJ_FLOPS_3D}},
+    }
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_1810_01054_gb300 import mpm
@@ -426,6 +545,18 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_stream(stream)
     ctx = mpm.Context(local_rank, stream=stream)
     spec = workload(args.workload, rank)
+
+    if args.ncu_fp64:
+        from paper_1810_01054_gb300 import scenes as S
+        fspec = S.box_cluster_3d(n_particles=200_000, n=64)
+        sc = mpm.Scene64(ctx, fspec, act=table_of(fspec, 2))
+        sc.rollout(2)
+        seed = np.zeros_like(fspec.x0)
+        seed[:, 0] = 1.0 / fspec.n_particles
+        sc.backward(seed)
+        sc.close()
+        print(json.dumps({"ncu_run": "fp64 " + fspec.name, "particles": fspec.n_particles, "sim_steps": 2}), flush=True)
+        return
 
     if args.ncu:
         # short run for profilers: one rollout of --ncu steps (checkpoint interval kept) + reverse pass
@@ -458,6 +589,9 @@ def run_ours(args, rank, world, local_rank):
     serving = None
     if rank == 0 and not args.no_serve:
         serving = measure_serving(dev, stream)
+    fp64 = None
+    if rank == 0 and not args.no_fp64:
+        fp64 = measure_fp64(args, dev, stream)
     if rank != 0:
         return
     cpu = None if args.no_cpu_baseline else cpu_baseline(spec)
@@ -475,6 +609,7 @@ def run_ours(args, rank, world, local_rank):
         "roofline": r["roofline"], "kernel_share_of_profiled_step": r["share"],
         "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": r["gpu_launches"], "clocks": r["clocks"],
         "plain_form": r["plain"], "large_scene": large, "material": material, "serving": serving,
+        "fp64": fp64,
     }
     print(json.dumps(line), flush=True)
 

@@ -208,6 +208,60 @@ mpm_status mpm_batch_tick(mpm_batch* batch, int max_steps);
 mpm_status mpm_batch_poll(mpm_batch* batch, int slot, int* done);
 mpm_status mpm_batch_release(mpm_batch* batch, int slot);
 
+/* Double-precision plain form (an extension for the accuracy study of Section VI, whose case B
+ * runs colliding elastic bodies in float64 and checks the adjoint against central finite
+ * differences).  The same step (Eqs. 3-10) and reverse pass (Supplement S2-S5, (A)-(L)) in FP64,
+ * one thread per particle with atomic scatter: run-to-run results agree to rounding, not bit for
+ * bit (the tile form above is the deterministic one).  Scope: uniform material, per-wall boundary,
+ * and actuation given per step as a table (the MPM_CTRL_TABLE form: a_g(t_n) = U[n][g] for
+ * n < L, 0 after); other controller families and per-particle material stay FP32-only.
+ * A rollout always starts from the scene's initial state at step 0 and keeps every state on the
+ * device ((T + 1) (2 dim + 2 dim^2) N doubles).  All pointers are host pointers; arrays are
+ * row-major and particle-major as in the FP32 API ([N][dim], [N][dim][dim]). */
+typedef struct mpm_scene64 mpm_scene64;
+typedef struct {
+  int dim;               /* 2 or 3 */
+  int n_grid[3];         /* nodes per axis, each >= 5 */
+  double dx, dt;         /* dt <= dx sqrt(rho / E) (Section VI) */
+  double gravity[3];
+  double E, nu;          /* Young's modulus > 0, Poisson ratio in (-1, 0.5) */
+  double p_mass, p_vol;  /* m_p and V_p^0 of every particle (> 0) */
+  int bc_width;          /* band depth of every wall */
+  int wall_kind[6];      /* wall w = 2 axis + side: MPM_BC_STICKY, MPM_BC_SLIP or MPM_BC_OPEN */
+  double wall_c[6];      /* Coulomb coefficient of each slip wall (>= 0, Supplement S5) */
+  int n_particles;       /* 0 <= N < 2^26 */
+  const double* x0;      /* [N][dim] */
+  const double* v0;      /* [N][dim], NULL = 0 */
+  const double* C0;      /* [N][dim][dim], NULL = 0 */
+  const double* F0;      /* [N][dim][dim], NULL = identity */
+  const int32_t* group;  /* [N] actuation group in [-1, G), NULL = all -1 */
+  int n_groups;          /* 0 <= G <= 64 */
+  const double* act_dir; /* [G][dim]: sigma_a = a_g Diag(dir_g) */
+  int n_act_steps;       /* L >= 0 */
+  const double* act;     /* [L][G] actuation table U (may be NULL when L G = 0) */
+} mpm_scene64_desc;
+
+/* Creates the scene (copies every input).  MPM_ERR_ARG for an invalid or non-finite input. */
+mpm_status mpm64_create(mpm_ctx* ctx, const mpm_scene64_desc* desc, mpm_scene64** out);
+mpm_status mpm64_destroy(mpm_scene64* scene);
+/* Replaces the initial state (NULL v, C = 0, NULL F = I); drops the stored rollout. */
+mpm_status mpm64_set_state(mpm_scene64* scene, const double* x, const double* v, const double* C, const double* F);
+/* Replaces the actuation table U [L][G]; drops the stored rollout. */
+mpm_status mpm64_set_actuation(mpm_scene64* scene, const double* U, int L);
+/* T steps from the initial state, every state kept (asynchronous; MPM_ERR_OOM if they do not
+ * fit).  Device errors (a stencil leaving the grid, det F <= 0) are reported by the next
+ * mpm64_get_state or mpm64_backward. */
+mpm_status mpm64_rollout(mpm_scene64* scene, int n_steps);
+/* State at step 0..T of the last rollout (-1 = T); NULL skips an output.  Synchronises. */
+mpm_status mpm64_get_state(mpm_scene64* scene, int step, double* x, double* v, double* C, double* F);
+/* Reverse pass of the last rollout seeded by dL/d(x_T, v_T, C_T, F_T) (NULL = 0): dL/d of the
+ * initial x, v, C, F and dL/dU [L][G] (NULL skips one).  Synchronises. */
+mpm_status mpm64_backward(mpm_scene64* scene, const double* gx_T, const double* gv_T, const double* gC_T,
+                          const double* gF_T, double* gx0, double* gv0, double* gC0, double* gF0, double* g_act);
+/* Sizes: particles, groups, actuation steps L, steps of the stored rollout (-1: none). */
+mpm_status mpm64_info(const mpm_scene64* scene, int* n_particles, int* n_groups, int* n_act_steps,
+                      int* rollout_steps);
+
 /* Instrumentation.  Kernel kinds for timing: */
 enum {
   MPM_K_SORT = 0,       /* bin keys, tile histogram, scan, scatter */
@@ -219,7 +273,12 @@ enum {
   MPM_K_ADJ_GATHER = 6, /* adjoint gather (F)-(K), (J) */
   MPM_K_CTRL = 7,       /* controller forward/backward and group reductions */
   MPM_K_PLAIN = 8,      /* the plain (atomic) form's step or reverse step */
-  MPM_K_COUNT = 9
+  MPM_K_F64_P2G = 9,    /* FP64 form: P2G scatter (forward) */
+  MPM_K_F64_GRID = 10,  /* FP64 form: grid update, forward or reverse */
+  MPM_K_F64_G2P = 11,   /* FP64 form: G2P */
+  MPM_K_F64_P2G_ADJ = 12, /* FP64 form: P2G recompute + adjoint scatter (A)-(C) */
+  MPM_K_F64_ADJ = 13,   /* FP64 form: per-particle adjoint (F)-(K), (J) */
+  MPM_K_COUNT = 14
 };
 /* Starts timing every launch of the kinds in `mask` (bit k = kind k) with CUDA events on the
  * context stream, for at most max_launches launches; restarts the tally. */

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgbmpm.so")
-SOURCES = ["mpm_kernels.cu", "mpm_ctrl.cu", "mpm_api.cu", "mpm_batch.cu", "mpm_noalloc.cu", "mpm_tune.cu"]
+SOURCES = ["mpm_kernels.cu", "mpm_ctrl.cu", "mpm_api.cu", "mpm_batch.cu", "mpm_noalloc.cu", "mpm_tune.cu", "mpm_f64.cu"]
 HEADERS = ["mpm_device.cuh", "mpm_internal.h", "mpm_scene.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

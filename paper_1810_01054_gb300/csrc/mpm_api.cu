@@ -188,23 +188,6 @@ ScenePar rec_rev(const mpm_scene* s, float4* st, const float4* ain, float4* aout
   return p;
 }
 
-// Event pair around one launch of kind k (no-op unless k is being timed).
-struct ProfScope {
-  mpm_ctx* c;
-  cudaStream_t st;
-  int slot = -1;
-  ProfScope(mpm_ctx* ctx, cudaStream_t stream, int kind) : c(ctx), st(stream) {
-    if (!(c->prof_mask & (1u << kind))) return;
-    if (2 * (c->prof_used + 1) > int(c->prof_ev.size())) return;
-    slot = c->prof_used++;
-    c->prof_kind[slot] = kind;
-    cudaEventRecord(c->prof_ev[2 * slot], st);
-  }
-  ~ProfScope() {
-    if (slot >= 0) cudaEventRecord(c->prof_ev[2 * slot + 1], st);
-  }
-};
-
 // ---------------------------------------------------------------------------- step sequences
 // Forward step of phase ph (PH_STEP, PH_ROLL, PH_RCM) on stream st.
 mpm_status enqueue_forward(mpm_scene* s, int ph, cudaStream_t st) {

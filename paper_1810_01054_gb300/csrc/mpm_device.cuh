@@ -1,9 +1,11 @@
-// Device-side math of the differentiable MLS-MPM step (ChainQueen, arXiv 1810.01054), FP32.
+// Device-side math of the differentiable MLS-MPM step (ChainQueen, arXiv 1810.01054).
 //
 // Per-particle pieces used by every kernel of the library: the quadratic B-spline stencil and
 // its gradient, the neo-Hookean stress and its Hessian product (Section III and Supplement S4
 // (H)), the MLS momentum matrix G of Eq. 4, the boundary projection of Supplement S5 (L) and its
-// adjoint.  Layout helpers for the SoA float4 state planes live here too.
+// adjoint.  These are templates on the scalar type R: the tile and plain kernels run them in FP32,
+// the double-precision plain form (mpm_f64.cu) in FP64.  Layout helpers for the SoA float4 state
+// planes live here too.
 #pragma once
 
 #include <cstdint>
@@ -59,12 +61,12 @@ __device__ __forceinline__ void set_status(int* st, int code) {
 // One particle's state in the order x, F, v, C (row-major matrices).  The four-float planes of
 // the state arrays are consecutive chunks of this record, so the first XF_PLANES planes hold
 // exactly the inputs of G2P (x and F).
-template <int D>
+template <int D, class R = float>
 struct Part {
-  float x[D];
-  float F[D][D];
-  float v[D];
-  float C[D][D];
+  R x[D];
+  R F[D][D];
+  R v[D];
+  R C[D][D];
 };
 
 template <int D>
@@ -145,9 +147,22 @@ __device__ __forceinline__ void pdl_enter() {
   pdl_trigger();
 }
 
+// --------------------------------------------------------------------------- scalar functions
+// One name per function for both precisions (the float overloads are the FP32 library calls).
+__device__ __forceinline__ float s_log(float a) { return logf(a); }
+__device__ __forceinline__ double s_log(double a) { return log(a); }
+__device__ __forceinline__ float s_sqrt(float a) { return sqrtf(a); }
+__device__ __forceinline__ double s_sqrt(double a) { return sqrt(a); }
+__device__ __forceinline__ float s_floor(float a) { return floorf(a); }
+__device__ __forceinline__ double s_floor(double a) { return floor(a); }
+__device__ __forceinline__ float s_min(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double s_min(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float s_max(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double s_max(double a, double b) { return fmax(a, b); }
+
 // --------------------------------------------------------------------------- small matrices
-template <int D>
-__device__ __forceinline__ float det(const float (&F)[D][D]) {
+template <int D, class R>
+__device__ __forceinline__ R det(const R (&F)[D][D]) {
   if constexpr (D == 2) {
     return F[0][0] * F[1][1] - F[0][1] * F[1][0];
   } else {
@@ -157,9 +172,9 @@ __device__ __forceinline__ float det(const float (&F)[D][D]) {
 }
 
 // F^{-T} from the cofactor matrix: (F^{-T})_{ij} = cof(F)_{ij} / det F.
-template <int D>
-__device__ __forceinline__ void inv_transpose(const float (&F)[D][D], float J, float (&A)[D][D]) {
-  float rJ = 1.0f / J;
+template <int D, class R>
+__device__ __forceinline__ void inv_transpose(const R (&F)[D][D], R J, R (&A)[D][D]) {
+  R rJ = R(1) / J;
   if constexpr (D == 2) {
     A[0][0] = F[1][1] * rJ;
     A[0][1] = -F[1][0] * rJ;
@@ -179,40 +194,41 @@ __device__ __forceinline__ void inv_transpose(const float (&F)[D][D], float J, f
 // --------------------------------------------------------------------------- stencil
 // Quadratic B-spline: per axis base = floor(x/dx - 0.5), f = x/dx - base in [0.5, 1.5); node
 // base+k has weight w_k(f) and dw_k = d w_k / d x_p.
-template <int D>
+template <int D, class R = float>
 struct Sten {
   int base[D];
-  float f[D];
-  float w[D][3];
-  float dw[D][3];
+  R f[D];
+  R w[D][3];
+  R dw[D][3];
 };
 
-template <int D>
-__device__ __forceinline__ bool stencil_base(const float* x, float inv_dx, const int* n, int* base, float* f) {
+template <int D, class R>
+__device__ __forceinline__ bool stencil_base(const R* x, R inv_dx, const int* n, int* base, R* f) {
   bool ok = true;
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    float xs = x[a] * inv_dx;
-    float b = floorf(xs - 0.5f);
-    ok = ok && (b >= 0.0f) && (b <= float(n[a] - 3));
+    R xs = x[a] * inv_dx;
+    R b = s_floor(xs - R(0.5));
+    ok = ok && (b >= R(0)) && (b <= R(n[a] - 3));
     base[a] = ok ? int(b) : 0;
     f[a] = xs - b;
   }
   return ok;
 }
 
-__device__ __forceinline__ void bspline(float f, float inv_dx, float* w, float* dw) {
-  float t0 = 1.5f - f, t1 = f - 1.0f, t2 = f - 0.5f;
-  w[0] = 0.5f * t0 * t0;
-  w[1] = 0.75f - t1 * t1;
-  w[2] = 0.5f * t2 * t2;
+template <class R>
+__device__ __forceinline__ void bspline(R f, R inv_dx, R* w, R* dw) {
+  R t0 = R(1.5) - f, t1 = f - R(1), t2 = f - R(0.5);
+  w[0] = R(0.5) * t0 * t0;
+  w[1] = R(0.75) - t1 * t1;
+  w[2] = R(0.5) * t2 * t2;
   dw[0] = -t0 * inv_dx;
-  dw[1] = -2.0f * t1 * inv_dx;
+  dw[1] = R(-2) * t1 * inv_dx;
   dw[2] = t2 * inv_dx;
 }
 
-template <int D>
-__device__ __forceinline__ bool make_stencil(const float* x, float inv_dx, const int* n, Sten<D>& s) {
+template <int D, class R>
+__device__ __forceinline__ bool make_stencil(const R* x, R inv_dx, const int* n, Sten<D, R>& s) {
   bool ok = stencil_base<D>(x, inv_dx, n, s.base, s.f);
 #pragma unroll
   for (int a = 0; a < D; ++a) bspline(s.f[a], inv_dx, s.w[a], s.dw[a]);
@@ -220,19 +236,21 @@ __device__ __forceinline__ bool make_stencil(const float* x, float inv_dx, const
 }
 
 // --------------------------------------------------------------------------- constitutive
-struct Material {
-  float mu, la;
+template <class R>
+struct MaterialT {
+  R mu, la;
 };
+using Material = MaterialT<float>;
 
 // P = mu (F - F^{-T}) + lambda ln J F^{-T} + F sigma_a, sigma_a = a Diag(dir).
 // Returns J (caller checks J > 0 before trusting P).
-template <int D>
-__device__ __forceinline__ float stress(const float (&F)[D][D], Material m, const float* sig_diag, float (&P)[D][D],
-                                        float (&A)[D][D]) {
-  float J = det<D>(F);
-  float Js = J > 0.0f ? J : 1.0f;
+template <int D, class R>
+__device__ __forceinline__ R stress(const R (&F)[D][D], MaterialT<R> m, const R* sig_diag, R (&P)[D][D],
+                                    R (&A)[D][D]) {
+  R J = det<D>(F);
+  R Js = J > R(0) ? J : R(1);
   inv_transpose<D>(F, Js, A);
-  float lJ = logf(Js);
+  R lJ = s_log(Js);
 #pragma unroll
   for (int i = 0; i < D; ++i)
 #pragma unroll
@@ -241,14 +259,14 @@ __device__ __forceinline__ float stress(const float (&F)[D][D], Material m, cons
 }
 
 // G = -(4/dx^2) dt V0 P F^T + m C  (Eq. 4)
-template <int D>
-__device__ __forceinline__ void mls_G(const float (&P)[D][D], const float (&F)[D][D], const float (&C)[D][D], float kG,
-                                      float mass, float (&G)[D][D]) {
+template <int D, class R>
+__device__ __forceinline__ void mls_G(const R (&P)[D][D], const R (&F)[D][D], const R (&C)[D][D], R kG, R mass,
+                                      R (&G)[D][D]) {
 #pragma unroll
   for (int i = 0; i < D; ++i)
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-      float s = 0.0f;
+      R s = R(0);
 #pragma unroll
       for (int k = 0; k < D; ++k) s += P[i][k] * F[j][k];
       G[i][j] = kG * s + mass * C[i][j];
@@ -256,34 +274,34 @@ __device__ __forceinline__ void mls_G(const float (&P)[D][D], const float (&F)[D
 }
 
 // mu Pbar + (mu - lambda ln J) F^{-T} Pbar^T F^{-T} + lambda (F^{-T}:Pbar) F^{-T}
-template <int D>
-__device__ __forceinline__ void nh_hessian_apply(const float (&A)[D][D], float J, Material m, const float (&Pb)[D][D],
-                                                 float (&R)[D][D]) {
-  float lJ = logf(J > 0.0f ? J : 1.0f);
-  float AP = 0.0f;
+template <int D, class R>
+__device__ __forceinline__ void nh_hessian_apply(const R (&A)[D][D], R J, MaterialT<R> m, const R (&Pb)[D][D],
+                                                 R (&H)[D][D]) {
+  R lJ = s_log(J > R(0) ? J : R(1));
+  R AP = R(0);
 #pragma unroll
   for (int i = 0; i < D; ++i)
 #pragma unroll
     for (int j = 0; j < D; ++j) AP += A[i][j] * Pb[i][j];
-  float T[D][D];  // A Pb^T
+  R T[D][D];  // A Pb^T
 #pragma unroll
   for (int i = 0; i < D; ++i)
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-      float s = 0.0f;
+      R s = R(0);
 #pragma unroll
       for (int k = 0; k < D; ++k) s += A[i][k] * Pb[j][k];
       T[i][j] = s;
     }
-  float c = m.mu - m.la * lJ;
+  R c = m.mu - m.la * lJ;
 #pragma unroll
   for (int i = 0; i < D; ++i)
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-      float s = 0.0f;
+      R s = R(0);
 #pragma unroll
       for (int k = 0; k < D; ++k) s += T[i][k] * A[k][j];
-      R[i][j] = m.mu * Pb[i][j] + c * s + m.la * AP * A[i][j];
+      H[i][j] = m.mu * Pb[i][j] + c * s + m.la * AP * A[i][j];
     }
 }
 
@@ -291,13 +309,23 @@ __device__ __forceinline__ void nh_hessian_apply(const float (&A)[D][D], float J
 // Boundary of the grid: a band `width` nodes deep along each of the 2 dim walls; wall w = 2a + side
 // (axis a, low side 0) is sticky (kind 0), slip with Coulomb friction c[w] (kind 1, S5) or open
 // (kind 2).
-struct BCPar {
+template <class R>
+struct BCParT {
   int width;
   int kind[6];
-  float c[6];
+  R c[6];
 };
+using BCPar = BCParT<float>;
 
-constexpr float kBCEps = 1e-20f;
+// Regulariser of the tangential norm (keeps the projection differentiable at v_t = 0).
+template <class R>
+__device__ __forceinline__ R bc_eps() {
+  return R(1e-20);
+}
+template <>
+__device__ __forceinline__ float bc_eps<float>() {
+  return 1e-20f;
+}
 
 // Whether node idx lies in wall w's band.
 __device__ __forceinline__ bool wall_hit(const int* idx, const int* n, int width, int w) {
@@ -306,64 +334,64 @@ __device__ __forceinline__ bool wall_hit(const int* idx, const int* n, int width
 }
 
 // One wall: v <- l_t* v_t / l_t + max(l_n, 0) n, l_t* = max(l_t + c min(l_n, 0), 0).
-template <int D>
-__device__ __forceinline__ void project(float* v, int axis, float sgn, float c) {
-  float ln = v[axis] * sgn;
-  float vt[D];
-  float lt2 = 0.0f;
+template <int D, class R>
+__device__ __forceinline__ void project(R* v, int axis, R sgn, R c) {
+  R ln = v[axis] * sgn;
+  R vt[D];
+  R lt2 = R(0);
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    vt[a] = v[a] - (a == axis ? ln * sgn : 0.0f);
+    vt[a] = v[a] - (a == axis ? ln * sgn : R(0));
     lt2 += vt[a] * vt[a];
   }
-  float lt = sqrtf(lt2 + kBCEps);
-  float R = lt + c * fminf(ln, 0.0f);
-  float lts = fmaxf(R, 0.0f);
-  float s = lts / lt;
+  R lt = s_sqrt(lt2 + bc_eps<R>());
+  R Rt = lt + c * s_min(ln, R(0));
+  R lts = s_max(Rt, R(0));
+  R s = lts / lt;
 #pragma unroll
-  for (int a = 0; a < D; ++a) v[a] = s * vt[a] + (a == axis ? fmaxf(ln, 0.0f) * sgn : 0.0f);
+  for (int a = 0; a < D; ++a) v[a] = s * vt[a] + (a == axis ? s_max(ln, R(0)) * sgn : R(0));
 }
 
 // Adjoint of `project` at input v (forward value recomputed here), g in/out.
-template <int D>
-__device__ __forceinline__ void project_adj(const float* v, int axis, float sgn, float c, float* g) {
-  float ln = v[axis] * sgn;
-  float vt[D];
-  float lt2 = 0.0f;
+template <int D, class R>
+__device__ __forceinline__ void project_adj(const R* v, int axis, R sgn, R c, R* g) {
+  R ln = v[axis] * sgn;
+  R vt[D];
+  R lt2 = R(0);
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    vt[a] = v[a] - (a == axis ? ln * sgn : 0.0f);
+    vt[a] = v[a] - (a == axis ? ln * sgn : R(0));
     lt2 += vt[a] * vt[a];
   }
-  float lt = sqrtf(lt2 + kBCEps);
-  float R = lt + c * fminf(ln, 0.0f);
-  float lts = fmaxf(R, 0.0f);
-  float rlt = 1.0f / lt;
-  float g_lts = 0.0f, s = 0.0f, gn = g[axis] * sgn;
+  R lt = s_sqrt(lt2 + bc_eps<R>());
+  R Rt = lt + c * s_min(ln, R(0));
+  R lts = s_max(Rt, R(0));
+  R rlt = R(1) / lt;
+  R g_lts = R(0), s = R(0), gn = g[axis] * sgn;
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     g_lts += g[a] * vt[a] * rlt;
     s += vt[a] * g[a] * lts;  // v_t . vhat_bar with vhat_bar = g l_t*
   }
-  float HR = R >= 0.0f ? 1.0f : 0.0f;
-  float g_lt = -s * rlt * rlt + g_lts * HR;
-  float gvt[D];
-  float vtn = 0.0f;
+  R HR = Rt >= R(0) ? R(1) : R(0);
+  R g_lt = -s * rlt * rlt + g_lts * HR;
+  R gvt[D];
+  R vtn = R(0);
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     gvt[a] = (g_lt * vt[a] + g[a] * lts) * rlt;
-    vtn += (a == axis ? gvt[a] * sgn : 0.0f);
+    vtn += (a == axis ? gvt[a] * sgn : R(0));
   }
-  float g_ln = -vtn + g_lts * HR * c * (ln <= 0.0f ? 1.0f : 0.0f) + (ln >= 0.0f ? 1.0f : 0.0f) * gn;
+  R g_ln = -vtn + g_lts * HR * c * (ln <= R(0) ? R(1) : R(0)) + (ln >= R(0) ? R(1) : R(0)) * gn;
 #pragma unroll
-  for (int a = 0; a < D; ++a) g[a] = gvt[a] + (a == axis ? g_ln * sgn : 0.0f);
+  for (int a = 0; a < D; ++a) g[a] = gvt[a] + (a == axis ? g_ln * sgn : R(0));
 }
 
 // Boundary condition on the node velocity (gravity already added).  A node in a sticky wall's
 // band is fixed; otherwise the slip walls whose band contains it are applied in sequence: axis
 // 0, 1, 2, low side before high side, each with its own friction; open walls do nothing.
-template <int D>
-__device__ __forceinline__ void bc_apply(const int* idx, const int* n, const BCPar& bc, float* v) {
+template <int D, class R>
+__device__ __forceinline__ void bc_apply(const int* idx, const int* n, const BCParT<R>& bc, R* v) {
   bool hit[2 * D], any = false, sticky = false;
 #pragma unroll
   for (int w = 0; w < 2 * D; ++w) {
@@ -374,18 +402,17 @@ __device__ __forceinline__ void bc_apply(const int* idx, const int* n, const BCP
   if (!any) return;
   if (sticky) {
 #pragma unroll
-    for (int a = 0; a < D; ++a) v[a] = 0.0f;
+    for (int a = 0; a < D; ++a) v[a] = R(0);
     return;
   }
 #pragma unroll
   for (int w = 0; w < 2 * D; ++w)
-    if (hit[w] && bc.kind[w] == 1) project<D>(v, w >> 1, (w & 1) ? -1.0f : 1.0f, bc.c[w]);
+    if (hit[w] && bc.kind[w] == 1) project<D>(v, w >> 1, (w & 1) ? R(-1) : R(1), bc.c[w]);
 }
 
 // Adjoint of bc_apply: g holds dL/dv* on entry and dL/dv_g on exit; vg = velocity before BC.
-template <int D>
-__device__ __forceinline__ void bc_adjoint(const int* idx, const int* n, const BCPar& bc, const float* vg,
-                                           float* g) {
+template <int D, class R>
+__device__ __forceinline__ void bc_adjoint(const int* idx, const int* n, const BCParT<R>& bc, const R* vg, R* g) {
   bool hit[2 * D], any = false, sticky = false;
 #pragma unroll
   for (int w = 0; w < 2 * D; ++w) {
@@ -396,24 +423,24 @@ __device__ __forceinline__ void bc_adjoint(const int* idx, const int* n, const B
   if (!any) return;
   if (sticky) {
 #pragma unroll
-    for (int a = 0; a < D; ++a) g[a] = 0.0f;
+    for (int a = 0; a < D; ++a) g[a] = R(0);
     return;
   }
   // replay the wall sequence (wall w: axis w / 2, low side for even w) to get every wall's input,
   // then walk it backwards; the loops are unrolled so the inputs stay in registers
-  float vin[2 * D][D];
-  float v[D];
+  R vin[2 * D][D];
+  R v[D];
 #pragma unroll
   for (int a = 0; a < D; ++a) v[a] = vg[a];
 #pragma unroll
   for (int w = 0; w < 2 * D; ++w) {
 #pragma unroll
     for (int b = 0; b < D; ++b) vin[w][b] = v[b];
-    if (hit[w]) project<D>(v, w >> 1, (w & 1) ? -1.0f : 1.0f, bc.c[w]);
+    if (hit[w]) project<D>(v, w >> 1, (w & 1) ? R(-1) : R(1), bc.c[w]);
   }
 #pragma unroll
   for (int w = 2 * D - 1; w >= 0; --w)
-    if (hit[w]) project_adj<D>(vin[w], w >> 1, (w & 1) ? -1.0f : 1.0f, bc.c[w], g);
+    if (hit[w]) project_adj<D>(vin[w], w >> 1, (w & 1) ? R(-1) : R(1), bc.c[w], g);
 }
 
 }  // namespace gbmpm

@@ -122,6 +122,23 @@ void invalidate_graphs(mpm_scene* s);
 // Records rebuilt after the scene template changed (mpm_scene_set_material / _set_walls).
 mpm_status refresh_records(mpm_scene* s);
 
+// Event pair around one launch of kind k (no-op unless k is being timed).
+struct ProfScope {
+  mpm_ctx* c;
+  cudaStream_t st;
+  int slot = -1;
+  ProfScope(mpm_ctx* ctx, cudaStream_t stream, int kind) : c(ctx), st(stream) {
+    if (!(c->prof_mask & (1u << kind))) return;
+    if (2 * (c->prof_used + 1) > int(c->prof_ev.size())) return;
+    slot = c->prof_used++;
+    c->prof_kind[slot] = kind;
+    cudaEventRecord(c->prof_ev[2 * slot], st);
+  }
+  ~ProfScope() {
+    if (slot >= 0) cudaEventRecord(c->prof_ev[2 * slot + 1], st);
+  }
+};
+
 // Autotuner (mpm_tune.cu).
 // Looks the scene's workload up in the cache, or arms trials for its tile kernels (mode AUTO/FORCE).
 mpm_status tune_init(mpm_scene* s);

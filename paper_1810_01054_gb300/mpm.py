@@ -98,6 +98,34 @@ class NoAllocStep(C.Structure):
     ]
 
 
+class SceneDesc64(C.Structure):
+    """Mirror of mpm_scene64_desc (include/mpm.h)."""
+    _fields_ = [
+        ("dim", C.c_int),
+        ("n_grid", C.c_int * 3),
+        ("dx", C.c_double),
+        ("dt", C.c_double),
+        ("gravity", C.c_double * 3),
+        ("E", C.c_double),
+        ("nu", C.c_double),
+        ("p_mass", C.c_double),
+        ("p_vol", C.c_double),
+        ("bc_width", C.c_int),
+        ("wall_kind", C.c_int * 6),
+        ("wall_c", C.c_double * 6),
+        ("n_particles", C.c_int),
+        ("x0", C.c_void_p),
+        ("v0", C.c_void_p),
+        ("C0", C.c_void_p),
+        ("F0", C.c_void_p),
+        ("group", C.c_void_p),
+        ("n_groups", C.c_int),
+        ("act_dir", C.c_void_p),
+        ("n_act_steps", C.c_int),
+        ("act", C.c_void_p),
+    ]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -136,13 +164,23 @@ _SIGS = {
     "mpm_tune_cache_store": [C.c_int, C.c_longlong, C.c_longlong, C.c_int, C.POINTER(C.c_int)],
     "mpm_tune_cache_save": [C.c_char_p],
     "mpm_tune_cache_load": [C.c_char_p],
+    "mpm64_create": [C.c_void_p, C.POINTER(SceneDesc64), C.POINTER(C.c_void_p)],
+    "mpm64_destroy": [C.c_void_p],
+    "mpm64_set_state": [C.c_void_p] + [C.c_void_p] * 4,
+    "mpm64_set_actuation": [C.c_void_p, C.c_void_p, C.c_int],
+    "mpm64_rollout": [C.c_void_p, C.c_int],
+    "mpm64_get_state": [C.c_void_p, C.c_int] + [C.c_void_p] * 4,
+    "mpm64_backward": [C.c_void_p] + [C.c_void_p] * 9,
+    "mpm64_info": [C.c_void_p] + [C.POINTER(C.c_int)] * 4,
 }
 
 K_SORT, K_P2G, K_GRID, K_G2P, K_P2G_ADJ, K_GRID_ADJ, K_ADJ_GATHER, K_CTRL, K_PLAIN = range(9)
+K_F64_P2G, K_F64_GRID, K_F64_G2P, K_F64_P2G_ADJ, K_F64_ADJ = range(9, 14)
 TUNE_OFF, TUNE_AUTO, TUNE_FORCE = 0, 1, 2
 TK_P2G, TK_G2P, TK_P2G_ADJ, TK_ADJ_GATHER = range(4)
 TILE_KERNELS = ["p2g", "g2p", "p2g_adj", "adj_gather"]
-KERNEL_NAMES = ["sort", "p2g", "grid", "g2p", "p2g_adj", "grid_adj", "adj_gather", "ctrl", "plain"]
+KERNEL_NAMES = ["sort", "p2g", "grid", "g2p", "p2g_adj", "grid_adj", "adj_gather", "ctrl", "plain",
+                "f64_p2g", "f64_grid", "f64_g2p", "f64_p2g_adj", "f64_adj"]
 
 
 def launch_count() -> int:
@@ -495,6 +533,123 @@ class Scene:
             pass
 
 
+def _f64(a, shape):
+    if a is None:
+        return None
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(shape))
+
+
+class Scene64:
+    """The double-precision plain form (mpm64_*): one scene in FP64 on the GPU for accuracy
+    studies (Section VI, float64 cases).  Host numpy arrays in and out.  Actuation is a per-step
+    table: the spec's MPM_CTRL_TABLE parameters, or ``act`` [L, G] given here (required for other
+    controller families with groups; pass np.zeros((0, G)) for a passive run)."""
+
+    def __init__(self, ctx: Context, spec, act=None):
+        if getattr(spec, "E_arr", None) is not None or getattr(spec, "mass_arr", None) is not None:
+            raise ValueError("the FP64 form takes a uniform material")
+        d = int(spec.dim)
+        self.ctx, self.dim, self.spec = ctx, d, spec
+        N = int(np.asarray(spec.x0).shape[0])
+        G = int(np.asarray(spec.act_dir).shape[0])
+        self.N, self.G = N, G
+        if act is None:
+            if int(spec.ctrl_type) == 3:  # MPM_CTRL_TABLE
+                act = np.asarray(spec.ctrl_params, np.float64).reshape(int(spec.ctrl_hidden), G)
+            elif G > 0:
+                raise ValueError("the FP64 form takes actuation as a per-step table: pass act=[L, G]")
+            else:
+                act = np.zeros((0, 0))
+        self._keep = []
+
+        def arr(a, shape):
+            t = _f64(a, shape)
+            self._keep.append(t)
+            return _ptr(t)
+
+        desc = SceneDesc64()
+        desc.dim = d
+        ng = list(spec.n_grid) + [1] * (3 - len(spec.n_grid))
+        for a in range(3):
+            desc.n_grid[a] = int(ng[a])
+        desc.dx, desc.dt = float(spec.dx), float(spec.dt)
+        g = list(spec.gravity) + [0.0] * (3 - len(spec.gravity))
+        for a in range(3):
+            desc.gravity[a] = float(g[a])
+        desc.E, desc.nu = float(spec.E), float(spec.nu)
+        desc.p_mass, desc.p_vol = float(spec.p_mass), float(spec.p_vol)
+        desc.bc_width = int(spec.bc_width)
+        kinds = spec.wall_kind if getattr(spec, "wall_kind", None) is not None else [spec.bc_type] * (2 * d)
+        cs = spec.wall_c if getattr(spec, "wall_c", None) is not None else [spec.friction_c] * (2 * d)
+        for w in range(6):
+            desc.wall_kind[w] = int(kinds[w]) if w < 2 * d else 2
+            desc.wall_c[w] = float(cs[w]) if w < 2 * d else 0.0
+        desc.n_particles = N
+        desc.x0 = arr(spec.x0, (N, d))
+        desc.v0 = arr(spec.v0, (N, d)) if spec.v0 is not None else None
+        desc.C0 = arr(spec.C0, (N, d, d)) if spec.C0 is not None else None
+        desc.F0 = arr(spec.F0, (N, d, d)) if spec.F0 is not None else None
+        grp = np.ascontiguousarray(np.asarray(spec.group, dtype=np.int32).reshape(N))
+        self._keep.append(grp)
+        desc.group = _ptr(grp)
+        desc.n_groups = G
+        desc.act_dir = arr(spec.act_dir, (max(G, 1), d)) if G else None
+        act = np.asarray(act, np.float64)
+        self.L = int(act.shape[0]) if act.size or act.ndim == 2 else 0
+        desc.n_act_steps = self.L
+        desc.act = arr(act, (self.L, G)) if self.L * G else None
+        h = C.c_void_p()
+        _check(lib().mpm64_create(ctx.handle, C.byref(desc), C.byref(h)), "mpm64_create")
+        self._keep = []
+        self.handle = h
+        ctx._adopt(self)
+
+    def set_state(self, x, v=None, C_=None, F=None):
+        d, N = self.dim, self.N
+        a = [_f64(x, (N, d)), _f64(v, (N, d)), _f64(C_, (N, d, d)), _f64(F, (N, d, d))]
+        _check(lib().mpm64_set_state(self.handle, *[_ptr(t) for t in a]), "mpm64_set_state")
+
+    def set_actuation(self, U):
+        U = np.ascontiguousarray(np.asarray(U, np.float64).reshape(-1, self.G))
+        _check(lib().mpm64_set_actuation(self.handle, _ptr(U), int(U.shape[0])), "mpm64_set_actuation")
+        self.L = int(U.shape[0])
+
+    def rollout(self, n_steps: int):
+        _check(lib().mpm64_rollout(self.handle, int(n_steps)), "mpm64_rollout")
+
+    def get_state(self, step: int = -1):
+        d, N = self.dim, self.N
+        out = [np.empty((N, d)), np.empty((N, d)), np.empty((N, d, d)), np.empty((N, d, d))]
+        _check(lib().mpm64_get_state(self.handle, int(step), *[_ptr(t) for t in out]), "mpm64_get_state")
+        return tuple(out)
+
+    def backward(self, gx=None, gv=None, gC=None, gF=None):
+        """dL/d(initial x, v, C, F) and dL/dU [L, G] for seeds dL/d(final x, v, C, F)."""
+        d, N = self.dim, self.N
+        seeds = [_f64(gx, (N, d)), _f64(gv, (N, d)), _f64(gC, (N, d, d)), _f64(gF, (N, d, d))]
+        out = [np.empty((N, d)), np.empty((N, d)), np.empty((N, d, d)), np.empty((N, d, d)),
+               np.zeros((self.L, self.G))]
+        _check(lib().mpm64_backward(self.handle, *[_ptr(t) for t in seeds], *[_ptr(t) for t in out]),
+               "mpm64_backward")
+        return tuple(out)
+
+    def info(self):
+        n, g, L, T = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        _check(lib().mpm64_info(self.handle, C.byref(n), C.byref(g), C.byref(L), C.byref(T)), "mpm64_info")
+        return {"n_particles": n.value, "n_groups": g.value, "act_steps": L.value, "rollout_steps": T.value}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(lib().mpm64_destroy(self.handle), "mpm64_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Batch:
     """Scenes of one dimension advanced together by the same launches (mpm_batch_*).  A request is
     a rollout of n_steps and, with want_grad, its reverse pass seeded by loss = mean final x_0;
@@ -551,4 +706,4 @@ def header_symbols(header_path: str):
     import re
     text = open(header_path).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(mpm_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(mpm(?:64)?_[a-z0-9_]+)\s*\(", text)))

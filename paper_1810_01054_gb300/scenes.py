@@ -355,6 +355,43 @@ def serving_request(req_id: int, seed: int = 4) -> tuple:
     return spec, want_grad
 
 
+def billiards_2d(seed: int = 5, *, n: int = 64, radius_cells: float = 5.0, gap_cells: float = 3.0,
+                 speed: float = 0.6, offset: float = 0.35, E: float = 100.0, dt: float = 1e-3,
+                 n_steps: int = 1000) -> SceneSpec:
+    """Two colliding elastic discs in 2D (the float64 accuracy case of Section VI, whose geometry
+    the paper does not give): 64^2 grid, dx = 1/64, discs of radius 5 dx on a lattice of spacing
+    dx/2 (jitter +-0.1 of it, seeded), ball A centred at (0.2, 0.5) moving at (0.6, 0), ball B at
+    rest 3 dx beyond it along x and 0.35 radii higher (an oblique hit), no gravity, sticky walls
+    3 cells deep; E = 100, nu = 0.3, rho = 1, dt = 1e-3 (0.64 of the explicit limit).  The
+    discs first touch (share grid nodes) after about 25 steps, so a 1- or 10-step rollout has no
+    collision and 100 or 1000 steps do; B leaves at ~0.43 and never reaches a wall within 1000
+    steps.  Particles of A come first."""
+    rng = np.random.default_rng(seed)
+    dx = 1.0 / n
+    s = dx / 2
+    R = radius_cells * dx
+    ca = np.array([0.2, 0.5])
+    cb = ca + np.array([2 * R + gap_cells * dx, offset * R])
+    pts = []
+    for c in (ca, cb):
+        ax = _lattice_box(c - R, c + R, s)
+        I, J = np.meshgrid(ax[0], ax[1], indexing="ij")
+        p = np.stack([(I.ravel() + 0.5) * s, (J.ravel() + 0.5) * s], axis=1)
+        pts.append(p[np.linalg.norm(p - c, axis=1) <= R])
+    na = pts[0].shape[0]
+    pos = np.concatenate(pts)
+    N = pos.shape[0]
+    spec = _finish("billiards_2d", 2, n, dx, dt, E, s, pos, np.full(N, -1), np.zeros((0, 2)), CTRL_TABLE,
+                   np.zeros(0), rng, 0.1 * s, n_steps=n_steps, bc_width=3, gravity=(0.0, 0.0))
+    spec.v0[:na] = [speed, 0.0]
+    return spec
+
+
+def billiards_ball_a(spec: SceneSpec) -> np.ndarray:
+    """Mask of ball A's particles in a billiards_2d scene (the ones moving at the start)."""
+    return np.linalg.norm(spec.v0, axis=1) > 0
+
+
 def blob(dim: int, n: int, n_particles: int, seed: int, *, dt: float = 1e-3, E: float = 20.0,
          nu: float = 0.3, bc_type: int = BC_STICKY, bc_width: int = 2, friction_c: float = 0.0,
          n_groups: int = 2, ctrl_type: int = CTRL_SIN, hidden: int = 8, gravity=None,

@@ -24,12 +24,11 @@ def test_binding_signatures_cover_the_header():
     assert names == set(mpm._SIGS), names ^ set(mpm._SIGS)
 
 
-def test_scene_descriptor_layout_matches_header():
-    """The ctypes mirror of mpm_scene_desc lists the header's fields in the header's order."""
+def _header_fields(start_marker, end_marker):
     import re
     text = open(HEADER).read()
-    body = text[text.index("typedef struct {", text.index("MPM_IMPL_PLAIN")):]
-    body = body[: body.index("} mpm_scene_desc;")]
+    body = text[text.index("typedef struct {", text.index(start_marker)):]
+    body = body[: body.index(end_marker)]
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
     fields = []
     for decl in body.split(";"):
@@ -37,6 +36,21 @@ def test_scene_descriptor_layout_matches_header():
         if not decl:
             continue
         for part in decl.split(","):
-            name = re.findall(r"[A-Za-z_][A-Za-z0-9_]*", part.split("[")[0])[-1]
-            fields.append(name)
-    assert fields == [f[0] for f in mpm.SceneDesc._fields_]
+            fields.append(re.findall(r"[A-Za-z_][A-Za-z0-9_]*", part.split("[")[0])[-1])
+    return fields
+
+
+def test_scene_descriptor_layout_matches_header():
+    """The ctypes mirror of mpm_scene_desc lists the header's fields in the header's order."""
+    assert _header_fields("MPM_IMPL_PLAIN", "} mpm_scene_desc;") == [f[0] for f in mpm.SceneDesc._fields_]
+
+
+def test_fp64_descriptor_layout_matches_header():
+    """The same for mpm_scene64_desc, and the field types are the header's double/int ones."""
+    import ctypes as C
+    assert _header_fields("typedef struct mpm_scene64 mpm_scene64;", "} mpm_scene64_desc;") == \
+        [f[0] for f in mpm.SceneDesc64._fields_]
+    types = dict(mpm.SceneDesc64._fields_)
+    for name in ("dx", "dt", "E", "nu", "p_mass", "p_vol"):
+        assert types[name] is C.c_double
+    assert types["wall_c"]._type_ is C.c_double and types["gravity"]._type_ is C.c_double
