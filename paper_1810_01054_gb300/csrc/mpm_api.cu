@@ -190,14 +190,17 @@ ScenePar rec_rev(const mpm_scene* s, float4* st, const float4* ain, float4* aout
 
 // ---------------------------------------------------------------------------- step sequences
 // Forward step of phase ph (PH_STEP, PH_ROLL, PH_RCM) on stream st.
+// The tiled form makes the step's record selection inside its first kernel (the sort here, the
+// keys in the reverse step); the plain form launches it separately.  The sort does not depend on
+// the controller, so the controller's forward runs after it.
 mpm_status enqueue_forward(mpm_scene* s, int ph, cudaStream_t st) {
   mpm_ctx* c = s->ctx;
-  CK(launch_select(s->dsel + ph, 1, s->cur, st));
-  {
-    ProfScope p(c, st, MPM_K_CTRL);
-    CK(ctrl_step_forward(s->hp, s->cur, s->ctrl, st));
-  }
   if (s->impl == MPM_IMPL_PLAIN) {
+    CK(launch_select(s->dsel + ph, 1, s->cur, st));
+    {
+      ProfScope p(c, st, MPM_K_CTRL);
+      CK(ctrl_step_forward(s->hp, s->cur, s->ctrl, st));
+    }
     ProfScope p(c, st, MPM_K_PLAIN);
     CK(s->dim == 2 ? launch_plain_step<2>(s->cur, s->hp, st) : launch_plain_step<3>(s->cur, s->hp, st));
     return MPM_OK;
@@ -205,7 +208,11 @@ mpm_status enqueue_forward(mpm_scene* s, int ph, cudaStream_t st) {
   const bool two = s->dim == 2;
   {
     ProfScope p(c, st, MPM_K_SORT);
-    CK(two ? launch_sort<2>(s->b, st) : launch_sort<3>(s->b, st));
+    CK(two ? launch_sort<2>(s->b, st, s->dsel + ph) : launch_sort<3>(s->b, st, s->dsel + ph));
+  }
+  {
+    ProfScope p(c, st, MPM_K_CTRL);
+    CK(ctrl_step_forward(s->hp, s->cur, s->ctrl, st));
   }
   {
     ProfScope p(c, st, MPM_K_P2G);
@@ -224,10 +231,11 @@ mpm_status enqueue_forward(mpm_scene* s, int ph, cudaStream_t st) {
 mpm_status enqueue_reverse(mpm_scene* s, cudaStream_t st) {
   mpm_ctx* c = s->ctx;
   const bool two = s->dim == 2;
-  CK(launch_select(s->dsel + PH_REV, 1, s->cur, st));
   if (s->impl != MPM_IMPL_PLAIN) {
     ProfScope p(c, st, MPM_K_SORT);
-    CK(two ? launch_keys<2>(s->b, st) : launch_keys<3>(s->b, st));
+    CK(two ? launch_keys<2>(s->b, st, s->dsel + PH_REV) : launch_keys<3>(s->b, st, s->dsel + PH_REV));
+  } else {
+    CK(launch_select(s->dsel + PH_REV, 1, s->cur, st));
   }
   {
     ProfScope p(c, st, MPM_K_CTRL);
@@ -263,8 +271,7 @@ mpm_status enqueue_reverse(mpm_scene* s, cudaStream_t st) {
 // Bin keys and tile histogram of the state the selection of phase ph names (tiled form only).
 mpm_status enqueue_keys(mpm_scene* s, int ph, cudaStream_t st) {
   if (s->impl == MPM_IMPL_PLAIN) return MPM_OK;
-  CK(launch_select(s->dsel + ph, 1, s->cur, st));
-  CK(s->dim == 2 ? launch_keys<2>(s->b, st) : launch_keys<3>(s->b, st));
+  CK(s->dim == 2 ? launch_keys<2>(s->b, st, s->dsel + ph) : launch_keys<3>(s->b, st, s->dsel + ph));
   return MPM_OK;
 }
 

@@ -136,10 +136,12 @@ inline void default_launch(BatchDev& b, int sm_count) {
 // Sets the kernels' launch attributes (large dynamic shared memory); once per process/device.
 cudaError_t configure_kernels();
 // Tiled (sorted, deterministic) form.
+// sel non-null (a single scene): the first kernel also makes the step's record selection (what
+// launch_select does), publishing it to b.scenes[0].
 template <int D>
-cudaError_t launch_keys(const BatchDev& b, cudaStream_t s);
+cudaError_t launch_keys(const BatchDev& b, cudaStream_t s, const SelectPar* sel = nullptr);
 template <int D>
-cudaError_t launch_sort(const BatchDev& b, cudaStream_t s);
+cudaError_t launch_sort(const BatchDev& b, cudaStream_t s, const SelectPar* sel = nullptr);
 template <int D>
 cudaError_t launch_p2g(const BatchDev& b, bool with_adjoint, cudaStream_t s);
 // G2P (Eqs. 7-10) including the grid update of its node block (Eq. 6, gravity, boundary).

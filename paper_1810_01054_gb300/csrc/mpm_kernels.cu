@@ -147,14 +147,57 @@ __device__ __forceinline__ float particle_G(const Part<D>& q, const ScenePar& sp
   return J;
 }
 
+// ============================================================================ record selection
+// Scene record of step n = *ctr: table[map[n - base]] (map NULL: table[0]) with the batch offsets
+// patched in, copied to dst by the calling CTA's threads (no barrier: each thread writes its own
+// words, the offsets in place of the copied ones).
+__device__ __forceinline__ int selected_index(const SelectPar& q, int n) { return q.map ? q.map[n - q.base] : 0; }
+
+__device__ __forceinline__ void select_copy(const SelectPar& q, int n, ScenePar* dst) {
+  const int* src = reinterpret_cast<const int*>(q.table + selected_index(q, n));
+  int* d = reinterpret_cast<int*>(dst);
+  constexpr int W = int(sizeof(ScenePar) / sizeof(int));
+  constexpr int TB = int(offsetof(ScenePar, tile_base) / sizeof(int));
+  constexpr int PB = int(offsetof(ScenePar, pbase) / sizeof(int));
+  for (int i = threadIdx.x; i < W; i += blockDim.x) d[i] = i == TB ? q.tile_base : (i == PB ? q.pbase : src[i]);
+}
+
+// The step's selection for one scene: its record into cur, and the sinusoid and table
+// controllers' actuation a_g(t_n) into q.act.
+__device__ __forceinline__ void select_publish(const SelectPar& q, ScenePar* cur) {
+  const int n = *q.ctr;
+  select_copy(q, n, cur);
+  const float tt = float(n) * q.dt;
+  const int g = threadIdx.x;
+  if (g < q.G && q.ctrl_type == 0) {
+    q.act[g] = q.params[g] * sinf(6.283185307179586f * q.freq * tt);
+  } else if (g < q.G && q.ctrl_type == 1) {
+    const float w = 6.283185307179586f * q.freq * tt;
+    q.act[g] = q.params[g * 4] * sinf(w) + q.params[g * 4 + 1] * cosf(w) + q.params[g * 4 + 2] * sinf(2.0f * w) +
+               q.params[g * 4 + 3] * cosf(2.0f * w);
+  } else if (g < q.G && q.ctrl_type == 3) {
+    q.act[g] = (n >= 0 && n < q.ctrl_len) ? q.params[size_t(n) * q.G + g] : 0.0f;
+  }
+}
+
 // ============================================================================ keys / sort
 // Bin keys of the state being read, and the tile histogram (tile_count must be zero on entry).
-template <int D>
-__global__ void k_keys(BatchDev b) {
+// With SEL (a single scene) the kernel also makes the step's selection: every CTA copies the
+// selected record to shared memory for its own use and CTA 0 publishes it (and the actuation) for
+// the kernels that follow, which replaces the selection launch.
+template <int D, bool SEL>
+__global__ void k_keys(BatchDev b, const SelectPar* __restrict__ sel) {
   pdl_enter();
+  __shared__ __align__(16) ScenePar srec[1];
+  if constexpr (SEL) {
+    const int n = *sel->ctr;
+    select_copy(*sel, n, srec);
+    if (blockIdx.x == 0) select_publish(*sel, b.scenes);
+    __syncthreads();
+  }
   int gp = blockIdx.x * blockDim.x + threadIdx.x;
   if (gp >= b.total_particles) return;
-  const ScenePar& sp = b.scenes[find_scene(b.scene_pbase, b.n_scenes, gp)];
+  const ScenePar& sp = SEL ? srec[0] : b.scenes[find_scene(b.scene_pbase, b.n_scenes, gp)];
   int p = gp - sp.pbase;
   float4 q = sp.planes[p];
   float x[3] = {q.x, q.y, q.z};
@@ -211,8 +254,10 @@ constexpr int SCAN_TILE = SCAN_THREADS * SCAN_PER_THREAD;
 __host__ __device__ __forceinline__ bool fused_scan(const BatchDev& b) { return b.total_tiles <= SCAN_TILE; }
 
 // Phase 1 of the tile scan: per-block totals of particle counts and of active tiles.
-__global__ void k_scan_reduce(BatchDev b) {
+template <bool SEL>
+__global__ void k_scan_reduce(BatchDev b, const SelectPar* __restrict__ sel) {
   pdl_enter();
+  if (SEL && blockIdx.x == 0) select_publish(*sel, b.scenes);  // the step's selection (k_keys)
   int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_PER_THREAD;
   uint32_t s = 0, c = 0;
 #pragma unroll
@@ -298,9 +343,13 @@ __global__ void k_scan_down(BatchDev b) {
 // SCAN_TILE) the tile scan is done here instead of by the scan kernels: every CTA scans the whole
 // histogram in shared memory (it is small), CTA 0 publishes tile_start, tile_slot, the active list
 // and n_active; the P2G that follows clears the per-step counters.
-template <int D, bool FUSED>
-__global__ void __launch_bounds__(256) k_scatter(BatchDev b) {
+// With SEL (a single scene, fused scan) CTA 0 also makes the step's selection (see k_keys); the
+// scatter itself reads only the record's step-invariant fields (keys, offsets, status), which it
+// takes from the phase's first record instead of the one being published.
+template <int D, bool FUSED, bool SEL>
+__global__ void __launch_bounds__(256) k_scatter(BatchDev b, const SelectPar* __restrict__ sel) {
   pdl_enter();
+  if (SEL && blockIdx.x == 0) select_publish(*sel, b.scenes);
   constexpr int PER = FUSED ? SCAN_TILE / 256 : 1;
   __shared__ uint32_t sstart[FUSED ? SCAN_TILE + 1 : 1];
   if constexpr (FUSED) {
@@ -344,10 +393,11 @@ __global__ void __launch_bounds__(256) k_scatter(BatchDev b) {
   }
   int gp = blockIdx.x * blockDim.x + threadIdx.x;
   if (gp >= b.total_particles) return;
-  const ScenePar& sp = b.scenes[find_scene(b.scene_pbase, b.n_scenes, gp)];
-  int p = gp - sp.pbase;
+  const ScenePar& sp = SEL ? sel->table[0] : b.scenes[find_scene(b.scene_pbase, b.n_scenes, gp)];
+  const int pbase = SEL ? sel->pbase : sp.pbase, tbase = SEL ? sel->tile_base : sp.tile_base;
+  int p = gp - pbase;
   const uint32_t k = sp.key[p];
-  const int t = k != KEY_INVALID ? int(sp.tile_base + (k >> 6)) : -1;
+  const int t = k != KEY_INVALID ? int(tbase + (k >> 6)) : -1;
   const uint32_t rank = warp_aggregated_inc(b.tile_fill, t);
   if (t < 0) return;
   const uint32_t start = FUSED ? sstart[t] : b.tile_start[t];
@@ -1368,28 +1418,42 @@ __global__ void __launch_bounds__(kAdjThreads<D>, 512 / kAdjThreads<D>) k_adj_ga
 
 // ============================================================================ launchers (tiled)
 template <int D>
-cudaError_t launch_keys(const BatchDev& b, cudaStream_t s) {
+cudaError_t launch_keys(const BatchDev& b, cudaStream_t s, const SelectPar* sel) {
   cudaError_t e = cudaMemsetAsync(b.tile_count, 0, sizeof(uint32_t) * size_t(b.total_tiles), s);
   if (e != cudaSuccess) return e;
+  if (sel) {  // at least one CTA: the selection is published even without particles
+    const int nblk = b.total_particles > 0 ? (b.total_particles + 255) / 256 : 1;
+    launch_pdl(k_keys<D, true>, dim3(nblk), dim3(256), 0, s, b, sel);
+    count_launches(1);
+    return cudaGetLastError();
+  }
   if (b.total_particles == 0) return cudaSuccess;
-  launch_pdl(k_keys<D>, dim3((b.total_particles + 255) / 256), dim3(256), 0, s, b);
+  launch_pdl(k_keys<D, false>, dim3((b.total_particles + 255) / 256), dim3(256), 0, s, b, sel);
   count_launches(1);
   return cudaGetLastError();
 }
 
 template <int D>
-cudaError_t launch_sort(const BatchDev& b, cudaStream_t s) {
+cudaError_t launch_sort(const BatchDev& b, cudaStream_t s, const SelectPar* sel) {
   if (fused_scan(b)) {  // scan inside the scatter; at least one CTA so the scan results are written
     const int nblk = b.total_particles > 0 ? (b.total_particles + 255) / 256 : 1;
-    launch_pdl(k_scatter<D, true>, dim3(nblk), dim3(256), 0, s, b);
+    if (sel)
+      launch_pdl(k_scatter<D, true, true>, dim3(nblk), dim3(256), 0, s, b, sel);
+    else
+      launch_pdl(k_scatter<D, true, false>, dim3(nblk), dim3(256), 0, s, b, sel);
     count_launches(1);
     return cudaGetLastError();
   }
   const int nblk = (b.total_tiles + SCAN_TILE - 1) / SCAN_TILE;
-  launch_pdl(k_scan_reduce, dim3(nblk), dim3(SCAN_THREADS), 0, s, b);
+  if (sel)
+    launch_pdl(k_scan_reduce<true>, dim3(nblk), dim3(SCAN_THREADS), 0, s, b, sel);
+  else
+    launch_pdl(k_scan_reduce<false>, dim3(nblk), dim3(SCAN_THREADS), 0, s, b, sel);
   launch_pdl(k_scan_top, dim3(1), dim3(SCAN_THREADS), 0, s, b, nblk);
   launch_pdl(k_scan_down, dim3(nblk), dim3(SCAN_THREADS), 0, s, b);
-  if (b.total_particles > 0) launch_pdl(k_scatter<D, false>, dim3((b.total_particles + 255) / 256), dim3(256), 0, s, b);
+  if (b.total_particles > 0)
+    launch_pdl(k_scatter<D, false, false>, dim3((b.total_particles + 255) / 256), dim3(256), 0, s, b,
+               static_cast<const SelectPar*>(nullptr));
   count_launches((b.total_particles > 0 ? 1 : 0) + 3);
   return cudaGetLastError();
 }
@@ -1451,10 +1515,10 @@ cudaError_t launch_adj_gather(const BatchDev& b, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template cudaError_t launch_keys<2>(const BatchDev&, cudaStream_t);
-template cudaError_t launch_keys<3>(const BatchDev&, cudaStream_t);
-template cudaError_t launch_sort<2>(const BatchDev&, cudaStream_t);
-template cudaError_t launch_sort<3>(const BatchDev&, cudaStream_t);
+template cudaError_t launch_keys<2>(const BatchDev&, cudaStream_t, const SelectPar*);
+template cudaError_t launch_keys<3>(const BatchDev&, cudaStream_t, const SelectPar*);
+template cudaError_t launch_sort<2>(const BatchDev&, cudaStream_t, const SelectPar*);
+template cudaError_t launch_sort<3>(const BatchDev&, cudaStream_t, const SelectPar*);
 template cudaError_t launch_p2g<2>(const BatchDev&, bool, cudaStream_t);
 template cudaError_t launch_p2g<3>(const BatchDev&, bool, cudaStream_t);
 template cudaError_t launch_g2p<2>(const BatchDev&, cudaStream_t);
@@ -1755,32 +1819,11 @@ __global__ void k_unpack(int dim, int N, int npad, const float4* planes, float* 
 // Device-side choice of this step's scene records: scene s of the launch uses
 // table[map[*ctr - base]] (map NULL: table[0]), with the batch offsets patched in; the
 // sinusoid controllers' actuation a_g(t_n) is evaluated here too.  Every step of a rollout is
-// then the same launch sequence, which CUDA graphs replay.
+// then the same launch sequence, which CUDA graphs replay.  (A single tiled scene makes this
+// selection inside the first kernel of its step instead: k_keys, k_scatter, k_scan_reduce.)
 __global__ void k_select(const SelectPar* __restrict__ sel, ScenePar* __restrict__ cur) {
   pdl_enter();
-  const SelectPar& q = sel[blockIdx.x];
-  const int n = *q.ctr;
-  const int idx = q.map ? q.map[n - q.base] : 0;
-  const int* src = reinterpret_cast<const int*>(q.table + idx);
-  int* dst = reinterpret_cast<int*>(cur + blockIdx.x);
-  constexpr int W = int(sizeof(ScenePar) / sizeof(int));
-  for (int i = threadIdx.x; i < W; i += blockDim.x) dst[i] = src[i];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    cur[blockIdx.x].tile_base = q.tile_base;
-    cur[blockIdx.x].pbase = q.pbase;
-  }
-  const float tt = float(n) * q.dt;
-  const int g = threadIdx.x;
-  if (g < q.G && q.ctrl_type == 0) {
-    q.act[g] = q.params[g] * sinf(6.283185307179586f * q.freq * tt);
-  } else if (g < q.G && q.ctrl_type == 1) {
-    const float w = 6.283185307179586f * q.freq * tt;
-    q.act[g] = q.params[g * 4] * sinf(w) + q.params[g * 4 + 1] * cosf(w) + q.params[g * 4 + 2] * sinf(2.0f * w) +
-               q.params[g * 4 + 3] * cosf(2.0f * w);
-  } else if (g < q.G && q.ctrl_type == 3) {
-    q.act[g] = (n >= 0 && n < q.ctrl_len) ? q.params[size_t(n) * q.G + g] : 0.0f;
-  }
+  select_publish(sel[blockIdx.x], cur + blockIdx.x);
 }
 
 cudaError_t launch_select(const SelectPar* sel, int n_scenes, ScenePar* cur, cudaStream_t s) {
