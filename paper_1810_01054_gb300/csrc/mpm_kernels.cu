@@ -257,7 +257,10 @@ __host__ __device__ __forceinline__ bool fused_scan(const BatchDev& b) { return 
 template <bool SEL>
 __global__ void k_scan_reduce(BatchDev b, const SelectPar* __restrict__ sel) {
   pdl_enter();
-  if (SEL && blockIdx.x == 0) select_publish(*sel, b.scenes);  // the step's selection (k_keys)
+  if (SEL && blockIdx.x == gridDim.x - 1) {  // an extra CTA makes the step's selection (k_scatter)
+    select_publish(*sel, b.scenes);
+    return;
+  }
   int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_PER_THREAD;
   uint32_t s = 0, c = 0;
 #pragma unroll
@@ -343,13 +346,17 @@ __global__ void k_scan_down(BatchDev b) {
 // SCAN_TILE) the tile scan is done here instead of by the scan kernels: every CTA scans the whole
 // histogram in shared memory (it is small), CTA 0 publishes tile_start, tile_slot, the active list
 // and n_active; the P2G that follows clears the per-step counters.
-// With SEL (a single scene, fused scan) CTA 0 also makes the step's selection (see k_keys); the
-// scatter itself reads only the record's step-invariant fields (keys, offsets, status), which it
-// takes from the phase's first record instead of the one being published.
+// With SEL (a single scene, fused scan) one extra CTA, launched after the scatter's own, makes the
+// step's selection (see k_keys) alongside them; the scatter reads only the record's step-invariant
+// fields (keys, offsets, status), which it takes from the phase's first record instead of the
+// one being published.
 template <int D, bool FUSED, bool SEL>
 __global__ void __launch_bounds__(256) k_scatter(BatchDev b, const SelectPar* __restrict__ sel) {
   pdl_enter();
-  if (SEL && blockIdx.x == 0) select_publish(*sel, b.scenes);
+  if (SEL && blockIdx.x == gridDim.x - 1) {
+    select_publish(*sel, b.scenes);
+    return;
+  }
   constexpr int PER = FUSED ? SCAN_TILE / 256 : 1;
   __shared__ uint32_t sstart[FUSED ? SCAN_TILE + 1 : 1];
   if constexpr (FUSED) {
@@ -1438,7 +1445,7 @@ cudaError_t launch_sort(const BatchDev& b, cudaStream_t s, const SelectPar* sel)
   if (fused_scan(b)) {  // scan inside the scatter; at least one CTA so the scan results are written
     const int nblk = b.total_particles > 0 ? (b.total_particles + 255) / 256 : 1;
     if (sel)
-      launch_pdl(k_scatter<D, true, true>, dim3(nblk), dim3(256), 0, s, b, sel);
+      launch_pdl(k_scatter<D, true, true>, dim3(nblk + 1), dim3(256), 0, s, b, sel);
     else
       launch_pdl(k_scatter<D, true, false>, dim3(nblk), dim3(256), 0, s, b, sel);
     count_launches(1);
@@ -1446,7 +1453,7 @@ cudaError_t launch_sort(const BatchDev& b, cudaStream_t s, const SelectPar* sel)
   }
   const int nblk = (b.total_tiles + SCAN_TILE - 1) / SCAN_TILE;
   if (sel)
-    launch_pdl(k_scan_reduce<true>, dim3(nblk), dim3(SCAN_THREADS), 0, s, b, sel);
+    launch_pdl(k_scan_reduce<true>, dim3(nblk + 1), dim3(SCAN_THREADS), 0, s, b, sel);
   else
     launch_pdl(k_scan_reduce<false>, dim3(nblk), dim3(SCAN_THREADS), 0, s, b, sel);
   launch_pdl(k_scan_top, dim3(1), dim3(SCAN_THREADS), 0, s, b, nblk);
