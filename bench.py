@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-material", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-replicas", action="store_true")
+    ap.add_argument("--no-budget-sweep", action="store_true")
     ap.add_argument("--ncu-fp64", action="store_true",
                     help="short run for profilers: the FP64 form on a 200k-particle 3D cluster (64^3 grid), "
                          "2 steps and their reverse pass")
@@ -387,6 +389,116 @@ def measure(args, spec, rank, world, dev, stream, ctx, *, e2e=True, plain=True):
             "N": N, "T": T, "k": k, "launch": launch}
 
 
+def measure_replicas(args, dev, stream, sizes=(1, 64, 1024, 4096)):
+    """The smallest workload (walker_square_2d: 1,024 particles, 100 steps, forward + reverse) as B
+    independent replicas advanced together by one batch, B in `sizes`: one such scene leaves the
+    GPU idle (launch and latency bound); a batch fills it.  Each request is a rollout with its
+    reverse pass (loss = mean final x_0); the timed span is admission to the last result (the
+    replicas' states are reset before it, untimed), L2 flushed before it."""
+    import torch
+    from paper_1810_01054_gb300 import mpm
+    from paper_1810_01054_gb300 import scenes as S
+    spec = S.walker_square_2d(0)
+    T, N = spec.n_steps, spec.n_particles
+    ctx = mpm.Context(dev.index, stream=stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    out = {}
+    for B in sizes:
+        scenes = [mpm.Scene(ctx, spec) for _ in range(B)]
+        batch = mpm.Batch(ctx, 2)
+
+        def reset():
+            for sc in scenes:
+                sc.set_state(spec.x0, spec.v0, spec.C0, spec.F0, step=0)
+
+        def run():
+            slots = [batch.admit(sc, T, True) for sc in scenes]
+            while not all(batch.poll(sl) for sl in slots):
+                batch.tick(16)
+            bad = [batch.status(sl) for sl in slots if batch.status(sl) != mpm.MPM_OK]
+            for sl in slots:
+                batch.release(sl)
+            if bad:
+                raise RuntimeError(f"replica requests failed: {bad[:4]}")
+
+        for _ in range(max(1, args.warmup)):
+            reset()
+            run()
+        ms = []
+        for _ in range(max(1, min(args.steps, 3))):
+            reset()
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            run()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms.append(e0.elapsed_time(e1))
+        batch.close()
+        for sc in scenes:
+            sc.close()
+        best = float(np.median(ms))
+        out[str(B)] = {"value": B * N * T / (best / 1e3), "ms": best}
+    ctx.close()
+    return {"workload": spec.name, "particles_per_replica": N, "sim_steps": T, "unit": UNIT,
+            "pass": "forward+reverse per replica, one batch", "by_replicas": out}
+
+
+def measure_budget_sweep(args, dev, stream, budgets_gib=(1, 4, 32)):
+    """Full-horizon gradient of the 1M-particle cluster (200 steps) under device-memory budgets for
+    the checkpoint store: the library keeps every state when they fit (k = 1), else every
+    ceil(sqrt(T))-th and recomputes the segments; a budget below that is refused (MPM_ERR_OOM)."""
+    import torch
+    from paper_1810_01054_gb300 import mpm
+    spec = workload("box_cluster_3d")
+    T, N, d = spec.n_steps, spec.n_particles, spec.dim
+    ctx = mpm.Context(dev.index, stream=stream)
+    sc = mpm.Scene(ctx, spec)
+    t = lambda a: torch.tensor(a, dtype=torch.float32, device=dev)
+    x0, v0, C0, F0 = t(spec.x0), t(spec.v0), t(spec.C0), t(spec.F0)
+    seed = torch.zeros((N, d), dtype=torch.float32, device=dev)
+    seed[:, 0] = 1.0 / N
+    outs = [torch.empty((N, d), device=dev), torch.empty((N, d), device=dev), torch.empty((N, d, d), device=dev),
+            torch.empty((N, d, d), device=dev), torch.empty((max(sc.n_params, 1),), device=dev)]
+    S = sc.info()["state_bytes"]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    res = {}
+    for gib in budgets_gib:
+        budget = gib << 30
+        k = 1 if T * S <= budget else int(np.ceil(np.sqrt(T)))
+        stored = (T + k - 1) // k + (k - 1)  # checkpoints + one segment's recompute buffers
+        rec = {"ckpt_interval": k, "stored_states": stored, "store_gb": stored * S / 1e9}
+
+        def one():
+            sc.set_state(x0, v0, C0, F0, step=0)
+            sc.rollout(T, 0, budget)
+            sc.backward(seed, out=outs)
+
+        try:
+            one()
+        except mpm.MPMError as e:
+            rec["status"] = e.status
+            res[f"{gib}GiB"] = rec
+            continue
+        ms = []
+        for _ in range(2):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            one()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms.append(e0.elapsed_time(e1))
+        rec["value"] = N * T / (min(ms) / 1e3)
+        rec["ms"] = min(ms)
+        res[f"{gib}GiB"] = rec
+    sc.close()
+    ctx.close()
+    return {"workload": spec.name, "particles": N, "sim_steps": T, "unit": UNIT, "by_budget": res}
+
+
 def measure_serving(dev, stream, n_requests=32, seed=4):
     """Serving mix (Poisson stream of rollout/gradient requests, 2D and 3D box clusters): first the
     saturation rate (all requests queued at once), then Poisson arrivals at 0.75x that rate;
@@ -577,6 +689,12 @@ def run_ours(args, rank, world, local_rank):
         large = {"workload": lspec.name, "particles": lr["N"], "sim_steps": lr["T"], "value": lr["value"],
                  "value_fwd": lr["value_fwd"], "unit": UNIT, "ms_per_step": lr["tot_ms"] / args.steps,
                  "roofline": lr["roofline"], "kernel_share_of_profiled_step": lr["share"]}
+    sweep = None
+    if rank == 0 and args.workload != "box_cluster_3d" and not args.no_large and not args.no_budget_sweep:
+        sweep = measure_budget_sweep(args, dev, stream)
+    replicas = None
+    if rank == 0 and not args.no_replicas:
+        replicas = measure_replicas(args, dev, stream)
     material = None
     if args.workload == "walker_2d" and not args.no_material:
         # the same workload with per-particle Young's modulus and mass and their gradients
@@ -609,7 +727,7 @@ def run_ours(args, rank, world, local_rank):
         "roofline": r["roofline"], "kernel_share_of_profiled_step": r["share"],
         "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": r["gpu_launches"], "clocks": r["clocks"],
         "plain_form": r["plain"], "large_scene": large, "material": material, "serving": serving,
-        "fp64": fp64,
+        "fp64": fp64, "large_scene_budgets": sweep, "small_scene_replicas": replicas,
     }
     print(json.dumps(line), flush=True)
 

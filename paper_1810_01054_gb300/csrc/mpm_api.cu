@@ -367,6 +367,10 @@ mpm_status refresh_records(mpm_scene* s) {
 }
 
 mpm_status set_counter(mpm_scene* s, int* dctr, int value) {
+  if (s->ctr_sink) {
+    s->ctr_sink->emplace_back(dctr, value);
+    return MPM_OK;
+  }
   CK(launch_set_int(dctr, value, s->ctx->stream));
   return MPM_OK;
 }
@@ -450,28 +454,32 @@ mpm_status prepare_rollout(mpm_scene* s, int T, int k, size_t budget) {
 // Reverse-pass set-up: adjoint of the final state from the seeds, controller adjoint zeroed, the
 // record table of every segment's recompute and reverse steps, their maps, the reverse counter.
 mpm_status prepare_backward(mpm_scene* s, const float* gxT, const float* gvT, const float* gCT, const float* gFT,
-                            int mem_space) {
+                            int mem_space, bool mean_x0_seed) {
   cudaStream_t st = s->ctx->stream;
   const int dim = s->dim, N = s->N, T = s->roll_T, k = s->roll_k, nseg = s->roll_nseg, n0 = s->roll_start;
   const size_t xb = sizeof(float) * size_t(N) * dim, mb = xb * dim;
-  CKS(ensure_scratch(s, 2 * xb + 2 * mb + 256));
-  const void *a, *bv, *c, *f;
-  CKS(stage(s, gxT, xb, mem_space, 0, &a));
-  CKS(stage(s, gvT, xb, mem_space, xb, &bv));
-  CKS(stage(s, gCT, mb, mem_space, 2 * xb, &c));
-  CKS(stage(s, gFT, mb, mem_space, 2 * xb + mb, &f));
-  // adjoint of the final state; a missing F seed is 0 (the packer's default is the identity)
-  char* sc = reinterpret_cast<char*>(s->scratch);
-  if (!f && N > 0) {
-    CK(cudaMemsetAsync(sc + 2 * xb + mb, 0, mb, st));
-    f = sc + 2 * xb + mb;
+  if (mean_x0_seed) {  // dL/dx_T = e_0 / N written on the device
+    CK(launch_seed_mean_x0(dim, N, s->npad, s->adj[0], st));
+  } else {
+    CKS(ensure_scratch(s, 2 * xb + 2 * mb + 256));
+    const void *a, *bv, *c, *f;
+    CKS(stage(s, gxT, xb, mem_space, 0, &a));
+    CKS(stage(s, gvT, xb, mem_space, xb, &bv));
+    CKS(stage(s, gCT, mb, mem_space, 2 * xb, &c));
+    CKS(stage(s, gFT, mb, mem_space, 2 * xb + mb, &f));
+    // adjoint of the final state; a missing F seed is 0 (the packer's default is the identity)
+    char* sc = reinterpret_cast<char*>(s->scratch);
+    if (!f && N > 0) {
+      CK(cudaMemsetAsync(sc + 2 * xb + mb, 0, mb, st));
+      f = sc + 2 * xb + mb;
+    }
+    if (!a && N > 0) {
+      CK(cudaMemsetAsync(sc, 0, xb, st));
+      a = sc;
+    }
+    CK(launch_pack(dim, N, s->npad, (const float*)a, (const float*)bv, (const float*)c, (const float*)f, s->adj[0],
+                   s->d_status, st));
   }
-  if (!a && N > 0) {
-    CK(cudaMemsetAsync(sc, 0, xb, st));
-    a = sc;
-  }
-  CK(launch_pack(dim, N, s->npad, (const float*)a, (const float*)bv, (const float*)c, (const float*)f, s->adj[0],
-                 s->d_status, st));
   CK(cudaMemsetAsync(s->ctrl.gparams, 0, sizeof(float) * std::max(1, s->nparams), st));
   if (s->hp.gmat && N > 0) CK(cudaMemsetAsync(s->hp.gmat, 0, sizeof(float2) * size_t(N), st));
   // table 2: per segment the recompute records F_{sg,j} (state j -> j+1) and the reverse records
@@ -510,11 +518,15 @@ mpm_status prepare_backward(mpm_scene* s, const float* gxT, const float* gvT, co
 
 // dL/dx_T = e_0 / N: the seed of the loss "mean final x_0" used by batched gradient requests.
 mpm_status seed_mean_x0(mpm_scene* s) {
-  const int N = s->N, dim = s->dim;
-  std::vector<float> h(size_t(N) * dim, 0.0f);
-  for (int p = 0; p < N; ++p) h[size_t(p) * dim] = 1.0f / float(N);
-  return prepare_backward(s, N > 0 ? h.data() : nullptr, nullptr, nullptr, nullptr, 0);
+  return prepare_backward(s, nullptr, nullptr, nullptr, nullptr, 0, true);
 }
+
+void finish_backward_quiet(mpm_scene* s) {
+  s->have_grad = true;
+  set_counter(s, s->d_step, s->step);
+}
+
+mpm_status restore_keys(mpm_scene* s) { return enqueue_keys(s, PH_STEP, s->ctx->stream); }
 
 // Reads the result of the finished reverse pass (adjoint of the rollout's first state and of the
 // controller parameters) and restores the bin keys and forward counter of the current state.

@@ -92,6 +92,12 @@ struct mpm_batch {
   float4 *partial = nullptr, *partial_b = nullptr;  // node blocks, shared by the two sub-batches
   int cap_blocks = 0;
   bool dirty = true;
+  // per-tick bookkeeping: counter writes of the scenes changing phase (one launch), the slots whose
+  // request finished (one status gather), device array of the gathered status words
+  std::vector<std::pair<int*, int>> pend_ctr;
+  std::vector<int> finishing;
+  int* d_status = nullptr;
+  int status_cap = 0;
 };
 
 namespace {
@@ -261,40 +267,100 @@ mpm_status begin_segment(mpm_batch* B, Slot& sl) {
   return MPM_OK;
 }
 
-// Slot bookkeeping after one batched step.
+// Writes the counters the scenes' phase changes asked for (set_counter through the sink), in
+// order, with as few launches as the list needs.
+mpm_status flush_counters(mpm_batch* B) {
+  cudaStream_t st = B->ctx->stream;
+  for (size_t i0 = 0; i0 < B->pend_ctr.size(); i0 += INT_LIST_MAX) {
+    IntPtrList l;
+    l.n = int(std::min<size_t>(INT_LIST_MAX, B->pend_ctr.size() - i0));
+    for (int i = 0; i < l.n; ++i) {
+      l.ptr[i] = B->pend_ctr[i0 + i].first;
+      l.val[i] = B->pend_ctr[i0 + i].second;
+    }
+    CK(launch_set_int_list(l, st));
+  }
+  B->pend_ctr.clear();
+  return MPM_OK;
+}
+
+// Finished requests: the reverse passes' scenes get the bin keys of their current state back, then
+// one gather and one copy read every finished scene's status word.
+mpm_status finish_requests(mpm_batch* B) {
+  if (B->finishing.empty()) return MPM_OK;
+  cudaStream_t st = B->ctx->stream;
+  for (int idx : B->finishing)
+    if (B->slots[idx].want_grad) CKS(restore_keys(B->slots[idx].s));
+  const int n = int(B->finishing.size());
+  if (n > B->status_cap) {
+    CK(cudaStreamSynchronize(st));
+    dfree(B->d_status);
+    B->status_cap = 0;
+    CK(cudaMalloc(&B->d_status, sizeof(int) * n));
+    B->status_cap = n;
+  }
+  for (int i0 = 0; i0 < n; i0 += INT_LIST_MAX) {
+    IntPtrList l;
+    l.n = std::min(INT_LIST_MAX, n - i0);
+    for (int i = 0; i < l.n; ++i) l.ptr[i] = B->slots[B->finishing[i0 + i]].s->d_status;
+    CK(launch_gather_ints(l, B->d_status + i0, st));
+  }
+  std::vector<int> h(n);
+  CK(cudaMemcpyAsync(h.data(), B->d_status, sizeof(int) * n, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int i = 0; i < n; ++i) {
+    Slot& sl = B->slots[B->finishing[i]];
+    sl.status = mpm_status(h[i]);
+    sl.state = S_DONE;
+  }
+  B->finishing.clear();
+  B->dirty = true;
+  return MPM_OK;
+}
+
+// Slot bookkeeping after one batched step.  Counter writes are collected (one launch for all
+// scenes), finished requests are closed together.
 mpm_status advance(mpm_batch* B) {
-  for (Slot& sl : B->slots) {
+  for (int idx = 0; idx < int(B->slots.size()); ++idx) {
+    Slot& sl = B->slots[idx];
+    if (sl.state != S_FWD && sl.state != S_RCM && sl.state != S_REV) continue;
+    mpm_scene* s = sl.s;
+    s->ctr_sink = &B->pend_ctr;
+    mpm_status st = MPM_OK;
     if (sl.state == S_FWD) {
-      if (++sl.done_steps < sl.T) continue;
-      mpm_scene* s = sl.s;
-      s->step += sl.T;
-      s->have_rollout = true;
-      if (sl.want_grad) {
-        CKS(seed_mean_x0(s));
-        sl.seg = s->roll_nseg - 1;
-        CKS(begin_segment(B, sl));
-      } else {
-        sl.state = S_DONE;
-        B->dirty = true;
+      if (++sl.done_steps >= sl.T) {
+        s->step += sl.T;
+        s->have_rollout = true;
+        if (sl.want_grad) {
+          st = seed_mean_x0(s);
+          sl.seg = s->roll_nseg - 1;
+          if (st == MPM_OK) st = begin_segment(B, sl);
+        } else {
+          sl.state = S_DONE;  // status read in finish_requests
+          B->finishing.push_back(idx);
+        }
       }
     } else if (sl.state == S_RCM) {
-      if (--sl.left > 0) continue;
-      const int L = std::min(sl.s->roll_k, sl.s->roll_T - sl.seg * sl.s->roll_k);
-      sl.state = S_REV;
-      sl.left = L;
-      B->dirty = true;
-    } else if (sl.state == S_REV) {
-      if (--sl.left > 0) continue;
-      if (--sl.seg >= 0) {
-        CKS(begin_segment(B, sl));
-      } else {
-        sl.status = finish_backward(sl.s, nullptr, nullptr, nullptr, nullptr, nullptr, 0);
-        sl.state = S_DONE;
+      if (--sl.left <= 0) {
+        const int L = std::min(s->roll_k, s->roll_T - sl.seg * s->roll_k);
+        sl.state = S_REV;
+        sl.left = L;
         B->dirty = true;
       }
+    } else if (--sl.left <= 0) {  // S_REV
+      if (--sl.seg >= 0) {
+        st = begin_segment(B, sl);
+      } else {
+        finish_backward_quiet(s);
+        sl.state = S_DONE;
+        B->finishing.push_back(idx);
+      }
     }
+    s->ctr_sink = nullptr;
+    if (st != MPM_OK) return st;
   }
-  return MPM_OK;
+  CKS(flush_counters(B));
+  return finish_requests(B);
 }
 
 size_t request_bytes(const mpm_scene* s, int T) {
@@ -328,6 +394,7 @@ mpm_status mpm_batch_destroy(mpm_batch* B) {
   free_sub(B->rev);
   dfree(B->partial);
   dfree(B->partial_b);
+  dfree(B->d_status);
   B->ctx->live.fetch_sub(1);
   delete B;
   return MPM_OK;

@@ -195,6 +195,19 @@ cudaError_t ctrl_scatter_x(const ScenePar& sp, const ScenePar* dsp, const CtrlPa
 
 // Copies every scene's record for the current step into cur[] (one block per scene).
 cudaError_t launch_select(const SelectPar* sel, int n_scenes, ScenePar* cur, cudaStream_t s);
+// Adjoint planes of the seed dL/dx_T = e_0 / N (the batched gradient requests' loss).
+cudaError_t launch_seed_mean_x0(int dim, int N, int npad, float4* planes, cudaStream_t s);
+// A list of device ints passed by value (kernel parameters hold up to INT_LIST_MAX entries).
+constexpr int INT_LIST_MAX = 1024;
+struct IntPtrList {
+  int n;
+  int* ptr[INT_LIST_MAX];
+  int val[INT_LIST_MAX];
+};
+// *ptr[i] = val[i] in list order.
+cudaError_t launch_set_int_list(const IntPtrList& l, cudaStream_t s);
+// out[i] = *ptr[i].
+cudaError_t launch_gather_ints(const IntPtrList& l, int* out, cudaStream_t s);
 // *p = v on the stream (kernel argument, so no host buffer outlives the call).
 cudaError_t launch_set_int(int* p, int v, cudaStream_t s);
 

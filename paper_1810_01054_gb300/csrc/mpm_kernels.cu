@@ -1840,6 +1840,49 @@ cudaError_t launch_select(const SelectPar* sel, int n_scenes, ScenePar* cur, cud
   return cudaGetLastError();
 }
 
+// Adjoint planes of the seed dL/dx_T = e_0 / N (loss = mean final x_0), zero elsewhere and in the
+// padding: what k_pack writes for that seed with zero v, C and F seeds.
+__global__ void k_seed_mean_x0(int dim, int N, int npad, float4* planes) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npad) return;
+  const int S = dim == 2 ? 12 : 24;
+  const float s0 = p < N ? 1.0f / float(N) : 0.0f;
+  for (int j = 0; j < S / 4; ++j) planes[size_t(j) * npad + p] = make_float4(j == 0 ? s0 : 0.0f, 0.0f, 0.0f, 0.0f);
+}
+
+cudaError_t launch_seed_mean_x0(int dim, int N, int npad, float4* planes, cudaStream_t s) {
+  if (npad == 0) return cudaSuccess;
+  k_seed_mean_x0<<<(npad + 255) / 256, 256, 0, s>>>(dim, N, npad, planes);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// Writes of many counters in one launch, in list order (one thread: the list may name a counter
+// twice), and the gather of many status words into one array.
+__global__ void k_set_int_list(IntPtrList l) {
+  if (threadIdx.x == 0)
+    for (int i = 0; i < l.n; ++i) *l.ptr[i] = l.val[i];
+}
+
+__global__ void k_gather_ints(IntPtrList l, int* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < l.n) out[i] = *l.ptr[i];
+}
+
+cudaError_t launch_set_int_list(const IntPtrList& l, cudaStream_t s) {
+  if (l.n <= 0) return cudaSuccess;
+  k_set_int_list<<<1, 32, 0, s>>>(l);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_ints(const IntPtrList& l, int* out, cudaStream_t s) {
+  if (l.n <= 0) return cudaSuccess;
+  k_gather_ints<<<(l.n + 255) / 256, 256, 0, s>>>(l, out);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 __global__ void k_set_int(int* p, int v) { *p = v; }
 
 cudaError_t launch_set_int(int* p, int v, cudaStream_t s) {

@@ -5,6 +5,7 @@
 #include <atomic>
 #include <cstring>
 #include <mutex>
+#include <utility>
 #include <vector>
 
 #include "../../include/mpm.h"
@@ -100,6 +101,9 @@ struct mpm_scene {
   size_t scratch_bytes = 0;
   TuneState tune;
   int batch_refs = 0;  // batch slots holding the scene (admitted, not yet released)
+  // while set, set_counter appends (counter, value) here instead of launching a write: the batch
+  // scheduler writes the counters of all its scenes with one launch
+  std::vector<std::pair<int*, int>>* ctr_sink = nullptr;
 };
 
 
@@ -107,10 +111,17 @@ namespace gbmpm {
 // Helpers the batch scheduler shares with the single-scene entry points (mpm_api.cu).
 mpm_status prepare_rollout(mpm_scene* s, int T, int k, size_t budget);
 mpm_status prepare_backward(mpm_scene* s, const float* gxT, const float* gvT, const float* gCT, const float* gFT,
-                            int mem_space);
+                            int mem_space, bool mean_x0_seed = false);
 mpm_status seed_mean_x0(mpm_scene* s);
 mpm_status finish_backward(mpm_scene* s, float* gx0, float* gv0, float* gC0, float* gF0, float* gctrl,
                            int mem_space);
+// The part of finish_backward a batch needs when nothing is read out: the gradient is marked
+// available and the forward counter restored (through the counter sink); the caller then restores
+// the bin keys (restore_keys, after the counter is written) and reads the status.
+void finish_backward_quiet(mpm_scene* s);
+// Bin keys and tile histogram of the scene's current state (after a reverse pass left those of
+// the rollout's first state).
+mpm_status restore_keys(mpm_scene* s);
 mpm_status set_counter(mpm_scene* s, int* dctr, int value);
 mpm_status read_status(mpm_scene* s);
 mpm_status scene_sync_status(mpm_scene* s);
