@@ -164,3 +164,30 @@ def test_fp64_errors_are_reported(M, ctx):
         sc.backward()  # no rollout yet
     assert e.value.status == -7
     sc.close()
+
+
+def test_fp64_empty_scene_and_table_replacement(M, ctx):
+    empty = S.blob(2, 16, 0, 64, radius_cells=1.0)
+    sc = M.Scene64(ctx, empty, act=np.zeros((0, empty.n_groups)))
+    sc.rollout(5)
+    assert all(a.size == 0 for a in sc.get_state())
+    assert all(a.size == 0 for a in sc.backward()[:4])
+    sc.close()
+    # a new actuation table replaces the old one: the rollout and dL/dU follow the oracle
+    spec, T = _cases()["2d_table_walls"]
+    U2 = 0.5 * np.asarray(spec.ctrl_params).reshape(spec.ctrl_hidden, spec.n_groups)[:30]
+    sc = M.Scene64(ctx, spec)
+    sc.set_actuation(U2)
+    sc.rollout(T)
+    N, d = spec.n_particles, spec.dim
+    w = np.random.default_rng(9).normal(size=(N, d)) / N
+    gU = sc.backward(w)[4]
+    x = sc.get_state()[0]
+    sc.close()
+    ospec = spec.copy(ctrl_params=U2.ravel(), ctrl_hidden=U2.shape[0])
+    osc = O.Scene(ospec)
+    traj = osc.rollout(T)
+    ogp = osc.backward(traj, (w, None, None, None))[4]
+    _close(x, traj[0][T], "x after a new table", scale=1.0)
+    assert gU.shape == U2.shape
+    _close(gU.ravel(), np.asarray(ogp).ravel(), "dL/dU of the new table")
