@@ -213,10 +213,11 @@ __global__ void __launch_bounds__(F64_THREADS) k64_grid(Par64 p, int n_nodes) {
   double* gp = p.grid + size_t(nl) * 4;
   const double m = gp[3];
   double vraw[D], v[D];
+  const double rm = m > 0.0 ? 1.0 / m : 0.0;  // one division per node (FP64 divides are long chains)
   if (m > 0.0) {
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-      vraw[a] = gp[a] / m;
+      vraw[a] = gp[a] * rm;
       v[a] = vraw[a] + p.dt * p.gravity[a];
     }
     bc_apply<D>(node, p.n, p.bc, v);
@@ -239,10 +240,10 @@ __global__ void __launch_bounds__(F64_THREADS) k64_grid(Par64 p, int n_nodes) {
       double dot = 0.0;
 #pragma unroll
       for (int a = 0; a < D; ++a) {
-        pb[a] = g[a] / m;
+        pb[a] = g[a] * rm;
         dot += vraw[a] * g[a];
       }
-      mb = -dot / m;
+      mb = -dot * rm;
     } else {
 #pragma unroll
       for (int a = 0; a < D; ++a) pb[a] = 0.0;
@@ -428,8 +429,7 @@ Shape shape_for(int n, int sms) {
 }
 
 template <int D>
-cudaError_t launch_step64(const Par64& p, int n_nodes, mpm_ctx* c) {
-  cudaStream_t s = c->stream;
+cudaError_t launch_step64(const Par64& p, int n_nodes, mpm_ctx* c, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(p.grid, 0, sizeof(double) * 4 * size_t(n_nodes), s);
   if (e != cudaSuccess) return e;
   if (p.N > 0) {
@@ -452,8 +452,7 @@ cudaError_t launch_step64(const Par64& p, int n_nodes, mpm_ctx* c) {
 }
 
 template <int D>
-cudaError_t launch_reverse64(const Par64& p, int n_nodes, mpm_ctx* c) {
-  cudaStream_t s = c->stream;
+cudaError_t launch_reverse64(const Par64& p, int n_nodes, mpm_ctx* c, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(p.grid, 0, sizeof(double) * 4 * size_t(n_nodes), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(p.grid_b, 0, sizeof(double) * 4 * size_t(n_nodes), s);
   if (e != cudaSuccess) return e;
@@ -494,6 +493,13 @@ struct mpm_scene64 {
   int T = -1;                  // steps of the last rollout (-1: none)
   size_t hist_cap = 0;         // states hist can hold
   std::vector<void*> allocs;
+  // whole rollouts and reverse passes replayed as CUDA graphs (one launch instead of ~4 per step);
+  // captured for a rollout length T and dropped when a buffer they name is reallocated
+  struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    int T = -1;
+    long long kernels = 0;
+  } gfwd, grev;
 };
 
 namespace {
@@ -580,6 +586,80 @@ const double* step_act(const mpm_scene64* s, int t) {
   return (s->G > 0 && t < s->L) ? s->act + size_t(t) * s->G : nullptr;
 }
 
+void drop_graphs(mpm_scene64* s) {
+  for (mpm_scene64::Graph* g : {&s->gfwd, &s->grev}) {
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    *g = mpm_scene64::Graph();
+  }
+}
+
+// The T steps of a rollout from the initial state (status cleared first).
+mpm_status enqueue_rollout(mpm_scene64* s, int T, cudaStream_t str) {
+  const size_t stride = size_t(s->S) * std::max(1, s->N);
+  CK64(cudaMemsetAsync(s->hp.status, 0, sizeof(int), str));
+  CK64(cudaMemcpyAsync(s->hist, s->init, sizeof(double) * stride, cudaMemcpyDeviceToDevice, str));
+  for (int t = 0; t < T; ++t) {
+    Par64 p = s->hp;
+    p.st = s->hist + size_t(t) * stride;
+    p.st_out = s->hist + size_t(t + 1) * stride;
+    p.act = step_act(s, t);
+    CK64(s->dim == 2 ? gbmpm::launch_step64<2>(p, s->n_nodes, s->ctx, str)
+                     : gbmpm::launch_step64<3>(p, s->n_nodes, s->ctx, str));
+  }
+  return MPM_OK;
+}
+
+// The reverse steps T-1 .. 0 (adjoint of state T in adj[0]; that of state 0 ends in adj[T & 1]).
+mpm_status enqueue_reverse(mpm_scene64* s, int T, cudaStream_t str) {
+  const size_t stride = size_t(s->S) * std::max(1, s->N);
+  if (size_t(s->L) * s->G > 0) CK64(cudaMemsetAsync(s->g_act, 0, sizeof(double) * size_t(s->L) * s->G, str));
+  int cur = 0;
+  for (int t = T - 1; t >= 0; --t) {
+    Par64 p = s->hp;
+    p.st = s->hist + size_t(t) * stride;
+    p.adj_in = s->adj[cur];
+    p.adj_out = s->adj[cur ^ 1];
+    p.act = step_act(s, t);
+    p.g_act = p.act ? s->g_act + size_t(t) * s->G : nullptr;
+    CK64(s->dim == 2 ? gbmpm::launch_reverse64<2>(p, s->n_nodes, s->ctx, str)
+                     : gbmpm::launch_reverse64<3>(p, s->n_nodes, s->ctx, str));
+    cur ^= 1;
+  }
+  return MPM_OK;
+}
+
+// Runs the rollout (reverse = false) or reverse pass of length T on the context stream: directly
+// while launch timing is on, else as a graph, captured on first use for this T.
+mpm_status run64(mpm_scene64* s, bool reverse, int T) {
+  mpm_ctx* c = s->ctx;
+  if (c->prof_mask) return reverse ? enqueue_reverse(s, T, c->stream) : enqueue_rollout(s, T, c->stream);
+  mpm_scene64::Graph& g = reverse ? s->grev : s->gfwd;
+  if (!g.exec || g.T != T) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g = mpm_scene64::Graph();
+    long long tally = 0;
+    CK64(cudaStreamBeginCapture(c->capture, cudaStreamCaptureModeThreadLocal));
+    gbmpm::capture_tally(&tally);
+    mpm_status st = reverse ? enqueue_reverse(s, T, c->capture) : enqueue_rollout(s, T, c->capture);
+    gbmpm::capture_tally(nullptr);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->capture, &graph);
+    if (st != MPM_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    CK64(e);
+    e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK64(e);
+    g.T = T;
+    g.kernels = tally;
+  }
+  CK64(cudaGraphLaunch(g.exec, c->stream));
+  gbmpm::count_launches(int(g.kernels));
+  return MPM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -588,6 +668,7 @@ mpm_status mpm64_destroy(mpm_scene64* s) {
   if (!s) return MPM_ERR_ARG;
   cudaSetDevice(s->ctx->device);
   cudaStreamSynchronize(s->ctx->stream);
+  drop_graphs(s);
   for (void* p : s->allocs) cudaFree(p);
   if (s->hist) cudaFree(s->hist);
   s->ctx->live.fetch_sub(1);
@@ -710,6 +791,7 @@ mpm_status mpm64_set_actuation(mpm_scene64* s, const double* U, int L) {
   if (n > 0 && !finite_all(U, n)) return MPM_ERR_ARG;
   CK64(cudaSetDevice(s->ctx->device));
   CK64(cudaStreamSynchronize(s->ctx->stream));
+  drop_graphs(s);  // they name the old table buffers
   for (double* q : {s->act, s->g_act}) {
     if (!q) continue;
     s->allocs.erase(std::find(s->allocs.begin(), s->allocs.end(), static_cast<void*>(q)));
@@ -735,6 +817,7 @@ mpm_status mpm64_rollout(mpm_scene64* s, int T) {
   const size_t state = sizeof(double) * size_t(s->S) * std::max(1, s->N);
   if (size_t(T) + 1 > s->hist_cap) {
     CK64(cudaStreamSynchronize(s->ctx->stream));
+    drop_graphs(s);  // they name the old history buffer
     if (s->hist) cudaFree(s->hist);
     s->hist = nullptr;
     s->hist_cap = 0;
@@ -744,17 +827,8 @@ mpm_status mpm64_rollout(mpm_scene64* s, int T) {
     s->hist = static_cast<double*>(q);
     s->hist_cap = size_t(T) + 1;
   }
-  cudaStream_t str = s->ctx->stream;
-  CK64(cudaMemsetAsync(s->hp.status, 0, sizeof(int), str));
-  CK64(cudaMemcpyAsync(s->hist, s->init, state, cudaMemcpyDeviceToDevice, str));
-  const size_t stride = size_t(s->S) * std::max(1, s->N);
-  for (int t = 0; t < T; ++t) {
-    Par64 p = s->hp;
-    p.st = s->hist + size_t(t) * stride;
-    p.st_out = s->hist + size_t(t + 1) * stride;
-    p.act = step_act(s, t);
-    CK64(s->dim == 2 ? gbmpm::launch_step64<2>(p, s->n_nodes, s->ctx) : gbmpm::launch_step64<3>(p, s->n_nodes, s->ctx));
-  }
+  mpm_status st = run64(s, false, T);
+  if (st != MPM_OK) return st;
   s->T = T;
   return MPM_OK;
 }
@@ -783,22 +857,11 @@ mpm_status mpm64_backward(mpm_scene64* s, const double* gx_T, const double* gv_T
   st = upload_state(s, s->adj[0], gx_T ? gx_T : zx.data(), gv_T, gC_T, gF_T ? gF_T : zF.data());
   if (st != MPM_OK) return st;
   cudaStream_t str = s->ctx->stream;
-  if (size_t(s->L) * s->G > 0) CK64(cudaMemsetAsync(s->g_act, 0, sizeof(double) * size_t(s->L) * s->G, str));
-  const size_t stride = size_t(s->S) * std::max(1, N);
-  int cur = 0;
-  for (int t = s->T - 1; t >= 0; --t) {
-    Par64 p = s->hp;
-    p.st = s->hist + size_t(t) * stride;
-    p.adj_in = s->adj[cur];
-    p.adj_out = s->adj[cur ^ 1];
-    p.act = step_act(s, t);
-    p.g_act = p.act ? s->g_act + size_t(t) * s->G : nullptr;
-    CK64(D == 2 ? gbmpm::launch_reverse64<2>(p, s->n_nodes, s->ctx) : gbmpm::launch_reverse64<3>(p, s->n_nodes, s->ctx));
-    cur ^= 1;
-  }
+  st = run64(s, true, s->T);
+  if (st != MPM_OK) return st;
   st = read_status64(s);
   if (st != MPM_OK) return st;
-  st = download_state(s, s->adj[cur], gx0, gv0, gC0, gF0);
+  st = download_state(s, s->adj[s->T & 1], gx0, gv0, gC0, gF0);
   if (st != MPM_OK) return st;
   const size_t n = size_t(s->L) * s->G;
   if (g_act && n > 0) {
