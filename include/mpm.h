@@ -290,16 +290,18 @@ mpm_status mpm_launch_count(long long* count);
 
 /* Launch-shape autotuning (no counterpart in the paper, whose kernels were launched with fixed
  * shapes on its own GPU).  The four tile kernels -- P2G, G2P, the adjoint scatter and the
- * adjoint gather -- run as persistent grids; how many CTAs per SM each gets (and, for G2P, 128 or
- * 256 threads per CTA) is chosen per workload.  Under MPM_TUNE_AUTO (the default) a scene looks
+ * adjoint gather -- run as persistent grids; how many CTAs per SM each gets (and, for G2P and in 2D
+ * for P2G and the adjoint scatter, 128 or 256 threads per CTA) is chosen per workload.  Under MPM_TUNE_AUTO (the default) a scene looks
  * its workload key -- dimension, log2 buckets of its particle and grid-tile counts, SM count -- up
  * in a process-wide cache; on a miss its next steps try every candidate shape of each kernel in
  * turn (two timed launches each, CUDA events, launched directly instead of from graphs), keep
  * the fastest and store it in the cache.  Every tile is processed whole by one CTA, so results
- * are bitwise the same under every shape and the trial steps are ordinary steps.  Batches use
- * the cache entry of their composition's key when there is one, the default shape (4 CTAs of
- * 256 threads per SM) otherwise.  MPM_TUNE_FORCE re-tunes ignoring the cache; MPM_TUNE_OFF uses
- * the default shapes. */
+ * are bitwise the same under every shape and the trial steps are ordinary steps.  A batch keys
+ * each of its two compositions (scenes in forward steps, scenes in reverse steps) the same way:
+ * it takes the cache entry when there is one, else its own steps try the candidates of the kernels
+ * that composition runs (the key's entry is complete, and saved, once both halves are tuned).
+ * MPM_TUNE_FORCE re-tunes ignoring the cache; MPM_TUNE_OFF uses the default shapes (4 CTAs of
+ * 256 threads per SM). */
 enum { MPM_TUNE_OFF = 0, MPM_TUNE_AUTO = 1, MPM_TUNE_FORCE = 2 };
 /* Tile kernels, for mpm_scene_launch and the cache arrays below (in this order). */
 enum { MPM_TK_P2G = 0, MPM_TK_G2P = 1, MPM_TK_P2G_ADJ = 2, MPM_TK_ADJ_GATHER = 3, MPM_TK_COUNT = 4 };

@@ -216,12 +216,12 @@ mpm_status enqueue_forward(mpm_scene* s, int ph, cudaStream_t st) {
   }
   {
     ProfScope p(c, st, MPM_K_P2G);
-    TuneScope t(s, TK_P2G, st);
+    TuneScope t(s->tune, TK_P2G, st);
     CK(two ? launch_p2g<2>(s->b, false, st) : launch_p2g<3>(s->b, false, st));
   }
   {
     ProfScope p(c, st, MPM_K_G2P);
-    TuneScope t(s, TK_G2P, st);
+    TuneScope t(s->tune, TK_G2P, st);
     CK(two ? launch_g2p<2>(s->b, st) : launch_g2p<3>(s->b, st));
   }
   return MPM_OK;
@@ -252,12 +252,12 @@ mpm_status enqueue_reverse(mpm_scene* s, cudaStream_t st) {
     }
     {
       ProfScope p(c, st, MPM_K_P2G_ADJ);
-      TuneScope t(s, TK_P2G_ADJ, st);
+      TuneScope t(s->tune, TK_P2G_ADJ, st);
       CK(two ? launch_p2g<2>(s->b, true, st) : launch_p2g<3>(s->b, true, st));
     }
     {
       ProfScope p(c, st, MPM_K_ADJ_GATHER);
-      TuneScope t(s, TK_ADJ_GATHER, st);
+      TuneScope t(s->tune, TK_ADJ_GATHER, st);
       CK(two ? launch_adj_gather<2>(s->b, st) : launch_adj_gather<3>(s->b, st));
     }
   }

@@ -42,6 +42,9 @@ struct SubBatch {
   int* pbase = nullptr;
   int cap_scenes = 0, cap_tiles = 0, cap_particles = 0;
   bool need_keys = true;  // composition changed: bin keys and histogram from the selected states
+  // launch shapes: the cache entry of the composition's key, else trials during its steps
+  TuneState tune;
+  long long key_particles = -1, key_tiles = -1;
 };
 
 #define CK(expr)                                                                   \
@@ -62,6 +65,8 @@ void dfree(T*& p) {
 }
 
 void free_sub(SubBatch& sb) {
+  batch_tune_release(sb.tune);
+  sb.key_particles = sb.key_tiles = -1;
   dfree(sb.dsel);
   dfree(sb.cur);
   dfree(sb.dctrl);
@@ -185,8 +190,16 @@ mpm_status compose(mpm_batch* B, SubBatch& sb) {
   sb.b.scene_pbase = sb.pbase;
   sb.b.total_particles = particles;
   sb.b.total_tiles = tiles;
-  default_launch(sb.b, B->ctx->sm_count);
-  tune_apply_cached(sb.b, B->dim);
+  // a new workload key takes its shapes anew; an empty composition keeps the last key's shapes
+  // and trials (a lockstep batch alternates each half between its members and nothing)
+  if (!sb.members.empty() && (particles != sb.key_particles || tiles != sb.key_tiles)) {
+    default_launch(sb.b, B->ctx->sm_count);
+    const unsigned kernels = &sb == &B->fwd ? (1u << TK_P2G) | (1u << TK_G2P)
+                                            : (1u << TK_P2G_ADJ) | (1u << TK_ADJ_GATHER);
+    CKS(batch_tune_init(sb.tune, sb.b, B->dim, kernels));
+    sb.key_particles = particles;
+    sb.key_tiles = tiles;
+  }
   sb.b.has_material = 0;
   for (int m : sb.members) sb.b.has_material |= B->slots[m].s->hp.gmat ? 1 : 0;
   sb.need_keys = true;
@@ -223,9 +236,16 @@ mpm_status forward_step(mpm_batch* B) {
     sb.need_keys = false;
   }
   CK(launch_sort<D>(sb.b, st));
-  CK(launch_p2g<D>(sb.b, false, st));
-  CK(launch_g2p<D>(sb.b, st));  // advances every member's forward counter, bins state n+1
-  return MPM_OK;
+  batch_tune_begin(sb.tune, sb.b, D);
+  {
+    TuneScope ts(sb.tune, TK_P2G, st);
+    CK(launch_p2g<D>(sb.b, false, st));
+  }
+  {
+    TuneScope ts(sb.tune, TK_G2P, st);
+    CK(launch_g2p<D>(sb.b, st));  // advances every member's forward counter, bins state n+1
+  }
+  return batch_tune_end(sb.tune, sb.b, D);
 }
 
 template <int D>
@@ -241,8 +261,16 @@ mpm_status reverse_step(mpm_batch* B) {
     if (ctrl_reads_state(s->ctrl)) CK(ctrl_step_forward(s->hp, sb.cur + m, s->ctrl, st));
   }
   CK(launch_sort<D>(sb.b, st));
-  CK(launch_p2g<D>(sb.b, true, st));
-  CK(launch_adj_gather<D>(sb.b, st));
+  batch_tune_begin(sb.tune, sb.b, D);
+  {
+    TuneScope ts(sb.tune, TK_P2G_ADJ, st);
+    CK(launch_p2g<D>(sb.b, true, st));
+  }
+  {
+    TuneScope ts(sb.tune, TK_ADJ_GATHER, st);
+    CK(launch_adj_gather<D>(sb.b, st));
+  }
+  CKS(batch_tune_end(sb.tune, sb.b, D));
   CK(ctrl_backward_batched(sb.cur, sb.dctrl, n, st));  // rewinds every member's reverse counter
   for (int m = 0; m < n; ++m) {
     mpm_scene* s = B->slots[sb.members[m]].s;

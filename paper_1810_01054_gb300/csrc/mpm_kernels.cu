@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(256) k_scatter(BatchDev b, const SelectPar* __
 // Phase C  work item = (cell, part): 2D one stencil node, 3D one x-slab of 9 nodes; a thread
 //          accumulates its item over the cell's particles in registers (fixed particle order).
 // Phase D  node block = fixed-order sum of the cell stencils covering each node -> global.
-template <int D, bool ADJ>
+template <int D, bool ADJ, int T = 256>
 struct P2GCfg {
   static constexpr int RF = 2 * D + D * D + 1;             // f, a, M, mass
   static constexpr int RA = ADJ ? D + D * D : 0;           // a', M'
@@ -434,8 +434,9 @@ struct P2GCfg {
   static constexpr int CH = CHF + CHA;
   static constexpr int PARTS = D == 2 ? 9 : 3;             // work items per cell
   static constexpr int NK = D == 2 ? 1 : 9;                // stencil nodes per work item
-  static constexpr int THREADS = 256;
+  static constexpr int THREADS = T;
   static constexpr int ITEMS = Cfg<D>::CELLS * PARTS;      // 2D 144, 3D 192
+  static constexpr int IPT = (ITEMS + T - 1) / T;          // work items per thread
   static constexpr int REC_CAP = D == 2 ? 1024 : 512;      // records staged at once
   static constexpr int CAP = Cfg<D>::SORT_CAP;
   static constexpr size_t REC_BYTES = size_t(REC_CAP) * RW * 4;
@@ -444,14 +445,16 @@ struct P2GCfg {
   static constexpr size_t U1 = REC_BYTES > ACC_BYTES ? REC_BYTES : ACC_BYTES;
   static constexpr size_t U_BYTES = U1 > IDS_BYTES ? U1 : IDS_BYTES;
   static constexpr size_t SMEM = IDS_BYTES + U_BYTES;
-  static_assert(ITEMS <= THREADS, "one work item per thread");
+  static_assert(D == 2 || IPT == 1, "a 3D work item holds 9 nodes: one item per thread");
   static_assert(Cfg<D>::BLOCK_NODES <= THREADS, "one node per thread in phase D");
 };
 
-template <int D, bool ADJ>
-__global__ void __launch_bounds__(256, 2) k_p2g(BatchDev b) {
+// T threads per CTA (256; 128 in 2D, where a thread then owns up to two of the 144 work items):
+// the work items and every sum keep their order, so T changes no bit of the results.
+template <int D, bool ADJ, int T>
+__global__ void __launch_bounds__(T, T == 256 ? 2 : 4) k_p2g(BatchDev b) {
   pdl_enter();
-  using K = P2GCfg<D, ADJ>;
+  using K = P2GCfg<D, ADJ, T>;
   constexpr int B = Cfg<D>::B, CELLS = Cfg<D>::CELLS, NB = Cfg<D>::BLOCK_NODES, BN = Cfg<D>::BN;
   constexpr int ST = Cfg<D>::STENCIL;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -483,15 +486,23 @@ __global__ void __launch_bounds__(256, 2) k_p2g(BatchDev b) {
     }
     int t[D];
     unlin<D>(gt - sp.tile_base, sp.nt, t);
-    const bool item_thread = tid < K::ITEMS;
-    const int my_cell = tid / K::PARTS, my_part = tid - K::PARTS * (tid / K::PARTS);
-    const int ikx = D == 2 ? my_part / 3 : my_part;  // stencil x offset of the item
-    const int iky = D == 2 ? my_part % 3 : 0;        // 2D: stencil y offset of the item
-    float acc[K::NK][K::CH];
+    // this thread's work items tid + j T: (cell, stencil part)
+    bool item_thread[K::IPT];
+    int my_cell[K::IPT], my_part[K::IPT], ikx[K::IPT], iky[K::IPT];
+    float acc[K::IPT][K::NK][K::CH];
 #pragma unroll
-    for (int k = 0; k < K::NK; ++k)
+    for (int j = 0; j < K::IPT; ++j) {
+      const int it = tid + j * T;
+      item_thread[j] = it < K::ITEMS;
+      my_cell[j] = it / K::PARTS;
+      my_part[j] = it - K::PARTS * my_cell[j];
+      ikx[j] = D == 2 ? my_part[j] / 3 : my_part[j];  // stencil x offset of the item
+      iky[j] = D == 2 ? my_part[j] % 3 : 0;           // 2D: stencil y offset of the item
 #pragma unroll
-      for (int c = 0; c < K::CH; ++c) acc[k][c] = 0.0f;
+      for (int k = 0; k < K::NK; ++k)
+#pragma unroll
+        for (int c = 0; c < K::CH; ++c) acc[j][k][c] = 0.0f;
+    }
     const float dx = sp.dx, dt = sp.dt;
     const float Dx4 = 4.0f * sp.inv_dx;  // (4/dx^2) * dx
 
@@ -572,9 +583,9 @@ __global__ void __launch_bounds__(256, 2) k_p2g(BatchDev b) {
       }
     };
 
-    // Phase C over staged rows [lo, hi) (row = canonical position - c0): this thread's work item
+    // Phase C over staged rows [lo, hi) (row = canonical position - c0): this thread's work item j
     // accumulates its stencil nodes over the cell's particles in canonical order.
-    auto accumulate = [&](int lo, int hi, int c0) {
+    auto accumulate = [&](int j, int lo, int hi, int c0) {
       for (int ei = lo; ei < hi; ++ei) {
         const float* rec = U + size_t(ei - c0) * K::RW;
         const float mass = rec[K::RF - 1];
@@ -584,26 +595,26 @@ __global__ void __launch_bounds__(256, 2) k_p2g(BatchDev b) {
         const float* av = rec + D;      // a
         const float* Mv = rec + 2 * D;  // M, row-major
         // the item's own offsets select weights by value: a runtime index would put w in local memory
-        const float wx = ikx == 0 ? w[0][0] : (ikx == 1 ? w[0][1] : w[0][2]);
+        const float wx = ikx[j] == 0 ? w[0][0] : (ikx[j] == 1 ? w[0][1] : w[0][2]);
         if constexpr (D == 2) {
-          const float N = wx * (iky == 0 ? w[1][0] : (iky == 1 ? w[1][1] : w[1][2]));
+          const float N = wx * (iky[j] == 0 ? w[1][0] : (iky[j] == 1 ? w[1][1] : w[1][2]));
 #pragma unroll
-          for (int a = 0; a < D; ++a) acc[0][a] += N * (av[a] + Mv[a * D] * float(ikx) + Mv[a * D + 1] * float(iky));
-          acc[0][D] += N * mass;
+          for (int a = 0; a < D; ++a) acc[j][0][a] += N * (av[a] + Mv[a * D] * float(ikx[j]) + Mv[a * D + 1] * float(iky[j]));
+          acc[j][0][D] += N * mass;
           if constexpr (ADJ) {
             const float* aa = rec + K::RF;
             const float* Ma = aa + D;
 #pragma unroll
             for (int a = 0; a < D; ++a)
-              acc[0][K::CHF + a] += N * (aa[a] + Ma[a * D] * float(ikx) + Ma[a * D + 1] * float(iky));
+              acc[j][0][K::CHF + a] += N * (aa[a] + Ma[a * D] * float(ikx[j]) + Ma[a * D + 1] * float(iky[j]));
           }
         } else {
           float u[D], ua[D];
 #pragma unroll
-          for (int a = 0; a < D; ++a) u[a] = av[a] + Mv[a * D] * float(ikx);
+          for (int a = 0; a < D; ++a) u[a] = av[a] + Mv[a * D] * float(ikx[j]);
           if constexpr (ADJ) {
 #pragma unroll
-            for (int a = 0; a < D; ++a) ua[a] = rec[K::RF + a] + rec[K::RF + D + a * D] * float(ikx);
+            for (int a = 0; a < D; ++a) ua[a] = rec[K::RF + a] + rec[K::RF + D + a * D] * float(ikx[j]);
           }
 #pragma unroll
           for (int ky = 0; ky < 3; ++ky) {
@@ -620,12 +631,12 @@ __global__ void __launch_bounds__(256, 2) k_p2g(BatchDev b) {
               const float N = wxy * w[D == 3 ? 2 : 0][kz];
               const int k = ky * 3 + kz;
 #pragma unroll
-              for (int a = 0; a < D; ++a) acc[k][a] += N * (u2[a] + Mv[a * D + D - 1] * float(kz));
-              acc[k][D] += N * mass;
+              for (int a = 0; a < D; ++a) acc[j][k][a] += N * (u2[a] + Mv[a * D + D - 1] * float(kz));
+              acc[j][k][D] += N * mass;
               if constexpr (ADJ) {
 #pragma unroll
                 for (int a = 0; a < D; ++a)
-                  acc[k][K::CHF + a] += N * (ua2[a] + rec[K::RF + D + a * D + D - 1] * float(kz));
+                  acc[j][k][K::CHF + a] += N * (ua2[a] + rec[K::RF + D + a * D + D - 1] * float(kz));
               }
             }
           }
@@ -697,7 +708,9 @@ __global__ void __launch_bounds__(256, 2) k_p2g(BatchDev b) {
         }
       }
       __syncthreads();
-      if (item_thread) accumulate(cstart[my_cell], cstart[my_cell + 1], 0);
+#pragma unroll
+      for (int j = 0; j < K::IPT; ++j)
+        if (item_thread[j]) accumulate(j, cstart[my_cell[j]], cstart[my_cell[j] + 1], 0);
     } else {
       // ---- general path: bucket, insertion-sort each cell's ids, stage records in chunks
       uint32_t* raw = reinterpret_cast<uint32_t*>(U);
@@ -733,7 +746,12 @@ __global__ void __launch_bounds__(256, 2) k_p2g(BatchDev b) {
       }
       __syncthreads();
       for (int i = tid; i < cnt; i += blockDim.x) b.sorted[st + i] = ids[i];
-      const int cs = item_thread ? cstart[my_cell] : 0, ce = item_thread ? cstart[my_cell + 1] : 0;
+      int cs[K::IPT], ce[K::IPT];
+#pragma unroll
+      for (int j = 0; j < K::IPT; ++j) {
+        cs[j] = item_thread[j] ? cstart[my_cell[j]] : 0;
+        ce[j] = item_thread[j] ? cstart[my_cell[j] + 1] : 0;
+      }
       for (int c0 = 0; c0 < cnt; c0 += K::REC_CAP) {
         __syncthreads();  // previous records consumed (and phase A's scratch released)
         const int c1 = cnt < c0 + K::REC_CAP ? cnt : c0 + K::REC_CAP;
@@ -744,16 +762,20 @@ __global__ void __launch_bounds__(256, 2) k_p2g(BatchDev b) {
           make_record(id, sp.key[id] & 63u, group_of(sp, id), r, e - c0);
         }
         __syncthreads();
-        if (item_thread) accumulate(cs > c0 ? cs : c0, ce < c1 ? ce : c1, c0);
+#pragma unroll
+        for (int j = 0; j < K::IPT; ++j)
+          if (item_thread[j]) accumulate(j, cs[j] > c0 ? cs[j] : c0, ce[j] < c1 ? ce[j] : c1, c0);
       }
     }
     __syncthreads();  // records done; U becomes the per-cell stencil accumulator array
-    if (item_thread) {
-      float* ca = U + size_t(my_cell) * ST * K::CH;
+#pragma unroll
+    for (int j = 0; j < K::IPT; ++j) {
+      if (!item_thread[j]) continue;
+      float* ca = U + size_t(my_cell[j]) * ST * K::CH;
 #pragma unroll
       for (int k = 0; k < K::NK; ++k)
 #pragma unroll
-        for (int c = 0; c < K::CH; ++c) ca[(my_part * K::NK + k) * K::CH + c] = acc[k][c];
+        for (int c = 0; c < K::CH; ++c) ca[(my_part[j] * K::NK + k) * K::CH + c] = acc[j][k][c];
     }
     __syncthreads();
     // ---- phase D: node block = fixed-order sum over the cells whose stencil covers it -----
@@ -1467,8 +1489,14 @@ cudaError_t launch_sort(const BatchDev& b, cudaStream_t s, const SelectPar* sel)
 
 template <int D, bool ADJ>
 static cudaError_t p2g_configure() {
-  using K = P2GCfg<D, ADJ>;
-  return cudaFuncSetAttribute(k_p2g<D, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(K::SMEM));
+  cudaError_t e = cudaFuncSetAttribute(k_p2g<D, ADJ, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(P2GCfg<D, ADJ, 256>::SMEM));
+  if constexpr (D == 2) {
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_p2g<D, ADJ, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               int(P2GCfg<D, ADJ, 128>::SMEM));
+  }
+  return e;
 }
 
 cudaError_t configure_kernels() {
@@ -1488,9 +1516,14 @@ static int tile_grid(const BatchDev& b, int k) {
 
 template <int D, bool ADJ>
 static cudaError_t p2g_impl(const BatchDev& b, cudaStream_t s) {
-  using K = P2GCfg<D, ADJ>;
-  const int grid = tile_grid(b, ADJ ? TK_P2G_ADJ : TK_P2G);
-  launch_pdl(k_p2g<D, ADJ>, dim3(grid), dim3(K::THREADS), K::SMEM, s, b);
+  const int k = ADJ ? TK_P2G_ADJ : TK_P2G;
+  const int grid = tile_grid(b, k);
+  bool small = false;  // 128-thread CTAs (2D only)
+  if constexpr (D == 2) small = b.launch[k].threads == 128;
+  if constexpr (D == 2) {
+    if (small) launch_pdl(k_p2g<D, ADJ, 128>, dim3(grid), dim3(128), P2GCfg<D, ADJ, 128>::SMEM, s, b);
+  }
+  if (!small) launch_pdl(k_p2g<D, ADJ, 256>, dim3(grid), dim3(256), P2GCfg<D, ADJ, 256>::SMEM, s, b);
   count_launches(1);
   return cudaGetLastError();
 }

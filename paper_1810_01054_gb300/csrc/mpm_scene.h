@@ -158,20 +158,28 @@ void tune_release(mpm_scene* s);
 bool tune_wants(const mpm_scene* s, int ph);
 // One directly-launched step of phase ph with the candidate shapes under trial, timed.
 mpm_status tune_step(mpm_scene* s, int ph);
-// Shapes of the cache entry of a batch's key, if there is one (defaults stay otherwise).
-void tune_apply_cached(BatchDev& b, int dim);
+// Batches (mpm_batch.cu): a sub-batch composition's shapes come from the cache; on a miss the
+// kernels it runs are tried the way a scene's are, during its ordinary steps.
+//  batch_tune_init   cache shapes of the composition's key, or trials armed for `kernels` (mask)
+//  batch_tune_begin  candidate shapes of the kernels under trial into b (before a step)
+//  batch_tune_end    times of that step's trials; when the last finishes, the key's cache entry
+//                    takes the chosen shapes of these kernels
+mpm_status batch_tune_init(TuneState& t, BatchDev& b, int dim, unsigned kernels);
+void batch_tune_begin(TuneState& t, BatchDev& b, int dim);
+mpm_status batch_tune_end(TuneState& t, BatchDev& b, int dim);
+void batch_tune_release(TuneState& t);
 // Records CUDA events around one launch of tile kernel k while its shape is being tried.
 struct TuneScope {
-  mpm_scene* s;
+  TuneState& t;
   int k;
   cudaStream_t st;
   bool on;
-  TuneScope(mpm_scene* scene, int kernel, cudaStream_t stream)
-      : s(scene), k(kernel), st(stream), on(scene->tune.timing && scene->tune.pending[kernel]) {
-    if (on) cudaEventRecord(s->tune.ev[k][0], st);
+  TuneScope(TuneState& state, int kernel, cudaStream_t stream)
+      : t(state), k(kernel), st(stream), on(state.timing && state.pending[kernel]) {
+    if (on) cudaEventRecord(t.ev[k][0], st);
   }
   ~TuneScope() {
-    if (on) cudaEventRecord(s->tune.ev[k][1], st);
+    if (on) cudaEventRecord(t.ev[k][1], st);
   }
 };
 }  // namespace gbmpm

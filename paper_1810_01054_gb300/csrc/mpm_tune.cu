@@ -32,7 +32,9 @@ namespace {
 
 constexpr int kReps = 2;  // timed launches per candidate; the faster one counts
 
-const TileLaunch kCandP2G[] = {{2, 256}, {3, 256}, {4, 256}, {6, 256}, {8, 256}};
+// P2G and the adjoint scatter take 128-thread CTAs in 2D only (a 3D work item is 9 nodes)
+const TileLaunch kCandP2G3[] = {{2, 256}, {3, 256}, {4, 256}, {6, 256}, {8, 256}};
+const TileLaunch kCandP2G2[] = {{2, 256}, {3, 256}, {4, 256}, {6, 256}, {8, 256}, {4, 128}, {6, 128}};
 const TileLaunch kCandG2P[] = {{2, 256}, {3, 256}, {4, 256}, {8, 256}, {16, 256}, {6, 128}, {8, 128}, {16, 128}};
 const TileLaunch kCandAdj[] = {{2, 256}, {3, 256}, {4, 256}, {6, 256}, {8, 256}};
 
@@ -41,11 +43,12 @@ struct CandList {
   int n;
 };
 
-CandList cands(int k) {
+CandList cands(int k, int dim) {
   switch (k) {
     case TK_P2G:
     case TK_P2G_ADJ:
-      return {kCandP2G, int(sizeof(kCandP2G) / sizeof(kCandP2G[0]))};
+      if (dim == 2) return {kCandP2G2, int(sizeof(kCandP2G2) / sizeof(kCandP2G2[0]))};
+      return {kCandP2G3, int(sizeof(kCandP2G3) / sizeof(kCandP2G3[0]))};
     case TK_G2P:
       return {kCandG2P, int(sizeof(kCandG2P) / sizeof(kCandG2P[0]))};
     default:
@@ -53,8 +56,8 @@ CandList cands(int k) {
   }
 }
 
-bool is_candidate(int k, TileLaunch t) {
-  const CandList l = cands(k);
+bool is_candidate(int k, int dim, TileLaunch t) {
+  const CandList l = cands(k, dim);
   for (int i = 0; i < l.n; ++i)
     if (l.c[i].ctas_per_sm == t.ctas_per_sm && l.c[i].threads == t.threads) return true;
   return false;
@@ -76,6 +79,9 @@ struct Entry {
 
 std::mutex g_mu;
 std::map<Key, Entry> g_cache;
+// keys whose entry came from batch trials that tuned only some kernels: bit k = kernel k tuned
+// (absent: every kernel of the entry is tuned)
+std::map<Key, unsigned> g_partial;
 bool g_env_loaded = false;
 
 Key make_key(int dim, long long particles, long long tiles, int sms) {
@@ -111,7 +117,7 @@ mpm_status load_locked(const char* path) {
     Entry e;
     for (int k = 0; k < TK_COUNT; ++k) {
       e.l[k] = TileLaunch{v[4 + 2 * k], v[5 + 2 * k]};
-      bad = bad || !is_candidate(k, e.l[k]);
+      bad = bad || !is_candidate(k, v[0], e.l[k]);
     }
     add[Key(v[0], v[1], v[2], v[3])] = e;
   }
@@ -130,8 +136,9 @@ mpm_status save_locked(const char* path) {
   FILE* f = std::fopen(tmp.c_str(), "w");
   if (!f) return MPM_ERR_ARG;
   std::fprintf(f, "gbmpm-tune 1 (dim log2_particles log2_tiles sms, then ctas_per_sm threads of p2g g2p p2g_adj "
-                 "adj_gather; threads are chosen for g2p only)\n");
+                 "adj_gather; threads are chosen for g2p, and in 2D for p2g and p2g_adj)\n");
   for (auto& kv : g_cache) {
+    if (g_partial.count(kv.first)) continue;  // some kernels of this key not tuned yet
     std::fprintf(f, "%d %d %d %d", std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
                  std::get<3>(kv.first));
     for (int k = 0; k < TK_COUNT; ++k) std::fprintf(f, " %d %d", kv.second.l[k].ctas_per_sm, kv.second.l[k].threads);
@@ -154,7 +161,7 @@ bool lookup(const Key& key, Entry* out) {
   std::lock_guard<std::mutex> lk(g_mu);
   env_load_locked();
   auto it = g_cache.find(key);
-  if (it == g_cache.end()) return false;
+  if (it == g_cache.end() || g_partial.count(key)) return false;
   *out = it->second;
   return true;
 }
@@ -163,6 +170,7 @@ void store(const Key& key, const Entry& e) {
   std::lock_guard<std::mutex> lk(g_mu);
   env_load_locked();
   g_cache[key] = e;
+  g_partial.erase(key);
   const char* p = std::getenv("GBMPM_TUNE_CACHE");
   if (p && *p) save_locked(p);
 }
@@ -217,17 +225,20 @@ bool tune_wants(const mpm_scene* s, int ph) {
   return false;
 }
 
-mpm_status tune_step(mpm_scene* s, int ph) {
-  TuneState& t = s->tune;
+namespace {
+
+// Shapes under trial into b (kernels pending and, with ph >= 0, run by phase ph).
+void trial_begin(TuneState& t, BatchDev& b, int dim, int ph) {
   for (int k = 0; k < TK_COUNT; ++k)
-    if (t.pending[k] && phase_runs(ph, k)) s->b.launch[k] = cands(k).c[t.cand[k]];
-  t.timing = true;
-  const mpm_status st = enqueue_step(s, ph, s->ctx->stream);
-  t.timing = false;
-  CKS(st);
-  bool finished = false;
+    if (t.pending[k] && (ph < 0 || phase_runs(ph, k))) b.launch[k] = cands(k, dim).c[t.cand[k]];
+}
+
+// After a timed step: each pending kernel's time, next candidate, and when a kernel has tried
+// them all its fastest shape into b.  *finished = some kernel finished in this step.
+mpm_status trial_end(TuneState& t, BatchDev& b, int dim, int ph, bool* finished) {
+  *finished = false;
   for (int k = 0; k < TK_COUNT; ++k) {
-    if (!(t.pending[k] && phase_runs(ph, k))) continue;
+    if (!(t.pending[k] && (ph < 0 || phase_runs(ph, k)))) continue;
     CK(cudaEventSynchronize(t.ev[k][1]));
     float ms = 0.0f;
     CK(cudaEventElapsedTime(&ms, t.ev[k][0], t.ev[k][1]));
@@ -238,13 +249,43 @@ mpm_status tune_step(mpm_scene* s, int ph) {
       t.best_ms[k] = t.cur_ms[k];
     }
     t.rep[k] = 0;
-    if (++t.cand[k] == cands(k).n) {
+    if (++t.cand[k] == cands(k, dim).n) {
       t.pending[k] = false;
       t.tuned[k] = true;
-      s->b.launch[k] = cands(k).c[t.best[k]];
-      finished = true;
+      b.launch[k] = cands(k, dim).c[t.best[k]];
+      *finished = true;
     }
   }
+  return MPM_OK;
+}
+
+mpm_status create_events(TuneState& t) {
+  for (int k = 0; k < TK_COUNT; ++k)
+    for (int j = 0; j < 2; ++j)
+      if (!t.ev[k][j]) CK(cudaEventCreate(&t.ev[k][j]));
+  return MPM_OK;
+}
+
+void destroy_state_events(TuneState& t) {
+  for (int k = 0; k < TK_COUNT; ++k)
+    for (int j = 0; j < 2; ++j)
+      if (t.ev[k][j]) {
+        cudaEventDestroy(t.ev[k][j]);
+        t.ev[k][j] = nullptr;
+      }
+}
+
+}  // namespace
+
+mpm_status tune_step(mpm_scene* s, int ph) {
+  TuneState& t = s->tune;
+  trial_begin(t, s->b, s->dim, ph);
+  t.timing = true;
+  const mpm_status st = enqueue_step(s, ph, s->ctx->stream);
+  t.timing = false;
+  CKS(st);
+  bool finished = false;
+  CKS(trial_end(t, s->b, s->dim, ph, &finished));
   if (finished) {
     bool all = true;
     for (int k = 0; k < TK_COUNT; ++k) all = all && t.tuned[k];
@@ -258,11 +299,90 @@ mpm_status tune_step(mpm_scene* s, int ph) {
   return MPM_OK;
 }
 
-void tune_apply_cached(BatchDev& b, int dim) {
+mpm_status batch_tune_init(TuneState& t, BatchDev& b, int dim, unsigned kernels) {
+  for (int k = 0; k < TK_COUNT; ++k) {
+    t.pending[k] = t.tuned[k] = false;
+    t.cand[k] = t.rep[k] = t.best[k] = 0;
+  }
+  t.timing = false;
+  const Key key = make_key(dim, b.total_particles, b.total_tiles, b.sm_count);
   Entry e;
-  if (lookup(make_key(dim, b.total_particles, b.total_tiles, b.sm_count), &e))
-    for (int k = 0; k < TK_COUNT; ++k) b.launch[k] = e.l[k];
+  bool have;
+  unsigned mask = 0;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    env_load_locked();
+    auto it = g_cache.find(key);
+    have = it != g_cache.end();
+    if (have) e = it->second;
+    auto m = g_partial.find(key);
+    mask = have ? (m == g_partial.end() ? ~0u : m->second) : 0u;
+  }
+  for (int k = 0; k < TK_COUNT; ++k) {
+    if (have) b.launch[k] = e.l[k];
+    if (!(kernels & (1u << k))) continue;
+    if (mask & (1u << k)) {
+      t.tuned[k] = true;
+    } else {
+      t.pending[k] = true;
+    }
+  }
+  bool any = false;
+  for (int k = 0; k < TK_COUNT; ++k) any = any || t.pending[k];
+  if (any) CKS(create_events(t));
+  return MPM_OK;
 }
+
+void batch_tune_begin(TuneState& t, BatchDev& b, int dim) {
+  bool any = false;
+  for (int k = 0; k < TK_COUNT; ++k) any = any || t.pending[k];
+  if (!any) return;
+  trial_begin(t, b, dim, -1);
+  t.timing = true;
+}
+
+mpm_status batch_tune_end(TuneState& t, BatchDev& b, int dim) {
+  if (!t.timing) return MPM_OK;
+  t.timing = false;
+  bool finished = false;
+  CKS(trial_end(t, b, dim, -1, &finished));
+  bool left = false;
+  for (int k = 0; k < TK_COUNT; ++k) left = left || t.pending[k];
+  if (finished && !left) {
+    // merge this composition's kernels into the key's entry; a key whose four kernels are not all
+    // tuned yet stays out of the cache file
+    const Key key = make_key(dim, b.total_particles, b.total_tiles, b.sm_count);
+    std::lock_guard<std::mutex> lk(g_mu);
+    env_load_locked();
+    auto it = g_cache.find(key);
+    Entry e;
+    unsigned mask = 0;
+    if (it != g_cache.end()) {
+      e = it->second;
+      auto m = g_partial.find(key);
+      mask = m == g_partial.end() ? ~0u : m->second;
+    } else {
+      for (int k = 0; k < TK_COUNT; ++k) e.l[k] = kDefaultLaunch;
+    }
+    for (int k = 0; k < TK_COUNT; ++k)
+      if (t.tuned[k]) {
+        e.l[k] = b.launch[k];
+        mask |= 1u << k;
+      }
+    g_cache[key] = e;
+    if ((mask & ((1u << TK_COUNT) - 1)) == (1u << TK_COUNT) - 1) {
+      g_partial.erase(key);
+      const char* p = std::getenv("GBMPM_TUNE_CACHE");
+      if (p && *p) save_locked(p);
+    } else {
+      g_partial[key] = mask;
+    }
+    destroy_state_events(t);
+  }
+  return MPM_OK;
+}
+
+void batch_tune_release(TuneState& t) { destroy_state_events(t); }
 
 }  // namespace gbmpm
 
@@ -282,7 +402,7 @@ mpm_status mpm_scene_set_tuning(mpm_scene* s, int mode) {
 mpm_status mpm_scene_launch(const mpm_scene* s, int kernel, int* ctas_per_sm, int* threads, int* tuned) {
   if (!s || kernel < 0 || kernel >= TK_COUNT) return MPM_ERR_ARG;
   if (ctas_per_sm) *ctas_per_sm = s->b.launch[kernel].ctas_per_sm;
-  if (threads) *threads = kernel == TK_G2P ? s->b.launch[kernel].threads : (kernel == TK_ADJ_GATHER && s->dim == 3 ? 128 : 256);
+  if (threads) *threads = kernel == TK_ADJ_GATHER ? (s->dim == 3 ? 128 : 256) : s->b.launch[kernel].threads;
   if (tuned) *tuned = s->tune.tuned[kernel] ? 1 : 0;
   return MPM_OK;
 }
@@ -305,7 +425,7 @@ mpm_status mpm_tune_cache_store(int dim, long long particles, long long grid_til
   Entry e;
   for (int k = 0; k < TK_COUNT; ++k) {
     e.l[k] = TileLaunch{shape[2 * k], shape[2 * k + 1]};
-    if (!is_candidate(k, e.l[k])) return MPM_ERR_ARG;
+    if (!is_candidate(k, dim, e.l[k])) return MPM_ERR_ARG;
   }
   store(make_key(dim, particles, grid_tiles, sm_count), e);
   return MPM_OK;

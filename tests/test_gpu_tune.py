@@ -49,8 +49,56 @@ def test_tuned_results_are_bitwise_default_and_cached(M, ctx, spec):
     for a, b in zip(g0, g1):
         assert np.array_equal(a, b)
     assert all(tuned for _, _, tuned in sh1), sh1
-    assert sh1[M.TK_P2G][1] == 256 and sh1[M.TK_ADJ_GATHER][1] == adj_threads
+    p2g_threads = (128, 256) if spec.dim == 2 else (256,)
+    assert sh1[M.TK_P2G][1] in p2g_threads and sh1[M.TK_P2G_ADJ][1] in p2g_threads
+    assert sh1[M.TK_ADJ_GATHER][1] == adj_threads
     # a new scene of the same workload takes the cached shapes at creation
     sc = M.Scene(ctx, spec)
     assert [sc.launch(kk) for kk in range(4)] == sh1
     sc.close()
+
+
+
+def test_p2g_with_128_thread_ctas_is_bitwise_the_default(M, ctx):
+    """2D P2G and adjoint scatter with 128-thread CTAs (a thread owns up to two work items) give
+    the bits of the 256-thread CTAs: the work items and every sum keep their order."""
+    import torch
+    spec = S.blob(2, 48, 3000, 23, radius_cells=9.0, v_scale=0.3, c_scale=0.5, amp=2.0)
+    T, k = 24, 6
+    st0, g0, _ = _run(M, ctx, spec, T, k, M.TUNE_OFF)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    shapes = [(4, 128), (4, 256), (6, 128), (4, 256)]
+    M.tune_cache_store(2, spec.n_particles, (48 // 4) ** 2, sms, shapes)
+    st1, g1, sh1 = _run(M, ctx, spec, T, k, M.TUNE_AUTO)  # takes the cached shapes, no trials
+    assert [s[:2] for s in sh1] == shapes
+    for a, b in zip(st0 + g0, st1 + g1):
+        assert np.array_equal(a, b)
+
+
+def test_a_batch_tunes_its_composition_and_keeps_the_bits(M, ctx):
+    """A batch whose composition has no cache entry tries the candidate shapes during its own
+    steps; its results stay bitwise those of the scenes run alone, and afterwards the key of the
+    composition is cached for the next batch."""
+    import torch
+    spec = S.blob(2, 40, 700, 24, radius_cells=6.0, v_scale=0.3, amp=2.0)
+    B, T = 6, 30
+    alone = []
+    for _ in range(B):
+        st, g, _ = _run(M, ctx, spec, T, int(np.ceil(np.sqrt(T))), M.TUNE_OFF)
+        alone.append(st + g)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    key = (2, B * spec.n_particles, B * (40 // 4) ** 2, sms)
+    assert M.tune_cache_lookup(*key) is None
+    batch = M.Batch(ctx, 2)
+    scenes = [M.Scene(ctx, spec) for _ in range(B)]
+    slots = [batch.admit(sc, T, True) for sc in scenes]
+    while not all(batch.poll(sl) for sl in slots):
+        batch.tick(4)
+    for sc, ref in zip(scenes, alone):
+        for a, b in zip(sc.get_state() + sc.gradients(), ref):
+            assert np.array_equal(a, b)
+    batch.close()
+    for sc in scenes:
+        sc.close()
+    shapes = M.tune_cache_lookup(*key)
+    assert shapes is not None and shapes[M.TK_ADJ_GATHER][1] == 256

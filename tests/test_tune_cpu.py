@@ -31,9 +31,16 @@ def test_shapes_outside_the_candidates_are_refused():
     bad = [(5, 256), (8, 128), (2, 256), (6, 256)]  # 5 CTAs per SM is not a P2G candidate
     with pytest.raises(mpm.MPMError):
         mpm.tune_cache_store(3, 1000, 64, 152, bad)
-    with pytest.raises(mpm.MPMError):  # 128 threads are a candidate of G2P only
-        mpm.tune_cache_store(3, 1000, 64, 152, [(2, 128)] + SHAPES[1:])
+    with pytest.raises(mpm.MPMError):  # 128-thread P2G CTAs exist in 2D only
+        mpm.tune_cache_store(3, 1000, 64, 152, [(4, 128)] + SHAPES[1:])
+    with pytest.raises(mpm.MPMError):  # and only at the listed CTAs per SM
+        mpm.tune_cache_store(2, 1000, 64, 152, [(2, 128)] + SHAPES[1:])
+    with pytest.raises(mpm.MPMError):  # the adjoint gather's CTA size is not tuned
+        mpm.tune_cache_store(2, 1000, 64, 152, SHAPES[:3] + [(4, 128)])
     assert mpm.tune_cache_lookup(3, 1000, 64, 152) is None
+    assert mpm.tune_cache_lookup(2, 1000, 64, 152) is None
+    mpm.tune_cache_store(2, 1000, 64, 152, [(4, 128), (8, 128), (6, 128), (6, 256)])
+    assert mpm.tune_cache_lookup(2, 1000, 64, 152) == [(4, 128), (8, 128), (6, 128), (6, 256)]
 
 
 def test_file_round_trip(tmp_path):
