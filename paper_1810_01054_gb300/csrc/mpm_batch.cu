@@ -45,7 +45,12 @@ struct SubBatch {
   // launch shapes: the cache entry of the composition's key, else trials during its steps
   TuneState tune;
   long long key_particles = -1, key_tiles = -1;
+  int trial_wait = 0;  // steps of this key left before its trials start (0: none pending)
 };
+
+// Steps a composition key must run before its launch-shape trials start: a serving mix changes
+// composition every few ticks, and trials that never finish would only cost time.
+constexpr int kTrialWait = 32;
 
 #define CK(expr)                                                                   \
   do {                                                                             \
@@ -141,6 +146,12 @@ mpm_status grow(mpm_batch* B, SubBatch& sb, int n_scenes, int tiles, int particl
   return MPM_OK;
 }
 
+// Tile kernels a half of the batch runs: forward steps P2G and G2P, reverse steps the adjoint
+// scatter and gather.
+unsigned half_kernels(const mpm_batch* B, const SubBatch& sb) {
+  return &sb == &B->fwd ? (1u << TK_P2G) | (1u << TK_G2P) : (1u << TK_P2G_ADJ) | (1u << TK_ADJ_GATHER);
+}
+
 int phase_of(int state) { return state == S_FWD ? PH_ROLL : state == S_RCM ? PH_RCM : PH_REV; }
 
 // Lays the members of a sub-batch out in the batch's tile and particle spaces and uploads the
@@ -194,15 +205,20 @@ mpm_status compose(mpm_batch* B, SubBatch& sb) {
   // and trials (a lockstep batch alternates each half between its members and nothing)
   if (!sb.members.empty() && (particles != sb.key_particles || tiles != sb.key_tiles)) {
     default_launch(sb.b, B->ctx->sm_count);
-    const unsigned kernels = &sb == &B->fwd ? (1u << TK_P2G) | (1u << TK_G2P)
-                                            : (1u << TK_P2G_ADJ) | (1u << TK_ADJ_GATHER);
-    CKS(batch_tune_init(sb.tune, sb.b, B->dim, kernels));
+    CKS(batch_tune_init(sb.tune, sb.b, B->dim, 0u));  // cached shapes, no trials yet
+    sb.trial_wait = batch_tune_cached(sb.b, B->dim, half_kernels(B, sb)) ? 0 : kTrialWait;
     sb.key_particles = particles;
     sb.key_tiles = tiles;
   }
   sb.b.has_material = 0;
   for (int m : sb.members) sb.b.has_material |= B->slots[m].s->hp.gmat ? 1 : 0;
   sb.need_keys = true;
+  return MPM_OK;
+}
+
+// Counts a step of the half's key; its trials start once the key has run kTrialWait steps.
+mpm_status trial_clock(mpm_batch* B, SubBatch& sb) {
+  if (sb.trial_wait > 0 && --sb.trial_wait == 0) CKS(batch_tune_init(sb.tune, sb.b, B->dim, half_kernels(B, sb)));
   return MPM_OK;
 }
 
@@ -236,6 +252,7 @@ mpm_status forward_step(mpm_batch* B) {
     sb.need_keys = false;
   }
   CK(launch_sort<D>(sb.b, st));
+  CKS(trial_clock(B, sb));
   batch_tune_begin(sb.tune, sb.b, D);
   {
     TuneScope ts(sb.tune, TK_P2G, st);
@@ -261,6 +278,7 @@ mpm_status reverse_step(mpm_batch* B) {
     if (ctrl_reads_state(s->ctrl)) CK(ctrl_step_forward(s->hp, sb.cur + m, s->ctrl, st));
   }
   CK(launch_sort<D>(sb.b, st));
+  CKS(trial_clock(B, sb));
   batch_tune_begin(sb.tune, sb.b, D);
   {
     TuneScope ts(sb.tune, TK_P2G_ADJ, st);

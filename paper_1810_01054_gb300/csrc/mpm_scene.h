@@ -54,6 +54,11 @@ struct TuneState {
   float best_ms[gbmpm::TK_COUNT] = {};
   bool timing = false;                  // the step being enqueued records the events below
   cudaEvent_t ev[gbmpm::TK_COUNT][2] = {};
+  // batches read a step's trial times one step later, so the host never waits for the GPU: two
+  // event sets in turn (ev points at the one being recorded) and the candidate each set timed
+  cudaEvent_t evs[2][gbmpm::TK_COUNT][2] = {};
+  int timed[2][gbmpm::TK_COUNT] = {{-1, -1, -1, -1}, {-1, -1, -1, -1}};
+  int set = 0;
 };
 
 struct mpm_scene {
@@ -165,6 +170,8 @@ mpm_status tune_step(mpm_scene* s, int ph);
 //  batch_tune_end    times of that step's trials; when the last finishes, the key's cache entry
 //                    takes the chosen shapes of these kernels
 mpm_status batch_tune_init(TuneState& t, BatchDev& b, int dim, unsigned kernels);
+// True when the cache entry of b's key has every kernel of the mask tuned (shapes then in b).
+bool batch_tune_cached(BatchDev& b, int dim, unsigned kernels);
 void batch_tune_begin(TuneState& t, BatchDev& b, int dim);
 mpm_status batch_tune_end(TuneState& t, BatchDev& b, int dim);
 void batch_tune_release(TuneState& t);

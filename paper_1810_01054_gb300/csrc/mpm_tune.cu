@@ -235,6 +235,23 @@ void trial_begin(TuneState& t, BatchDev& b, int dim, int ph) {
 
 // After a timed step: each pending kernel's time, next candidate, and when a kernel has tried
 // them all its fastest shape into b.  *finished = some kernel finished in this step.
+// One timed launch of kernel k's current candidate; true when k has now tried every candidate
+// (its fastest shape is then in b).
+bool record_time(TuneState& t, BatchDev& b, int dim, int k, float ms) {
+  t.cur_ms[k] = t.rep[k] == 0 ? ms : std::fmin(t.cur_ms[k], ms);
+  if (++t.rep[k] < kReps) return false;
+  if (t.cand[k] == 0 || t.cur_ms[k] < t.best_ms[k]) {
+    t.best[k] = t.cand[k];
+    t.best_ms[k] = t.cur_ms[k];
+  }
+  t.rep[k] = 0;
+  if (++t.cand[k] < cands(k, dim).n) return false;
+  t.pending[k] = false;
+  t.tuned[k] = true;
+  b.launch[k] = cands(k, dim).c[t.best[k]];
+  return true;
+}
+
 mpm_status trial_end(TuneState& t, BatchDev& b, int dim, int ph, bool* finished) {
   *finished = false;
   for (int k = 0; k < TK_COUNT; ++k) {
@@ -242,37 +259,31 @@ mpm_status trial_end(TuneState& t, BatchDev& b, int dim, int ph, bool* finished)
     CK(cudaEventSynchronize(t.ev[k][1]));
     float ms = 0.0f;
     CK(cudaEventElapsedTime(&ms, t.ev[k][0], t.ev[k][1]));
-    t.cur_ms[k] = t.rep[k] == 0 ? ms : std::fmin(t.cur_ms[k], ms);
-    if (++t.rep[k] < kReps) continue;
-    if (t.cand[k] == 0 || t.cur_ms[k] < t.best_ms[k]) {
-      t.best[k] = t.cand[k];
-      t.best_ms[k] = t.cur_ms[k];
-    }
-    t.rep[k] = 0;
-    if (++t.cand[k] == cands(k, dim).n) {
-      t.pending[k] = false;
-      t.tuned[k] = true;
-      b.launch[k] = cands(k, dim).c[t.best[k]];
-      *finished = true;
-    }
+    *finished = record_time(t, b, dim, k, ms) || *finished;
   }
   return MPM_OK;
 }
 
-mpm_status create_events(TuneState& t) {
-  for (int k = 0; k < TK_COUNT; ++k)
-    for (int j = 0; j < 2; ++j)
-      if (!t.ev[k][j]) CK(cudaEventCreate(&t.ev[k][j]));
+mpm_status create_batch_events(TuneState& t) {
+  for (int s = 0; s < 2; ++s)
+    for (int k = 0; k < TK_COUNT; ++k) {
+      t.timed[s][k] = -1;
+      for (int j = 0; j < 2; ++j)
+        if (!t.evs[s][k][j]) CK(cudaEventCreate(&t.evs[s][k][j]));
+    }
+  t.set = 0;
   return MPM_OK;
 }
 
-void destroy_state_events(TuneState& t) {
-  for (int k = 0; k < TK_COUNT; ++k)
-    for (int j = 0; j < 2; ++j)
-      if (t.ev[k][j]) {
-        cudaEventDestroy(t.ev[k][j]);
-        t.ev[k][j] = nullptr;
-      }
+void destroy_batch_events(TuneState& t) {
+  for (int s = 0; s < 2; ++s)
+    for (int k = 0; k < TK_COUNT; ++k)
+      for (int j = 0; j < 2; ++j)
+        if (t.evs[s][k][j]) {
+          cudaEventDestroy(t.evs[s][k][j]);
+          t.evs[s][k][j] = nullptr;
+        }
+  for (int k = 0; k < TK_COUNT; ++k) t.ev[k][0] = t.ev[k][1] = nullptr;
 }
 
 }  // namespace
@@ -329,8 +340,21 @@ mpm_status batch_tune_init(TuneState& t, BatchDev& b, int dim, unsigned kernels)
   }
   bool any = false;
   for (int k = 0; k < TK_COUNT; ++k) any = any || t.pending[k];
-  if (any) CKS(create_events(t));
+  if (any) CKS(create_batch_events(t));
   return MPM_OK;
+}
+
+bool batch_tune_cached(BatchDev& b, int dim, unsigned kernels) {
+  const Key key = make_key(dim, b.total_particles, b.total_tiles, b.sm_count);
+  std::lock_guard<std::mutex> lk(g_mu);
+  env_load_locked();
+  auto it = g_cache.find(key);
+  if (it == g_cache.end()) return false;
+  auto m = g_partial.find(key);
+  const unsigned mask = m == g_partial.end() ? ~0u : m->second;
+  if ((mask & kernels) != kernels) return false;
+  for (int k = 0; k < TK_COUNT; ++k) b.launch[k] = it->second.l[k];
+  return true;
 }
 
 void batch_tune_begin(TuneState& t, BatchDev& b, int dim) {
@@ -338,14 +362,31 @@ void batch_tune_begin(TuneState& t, BatchDev& b, int dim) {
   for (int k = 0; k < TK_COUNT; ++k) any = any || t.pending[k];
   if (!any) return;
   trial_begin(t, b, dim, -1);
+  for (int k = 0; k < TK_COUNT; ++k) {  // this step records into the current event set
+    t.ev[k][0] = t.evs[t.set][k][0];
+    t.ev[k][1] = t.evs[t.set][k][1];
+    t.timed[t.set][k] = t.pending[k] ? t.cand[k] : -1;
+  }
   t.timing = true;
 }
 
+// The times of the previous timed step (whose events are done by now or soon: this step is
+// already queued behind it) count for the candidate they timed, if it is still the current one.
 mpm_status batch_tune_end(TuneState& t, BatchDev& b, int dim) {
   if (!t.timing) return MPM_OK;
   t.timing = false;
+  const int prev = t.set ^ 1;
   bool finished = false;
-  CKS(trial_end(t, b, dim, -1, &finished));
+  for (int k = 0; k < TK_COUNT; ++k) {
+    const int c = t.timed[prev][k];
+    t.timed[prev][k] = -1;
+    if (c < 0 || !t.pending[k] || c != t.cand[k]) continue;
+    CK(cudaEventSynchronize(t.evs[prev][k][1]));
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, t.evs[prev][k][0], t.evs[prev][k][1]));
+    finished = record_time(t, b, dim, k, ms) || finished;
+  }
+  t.set = prev;
   bool left = false;
   for (int k = 0; k < TK_COUNT; ++k) left = left || t.pending[k];
   if (finished && !left) {
@@ -377,12 +418,12 @@ mpm_status batch_tune_end(TuneState& t, BatchDev& b, int dim) {
     } else {
       g_partial[key] = mask;
     }
-    destroy_state_events(t);
+    destroy_batch_events(t);
   }
   return MPM_OK;
 }
 
-void batch_tune_release(TuneState& t) { destroy_state_events(t); }
+void batch_tune_release(TuneState& t) { destroy_batch_events(t); }
 
 }  // namespace gbmpm
 

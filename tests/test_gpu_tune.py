@@ -77,11 +77,11 @@ def test_p2g_with_128_thread_ctas_is_bitwise_the_default(M, ctx):
 
 def test_a_batch_tunes_its_composition_and_keeps_the_bits(M, ctx):
     """A batch whose composition has no cache entry tries the candidate shapes during its own
-    steps; its results stay bitwise those of the scenes run alone, and afterwards the key of the
-    composition is cached for the next batch."""
+    steps (once the composition has run 32 steps); its results stay bitwise those of the scenes run
+    alone, and afterwards the key of the composition is cached for the next batch."""
     import torch
-    spec = S.blob(2, 40, 700, 24, radius_cells=6.0, v_scale=0.3, amp=2.0)
-    B, T = 6, 30
+    spec = S.blob(2, 40, 700, 24, radius_cells=6.0, v_scale=0.3, amp=2.0, dt=5e-4)
+    B, T = 6, 100  # long enough for both halves' trials (they start after 32 steps of a key)
     alone = []
     for _ in range(B):
         st, g, _ = _run(M, ctx, spec, T, int(np.ceil(np.sqrt(T))), M.TUNE_OFF)
