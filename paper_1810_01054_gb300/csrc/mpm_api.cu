@@ -178,6 +178,18 @@ ScenePar rec_fwd(const mpm_scene* s, float4* in, float4* out) {
   return p;
 }
 
+// Record of a recompute step: with workspace 2 it bins into key2, takes its actuation from act2
+// and writes its inspection grid to grid2, so it shares nothing the reverse steps write.
+ScenePar rec_rcm(const mpm_scene* s, float4* in, float4* out) {
+  ScenePar p = rec_fwd(s, in, out);
+  if (s->rcm_ws2) {
+    p.key = s->key2;
+    p.act = s->act2;
+    p.grid = s->grid2;
+  }
+  return p;
+}
+
 ScenePar rec_rev(const mpm_scene* s, float4* st, const float4* ain, float4* aout) {
   ScenePar p = s->hp;
   p.planes = st;
@@ -193,6 +205,16 @@ ScenePar rec_rev(const mpm_scene* s, float4* st, const float4* ain, float4* aout
 // The tiled form makes the step's record selection inside its first kernel (the sort here, the
 // keys in the reverse step); the plain form launches it separately.  The sort does not depend on
 // the controller, so the controller's forward runs after it.
+// Workspace of phase ph: the recompute (and the bin keys of its checkpoint) use workspace 2 when
+// the reverse tables say so; its launch shapes follow the scene's.
+BatchDev& workspace(mpm_scene* s, int ph) {
+  if ((ph == PH_RCM || ph == PH_PREP) && s->rcm_ws2) {
+    for (int k = 0; k < TK_COUNT; ++k) s->b2.launch[k] = s->b.launch[k];
+    return s->b2;
+  }
+  return s->b;
+}
+
 mpm_status enqueue_forward(mpm_scene* s, int ph, cudaStream_t st) {
   mpm_ctx* c = s->ctx;
   if (s->impl == MPM_IMPL_PLAIN) {
@@ -206,23 +228,24 @@ mpm_status enqueue_forward(mpm_scene* s, int ph, cudaStream_t st) {
     return MPM_OK;
   }
   const bool two = s->dim == 2;
+  BatchDev& b = workspace(s, ph);
   {
     ProfScope p(c, st, MPM_K_SORT);
-    CK(two ? launch_sort<2>(s->b, st, s->dsel + ph) : launch_sort<3>(s->b, st, s->dsel + ph));
+    CK(two ? launch_sort<2>(b, st, s->dsel + ph) : launch_sort<3>(b, st, s->dsel + ph));
   }
   {
     ProfScope p(c, st, MPM_K_CTRL);
-    CK(ctrl_step_forward(s->hp, s->cur, s->ctrl, st));
+    CK(ctrl_step_forward(s->hp, b.scenes, s->ctrl, st));
   }
   {
     ProfScope p(c, st, MPM_K_P2G);
     TuneScope t(s->tune, TK_P2G, st);
-    CK(two ? launch_p2g<2>(s->b, false, st) : launch_p2g<3>(s->b, false, st));
+    CK(two ? launch_p2g<2>(b, false, st) : launch_p2g<3>(b, false, st));
   }
   {
     ProfScope p(c, st, MPM_K_G2P);
     TuneScope t(s->tune, TK_G2P, st);
-    CK(two ? launch_g2p<2>(s->b, st) : launch_g2p<3>(s->b, st));
+    CK(two ? launch_g2p<2>(b, st) : launch_g2p<3>(b, st));
   }
   return MPM_OK;
 }
@@ -271,7 +294,8 @@ mpm_status enqueue_reverse(mpm_scene* s, cudaStream_t st) {
 // Bin keys and tile histogram of the state the selection of phase ph names (tiled form only).
 mpm_status enqueue_keys(mpm_scene* s, int ph, cudaStream_t st) {
   if (s->impl == MPM_IMPL_PLAIN) return MPM_OK;
-  CK(s->dim == 2 ? launch_keys<2>(s->b, st, s->dsel + ph) : launch_keys<3>(s->b, st, s->dsel + ph));
+  BatchDev& b = workspace(s, ph);
+  CK(s->dim == 2 ? launch_keys<2>(b, st, s->dsel + ph) : launch_keys<3>(b, st, s->dsel + ph));
   return MPM_OK;
 }
 
@@ -305,8 +329,9 @@ mpm_status capture(mpm_scene* s, int ph, int steps, Graph* g) {
 
 // Runs `count` steps of phase ph on the context stream: graph replays, or direct launches while
 // launch timing is on.
-mpm_status run_phase(mpm_scene* s, int ph, int count) {
+mpm_status run_phase(mpm_scene* s, int ph, int count, cudaStream_t graph_stream = nullptr) {
   mpm_ctx* c = s->ctx;
+  cudaStream_t gs = graph_stream ? graph_stream : c->stream;
   // steps that still try launch shapes run one at a time, launched directly and timed; graphs are
   // captured only once the shapes of the phase's kernels are settled
   for (; count > 0 && tune_wants(s, ph); --count) CKS(tune_step(s, ph));
@@ -319,11 +344,11 @@ mpm_status run_phase(mpm_scene* s, int ph, int count) {
   if (big > 0 && !s->graphs[ph][1].exec) CKS(capture(s, ph, GRAPH_STEPS, &s->graphs[ph][1]));
   if (small > 0 && !s->graphs[ph][0].exec) CKS(capture(s, ph, 1, &s->graphs[ph][0]));
   for (int i = 0; i < big; ++i) {
-    CK(cudaGraphLaunch(s->graphs[ph][1].exec, c->stream));
+    CK(cudaGraphLaunch(s->graphs[ph][1].exec, gs));
     count_launches(int(s->graphs[ph][1].kernels));
   }
   for (int i = 0; i < small; ++i) {
-    CK(cudaGraphLaunch(s->graphs[ph][0].exec, c->stream));
+    CK(cudaGraphLaunch(s->graphs[ph][0].exec, gs));
     count_launches(int(s->graphs[ph][0].kernels));
   }
   return MPM_OK;
@@ -336,7 +361,56 @@ void free_rollout(mpm_scene* s) {
   s->roll_allocs.clear();
   s->ckpt.clear();
   s->seg.clear();
+  s->seg2.clear();
   s->have_rollout = false;
+}
+
+// Workspace 2 (allocated on the first reverse pass that overlaps its recompute).
+mpm_status ensure_ws2(mpm_scene* s) {
+  if (s->cur2) return MPM_OK;
+  BatchDev& b = s->b2;
+  b = s->b;  // scene tables, offsets and launch shapes; the tile arrays below are its own
+  const int nt = s->hp.n_tiles, NB = block_nodes(s->dim);
+  std::vector<void*>& L = s->ws2_allocs;
+  CKS(dalloc(&s->cur2, 1, L));
+  CKS(dalloc(&s->key2, s->npad, L));
+  CKS(dalloc(&s->act2, std::max(1, s->G), L));
+  CKS(dalloc(&s->grid2, s->n_nodes, L));
+  CKS(dalloc(&b.tile_count, nt, L));
+  CKS(dalloc(&b.tile_fill, nt, L));
+  CKS(dalloc(&b.tile_start, nt + 1, L));
+  CKS(dalloc(&b.tile_slot, nt, L));
+  CKS(dalloc(&b.active, nt, L));
+  CKS(dalloc(&b.n_active, 1, L));
+  CKS(dalloc(&b.block_sums, 2 * ((nt + 2047) / 2048) + 2, L));
+  CKS(dalloc(&b.sorted, s->npad, L));
+  CKS(dalloc(&b.partial, size_t(nt) * NB, L));
+  CKS(dalloc(&b.partial_b, size_t(nt) * NB, L));
+  b.scenes = s->cur2;
+  cudaStream_t st = s->ctx->stream;
+  CK(cudaMemsetAsync(b.tile_count, 0, sizeof(uint32_t) * nt, st));
+  CK(cudaMemsetAsync(b.tile_fill, 0, sizeof(uint32_t) * nt, st));
+  CK(cudaMemsetAsync(s->act2, 0, sizeof(float) * std::max(1, s->G), st));
+  CK(cudaMemsetAsync(s->grid2, 0, sizeof(float4) * s->n_nodes, st));
+  for (int i = 0; i < 2; ++i) {
+    CK(cudaEventCreateWithFlags(&s->ev_rcm[i], cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&s->ev_rev[i], cudaEventDisableTiming));
+  }
+  CK(cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming));
+  return MPM_OK;
+}
+
+void free_ws2(mpm_scene* s) {
+  for (void* p : s->ws2_allocs) cudaFree(p);
+  s->ws2_allocs.clear();
+  s->cur2 = nullptr;
+  for (int i = 0; i < 2; ++i) {
+    if (s->ev_rcm[i]) cudaEventDestroy(s->ev_rcm[i]);
+    if (s->ev_rev[i]) cudaEventDestroy(s->ev_rev[i]);
+    s->ev_rcm[i] = s->ev_rev[i] = nullptr;
+  }
+  if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+  s->ev_fork = nullptr;
 }
 
 }  // namespace
@@ -448,6 +522,7 @@ mpm_status prepare_rollout(mpm_scene* s, int T, int k, size_t budget) {
   s->roll_k = k;
   s->roll_nseg = nseg;
   s->roll_start = s->step;
+  s->roll_budget = budget;
   return MPM_OK;
 }
 
@@ -482,16 +557,44 @@ mpm_status prepare_backward(mpm_scene* s, const float* gxT, const float* gvT, co
   }
   CK(cudaMemsetAsync(s->ctrl.gparams, 0, sizeof(float) * std::max(1, s->nparams), st));
   if (s->hp.gmat && N > 0) CK(cudaMemsetAsync(s->hp.gmat, 0, sizeof(float2) * size_t(N), st));
+  // A single scene's reverse pass recomputes segment sg-1 on the second stream while the reverse
+  // steps of segment sg run: the recompute gets workspace 2 and odd segments a second set of
+  // recompute buffers.  Not for batches (mean_x0_seed), controllers that read the state (their
+  // reduction scratch is shared), the plain form, or when the extra buffers break the budget.
+  const size_t S = s->state_bytes;
+  const bool overlap = !mean_x0_seed && s->impl == MPM_IMPL_TILED && !ctrl_reads_state(s->ctrl) && k > 1 &&
+                       nseg > 1 &&
+                       (s->roll_budget == 0 || (size_t(nseg) + 2 * size_t(k - 1)) * S <= s->roll_budget);
+  if (overlap) {
+    CKS(ensure_ws2(s));
+    if (int(s->seg2.size()) != k - 1) {
+      s->seg2.assign(k - 1, nullptr);
+      for (int i = 0; i < k - 1; ++i) CKS(dalloc(&s->seg2[i], S / sizeof(float4), s->roll_allocs));
+    }
+  }
+  if (s->graphs_ws2 != overlap) {  // recompute graphs name the workspace they were captured with
+    for (int ph : {PH_RCM, PH_PREP})
+      for (auto& g : s->graphs[ph])
+        if (g.exec) {
+          cudaGraphExecDestroy(g.exec);
+          g = Graph();
+        }
+    s->graphs_ws2 = overlap;
+  }
+  s->rcm_ws2 = overlap;
   // table 2: per segment the recompute records F_{sg,j} (state j -> j+1) and the reverse records
-  // B_{sg,n,parity} (state n, adjoint buffers by parity); maps by global step
+  // B_{sg,n,parity} (state n, adjoint buffers by parity); maps by global step.  Record 0 is a
+  // recompute record whenever a recompute runs (segment 0 then has k > 1 steps): the recompute's
+  // fused scatter reads its step-invariant fields (bin keys) there.
   std::vector<ScenePar> recs;
   std::vector<int> rcm(T, 0), rev(T, 0);
   for (int sg = 0; sg < nseg; ++sg) {
     const int L = std::min(k, T - sg * k);
-    auto segp = [&](int j) { return j == 0 ? s->ckpt[sg] : s->seg[j - 1]; };
+    const std::vector<float4*>& segs = overlap && (sg & 1) ? s->seg2 : s->seg;
+    auto segp = [&](int j) { return j == 0 ? s->ckpt[sg] : segs[j - 1]; };
     for (int j = 0; j + 1 < L; ++j) {
       rcm[sg * k + j] = int(recs.size());
-      recs.push_back(rec_fwd(s, segp(j), segp(j + 1)));
+      recs.push_back(rec_rcm(s, segp(j), segp(j + 1)));
     }
     for (int n = 0; n < L; ++n) {
       const int gstep = sg * k + n;
@@ -506,6 +609,12 @@ mpm_status prepare_backward(mpm_scene* s, const float* gxT, const float* gvT, co
   for (int ph : {PH_RCM, PH_REV, PH_PREP})
     if (s->hsel[ph].table != s->tables[2].dev) {
       s->hsel[ph].table = s->tables[2].dev;
+      sel_dirty = true;
+    }
+  float* rcm_act = overlap ? s->act2 : s->hp.act;  // the recompute's selection writes its actuation
+  for (int ph : {PH_RCM, PH_PREP})
+    if (s->hsel[ph].act != rcm_act) {
+      s->hsel[ph].act = rcm_act;
       sel_dirty = true;
     }
   if (sel_dirty) CKS(upload_sel(s));
@@ -605,12 +714,19 @@ mpm_status mpm_ctx_create(mpm_ctx** out, int device, void* cuda_stream) {
     delete c;
     return cuda_fail(e);
   }
+  e = cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(c->capture);
+    delete c;
+    return cuda_fail(e);
+  }
   if (cuda_stream) {
     c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
   } else {
     e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
       cudaStreamDestroy(c->capture);
+      cudaStreamDestroy(c->aux);
       delete c;
       return cuda_fail(e);
     }
@@ -625,8 +741,10 @@ mpm_status mpm_ctx_destroy(mpm_ctx* c) {
   if (!c) return MPM_ERR_ARG;
   if (c->live.load() != 0) return MPM_ERR_STATE;  // its scenes and batches still use its stream
   cudaStreamSynchronize(c->stream);
+  cudaStreamSynchronize(c->aux);
   for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
   cudaStreamDestroy(c->capture);
+  cudaStreamDestroy(c->aux);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
   return MPM_OK;
@@ -643,7 +761,9 @@ mpm_status mpm_scene_destroy(mpm_scene* s) {
   if (!s) return MPM_ERR_ARG;
   if (s->batch_refs > 0) return MPM_ERR_STATE;  // a batch still holds it
   cudaStreamSynchronize(s->ctx->stream);
+  cudaStreamSynchronize(s->ctx->aux);
   free_rollout(s);
+  free_ws2(s);
   invalidate_graphs(s);
   tune_release(s);
   for (void* p : s->allocs) cudaFree(p);
@@ -950,14 +1070,41 @@ mpm_status mpm_backward(mpm_scene* s, const float* gxT, const float* gvT, const 
   if (!s->have_rollout) return MPM_ERR_STATE;
   CKS(prepare_backward(s, gxT, gvT, gCT, gFT, mem_space));
   const int T = s->roll_T, k = s->roll_k, nseg = s->roll_nseg, n0 = s->roll_start;
-  for (int sg = nseg - 1; sg >= 0; --sg) {
+  mpm_ctx* c = s->ctx;
+  // recompute of segment sg (keys of its checkpoint, then its L - 1 forward steps) on stream st
+  auto recompute = [&](int sg, cudaStream_t st) -> mpm_status {
     const int L = std::min(k, T - sg * k);
-    if (L > 1) {
-      CKS(set_counter(s, s->d_step, n0 + sg * k));
-      CKS(run_phase(s, PH_PREP, 1));  // bin keys of the checkpoint the recompute starts from
-      CKS(run_phase(s, PH_RCM, L - 1));
+    if (L <= 1) return MPM_OK;
+    CK(launch_set_int(s->d_step, n0 + sg * k, st));
+    CKS(run_phase(s, PH_PREP, 1, st));  // bin keys of the checkpoint the recompute starts from
+    return run_phase(s, PH_RCM, L - 1, st);
+  };
+  const bool overlap = s->rcm_ws2 && !c->prof_mask && !tune_wants(s, PH_RCM) && !tune_wants(s, PH_REV) &&
+                       !tune_wants(s, PH_PREP);
+  if (!overlap) {
+    for (int sg = nseg - 1; sg >= 0; --sg) {
+      CKS(recompute(sg, c->stream));
+      CKS(run_phase(s, PH_REV, std::min(k, T - sg * k)));
     }
-    CKS(run_phase(s, PH_REV, L));
+    return finish_backward(s, gx0, gv0, gC0, gF0, gctrl, mem_space);
+  }
+  // Segment sg-1 is recomputed on the second stream while the reverse steps of segment sg run on
+  // the first.  Odd and even segments recompute into different buffers: a recompute waits for the
+  // reverse steps that last read its buffers, a segment's reverse steps for its recompute.
+  cudaStream_t ms = c->stream, as = c->aux;
+  CK(cudaEventRecord(s->ev_fork, ms));
+  CK(cudaStreamWaitEvent(as, s->ev_fork, 0));
+  CKS(recompute(nseg - 1, as));
+  CK(cudaEventRecord(s->ev_rcm[(nseg - 1) & 1], as));
+  for (int sg = nseg - 1; sg >= 0; --sg) {
+    if (sg >= 1) {
+      if (sg + 1 < nseg) CK(cudaStreamWaitEvent(as, s->ev_rev[(sg + 1) & 1], 0));
+      CKS(recompute(sg - 1, as));
+      CK(cudaEventRecord(s->ev_rcm[(sg - 1) & 1], as));
+    }
+    CK(cudaStreamWaitEvent(ms, s->ev_rcm[sg & 1], 0));
+    CKS(run_phase(s, PH_REV, std::min(k, T - sg * k), ms));
+    CK(cudaEventRecord(s->ev_rev[sg & 1], ms));
   }
   return finish_backward(s, gx0, gv0, gC0, gF0, gctrl, mem_space);
 }

@@ -26,6 +26,7 @@ struct mpm_ctx {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   cudaStream_t capture = nullptr;  // private stream graphs are captured on
+  cudaStream_t aux = nullptr;      // second stream: a reverse pass's segment recompute runs here
   int sm_count = 1;
   // launch timing (mpm_profile_*): event pairs around launches of the selected kinds; while a
   // mask is set, steps are launched directly (not from graphs) so every launch can be bracketed
@@ -106,6 +107,20 @@ struct mpm_scene {
   size_t scratch_bytes = 0;
   TuneState tune;
   int batch_refs = 0;  // batch slots holding the scene (admitted, not yet released)
+  // The segment recompute's own workspace (tile arrays, selected record, bin keys, actuation,
+  // grid), so that mpm_backward can run it on the context's second stream beside the reverse
+  // steps; odd segments recompute into seg2 while the reverse steps still read seg.
+  BatchDev b2{};
+  ScenePar* cur2 = nullptr;
+  uint32_t* key2 = nullptr;
+  float* act2 = nullptr;
+  float4* grid2 = nullptr;
+  std::vector<void*> ws2_allocs;
+  std::vector<float4*> seg2;
+  bool rcm_ws2 = false;     // the reverse tables send the recompute to workspace 2
+  bool graphs_ws2 = false;  // workspace the recompute graphs were captured with
+  size_t roll_budget = 0;
+  cudaEvent_t ev_rcm[2] = {}, ev_rev[2] = {}, ev_fork = nullptr;
   // while set, set_counter appends (counter, value) here instead of launching a write: the batch
   // scheduler writes the counters of all its scenes with one launch
   std::vector<std::pair<int*, int>>* ctr_sink = nullptr;
