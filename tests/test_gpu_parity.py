@@ -150,6 +150,28 @@ def test_tiled_is_bitwise_deterministic_and_checkpoint_invariant(M, ctx):
             assert np.array_equal(a, b)
 
 
+def test_recompute_beside_reverse_steps_is_bitwise_the_sequential_pass(M, ctx):
+    """The reverse pass recomputes the next segment on a second stream (own workspace, odd
+    segments in a second buffer set) unless the memory budget leaves no room for those buffers;
+    both schedules, and repeated passes reusing the captured graphs, give the same bits.  The
+    walker-size scene with the sinusoid-basis controller and uneven last segment (T = 150, k = 16)."""
+    spec = S.walker_2d(1, n_steps=150)
+    seed = mean_x0_seed(spec.n_particles, 2)
+    sc = M.Scene(ctx, spec)
+    S_bytes = sc.info()["state_bytes"]
+    T, k = 150, 16
+    nseg = (T + k - 1) // k
+    outs = []
+    for budget in (0, (nseg + k - 1) * S_bytes, 0):  # overlapped, sequential (tight budget), overlapped
+        sc.set_state(spec.x0, spec.v0, spec.C0, spec.F0, step=0)
+        sc.rollout(T, k, budget)
+        outs.append(sc.get_state() + sc.backward(seed))
+    sc.close()
+    for o in outs[1:]:
+        for a, b in zip(o, outs[0]):
+            assert np.array_equal(a, b)
+
+
 def test_plain_and_tiled_agree(M, ctx):
     spec = S.walker_square_2d(0)
     res = []
