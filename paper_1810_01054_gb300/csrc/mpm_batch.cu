@@ -4,7 +4,9 @@
 // a sub-batch through one scene table (one record per scene, selected on the device from that
 // scene's own tables and step counter, with the scene's tile and particle offsets in the batch).
 // Scenes whose next work is a forward step (rollout or segment recompute) form the forward
-// sub-batch; scenes in their reverse pass form the reverse sub-batch.  Both run every tick.  Tiles
+// sub-batch; scenes in their reverse pass form the reverse sub-batch.  Both run every tick, the
+// reverse one on the context's second stream beside the forward one (disjoint scenes, each with
+// its own tile arrays and node blocks), joined before the tick's bookkeeping.  Tiles
 // never span scenes and every sum inside a tile has a fixed order, so a scene's results are the
 // same bits alone or in any mix.
 //
@@ -46,6 +48,7 @@ struct SubBatch {
   TuneState tune;
   long long key_particles = -1, key_tiles = -1;
   int trial_wait = 0;  // steps of this key left before its trials start (0: none pending)
+  float4 *partial = nullptr, *partial_b = nullptr;  // node blocks (each half its own: they run at once)
 };
 
 // Steps a composition key must run before its launch-shape trials start: a serving mix changes
@@ -86,6 +89,8 @@ void free_sub(SubBatch& sb) {
   dfree(sb.b.block_sums);
   dfree(sb.b.sorted);
   dfree(sb.b.gpartial);
+  dfree(sb.partial);
+  dfree(sb.partial_b);
   sb.cap_scenes = sb.cap_tiles = sb.cap_particles = 0;
 }
 
@@ -99,9 +104,8 @@ struct mpm_batch {
   size_t budget = 0, used = 0;
   std::vector<Slot> slots;
   SubBatch fwd, rev;
-  float4 *partial = nullptr, *partial_b = nullptr;  // node blocks, shared by the two sub-batches
-  int cap_blocks = 0;
   bool dirty = true;
+  cudaEvent_t fork = nullptr, join = nullptr;  // the reverse half runs on the second stream
   // per-tick bookkeeping: counter writes of the scenes changing phase (one launch), the slots whose
   // request finished (one status gather), device array of the gathered status words
   std::vector<std::pair<int*, int>> pend_ctr;
@@ -136,13 +140,8 @@ mpm_status grow(mpm_batch* B, SubBatch& sb, int n_scenes, int tiles, int particl
   sb.cap_scenes = sc;
   sb.cap_tiles = tl;
   sb.cap_particles = pc;
-  if (tl > B->cap_blocks) {
-    dfree(B->partial);
-    dfree(B->partial_b);
-    CK(cudaMalloc(&B->partial, sizeof(float4) * size_t(tl) * block_nodes(B->dim)));
-    CK(cudaMalloc(&B->partial_b, sizeof(float4) * size_t(tl) * block_nodes(B->dim)));
-    B->cap_blocks = tl;
-  }
+  CK(cudaMalloc(&sb.partial, sizeof(float4) * size_t(tl) * block_nodes(B->dim)));
+  CK(cudaMalloc(&sb.partial_b, sizeof(float4) * size_t(tl) * block_nodes(B->dim)));
   return MPM_OK;
 }
 
@@ -163,10 +162,8 @@ mpm_status compose(mpm_batch* B, SubBatch& sb) {
     particles += B->slots[i].s->N;
   }
   CKS(grow(B, sb, int(sb.members.size()), tiles, particles));
-  for (SubBatch* o : {&B->fwd, &B->rev}) {  // the two sub-batches share the node blocks
-    o->b.partial = B->partial;
-    o->b.partial_b = B->partial_b;
-  }
+  sb.b.partial = sb.partial;
+  sb.b.partial_b = sb.partial_b;
   std::vector<SelectPar> sel;
   std::vector<CtrlPar> ctl;
   std::vector<int> pb(1, 0), tscene(std::max(1, tiles), 0);
@@ -237,11 +234,10 @@ mpm_status recompose(mpm_batch* B) {
 }
 
 template <int D>
-mpm_status forward_step(mpm_batch* B) {
+mpm_status forward_step(mpm_batch* B, cudaStream_t st) {
   SubBatch& sb = B->fwd;
   const int n = int(sb.members.size());
   if (n == 0) return MPM_OK;
-  cudaStream_t st = B->ctx->stream;
   CK(launch_select(sb.dsel, n, sb.cur, st));
   for (int m = 0; m < n; ++m) {
     mpm_scene* s = B->slots[sb.members[m]].s;
@@ -266,11 +262,10 @@ mpm_status forward_step(mpm_batch* B) {
 }
 
 template <int D>
-mpm_status reverse_step(mpm_batch* B) {
+mpm_status reverse_step(mpm_batch* B, cudaStream_t st) {
   SubBatch& sb = B->rev;
   const int n = int(sb.members.size());
   if (n == 0) return MPM_OK;
-  cudaStream_t st = B->ctx->stream;
   CK(launch_select(sb.dsel, n, sb.cur, st));
   CK(launch_keys<D>(sb.b, st));
   for (int m = 0; m < n; ++m) {
@@ -424,9 +419,15 @@ mpm_status mpm_batch_create(mpm_ctx* ctx, int dim, size_t mem_budget, mpm_batch*
   mpm_batch* B = new (std::nothrow) mpm_batch();
   if (!B) return MPM_ERR_OOM;
   B->ctx = ctx;
-  ctx->live.fetch_add(1);
   B->dim = dim;
   B->budget = mem_budget;
+  if (cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&B->join, cudaEventDisableTiming) != cudaSuccess) {
+    if (B->fork) cudaEventDestroy(B->fork);
+    delete B;
+    return MPM_ERR_CUDA;
+  }
+  ctx->live.fetch_add(1);
   *out = B;
   return MPM_OK;
 }
@@ -434,13 +435,14 @@ mpm_status mpm_batch_create(mpm_ctx* ctx, int dim, size_t mem_budget, mpm_batch*
 mpm_status mpm_batch_destroy(mpm_batch* B) {
   if (!B) return MPM_ERR_ARG;
   cudaStreamSynchronize(B->ctx->stream);
+  cudaStreamSynchronize(B->ctx->aux);
   for (Slot& sl : B->slots)  // the scenes of unreleased slots are the caller's again
     if (sl.state != S_FREE && sl.s) sl.s->batch_refs -= 1;
   free_sub(B->fwd);
   free_sub(B->rev);
-  dfree(B->partial);
-  dfree(B->partial_b);
   dfree(B->d_status);
+  cudaEventDestroy(B->fork);
+  cudaEventDestroy(B->join);
   B->ctx->live.fetch_sub(1);
   delete B;
   return MPM_OK;
@@ -488,13 +490,20 @@ mpm_status mpm_batch_tick(mpm_batch* B, int max_steps) {
     for (const Slot& sl : B->slots) busy = busy || sl.state == S_FWD || sl.state == S_RCM || sl.state == S_REV;
     if (!busy) break;
     if (B->dirty) CKS(recompose(B));
+    // the two halves touch disjoint scenes and buffers: the reverse half runs on the second
+    // stream beside the forward half, joined before the bookkeeping
+    cudaStream_t ms = B->ctx->stream, as = B->ctx->aux;
+    CK(cudaEventRecord(B->fork, ms));
+    CK(cudaStreamWaitEvent(as, B->fork, 0));
     if (B->dim == 2) {
-      CKS(forward_step<2>(B));
-      CKS(reverse_step<2>(B));
+      CKS(forward_step<2>(B, ms));
+      CKS(reverse_step<2>(B, as));
     } else {
-      CKS(forward_step<3>(B));
-      CKS(reverse_step<3>(B));
+      CKS(forward_step<3>(B, ms));
+      CKS(reverse_step<3>(B, as));
     }
+    CK(cudaEventRecord(B->join, as));
+    CK(cudaStreamWaitEvent(ms, B->join, 0));
     CKS(advance(B));
   }
   CK(cudaGetLastError());
