@@ -180,23 +180,32 @@ ScenePar rec_fwd(const mpm_scene* s, float4* in, float4* out) {
 
 // Record of a recompute step: with workspace 2 it bins into key2, takes its actuation from act2
 // and writes its inspection grid to grid2, so it shares nothing the reverse steps write.
-ScenePar rec_rcm(const mpm_scene* s, float4* in, float4* out) {
+ScenePar rec_rcm(const mpm_scene* s, float4* in, float4* out, uint32_t* sort_slot) {
   ScenePar p = rec_fwd(s, in, out);
   if (s->rcm_ws2) {
     p.key = s->key2;
     p.act = s->act2;
     p.grid = s->grid2;
+    p.sort_slot = sort_slot;  // where this step stores the sort of the state it reads
   }
   return p;
 }
 
-ScenePar rec_rev(const mpm_scene* s, float4* st, const float4* ain, float4* aout) {
+// Slot of the sort store for state j of segment sg (NULL without the store).
+uint32_t* sort_slot_of(const mpm_scene* s, int sg, int j) {
+  if (!s->sort_store) return nullptr;
+  const size_t w = sort_slot_words(s->npad, s->hp.n_tiles);
+  return s->sort_store + (size_t(sg & 1) * s->roll_k + j) * w;
+}
+
+ScenePar rec_rev(const mpm_scene* s, float4* st, const float4* ain, float4* aout, uint32_t* sort_slot = nullptr) {
   ScenePar p = s->hp;
   p.planes = st;
   p.planes_out = st;
   p.adj_in = ain;
   p.adj_out = aout;
   p.step_ctr = s->d_bstep;
+  p.sort_slot = sort_slot;  // where the recompute stored the sort of this state
   return p;
 }
 
@@ -232,6 +241,8 @@ mpm_status enqueue_forward(mpm_scene* s, int ph, cudaStream_t st) {
   {
     ProfScope p(c, st, MPM_K_SORT);
     CK(two ? launch_sort<2>(b, st, s->dsel + ph) : launch_sort<3>(b, st, s->dsel + ph));
+    if (ph == PH_RCM && s->rcm_ws2)  // keep the sort of this state for its reverse step
+      CK(two ? launch_store_sort<2>(b, nullptr, st) : launch_store_sort<3>(b, nullptr, st));
   }
   {
     ProfScope p(c, st, MPM_K_CTRL);
@@ -254,7 +265,11 @@ mpm_status enqueue_forward(mpm_scene* s, int ph, cudaStream_t st) {
 mpm_status enqueue_reverse(mpm_scene* s, cudaStream_t st) {
   mpm_ctx* c = s->ctx;
   const bool two = s->dim == 2;
-  if (s->impl != MPM_IMPL_PLAIN) {
+  const bool stored = s->impl != MPM_IMPL_PLAIN && s->rcm_ws2;  // the recompute kept this state's sort
+  if (stored) {
+    ProfScope p(c, st, MPM_K_SORT);
+    CK(two ? launch_load_sort<2>(s->b, s->dsel + PH_REV, st) : launch_load_sort<3>(s->b, s->dsel + PH_REV, st));
+  } else if (s->impl != MPM_IMPL_PLAIN) {
     ProfScope p(c, st, MPM_K_SORT);
     CK(two ? launch_keys<2>(s->b, st, s->dsel + PH_REV) : launch_keys<3>(s->b, st, s->dsel + PH_REV));
   } else {
@@ -269,7 +284,7 @@ mpm_status enqueue_reverse(mpm_scene* s, cudaStream_t st) {
     CK(two ? launch_plain_adjoint<2>(s->cur, s->hp, s->b.gpartial, st)
            : launch_plain_adjoint<3>(s->cur, s->hp, s->b.gpartial, st));
   } else {
-    {
+    if (!stored) {
       ProfScope p(c, st, MPM_K_SORT);
       CK(two ? launch_sort<2>(s->b, st) : launch_sort<3>(s->b, st));
     }
@@ -362,6 +377,7 @@ void free_rollout(mpm_scene* s) {
   s->ckpt.clear();
   s->seg.clear();
   s->seg2.clear();
+  s->sort_store = nullptr;
   s->have_rollout = false;
 }
 
@@ -562,18 +578,22 @@ mpm_status prepare_backward(mpm_scene* s, const float* gxT, const float* gvT, co
   // recompute buffers.  Not for batches (mean_x0_seed), controllers that read the state (their
   // reduction scratch is shared), the plain form, or when the extra buffers break the budget.
   const size_t S = s->state_bytes;
+  const size_t store_bytes = 2 * size_t(k) * sort_slot_words(s->npad, s->hp.n_tiles) * sizeof(uint32_t);
   const bool overlap = !mean_x0_seed && s->impl == MPM_IMPL_TILED && !ctrl_reads_state(s->ctrl) && k > 1 &&
                        nseg > 1 &&
-                       (s->roll_budget == 0 || (size_t(nseg) + 2 * size_t(k - 1)) * S <= s->roll_budget);
+                       (s->roll_budget == 0 ||
+                        (size_t(nseg) + 2 * size_t(k - 1)) * S + store_bytes <= s->roll_budget);
   if (overlap) {
     CKS(ensure_ws2(s));
     if (int(s->seg2.size()) != k - 1) {
       s->seg2.assign(k - 1, nullptr);
       for (int i = 0; i < k - 1; ++i) CKS(dalloc(&s->seg2[i], S / sizeof(float4), s->roll_allocs));
     }
+    // the sorts of every recomputed state, by segment parity (each reverse step loads its own)
+    if (!s->sort_store) CKS(dalloc(&s->sort_store, store_bytes / sizeof(uint32_t), s->roll_allocs));
   }
-  if (s->graphs_ws2 != overlap) {  // recompute graphs name the workspace they were captured with
-    for (int ph : {PH_RCM, PH_PREP})
+  if (s->graphs_ws2 != overlap) {  // recompute and reverse graphs name the workspace and sort path
+    for (int ph : {PH_RCM, PH_PREP, PH_REV})
       for (auto& g : s->graphs[ph])
         if (g.exec) {
           cudaGraphExecDestroy(g.exec);
@@ -594,14 +614,19 @@ mpm_status prepare_backward(mpm_scene* s, const float* gxT, const float* gvT, co
     auto segp = [&](int j) { return j == 0 ? s->ckpt[sg] : segs[j - 1]; };
     for (int j = 0; j + 1 < L; ++j) {
       rcm[sg * k + j] = int(recs.size());
-      recs.push_back(rec_rcm(s, segp(j), segp(j + 1)));
+      recs.push_back(rec_rcm(s, segp(j), segp(j + 1), sort_slot_of(s, sg, j)));
+    }
+    if (L == 1 && overlap) {  // no recompute step: the keys of the checkpoint still need its record
+      rcm[sg * k] = int(recs.size());
+      recs.push_back(rec_rcm(s, s->ckpt[sg], s->ckpt[sg], sort_slot_of(s, sg, 0)));
     }
     for (int n = 0; n < L; ++n) {
       const int gstep = sg * k + n;
       const int parity = (T - 1 - gstep) & 1;  // reverse step T-1 reads adj[0]
       rev[gstep] = int(recs.size()) + parity;
-      recs.push_back(rec_rev(s, segp(n), s->adj[0], s->adj[1]));
-      recs.push_back(rec_rev(s, segp(n), s->adj[1], s->adj[0]));
+      uint32_t* slot = overlap ? sort_slot_of(s, sg, n) : nullptr;
+      recs.push_back(rec_rev(s, segp(n), s->adj[0], s->adj[1], slot));
+      recs.push_back(rec_rev(s, segp(n), s->adj[1], s->adj[0], slot));
     }
   }
   CKS(upload_table(s, 2, recs));
@@ -1074,10 +1099,22 @@ mpm_status mpm_backward(mpm_scene* s, const float* gxT, const float* gvT, const 
   // recompute of segment sg (keys of its checkpoint, then its L - 1 forward steps) on stream st
   auto recompute = [&](int sg, cudaStream_t st) -> mpm_status {
     const int L = std::min(k, T - sg * k);
-    if (L <= 1) return MPM_OK;
+    if (L <= 1 && !s->rcm_ws2) return MPM_OK;
     CK(launch_set_int(s->d_step, n0 + sg * k, st));
     CKS(run_phase(s, PH_PREP, 1, st));  // bin keys of the checkpoint the recompute starts from
-    return run_phase(s, PH_RCM, L - 1, st);
+    if (L > 1) CKS(run_phase(s, PH_RCM, L - 1, st));
+    if (s->rcm_ws2) {
+      // the segment's last state has its keys (from the last recompute step, or the checkpoint's
+      // own for L = 1) but no scatter yet: sort it into its slot and leave the counters clear
+      BatchDev& b2 = workspace(s, PH_RCM);
+      const bool two = s->dim == 2;
+      CK(two ? launch_sort<2>(b2, st) : launch_sort<3>(b2, st));
+      uint32_t* slot = sort_slot_of(s, sg, L - 1);
+      CK(two ? launch_store_sort<2>(b2, slot, st) : launch_store_sort<3>(b2, slot, st));
+      CK(cudaMemsetAsync(b2.tile_count, 0, sizeof(uint32_t) * size_t(b2.total_tiles), st));
+      CK(cudaMemsetAsync(b2.tile_fill, 0, sizeof(uint32_t) * size_t(b2.total_tiles), st));
+    }
+    return MPM_OK;
   };
   const bool overlap = s->rcm_ws2 && !c->prof_mask && !tune_wants(s, PH_RCM) && !tune_wants(s, PH_REV) &&
                        !tune_wants(s, PH_PREP);

@@ -76,7 +76,14 @@ struct ScenePar {
   float* sig_contrib;     // [N] per-particle part of dL/da (S4 (K))
   int* status;            // first-error status word
   int* step_ctr;          // step counter the step advances (G2P) or rewinds (controller adjoint)
+  // sort store (reverse pass with the recompute beside it): a recompute step stores the sort of
+  // the state it reads here, a reverse step loads the sort of its state from here (NULL: none)
+  uint32_t* sort_slot;
 };
+
+// Words of one sort-store slot: sorted ids [npad] | bin keys [npad] | tile_start [nt + 1] |
+// tile_slot [nt] | active [nt] | n_active [1].
+inline size_t sort_slot_words(int npad, int nt) { return 2 * size_t(npad) + 3 * size_t(nt) + 2; }
 
 // Where a scene's record for the current step comes from (see k_select).
 struct SelectPar {
@@ -195,6 +202,13 @@ cudaError_t ctrl_scatter_x(const ScenePar& sp, const ScenePar* dsp, const CtrlPa
 
 // Copies every scene's record for the current step into cur[] (one block per scene).
 cudaError_t launch_select(const SelectPar* sel, int n_scenes, ScenePar* cur, cudaStream_t s);
+// Sort store of a single scene: the sort just made in b (raw tile lists, tile arrays, keys) into
+// slot `dst` (NULL: the slot named by the published record b.scenes[0]), and the sort of the
+// state the reverse selection `sel` names back into b (publishing the record, like launch_keys).
+template <int D>
+cudaError_t launch_store_sort(const BatchDev& b, uint32_t* dst, cudaStream_t s);
+template <int D>
+cudaError_t launch_load_sort(const BatchDev& b, const SelectPar* sel, cudaStream_t s);
 // Adjoint planes of the seed dL/dx_T = e_0 / N (the batched gradient requests' loss).
 cudaError_t launch_seed_mean_x0(int dim, int N, int npad, float4* planes, cudaStream_t s);
 // A list of device ints passed by value (kernel parameters hold up to INT_LIST_MAX entries).

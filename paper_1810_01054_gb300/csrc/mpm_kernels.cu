@@ -15,6 +15,7 @@
 //
 // Every floating-point sum has a fixed order, so results are bitwise reproducible run to run and
 // independent of which other scenes share the launch.
+#include <algorithm>
 #include <atomic>
 #include <cstdio>
 
@@ -415,6 +416,93 @@ __global__ void __launch_bounds__(256) k_scatter(BatchDev b, const SelectPar* __
   }
   b.sorted[start + rank] = ((k & 63u) << 26) | uint32_t(p);  // cell in tile, particle id
 }
+
+// ============================================================================ sort store
+// A reverse pass whose recompute runs beside it keeps the sort of every recomputed state: the
+// recompute copies it out right after its scatter, the reverse step copies it back instead of
+// binning and scattering again.  Single scene; slot layout of sort_slot_words.
+// The pieces of one sort: raw tile lists and bin keys (N each), tile_start (nt + 1), tile_slot,
+// active (nt each), n_active; copied from the src pointers to the dst pointers.
+struct SortRefs {
+  uint32_t *sorted, *key, *tstart;
+  int *tslot, *active, *n_active;
+};
+
+__device__ __forceinline__ SortRefs slot_refs(uint32_t* o, int np, int nt) {
+  return {o, o + np, o + 2 * np, reinterpret_cast<int*>(o + 2 * np + nt + 1),
+          reinterpret_cast<int*>(o + 2 * np + 2 * nt + 1), reinterpret_cast<int*>(o + 2 * np + 3 * nt + 1)};
+}
+
+__device__ __forceinline__ void sort_copy(const SortRefs& src, const SortRefs& dst, int N, int nt) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+    dst.sorted[i] = src.sorted[i];
+    dst.key[i] = src.key[i];
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= nt; i += stride) {
+    dst.tstart[i] = src.tstart[i];
+    if (i < nt) {
+      dst.tslot[i] = src.tslot[i];
+      dst.active[i] = src.active[i];
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *dst.n_active = *src.n_active;
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_store_sort(BatchDev b, uint32_t* dst) {
+  pdl_enter();
+  const ScenePar& sp = b.scenes[0];
+  uint32_t* slot = dst ? dst : sp.sort_slot;
+  if (!slot) return;
+  const int nt = b.total_tiles;
+  const SortRefs from{b.sorted, sp.key, b.tile_start, b.tile_slot, b.active, b.n_active};
+  sort_copy(from, slot_refs(slot, sp.npad, nt), b.total_particles, nt);
+}
+
+// Every CTA reads the selected record's slot itself; CTA 0 publishes the record and actuation.
+template <int D>
+__global__ void __launch_bounds__(256) k_load_sort(BatchDev b, const SelectPar* __restrict__ sel) {
+  pdl_enter();
+  __shared__ uint32_t* src;
+  __shared__ uint32_t* key;
+  __shared__ int np;
+  if (threadIdx.x == 0) {
+    const ScenePar& r = sel->table[selected_index(*sel, *sel->ctr)];
+    src = r.sort_slot;
+    key = r.key;
+    np = r.npad;
+  }
+  if (blockIdx.x == 0) select_publish(*sel, b.scenes);
+  __syncthreads();
+  if (!src) return;  // uniform across the CTA
+  const int nt = b.total_tiles;
+  const SortRefs to{b.sorted, key, b.tile_start, b.tile_slot, b.active, b.n_active};
+  sort_copy(slot_refs(src, np, nt), to, b.total_particles, nt);
+}
+
+template <int D>
+cudaError_t launch_store_sort(const BatchDev& b, uint32_t* dst, cudaStream_t s) {
+  const int n = std::max(b.total_particles, b.total_tiles + 1);
+  const int grid = std::max(1, std::min((n + 255) / 256, 4 * b.sm_count));
+  launch_pdl(k_store_sort<D>, dim3(grid), dim3(256), 0, s, b, dst);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t launch_load_sort(const BatchDev& b, const SelectPar* sel, cudaStream_t s) {
+  const int n = std::max(b.total_particles, b.total_tiles + 1);
+  const int grid = std::max(1, std::min((n + 255) / 256, 4 * b.sm_count));
+  launch_pdl(k_load_sort<D>, dim3(grid), dim3(256), 0, s, b, sel);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_store_sort<2>(const BatchDev&, uint32_t*, cudaStream_t);
+template cudaError_t launch_store_sort<3>(const BatchDev&, uint32_t*, cudaStream_t);
+template cudaError_t launch_load_sort<2>(const BatchDev&, const SelectPar*, cudaStream_t);
+template cudaError_t launch_load_sort<3>(const BatchDev&, const SelectPar*, cudaStream_t);
 
 // ============================================================================ P2G (tiled)
 // Phase A  canonical order of the tile's particles: by cell, then by particle id (counting sort
