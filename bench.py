@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--no-material", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-replicas", action="store_true")
+    ap.add_argument("--no-soft", action="store_true")
     ap.add_argument("--no-budget-sweep", action="store_true")
     ap.add_argument("--ncu-fp64", action="store_true",
                     help="short run for profilers: the FP64 form on a 200k-particle 3D cluster (64^3 grid), "
@@ -689,6 +690,17 @@ def run_ours(args, rank, world, local_rank):
         large = {"workload": lspec.name, "particles": lr["N"], "sim_steps": lr["T"], "value": lr["value"],
                  "value_fwd": lr["value_fwd"], "unit": UNIT, "ms_per_step": lr["tot_ms"] / args.steps,
                  "roofline": lr["roofline"], "kernel_share_of_profiled_step": lr["share"]}
+    soft = None
+    if args.workload == "walker_2d" and not args.no_soft:
+        # the 3D soft body with its MLP controller on group centroids, 500 steps, checkpoint every
+        # ceil(sqrt(500)) = 23 steps (forward+backward with recomputation)
+        sspec = workload("soft_body_3d", rank)
+        sspec = sspec.copy(ckpt_interval=int(np.ceil(np.sqrt(sspec.n_steps))))
+        sr = measure(args, sspec, rank, world, dev, stream, ctx, e2e=False, plain=False)
+        soft = {"workload": sspec.name, "particles": sr["N"], "sim_steps": sr["T"], "ckpt_interval": sr["k"],
+                "value": sr["value"], "value_fwd": sr["value_fwd"], "unit": UNIT,
+                "ms_per_step": sr["tot_ms"] / args.steps, "roofline": sr["roofline"],
+                "kernel_share_of_profiled_step": sr["share"]}
     sweep = None
     if rank == 0 and args.workload != "box_cluster_3d" and not args.no_large and not args.no_budget_sweep:
         sweep = measure_budget_sweep(args, dev, stream)
@@ -727,7 +739,7 @@ def run_ours(args, rank, world, local_rank):
         "roofline": r["roofline"], "kernel_share_of_profiled_step": r["share"],
         "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": r["gpu_launches"], "clocks": r["clocks"],
         "plain_form": r["plain"], "large_scene": large, "material": material, "serving": serving,
-        "fp64": fp64, "large_scene_budgets": sweep, "small_scene_replicas": replicas,
+        "fp64": fp64, "large_scene_budgets": sweep, "small_scene_replicas": replicas, "soft_body": soft,
     }
     print(json.dumps(line), flush=True)
 

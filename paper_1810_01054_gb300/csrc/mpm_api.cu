@@ -246,7 +246,7 @@ mpm_status enqueue_forward(mpm_scene* s, int ph, cudaStream_t st) {
   }
   {
     ProfScope p(c, st, MPM_K_CTRL);
-    CK(ctrl_step_forward(s->hp, b.scenes, s->ctrl, st));
+    CK(ctrl_step_forward(s->hp, b.scenes, &b == &s->b2 ? s->ctrl2 : s->ctrl, st));
   }
   {
     ProfScope p(c, st, MPM_K_P2G);
@@ -403,6 +403,10 @@ mpm_status ensure_ws2(mpm_scene* s) {
   CKS(dalloc(&b.partial, size_t(nt) * NB, L));
   CKS(dalloc(&b.partial_b, size_t(nt) * NB, L));
   b.scenes = s->cur2;
+  // the recompute's controller forward (group means, MLP inputs) writes its own scratch
+  s->ctrl2 = s->ctrl;
+  CKS(dalloc(&s->ctrl2.centroid, 3 * (1 + 2 * MAX_GROUPS), L));
+  CKS(dalloc(&s->ctrl2.partials, 2 * size_t(std::max(1, reduction_rows(s->N))) * RED_ROW_FLOATS, L));
   cudaStream_t st = s->ctx->stream;
   CK(cudaMemsetAsync(b.tile_count, 0, sizeof(uint32_t) * nt, st));
   CK(cudaMemsetAsync(b.tile_fill, 0, sizeof(uint32_t) * nt, st));
@@ -574,13 +578,12 @@ mpm_status prepare_backward(mpm_scene* s, const float* gxT, const float* gvT, co
   CK(cudaMemsetAsync(s->ctrl.gparams, 0, sizeof(float) * std::max(1, s->nparams), st));
   if (s->hp.gmat && N > 0) CK(cudaMemsetAsync(s->hp.gmat, 0, sizeof(float2) * size_t(N), st));
   // A single scene's reverse pass recomputes segment sg-1 on the second stream while the reverse
-  // steps of segment sg run: the recompute gets workspace 2 and odd segments a second set of
-  // recompute buffers.  Not for batches (mean_x0_seed), controllers that read the state (their
-  // reduction scratch is shared), the plain form, or when the extra buffers break the budget.
+  // steps of segment sg run: the recompute gets workspace 2 (with its own controller scratch) and
+  // odd segments a second set of recompute buffers.  Not for batches (mean_x0_seed), the plain
+  // form, or when the extra buffers break the budget.
   const size_t S = s->state_bytes;
   const size_t store_bytes = 2 * size_t(k) * sort_slot_words(s->npad, s->hp.n_tiles) * sizeof(uint32_t);
-  const bool overlap = !mean_x0_seed && s->impl == MPM_IMPL_TILED && !ctrl_reads_state(s->ctrl) && k > 1 &&
-                       nseg > 1 &&
+  const bool overlap = !mean_x0_seed && s->impl == MPM_IMPL_TILED && k > 1 && nseg > 1 &&
                        (s->roll_budget == 0 ||
                         (size_t(nseg) + 2 * size_t(k - 1)) * S + store_bytes <= s->roll_budget);
   if (overlap) {

@@ -111,6 +111,7 @@ struct mpm_scene {
   // grid), so that mpm_backward can run it on the context's second stream beside the reverse
   // steps; odd segments recompute into seg2 while the reverse steps still read seg.
   BatchDev b2{};
+  CtrlPar ctrl2{};  // the controller with its own reduction scratch (state-reading forms)
   ScenePar* cur2 = nullptr;
   uint32_t* key2 = nullptr;
   float* act2 = nullptr;

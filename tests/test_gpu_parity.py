@@ -173,6 +173,31 @@ def test_recompute_beside_reverse_steps_is_bitwise_the_sequential_pass(M, ctx):
     sc.close()
 
 
+@pytest.mark.parametrize("ctrl", ["mlp_3d", "com_2d"])
+def test_recompute_beside_reverse_steps_with_state_reading_controllers(M, ctx, ctrl):
+    """Controllers that read the state (MLP on group centroids, closed loop on group means) run
+    their forward in the recompute with scratch of their own: overlapped and sequential reverse
+    passes give the same bits."""
+    if ctrl == "mlp_3d":
+        spec = S.blob(3, 20, 1500, 71, ctrl_type=S.CTRL_MLP, n_groups=4, hidden=16, scale=5.0,
+                      radius_cells=3.5, v_scale=0.3)
+    else:
+        spec = S.blob(2, 32, 800, 72, ctrl_type=S.CTRL_COM, n_groups=3, radius_cells=5.0, v_scale=0.3)
+    seed = mean_x0_seed(spec.n_particles, spec.dim)
+    sc = M.Scene(ctx, spec)
+    S_bytes = sc.info()["state_bytes"]
+    T, k = 40, 7
+    nseg = (T + k - 1) // k
+    outs = []
+    for budget in (0, (nseg + k - 1) * S_bytes):
+        sc.set_state(spec.x0, spec.v0, spec.C0, spec.F0, step=0)
+        sc.rollout(T, k, budget)
+        outs.append(sc.get_state() + sc.backward(seed))
+    sc.close()
+    for a, b in zip(outs[1], outs[0]):
+        assert np.array_equal(a, b)
+
+
 def test_plain_and_tiled_agree(M, ctx):
     spec = S.walker_square_2d(0)
     res = []
