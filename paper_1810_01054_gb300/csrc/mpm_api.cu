@@ -381,9 +381,18 @@ void free_rollout(mpm_scene* s) {
   s->have_rollout = false;
 }
 
-// Workspace 2 (allocated on the first reverse pass that overlaps its recompute).
+void free_ws2(mpm_scene* s);
+
+// Workspace 2 (allocated on the first reverse pass that overlaps its recompute; all or nothing).
+mpm_status ensure_ws2_parts(mpm_scene* s);
 mpm_status ensure_ws2(mpm_scene* s) {
-  if (s->cur2) return MPM_OK;
+  if (s->ev_fork) return MPM_OK;  // the last thing made: the workspace is complete
+  const mpm_status st = ensure_ws2_parts(s);
+  if (st != MPM_OK) free_ws2(s);
+  return st;
+}
+
+mpm_status ensure_ws2_parts(mpm_scene* s) {
   BatchDev& b = s->b2;
   b = s->b;  // scene tables, offsets and launch shapes; the tile arrays below are its own
   const int nt = s->hp.n_tiles, NB = block_nodes(s->dim);
@@ -416,7 +425,7 @@ mpm_status ensure_ws2(mpm_scene* s) {
     CK(cudaEventCreateWithFlags(&s->ev_rcm[i], cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&s->ev_rev[i], cudaEventDisableTiming));
   }
-  CK(cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming));  // last: marks completion
   return MPM_OK;
 }
 
@@ -424,6 +433,9 @@ void free_ws2(mpm_scene* s) {
   for (void* p : s->ws2_allocs) cudaFree(p);
   s->ws2_allocs.clear();
   s->cur2 = nullptr;
+  s->key2 = nullptr;
+  s->act2 = nullptr;
+  s->grid2 = nullptr;
   for (int i = 0; i < 2; ++i) {
     if (s->ev_rcm[i]) cudaEventDestroy(s->ev_rcm[i]);
     if (s->ev_rev[i]) cudaEventDestroy(s->ev_rev[i]);
@@ -589,8 +601,9 @@ mpm_status prepare_backward(mpm_scene* s, const float* gxT, const float* gvT, co
   if (overlap) {
     CKS(ensure_ws2(s));
     if (int(s->seg2.size()) != k - 1) {
-      s->seg2.assign(k - 1, nullptr);
-      for (int i = 0; i < k - 1; ++i) CKS(dalloc(&s->seg2[i], S / sizeof(float4), s->roll_allocs));
+      std::vector<float4*> segs(k - 1, nullptr);  // the scene keeps them only once all exist
+      for (int i = 0; i < k - 1; ++i) CKS(dalloc(&segs[i], S / sizeof(float4), s->roll_allocs));
+      s->seg2 = segs;
     }
     // the sorts of every recomputed state, by segment parity (each reverse step loads its own)
     if (!s->sort_store) CKS(dalloc(&s->sort_store, store_bytes / sizeof(uint32_t), s->roll_allocs));
