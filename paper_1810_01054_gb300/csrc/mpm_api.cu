@@ -293,13 +293,29 @@ mpm_status enqueue_reverse(mpm_scene* s, cudaStream_t st) {
       TuneScope t(s->tune, TK_P2G_ADJ, st);
       CK(two ? launch_p2g<2>(s->b, true, st) : launch_p2g<3>(s->b, true, st));
     }
+    if (s->ctrl_join) {  // the previous step's controller reverse still reads the group sums
+      CK(cudaStreamWaitEvent(st, s->ev_ctrl[1], 0));
+      s->ctrl_join = false;
+    }
     {
       ProfScope p(c, st, MPM_K_ADJ_GATHER);
       TuneScope t(s->tune, TK_ADJ_GATHER, st);
       CK(two ? launch_adj_gather<2>(s->b, st) : launch_adj_gather<3>(s->b, st));
     }
   }
-  {
+  if (s->ctrl_branch) {  // the adjoint gather rewound the counter; nothing below reads the result
+    const ScenePar& hp = s->hp;
+    if (st == c->capture) {
+      CK(cudaEventRecord(s->ev_ctrl[0], st));
+      CK(cudaStreamWaitEvent(c->capture2, s->ev_ctrl[0], 0));
+      CK(ctrl_backward_open(s->ctrl, s->d_bstep, s->d_rows, hp.dt, hp.act_grad, c->capture2));
+      CK(cudaEventRecord(s->ev_ctrl[1], c->capture2));
+      s->ctrl_join = true;
+    } else {
+      ProfScope p(c, st, MPM_K_CTRL);
+      CK(ctrl_backward_open(s->ctrl, s->d_bstep, s->d_rows, hp.dt, hp.act_grad, st));
+    }
+  } else {
     ProfScope p(c, st, MPM_K_CTRL);
     CK(ctrl_step_backward(s->hp, s->cur, s->ctrl, st));
   }
@@ -327,6 +343,11 @@ mpm_status capture(mpm_scene* s, int ph, int steps, Graph* g) {
   capture_tally(&tally);
   mpm_status st = MPM_OK;
   for (int i = 0; i < steps && st == MPM_OK; ++i) st = enqueue_phase(s, ph, c->capture);
+  if (s->ctrl_join) {  // the last step's controller branch joins before the graph ends
+    const cudaError_t je = cudaStreamWaitEvent(c->capture, s->ev_ctrl[1], 0);
+    if (je != cudaSuccess && st == MPM_OK) st = cuda_fail(je);
+    s->ctrl_join = false;
+  }
   capture_tally(nullptr);
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(c->capture, &graph);
@@ -761,12 +782,20 @@ mpm_status mpm_ctx_create(mpm_ctx** out, int device, void* cuda_stream) {
     delete c;
     return cuda_fail(e);
   }
+  e = cudaStreamCreateWithFlags(&c->capture2, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(c->capture);
+    cudaStreamDestroy(c->aux);
+    delete c;
+    return cuda_fail(e);
+  }
   if (cuda_stream) {
     c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
   } else {
     e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
       cudaStreamDestroy(c->capture);
+      cudaStreamDestroy(c->capture2);
       cudaStreamDestroy(c->aux);
       delete c;
       return cuda_fail(e);
@@ -785,6 +814,7 @@ mpm_status mpm_ctx_destroy(mpm_ctx* c) {
   cudaStreamSynchronize(c->aux);
   for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
   cudaStreamDestroy(c->capture);
+  cudaStreamDestroy(c->capture2);
   cudaStreamDestroy(c->aux);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -815,6 +845,8 @@ mpm_status mpm_scene_destroy(mpm_scene* s) {
   if (s->scratch) cudaFree(s->scratch);
   for (void* q : {s->d_pE, s->d_pmass, s->d_gmat})
     if (q) cudaFree(q);
+  for (cudaEvent_t e : s->ev_ctrl)
+    if (e) cudaEventDestroy(e);
   s->ctx->live.fetch_sub(1);
   delete s;
   return MPM_OK;
@@ -1000,6 +1032,13 @@ mpm_status mpm_scene_create(mpm_ctx* c, const mpm_scene_desc* d, mpm_scene** out
   b.scene_pbase = pbase;
   b.tile_scene = tile_scene;
   default_launch(b, c->sm_count);
+  if (s->impl == MPM_IMPL_TILED && !ctrl_reads_state(cp)) {
+    ALLOC(s->d_rows, 1);
+    for (cudaEvent_t& e : s->ev_ctrl) TRY(cuda_fail(cudaEventCreateWithFlags(&e, cudaEventDisableTiming)));
+    b.rewind_ctr = s->d_bstep;
+    b.rewind_rows = s->d_rows;
+    s->ctrl_branch = true;
+  }
   cudaStream_t stream = c->stream;
   TRY(cuda_fail(cudaMemsetAsync(b.tile_count, 0, sizeof(uint32_t) * p.n_tiles, stream)));
   TRY(cuda_fail(cudaMemsetAsync(b.tile_fill, 0, sizeof(uint32_t) * p.n_tiles, stream)));

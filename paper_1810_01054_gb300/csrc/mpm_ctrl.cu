@@ -220,6 +220,44 @@ __device__ __forceinline__ int first_at_least(const int* a, int n, int key) {
   return lo;
 }
 
+// dL/da_g of one step = sum of rows [lo, hi) of the per-tile (per-block) partials, 16 fixed
+// interleaved splits per group combined in split order; into ga (shared) and act_grad.
+__device__ void ctrl_group_sums(const CtrlPar& c, int lo, int hi, float* ga, float* act_grad) {
+  __shared__ float part[16][MAX_GROUPS];
+  const int G = c.G, tid = threadIdx.x;
+  const int g = tid & (MAX_GROUPS - 1), split = tid >> 6;
+  float acc = 0.0f;
+  if (g < G)
+    for (int r = lo + split; r < hi; r += 16) acc += c.gpart[size_t(r) * MAX_GROUPS + g];
+  part[split][g] = acc;
+  __syncthreads();
+  if (tid < G) {
+    float t = 0.0f;
+    for (int k = 0; k < 16; ++k) t += part[k][tid];
+    ga[tid] = t;
+    act_grad[tid] = t;
+  }
+  __syncthreads();
+}
+
+// Parameter adjoint of the forms that read no state, step n at time t: sinusoid amplitude (type 0),
+// sinusoid basis (type 1), per-step table (type 3).
+__device__ void ctrl_open_params(const CtrlPar& c, int n, float t, const float* ga) {
+  const int G = c.G, tid = threadIdx.x;
+  if (c.type == 0) {
+    if (tid < G) c.gparams[tid] += ga[tid] * sinf(kTwoPi * c.freq * t);
+  } else if (c.type == 3) {  // table: dL/dU[n][g] = dL/da_g(t_n)
+    if (tid < G && n >= 0 && n < c.hidden) c.gparams[size_t(n) * G + tid] += ga[tid];
+  } else if (c.type == 1) {
+    if (tid < G * 4) {
+      const int g = tid / 4, j = tid - 4 * g;
+      const float w = kTwoPi * c.freq * t;
+      const float bs[4] = {sinf(w), cosf(w), sinf(2.0f * w), cosf(2.0f * w)};
+      c.gparams[tid] += ga[g] * bs[j];
+    }
+  }
+}
+
 __device__ void ctrl_backward_body(const ScenePar& sp, const CtrlPar& c) {
   __shared__ float ga[MAX_GROUPS], z[MAX_GROUPS * 3], h1[MAX_HIDDEN], h2[MAX_HIDDEN], o3[MAX_GROUPS];
   __shared__ float gu3[MAX_GROUPS], gu2[MAX_HIDDEN], gu1[MAX_HIDDEN];
@@ -227,11 +265,8 @@ __device__ void ctrl_backward_body(const ScenePar& sp, const CtrlPar& c) {
   const int n = *step_ctr;
   const float t = float(n) * sp.dt;
   const int G = c.G, tid = threadIdx.x;
-  // dL/da_g = sum of the per-tile (per-block) partials of this scene, rows in order, 16 fixed
-  // interleaved splits per group combined in split order
   {
-    __shared__ float part[16][MAX_GROUPS];
-    __shared__ int range[2];
+    __shared__ int range[2];  // this scene's rows
     if (tid < 32) {
       int lo = 0, hi = c.plain_rows;
       if (c.active) {
@@ -249,24 +284,10 @@ __device__ void ctrl_backward_body(const ScenePar& sp, const CtrlPar& c) {
       }
     }
     __syncthreads();
-    const int g = tid & (MAX_GROUPS - 1), split = tid >> 6;
-    float acc = 0.0f;
-    if (g < G)
-      for (int r = range[0] + split; r < range[1]; r += 16) acc += c.gpart[size_t(r) * MAX_GROUPS + g];
-    part[split][g] = acc;
-    __syncthreads();
-    if (tid < G) {
-      float t = 0.0f;
-      for (int k = 0; k < 16; ++k) t += part[k][tid];
-      ga[tid] = t;
-      sp.act_grad[tid] = t;
-    }
-    __syncthreads();
+    ctrl_group_sums(c, range[0], range[1], ga, sp.act_grad);
   }
-  if (c.type == 0) {
-    if (tid < G) c.gparams[tid] += ga[tid] * sinf(kTwoPi * c.freq * t);
-  } else if (c.type == 3) {  // table: dL/dU[n][g] = dL/da_g(t_n)
-    if (tid < G && n >= 0 && n < c.hidden) c.gparams[size_t(n) * G + tid] += ga[tid];
+  if (c.type == 0 || c.type == 1 || c.type == 3) {
+    ctrl_open_params(c, n, t, ga);
   } else if (c.type == 4) {  // closed loop: z of this step from the forward replay in c.centroid
     const int dim = c.dim, Z = dim * (1 + 2 * G);
     __shared__ float gu4[MAX_GROUPS];
@@ -287,13 +308,6 @@ __device__ void ctrl_backward_body(const ScenePar& sp, const CtrlPar& c) {
         c.gparams[tid] += sacc;
       else
         c.gz[tid - dim] = sacc;  // [c_g part (G*dim)][u_g part (G*dim)]
-    }
-  } else if (c.type == 1) {
-    if (tid < G * 4) {
-      const int g = tid / 4, j = tid - 4 * g;
-      const float w = kTwoPi * c.freq * t;
-      const float bs[4] = {sinf(w), cosf(w), sinf(2.0f * w), cosf(2.0f * w)};
-      c.gparams[tid] += ga[g] * bs[j];
     }
   } else {
     const int dim = c.dim, Z = G * dim, H = c.hidden;
@@ -362,6 +376,19 @@ __device__ void ctrl_backward_body(const ScenePar& sp, const CtrlPar& c) {
 __global__ void __launch_bounds__(1024) k_ctrl_backward(const ScenePar* __restrict__ dsp, CtrlPar c) {
   pdl_enter();
   ctrl_backward_body(*dsp, c);
+}
+
+// Reverse of a form that reads no state for one step of a scene alone: the adjoint gather of the
+// step rewound the counter to n - 1 and kept the step's active-slot count in *rows.  Reads no scene
+// record, so it may run while the next reverse step selects and publishes its own.
+__global__ void __launch_bounds__(1024) k_ctrl_backward_open(CtrlPar c, const int* __restrict__ ctr,
+                                                             const int* __restrict__ rows, float dt,
+                                                             float* act_grad) {
+  pdl_enter();
+  __shared__ float ga[MAX_GROUPS];
+  const int n = *ctr + 1;
+  ctrl_group_sums(c, 0, *rows, ga, act_grad);
+  ctrl_open_params(c, n, float(n) * dt, ga);
 }
 
 // One block per scene of a batch: scene i uses cur[i] and cs[i].
@@ -437,6 +464,13 @@ cudaError_t ctrl_step_forward(const ScenePar& sp, const ScenePar* dsp, const Ctr
   else
     launch_pdl(k_ctrl_forward, dim3(1), dim3(1024), 0, s, dsp, c, c.partials, rows);
   count_launches(n + 1);
+  return cudaGetLastError();
+}
+
+cudaError_t ctrl_backward_open(const CtrlPar& c, const int* ctr, const int* rows, float dt, float* act_grad,
+                               cudaStream_t s) {
+  launch_pdl(k_ctrl_backward_open, dim3(1), dim3(1024), 0, s, c, ctr, rows, dt, act_grad);
+  count_launches(1);
   return cudaGetLastError();
 }
 

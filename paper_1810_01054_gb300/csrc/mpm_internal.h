@@ -131,6 +131,11 @@ struct BatchDev {
   int has_material;             // some scene has per-particle material (gmat): material gradients
   int sm_count;                 // SMs of the device
   TileLaunch launch[TK_COUNT];  // launch shape of each tile kernel
+  // A scene alone whose controller reads no state: CTA 0 of the adjoint gather rewinds its reverse
+  // step counter (instead of the controller reverse) and keeps the step's active-slot count in
+  // rewind_rows, so the controller reverse can run beside the next reverse step (null: off).
+  int* rewind_ctr;
+  int* rewind_rows;
 };
 
 // Sets every tile kernel of b to the default launch shape.
@@ -196,6 +201,11 @@ constexpr int RED_ROW_FLOATS = MAX_GROUPS * 3 + 3;  // floats per partial row
 // the step *sp.step_ctr, which it then decrements.
 cudaError_t ctrl_step_forward(const ScenePar& sp, const ScenePar* dsp, const CtrlPar& c, cudaStream_t s);
 cudaError_t ctrl_step_backward(const ScenePar& sp, const ScenePar* dsp, const CtrlPar& c, cudaStream_t s);
+// Reverse of a controller that reads no state (sinusoid and table forms) for the step after the
+// one *ctr names, whose group sums are rows [0, *rows) of c.gpart: the counter was already rewound
+// by the adjoint gather (BatchDev::rewind_ctr), so the launch depends on nothing but that kernel.
+cudaError_t ctrl_backward_open(const CtrlPar& c, const int* ctr, const int* rows, float dt, float* act_grad,
+                               cudaStream_t s);
 // Batched form: one block per scene; records and controllers are device arrays of n entries.
 cudaError_t ctrl_backward_batched(const ScenePar* cur, const CtrlPar* cs, int n, cudaStream_t s);
 cudaError_t ctrl_scatter_x(const ScenePar& sp, const ScenePar* dsp, const CtrlPar& c, cudaStream_t s);

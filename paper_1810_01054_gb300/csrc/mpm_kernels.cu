@@ -1465,6 +1465,10 @@ __global__ void __launch_bounds__(kAdjThreads<D>, 512 / kAdjThreads<D>) k_adj_ga
   __shared__ float wpart[8][MAX_GROUPS];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n_active = *b.n_active;
+  if (b.rewind_ctr && blockIdx.x == 0 && tid == 0) {
+    *b.rewind_rows = n_active;
+    *b.rewind_ctr -= 1;
+  }
   for (int slot = blockIdx.x; slot < n_active; slot += gridDim.x) {
     const int gt = b.active[slot];
     const ScenePar& sp = b.scenes[b.tile_scene[gt]];

@@ -27,6 +27,7 @@ struct mpm_ctx {
   bool own_stream = false;
   cudaStream_t capture = nullptr;  // private stream graphs are captured on
   cudaStream_t aux = nullptr;      // second stream: a reverse pass's segment recompute runs here
+  cudaStream_t capture2 = nullptr; // branch of a capture: an open-loop controller's reverse
   int sm_count = 1;
   // launch timing (mpm_profile_*): event pairs around launches of the selected kinds; while a
   // mask is set, steps are launched directly (not from graphs) so every launch can be bracketed
@@ -123,6 +124,13 @@ struct mpm_scene {
   bool graphs_ws2 = false;  // workspace the recompute graphs were captured with
   size_t roll_budget = 0;
   cudaEvent_t ev_rcm[2] = {}, ev_rev[2] = {}, ev_fork = nullptr;
+  // Reverse graphs of a tiled scene whose controller reads no state: each step's controller
+  // reverse is captured on a branch (ctx->capture2) that the next step's adjoint gather joins, so it
+  // runs beside that step's sort and adjoint scatter (BatchDev::rewind_ctr).
+  bool ctrl_branch = false;
+  bool ctrl_join = false;          // a branch is captured and not yet joined
+  int* d_rows = nullptr;           // active-slot count of the last adjoint gather
+  cudaEvent_t ev_ctrl[2] = {};     // fork, join
   // while set, set_counter appends (counter, value) here instead of launching a write: the batch
   // scheduler writes the counters of all its scenes with one launch
   std::vector<std::pair<int*, int>>* ctr_sink = nullptr;

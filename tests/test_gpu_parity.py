@@ -173,6 +173,37 @@ def test_recompute_beside_reverse_steps_is_bitwise_the_sequential_pass(M, ctx):
     sc.close()
 
 
+@pytest.mark.parametrize("ctrl", ["basis_2d", "table_3d"])
+def test_controller_reverse_beside_next_step_is_bitwise_the_serial_pass(M, ctx, ctrl):
+    """Controllers that read no state (sinusoid basis, per-step table) have their reverse captured
+    on a branch of the reverse graphs, beside the next step's sort and adjoint scatter; with launch
+    timing on, the same steps are launched one after another on one stream.  Both give the same
+    bits (T = 50, k = 16: segments replayed as 8-step and single-step graphs)."""
+    if ctrl == "basis_2d":
+        spec = S.walker_2d(1, n_steps=50)
+    else:
+        spec = S.blob(3, 16, 1200, 73, ctrl_type=S.CTRL_TABLE, n_groups=3, hidden=40, amp=3.0,
+                      radius_cells=3.0, v_scale=0.3)
+    seed = mean_x0_seed(spec.n_particles, spec.dim)
+    T, k = 50, 16
+    sc = M.Scene(ctx, spec)
+    outs = []
+    for direct in (False, True, False):
+        if direct:
+            ctx.profile_start([M.K_CTRL])
+        sc.set_state(spec.x0, spec.v0, spec.C0, spec.F0, step=0)
+        sc.rollout(T, k)
+        outs.append(sc.get_state() + sc.backward(seed))
+        if direct:
+            assert ctx.profile_read(M.K_CTRL)[0] >= T  # the steps were launched directly
+            ctx.profile_start([])
+    sc.close()
+    assert np.abs(outs[0][-1]).max() > 0
+    for o in outs[1:]:
+        for a, b in zip(o, outs[0]):
+            assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("ctrl", ["mlp_3d", "com_2d"])
 def test_recompute_beside_reverse_steps_with_state_reading_controllers(M, ctx, ctrl):
     """Controllers that read the state (MLP on group centroids, closed loop on group means) run
