@@ -107,7 +107,24 @@ mpm_status ensure_scratch(mpm_scene* s, size_t bytes) {
 
 // The selection of every phase points at tables and maps through device SelectPar records, so
 // graphs captured once stay valid when tables or maps are re-uploaded or grown.
+// The branch loads' selections follow the reverse phase's (table, map), stepping back from the
+// graph's first step; set B publishes its own bin keys and actuation.  True if they changed.
+bool refresh_branch_sel(mpm_scene* s) {
+  if (!s->d_gstep) return false;
+  SelectPar a = s->hsel[PH_REV];
+  a.ctr = s->d_gstep;
+  SelectPar b = a;
+  b.act = b.act_rec = s->actB;
+  b.key_rec = s->keyB;
+  const bool same = std::memcmp(&a, &s->hsel[SEL_LOAD_A], sizeof(a)) == 0 &&
+                    std::memcmp(&b, &s->hsel[SEL_LOAD_B], sizeof(b)) == 0;
+  s->hsel[SEL_LOAD_A] = a;
+  s->hsel[SEL_LOAD_B] = b;
+  return !same;
+}
+
 mpm_status upload_sel(mpm_scene* s) {
+  refresh_branch_sel(s);
   CK(cudaStreamSynchronize(s->ctx->stream));
   CK(cudaMemcpy(s->dsel, s->hsel, sizeof(s->hsel), cudaMemcpyHostToDevice));
   return MPM_OK;
@@ -241,7 +258,9 @@ mpm_status enqueue_forward(mpm_scene* s, int ph, cudaStream_t st) {
   {
     ProfScope p(c, st, MPM_K_SORT);
     CK(two ? launch_sort<2>(b, st, s->dsel + ph) : launch_sort<3>(b, st, s->dsel + ph));
-    if (ph == PH_RCM && s->rcm_ws2)  // keep the sort of this state for its reverse step
+    // keep the sort of this state for its reverse step (before P2G rewrites the tile lists in
+    // canonical order without their cell tags)
+    if (ph == PH_RCM && s->rcm_ws2)
       CK(two ? launch_store_sort<2>(b, nullptr, st) : launch_store_sort<3>(b, nullptr, st));
   }
   {
@@ -257,6 +276,45 @@ mpm_status enqueue_forward(mpm_scene* s, int ph, cudaStream_t st) {
     ProfScope p(c, st, MPM_K_G2P);
     TuneScope t(s->tune, TK_G2P, st);
     CK(two ? launch_g2p<2>(b, st) : launch_g2p<3>(b, st));
+  }
+  return MPM_OK;
+}
+
+// Adjoint scatter and gather of a tiled reverse step reading buffer set b, then the controller
+// reverse: in line, or (open-loop forms, while capturing) on a branch that the next step's adjoint
+// gather joins.
+mpm_status enqueue_adjoint(mpm_scene* s, BatchDev& b, cudaStream_t st) {
+  mpm_ctx* c = s->ctx;
+  const bool two = s->dim == 2;
+  {
+    ProfScope p(c, st, MPM_K_P2G_ADJ);
+    TuneScope t(s->tune, TK_P2G_ADJ, st);
+    CK(two ? launch_p2g<2>(b, true, st) : launch_p2g<3>(b, true, st));
+  }
+  if (s->ctrl_join) {  // the previous step's controller reverse still reads the group sums
+    CK(cudaStreamWaitEvent(st, s->ev_ctrl[1], 0));
+    s->ctrl_join = false;
+  }
+  {
+    ProfScope p(c, st, MPM_K_ADJ_GATHER);
+    TuneScope t(s->tune, TK_ADJ_GATHER, st);
+    CK(two ? launch_adj_gather<2>(b, st) : launch_adj_gather<3>(b, st));
+  }
+  if (s->ctrl_branch) {  // the adjoint gather rewound the counter; nothing below reads the result
+    const ScenePar& hp = s->hp;
+    if (st == c->capture) {
+      CK(cudaEventRecord(s->ev_ctrl[0], st));
+      CK(cudaStreamWaitEvent(c->capture2, s->ev_ctrl[0], 0));
+      CK(ctrl_backward_open(s->ctrl, s->d_bstep, s->d_rows, hp.dt, hp.act_grad, c->capture2));
+      CK(cudaEventRecord(s->ev_ctrl[1], c->capture2));
+      s->ctrl_join = true;
+    } else {
+      ProfScope p(c, st, MPM_K_CTRL);
+      CK(ctrl_backward_open(s->ctrl, s->d_bstep, s->d_rows, hp.dt, hp.act_grad, st));
+    }
+  } else {
+    ProfScope p(c, st, MPM_K_CTRL);
+    CK(ctrl_step_backward(s->hp, s->cur, s->ctrl, st));
   }
   return MPM_OK;
 }
@@ -280,44 +338,68 @@ mpm_status enqueue_reverse(mpm_scene* s, cudaStream_t st) {
     CK(ctrl_step_forward(s->hp, s->cur, s->ctrl, st));
   }
   if (s->impl == MPM_IMPL_PLAIN) {
-    ProfScope p(c, st, MPM_K_PLAIN);
-    CK(two ? launch_plain_adjoint<2>(s->cur, s->hp, s->b.gpartial, st)
-           : launch_plain_adjoint<3>(s->cur, s->hp, s->b.gpartial, st));
-  } else {
-    if (!stored) {
-      ProfScope p(c, st, MPM_K_SORT);
-      CK(two ? launch_sort<2>(s->b, st) : launch_sort<3>(s->b, st));
-    }
     {
-      ProfScope p(c, st, MPM_K_P2G_ADJ);
-      TuneScope t(s->tune, TK_P2G_ADJ, st);
-      CK(two ? launch_p2g<2>(s->b, true, st) : launch_p2g<3>(s->b, true, st));
+      ProfScope p(c, st, MPM_K_PLAIN);
+      CK(two ? launch_plain_adjoint<2>(s->cur, s->hp, s->b.gpartial, st)
+             : launch_plain_adjoint<3>(s->cur, s->hp, s->b.gpartial, st));
     }
-    if (s->ctrl_join) {  // the previous step's controller reverse still reads the group sums
-      CK(cudaStreamWaitEvent(st, s->ev_ctrl[1], 0));
-      s->ctrl_join = false;
-    }
-    {
-      ProfScope p(c, st, MPM_K_ADJ_GATHER);
-      TuneScope t(s->tune, TK_ADJ_GATHER, st);
-      CK(two ? launch_adj_gather<2>(s->b, st) : launch_adj_gather<3>(s->b, st));
-    }
-  }
-  if (s->ctrl_branch) {  // the adjoint gather rewound the counter; nothing below reads the result
-    const ScenePar& hp = s->hp;
-    if (st == c->capture) {
-      CK(cudaEventRecord(s->ev_ctrl[0], st));
-      CK(cudaStreamWaitEvent(c->capture2, s->ev_ctrl[0], 0));
-      CK(ctrl_backward_open(s->ctrl, s->d_bstep, s->d_rows, hp.dt, hp.act_grad, c->capture2));
-      CK(cudaEventRecord(s->ev_ctrl[1], c->capture2));
-      s->ctrl_join = true;
-    } else {
-      ProfScope p(c, st, MPM_K_CTRL);
-      CK(ctrl_backward_open(s->ctrl, s->d_bstep, s->d_rows, hp.dt, hp.act_grad, st));
-    }
-  } else {
     ProfScope p(c, st, MPM_K_CTRL);
     CK(ctrl_step_backward(s->hp, s->cur, s->ctrl, st));
+    return MPM_OK;
+  }
+  if (!stored) {
+    ProfScope p(c, st, MPM_K_SORT);
+    CK(two ? launch_sort<2>(s->b, st) : launch_sort<3>(s->b, st));
+  }
+  return enqueue_adjoint(s, s->b, st);
+}
+
+// True when the reverse graphs load the sorts on a branch (stored sorts, open-loop controller,
+// buffer set B allocated).
+bool load_branch(const mpm_scene* s) { return s->rcm_ws2 && s->ctrl_branch && s->d_gstep; }
+
+// `steps` reverse steps captured on ctx->capture with the sort loads on ctx->capture3: the first
+// step loads its sort in line (and keeps its step number n in d_gstep); the load of step j >= 1
+// (state n - j, buffer set A for even j, B for odd j) waits for the adjoint gather of step j - 2,
+// the last reader of that set, and step j's adjoint scatter waits for its load.  So each load runs
+// beside the two steps before it.  The controller reads no state (ctrl_forward launches nothing).
+mpm_status capture_reverse_branched(mpm_scene* s, int steps) {
+  mpm_ctx* c = s->ctx;
+  cudaStream_t st = c->capture, br = c->capture3;
+  const bool two = s->dim == 2;
+  BatchDev sets[2] = {s->b, s->b};  // set B: the scene's batch with its own sort arrays and record
+  const BatchDev& bb = s->bB;
+  sets[1].scenes = bb.scenes;
+  sets[1].tile_start = bb.tile_start;
+  sets[1].tile_slot = bb.tile_slot;
+  sets[1].active = bb.active;
+  sets[1].n_active = bb.n_active;
+  sets[1].sorted = bb.sorted;
+  auto set = [&](int j) -> BatchDev& { return sets[j & 1]; };
+  auto load = [&](int j, cudaStream_t on) -> mpm_status {
+    const SelectPar* q = s->dsel + (j == 0 ? PH_REV : (j & 1) ? SEL_LOAD_B : SEL_LOAD_A);
+    int* snap = j == 0 ? s->d_gstep : nullptr;
+    const int back = j == 0 ? 0 : j;
+    BatchDev& b = set(j);
+    CK(two ? launch_load_sort<2>(b, q, on, back, snap) : launch_load_sort<3>(b, q, on, back, snap));
+    return MPM_OK;
+  };
+  CKS(load(0, st));
+  if (steps > 1) {
+    CK(cudaEventRecord(s->ev_load[2], st));
+    CK(cudaStreamWaitEvent(br, s->ev_load[2], 0));
+    CKS(load(1, br));
+    CK(cudaEventRecord(s->ev_load[1], br));
+  }
+  for (int j = 0; j < steps; ++j) {
+    if (j > 0) CK(cudaStreamWaitEvent(st, s->ev_load[j & 1], 0));
+    CKS(enqueue_adjoint(s, set(j), st));
+    if (j + 2 < steps) {
+      CK(cudaEventRecord(s->ev_gather, st));
+      CK(cudaStreamWaitEvent(br, s->ev_gather, 0));
+      CKS(load(j + 2, br));
+      CK(cudaEventRecord(s->ev_load[j & 1], br));
+    }
   }
   return MPM_OK;
 }
@@ -342,7 +424,10 @@ mpm_status capture(mpm_scene* s, int ph, int steps, Graph* g) {
   CK(cudaStreamBeginCapture(c->capture, cudaStreamCaptureModeThreadLocal));
   capture_tally(&tally);
   mpm_status st = MPM_OK;
-  for (int i = 0; i < steps && st == MPM_OK; ++i) st = enqueue_phase(s, ph, c->capture);
+  if (ph == PH_REV && load_branch(s))
+    st = capture_reverse_branched(s, steps);
+  else
+    for (int i = 0; i < steps && st == MPM_OK; ++i) st = enqueue_phase(s, ph, c->capture);
   if (s->ctrl_join) {  // the last step's controller branch joins before the graph ends
     const cudaError_t je = cudaStreamWaitEvent(c->capture, s->ev_ctrl[1], 0);
     if (je != cudaSuccess && st == MPM_OK) st = cuda_fail(je);
@@ -446,6 +531,23 @@ mpm_status ensure_ws2_parts(mpm_scene* s) {
     CK(cudaEventCreateWithFlags(&s->ev_rcm[i], cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&s->ev_rev[i], cudaEventDisableTiming));
   }
+  if (s->ctrl_branch) {  // buffer set B of the reverse steps whose sorts load on a branch
+    BatchDev& bb = s->bB;  // only its sort arrays and record are used
+    bb = BatchDev{};
+    CKS(dalloc(&s->curB, 1, L));
+    CKS(dalloc(&s->keyB, s->npad, L));
+    CKS(dalloc(&s->actB, std::max(1, s->G), L));
+    CKS(dalloc(&s->d_gstep, 1, L));
+    CKS(dalloc(&bb.tile_start, nt + 1, L));
+    CKS(dalloc(&bb.tile_slot, nt, L));
+    CKS(dalloc(&bb.active, nt, L));
+    CKS(dalloc(&bb.n_active, 1, L));
+    CKS(dalloc(&bb.sorted, s->npad, L));
+    bb.scenes = s->curB;
+    CK(cudaMemsetAsync(s->actB, 0, sizeof(float) * std::max(1, s->G), st));
+    for (cudaEvent_t& e : s->ev_load) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&s->ev_gather, cudaEventDisableTiming));
+  }
   CK(cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming));  // last: marks completion
   return MPM_OK;
 }
@@ -464,6 +566,16 @@ void free_ws2(mpm_scene* s) {
   }
   if (s->ev_fork) cudaEventDestroy(s->ev_fork);
   s->ev_fork = nullptr;
+  s->curB = nullptr;
+  s->keyB = nullptr;
+  s->actB = nullptr;
+  s->d_gstep = nullptr;
+  for (cudaEvent_t& e : s->ev_load) {
+    if (e) cudaEventDestroy(e);
+    e = nullptr;
+  }
+  if (s->ev_gather) cudaEventDestroy(s->ev_gather);
+  s->ev_gather = nullptr;
 }
 
 }  // namespace
@@ -679,6 +791,7 @@ mpm_status prepare_backward(mpm_scene* s, const float* gxT, const float* gvT, co
       s->hsel[ph].act = rcm_act;
       sel_dirty = true;
     }
+  if (refresh_branch_sel(s)) sel_dirty = true;
   if (sel_dirty) CKS(upload_sel(s));
   CKS(upload_map(s, 1, rcm, n0));
   CKS(upload_map(s, 2, rev, n0));
@@ -789,6 +902,14 @@ mpm_status mpm_ctx_create(mpm_ctx** out, int device, void* cuda_stream) {
     delete c;
     return cuda_fail(e);
   }
+  e = cudaStreamCreateWithFlags(&c->capture3, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(c->capture);
+    cudaStreamDestroy(c->capture2);
+    cudaStreamDestroy(c->aux);
+    delete c;
+    return cuda_fail(e);
+  }
   if (cuda_stream) {
     c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
   } else {
@@ -796,6 +917,7 @@ mpm_status mpm_ctx_create(mpm_ctx** out, int device, void* cuda_stream) {
     if (e != cudaSuccess) {
       cudaStreamDestroy(c->capture);
       cudaStreamDestroy(c->capture2);
+      cudaStreamDestroy(c->capture3);
       cudaStreamDestroy(c->aux);
       delete c;
       return cuda_fail(e);
@@ -815,6 +937,7 @@ mpm_status mpm_ctx_destroy(mpm_ctx* c) {
   for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
   cudaStreamDestroy(c->capture);
   cudaStreamDestroy(c->capture2);
+  cudaStreamDestroy(c->capture3);
   cudaStreamDestroy(c->aux);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -961,7 +1084,7 @@ mpm_status mpm_scene_create(mpm_ctx* c, const mpm_scene_desc* d, mpm_scene** out
   ALLOC(s->d_bstep, 1);
   ALLOC(s->d_status, 1);
   ALLOC(s->cur, 1);
-  ALLOC(s->dsel, PH_COUNT);
+  ALLOC(s->dsel, SEL_COUNT);
   p.planes = p.planes_out = s->state;
   p.key = key;
   p.grid = grid;

@@ -97,6 +97,10 @@ struct SelectPar {
   float freq, dt;
   const float* params;
   float* act;
+  // non-NULL: the published record's bin keys and actuation are these instead of the table's (a
+  // second set of reverse-step buffers, so the next step's sort can be loaded beside this one)
+  uint32_t* key_rec;
+  float* act_rec;
 };
 
 // Tile kernels whose launch shape (CTAs per SM of the persistent grid, threads per CTA) is
@@ -215,10 +219,12 @@ cudaError_t launch_select(const SelectPar* sel, int n_scenes, ScenePar* cur, cud
 // Sort store of a single scene: the sort just made in b (raw tile lists, tile arrays, keys) into
 // slot `dst` (NULL: the slot named by the published record b.scenes[0]), and the sort of the
 // state the reverse selection `sel` names back into b (publishing the record, like launch_keys).
+// The load selects step *sel->ctr - back; with `snap` it also writes that step number there.
 template <int D>
 cudaError_t launch_store_sort(const BatchDev& b, uint32_t* dst, cudaStream_t s);
 template <int D>
-cudaError_t launch_load_sort(const BatchDev& b, const SelectPar* sel, cudaStream_t s);
+cudaError_t launch_load_sort(const BatchDev& b, const SelectPar* sel, cudaStream_t s, int back = 0,
+                             int* snap = nullptr);
 // Adjoint planes of the seed dL/dx_T = e_0 / N (the batched gradient requests' loss).
 cudaError_t launch_seed_mean_x0(int dim, int N, int npad, float4* planes, cudaStream_t s);
 // A list of device ints passed by value (kernel parameters hold up to INT_LIST_MAX entries).

@@ -154,19 +154,32 @@ __device__ __forceinline__ float particle_G(const Part<D>& q, const ScenePar& sp
 // words, the offsets in place of the copied ones).
 __device__ __forceinline__ int selected_index(const SelectPar& q, int n) { return q.map ? q.map[n - q.base] : 0; }
 
+// Word i of pointer v (little-endian halves).
+__device__ __forceinline__ int ptr_word(const void* v, int i) {
+  const unsigned long long u = reinterpret_cast<unsigned long long>(v);
+  return int(uint32_t(i ? u >> 32 : u));
+}
+
 __device__ __forceinline__ void select_copy(const SelectPar& q, int n, ScenePar* dst) {
   const int* src = reinterpret_cast<const int*>(q.table + selected_index(q, n));
   int* d = reinterpret_cast<int*>(dst);
   constexpr int W = int(sizeof(ScenePar) / sizeof(int));
   constexpr int TB = int(offsetof(ScenePar, tile_base) / sizeof(int));
   constexpr int PB = int(offsetof(ScenePar, pbase) / sizeof(int));
-  for (int i = threadIdx.x; i < W; i += blockDim.x) d[i] = i == TB ? q.tile_base : (i == PB ? q.pbase : src[i]);
+  constexpr int KO = int(offsetof(ScenePar, key) / sizeof(int));
+  constexpr int AO = int(offsetof(ScenePar, act) / sizeof(int));
+  static_assert(offsetof(ScenePar, key) % 8 == 0 && offsetof(ScenePar, act) % 8 == 0, "pointer words");
+  for (int i = threadIdx.x; i < W; i += blockDim.x) {
+    int v = i == TB ? q.tile_base : (i == PB ? q.pbase : src[i]);
+    if (q.key_rec && (i == KO || i == KO + 1)) v = ptr_word(q.key_rec, i - KO);
+    if (q.act_rec && (i == AO || i == AO + 1)) v = ptr_word(q.act_rec, i - AO);
+    d[i] = v;
+  }
 }
 
-// The step's selection for one scene: its record into cur, and the sinusoid and table
+// The selection of step n for one scene: its record into cur, and the sinusoid and table
 // controllers' actuation a_g(t_n) into q.act.
-__device__ __forceinline__ void select_publish(const SelectPar& q, ScenePar* cur) {
-  const int n = *q.ctr;
+__device__ __forceinline__ void select_publish_at(const SelectPar& q, int n, ScenePar* cur) {
   select_copy(q, n, cur);
   const float tt = float(n) * q.dt;
   const int g = threadIdx.x;
@@ -180,6 +193,9 @@ __device__ __forceinline__ void select_publish(const SelectPar& q, ScenePar* cur
     q.act[g] = (n >= 0 && n < q.ctrl_len) ? q.params[size_t(n) * q.G + g] : 0.0f;
   }
 }
+
+// The selection of the step the counter names.
+__device__ __forceinline__ void select_publish(const SelectPar& q, ScenePar* cur) { select_publish_at(q, *q.ctr, cur); }
 
 // ============================================================================ keys / sort
 // Bin keys of the state being read, and the tile histogram (tile_count must be zero on entry).
@@ -460,20 +476,26 @@ __global__ void __launch_bounds__(256) k_store_sort(BatchDev b, uint32_t* dst) {
   sort_copy(from, slot_refs(slot, sp.npad, nt), b.total_particles, nt);
 }
 
-// Every CTA reads the selected record's slot itself; CTA 0 publishes the record and actuation.
+// Every CTA reads the selected record's slot itself; CTA 0 publishes the record and actuation
+// (and, with snap, the selected step number).
 template <int D>
-__global__ void __launch_bounds__(256) k_load_sort(BatchDev b, const SelectPar* __restrict__ sel) {
+__global__ void __launch_bounds__(256) k_load_sort(BatchDev b, const SelectPar* __restrict__ sel, int back,
+                                                   int* snap) {
   pdl_enter();
   __shared__ uint32_t* src;
   __shared__ uint32_t* key;
   __shared__ int np;
+  const int n = *sel->ctr - back;
   if (threadIdx.x == 0) {
-    const ScenePar& r = sel->table[selected_index(*sel, *sel->ctr)];
+    const ScenePar& r = sel->table[selected_index(*sel, n)];
     src = r.sort_slot;
-    key = r.key;
+    key = sel->key_rec ? sel->key_rec : r.key;
     np = r.npad;
   }
-  if (blockIdx.x == 0) select_publish(*sel, b.scenes);
+  if (blockIdx.x == 0) {
+    select_publish_at(*sel, n, b.scenes);
+    if (snap && threadIdx.x == 0) *snap = n;
+  }
   __syncthreads();
   if (!src) return;  // uniform across the CTA
   const int nt = b.total_tiles;
@@ -491,18 +513,18 @@ cudaError_t launch_store_sort(const BatchDev& b, uint32_t* dst, cudaStream_t s) 
 }
 
 template <int D>
-cudaError_t launch_load_sort(const BatchDev& b, const SelectPar* sel, cudaStream_t s) {
+cudaError_t launch_load_sort(const BatchDev& b, const SelectPar* sel, cudaStream_t s, int back, int* snap) {
   const int n = std::max(b.total_particles, b.total_tiles + 1);
   const int grid = std::max(1, std::min((n + 255) / 256, 4 * b.sm_count));
-  launch_pdl(k_load_sort<D>, dim3(grid), dim3(256), 0, s, b, sel);
+  launch_pdl(k_load_sort<D>, dim3(grid), dim3(256), 0, s, b, sel, back, snap);
   count_launches(1);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_store_sort<2>(const BatchDev&, uint32_t*, cudaStream_t);
 template cudaError_t launch_store_sort<3>(const BatchDev&, uint32_t*, cudaStream_t);
-template cudaError_t launch_load_sort<2>(const BatchDev&, const SelectPar*, cudaStream_t);
-template cudaError_t launch_load_sort<3>(const BatchDev&, const SelectPar*, cudaStream_t);
+template cudaError_t launch_load_sort<2>(const BatchDev&, const SelectPar*, cudaStream_t, int, int*);
+template cudaError_t launch_load_sort<3>(const BatchDev&, const SelectPar*, cudaStream_t, int, int*);
 
 // ============================================================================ P2G (tiled)
 // Phase A  canonical order of the tile's particles: by cell, then by particle id (counting sort

@@ -14,6 +14,9 @@
 namespace gbmpm {
 constexpr int GRAPH_STEPS = 8;  // steps per replayed graph
 enum Phase { PH_STEP = 0, PH_ROLL = 1, PH_RCM = 2, PH_REV = 3, PH_PREP = 4, PH_COUNT = 5 };
+// Selections beyond the phases': the reverse sort loads on a graph branch, into buffer set A (the
+// scene's own) and set B (mpm_scene::bB), stepping back from the graph's first reverse step.
+enum BranchSel { SEL_LOAD_A = PH_COUNT, SEL_LOAD_B = PH_COUNT + 1, SEL_COUNT = PH_COUNT + 2 };
 }  // namespace gbmpm
 
 using gbmpm::BatchDev;
@@ -28,6 +31,7 @@ struct mpm_ctx {
   cudaStream_t capture = nullptr;  // private stream graphs are captured on
   cudaStream_t aux = nullptr;      // second stream: a reverse pass's segment recompute runs here
   cudaStream_t capture2 = nullptr; // branch of a capture: an open-loop controller's reverse
+  cudaStream_t capture3 = nullptr; // branch of a capture: the reverse steps' sort loads
   int sm_count = 1;
   // launch timing (mpm_profile_*): event pairs around launches of the selected kinds; while a
   // mask is set, steps are launched directly (not from graphs) so every launch can be bracketed
@@ -81,8 +85,8 @@ struct mpm_scene {
   float* d_pmass = nullptr;
   float* d_gmat = nullptr;
   ScenePar* cur = nullptr;   // device: the record of the running step
-  SelectPar* dsel = nullptr; // device: one selection per phase
-  SelectPar hsel[gbmpm::PH_COUNT]{};
+  SelectPar* dsel = nullptr; // device: one selection per phase, then the branch loads'
+  SelectPar hsel[gbmpm::SEL_COUNT]{};
   int step = 0;              // host mirror of the current step
   // device record tables, one per phase family (uploaded only when their content changes)
   struct Table {
@@ -127,6 +131,16 @@ struct mpm_scene {
   // Reverse graphs of a tiled scene whose controller reads no state: each step's controller
   // reverse is captured on a branch (ctx->capture2) that the next step's adjoint gather joins, so it
   // runs beside that step's sort and adjoint scatter (BatchDev::rewind_ctr).
+  // With it, and the sorts kept by the recompute, the reverse graphs load the sort of step j + 2
+  // on a second branch (ctx->capture3) while steps j and j + 1 run: odd steps of a graph use the
+  // buffer set B below (tile arrays, bin keys, actuation, published record), even steps the scene's.
+  BatchDev bB{};
+  ScenePar* curB = nullptr;
+  uint32_t* keyB = nullptr;
+  float* actB = nullptr;
+  int* d_gstep = nullptr;          // first reverse step of the running graph
+  cudaEvent_t ev_load[3] = {};     // fork after the first load; loads of even and odd steps done
+  cudaEvent_t ev_gather = nullptr; // a step's adjoint gather done (its buffer set is free)
   bool ctrl_branch = false;
   bool ctrl_join = false;          // a branch is captured and not yet joined
   int* d_rows = nullptr;           // active-slot count of the last adjoint gather
