@@ -377,7 +377,7 @@ mpm_status capture_reverse_branched(mpm_scene* s, int steps) {
   sets[1].sorted = bb.sorted;
   auto set = [&](int j) -> BatchDev& { return sets[j & 1]; };
   auto load = [&](int j, cudaStream_t on) -> mpm_status {
-    const SelectPar* q = s->dsel + (j == 0 ? PH_REV : (j & 1) ? SEL_LOAD_B : SEL_LOAD_A);
+    const SelectPar* q = s->dsel + (j == 0 ? int(PH_REV) : (j & 1) ? int(SEL_LOAD_B) : int(SEL_LOAD_A));
     int* snap = j == 0 ? s->d_gstep : nullptr;
     const int back = j == 0 ? 0 : j;
     BatchDev& b = set(j);
@@ -1204,6 +1204,24 @@ mpm_status mpm_scene_create(mpm_ctx* c, const mpm_scene_desc* d, mpm_scene** out
   for (int i = 0; i < s->N; ++i)
     if (hgroup[i] >= 0 && hgroup[i] < s->G) count[hgroup[i]]++;
   for (int g = 0; g < s->G; ++g) hinv[g] = count[g] > 0 ? 1.0f / float(count[g]) : 0.0f;
+  if (ctrl_reads_state(cp)) {  // the particles in group order for the group reductions
+    std::vector<int> start(s->G + 2, 0), hperm(std::max(1, s->N)), hpg(std::max(1, s->N), -1);
+    auto key = [&](int i) { return (hgroup[i] >= 0 && hgroup[i] < s->G) ? hgroup[i] + 1 : 0; };
+    for (int i = 0; i < s->N; ++i) start[key(i) + 1]++;
+    for (int g = 0; g <= s->G; ++g) start[g + 1] += start[g];
+    for (int i = 0; i < s->N; ++i) {
+      const int at = start[key(i)]++;
+      hperm[at] = i;
+      hpg[at] = key(i) - 1;
+    }
+    int *perm, *pgroup;
+    ALLOC(perm, hperm.size());
+    ALLOC(pgroup, hpg.size());
+    TRY(cuda_fail(cudaMemcpy(perm, hperm.data(), sizeof(int) * hperm.size(), cudaMemcpyHostToDevice)));
+    TRY(cuda_fail(cudaMemcpy(pgroup, hpg.data(), sizeof(int) * hpg.size(), cudaMemcpyHostToDevice)));
+    cp.perm = perm;
+    cp.pgroup = pgroup;
+  }
   TRY(cuda_fail(cudaMemcpy(act_dir, hdir.data(), sizeof(float) * hdir.size(), cudaMemcpyHostToDevice)));
   TRY(cuda_fail(cudaMemcpy(params, hparams.data(), sizeof(float) * hparams.size(), cudaMemcpyHostToDevice)));
   TRY(cuda_fail(cudaMemcpy(inv_count, hinv.data(), sizeof(float) * hinv.size(), cudaMemcpyHostToDevice)));

@@ -2,8 +2,10 @@
 // actuation of every group at every step), plus the deterministic per-group reductions they
 // need: group centroids of x (controller input) and per-group sums of dL/da (Supplement S4 (K)).
 //
-// Reductions are two-level with a fixed order at both levels (lanes own groups, warps combine in
-// warp order, rows combine in row order), so they are bitwise reproducible.
+// Reductions are two-level with a fixed order at both levels (group sums of x and v: segmented
+// scans over the particles in group order, warps combine in warp order, rows in row order; dL/da:
+// per-tile rows in row order), so they are bitwise reproducible.  The MLP's dot products give each
+// output 16 threads and a fixed butterfly.
 #include "mpm_internal.h"
 
 namespace gbmpm {
@@ -16,65 +18,76 @@ constexpr int RED_STRIDE = MAX_GROUPS * 3 + 3;    // floats per row: [64 groups]
 
 int reduction_rows(int N) { return (N + RED_ROW - 1) / RED_ROW; }
 
-// Group sums of x (dim channels) and the body sum, for the MLP controller's centroids.
+// Group sums of x (mode 0) or v (mode 2), dim channels, and the body sum, over the particles in
+// group order: perm lists the particles by group (stable; ungrouped first) and pgroup[i] is the
+// group of perm[i] (-1: none), both fixed at scene creation.  A warp takes 32 consecutive entries
+// at a time, where every group is one run of lanes: a segmented scan over the lanes gives each
+// run's sum at its last lane, which adds it to the warp's accumulator of that group (one writer
+// per group and chunk, chunks in order).  Warps then combine in warp order into the block's row.
 template <int CH>
 __global__ void __launch_bounds__(256) k_group_rows(const ScenePar* __restrict__ dsp, float* __restrict__ rows,
-                                                    int mode) {
+                                                    int mode, const int* __restrict__ perm,
+                                                    const int* __restrict__ pgroup) {
   pdl_enter();
   const ScenePar& sp = *dsp;
   __shared__ float wacc[RED_WARPS][MAX_GROUPS][CH];
   __shared__ float wbody[RED_WARPS][CH];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int start = blockIdx.x * RED_ROW + w * RED_WR;
-  float lo[CH], hi[CH], body[CH];
+  const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);  // lanes 0..lane
 #pragma unroll
-  for (int c = 0; c < CH; ++c) lo[c] = hi[c] = body[c] = 0.0f;
+  for (int c = 0; c < CH; ++c) {
+    wacc[w][lane][c] = 0.0f;
+    wacc[w][lane + 32][c] = 0.0f;
+  }
+  __syncwarp();
+  float body[CH];
+#pragma unroll
+  for (int c = 0; c < CH; ++c) body[c] = 0.0f;
   for (int k = 0; k < RED_WR; k += 32) {
-    const int p = start + k + lane;
-    int g = -1;
+    const int i = start + k + lane;
+    int g = -2;  // past the end
     float val[CH];
 #pragma unroll
     for (int c = 0; c < CH; ++c) val[c] = 0.0f;
-    if (p < sp.N) {
-      g = sp.group ? sp.group[p] : -1;
-      if (g >= sp.G) g = -1;
+    if (i < sp.N) {
+      const int p = perm[i];
+      g = pgroup[i];
       if (mode == 0) {
         const float4 q = sp.planes[p];
         const float xv[3] = {q.x, q.y, q.z};
 #pragma unroll
         for (int c = 0; c < CH; ++c) val[c] = xv[c];
-      } else if (mode == 2) {  // v: floats D + D*D .. of the state, inside one plane for D = 2, 3
+      } else {  // v: floats D + D*D .. of the state, inside one plane for D = 2, 3
         constexpr int O = CH + CH * CH;
         const float4 q = sp.planes[size_t(O / 4) * sp.npad + p];
         const float qv[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
         for (int c = 0; c < CH; ++c) val[c] = qv[O % 4 + c];
-      } else {
-        val[0] = sp.sig_contrib[p];
       }
     }
 #pragma unroll
     for (int c = 0; c < CH; ++c) body[c] += val[c];
-    for (int j = 0; j < 32; ++j) {
-      const int gj = __shfl_sync(0xffffffffu, g, j);
-      float vj[CH];
+    const int gp = __shfl_up_sync(0xffffffffu, g, 1);
+    const int gn = __shfl_down_sync(0xffffffffu, g, 1);
+    const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || gp != g);
+    const int first = 31 - __clz(heads & upto);  // first lane of this lane's run
 #pragma unroll
-      for (int c = 0; c < CH; ++c) vj[c] = __shfl_sync(0xffffffffu, val[c], j);
-      if (gj >= 0 && (gj & 31) == lane) {
-        if (gj >> 5) {
+    for (int o = 1; o < 32; o <<= 1) {
 #pragma unroll
-          for (int c = 0; c < CH; ++c) hi[c] += vj[c];
-        } else {
-#pragma unroll
-          for (int c = 0; c < CH; ++c) lo[c] += vj[c];
-        }
+      for (int c = 0; c < CH; ++c) {
+        const float t = __shfl_up_sync(0xffffffffu, val[c], o);
+        if (lane - o >= first) val[c] += t;
       }
     }
+    if (g >= 0 && (lane == 31 || gn != g)) {
+#pragma unroll
+      for (int c = 0; c < CH; ++c) wacc[w][g][c] += val[c];
+    }
+    __syncwarp();
   }
 #pragma unroll
   for (int c = 0; c < CH; ++c) {
-    wacc[w][lane][c] = lo[c];
-    wacc[w][lane + 32][c] = hi[c];
     float b = body[c];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
@@ -115,6 +128,42 @@ __device__ void reduce_rows(const float* __restrict__ rows, int n_rows, int G, i
   __syncthreads();
 }
 
+// out_o = sum_j A[o * so + j * sj] x[j] for o < n_out, j < n_in, in a 1024-thread CTA: 16 threads
+// per output (thread t sums j = t, t + 16, ... in order, then a fixed butterfly over the 16), 64
+// outputs per pass; fin(o, sum) runs on the first thread of each output.  Every thread calls it.
+template <class F>
+__device__ __forceinline__ void dot_rows(const float* A, int so, int sj, const float* x, int n_in, int n_out, F fin) {
+  const int t = threadIdx.x & 15;
+  for (int o0 = 0; o0 < n_out; o0 += 64) {
+    const int o = o0 + (threadIdx.x >> 4);
+    float u = 0.0f;
+    if (o < n_out)
+      for (int j = t; j < n_in; j += 16) u += A[size_t(o) * so + size_t(j) * sj] * x[j];
+#pragma unroll
+    for (int m = 8; m > 0; m >>= 1) u += __shfl_xor_sync(0xffffffffu, u, m);
+    if (o < n_out && t == 0) fin(o, u);
+  }
+}
+
+// The MLP's three layers from its input z (shared): h1, h2 (shared) and fin3(g, u3), u3 the last
+// layer's pre-activation.  The forward and the reverse step's replay share it, so they agree bit
+// for bit.
+template <class F>
+__device__ __forceinline__ void mlp_layers(const CtrlPar& c, const float* z, float* h1, float* h2, F fin3) {
+  const int G = c.G, Z = G * c.dim, H = c.hidden;
+  const float* W1 = c.params;
+  const float* b1 = W1 + H * Z;
+  const float* W2 = b1 + H;
+  const float* b2 = W2 + H * H;
+  const float* W3 = b2 + H;
+  const float* b3 = W3 + G * H;
+  dot_rows(W1, Z, 1, z, Z, H, [&](int o, float u) { h1[o] = tanhf(u + b1[o]); });
+  __syncthreads();
+  dot_rows(W2, H, 1, h1, H, H, [&](int o, float u) { h2[o] = tanhf(u + b2[o]); });
+  __syncthreads();
+  dot_rows(W3, H, 1, h2, H, G, [&](int o, float u) { fin3(o, u + b3[o]); });
+}
+
 // ----------------------------------------------------------------------------- forward
 // MLP controller of step n = *step_ctr (the sinusoid forms are evaluated by the record
 // selection): group centroids from the partial rows, then the three tanh layers -> sp.act.
@@ -125,7 +174,7 @@ __global__ void __launch_bounds__(1024) k_ctrl_forward(const ScenePar* __restric
   __shared__ float red[MAX_GROUPS * 3 + 3];
   __shared__ float z[MAX_GROUPS * 3], h1[MAX_HIDDEN], h2[MAX_HIDDEN];
   const int G = c.G, tid = threadIdx.x;
-  const int dim = c.dim, Z = G * dim, H = c.hidden;
+  const int dim = c.dim, Z = G * dim;
   reduce_rows(rows, n_rows, G, dim, red);
   if (tid < Z) {
     const int g = tid / dim, a = tid - g * dim;
@@ -136,29 +185,7 @@ __global__ void __launch_bounds__(1024) k_ctrl_forward(const ScenePar* __restric
     if (tid < dim) c.centroid[Z + tid] = cb;
   }
   __syncthreads();
-  const float* W1 = c.params;
-  const float* b1 = W1 + H * Z;
-  const float* W2 = b1 + H;
-  const float* b2 = W2 + H * H;
-  const float* W3 = b2 + H;
-  const float* b3 = W3 + G * H;
-  if (tid < H) {
-    float u = b1[tid];
-    for (int j = 0; j < Z; ++j) u += W1[tid * Z + j] * z[j];
-    h1[tid] = tanhf(u);
-  }
-  __syncthreads();
-  if (tid < H) {
-    float u = b2[tid];
-    for (int j = 0; j < H; ++j) u += W2[tid * H + j] * h1[j];
-    h2[tid] = tanhf(u);
-  }
-  __syncthreads();
-  if (tid < G) {
-    float u = b3[tid];
-    for (int j = 0; j < H; ++j) u += W3[tid * H + j] * h2[j];
-    sp.act[tid] = c.scale * tanhf(u);
-  }
+  mlp_layers(c, z, h1, h2, [&](int g, float u) { sp.act[g] = c.scale * tanhf(u); });
 }
 
 // Closed-loop controller of step n (type 4, Section V-B): z = [target, c_g, u_g] with c_g, u_g the
@@ -188,12 +215,8 @@ __global__ void __launch_bounds__(1024) k_ctrl_forward_com(const ScenePar* __res
     c.centroid[tid] = val;
   }
   __syncthreads();
-  if (tid < G) {
-    const float* W = c.params + dim + size_t(tid) * Z;
-    float u = c.params[dim + size_t(G) * Z + tid];
-    for (int j = 0; j < Z; ++j) u += W[j] * z[j];
-    sp.act[tid] = c.scale * tanhf(u);
-  }
+  const float* b = c.params + dim + size_t(G) * Z;
+  dot_rows(c.params + dim, Z, 1, z, Z, G, [&](int g, float u) { sp.act[g] = c.scale * tanhf(u + b[g]); });
 }
 
 // ----------------------------------------------------------------------------- backward
@@ -291,24 +314,21 @@ __device__ void ctrl_backward_body(const ScenePar& sp, const CtrlPar& c) {
   } else if (c.type == 4) {  // closed loop: z of this step from the forward replay in c.centroid
     const int dim = c.dim, Z = dim * (1 + 2 * G);
     __shared__ float gu4[MAX_GROUPS];
-    if (tid < G) {
-      const float* W = c.params + dim + size_t(tid) * Z;
-      float u = c.params[dim + size_t(G) * Z + tid];
-      for (int j = 0; j < Z; ++j) u += W[j] * c.centroid[j];
-      const float th = tanhf(u);
-      gu4[tid] = ga[tid] * c.scale * (1.0f - th * th);
-      c.gparams[dim + size_t(G) * Z + tid] += gu4[tid];  // b
-    }
+    const float* b = c.params + dim + size_t(G) * Z;
+    dot_rows(c.params + dim, Z, 1, c.centroid, Z, G, [&](int g, float u) {
+      const float th = tanhf(u + b[g]);
+      gu4[g] = ga[g] * c.scale * (1.0f - th * th);
+      c.gparams[dim + size_t(G) * Z + g] += gu4[g];  // b
+    });
     __syncthreads();
     for (int i = tid; i < G * Z; i += blockDim.x) c.gparams[dim + i] += gu4[i / Z] * c.centroid[i % Z];  // W
-    if (tid < Z) {  // dL/dz: the target's part goes to its parameters, the group means' to gz
-      float sacc = 0.0f;
-      for (int g = 0; g < G; ++g) sacc += c.params[dim + size_t(g) * Z + tid] * gu4[g];
-      if (tid < dim)
-        c.gparams[tid] += sacc;
+    // dL/dz: the target's part goes to its parameters, the group means' to gz
+    dot_rows(c.params + dim, 1, Z, gu4, G, Z, [&](int j, float u) {
+      if (j < dim)
+        c.gparams[j] += u;
       else
-        c.gz[tid - dim] = sacc;  // [c_g part (G*dim)][u_g part (G*dim)]
-    }
+        c.gz[j - dim] = u;  // [c_g part (G*dim)][u_g part (G*dim)]
+    });
   } else {
     const int dim = c.dim, Z = G * dim, H = c.hidden;
     const float* W1 = c.params;
@@ -316,7 +336,6 @@ __device__ void ctrl_backward_body(const ScenePar& sp, const CtrlPar& c) {
     const float* W2 = b1 + H;
     const float* b2 = W2 + H * H;
     const float* W3 = b2 + H;
-    const float* b3 = W3 + G * H;
     float* gW1 = c.gparams;
     float* gb1 = gW1 + H * Z;
     float* gW2 = gb1 + H;
@@ -326,48 +345,26 @@ __device__ void ctrl_backward_body(const ScenePar& sp, const CtrlPar& c) {
     // forward replay from the centroids of this step (written by k_ctrl_forward)
     if (tid < Z) z[tid] = c.centroid[tid] - c.centroid[Z + tid % dim];
     __syncthreads();
-    if (tid < H) {
-      float u = b1[tid];
-      for (int j = 0; j < Z; ++j) u += W1[tid * Z + j] * z[j];
-      h1[tid] = tanhf(u);
-    }
-    __syncthreads();
-    if (tid < H) {
-      float u = b2[tid];
-      for (int j = 0; j < H; ++j) u += W2[tid * H + j] * h1[j];
-      h2[tid] = tanhf(u);
-    }
-    __syncthreads();
-    if (tid < G) {
-      float u = b3[tid];
-      for (int j = 0; j < H; ++j) u += W3[tid * H + j] * h2[j];
-      o3[tid] = tanhf(u);
-      gu3[tid] = ga[tid] * c.scale * (1.0f - o3[tid] * o3[tid]);
-      gb3[tid] += gu3[tid];
-    }
+    mlp_layers(c, z, h1, h2, [&](int g, float u) {
+      o3[g] = tanhf(u);
+      gu3[g] = ga[g] * c.scale * (1.0f - o3[g] * o3[g]);
+      gb3[g] += gu3[g];
+    });
     __syncthreads();
     for (int i = tid; i < G * H; i += blockDim.x) gW3[i] += gu3[i / H] * h2[i % H];
-    if (tid < H) {
-      float s = 0.0f;
-      for (int g = 0; g < G; ++g) s += gu3[g] * W3[g * H + tid];
-      gu2[tid] = s * (1.0f - h2[tid] * h2[tid]);
-      gb2[tid] += gu2[tid];
-    }
+    dot_rows(W3, 1, H, gu3, G, H, [&](int i, float u) {
+      gu2[i] = u * (1.0f - h2[i] * h2[i]);
+      gb2[i] += gu2[i];
+    });
     __syncthreads();
     for (int i = tid; i < H * H; i += blockDim.x) gW2[i] += gu2[i / H] * h1[i % H];
-    if (tid < H) {
-      float s = 0.0f;
-      for (int i = 0; i < H; ++i) s += gu2[i] * W2[i * H + tid];
-      gu1[tid] = s * (1.0f - h1[tid] * h1[tid]);
-      gb1[tid] += gu1[tid];
-    }
+    dot_rows(W2, 1, H, gu2, H, H, [&](int i, float u) {
+      gu1[i] = u * (1.0f - h1[i] * h1[i]);
+      gb1[i] += gu1[i];
+    });
     __syncthreads();
     for (int i = tid; i < H * Z; i += blockDim.x) gW1[i] += gu1[i / Z] * z[i % Z];
-    if (tid < Z) {
-      float s = 0.0f;
-      for (int i = 0; i < H; ++i) s += gu1[i] * W1[i * Z + tid];
-      c.gz[tid] = s;
-    }
+    dot_rows(W1, 1, Z, gu1, H, Z, [&](int j, float u) { c.gz[j] = u; });
   }
   __syncthreads();
   if (tid == 0) *step_ctr = n - 1;
@@ -451,11 +448,11 @@ cudaError_t ctrl_step_forward(const ScenePar& sp, const ScenePar* dsp, const Ctr
   if (rows > 0) {
     float* vrows = c.partials + size_t(rows) * RED_STRIDE;
     if (sp.dim == 2) {
-      launch_pdl(k_group_rows<2>, dim3(rows), dim3(256), 0, s, dsp, c.partials, 0);
-      if (com) launch_pdl(k_group_rows<2>, dim3(rows), dim3(256), 0, s, dsp, vrows, 2);
+      launch_pdl(k_group_rows<2>, dim3(rows), dim3(256), 0, s, dsp, c.partials, 0, c.perm, c.pgroup);
+      if (com) launch_pdl(k_group_rows<2>, dim3(rows), dim3(256), 0, s, dsp, vrows, 2, c.perm, c.pgroup);
     } else {
-      launch_pdl(k_group_rows<3>, dim3(rows), dim3(256), 0, s, dsp, c.partials, 0);
-      if (com) launch_pdl(k_group_rows<3>, dim3(rows), dim3(256), 0, s, dsp, vrows, 2);
+      launch_pdl(k_group_rows<3>, dim3(rows), dim3(256), 0, s, dsp, c.partials, 0, c.perm, c.pgroup);
+      if (com) launch_pdl(k_group_rows<3>, dim3(rows), dim3(256), 0, s, dsp, vrows, 2, c.perm, c.pgroup);
     }
     n += com ? 2 : 1;
   }

@@ -187,6 +187,10 @@ struct CtrlPar {
   float* gz;              // device [G*dim] scratch: dL/dz of the MLP input
   float* partials;        // device scratch for the deterministic group reductions
   int n_partials;         // number of reduction partial rows available
+  // state-reading forms: the particles in group order (stable, ungrouped first) and the group of
+  // each entry (-1: none), for the group reductions of x and v
+  const int* perm;
+  const int* pgroup;
   // rows of per-tile (tiled form) or per-block (plain form) group sums of dL/da, MAX_GROUPS each:
   // the tiled rows of the scene are the active slots whose tile lies in the scene's tile range
   const float* gpart;
