@@ -44,28 +44,39 @@ __global__ void __launch_bounds__(256) k_group_rows(const ScenePar* __restrict__
   float body[CH];
 #pragma unroll
   for (int c = 0; c < CH; ++c) body[c] = 0.0f;
-  for (int k = 0; k < RED_WR; k += 32) {
-    const int i = start + k + lane;
-    int g = -2;  // past the end
-    float val[CH];
+  // every chunk's loads are issued first (K chunks per warp), then the chunks are summed in order
+  constexpr int K = RED_WR / 32;
+  int gk[K];
+  float vk[K][CH];
 #pragma unroll
-    for (int c = 0; c < CH; ++c) val[c] = 0.0f;
+  for (int k = 0; k < K; ++k) {
+    const int i = start + 32 * k + lane;
+    gk[k] = -2;  // past the end
+#pragma unroll
+    for (int c = 0; c < CH; ++c) vk[k][c] = 0.0f;
     if (i < sp.N) {
       const int p = perm[i];
-      g = pgroup[i];
+      gk[k] = pgroup[i];
       if (mode == 0) {
         const float4 q = sp.planes[p];
         const float xv[3] = {q.x, q.y, q.z};
 #pragma unroll
-        for (int c = 0; c < CH; ++c) val[c] = xv[c];
+        for (int c = 0; c < CH; ++c) vk[k][c] = xv[c];
       } else {  // v: floats D + D*D .. of the state, inside one plane for D = 2, 3
         constexpr int O = CH + CH * CH;
         const float4 q = sp.planes[size_t(O / 4) * sp.npad + p];
         const float qv[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-        for (int c = 0; c < CH; ++c) val[c] = qv[O % 4 + c];
+        for (int c = 0; c < CH; ++c) vk[k][c] = qv[O % 4 + c];
       }
     }
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int g = gk[k];
+    float val[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) val[c] = vk[k][c];
 #pragma unroll
     for (int c = 0; c < CH; ++c) body[c] += val[c];
     const int gp = __shfl_up_sync(0xffffffffu, g, 1);
@@ -145,13 +156,29 @@ __device__ __forceinline__ void dot_rows(const float* A, int so, int sj, const f
   }
 }
 
-// The MLP's three layers from its input z (shared): h1, h2 (shared) and fin3(g, u3), u3 the last
-// layer's pre-activation.  The forward and the reverse step's replay share it, so they agree bit
-// for bit.
-template <class F>
-__device__ __forceinline__ void mlp_layers(const CtrlPar& c, const float* z, float* h1, float* h2, F fin3) {
+// The MLP's parameters (W1, b1, W2, b2, W3, b3, contiguous) copied to shared memory in one pass
+// when they fit (the soft body's 48-64-64-16 network: 8336 floats), so the layers read no global
+// memory; else the global copy.  Every thread calls it; it ends with a barrier either way.
+constexpr int MLP_STAGE = 8704;
+__device__ const float* mlp_params(const CtrlPar& c) {
+  __shared__ float stage[MLP_STAGE];
   const int G = c.G, Z = G * c.dim, H = c.hidden;
-  const float* W1 = c.params;
+  const int n = H * Z + H + H * H + H + G * H + G;
+  const bool fits = n <= MLP_STAGE;  // uniform
+  if (fits)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) stage[i] = c.params[i];
+  __syncthreads();
+  return fits ? stage : c.params;
+}
+
+// The MLP's three layers from its input z (shared): h1, h2 (shared) and fin3(g, u3), u3 the last
+// layer's pre-activation, with parameters P (mlp_params).  The forward and the reverse step's
+// replay share it, so they agree bit for bit.
+template <class F>
+__device__ __forceinline__ void mlp_layers(const CtrlPar& c, const float* P, const float* z, float* h1, float* h2,
+                                           F fin3) {
+  const int G = c.G, Z = G * c.dim, H = c.hidden;
+  const float* W1 = P;
   const float* b1 = W1 + H * Z;
   const float* W2 = b1 + H;
   const float* b2 = W2 + H * H;
@@ -184,8 +211,8 @@ __global__ void __launch_bounds__(1024) k_ctrl_forward(const ScenePar* __restric
     c.centroid[tid] = cg;
     if (tid < dim) c.centroid[Z + tid] = cb;
   }
-  __syncthreads();
-  mlp_layers(c, z, h1, h2, [&](int g, float u) { sp.act[g] = c.scale * tanhf(u); });
+  const float* P = mlp_params(c);  // its barrier also publishes z
+  mlp_layers(c, P, z, h1, h2, [&](int g, float u) { sp.act[g] = c.scale * tanhf(u); });
 }
 
 // Closed-loop controller of step n (type 4, Section V-B): z = [target, c_g, u_g] with c_g, u_g the
@@ -331,7 +358,8 @@ __device__ void ctrl_backward_body(const ScenePar& sp, const CtrlPar& c) {
     });
   } else {
     const int dim = c.dim, Z = G * dim, H = c.hidden;
-    const float* W1 = c.params;
+    const float* P = mlp_params(c);
+    const float* W1 = P;
     const float* b1 = W1 + H * Z;
     const float* W2 = b1 + H;
     const float* b2 = W2 + H * H;
@@ -345,7 +373,7 @@ __device__ void ctrl_backward_body(const ScenePar& sp, const CtrlPar& c) {
     // forward replay from the centroids of this step (written by k_ctrl_forward)
     if (tid < Z) z[tid] = c.centroid[tid] - c.centroid[Z + tid % dim];
     __syncthreads();
-    mlp_layers(c, z, h1, h2, [&](int g, float u) {
+    mlp_layers(c, P, z, h1, h2, [&](int g, float u) {
       o3[g] = tanhf(u);
       gu3[g] = ga[g] * c.scale * (1.0f - o3[g] * o3[g]);
       gb3[g] += gu3[g];
