@@ -197,13 +197,17 @@ ScenePar rec_fwd(const mpm_scene* s, float4* in, float4* out) {
 
 // Record of a recompute step: with workspace 2 it bins into key2, takes its actuation from act2
 // and writes its inspection grid to grid2, so it shares nothing the reverse steps write.
-ScenePar rec_rcm(const mpm_scene* s, float4* in, float4* out, uint32_t* sort_slot) {
+ScenePar rec_rcm(const mpm_scene* s, float4* in, float4* out, uint32_t* sort_slot, float* ctrl_slot) {
   ScenePar p = rec_fwd(s, in, out);
   if (s->rcm_ws2) {
     p.key = s->key2;
     p.act = s->act2;
     p.grid = s->grid2;
     p.sort_slot = sort_slot;  // where this step stores the sort of the state it reads
+    if (ctrl_slot) {          // and its controller input and actuation
+      p.ctrl_z = ctrl_slot;
+      p.act = ctrl_slot + CTRL_Z_CAP;
+    }
   }
   return p;
 }
@@ -215,7 +219,14 @@ uint32_t* sort_slot_of(const mpm_scene* s, int sg, int j) {
   return s->sort_store + (size_t(sg & 1) * s->roll_k + j) * w;
 }
 
-ScenePar rec_rev(const mpm_scene* s, float4* st, const float4* ain, float4* aout, uint32_t* sort_slot = nullptr) {
+// Slot of the controller store for state j of segment sg (NULL without the store).
+float* ctrl_slot_of(const mpm_scene* s, int sg, int j) {
+  if (!s->ctrl_store) return nullptr;
+  return s->ctrl_store + (size_t(sg & 1) * s->roll_k + j) * CTRL_SLOT_FLOATS;
+}
+
+ScenePar rec_rev(const mpm_scene* s, float4* st, const float4* ain, float4* aout, uint32_t* sort_slot = nullptr,
+                 float* ctrl_slot = nullptr) {
   ScenePar p = s->hp;
   p.planes = st;
   p.planes_out = st;
@@ -223,6 +234,10 @@ ScenePar rec_rev(const mpm_scene* s, float4* st, const float4* ain, float4* aout
   p.adj_out = aout;
   p.step_ctr = s->d_bstep;
   p.sort_slot = sort_slot;  // where the recompute stored the sort of this state
+  if (ctrl_slot) {          // and its controller input and actuation
+    p.ctrl_z = ctrl_slot;
+    p.act = ctrl_slot + CTRL_Z_CAP;
+  }
   return p;
 }
 
@@ -333,7 +348,7 @@ mpm_status enqueue_reverse(mpm_scene* s, cudaStream_t st) {
   } else {
     CK(launch_select(s->dsel + PH_REV, 1, s->cur, st));
   }
-  {
+  if (!(stored && s->ctrl_store)) {  // else the recompute kept this state's controller input
     ProfScope p(c, st, MPM_K_CTRL);
     CK(ctrl_step_forward(s->hp, s->cur, s->ctrl, st));
   }
@@ -484,6 +499,7 @@ void free_rollout(mpm_scene* s) {
   s->seg.clear();
   s->seg2.clear();
   s->sort_store = nullptr;
+  s->ctrl_store = nullptr;
   s->have_rollout = false;
 }
 
@@ -727,7 +743,10 @@ mpm_status prepare_backward(mpm_scene* s, const float* gxT, const float* gvT, co
   // odd segments a second set of recompute buffers.  Not for batches (mean_x0_seed), the plain
   // form, or when the extra buffers break the budget.
   const size_t S = s->state_bytes;
-  const size_t store_bytes = 2 * size_t(k) * sort_slot_words(s->npad, s->hp.n_tiles) * sizeof(uint32_t);
+  const bool keep_ctrl = ctrl_reads_state(s->ctrl);  // controller inputs kept beside the sorts
+  const size_t ctrl_bytes = keep_ctrl ? 2 * size_t(k) * CTRL_SLOT_FLOATS * sizeof(float) : 0;
+  const size_t store_bytes =
+      2 * size_t(k) * sort_slot_words(s->npad, s->hp.n_tiles) * sizeof(uint32_t) + ctrl_bytes;
   const bool overlap = !mean_x0_seed && s->impl == MPM_IMPL_TILED && k > 1 && nseg > 1 &&
                        (s->roll_budget == 0 ||
                         (size_t(nseg) + 2 * size_t(k - 1)) * S + store_bytes <= s->roll_budget);
@@ -739,7 +758,9 @@ mpm_status prepare_backward(mpm_scene* s, const float* gxT, const float* gvT, co
       s->seg2 = segs;
     }
     // the sorts of every recomputed state, by segment parity (each reverse step loads its own)
-    if (!s->sort_store) CKS(dalloc(&s->sort_store, store_bytes / sizeof(uint32_t), s->roll_allocs));
+    if (!s->sort_store)
+      CKS(dalloc(&s->sort_store, (store_bytes - ctrl_bytes) / sizeof(uint32_t), s->roll_allocs));
+    if (keep_ctrl && !s->ctrl_store) CKS(dalloc(&s->ctrl_store, ctrl_bytes / sizeof(float), s->roll_allocs));
   }
   if (s->graphs_ws2 != overlap) {  // recompute and reverse graphs name the workspace and sort path
     for (int ph : {PH_RCM, PH_PREP, PH_REV})
@@ -763,19 +784,22 @@ mpm_status prepare_backward(mpm_scene* s, const float* gxT, const float* gvT, co
     auto segp = [&](int j) { return j == 0 ? s->ckpt[sg] : segs[j - 1]; };
     for (int j = 0; j + 1 < L; ++j) {
       rcm[sg * k + j] = int(recs.size());
-      recs.push_back(rec_rcm(s, segp(j), segp(j + 1), sort_slot_of(s, sg, j)));
+      recs.push_back(rec_rcm(s, segp(j), segp(j + 1), sort_slot_of(s, sg, j), ctrl_slot_of(s, sg, j)));
     }
-    if (L == 1 && overlap) {  // no recompute step: the keys of the checkpoint still need its record
-      rcm[sg * k] = int(recs.size());
-      recs.push_back(rec_rcm(s, s->ckpt[sg], s->ckpt[sg], sort_slot_of(s, sg, 0)));
+    // the segment's last state: its record for the keys of a lone checkpoint (L = 1) and for the
+    // controller forward that keeps its controller input (state-reading controllers)
+    if (overlap && (L == 1 || s->ctrl_store)) {
+      rcm[sg * k + L - 1] = int(recs.size());
+      recs.push_back(rec_rcm(s, segp(L - 1), segp(L - 1), sort_slot_of(s, sg, L - 1), ctrl_slot_of(s, sg, L - 1)));
     }
     for (int n = 0; n < L; ++n) {
       const int gstep = sg * k + n;
       const int parity = (T - 1 - gstep) & 1;  // reverse step T-1 reads adj[0]
       rev[gstep] = int(recs.size()) + parity;
       uint32_t* slot = overlap ? sort_slot_of(s, sg, n) : nullptr;
-      recs.push_back(rec_rev(s, segp(n), s->adj[0], s->adj[1], slot));
-      recs.push_back(rec_rev(s, segp(n), s->adj[1], s->adj[0], slot));
+      float* cslot = overlap ? ctrl_slot_of(s, sg, n) : nullptr;
+      recs.push_back(rec_rev(s, segp(n), s->adj[0], s->adj[1], slot, cslot));
+      recs.push_back(rec_rev(s, segp(n), s->adj[1], s->adj[0], slot, cslot));
     }
   }
   CKS(upload_table(s, 2, recs));
@@ -1309,6 +1333,10 @@ mpm_status mpm_backward(mpm_scene* s, const float* gxT, const float* gvT, const 
       CK(two ? launch_store_sort<2>(b2, slot, st) : launch_store_sort<3>(b2, slot, st));
       CK(cudaMemsetAsync(b2.tile_count, 0, sizeof(uint32_t) * size_t(b2.total_tiles), st));
       CK(cudaMemsetAsync(b2.tile_fill, 0, sizeof(uint32_t) * size_t(b2.total_tiles), st));
+      if (s->ctrl_store) {  // the last state's controller input and actuation into its slot
+        CK(launch_select(s->dsel + PH_RCM, 1, s->cur2, st));
+        CK(ctrl_step_forward(s->hp, s->cur2, s->ctrl2, st));
+      }
     }
     return MPM_OK;
   };

@@ -208,8 +208,9 @@ __global__ void __launch_bounds__(1024) k_ctrl_forward(const ScenePar* __restric
     const float cg = red[g * 3 + a] * c.inv_count[g];
     const float cb = red[MAX_GROUPS * 3 + a] * c.inv_n;
     z[tid] = cg - cb;
-    c.centroid[tid] = cg;
-    if (tid < dim) c.centroid[Z + tid] = cb;
+    float* cen = sp.ctrl_z ? sp.ctrl_z : c.centroid;
+    cen[tid] = cg;
+    if (tid < dim) cen[Z + tid] = cb;
   }
   const float* P = mlp_params(c);  // its barrier also publishes z
   mlp_layers(c, P, z, h1, h2, [&](int g, float u) { sp.act[g] = c.scale * tanhf(u); });
@@ -217,7 +218,7 @@ __global__ void __launch_bounds__(1024) k_ctrl_forward(const ScenePar* __restric
 
 // Closed-loop controller of step n (type 4, Section V-B): z = [target, c_g, u_g] with c_g, u_g the
 // group means of x and v (partial rows of x, then of v), a = scale * tanh(W z + b) -> sp.act; z is
-// kept in c.centroid for the reverse step.
+// kept for the reverse step (in the record's controller slot, else in c.centroid).
 __global__ void __launch_bounds__(1024) k_ctrl_forward_com(const ScenePar* __restrict__ dsp, CtrlPar c,
                                                            const float* rows, int n_rows) {
   pdl_enter();
@@ -239,7 +240,7 @@ __global__ void __launch_bounds__(1024) k_ctrl_forward_com(const ScenePar* __res
       val = rv[(i / dim) * 3 + i % dim] * c.inv_count[i / dim];
     }
     z[tid] = val;
-    c.centroid[tid] = val;
+    (sp.ctrl_z ? sp.ctrl_z : c.centroid)[tid] = val;
   }
   __syncthreads();
   const float* b = c.params + dim + size_t(G) * Z;
@@ -338,17 +339,18 @@ __device__ void ctrl_backward_body(const ScenePar& sp, const CtrlPar& c) {
   }
   if (c.type == 0 || c.type == 1 || c.type == 3) {
     ctrl_open_params(c, n, t, ga);
-  } else if (c.type == 4) {  // closed loop: z of this step from the forward replay in c.centroid
+  } else if (c.type == 4) {  // closed loop: z of this step as its forward kept it
     const int dim = c.dim, Z = dim * (1 + 2 * G);
+    const float* cen = sp.ctrl_z ? sp.ctrl_z : c.centroid;
     __shared__ float gu4[MAX_GROUPS];
     const float* b = c.params + dim + size_t(G) * Z;
-    dot_rows(c.params + dim, Z, 1, c.centroid, Z, G, [&](int g, float u) {
+    dot_rows(c.params + dim, Z, 1, cen, Z, G, [&](int g, float u) {
       const float th = tanhf(u + b[g]);
       gu4[g] = ga[g] * c.scale * (1.0f - th * th);
       c.gparams[dim + size_t(G) * Z + g] += gu4[g];  // b
     });
     __syncthreads();
-    for (int i = tid; i < G * Z; i += blockDim.x) c.gparams[dim + i] += gu4[i / Z] * c.centroid[i % Z];  // W
+    for (int i = tid; i < G * Z; i += blockDim.x) c.gparams[dim + i] += gu4[i / Z] * cen[i % Z];  // W
     // dL/dz: the target's part goes to its parameters, the group means' to gz
     dot_rows(c.params + dim, 1, Z, gu4, G, Z, [&](int j, float u) {
       if (j < dim)
@@ -370,8 +372,9 @@ __device__ void ctrl_backward_body(const ScenePar& sp, const CtrlPar& c) {
     float* gb2 = gW2 + H * H;
     float* gW3 = gb2 + H;
     float* gb3 = gW3 + G * H;
-    // forward replay from the centroids of this step (written by k_ctrl_forward)
-    if (tid < Z) z[tid] = c.centroid[tid] - c.centroid[Z + tid % dim];
+    // forward replay from the centroids of this step (kept by k_ctrl_forward)
+    const float* cen = sp.ctrl_z ? sp.ctrl_z : c.centroid;
+    if (tid < Z) z[tid] = cen[tid] - cen[Z + tid % dim];
     __syncthreads();
     mlp_layers(c, P, z, h1, h2, [&](int g, float u) {
       o3[g] = tanhf(u);

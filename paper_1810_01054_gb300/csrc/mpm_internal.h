@@ -79,7 +79,16 @@ struct ScenePar {
   // sort store (reverse pass with the recompute beside it): a recompute step stores the sort of
   // the state it reads here, a reverse step loads the sort of its state from here (NULL: none)
   uint32_t* sort_slot;
+  // controllers that read the state, same reverse pass: the forward of a recompute step writes its
+  // controller input z (and, through act, its actuation) into this state's slot; the reverse step
+  // reads both from there instead of evaluating the controller again (NULL: the controller's own
+  // scratch)
+  float* ctrl_z;
 };
+
+// Floats of one controller slot: input z (at most 3 (1 + 2 MAX_GROUPS)), then the actuation.
+constexpr int CTRL_Z_CAP = 3 * (1 + 2 * 64);
+constexpr int CTRL_SLOT_FLOATS = CTRL_Z_CAP + 64 + 1;
 
 // Words of one sort-store slot: sorted ids [npad] | bin keys [npad] | tile_start [nt + 1] |
 // tile_slot [nt] | active [nt] | n_active [1].

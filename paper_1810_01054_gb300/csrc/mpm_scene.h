@@ -124,6 +124,8 @@ struct mpm_scene {
   std::vector<void*> ws2_allocs;
   std::vector<float4*> seg2;
   uint32_t* sort_store = nullptr;  // 2 x k slots (segment parity, state in segment) of sorts
+  float* ctrl_store = nullptr;     // the same slots of controller inputs and actuations (controllers
+                                   // that read the state)
   bool rcm_ws2 = false;     // the reverse tables send the recompute to workspace 2
   bool graphs_ws2 = false;  // workspace the recompute graphs were captured with
   size_t roll_budget = 0;
