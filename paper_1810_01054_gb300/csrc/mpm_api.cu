@@ -27,6 +27,10 @@
 
 using namespace gbmpm;
 
+namespace gbmpm {
+thread_local int g_launch_priority = 0;
+}
+
 namespace {
 std::mutex g_config_mutex;
 bool g_configured[64] = {};
@@ -433,9 +437,20 @@ mpm_status enqueue_phase(mpm_scene* s, int ph, cudaStream_t st) {
   return enqueue_forward(s, ph, st);
 }
 
+// Sets the launch priority for its lifetime.
+struct LaunchPriority {
+  int old;
+  explicit LaunchPriority(int p) : old(g_launch_priority) { g_launch_priority = p; }
+  ~LaunchPriority() { g_launch_priority = old; }
+};
+
 mpm_status capture(mpm_scene* s, int ph, int steps, Graph* g) {
   mpm_ctx* c = s->ctx;
   long long tally = 0;
+  // the reverse steps are the critical path of an overlapped reverse pass: their kernels go first
+  int least = 0, greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&least, &greatest);
+  LaunchPriority prio(ph == PH_REV ? greatest : 0);
   CK(cudaStreamBeginCapture(c->capture, cudaStreamCaptureModeThreadLocal));
   capture_tally(&tally);
   mpm_status st = MPM_OK;
@@ -456,7 +471,7 @@ mpm_status capture(mpm_scene* s, int ph, int steps, Graph* g) {
     return st;
   }
   CK(e);
-  e = cudaGraphInstantiate(&g->exec, graph, 0);
+  e = cudaGraphInstantiate(&g->exec, graph, ph == PH_REV ? cudaGraphInstantiateFlagUseNodePriority : 0);
   cudaGraphDestroy(graph);
   CK(e);
   g->kernels = tally;

@@ -17,6 +17,11 @@ void count_launches(int n);
 long long launch_total();
 void capture_tally(long long* tally);  // non-null: this thread is capturing
 
+// Scheduling priority given to the kernels this thread launches (0: the stream's).  Reverse-pass
+// graphs are captured with the device's highest priority, so their kernels' CTAs go ahead of the
+// recompute running beside them on the second stream.
+extern thread_local int g_launch_priority;
+
 // Launches kernel k with programmatic stream serialization (its CTAs may be scheduled while the
 // previous kernel on s finishes).  k must begin with pdl_enter().
 template <class... P, class... A>
@@ -26,11 +31,13 @@ cudaError_t launch_pdl(void (*k)(P...), dim3 grid, dim3 block, size_t smem, cuda
   cfg.blockDim = block;
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
-  cudaLaunchAttribute at[1];
+  cudaLaunchAttribute at[2];
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   at[0].val.programmaticStreamSerializationAllowed = 1;
+  at[1].id = cudaLaunchAttributePriority;
+  at[1].val.priority = g_launch_priority;
   cfg.attrs = at;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = g_launch_priority ? 2 : 1;
   return cudaLaunchKernelEx(&cfg, k, static_cast<P>(args)...);
 }
 
