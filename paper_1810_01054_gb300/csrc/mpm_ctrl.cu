@@ -309,6 +309,9 @@ __device__ void ctrl_open_params(const CtrlPar& c, int n, float t, const float* 
   }
 }
 
+// STATE: the forms that read the state (closed loop, MLP) are compiled in; without it the kernel
+// handles only the open-loop forms and needs no room for the MLP's parameters.
+template <bool STATE>
 __device__ void ctrl_backward_body(const ScenePar& sp, const CtrlPar& c) {
   __shared__ float ga[MAX_GROUPS], z[MAX_GROUPS * 3], h1[MAX_HIDDEN], h2[MAX_HIDDEN], o3[MAX_GROUPS];
   __shared__ float gu3[MAX_GROUPS], gu2[MAX_HIDDEN], gu1[MAX_HIDDEN];
@@ -337,7 +340,7 @@ __device__ void ctrl_backward_body(const ScenePar& sp, const CtrlPar& c) {
     __syncthreads();
     ctrl_group_sums(c, range[0], range[1], ga, sp.act_grad);
   }
-  if (c.type == 0 || c.type == 1 || c.type == 3) {
+  if (!STATE || c.type == 0 || c.type == 1 || c.type == 3) {
     ctrl_open_params(c, n, t, ga);
   } else if (c.type == 4) {  // closed loop: z of this step as its forward kept it
     const int dim = c.dim, Z = dim * (1 + 2 * G);
@@ -401,9 +404,10 @@ __device__ void ctrl_backward_body(const ScenePar& sp, const CtrlPar& c) {
   if (tid == 0) *step_ctr = n - 1;
 }
 
+template <bool STATE>
 __global__ void __launch_bounds__(1024) k_ctrl_backward(const ScenePar* __restrict__ dsp, CtrlPar c) {
   pdl_enter();
-  ctrl_backward_body(*dsp, c);
+  ctrl_backward_body<STATE>(*dsp, c);
 }
 
 // Reverse of a form that reads no state for one step of a scene alone: the adjoint gather of the
@@ -423,7 +427,7 @@ __global__ void __launch_bounds__(1024) k_ctrl_backward_open(CtrlPar c, const in
 __global__ void __launch_bounds__(1024) k_ctrl_backward_multi(const ScenePar* __restrict__ cur,
                                                               const CtrlPar* __restrict__ cs) {
   pdl_enter();
-  ctrl_backward_body(cur[blockIdx.x], cs[blockIdx.x]);
+  ctrl_backward_body<true>(cur[blockIdx.x], cs[blockIdx.x]);
 }
 
 // x (and, for the closed-loop form, v) adjoint of the controller input: the MLP's centroids
@@ -524,7 +528,10 @@ cudaError_t ctrl_scatter_x(const ScenePar& sp, const ScenePar* dsp, const CtrlPa
 // Controller backward for one reverse step: group sums of (K), parameter adjoint, and (MLP) the
 // centroid adjoint added to dL/dx of state n.  Rewinds the scene's step counter.
 cudaError_t ctrl_step_backward(const ScenePar& sp, const ScenePar* dsp, const CtrlPar& c, cudaStream_t s) {
-  launch_pdl(k_ctrl_backward, dim3(1), dim3(1024), 0, s, dsp, c);
+  if (ctrl_reads_state(c))
+    launch_pdl(k_ctrl_backward<true>, dim3(1), dim3(1024), 0, s, dsp, c);
+  else
+    launch_pdl(k_ctrl_backward<false>, dim3(1), dim3(1024), 0, s, dsp, c);
   if (ctrl_reads_state(c) && sp.N > 0) {
     if (sp.dim == 2)
       launch_pdl(k_ctrl_scatter_x<2>, dim3((sp.N + 255) / 256), dim3(256), 0, s, dsp, c);
