@@ -388,10 +388,11 @@ def measure(args, spec, rank, world, dev, stream, ctx, *, e2e=True, plain=True):
             "traffic": measured_traffic(dom, spec.name, N), "peak_source": src, "algo_bytes_per_particle": bpp,
             "launches": cnt, "avg_launch_us": 1e3 * launch_ms,
             "timing": "CUDA events around every launch of the kernel in a directly-launched repeat of the timed steps"}
-    state_mb = N * PLANES_BYTES[d] / 1e6
-    if state_mb * 1e6 < L2_BYTES:  # the whole state stays in L2 between steps: HBM is not the limit
-        roof["regime"] = (f"latency: the {state_mb:.1f} MB state stays in the 129 MB L2 across steps and each "
-                          f"launch is one chain of per-tile dependent loads; the HBM-scale case is large_scene")
+    work_mb = 3 * N * PLANES_BYTES[d] / 1e6  # a reverse step's state, adjoint in and adjoint out
+    if work_mb * 1e6 < L2_BYTES:  # the step's working set stays in L2: HBM is not the limit
+        roof["regime"] = (f"latency: a step's {work_mb:.1f} MB working set (state, adjoint in and out) stays in "
+                          f"the 129 MB L2 across steps and each launch is one chain of per-tile dependent loads; "
+                          f"the HBM-scale case is large_scene")
     share = {kk: round(v[1] / prof_total_ms, 4) for kk, v in prof.items()}
     return {"value": value, "tot_ms": tot_ms, "step_ms": step_ms, "value_fwd": value_fwd, "roofline": roof,
             "share": share, "e2e": e2e_rec, "plain": plain_rec, "gpu_launches": n_launch, "clocks": clk.summary(),
