@@ -12,7 +12,7 @@ namespace gbmpm {
 
 constexpr float kTwoPi = 6.283185307179586f;
 constexpr int RED_WARPS = 8;
-constexpr int RED_WR = 256;                       // particles per warp
+constexpr int RED_WR = 64;                        // particles per warp
 constexpr int RED_ROW = RED_WARPS * RED_WR;       // particles per partial row
 constexpr int RED_STRIDE = MAX_GROUPS * 3 + 3;    // floats per row: [64 groups][3] + body[3]
 
@@ -119,22 +119,32 @@ __global__ void __launch_bounds__(256) k_group_rows(const ScenePar* __restrict__
   }
 }
 
-// Sum rows in a fixed order into out[g*3+c] (groups) and out[192+c] (body); 1024-thread CTA.
+// Sum rows in a fixed order into out[g*3+c] (groups) and out[192+c] (body); 1024-thread CTA.  Only
+// the U = (G + 1) CH outputs in use are summed, each by S = 1024 / U interleaved splits combined
+// in split order; the other outputs are set to zero.
 __device__ void reduce_rows(const float* __restrict__ rows, int n_rows, int G, int CH, float* out) {
   __shared__ float part[1024];
-  const int O = MAX_GROUPS * 3 + 3;  // outputs, some unused
-  const int S = blockDim.x / O;      // splits per output (5 with 1024 threads)
-  const int o = threadIdx.x % O, s = threadIdx.x / O;
+  const int O = MAX_GROUPS * 3 + 3;  // outputs
+  const int U = (G + 1) * CH;        // outputs in use
+  const int S = blockDim.x / U;      // splits per output in use
+  const int u = threadIdx.x % U, s = threadIdx.x / U;
+  auto out_index = [&](int v) { return v < G * CH ? (v / CH) * 3 + v % CH : MAX_GROUPS * 3 + (v - G * CH); };
   float acc = 0.0f;
-  const bool used = s < S && ((o < MAX_GROUPS * 3 && (o / 3) < G && (o % 3) < CH) || (o >= MAX_GROUPS * 3 && (o - MAX_GROUPS * 3) < CH));
-  if (used)
+  if (s < S) {
+    const int o = out_index(u);
     for (int r = s; r < n_rows; r += S) acc += rows[size_t(r) * RED_STRIDE + o];
+  }
   part[threadIdx.x] = acc;
   __syncthreads();
-  if (threadIdx.x < O) {
+  if (threadIdx.x < U) {
     float t = 0.0f;
-    for (int k = 0; k < S; ++k) t += part[k * O + threadIdx.x];
-    out[threadIdx.x] = t;
+    for (int k = 0; k < S; ++k) t += part[k * U + threadIdx.x];
+    out[out_index(threadIdx.x)] = t;
+  }
+  if (threadIdx.x < O) {
+    const int o = threadIdx.x;
+    const bool used = o < MAX_GROUPS * 3 ? (o / 3 < G && o % 3 < CH) : (o - MAX_GROUPS * 3 < CH);
+    if (!used) out[o] = 0.0f;
   }
   __syncthreads();
 }
