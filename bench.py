@@ -81,7 +81,7 @@ def material_variant(spec):
 def workload(name, rank=0):
     from paper_1810_01054_gb300 import scenes as S
     seeds = {"walker_square_2d": 0, "walker_2d": 1, "soft_body_3d": 2, "box_cluster_3d": 3}
-    spec = S.CONFIGS[name](seeds[name] + 1000 * rank)
+    spec = S.WORKLOADS[name](seeds[name] + 1000 * rank)
     return spec
 
 

@@ -13,7 +13,7 @@
 // Loops run particle -> stencil node with no sorting, tiling or fusion; every quantity is
 // recomputed from its definition.  Readings of passages the paper leaves open (weights'
 // base, grid geometry, empty nodes, gravity placement, boundary set, epsilon of S5, typos of
-// S1/S4) are listed in the design doc and restated where they are used below.
+// S1/S4) are restated where they are used below.
 //
 // Status codes: 0 ok, -1 bad argument, -3 a stencil left the grid, -4 det F <= 0.
 

@@ -431,7 +431,7 @@ def blob(dim: int, n: int, n_particles: int, seed: int, *, dt: float = 1e-3, E: 
     return spec
 
 
-CONFIGS = {
+WORKLOADS = {
     "walker_square_2d": walker_square_2d,
     "walker_2d": walker_2d,
     "soft_body_3d": soft_body_3d,
