@@ -381,7 +381,7 @@ bool load_branch(const mpm_scene* s) { return s->rcm_ws2 && s->ctrl_branch && s-
 // step loads its sort in line (and keeps its step number n in d_gstep); the load of step j >= 1
 // (state n - j, buffer set A for even j, B for odd j) waits for the adjoint gather of step j - 2,
 // the last reader of that set, and step j's adjoint scatter waits for its load.  So each load runs
-// beside the two steps before it.  The controller reads no state (ctrl_forward launches nothing).
+// beside the step before it.  The controller reads no state (ctrl_forward launches nothing).
 mpm_status capture_reverse_branched(mpm_scene* s, int steps) {
   mpm_ctx* c = s->ctx;
   cudaStream_t st = c->capture, br = c->capture3;
@@ -397,10 +397,9 @@ mpm_status capture_reverse_branched(mpm_scene* s, int steps) {
   auto set = [&](int j) -> BatchDev& { return sets[j & 1]; };
   auto load = [&](int j, cudaStream_t on) -> mpm_status {
     const SelectPar* q = s->dsel + (j == 0 ? int(PH_REV) : (j & 1) ? int(SEL_LOAD_B) : int(SEL_LOAD_A));
-    int* snap = j == 0 ? s->d_gstep : nullptr;
-    const int back = j == 0 ? 0 : j;
+    int* snap = j == 0 ? s->d_gstep : nullptr;  // the branch's selections step back j from there
     BatchDev& b = set(j);
-    CK(two ? launch_load_sort<2>(b, q, on, back, snap) : launch_load_sort<3>(b, q, on, back, snap));
+    CK(two ? launch_load_sort<2>(b, q, on, j, snap) : launch_load_sort<3>(b, q, on, j, snap));
     return MPM_OK;
   };
   CKS(load(0, st));
