@@ -176,9 +176,11 @@ def test_recompute_beside_reverse_steps_is_bitwise_the_sequential_pass(M, ctx):
 @pytest.mark.parametrize("ctrl", ["basis_2d", "table_3d"])
 def test_controller_reverse_beside_next_step_is_bitwise_the_serial_pass(M, ctx, ctrl):
     """Controllers that read no state (sinusoid basis, per-step table) have their reverse captured
-    on a branch of the reverse graphs, beside the next step's sort and adjoint scatter; with launch
-    timing on, the same steps are launched one after another on one stream.  Both give the same
-    bits (T = 50, k = 16: segments replayed as 8-step and single-step graphs)."""
+    on a branch of the reverse graphs, beside the next step's sort and adjoint scatter, and the
+    sorts of a graph's later steps load on a second branch into two alternating buffer sets; with
+    launch timing on, the same steps are launched one after another on one stream and one buffer
+    set.  Both give the same bits (T = 50, k = 16: segments replayed as 8-step and single-step
+    graphs)."""
     if ctrl == "basis_2d":
         spec = S.walker_2d(1, n_steps=50)
     else:
