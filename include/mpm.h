@@ -16,7 +16,8 @@
  *  - Every function returns mpm_status (0 = OK, < 0 = error); nothing throws or aborts across
  *    the ABI.  Work is enqueued on the context's stream (a reverse pass's segment recompute and a
  *    batch's reverse half run on a private second stream, always joined back into the context's
- *    stream before the call returns); device-side errors (a stencil leaving
+ *    stream before the call returns; the CUDA graphs a scene replays may branch inside, but each
+ *    completes as one unit in the context stream's order); device-side errors (a stencil leaving
  *    the grid, det F <= 0, a tile over capacity) are recorded in the scene's status word, first
  *    error wins, and reported by the next synchronising call (mpm_sync, mpm_get_state,
  *    mpm_backward).  A scene with a recorded error keeps it until mpm_set_state.
