@@ -27,3 +27,22 @@ def test_reference_arm_prints_one_contract_line():
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_committed_traffic_matches_the_kernel_sources_and_algorithmic_bytes():
+    """profiles/traffic.json holds ncu DRAM bytes per particle of the roofline kernels, keyed to a
+    hash of the kernel sources; the bench reports them only while the sources still match.  Each
+    entry names its committed summary, and DRAM traffic stays within a factor of the algorithmic
+    bytes (no kernel re-reads its inputs many times)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    dims = {"walker_2d": 0, "box_cluster_3d": 1}
+    for wl, kernels in rec.items():
+        for kern, e in kernels.items():
+            assert os.path.exists(os.path.join(ROOT, e["capture"])), e["capture"]
+            assert len(e["kernel_hash"]) == 12
+            algo = bench.ALGO_BYTES[kern][dims[wl]]
+            assert 0.5 * algo <= e["dram_bytes_per_particle"] <= 2.0 * algo, (wl, kern)
+            if e["kernel_hash"] == bench.kernel_source_hash():
+                assert bench.measured_traffic(kern, wl, 1000) == e["dram_bytes_per_particle"] * 1000
