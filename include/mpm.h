@@ -341,8 +341,14 @@ mpm_status mpm_tune_cache_load(const char* path);
  *    that device current; make that first call before any stream capture.
  *  - Every call shares the array and clears the part it uses before use; calls whose work
  *    overlaps on the GPU (e.g. on two streams) race on it.
- *  - device < 0 keeps the current device; status (device int, may be NULL) receives the first
- *    device-side error as in the rest of this header.
+ *  - device < 0 keeps the current device; device >= 0 is made current for the call and the
+ *    caller's current device is restored before it returns.  status (device int, may be NULL)
+ *    receives the first device-side error as in the rest of this header.
+ *  - Arguments are checked as mpm_scene_create checks them (each grid side and the node count
+ *    bounded before anything is multiplied or launched; bc_width >= 0, friction_c finite and
+ *    >= 0, p_mass > 0, p_vol > 0, the explicit-integration limit on dt): MPM_ERR_ARG.
+ *  - MPM_ERR_CUDA when one of its own launches fails; an error left pending by the caller's
+ *    earlier work is neither read nor cleared.
  * Asynchronous on cuda_stream (a cudaStream_t, NULL = the legacy default stream). */
 typedef struct {
   int device;

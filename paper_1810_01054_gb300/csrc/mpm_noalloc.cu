@@ -10,6 +10,7 @@
 // The step is the plain form of the library (P2G with float atomics into a dense grid, grid
 // update, G2P), so it matches mpm_step on an MPM_IMPL_PLAIN scene up to the order of the atomic
 // additions.
+#include <cmath>
 #include <mutex>
 
 #include "../../include/mpm.h"
@@ -219,6 +220,34 @@ mpm_status scratch_for_current_device(float4** out) {
   return MPM_OK;
 }
 
+// Launches one kernel and returns that launch's own error (cudaLaunchKernel reports it directly,
+// so an error left pending by the caller's earlier work is neither read nor cleared here).
+template <class... Args>
+cudaError_t na_launch(void (*kernel)(Args...), int blocks, cudaStream_t s, Args... args) {
+  void* argv[] = {static_cast<void*>(&args)...};
+  return cudaLaunchKernel(reinterpret_cast<const void*>(kernel), dim3(blocks), dim3(256), argv, 0, s);
+}
+
+// Restores the caller's current device when the entry point switched it.
+struct DeviceGuard {
+  int saved = -1;
+  ~DeviceGuard() {
+    if (saved >= 0) cudaSetDevice(saved);
+  }
+};
+
+template <int D>
+mpm_status na_enqueue(const NAPar& p, float4* grid, cudaStream_t s) {
+  const int nb = (p.n_nodes + 255) / 256, pb = (p.N + 255) / 256;
+  // the previous call's grid is still in the array
+  if (na_launch(k_na_clear, nb, s, grid, p.n_nodes) != cudaSuccess) return MPM_ERR_CUDA;
+  if (p.N > 0 && na_launch(k_na_p2g<D>, pb, s, p, grid) != cudaSuccess) return MPM_ERR_CUDA;
+  if (na_launch(k_na_grid<D>, nb, s, p, grid) != cudaSuccess) return MPM_ERR_CUDA;
+  if (p.N > 0 && na_launch(k_na_g2p<D>, pb, s, p, static_cast<const float4*>(grid)) != cudaSuccess)
+    return MPM_ERR_CUDA;
+  return MPM_OK;
+}
+
 }  // namespace
 
 extern "C" mpm_status mpm_step_noalloc(const mpm_noalloc_step* a, void* cuda_stream) {
@@ -227,16 +256,32 @@ extern "C" mpm_status mpm_step_noalloc(const mpm_noalloc_step* a, void* cuda_str
   if (D != 2 && D != 3) return MPM_ERR_ARG;
   long long nodes = 1;
   for (int k = 0; k < D; ++k) {
-    if (a->n_grid[k] < 5) return MPM_ERR_ARG;
+    // each side is bounded before it multiplies, so the product cannot wrap
+    if (a->n_grid[k] < 5 || a->n_grid[k] > kNoAllocMaxNodes) return MPM_ERR_ARG;
     nodes *= a->n_grid[k];
+    if (nodes > kNoAllocMaxNodes) return MPM_ERR_ARG;  // beyond the fixed scratch
   }
-  if (nodes > kNoAllocMaxNodes) return MPM_ERR_ARG;  // beyond the fixed scratch
-  if (a->n_particles < 0 || (a->n_particles > 0 && (!a->x || !a->x_out || !a->v_out || !a->C_out || !a->F_out)))
-    return MPM_ERR_ARG;
+  if (a->n_particles < 0 || a->n_particles >= (1 << 26)) return MPM_ERR_ARG;
+  if (a->n_particles > 0 && (!a->x || !a->x_out || !a->v_out || !a->C_out || !a->F_out)) return MPM_ERR_ARG;
   if (a->n_groups < 0 || (a->n_groups > 0 && (!a->act || !a->act_dir))) return MPM_ERR_ARG;
+  // the same checks as mpm_scene_create, whose plain form this step reproduces
   if (!(a->dx > 0.f) || !(a->dt > 0.f) || !(a->E > 0.f) || !(a->nu > -1.f && a->nu < 0.5f)) return MPM_ERR_ARG;
+  if (!(a->p_mass > 0.f) || !(a->p_vol > 0.f)) return MPM_ERR_ARG;
   if (a->bc_type != MPM_BC_STICKY && a->bc_type != MPM_BC_SLIP) return MPM_ERR_ARG;
-  if (a->device >= 0 && cudaSetDevice(a->device) != cudaSuccess) return MPM_ERR_CUDA;
+  if (a->bc_width < 0 || !(a->friction_c >= 0.f) || !std::isfinite(a->friction_c)) return MPM_ERR_ARG;
+  for (int k = 0; k < D; ++k)
+    if (!std::isfinite(a->gravity[k])) return MPM_ERR_ARG;
+  const double rho = double(a->p_mass) / double(a->p_vol);
+  if (double(a->dt) > double(a->dx) * std::sqrt(rho / double(a->E)) * (1.0 + 1e-6)) return MPM_ERR_ARG;
+  DeviceGuard guard;
+  if (a->device >= 0) {
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return MPM_ERR_CUDA;
+    if (cur != a->device) {
+      if (cudaSetDevice(a->device) != cudaSuccess) return MPM_ERR_CUDA;
+      guard.saved = cur;
+    }
+  }
   float4* grid = nullptr;
   mpm_status st = scratch_for_current_device(&grid);
   if (st != MPM_OK) return st;
@@ -273,16 +318,5 @@ extern "C" mpm_status mpm_step_noalloc(const mpm_noalloc_step* a, void* cuda_str
   p.Fo = a->F_out;
   p.status = a->status;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
-  const int nb = (p.n_nodes + 255) / 256, pb = (p.N + 255) / 256;
-  k_na_clear<<<nb, 256, 0, s>>>(grid, p.n_nodes);  // the previous call's grid is still in the array
-  if (D == 2) {
-    if (p.N > 0) k_na_p2g<2><<<pb, 256, 0, s>>>(p, grid);
-    k_na_grid<2><<<nb, 256, 0, s>>>(p, grid);
-    if (p.N > 0) k_na_g2p<2><<<pb, 256, 0, s>>>(p, grid);
-  } else {
-    if (p.N > 0) k_na_p2g<3><<<pb, 256, 0, s>>>(p, grid);
-    k_na_grid<3><<<nb, 256, 0, s>>>(p, grid);
-    if (p.N > 0) k_na_g2p<3><<<pb, 256, 0, s>>>(p, grid);
-  }
-  return cudaGetLastError() == cudaSuccess ? MPM_OK : MPM_ERR_CUDA;
+  return D == 2 ? na_enqueue<2>(p, grid, s) : na_enqueue<3>(p, grid, s);
 }
