@@ -381,8 +381,17 @@ class Scene:
         self.G = G
         self.impl = impl
 
+    # Every call that changes what the next reverse pass would differentiate (the state, the
+    # rollout, the parameters, the material, the walls, a batch admission) bumps ``generation``;
+    # the autograd Function records it and refuses a backward through a later rollout.
+    generation = 0
+
+    def _touch(self):
+        self.generation += 1
+
     # ------------------------------------------------------------------ forward
     def step(self, n: int = 1):
+        self._touch()
         _check(lib().mpm_step(self.handle, int(n)), "mpm_step")
 
     def set_tuning(self, mode: int):
@@ -397,6 +406,7 @@ class Scene:
         return a.value, t.value, bool(d.value)
 
     def rollout(self, n_steps: int, ckpt_interval: int = 0, mem_budget: int = 0):
+        self._touch()
         _check(lib().mpm_rollout(self.handle, int(n_steps), int(ckpt_interval), C.c_size_t(int(mem_budget))),
                "mpm_rollout")
 
@@ -421,12 +431,14 @@ class Scene:
         N, d = self.N, self.dim
         dev = _is_torch(x) and x.is_cuda
         arrs = [_f32(x, (N, d)), _f32(v, (N, d)), _f32(Cm, (N, d, d)), _f32(F, (N, d, d))]
+        self._touch()
         _check(lib().mpm_set_state(self.handle, *[_ptr(a) for a in arrs], int(step), 1 if dev else 0),
                "mpm_set_state")
 
     def set_params(self, params):
         dev = _is_torch(params) and params.is_cuda
         p = _f32(params, (self.n_params,))
+        self._touch()
         _check(lib().mpm_set_ctrl_params(self.handle, _ptr(p), self.n_params, 1 if dev else 0), "mpm_set_ctrl_params")
 
     def get_grid(self):
@@ -484,6 +496,7 @@ class Scene:
         for a in conv:
             if a is not None and (a.numel() if _is_torch(a) else a.size) != self.N:
                 raise ValueError("per-particle material arrays need one entry per particle")
+        self._touch()
         _check(lib().mpm_scene_set_material(self.handle, _ptr(conv[0]), _ptr(conv[1]), 1 if on_dev else 0),
                "mpm_scene_set_material")
 
@@ -496,6 +509,7 @@ class Scene:
         for a in (k, cc):
             if a is not None and a.size != nw:
                 raise ValueError(f"per-wall arrays need {nw} entries")
+        self._touch()
         _check(lib().mpm_scene_set_walls(self.handle, _ptr(k), _ptr(cc)), "mpm_scene_set_walls")
 
     def material_gradients(self):
@@ -664,6 +678,7 @@ class Batch:
 
     def admit(self, scene: "Scene", n_steps: int, want_grad: bool) -> int:
         slot = C.c_int(-1)
+        scene._touch()
         _check(lib().mpm_batch_admit(self.handle, scene.handle, int(n_steps), int(bool(want_grad)), C.byref(slot)),
                "mpm_batch_admit")
         return slot.value

@@ -31,6 +31,7 @@ class Rollout(torch.autograd.Function):
         FT = torch.empty((N, d, d), device=dev)
         scene.get_state(out=(xT, vT, CT, FT))
         ctx.scene = scene
+        ctx.generation = scene.generation
         ctx.n_params = params.numel()
         ctx.dev = dev
         return xT, vT, CT, FT
@@ -38,6 +39,10 @@ class Rollout(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gxT, gvT, gCT, gFT):
         scene = ctx.scene
+        if scene.generation != ctx.generation:
+            # the library differentiates the scene's latest rollout, not the one this graph recorded
+            raise RuntimeError("the scene was rolled out, stepped or changed again after this rollout's forward; "
+                               "run backward before reusing the scene, or give each rollout its own scene")
         N, d, dev = scene.N, scene.dim, ctx.dev
         seeds = [None if g is None else g.contiguous().to(dev, torch.float32) for g in (gxT, gvT, gCT, gFT)]
         outs = (torch.empty((N, d), device=dev), torch.empty((N, d), device=dev),

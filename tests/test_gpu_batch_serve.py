@@ -165,6 +165,27 @@ def test_autograd_function_matches_library_and_oracle(M, ctx):
     assert_grad_close(F0.grad.cpu().numpy(), ogF, "autograd dL/dF0")
 
 
+def test_autograd_refuses_a_backward_through_a_stale_rollout(M, ctx):
+    """The library differentiates a scene's latest rollout; a graph whose scene was rolled out
+    again before its backward is refused instead of returning the later rollout's gradients."""
+    torch = pytest.importorskip("torch")
+    from paper_1810_01054_gb300.rollout import rollout
+    dev = torch.device("cuda", 0)
+    spec = S.walker_square_2d(0, n_steps=10)
+    sc = M.Scene(ctx, spec)
+    t = lambda a: torch.tensor(np.asarray(a), dtype=torch.float32, device=dev, requires_grad=True)
+    leaves = lambda: (t(spec.x0), t(spec.v0), t(spec.C0), t(spec.F0), t(spec.ctrl_params))
+    first = leaves()
+    xT1 = rollout(sc, 10, *first)[0]
+    second = leaves()
+    xT2 = rollout(sc, 5, *second)[0]
+    with pytest.raises(RuntimeError, match="rolled out"):
+        xT1[:, 0].mean().backward()
+    xT2[:, 0].mean().backward()  # the latest rollout still differentiates
+    assert torch.isfinite(second[1].grad).all() and second[1].grad.abs().max() > 0
+    sc.close()
+
+
 def test_context_outlives_its_scenes_and_batches(M):
     """The C context refuses to go while scenes or batches use it; the binding closes them first."""
     c = M.Context(0)
