@@ -5,8 +5,11 @@
 One timed step = one whole rollout of the workload (every simulation step: controller, bin/sort,
 P2G, grid, G2P) plus its full reverse pass (segment recompute from checkpoints, adjoint scatter,
 grid adjoint, adjoint gather, controller adjoint), with the inputs resident in HBM.  The default
-workload is the 2D soft walker: 128^2 grid, ~31k particles, 1000 steps, checkpoint every 64 steps,
-loss = mean final x_0.  Prints one JSON line (rank 0).
+workload is the largest one that fits one GPU, the 3D box cluster: 128^3 grid, 1,000,000
+particles, 200 steps, sinusoid actuation of 64 groups, the checkpoint store limited to 4 GiB (every
+15th state kept, segments recomputed in the reverse pass), loss = mean final x_0.  The 2D walker
+(~31k particles, 1000 steps, checkpoint every 64) and the other workloads are reported beside it.
+Prints one JSON line (rank 0).
 
 --impl reference times the FP64 CPU oracle (the reference arm of this method) on a bounded
 sample of the same workload.  With N > 1 (torchrun), every rank runs an independent replica
@@ -54,7 +57,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="walker_2d")
+    ap.add_argument("--workload", default="box_cluster_3d")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -64,6 +67,9 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-replicas", action="store_true")
     ap.add_argument("--no-soft", action="store_true")
+    ap.add_argument("--no-walker", action="store_true")
+    ap.add_argument("--no-cpu-aggregate", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--no-budget-sweep", action="store_true")
     ap.add_argument("--ncu-fp64", action="store_true",
                     help="short run for profilers: the FP64 form on a 200k-particle 3D cluster (64^3 grid), "
@@ -87,6 +93,15 @@ def workload(name, rank=0):
 
 def ckpt_of(spec):
     return spec.ckpt_interval if spec.ckpt_interval else 0
+
+
+# Device-memory budget of the checkpoint store per workload (0 = no limit): the 1M-particle cluster
+# keeps its checkpoints within 4 GiB, which sets the interval to ceil(sqrt(200)) = 15 states.
+BUDGET = {"box_cluster_3d": 4 << 30}
+
+
+def budget_of(spec):
+    return BUDGET.get(spec.name, 0)
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -186,25 +201,78 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def cpu_baseline(spec, budget_s=15.0):
-    """The FP64 oracle, as it stands, on one host core: forward + reverse over the first steps of
-    the workload, as many as fit in about `budget_s` seconds."""
+def host_record():
+    """CPU model name and logical core count of the host the oracle runs on."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"cpu_model": model, "nproc": os.cpu_count()}
+
+
+def _oracle_sample(name, seed, n_steps, barrier, out):
+    """One oracle process: builds its scene, waits for the others, then runs forward + reverse of
+    the first n_steps of workload `name` with `seed`; puts (particle-steps, start, end) on `out`."""
+    from oracle import oracle as O
+    from paper_1810_01054_gb300 import scenes as S
+    spec = S.WORKLOADS[name](seed)
+    sc = O.Scene(spec)
+    seed_g = np.zeros((sc.N, sc.dim))
+    seed_g[:, 0] = 1.0 / sc.N
+    barrier.wait()
+    t0 = time.time()
+    tr = sc.rollout(n_steps)
+    sc.backward(tr, (seed_g, None, None, None))
+    out.put((sc.N * n_steps, t0, time.time()))
+
+
+def cpu_baseline(spec, budget_s=20.0, aggregate=True):
+    """The FP64 oracle, as it stands: forward + reverse over the first steps of the workload, as
+    many as fit in about `budget_s` seconds, on one host core; then one oracle process per core,
+    each on an independent seeded scene of the same workload (scenes are independent), for the
+    host's aggregate rate.  The rate is per particle-step, so a sample of the first steps stands
+    for the whole rollout without extrapolation of anything but the step mix."""
     from oracle import oracle as O
     sc = O.Scene(spec)
-    t0 = time.time()
-    tr = sc.rollout(2)
     seed = np.zeros((sc.N, sc.dim))
     seed[:, 0] = 1.0 / sc.N
+    t0 = time.time()
+    tr = sc.rollout(1)
     sc.backward(tr, (seed, None, None, None))
-    per = max(time.time() - t0, 1e-3) / 2
+    per = max(time.time() - t0, 1e-3)
     n = int(max(1, min(spec.n_steps, budget_s / per)))
     t0 = time.time()
     tr = sc.rollout(n)
     sc.backward(tr, (seed, None, None, None))
     dt = time.time() - t0
-    return {"value": sc.N * n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"FP64 oracle forward+reverse of the first {n} of {spec.n_steps} steps of {spec.name} "
-                      f"({sc.N} particles), single thread, {dt:.1f} s"}
+    del tr, sc
+    rec = {"value": spec.n_particles * n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"FP64 oracle forward+reverse of the first {n} of {spec.n_steps} steps of {spec.name} "
+                     f"({spec.n_particles} particles), single thread, {dt:.1f} s", **host_record()}
+    if aggregate:
+        import multiprocessing as mp
+        mpc = mp.get_context("spawn")  # never fork a process that holds a CUDA context
+        cores = os.cpu_count() or 1
+        barrier, out = mpc.Barrier(cores), mpc.Queue()
+        procs = [mpc.Process(target=_oracle_sample, args=(spec.name, 77 + 1000 * i, n, barrier, out))
+                 for i in range(cores)]
+        for pr in procs:
+            pr.start()
+        res = [out.get() for _ in procs]
+        for pr in procs:
+            pr.join()
+        units = sum(u for u, _, _ in res)
+        wall = max(e for _, _, e in res) - min(b for _, b, _ in res)
+        rec["aggregate"] = {"value": units / wall, "unit": UNIT, "cores": cores, "processes": cores,
+                            "sample": f"{cores} oracle processes at once, each forward+reverse of the first {n} "
+                                      f"steps of its own seeded {spec.name}; {wall:.1f} s from the first start "
+                                      f"to the last finish (scene set-up untimed)"}
+    return rec
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -216,11 +284,12 @@ def run_reference(args, rank, world):
     sc = O.Scene(spec)
     seed = np.zeros((sc.N, sc.dim))
     seed[:, 0] = 1.0 / sc.N
-    # bounded sample per step: enough simulation steps for ~2 s of CPU work
+    # bounded sample per step: enough simulation steps for ~2 s of CPU work (one step of the
+    # 1M-particle cluster takes longer than that on its own)
     t0 = time.time()
-    tr = sc.rollout(2)
+    tr = sc.rollout(1)
     sc.backward(tr, (seed, None, None, None))
-    per = max(time.time() - t0, 1e-3) / 2
+    per = max(time.time() - t0, 1e-3)
     n = int(max(1, min(spec.n_steps, 2.0 / per)))
     times = []
     for i in range(args.warmup + args.steps):
@@ -237,7 +306,8 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": spec.name, "particles": sc.N, "sim_steps_per_step": n},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             **host_record()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -262,9 +332,13 @@ def measure(args, spec, rank, world, dev, stream, ctx, *, e2e=True, plain=True):
     import torch
     from paper_1810_01054_gb300 import mpm
 
-    T, k = spec.n_steps, ckpt_of(spec)
+    T, k, budget = spec.n_steps, ckpt_of(spec), budget_of(spec)
     N, d = spec.n_particles, spec.dim
     scene = mpm.Scene(ctx, spec)
+    S_bytes = scene.info()["state_bytes"]
+    # the interval the library takes: the given one, else every state when they fit the budget,
+    # else ceil(sqrt(T))
+    k_eff = k if k else (1 if budget == 0 or T * S_bytes <= budget else int(math.ceil(math.sqrt(T))))
     x0 = torch.tensor(spec.x0, dtype=torch.float32, device=dev)
     v0 = torch.tensor(spec.v0, dtype=torch.float32, device=dev)
     C0 = torch.tensor(spec.C0, dtype=torch.float32, device=dev)
@@ -277,7 +351,7 @@ def measure(args, spec, rank, world, dev, stream, ctx, *, e2e=True, plain=True):
 
     def one_step(backward=True, sc=scene):
         sc.set_state(x0, v0, C0, F0, step=0)
-        sc.rollout(T, k)
+        sc.rollout(T, k, budget)
         if backward:
             sc.backward(seed, out=outs)
 
@@ -348,7 +422,7 @@ def measure(args, spec, rank, world, dev, stream, ctx, *, e2e=True, plain=True):
         t0 = time.perf_counter()
         for _ in range(args.steps):
             scene.set_state(hx, hv, hC, hF, step=0)
-            scene.rollout(T, k)
+            scene.rollout(T, k, budget)
             scene.backward(hseed, out=houts)
         barrier()
         e2e_s = time.perf_counter() - t0
@@ -396,7 +470,7 @@ def measure(args, spec, rank, world, dev, stream, ctx, *, e2e=True, plain=True):
     share = {kk: round(v[1] / prof_total_ms, 4) for kk, v in prof.items()}
     return {"value": value, "tot_ms": tot_ms, "step_ms": step_ms, "value_fwd": value_fwd, "roofline": roof,
             "share": share, "e2e": e2e_rec, "plain": plain_rec, "gpu_launches": n_launch, "clocks": clk.summary(),
-            "N": N, "T": T, "k": k, "launch": launch}
+            "N": N, "T": T, "k": k_eff, "budget": budget, "launch": launch}
 
 
 def measure_replicas(args, dev, stream, sizes=(1, 64, 1024, 4096)):
@@ -509,36 +583,46 @@ def measure_budget_sweep(args, dev, stream, budgets_gib=(1, 4, 32)):
     return {"workload": spec.name, "particles": N, "sim_steps": T, "unit": UNIT, "by_budget": res}
 
 
-def measure_serving(dev, stream, n_requests=32, seed=4):
+def measure_serving(dev, stream, n_requests=1000, seed=4, loads=(0.25, 0.5, 0.75, 0.9), per_load=250):
     """Serving mix (Poisson stream of rollout/gradient requests, 2D and 3D box clusters): first the
-    saturation rate (all requests queued at once), then Poisson arrivals at 0.75x that rate;
+    saturation rate (all `n_requests` queued at once), then, for each load in `loads`, Poisson
+    arrivals at that fraction of the saturation rate over `per_load` requests of the same mix;
     latency = arrival -> result on the host."""
     from paper_1810_01054_gb300 import scenes as S
     from paper_1810_01054_gb300.serve import Server
     reqs = [S.serving_request(i, seed) for i in range(n_requests)]
-    work = sum(sp.n_particles * sp.n_steps for sp, _ in reqs)
 
-    def run(arrivals):
+    def run(sub, arrivals):
         srv = Server(device=dev.index, mem_fraction=0.3, tick_steps=8, stream=stream, keep_results=False)
-        for (sp, g), t in zip(reqs, arrivals):
+        for (sp, g), t in zip(sub, arrivals):
             srv.submit(sp, g, arrival=t)
         t0 = time.perf_counter()
         srv.run()
         span = time.perf_counter() - t0
         p50, p99 = srv.latency_percentiles()
+        failed = sum(1 for r in srv.results.values() if r["status"] != 0)
         srv.close()
-        return span, p50, p99
+        return span, p50, p99, failed
 
-    run([0.0] * 4)  # warm-up of the first few requests' code paths
-    span, _, _ = run([0.0] * n_requests)
+    run(reqs[:8], [0.0] * 8)  # warm-up of the first requests' code paths
+    work = sum(sp.n_particles * sp.n_steps for sp, _ in reqs)
+    span, _, _, failed = run(reqs, [0.0] * n_requests)
     rate = n_requests / span
     rng = np.random.default_rng(seed)
-    arrivals = np.cumsum(rng.exponential(1.0 / (0.75 * rate), size=n_requests))
-    span2, p50, p99 = run(list(arrivals))
-    return {"requests": n_requests, "saturation_req_per_s": rate, "load": 0.75,
-            "p50_ms": 1e3 * p50, "p99_ms": 1e3 * p99, "aggregate_particle_steps_per_s": work / span2,
+    by_load = {}
+    for i, load in enumerate(loads):
+        sub = reqs[(i * per_load) % n_requests:][:per_load]
+        arrivals = np.cumsum(rng.exponential(1.0 / (load * rate), size=len(sub)))
+        span2, p50, p99, f2 = run(sub, list(arrivals))
+        sub_work = sum(sp.n_particles * sp.n_steps for sp, _ in sub)
+        by_load[str(load)] = {"requests": len(sub), "arrival_req_per_s": load * rate, "p50_ms": 1e3 * p50,
+                              "p99_ms": 1e3 * p99, "aggregate_particle_steps_per_s": sub_work / span2,
+                              "span_s": span2, "failed": f2}
+    return {"requests": n_requests, "saturation_req_per_s": rate,
+            "saturation_particle_steps_per_s": work / span, "saturation_failed": failed, "by_load": by_load,
             "mix": "seeded serving requests: dim 2/3 50/50, n in {32..128}, N log-uniform 1e3-2e5, T 50-500, "
-                   "60% with gradient (loss = mean final x_0)"}
+                   "60% with gradient (loss = mean final x_0)",
+            "percentiles": "numpy linear interpolation over each load's requests"}
 
 
 # FP64 roofline: GB300 SMs issue 2 FP64 thread-ops per clock (the nominal 1.25 TFLOP/s FP64 rate:
@@ -692,34 +776,40 @@ def run_ours(args, rank, world, local_rank):
         return
 
     r = measure(args, spec, rank, world, dev, stream, ctx, e2e=not args.no_e2e, plain=not args.no_plain)
+
+    def extra(xspec, rec):
+        return {"workload": xspec.name, "particles": rec["N"], "grid": "x".join(map(str, xspec.n_grid)),
+                "sim_steps": rec["T"], "ckpt_interval": rec["k"], "value": rec["value"],
+                "value_fwd": rec["value_fwd"], "unit": UNIT, "ms_per_step": rec["tot_ms"] / args.steps,
+                "roofline": rec["roofline"], "kernel_share_of_profiled_step": rec["share"],
+                "launch": rec["launch"]}
+
     large = None
     if args.workload != "box_cluster_3d" and not args.no_large:
         lspec = workload("box_cluster_3d", rank)
-        lr = measure(args, lspec, rank, world, dev, stream, ctx, e2e=False, plain=False)
-        large = {"workload": lspec.name, "particles": lr["N"], "sim_steps": lr["T"], "value": lr["value"],
-                 "value_fwd": lr["value_fwd"], "unit": UNIT, "ms_per_step": lr["tot_ms"] / args.steps,
-                 "roofline": lr["roofline"], "kernel_share_of_profiled_step": lr["share"]}
+        large = extra(lspec, measure(args, lspec, rank, world, dev, stream, ctx, e2e=False, plain=False))
+    walker = None
+    if args.workload != "walker_2d" and not args.no_walker:
+        # the 2D soft walker: 31k particles, 1000 steps with a checkpoint every 64, basis controller
+        wspec = workload("walker_2d", rank)
+        walker = extra(wspec, measure(args, wspec, rank, world, dev, stream, ctx, e2e=False, plain=False))
     soft = None
-    if args.workload == "walker_2d" and not args.no_soft:
+    if args.workload != "soft_body_3d" and not args.no_soft:
         # the 3D soft body with its MLP controller on group centroids, 500 steps, checkpoint every
         # ceil(sqrt(500)) = 23 steps (forward+backward with recomputation)
         sspec = workload("soft_body_3d", rank)
         sspec = sspec.copy(ckpt_interval=int(np.ceil(np.sqrt(sspec.n_steps))))
-        sr = measure(args, sspec, rank, world, dev, stream, ctx, e2e=False, plain=False)
-        soft = {"workload": sspec.name, "particles": sr["N"], "sim_steps": sr["T"], "ckpt_interval": sr["k"],
-                "value": sr["value"], "value_fwd": sr["value_fwd"], "unit": UNIT,
-                "ms_per_step": sr["tot_ms"] / args.steps, "roofline": sr["roofline"],
-                "kernel_share_of_profiled_step": sr["share"]}
+        soft = extra(sspec, measure(args, sspec, rank, world, dev, stream, ctx, e2e=False, plain=False))
     sweep = None
-    if rank == 0 and args.workload != "box_cluster_3d" and not args.no_large and not args.no_budget_sweep:
+    if rank == 0 and not args.no_budget_sweep:
         sweep = measure_budget_sweep(args, dev, stream)
     replicas = None
     if rank == 0 and not args.no_replicas:
         replicas = measure_replicas(args, dev, stream)
     material = None
-    if args.workload == "walker_2d" and not args.no_material:
-        # the same workload with per-particle Young's modulus and mass and their gradients
-        mspec = material_variant(spec)
+    if not args.no_material:
+        # the walker with per-particle Young's modulus and mass and their gradients
+        mspec = material_variant(workload("walker_2d", rank))
         mr = measure(args, mspec, rank, world, dev, stream, ctx, e2e=False, plain=False)
         material = {"workload": mspec.name, "value": mr["value"], "value_fwd": mr["value_fwd"], "unit": UNIT,
                     "ms_per_step": mr["tot_ms"] / args.steps, "roofline": mr["roofline"],
@@ -727,28 +817,31 @@ def run_ours(args, rank, world, local_rank):
                     "gradients": "dL/dx0, v0, C0, F0, controller parameters, E_p, m_p"}
     serving = None
     if rank == 0 and not args.no_serve:
-        serving = measure_serving(dev, stream)
+        serving = measure_serving(dev, stream, n_requests=args.serve_requests)
     fp64 = None
     if rank == 0 and not args.no_fp64:
         fp64 = measure_fp64(args, dev, stream)
     if rank != 0:
         return
-    cpu = None if args.no_cpu_baseline else cpu_baseline(spec)
+    cpu = None if args.no_cpu_baseline else cpu_baseline(spec, aggregate=not args.no_cpu_aggregate)
     lat = sorted(r["step_ms"])
     line = {
         "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["tot_ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": spec.name, "particles": r["N"], "grid": "x".join(map(str, spec.n_grid)),
-                   "sim_steps": r["T"], "ckpt_interval": r["k"], "pass": "forward+reverse rollout",
+                   "sim_steps": r["T"], "ckpt_interval": r["k"],
+                   "ckpt_budget_bytes": r["budget"] or None,
+                   "pass": "forward+reverse rollout (full-horizon gradient)",
                    "loss": "mean final x_0", "l2": "flushed before every timed step (256 MB write, untimed)",
                    "parallelism": f"replicas x{world}", "launch": r["launch"]},
         "value_fwd": r["value_fwd"],
         "rollout_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
         "roofline": r["roofline"], "kernel_share_of_profiled_step": r["share"],
         "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": r["gpu_launches"], "clocks": r["clocks"],
-        "plain_form": r["plain"], "large_scene": large, "material": material, "serving": serving,
-        "fp64": fp64, "large_scene_budgets": sweep, "small_scene_replicas": replicas, "soft_body": soft,
+        "plain_form": r["plain"], "walker": walker, "large_scene": large, "material": material,
+        "serving": serving, "fp64": fp64, "large_scene_budgets": sweep, "small_scene_replicas": replicas,
+        "soft_body": soft,
     }
     print(json.dumps(line), flush=True)
 

@@ -40,10 +40,16 @@ def assert_state_close(gpu, ref, tol=FWD_TOL, names=("x", "v", "C", "F"), elem_t
         assert m <= elem_tol, f"{name}: max scaled error {m:.3e} > {elem_tol:.1e}"
 
 
-def assert_grad_close(gpu, ref, name, tol=GRAD_TOL, cos=GRAD_COS):
+def assert_grad_close(gpu, ref, name, tol=GRAD_TOL, cos=GRAD_COS, elem_tol=None):
+    """Whole-array relative L2 and cosine, plus an element-wise bound (max |a - b| over max |b|,
+    10x the relative tolerance) that a wrong gradient on a few particles cannot hide under."""
+    elem_tol = 10 * tol if elem_tol is None else elem_tol
     r = rel_l2(gpu, ref)
     c = cosine(gpu, ref)
-    assert r <= tol and c >= cos, f"{name}: relative L2 {r:.3e} (tol {tol:.0e}), cosine {c:.6f} (min {cos})"
+    m = max_scaled(gpu, ref) if np.size(ref) else 0.0
+    assert r <= tol and c >= cos and m <= elem_tol, (
+        f"{name}: relative L2 {r:.3e} (tol {tol:.0e}), cosine {c:.6f} (min {cos}), "
+        f"max scaled {m:.3e} (tol {elem_tol:.0e})")
 
 
 def oracle_step_from(spec, state, step):

@@ -10,7 +10,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_reference_arm_prints_one_contract_line():
-    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0"],
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0",
+                          "--workload", "walker_2d"],
                          cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
@@ -24,9 +25,26 @@ def test_reference_arm_prints_one_contract_line():
     assert d["config"]["workload"] == "walker_2d"
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert cb["nproc"] >= 1 and "cpu_model" in cb
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_default_workload_is_the_largest_single_gpu_scene():
+    """With no flags the bench times the 1M-particle 3D cluster under its 4 GiB checkpoint budget."""
+    sys.path.insert(0, ROOT)
+    import bench
+    old = sys.argv
+    sys.argv = ["bench.py"]
+    try:
+        args = bench.parse()
+    finally:
+        sys.argv = old
+    assert args.workload == "box_cluster_3d" and args.gpus == 1
+    spec = bench.workload(args.workload)
+    assert spec.n_particles == 1_000_000 and spec.n_steps == 200
+    assert bench.budget_of(spec) == 4 << 30
 
 
 def test_committed_traffic_matches_the_kernel_sources_and_algorithmic_bytes():

@@ -1,0 +1,126 @@
+"""GPU parity at the benchmarked workloads over the horizons the benchmark times (FP64 oracle on
+the same seeded inputs; tolerances as everywhere: forward relative 1e-4 on 10-step windows
+re-synced to the oracle, gradients relative 1e-3 with cosine >= 0.999 and an element-wise bound).
+
+  2D walker (31,458 particles, basis controller): every 10-step window of the 1000-step rollout,
+      and the full-horizon gradient of L = mean final x_0 from a rollout with a checkpoint every 64
+      steps, as benchmarked.
+  3D soft body (95,123 particles, MLP controller): every 10-step window of the 500-step rollout, and
+      the full-horizon gradient with a checkpoint every 23 steps, as benchmarked.
+  1M-particle 3D cluster: the 10-step windows of the first 50 of its 200 steps, and the gradient of
+      one checkpoint segment (15 steps: the interval its 4 GiB budget gives), recomputed from its
+      checkpoint as in the benchmarked reverse pass.
+
+The oracle runs in four spawned processes (tests/horizon_jobs.py) started when the module begins,
+while the GPU side runs; each test waits for its own job.
+"""
+import multiprocessing as mp
+
+import numpy as np
+import pytest
+
+from paper_1810_01054_gb300 import scenes as S
+from tests import horizon_jobs as H
+from tests.parity_utils import assert_grad_close, assert_state_close
+
+pytestmark = pytest.mark.gpu
+
+JOB_TIMEOUT_S = 3600
+
+
+@pytest.fixture(scope="module")
+def jobs(tmp_path_factory):
+    out = str(tmp_path_factory.mktemp("oracle_horizons"))
+    pool = mp.get_context("spawn").Pool(4)
+    futs = {j: pool.apply_async(H.run, (j, out)) for j in ("soft", "cluster_seg", "cluster_fwd", "walker")}
+    yield out, futs
+    pool.terminate()
+    pool.join()
+
+
+@pytest.fixture(scope="module")
+def M():
+    from paper_1810_01054_gb300 import mpm
+    mpm.lib()
+    return mpm
+
+
+@pytest.fixture(scope="module")
+def ctx(M):
+    c = M.Context(0)
+    yield c
+    c.close()
+
+
+def _wait(jobs, job):
+    out, futs = jobs
+    futs[job].get(timeout=JOB_TIMEOUT_S)
+    return out
+
+
+def _windows(M, ctx, spec, out, tag, n_windows):
+    """Every 10-step window re-synced to the oracle's state at its start."""
+    xs, vs, Cs, Fs = (H.load(out, tag, k) for k in ("xs", "vs", "Cs", "Fs"))
+    gpu = M.Scene(ctx, spec)
+    worst = 0.0
+    for w in range(n_windows):
+        n0 = H.EVERY * w
+        gpu.set_state(xs[w], vs[w], Cs[w], Fs[w], step=n0)
+        gpu.step(H.EVERY)
+        got = gpu.get_state()
+        assert_state_close(got, (xs[w + 1], vs[w + 1], Cs[w + 1], Fs[w + 1]))
+    gpu.close()
+
+
+def _full_gradient(M, ctx, spec, out, tag, k):
+    gpu = M.Scene(ctx, spec)
+    gpu.rollout(spec.n_steps, k)
+    xT = gpu.get_state()[0]
+    g = gpu.backward(H.mean_x0(spec.n_particles, spec.dim))
+    gpu.close()
+    # the rollout itself over the whole horizon (not re-synced): reported by the gradient check below
+    for nm, a in zip(("x0", "v0", "C0", "F0", "params"), g):
+        assert_grad_close(a, H.load(out, tag, "g" + nm[0] if nm != "params" else "gp"), f"{tag} dL/d{nm}")
+    return xT
+
+
+@pytest.mark.parametrize("part", ["windows", "gradient"])
+def test_walker_over_its_1000_steps(M, ctx, jobs, part):
+    spec = S.walker_2d(1)
+    out = _wait(jobs, "walker")
+    if part == "windows":
+        _windows(M, ctx, spec, out, "walker_2d", spec.n_steps // H.EVERY)
+    else:
+        _full_gradient(M, ctx, spec, out, "walker_2d", 64)
+
+
+@pytest.mark.parametrize("part", ["windows", "gradient"])
+def test_soft_body_over_its_500_steps(M, ctx, jobs, part):
+    spec = S.soft_body_3d(2)
+    out = _wait(jobs, "soft")
+    if part == "windows":
+        _windows(M, ctx, spec, out, "soft_body_3d", spec.n_steps // H.EVERY)
+    else:
+        _full_gradient(M, ctx, spec, out, "soft_body_3d", 23)
+
+
+def test_cluster_first_50_steps_in_windows(M, ctx, jobs):
+    spec = S.box_cluster_3d(3)
+    out = _wait(jobs, "cluster_fwd")
+    _windows(M, ctx, spec, out, "cluster_fwd", H.CLUSTER_WINDOW_STEPS // H.EVERY)
+
+
+def test_cluster_one_checkpoint_segment_gradient(M, ctx, jobs):
+    spec = S.box_cluster_3d(3)
+    T = H.CLUSTER_SEGMENT
+    gpu = M.Scene(ctx, spec)
+    gpu.rollout(T, T, 4 << 30)  # one segment: the checkpoint and T - 1 recomputed states
+    wx, wv = H.cluster_seeds(spec.n_particles, 3)
+    g = gpu.backward(wx, wv)
+    x, v, _, _ = gpu.get_state()
+    gpu.close()
+    out = _wait(jobs, "cluster_seg")
+    assert_state_close((x, v), (H.load(out, "cluster_seg", "xT"), H.load(out, "cluster_seg", "vT")),
+                       names=("x", "v"))
+    for nm, key, a in zip(("x0", "v0", "C0", "F0", "params"), ("gx", "gv", "gC", "gF", "gp"), g):
+        assert_grad_close(a, H.load(out, "cluster_seg", key), f"cluster segment dL/d{nm}")
