@@ -529,10 +529,12 @@ def measure_replicas(args, dev, stream, sizes=(1, 64, 1024, 4096)):
             "pass": "forward+reverse per replica, one batch", "by_replicas": out}
 
 
-def measure_budget_sweep(args, dev, stream, budgets_gib=(1, 4, 32)):
+def measure_budget_sweep(args, dev, stream, budgets_gib=(32, 4, 1)):
     """Full-horizon gradient of the 1M-particle cluster (200 steps) under device-memory budgets for
-    the checkpoint store: the library keeps every state when they fit (k = 1), else every
-    ceil(sqrt(T))-th and recomputes the segments; a budget below that is refused (MPM_ERR_OOM)."""
+    the checkpoint store: every state when they fit (k = 1); else every ceil(sqrt(T))-th state with
+    the segments recomputed (the recompute beside the reverse steps when the budget leaves room);
+    below that the multi-level store (a recursive schedule planned for the fewest recomputed steps).
+    Each budget's final state and gradients are compared bit for bit with the first budget's."""
     import torch
     from paper_1810_01054_gb300 import mpm
     spec = workload("box_cluster_3d")
@@ -545,14 +547,18 @@ def measure_budget_sweep(args, dev, stream, budgets_gib=(1, 4, 32)):
     seed[:, 0] = 1.0 / N
     outs = [torch.empty((N, d), device=dev), torch.empty((N, d), device=dev), torch.empty((N, d, d), device=dev),
             torch.empty((N, d, d), device=dev), torch.empty((max(sc.n_params, 1),), device=dev)]
+    final = [torch.empty((N, d), device=dev), torch.empty((N, d), device=dev), torch.empty((N, d, d), device=dev),
+             torch.empty((N, d, d), device=dev)]
     S = sc.info()["state_bytes"]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    res = {}
+    res, ref = {}, None
     for gib in budgets_gib:
         budget = gib << 30
-        k = 1 if T * S <= budget else int(np.ceil(np.sqrt(T)))
-        stored = (T + k - 1) // k + (k - 1)  # checkpoints + one segment's recompute buffers
-        rec = {"ckpt_interval": k, "stored_states": stored, "store_gb": stored * S / 1e9}
+        fwd_steps, stored, multi = mpm.plan_checkpoints(T, budget // S)
+        rec = {"store": "multi-level" if multi else "single-level", "stored_states": stored,
+               "store_gb": stored * S / 1e9, "forward_steps": fwd_steps}
+        if not multi:
+            rec["ckpt_interval"] = 1 if T * S <= budget else int(np.ceil(np.sqrt(T)))
 
         def one():
             sc.set_state(x0, v0, C0, F0, step=0)
@@ -565,6 +571,12 @@ def measure_budget_sweep(args, dev, stream, budgets_gib=(1, 4, 32)):
             rec["status"] = e.status
             res[f"{gib}GiB"] = rec
             continue
+        sc.get_state(out=final)
+        got = [o.clone() for o in outs + final]
+        if ref is None:
+            ref = got
+        else:
+            rec["bitwise_equal_to_" + f"{budgets_gib[0]}GiB"] = all(torch.equal(a, b) for a, b in zip(got, ref))
         ms = []
         for _ in range(2):
             flush.zero_()
@@ -580,7 +592,8 @@ def measure_budget_sweep(args, dev, stream, budgets_gib=(1, 4, 32)):
         res[f"{gib}GiB"] = rec
     sc.close()
     ctx.close()
-    return {"workload": spec.name, "particles": N, "sim_steps": T, "unit": UNIT, "by_budget": res}
+    return {"workload": spec.name, "particles": N, "sim_steps": T, "unit": UNIT, "state_bytes": S,
+            "by_budget": res}
 
 
 def measure_serving(dev, stream, n_requests=1000, seed=4, loads=(0.25, 0.5, 0.75, 0.9), per_load=250):

@@ -129,9 +129,23 @@ mpm_status mpm_step(mpm_scene* scene, int n_steps);
  * asynchronously; the checkpoint buffers are kept for the next rollout of the same shape.
  * storing the state every ckpt_interval steps (0 = choose from mem_budget_bytes: every step if
  * all states fit, else about sqrt(n_steps)); the states in between are recomputed by
- * mpm_backward.  Fails with MPM_ERR_OOM if even the chosen interval exceeds the budget
- * (mem_budget_bytes = 0 means no limit). */
+ * mpm_backward.  mem_budget_bytes = 0 means no limit.
+ * With ckpt_interval = 0 and a budget below that single-level store ((ceil(T/k) + k - 1) states),
+ * the rollout keeps a multi-level store instead: a recursive schedule (store a state, reverse the
+ * later part, release it, reverse the earlier part) planned for the fewest recomputed steps within
+ * floor(budget / state size) states, at least 3 (the first and final states and one more), for
+ * rollouts of up to 8192 steps; mpm_plan_checkpoints reports its cost.  Its gradients are the same
+ * bits as the single-level store's.  Such a rollout supports one mpm_backward, and mpm_get_state
+ * of a stored step returns MPM_ERR_STATE.  MPM_ERR_OOM when neither store fits the budget. */
 mpm_status mpm_rollout(mpm_scene* scene, int n_steps, int ckpt_interval, size_t mem_budget_bytes);
+
+/* The schedule mpm_rollout(scene, n_steps, 0, budget) takes, for a budget of budget_states whole
+ * states (budget / state size; 0 = no limit): forward steps it runs over the rollout and its
+ * reverse pass together (n_steps when every state is kept; the reverse steps themselves are
+ * n_steps in every schedule), the number of states it stores at most, and whether the multi-level
+ * store is used (NULL outputs are skipped).  MPM_ERR_OOM when no schedule fits.  Host only. */
+mpm_status mpm_plan_checkpoints(int n_steps, long long budget_states, long long* forward_steps, int* states_used,
+                                int* multi_level);
 
 /* Reverse pass of the last rollout (Supplement S2-S5 at every step, chained to the first state
  * and to the controller parameters used at every step).  Seeds are dL/d(final x, v, C, F)

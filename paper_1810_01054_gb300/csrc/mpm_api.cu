@@ -19,6 +19,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/mpm.h"
@@ -505,12 +506,29 @@ mpm_status run_phase(mpm_scene* s, int ph, int count, cudaStream_t graph_stream 
 }
 
 
+void free_ml_pool(mpm_scene* s) {
+  if (!s->ml_allocs.empty()) cudaStreamSynchronize(s->ctx->stream);
+  for (void* p : s->ml_allocs) cudaFree(p);
+  s->ml_allocs.clear();
+  s->ml_pool.clear();
+  s->ml_free.clear();
+  s->ml_base_slots.clear();
+  s->ml_spine.clear();
+  s->roll_multi = false;
+  if (s->pool_backed) {
+    s->ckpt.clear();
+    s->seg.clear();
+    s->pool_backed = false;
+  }
+}
+
 void free_rollout(mpm_scene* s) {
   if (!s->roll_allocs.empty()) cudaStreamSynchronize(s->ctx->stream);
   for (void* p : s->roll_allocs) cudaFree(p);
   s->roll_allocs.clear();
   s->ckpt.clear();
   s->seg.clear();
+  s->pool_backed = false;
   s->seg2.clear();
   s->sort_store = nullptr;
   s->ctrl_store = nullptr;
@@ -654,15 +672,28 @@ mpm_status read_status(mpm_scene* s) {
 
 // Rollout set-up: checkpoint buffers (kept when the shape repeats), the record table and the
 // per-step record map, the forward counter, and checkpoint 0 = the current state.
-mpm_status prepare_rollout(mpm_scene* s, int T, int k, size_t budget) {
-  s->have_rollout = false;
-  s->have_grad = false;
+mpm_status rollout_records(mpm_scene* s, int T, int k, size_t budget, bool copy_start);
+
+// Interval the single-level store takes for T steps under a budget (0 = every state when they
+// fit or there is no budget, else ceil(sqrt(T))), and whether its states fit.
+int auto_interval(const mpm_scene* s, int T, int k, size_t budget, bool* fits) {
   const size_t S = s->state_bytes;
   if (k == 0) k = (budget == 0 || size_t(T) * S <= budget) ? 1 : int(std::ceil(std::sqrt(double(T))));
   k = std::min(k, T);
   const int nseg = (T + k - 1) / k;
-  const size_t need = (size_t(nseg) + size_t(k - 1)) * S;
-  if (budget != 0 && need > budget) return MPM_ERR_OOM;
+  *fits = budget == 0 || (size_t(nseg) + size_t(k - 1)) * S <= budget;
+  return k;
+}
+
+mpm_status prepare_rollout(mpm_scene* s, int T, int k, size_t budget) {
+  s->have_rollout = false;
+  s->have_grad = false;
+  const size_t S = s->state_bytes;
+  bool fits = false;
+  k = auto_interval(s, T, k, budget, &fits);
+  const int nseg = (T + k - 1) / k;
+  if (!fits) return MPM_ERR_OOM;
+  if (!s->ml_allocs.empty()) free_ml_pool(s);  // the single-level store replaces a multi-level one
   if (int(s->ckpt.size()) != nseg || int(s->seg.size()) != k - 1) {
     free_rollout(s);  // buffers of another shape
     s->ckpt.assign(nseg, nullptr);
@@ -682,6 +713,15 @@ mpm_status prepare_rollout(mpm_scene* s, int T, int k, size_t budget) {
       }
     }
   }
+  return rollout_records(s, T, k, budget, true);
+}
+
+// Record table, per-step map and counters of a rollout of T steps with interval k over the
+// buffers in s->ckpt / s->seg; with copy_start checkpoint 0 takes a copy of the current state,
+// else it already holds the range's start (the multi-level store's slot).
+mpm_status rollout_records(mpm_scene* s, int T, int k, size_t budget, bool copy_start) {
+  const size_t S = s->state_bytes;
+  const int nseg = (T + k - 1) / k;
   // records: [0] state->state, [1 + 2j] state->ckpt[j], [2 + 2j] ckpt[j]->state, then (k = 1)
   // ckpt[n] -> ckpt[n+1]; every stored state is written by the step that produces it.
   std::vector<ScenePar> recs;
@@ -711,7 +751,7 @@ mpm_status prepare_rollout(mpm_scene* s, int T, int k, size_t budget) {
     CKS(upload_sel(s));
   }
   CKS(upload_map(s, 0, map, s->step));
-  CK(cudaMemcpyAsync(s->ckpt[0], s->state, S, cudaMemcpyDeviceToDevice, s->ctx->stream));
+  if (copy_start) CK(cudaMemcpyAsync(s->ckpt[0], s->state, S, cudaMemcpyDeviceToDevice, s->ctx->stream));
   CKS(set_counter(s, s->d_step, s->step));
   s->roll_T = T;
   s->roll_k = k;
@@ -724,11 +764,13 @@ mpm_status prepare_rollout(mpm_scene* s, int T, int k, size_t budget) {
 // Reverse-pass set-up: adjoint of the final state from the seeds, controller adjoint zeroed, the
 // record table of every segment's recompute and reverse steps, their maps, the reverse counter.
 mpm_status prepare_backward(mpm_scene* s, const float* gxT, const float* gvT, const float* gCT, const float* gFT,
-                            int mem_space, bool mean_x0_seed) {
+                            int mem_space, bool mean_x0_seed, int flags) {
   cudaStream_t st = s->ctx->stream;
   const int dim = s->dim, N = s->N, T = s->roll_T, k = s->roll_k, nseg = s->roll_nseg, n0 = s->roll_start;
   const size_t xb = sizeof(float) * size_t(N) * dim, mb = xb * dim;
-  if (mean_x0_seed) {  // dL/dx_T = e_0 / N written on the device
+  if (flags & BW_KEEP_SEED) {
+    // the adjoint of the range's last state is already in adj[0]
+  } else if (mean_x0_seed) {  // dL/dx_T = e_0 / N written on the device
     CK(launch_seed_mean_x0(dim, N, s->npad, s->adj[0], st));
   } else {
     CKS(ensure_scratch(s, 2 * xb + 2 * mb + 256));
@@ -750,8 +792,10 @@ mpm_status prepare_backward(mpm_scene* s, const float* gxT, const float* gvT, co
     CK(launch_pack(dim, N, s->npad, (const float*)a, (const float*)bv, (const float*)c, (const float*)f, s->adj[0],
                    s->d_status, st));
   }
-  CK(cudaMemsetAsync(s->ctrl.gparams, 0, sizeof(float) * std::max(1, s->nparams), st));
-  if (s->hp.gmat && N > 0) CK(cudaMemsetAsync(s->hp.gmat, 0, sizeof(float2) * size_t(N), st));
+  if (!(flags & BW_ACCUMULATE)) {
+    CK(cudaMemsetAsync(s->ctrl.gparams, 0, sizeof(float) * std::max(1, s->nparams), st));
+    if (s->hp.gmat && N > 0) CK(cudaMemsetAsync(s->hp.gmat, 0, sizeof(float2) * size_t(N), st));
+  }
   // A single scene's reverse pass recomputes segment sg-1 on the second stream while the reverse
   // steps of segment sg run: the recompute gets workspace 2 (with its own controller scratch) and
   // odd segments a second set of recompute buffers.  Not for batches (mean_x0_seed), the plain
@@ -761,7 +805,7 @@ mpm_status prepare_backward(mpm_scene* s, const float* gxT, const float* gvT, co
   const size_t ctrl_bytes = keep_ctrl ? 2 * size_t(k) * CTRL_SLOT_FLOATS * sizeof(float) : 0;
   const size_t store_bytes =
       2 * size_t(k) * sort_slot_words(s->npad, s->hp.n_tiles) * sizeof(uint32_t) + ctrl_bytes;
-  const bool overlap = !mean_x0_seed && s->impl == MPM_IMPL_TILED && k > 1 && nseg > 1 &&
+  const bool overlap = !mean_x0_seed && !(flags & BW_NO_OVERLAP) && s->impl == MPM_IMPL_TILED && k > 1 && nseg > 1 &&
                        (s->roll_budget == 0 ||
                         (size_t(nseg) + 2 * size_t(k - 1)) * S + store_bytes <= s->roll_budget);
   if (overlap) {
@@ -885,6 +929,268 @@ mpm_status finish_backward(mpm_scene* s, float* gx0, float* gv0, float* gC0, flo
   return read_status(s);
 }
 
+
+// Recompute of segment sg of the prepared reverse pass (keys of its checkpoint, then its L - 1
+// forward steps; with workspace 2 also the sort and controller input of its last state) on st.
+mpm_status recompute_segment(mpm_scene* s, int sg, cudaStream_t st) {
+  const int T = s->roll_T, k = s->roll_k, n0 = s->roll_start;
+  const int L = std::min(k, T - sg * k);
+  if (L <= 1 && !s->rcm_ws2) return MPM_OK;
+  CK(launch_set_int(s->d_step, n0 + sg * k, st));
+  CKS(run_phase(s, PH_PREP, 1, st));  // bin keys of the checkpoint the recompute starts from
+  if (L > 1) CKS(run_phase(s, PH_RCM, L - 1, st));
+  if (s->rcm_ws2) {
+    // the segment's last state has its keys (from the last recompute step, or the checkpoint's
+    // own for L = 1) but no scatter yet: sort it into its slot and leave the counters clear
+    BatchDev& b2 = workspace(s, PH_RCM);
+    const bool two = s->dim == 2;
+    CK(two ? launch_sort<2>(b2, st) : launch_sort<3>(b2, st));
+    uint32_t* slot = sort_slot_of(s, sg, L - 1);
+    CK(two ? launch_store_sort<2>(b2, slot, st) : launch_store_sort<3>(b2, slot, st));
+    CK(cudaMemsetAsync(b2.tile_count, 0, sizeof(uint32_t) * size_t(b2.total_tiles), st));
+    CK(cudaMemsetAsync(b2.tile_fill, 0, sizeof(uint32_t) * size_t(b2.total_tiles), st));
+    if (s->ctrl_store) {  // the last state's controller input and actuation into its slot
+      CK(launch_select(s->dsel + PH_RCM, 1, s->cur2, st));
+      CK(ctrl_step_forward(s->hp, s->cur2, s->ctrl2, st));
+    }
+  }
+  return MPM_OK;
+}
+
+// The reverse steps of the prepared rollout, segments last to first, each after its recompute.
+mpm_status reverse_segments(mpm_scene* s) {
+  const int T = s->roll_T, k = s->roll_k, nseg = s->roll_nseg;
+  mpm_ctx* c = s->ctx;
+  const bool overlap = s->rcm_ws2 && !c->prof_mask && !tune_wants(s, PH_RCM) && !tune_wants(s, PH_REV) &&
+                       !tune_wants(s, PH_PREP);
+  if (!overlap) {
+    for (int sg = nseg - 1; sg >= 0; --sg) {
+      CKS(recompute_segment(s, sg, c->stream));
+      CKS(run_phase(s, PH_REV, std::min(k, T - sg * k)));
+    }
+    return MPM_OK;
+  }
+  // Segment sg-1 is recomputed on the second stream while the reverse steps of segment sg run on
+  // the first.  Odd and even segments recompute into different buffers: a recompute waits for the
+  // reverse steps that last read its buffers, a segment's reverse steps for its recompute.
+  cudaStream_t ms = c->stream, as = c->aux;
+  CK(cudaEventRecord(s->ev_fork, ms));
+  CK(cudaStreamWaitEvent(as, s->ev_fork, 0));
+  CKS(recompute_segment(s, nseg - 1, as));
+  CK(cudaEventRecord(s->ev_rcm[(nseg - 1) & 1], as));
+  for (int sg = nseg - 1; sg >= 0; --sg) {
+    if (sg >= 1) {
+      if (sg + 1 < nseg) CK(cudaStreamWaitEvent(as, s->ev_rev[(sg + 1) & 1], 0));
+      CKS(recompute_segment(s, sg - 1, as));
+      CK(cudaEventRecord(s->ev_rcm[(sg - 1) & 1], as));
+    }
+    CK(cudaStreamWaitEvent(ms, s->ev_rcm[sg & 1], 0));
+    CKS(run_phase(s, PH_REV, std::min(k, T - sg * k), ms));
+    CK(cudaEventRecord(s->ev_rev[sg & 1], ms));
+  }
+  return MPM_OK;
+}
+
+
+// ---------------------------------------------------------------------------- multi-level store
+// A rollout whose budget cannot hold the single-level store ((ceil(T/k) + k - 1) states) keeps
+// fewer states and recomputes more.  The schedule is recursive.  A range of L steps whose start
+// state sits in a slot, with `slots` further state slots free, is either
+//   - reversed by the single-level scheme from its start (interval k: ceil(L/k) - 1 further
+//     checkpoints and k - 1 recompute buffers, the start's slot serving as checkpoint 0), or
+//   - split at step j: march j steps from the start, keep that state in a slot, reverse [j, L)
+//     with one slot fewer, release the slot, then reverse [0, j) with the slots it had.
+// The planner picks, by dynamic programming over (L, slots), the choice with the fewest forward
+// steps (marches, single-level rollouts and their recompute); every schedule runs the same T
+// reverse steps, so the results are the bits of the single-level store.  The rollout runs the
+// splits of the last range on its way (the spine) and that range's single-level rollout; the
+// reverse pass reverses it, then the earlier ranges.  The rollout's first and final states keep a
+// slot each.
+constexpr long long ML_INF = (1LL << 60);
+constexpr int ML_MAX_T = 8192;    // longest rollout the multi-level store plans for
+constexpr int ML_MAX_SLOTS = 64;  // slots it plans with (more budget than this buys nothing here)
+
+MLChoice ml_best(std::unordered_map<long long, MLChoice>& memo, int L, int slots) {
+  const long long key = (long long)L * 128 + slots;
+  auto it = memo.find(key);
+  if (it != memo.end()) return it->second;
+  MLChoice best;
+  // single-level from the range's start: the smallest k that fits keeps the most checkpoints
+  for (int k = 1; k <= L; ++k) {
+    const int nseg = (L + k - 1) / k;
+    if (nseg - 1 + k - 1 <= slots) {
+      best.cost = 2LL * L - nseg;  // the rollout, then L - nseg recomputed steps
+      best.d = -k;
+      best.peak = nseg - 1 + k - 1;
+      break;
+    }
+  }
+  if (best.cost > L && slots >= 1) {  // a split can only help where the single level recomputes
+    const int stride = L <= 1024 ? 1 : (L + 127) / 128;
+    for (int j = 1; j < L; j += stride) {
+      const MLChoice right = ml_best(memo, L - j, slots - 1);
+      if (right.cost >= ML_INF) continue;
+      const MLChoice left = ml_best(memo, j, slots);
+      if (left.cost >= ML_INF) continue;
+      const long long c = j + right.cost + left.cost;
+      if (c < best.cost) {
+        best.cost = c;
+        best.d = j;
+        best.peak = std::max(1 + right.peak, left.peak);
+      }
+    }
+  }
+  memo.emplace(key, best);
+  return best;
+}
+
+int ml_pop(mpm_scene* s) {
+  const int i = s->ml_free.back();
+  s->ml_free.pop_back();
+  return i;
+}
+
+mpm_status ml_copy(mpm_scene* s, float4* dst, const float4* src) {
+  CK(cudaMemcpyAsync(dst, src, s->state_bytes, cudaMemcpyDeviceToDevice, s->ctx->stream));
+  return MPM_OK;
+}
+
+// Makes the state in slot `start` the current state of global step ml_start + a (counter, keys).
+mpm_status ml_resume(mpm_scene* s, int a, int start) {
+  CKS(ml_copy(s, s->state, s->ml_pool[start]));
+  s->step = s->ml_start + a;
+  CKS(set_counter(s, s->d_step, s->step));
+  return restore_keys(s);
+}
+
+// Single-level rollout of [a, a + L) from the current state (= slot start) with interval k, its
+// checkpoints and recompute buffers taken from the free slots.
+mpm_status ml_base_rollout(mpm_scene* s, int L, int start, int k) {
+  const int nseg = (L + k - 1) / k;
+  s->ml_base_slots.clear();
+  s->ckpt.assign(nseg, nullptr);
+  s->ckpt[0] = s->ml_pool[start];
+  for (int i = 1; i < nseg; ++i) {
+    const int slot = ml_pop(s);
+    s->ml_base_slots.push_back(slot);
+    s->ckpt[i] = s->ml_pool[slot];
+  }
+  s->seg.assign(k - 1, nullptr);
+  for (int i = 0; i + 1 < k; ++i) {
+    const int slot = ml_pop(s);
+    s->ml_base_slots.push_back(slot);
+    s->seg[i] = s->ml_pool[slot];
+  }
+  s->pool_backed = true;
+  CKS(rollout_records(s, L, k, 0, false));
+  CKS(run_phase(s, PH_ROLL, L));
+  s->step += L;
+  s->ml_fwd_steps += L;
+  return MPM_OK;
+}
+
+// Reverse pass of the single-level range just rolled out; the first one takes the caller's seeds,
+// later ones continue from the adjoint in adj[0] and add to the parameter gradients.
+mpm_status ml_base_reverse(mpm_scene* s, bool first, const float* gxT, const float* gvT, const float* gCT,
+                           const float* gFT, int mem_space) {
+  const int flags = BW_NO_OVERLAP | (first ? 0 : BW_KEEP_SEED | BW_ACCUMULATE);
+  CKS(prepare_backward(s, gxT, gvT, gCT, gFT, mem_space, false, flags));
+  CKS(reverse_segments(s));
+  s->ml_fwd_steps += s->roll_T - s->roll_nseg;
+  if (s->roll_T & 1) CKS(ml_copy(s, s->adj[0], s->adj[1]));  // the next range starts from adj[0]
+  for (int slot : s->ml_base_slots) s->ml_free.push_back(slot);
+  s->ml_base_slots.clear();
+  return MPM_OK;
+}
+
+// Forward along the spine of [a, a + L): from the current state (= slot start), march to each
+// split the plan makes and keep it, until the last range, whose single-level rollout runs.
+mpm_status ml_forward(mpm_scene* s, int a, int L, int start, int slots) {
+  for (;;) {
+    const MLChoice c = ml_best(s->ml_memo, L, slots);
+    if (c.cost >= ML_INF) return MPM_ERR_OOM;
+    if (c.d < 0) return ml_base_rollout(s, L, start, -c.d);
+    CKS(run_phase(s, PH_STEP, c.d));
+    s->step += c.d;
+    s->ml_fwd_steps += c.d;
+    const int child = ml_pop(s);
+    CKS(ml_copy(s, s->ml_pool[child], s->state));
+    s->ml_spine.push_back({a, L, start, slots, c.d, child});
+    a += c.d;
+    L -= c.d;
+    start = child;
+    slots -= 1;
+  }
+}
+
+// Whole reverse of [a, a + L) from slot start with `slots` free slots (adjoint of state a + L in
+// adj[0]; afterwards that of state a).
+mpm_status ml_range(mpm_scene* s, int a, int L, int start, int slots) {
+  const size_t depth0 = s->ml_spine.size();  // frames below are the callers'
+  CKS(ml_resume(s, a, start));
+  CKS(ml_forward(s, a, L, start, slots));
+  CKS(ml_base_reverse(s, false, nullptr, nullptr, nullptr, nullptr, 1));
+  while (s->ml_spine.size() > depth0) {
+    const mpm_scene::MLFrame f = s->ml_spine.back();
+    s->ml_spine.pop_back();
+    s->ml_free.push_back(f.child);  // its range is reversed
+    CKS(ml_range(s, f.a, f.j, f.start, f.slots));
+  }
+  return MPM_OK;
+}
+
+mpm_status ml_rollout(mpm_scene* s, int T, size_t budget) {
+  const size_t S = s->state_bytes;
+  const long long B = std::min<long long>(S ? (long long)(budget / S) : 0, 2 + ML_MAX_SLOTS);
+  if (T > ML_MAX_T || B < 3) return MPM_ERR_OOM;
+  const int top = int(B) - 2;  // the rollout's first and final states keep a slot each
+  const MLChoice c = ml_best(s->ml_memo, T, top);
+  if (c.cost >= ML_INF) return MPM_ERR_OOM;
+  const int P = 2 + c.peak;
+  free_rollout(s);  // the single-level buffers' memory belongs to the budget
+  if (int(s->ml_pool.size()) != P) {
+    free_ml_pool(s);
+    s->ml_pool.assign(P, nullptr);
+    for (int i = 0; i < P; ++i) {
+      const mpm_status st = dalloc(&s->ml_pool[i], S / sizeof(float4), s->ml_allocs);
+      if (st != MPM_OK) {
+        free_ml_pool(s);
+        return st;
+      }
+    }
+  }
+  s->ml_free.clear();
+  for (int i = P - 1; i >= 0; --i) s->ml_free.push_back(i);
+  s->ml_base_slots.clear();
+  s->ml_spine.clear();
+  s->ml_first = ml_pop(s);
+  s->ml_final = ml_pop(s);
+  s->ml_T = T;
+  s->ml_start = s->step;
+  s->ml_top_slots = top;
+  s->ml_fwd_steps = 0;
+  s->roll_multi = true;
+  CKS(set_counter(s, s->d_step, s->step));
+  CKS(ml_copy(s, s->ml_pool[s->ml_first], s->state));
+  return ml_forward(s, 0, T, s->ml_first, top);
+}
+
+mpm_status ml_backward(mpm_scene* s, const float* gxT, const float* gvT, const float* gCT, const float* gFT,
+                       int mem_space) {
+  // the rollout's final state is current now; later ranges overwrite it, so it is kept
+  CKS(ml_copy(s, s->ml_pool[s->ml_final], s->state));
+  CKS(ml_base_reverse(s, true, gxT, gvT, gCT, gFT, mem_space));
+  while (!s->ml_spine.empty()) {
+    const mpm_scene::MLFrame f = s->ml_spine.back();
+    s->ml_spine.pop_back();
+    s->ml_free.push_back(f.child);  // the range after the split is reversed
+    CKS(ml_range(s, f.a, f.j, f.start, f.slots));
+  }
+  CKS(ml_copy(s, s->state, s->ml_pool[s->ml_final]));
+  s->step = s->ml_start + s->ml_T;
+  s->have_rollout = false;  // the spine is spent: a second reverse pass needs a new rollout
+  return MPM_OK;
+}
 }  // namespace gbmpm
 
 extern "C" {
@@ -995,6 +1301,7 @@ mpm_status mpm_scene_destroy(mpm_scene* s) {
   cudaStreamSynchronize(s->ctx->stream);
   cudaStreamSynchronize(s->ctx->aux);
   free_rollout(s);
+  free_ml_pool(s);
   free_ws2(s);
   invalidate_graphs(s);
   tune_release(s);
@@ -1314,6 +1621,17 @@ mpm_status mpm_step(mpm_scene* s, int n_steps) {
 mpm_status mpm_rollout(mpm_scene* s, int T, int k, size_t budget) {
   if (!s || T < 1 || k < 0) return MPM_ERR_ARG;
   if (s->batch_refs > 0) return MPM_ERR_STATE;
+  bool fits = false;
+  auto_interval(s, T, k, budget, &fits);
+  if (!fits && k == 0) {  // below the single-level store: the multi-level one
+    s->have_rollout = false;
+    s->have_grad = false;
+    CKS(ml_rollout(s, T, budget));
+    s->have_rollout = true;
+    CK(cudaGetLastError());
+    return MPM_OK;
+  }
+  s->roll_multi = false;
   CKS(prepare_rollout(s, T, k, budget));
   CKS(run_phase(s, PH_ROLL, T));
   s->step += T;
@@ -1322,64 +1640,44 @@ mpm_status mpm_rollout(mpm_scene* s, int T, int k, size_t budget) {
   return MPM_OK;
 }
 
+mpm_status mpm_plan_checkpoints(int T, long long budget_states, long long* forward_steps, int* states_used,
+                                int* multi_level) {
+  if (T < 1 || budget_states < 0) return MPM_ERR_ARG;
+  long long fwd = 0;
+  int used = 0, multi = 0;
+  // the single-level store, as mpm_rollout chooses its interval (state size 1 here)
+  int k = (budget_states == 0 || T <= budget_states) ? 1 : int(std::ceil(std::sqrt(double(T))));
+  k = std::min(k, T);
+  const int nseg = (T + k - 1) / k;
+  if (budget_states == 0 || nseg + k - 1 <= budget_states) {
+    fwd = 2LL * T - nseg;  // the rollout, then the recompute of every segment
+    used = nseg + k - 1;
+  } else {
+    const long long B = std::min<long long>(budget_states, 2 + ML_MAX_SLOTS);
+    if (T > ML_MAX_T || B < 3) return MPM_ERR_OOM;
+    std::unordered_map<long long, MLChoice> memo;
+    const MLChoice c = ml_best(memo, T, int(B) - 2);
+    if (c.cost >= ML_INF) return MPM_ERR_OOM;
+    fwd = c.cost;
+    used = 2 + c.peak;
+    multi = 1;
+  }
+  if (forward_steps) *forward_steps = fwd;
+  if (states_used) *states_used = used;
+  if (multi_level) *multi_level = multi;
+  return MPM_OK;
+}
+
 mpm_status mpm_backward(mpm_scene* s, const float* gxT, const float* gvT, const float* gCT, const float* gFT,
                         float* gx0, float* gv0, float* gC0, float* gF0, float* gctrl, int mem_space) {
   if (!s || (mem_space != 0 && mem_space != 1)) return MPM_ERR_ARG;
   if (s->batch_refs > 0) return MPM_ERR_STATE;
   if (!s->have_rollout) return MPM_ERR_STATE;
-  CKS(prepare_backward(s, gxT, gvT, gCT, gFT, mem_space));
-  const int T = s->roll_T, k = s->roll_k, nseg = s->roll_nseg, n0 = s->roll_start;
-  mpm_ctx* c = s->ctx;
-  // recompute of segment sg (keys of its checkpoint, then its L - 1 forward steps) on stream st
-  auto recompute = [&](int sg, cudaStream_t st) -> mpm_status {
-    const int L = std::min(k, T - sg * k);
-    if (L <= 1 && !s->rcm_ws2) return MPM_OK;
-    CK(launch_set_int(s->d_step, n0 + sg * k, st));
-    CKS(run_phase(s, PH_PREP, 1, st));  // bin keys of the checkpoint the recompute starts from
-    if (L > 1) CKS(run_phase(s, PH_RCM, L - 1, st));
-    if (s->rcm_ws2) {
-      // the segment's last state has its keys (from the last recompute step, or the checkpoint's
-      // own for L = 1) but no scatter yet: sort it into its slot and leave the counters clear
-      BatchDev& b2 = workspace(s, PH_RCM);
-      const bool two = s->dim == 2;
-      CK(two ? launch_sort<2>(b2, st) : launch_sort<3>(b2, st));
-      uint32_t* slot = sort_slot_of(s, sg, L - 1);
-      CK(two ? launch_store_sort<2>(b2, slot, st) : launch_store_sort<3>(b2, slot, st));
-      CK(cudaMemsetAsync(b2.tile_count, 0, sizeof(uint32_t) * size_t(b2.total_tiles), st));
-      CK(cudaMemsetAsync(b2.tile_fill, 0, sizeof(uint32_t) * size_t(b2.total_tiles), st));
-      if (s->ctrl_store) {  // the last state's controller input and actuation into its slot
-        CK(launch_select(s->dsel + PH_RCM, 1, s->cur2, st));
-        CK(ctrl_step_forward(s->hp, s->cur2, s->ctrl2, st));
-      }
-    }
-    return MPM_OK;
-  };
-  const bool overlap = s->rcm_ws2 && !c->prof_mask && !tune_wants(s, PH_RCM) && !tune_wants(s, PH_REV) &&
-                       !tune_wants(s, PH_PREP);
-  if (!overlap) {
-    for (int sg = nseg - 1; sg >= 0; --sg) {
-      CKS(recompute(sg, c->stream));
-      CKS(run_phase(s, PH_REV, std::min(k, T - sg * k)));
-    }
-    return finish_backward(s, gx0, gv0, gC0, gF0, gctrl, mem_space);
-  }
-  // Segment sg-1 is recomputed on the second stream while the reverse steps of segment sg run on
-  // the first.  Odd and even segments recompute into different buffers: a recompute waits for the
-  // reverse steps that last read its buffers, a segment's reverse steps for its recompute.
-  cudaStream_t ms = c->stream, as = c->aux;
-  CK(cudaEventRecord(s->ev_fork, ms));
-  CK(cudaStreamWaitEvent(as, s->ev_fork, 0));
-  CKS(recompute(nseg - 1, as));
-  CK(cudaEventRecord(s->ev_rcm[(nseg - 1) & 1], as));
-  for (int sg = nseg - 1; sg >= 0; --sg) {
-    if (sg >= 1) {
-      if (sg + 1 < nseg) CK(cudaStreamWaitEvent(as, s->ev_rev[(sg + 1) & 1], 0));
-      CKS(recompute(sg - 1, as));
-      CK(cudaEventRecord(s->ev_rcm[(sg - 1) & 1], as));
-    }
-    CK(cudaStreamWaitEvent(ms, s->ev_rcm[sg & 1], 0));
-    CKS(run_phase(s, PH_REV, std::min(k, T - sg * k), ms));
-    CK(cudaEventRecord(s->ev_rev[sg & 1], ms));
+  if (s->roll_multi) {
+    CKS(ml_backward(s, gxT, gvT, gCT, gFT, mem_space));
+  } else {
+    CKS(prepare_backward(s, gxT, gvT, gCT, gFT, mem_space));
+    CKS(reverse_segments(s));
   }
   return finish_backward(s, gx0, gv0, gC0, gF0, gctrl, mem_space);
 }
@@ -1395,7 +1693,7 @@ mpm_status mpm_get_state(mpm_scene* s, int step, float* x, float* v, float* C, f
   if (!s || (mem_space != 0 && mem_space != 1)) return MPM_ERR_ARG;
   const float4* src = s->state;
   if (step >= 0) {
-    if (!s->have_rollout) return MPM_ERR_STATE;
+    if (!s->have_rollout || s->roll_multi) return MPM_ERR_STATE;
     const int local = step - s->roll_start;
     if (local < 0 || local % s->roll_k != 0 || local / s->roll_k >= s->roll_nseg) return MPM_ERR_ARG;
     src = s->ckpt[local / s->roll_k];

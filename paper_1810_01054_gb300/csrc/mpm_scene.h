@@ -5,6 +5,7 @@
 #include <atomic>
 #include <cstring>
 #include <mutex>
+#include <unordered_map>
 #include <utility>
 #include <vector>
 
@@ -17,6 +18,12 @@ enum Phase { PH_STEP = 0, PH_ROLL = 1, PH_RCM = 2, PH_REV = 3, PH_PREP = 4, PH_C
 // Selections beyond the phases': the reverse sort loads on a graph branch, into buffer set A (the
 // scene's own) and set B (mpm_scene::bB), stepping back from the graph's first reverse step.
 enum BranchSel { SEL_LOAD_A = PH_COUNT, SEL_LOAD_B = PH_COUNT + 1, SEL_COUNT = PH_COUNT + 2 };
+// One choice of the multi-level store's planner for a range (mpm_api.cu).
+struct MLChoice {
+  long long cost = 1LL << 60;  // forward steps; 2^60 = infeasible
+  int d = 0;                   // -k: single-level with interval k; j > 0: split at j
+  int peak = 0;                // most slots beyond the range's start in use at once
+};
 }  // namespace gbmpm
 
 using gbmpm::BatchDev;
@@ -107,6 +114,22 @@ struct mpm_scene {
   std::vector<float4*> ckpt;
   std::vector<float4*> seg;  // k - 1 recompute buffers
   std::vector<void*> roll_allocs;
+  // Multi-level store (a rollout whose budget is below the single-level store): state slots, the
+  // free ones, and the spine of split ranges the forward stored on its way to the last range.
+  // ckpt/seg then point into the slots (pool_backed) instead of roll_allocs.
+  struct MLFrame {
+    int a, L, start, slots, j, child;  // range [a, a + L) from slot start, split at j into slot child
+  };
+  bool roll_multi = false;
+  bool pool_backed = false;
+  std::vector<float4*> ml_pool;
+  std::vector<void*> ml_allocs;
+  std::vector<int> ml_free;
+  std::vector<int> ml_base_slots;  // slots the running single-level range took from ml_free
+  std::vector<MLFrame> ml_spine;
+  int ml_T = 0, ml_start = 0, ml_first = -1, ml_final = -1, ml_top_slots = 0;
+  long long ml_fwd_steps = 0;  // forward steps the schedule runs (rollout and reverse pass)
+  std::unordered_map<long long, gbmpm::MLChoice> ml_memo;  // planner choices by (length, slots)
   // staging scratch
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
@@ -156,8 +179,14 @@ struct mpm_scene {
 namespace gbmpm {
 // Helpers the batch scheduler shares with the single-scene entry points (mpm_api.cu).
 mpm_status prepare_rollout(mpm_scene* s, int T, int k, size_t budget);
+// flags of prepare_backward used by the multi-level store for its later ranges
+enum BackwardFlags {
+  BW_KEEP_SEED = 1,   // the adjoint of the range's last state is already in adj[0]
+  BW_ACCUMULATE = 2,  // controller-parameter and material gradients keep what earlier ranges added
+  BW_NO_OVERLAP = 4,  // the recompute runs in line (no second workspace)
+};
 mpm_status prepare_backward(mpm_scene* s, const float* gxT, const float* gvT, const float* gCT, const float* gFT,
-                            int mem_space, bool mean_x0_seed = false);
+                            int mem_space, bool mean_x0_seed = false, int flags = 0);
 mpm_status seed_mean_x0(mpm_scene* s);
 mpm_status finish_backward(mpm_scene* s, float* gx0, float* gv0, float* gC0, float* gF0, float* gctrl,
                            int mem_space);

@@ -154,6 +154,8 @@ _SIGS = {
     "mpm_profile_start": [C.c_void_p, C.c_uint, C.c_int],
     "mpm_profile_read": [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)],
     "mpm_launch_count": [C.POINTER(C.c_longlong)],
+    "mpm_plan_checkpoints": [C.c_int, C.c_longlong, C.POINTER(C.c_longlong), C.POINTER(C.c_int),
+                             C.POINTER(C.c_int)],
     "mpm_step_noalloc": [C.POINTER(NoAllocStep), C.c_void_p],
     "mpm_scene_set_tuning": [C.c_void_p, C.c_int],
     "mpm_scene_set_material": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int],
@@ -187,6 +189,15 @@ def launch_count() -> int:
     n = C.c_longlong()
     _check(lib().mpm_launch_count(C.byref(n)), "mpm_launch_count")
     return int(n.value)
+
+
+def plan_checkpoints(n_steps: int, budget_states: int):
+    """(forward steps over the rollout and its reverse pass, states stored at most, multi-level?)
+    of the checkpoint schedule mpm_rollout takes for a budget of ``budget_states`` states."""
+    f, u, m = C.c_longlong(), C.c_int(), C.c_int()
+    _check(lib().mpm_plan_checkpoints(int(n_steps), int(budget_states), C.byref(f), C.byref(u), C.byref(m)),
+           "mpm_plan_checkpoints")
+    return f.value, u.value, bool(m.value)
 
 
 def tune_cache_lookup(dim: int, particles: int, grid_tiles: int, sm_count: int):

@@ -367,3 +367,67 @@ def test_tile_over_capacity_is_reported(M, ctx, dim):
         g.get_state()
     assert e.value.status == -8
     g.close()
+
+
+# ----------------------------------------------------------------------------- multi-level store
+def _ml_case(case):
+    if case == "2d_sin":
+        return S.walker_square_2d(0, n_steps=40), 0, 40
+    if case == "2d_plain":
+        return S.walker_square_2d(0, n_steps=30), 1, 30
+    if case == "2d_table":  # per-step actuation: every range must resume at its own global step
+        return S.blob(2, 32, 300, 7, ctrl_type=S.CTRL_TABLE, n_groups=4, hidden=40, radius_cells=4.5,
+                      v_scale=0.3, amp=3.0), 0, 33
+    if case == "3d_mlp":  # a controller that reads the state
+        return S.blob(3, 16, 400, 6, ctrl_type=S.CTRL_MLP, n_groups=4, hidden=16, scale=5.0, radius_cells=3.5,
+                      v_scale=0.3), 0, 27
+    if case == "2d_material":
+        return S.with_material(S.walker_square_2d(0, n_steps=25), 5), 0, 25
+    raise ValueError(case)
+
+
+@pytest.mark.parametrize("case", ["2d_sin", "2d_plain", "2d_table", "3d_mlp", "2d_material"])
+def test_multi_level_store_is_bitwise_the_store_all(M, ctx, case):
+    """Budgets below the single-level store ((ceil(T/k) + k - 1) states) take the multi-level
+    store; it recomputes more but runs the same reverse steps on the same states, so the final
+    state and every gradient are the bits of a rollout that keeps every state (the tiled form; the
+    plain form's atomic sums agree to rounding)."""
+    spec, impl, T = _ml_case(case)
+    sc = M.Scene(ctx, spec, impl=impl)
+    S_bytes = sc.info()["state_bytes"]
+    rng = np.random.default_rng(11)
+    wx = rng.normal(size=(spec.n_particles, spec.dim)) / spec.n_particles
+    wv = rng.normal(size=(spec.n_particles, spec.dim)) / spec.n_particles
+    material = getattr(spec, "E_arr", None) is not None
+    outs = []
+    for states in (0, 5, 3):  # every state; 5 and 3 states (the least the store accepts)
+        if states:
+            assert M.plan_checkpoints(T, states)[2]  # the multi-level store is planned
+        sc.set_state(spec.x0, spec.v0, spec.C0, spec.F0, step=0)
+        sc.rollout(T, 0, states * S_bytes)
+        res = list(sc.get_state()) + list(sc.backward(wx, wv))
+        if material:
+            res += list(sc.material_gradients())
+        if states:  # the spine is spent: one reverse pass per multi-level rollout
+            with pytest.raises(M.MPMError) as e:
+                sc.backward(wx, wv)
+            assert e.value.status == -7
+            assert sc.info()["step"] == T  # the scene is back at the rollout's final state
+        outs.append(res)
+    sc.close()
+    assert np.abs(outs[0][5]).max() > 0
+    for o in outs[1:]:
+        for a, b in zip(o, outs[0]):
+            if impl == 0:
+                assert np.array_equal(a, b)
+            else:  # the plain form adds with float atomics: the same sums in another order
+                assert rel_l2(a, b) < 1e-5
+
+
+def test_multi_level_store_below_three_states_is_refused(M, ctx):
+    spec = S.walker_square_2d(0, n_steps=20)
+    sc = M.Scene(ctx, spec)
+    with pytest.raises(M.MPMError) as e:
+        sc.rollout(20, 0, 2 * sc.info()["state_bytes"])
+    assert e.value.status == -2
+    sc.close()
