@@ -561,8 +561,11 @@ struct P2GCfg {
 
 // T threads per CTA (256; 128 in 2D, where a thread then owns up to two of the 144 work items):
 // the work items and every sum keep their order, so T changes no bit of the results.
+// Resident CTAs: the 3D forward P2G keeps 3 of 256 threads per SM (85 registers, a few spills in
+// its record phase; 4 % faster on the 1M-particle cluster than 2 at 126 registers); the adjoint
+// scatter holds 63 accumulators and keeps 2.
 template <int D, bool ADJ, int T>
-__global__ void __launch_bounds__(T, T == 256 ? 2 : 4) k_p2g(BatchDev b) {
+__global__ void __launch_bounds__(T, T == 256 ? (D == 3 && !ADJ ? 3 : 2) : 4) k_p2g(BatchDev b) {
   pdl_enter();
   using K = P2GCfg<D, ADJ, T>;
   constexpr int B = Cfg<D>::B, CELLS = Cfg<D>::CELLS, NB = Cfg<D>::BLOCK_NODES, BN = Cfg<D>::BN;
@@ -1260,10 +1263,21 @@ __global__ void __launch_bounds__(T, 768 / T) k_g2p(BatchDev b) {
 // `fetch(kx,ky,kz, v, pb)` returns (v*, m) in v and (pbar, mbar) in pb.  With MAT and per-particle
 // material (sp.gmat) this step's dL/dE_p = (F - F^{-T}):Pbar dmu/dE + ln J (F^{-T}:Pbar) dlambda/dE
 // and dL/dm_p = sum_i N (mbar_i + pbar_i . (v_p + C_p (x_i - x_p))) are added into gmat[id].
-template <int D, bool MAT, class Fetch>
-__device__ __forceinline__ float adj_core(const Part<D>& q, const Part<D>& g1, const float* f, const float (&w)[D][3],
+// A load the compiler keeps where it is written (not merged with an earlier load of the same
+// address), so that values needed only after a long loop need not stay in registers through it.
+__device__ __forceinline__ float4 ldg_fresh(const float4* p) {
+  float4 r;
+  asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+               : "l"(p)
+               : "memory");
+  return r;
+}
+
+template <int D, bool MAT, class Fetch, class Reload>
+__device__ __forceinline__ float adj_core(Part<D>& q, Part<D>& g1, const float* f, const float (&w)[D][3],
                                           const float (&dw)[D][3], const ScenePar& sp, int id, int g, Fetch fetch,
-                                          Part<D>& g0) {
+                                          Reload reload, Part<D>& g0) {
   const PMat pm = pmat_of(sp, id);
   const float dt = sp.dt, dx = sp.dx, mass = pm.mass;
   const float Dinv = 4.0f * sp.inv_dx * sp.inv_dx;
@@ -1383,6 +1397,8 @@ __device__ __forceinline__ float adj_core(const Part<D>& q, const Part<D>& g1, c
       be[a] += Bc[0][a];
     }
   }
+  // the epilogue's inputs read again (same bits): not kept in registers through the stencil loop
+  reload(q, g1);
   // Gbar = sum N pbar d^T (= dx (sum N pbar k^T - spb f^T)), Cn = sum N v* (k - f)^T
   float Gbar[D][D], Cn[D][D];
 #pragma unroll
@@ -1532,12 +1548,52 @@ __global__ void __launch_bounds__(kAdjThreads<D>, 512 / kAdjThreads<D>) k_adj_ga
           inside = inside && base[a] >= 0 && base[a] < B;
         }
         if (inside) {
-          contrib = adj_core<D, MAT>(q, g1, f, w, dw, sp, id, gq, [&](int kx, int ky, int kz, float4& v, float4& p) {
+          auto fetch = [&](int kx, int ky, int kz, float4& v, float4& p) {
             int l = (base[0] + kx) * BN + base[1] + ky;
             if constexpr (D == 3) l = l * BN + base[2] + kz;
             v = sv[l];
             p = sb[l];
-          }, g0);
+          };
+          auto reload = [&](Part<D>& qq, Part<D>& gg) {
+            float rq[Cfg<D>::S], rg[Cfg<D>::S];
+            constexpr int NP = MAT ? Cfg<D>::PLANES : Cfg<D>::XF_PLANES;
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+              const float4 a = ldg_fresh(sp.planes + size_t(j) * sp.npad + id);
+              rq[4 * j] = a.x;
+              rq[4 * j + 1] = a.y;
+              rq[4 * j + 2] = a.z;
+              rq[4 * j + 3] = a.w;
+            }
+#pragma unroll
+            for (int j = 0; j < Cfg<D>::XF_PLANES; ++j) {
+              const float4 a = ldg_fresh(sp.adj_in + size_t(j) * sp.npad + id);
+              rg[4 * j] = a.x;
+              rg[4 * j + 1] = a.y;
+              rg[4 * j + 2] = a.z;
+              rg[4 * j + 3] = a.w;
+            }
+            // planes 0..XF_PLANES-1 hold x and F; with MAT also v and C
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+              qq.x[i] = rq[i];
+              gg.x[i] = rg[i];
+#pragma unroll
+              for (int c = 0; c < D; ++c) {
+                qq.F[i][c] = rq[D + i * D + c];
+                gg.F[i][c] = rg[D + i * D + c];
+              }
+            }
+            if constexpr (MAT) {
+#pragma unroll
+              for (int i = 0; i < D; ++i) {
+                qq.v[i] = rq[D + D * D + i];
+#pragma unroll
+                for (int c = 0; c < D; ++c) qq.C[i][c] = rq[2 * D + D * D + i * D + c];
+              }
+            }
+          };
+          contrib = adj_core<D, MAT>(q, g1, f, w, dw, sp, id, gq, fetch, reload, g0);
           pack<D>(g0, r);
           store_planes<D, Cfg<D>::PLANES>(sp.adj_out, sp.npad, id, r);
           g = gq;
@@ -1858,7 +1914,7 @@ __global__ void k_plain_gather(const ScenePar* __restrict__ dsp) {
     const int nl = lin3<D>(nd, sp.n);
     v = sp.grid[nl];
     p = sp.grid_b[nl];
-  }, g0);
+  }, [](Part<D>&, Part<D>&) {}, g0);
   pack<D>(g0, r);
   store_planes<D, Cfg<D>::PLANES>(sp.adj_out, sp.npad, id, r);
   sp.sig_contrib[id] = c;
