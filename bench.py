@@ -68,6 +68,7 @@ def parse():
     ap.add_argument("--no-replicas", action="store_true")
     ap.add_argument("--no-soft", action="store_true")
     ap.add_argument("--no-walker", action="store_true")
+    ap.add_argument("--no-permuted", action="store_true")
     ap.add_argument("--no-cpu-aggregate", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--no-budget-sweep", action="store_true")
@@ -813,6 +814,17 @@ def run_ours(args, rank, world, local_rank):
         sspec = workload("soft_body_3d", rank)
         sspec = sspec.copy(ckpt_interval=int(np.ceil(np.sqrt(sspec.n_steps))))
         soft = extra(sspec, measure(args, sspec, rank, world, dev, stream, ctx, e2e=False, plain=False))
+    permuted = None
+    if not args.no_permuted:
+        # the same workload with its particles handed over in a random order: the library's
+        # storage order (by tile, cell and position) makes the kernels read neighbouring memory
+        # anyway, so time and result bits match the ordered input
+        pr = np.random.default_rng(17).permutation(spec.n_particles)
+        pspec = spec.copy(x0=spec.x0[pr], v0=spec.v0[pr], C0=spec.C0[pr], F0=spec.F0[pr], group=spec.group[pr])
+        pr_rec = measure(args, pspec, rank, world, dev, stream, ctx, e2e=False, plain=False)
+        permuted = {"workload": spec.name + " (particles in a random order)", "value": pr_rec["value"],
+                    "value_fwd": pr_rec["value_fwd"], "unit": UNIT, "ms_per_step": pr_rec["tot_ms"] / args.steps,
+                    "ratio_to_ordered": pr_rec["value"] / r["value"], "roofline": pr_rec["roofline"]}
     sweep = None
     if rank == 0 and not args.no_budget_sweep:
         sweep = measure_budget_sweep(args, dev, stream)
@@ -854,7 +866,7 @@ def run_ours(args, rank, world, local_rank):
         "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": r["gpu_launches"], "clocks": r["clocks"],
         "plain_form": r["plain"], "walker": walker, "large_scene": large, "material": material,
         "serving": serving, "fp64": fp64, "large_scene_budgets": sweep, "small_scene_replicas": replicas,
-        "soft_body": soft,
+        "soft_body": soft, "permuted_order": permuted,
     }
     print(json.dumps(line), flush=True)
 

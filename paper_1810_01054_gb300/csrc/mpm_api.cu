@@ -84,6 +84,73 @@ int ctrl_param_count(int type, int G, int dim, int H) {
 }
 
 // Device pointer of caller data: copies host data into the scene scratch (offset bytes in).
+// Storage order of a new scene's particles (s->h_order / s->d_order: storage slot p holds caller
+// particle order[p]): sorted by the tile, then the cell in the tile, of each particle's initial
+// stencil base (two stable counting passes), then within a cell by initial position
+// (lexicographic), the caller's index breaking exact ties.  The tile kernels read a tile's
+// particles in this order, so they read neighbouring memory whatever order the caller's arrays
+// have, and the same particles given in another order get the same storage order (and so the
+// same summation orders and bits).  Non-finite positions go last (the packer reports them).
+mpm_status storage_order(mpm_scene* s, const mpm_scene_desc* d, int dim) {
+  const int N = s->N;
+  s->h_order.resize(std::max(N, 1));
+  for (int i = 0; i < N; ++i) s->h_order[i] = i;
+  // the plain form (one thread per particle, float atomics) keeps the caller's order: sorted by
+  // cell, consecutive threads would add into the same nodes and serialise their atomics
+  if (N == 0 || s->impl == MPM_IMPL_PLAIN) return MPM_OK;
+  std::vector<float> hx(size_t(N) * dim);
+  CK(cudaMemcpy(hx.data(), d->x0, sizeof(float) * hx.size(),
+                d->mem_space == 1 ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+  const ScenePar& p = s->hp;
+  constexpr int B = 4;
+  const int cells = dim == 2 ? B * B : B * B * B;
+  std::vector<int> tile(N), cell(N);
+  for (int i = 0; i < N; ++i) {
+    int tl = 0, cl = 0;
+    bool ok = true;
+    for (int a = 0; a < dim; ++a) {
+      const double u = double(hx[size_t(i) * dim + a]) * double(p.inv_dx) - 0.5;
+      ok = ok && std::isfinite(u);
+      int b = ok ? int(std::floor(std::min(std::max(u, 0.0), double(p.n[a] - 1)))) : 0;
+      tl = tl * p.nt[a] + b / B;
+      cl = cl * B + b % B;
+    }
+    tile[i] = ok ? tl : p.n_tiles;  // after every tile
+    cell[i] = ok ? cl : 0;
+  }
+  std::vector<int> by_cell(N), start;
+  auto pass = [&](const std::vector<int>& key, int nkeys, const std::vector<int>& in, std::vector<int>& out) {
+    start.assign(nkeys + 1, 0);
+    for (int i : in) start[key[i] + 1]++;
+    for (int k = 0; k < nkeys; ++k) start[k + 1] += start[k];
+    for (int i : in) out[start[key[i]]++] = i;
+  };
+  pass(cell, cells, s->h_order, by_cell);        // stable by cell
+  pass(tile, p.n_tiles + 1, by_cell, s->h_order);  // then stable by tile
+  // within each (tile, cell) run: by position, then caller index
+  auto before = [&](int i, int j) {
+    for (int a = 0; a < dim; ++a) {
+      const float xi = hx[size_t(i) * dim + a], xj = hx[size_t(j) * dim + a];
+      if (xi < xj) return true;
+      if (xj < xi) return false;
+    }
+    return i < j;
+  };
+  for (int r0 = 0; r0 < N;) {
+    int r1 = r0 + 1;
+    const int t0 = tile[s->h_order[r0]], c0 = cell[s->h_order[r0]];
+    while (r1 < N && tile[s->h_order[r1]] == t0 && cell[s->h_order[r1]] == c0) ++r1;
+    if (t0 < p.n_tiles)  // finite positions only (a NaN has no order)
+      std::sort(s->h_order.begin() + r0, s->h_order.begin() + r1, before);
+    r0 = r1;
+  }
+  int* dorder = nullptr;
+  CKS(dalloc(&dorder, size_t(N), s->allocs));
+  CK(cudaMemcpy(dorder, s->h_order.data(), sizeof(int) * size_t(N), cudaMemcpyHostToDevice));
+  s->d_order = dorder;
+  return MPM_OK;
+}
+
 mpm_status stage(mpm_scene* s, const void* src, size_t bytes, int mem_space, size_t offset, const void** out) {
   if (!src) {
     *out = nullptr;
@@ -790,7 +857,7 @@ mpm_status prepare_backward(mpm_scene* s, const float* gxT, const float* gvT, co
       a = sc;
     }
     CK(launch_pack(dim, N, s->npad, (const float*)a, (const float*)bv, (const float*)c, (const float*)f, s->adj[0],
-                   s->d_status, st));
+                   s->d_status, s->d_order, st));
   }
   if (!(flags & BW_ACCUMULATE)) {
     CK(cudaMemsetAsync(s->ctrl.gparams, 0, sizeof(float) * std::max(1, s->nparams), st));
@@ -905,7 +972,7 @@ mpm_status finish_backward(mpm_scene* s, float* gx0, float* gv0, float* gC0, flo
   char* sc = reinterpret_cast<char*>(s->scratch);
   const float4* res = s->adj[s->roll_T & 1];
   if (mem_space == 1) {
-    CK(launch_unpack(dim, N, s->npad, res, gx0, gv0, gC0, gF0, st));
+    CK(launch_unpack(dim, N, s->npad, res, gx0, gv0, gC0, gF0, s->d_order, st));
     if (gctrl && s->nparams > 0)
       CK(cudaMemcpyAsync(gctrl, s->ctrl.gparams, sizeof(float) * s->nparams, cudaMemcpyDeviceToDevice, st));
   } else {
@@ -913,7 +980,7 @@ mpm_status finish_backward(mpm_scene* s, float* gx0, float* gv0, float* gC0, flo
     float* dv_ = (float*)(sc + xb);
     float* dC_ = (float*)(sc + 2 * xb);
     float* dF_ = (float*)(sc + 2 * xb + mb);
-    CK(launch_unpack(dim, N, s->npad, res, dx_, dv_, dC_, dF_, st));
+    CK(launch_unpack(dim, N, s->npad, res, dx_, dv_, dC_, dF_, s->d_order, st));
     if (gx0 && xb) CK(cudaMemcpyAsync(gx0, dx_, xb, cudaMemcpyDeviceToHost, st));
     if (gv0 && xb) CK(cudaMemcpyAsync(gv0, dv_, xb, cudaMemcpyDeviceToHost, st));
     if (gC0 && mb) CK(cudaMemcpyAsync(gC0, dC_, mb, cudaMemcpyDeviceToHost, st));
@@ -1530,11 +1597,13 @@ mpm_status mpm_scene_create(mpm_ctx* c, const mpm_scene_desc* d, mpm_scene** out
   TRY(stage(s, d->v0, xb, d->mem_space, xb, &v0));
   TRY(stage(s, d->C0, mb, d->mem_space, 2 * xb, &C0));
   TRY(stage(s, d->F0, mb, d->mem_space, 2 * xb + mb, &F0));
-  TRY(stage(s, d->group, sizeof(int32_t) * s->N, d->mem_space, 2 * xb + 2 * mb, &grp));
+  (void)grp;
+  // storage order: the particles sorted by the tile, then the cell, of their initial stencil base
+  // (caller order within a cell), fixed for the scene's lifetime, so that a tile's particles are
+  // neighbours in memory whatever order the caller keeps them in
+  TRY(storage_order(s, d, dim));
   TRY(cuda_fail(launch_pack(dim, s->N, s->npad, (const float*)x0, (const float*)v0, (const float*)C0,
-                            (const float*)F0, s->state, s->d_status, stream)));
-  if (grp && s->N > 0)
-    TRY(cuda_fail(cudaMemcpyAsync(group, grp, sizeof(int32_t) * s->N, cudaMemcpyDeviceToDevice, stream)));
+                            (const float*)F0, s->state, s->d_status, s->d_order, stream)));
   TRY(cuda_fail(cudaStreamSynchronize(stream)));
   // small per-group arrays go through the host so group sizes can be counted there
   std::vector<float> hdir(std::max(1, s->G * dim), 0.f), hparams(std::max(1, np), 0.f), hinv(std::max(1, s->G), 0.f);
@@ -1543,7 +1612,12 @@ mpm_status mpm_scene_create(mpm_ctx* c, const mpm_scene_desc* d, mpm_scene** out
     cudaMemcpyKind k = d->mem_space == 1 ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
     if (s->G > 0) TRY(cuda_fail(cudaMemcpy(hdir.data(), d->act_dir, sizeof(float) * s->G * dim, k)));
     if (np > 0) TRY(cuda_fail(cudaMemcpy(hparams.data(), d->ctrl_params, sizeof(float) * np, k)));
-    if (d->group && s->N > 0) TRY(cuda_fail(cudaMemcpy(hgroup.data(), d->group, sizeof(int32_t) * s->N, k)));
+    if (d->group && s->N > 0) {
+      std::vector<int32_t> caller(s->N);
+      TRY(cuda_fail(cudaMemcpy(caller.data(), d->group, sizeof(int32_t) * s->N, k)));
+      for (int i = 0; i < s->N; ++i) hgroup[i] = caller[s->h_order[i]];
+      TRY(cuda_fail(cudaMemcpy(group, hgroup.data(), sizeof(int32_t) * s->N, cudaMemcpyHostToDevice)));
+    }
   }
   std::vector<int> count(std::max(1, s->G), 0);
   for (int i = 0; i < s->N; ++i)
@@ -1702,12 +1776,12 @@ mpm_status mpm_get_state(mpm_scene* s, int step, float* x, float* v, float* C, f
   const int dim = s->dim, N = s->N;
   const size_t xb = sizeof(float) * size_t(N) * dim, mb = xb * dim;
   if (mem_space == 1) {
-    CK(launch_unpack(dim, N, s->npad, src, x, v, C, F, st));
+    CK(launch_unpack(dim, N, s->npad, src, x, v, C, F, s->d_order, st));
   } else {
     CKS(ensure_scratch(s, 2 * xb + 2 * mb + 256));
     char* sc = reinterpret_cast<char*>(s->scratch);
     CK(launch_unpack(dim, N, s->npad, src, (float*)sc, (float*)(sc + xb), (float*)(sc + 2 * xb),
-                     (float*)(sc + 2 * xb + mb), st));
+                     (float*)(sc + 2 * xb + mb), s->d_order, st));
     if (x && xb) CK(cudaMemcpyAsync(x, sc, xb, cudaMemcpyDeviceToHost, st));
     if (v && xb) CK(cudaMemcpyAsync(v, sc + xb, xb, cudaMemcpyDeviceToHost, st));
     if (C && mb) CK(cudaMemcpyAsync(C, sc + 2 * xb, mb, cudaMemcpyDeviceToHost, st));
@@ -1732,7 +1806,7 @@ mpm_status mpm_set_state(mpm_scene* s, const float* x, const float* v, const flo
   CKS(stage(s, F, mb, mem_space, 2 * xb + mb, &f));
   CK(cudaMemsetAsync(s->d_status, 0, sizeof(int), st));
   CK(launch_pack(dim, N, s->npad, (const float*)a, (const float*)b, (const float*)c, (const float*)f, s->state,
-                 s->d_status, st));
+                 s->d_status, s->d_order, st));
   if (step >= 0) s->step = step;
   CKS(set_counter(s, s->d_step, s->step));
   CKS(enqueue_keys(s, PH_STEP, st));
@@ -1781,8 +1855,16 @@ mpm_status mpm_scene_set_material(mpm_scene* s, const float* E, const float* mas
     CK(cudaMalloc(&s->d_pmass, fb));
     CK(cudaMalloc(&s->d_gmat, 2 * fb));
   }
-  if (E && N > 0) CK(cudaMemcpy(s->d_pE, hE.data(), fb, cudaMemcpyHostToDevice));
-  if (mass && N > 0) CK(cudaMemcpy(s->d_pmass, hm.data(), fb, cudaMemcpyHostToDevice));
+  // into storage order
+  std::vector<float> tmp(std::max(N, 1));
+  if (E && N > 0) {
+    for (int p = 0; p < N; ++p) tmp[p] = hE[s->h_order[p]];
+    CK(cudaMemcpy(s->d_pE, tmp.data(), fb, cudaMemcpyHostToDevice));
+  }
+  if (mass && N > 0) {
+    for (int p = 0; p < N; ++p) tmp[p] = hm[s->h_order[p]];
+    CK(cudaMemcpy(s->d_pmass, tmp.data(), fb, cudaMemcpyHostToDevice));
+  }
   s->hp.pE = E ? s->d_pE : nullptr;
   s->hp.pmass = mass ? s->d_pmass : nullptr;
   s->hp.gmat = (E || mass) ? reinterpret_cast<float2*>(s->d_gmat) : nullptr;
@@ -1814,9 +1896,9 @@ mpm_status mpm_get_material_gradients(mpm_scene* s, float* gE, float* gm, int me
   std::vector<float> h(2 * size_t(N));
   if (N > 0) CK(cudaMemcpy(h.data(), s->d_gmat, sizeof(float) * 2 * size_t(N), cudaMemcpyDeviceToHost));
   std::vector<float> a(N), b(N);
-  for (int p = 0; p < N; ++p) {
-    a[p] = h[2 * size_t(p)];
-    b[p] = h[2 * size_t(p) + 1];
+  for (int p = 0; p < N; ++p) {  // storage slot p is caller particle h_order[p]
+    a[s->h_order[p]] = h[2 * size_t(p)];
+    b[s->h_order[p]] = h[2 * size_t(p) + 1];
   }
   cudaMemcpyKind kk = mem_space == 1 ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
   if (gE && N > 0) CK(cudaMemcpy(gE, a.data(), sizeof(float) * N, kk));

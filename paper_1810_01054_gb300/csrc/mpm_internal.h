@@ -261,10 +261,11 @@ cudaError_t launch_gather_ints(const IntPtrList& l, int* out, cudaStream_t s);
 // *p = v on the stream (kernel argument, so no host buffer outlives the call).
 cudaError_t launch_set_int(int* p, int v, cudaStream_t s);
 
-// Layout conversions between row-major [N][d], [N][d][d] arrays and the state planes.
+// Layout conversions between row-major [N][d], [N][d][d] arrays in the caller's particle order and
+// the state planes in storage order: storage slot p holds caller particle order[p] (NULL: p).
 cudaError_t launch_pack(int dim, int N, int npad, const float* x, const float* v, const float* C, const float* F,
-                        float4* planes, int* status, cudaStream_t s);
+                        float4* planes, int* status, const int* order, cudaStream_t s);
 cudaError_t launch_unpack(int dim, int N, int npad, const float4* planes, float* x, float* v, float* C, float* F,
-                          cudaStream_t s);
+                          const int* order, cudaStream_t s);
 
 }  // namespace gbmpm

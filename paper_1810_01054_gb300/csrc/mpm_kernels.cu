@@ -1983,18 +1983,20 @@ template cudaError_t launch_plain_adjoint<2>(const ScenePar*, const ScenePar&, f
 template cudaError_t launch_plain_adjoint<3>(const ScenePar*, const ScenePar&, float*, cudaStream_t);
 
 // ============================================================================ pack / unpack
+// Storage slot p takes caller particle q = order[p] (q = p without an order).
 __global__ void k_pack(int dim, int N, int npad, const float* x, const float* v, const float* C, const float* F,
-                       float4* planes, int* status) {
+                       float4* planes, int* status, const int* __restrict__ order) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= npad) return;
   const int S = dim == 2 ? 12 : 24, d2 = dim * dim;
   float r[24];
   if (p < N) {
+    const size_t q = order ? size_t(order[p]) : size_t(p);
     int o = 0;
-    for (int a = 0; a < dim; ++a) r[o++] = x[size_t(p) * dim + a];
-    for (int a = 0; a < d2; ++a) r[o++] = F ? F[size_t(p) * d2 + a] : ((a % (dim + 1)) == 0 ? 1.0f : 0.0f);
-    for (int a = 0; a < dim; ++a) r[o++] = v ? v[size_t(p) * dim + a] : 0.0f;
-    for (int a = 0; a < d2; ++a) r[o++] = C ? C[size_t(p) * d2 + a] : 0.0f;
+    for (int a = 0; a < dim; ++a) r[o++] = x[q * dim + a];
+    for (int a = 0; a < d2; ++a) r[o++] = F ? F[q * d2 + a] : ((a % (dim + 1)) == 0 ? 1.0f : 0.0f);
+    for (int a = 0; a < dim; ++a) r[o++] = v ? v[q * dim + a] : 0.0f;
+    for (int a = 0; a < d2; ++a) r[o++] = C ? C[q * d2 + a] : 0.0f;
     for (int a = 0; a < S; ++a)
       if (!(r[a] == r[a]) || fabsf(r[a]) > 3.0e38f) set_status(status, -1);
   } else {
@@ -2003,9 +2005,12 @@ __global__ void k_pack(int dim, int N, int npad, const float* x, const float* v,
   for (int j = 0; j < S / 4; ++j) planes[size_t(j) * npad + p] = make_float4(r[4 * j], r[4 * j + 1], r[4 * j + 2], r[4 * j + 3]);
 }
 
-__global__ void k_unpack(int dim, int N, int npad, const float4* planes, float* x, float* v, float* C, float* F) {
+// Storage slot p goes to caller particle q = order[p] (q = p without an order).
+__global__ void k_unpack(int dim, int N, int npad, const float4* planes, float* x, float* v, float* C, float* F,
+                         const int* __restrict__ order) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= N) return;
+  const size_t qo = order ? size_t(order[p]) : size_t(p);
   const int S = dim == 2 ? 12 : 24, d2 = dim * dim;
   float r[24];
   for (int j = 0; j < S / 4; ++j) {
@@ -2017,13 +2022,13 @@ __global__ void k_unpack(int dim, int N, int npad, const float4* planes, float* 
   }
   int o = 0;
   for (int a = 0; a < dim; ++a, ++o)
-    if (x) x[size_t(p) * dim + a] = r[o];
+    if (x) x[qo * dim + a] = r[o];
   for (int a = 0; a < d2; ++a, ++o)
-    if (F) F[size_t(p) * d2 + a] = r[o];
+    if (F) F[qo * d2 + a] = r[o];
   for (int a = 0; a < dim; ++a, ++o)
-    if (v) v[size_t(p) * dim + a] = r[o];
+    if (v) v[qo * dim + a] = r[o];
   for (int a = 0; a < d2; ++a, ++o)
-    if (C) C[size_t(p) * d2 + a] = r[o];
+    if (C) C[qo * d2 + a] = r[o];
 }
 
 // Device-side choice of this step's scene records: scene s of the launch uses
@@ -2095,17 +2100,17 @@ cudaError_t launch_set_int(int* p, int v, cudaStream_t s) {
 }
 
 cudaError_t launch_pack(int dim, int N, int npad, const float* x, const float* v, const float* C, const float* F,
-                        float4* planes, int* status, cudaStream_t s) {
+                        float4* planes, int* status, const int* order, cudaStream_t s) {
   if (npad == 0) return cudaSuccess;
-  k_pack<<<(npad + 255) / 256, 256, 0, s>>>(dim, N, npad, x, v, C, F, planes, status);
+  k_pack<<<(npad + 255) / 256, 256, 0, s>>>(dim, N, npad, x, v, C, F, planes, status, order);
   count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_unpack(int dim, int N, int npad, const float4* planes, float* x, float* v, float* C, float* F,
-                          cudaStream_t s) {
+                          const int* order, cudaStream_t s) {
   if (N == 0) return cudaSuccess;
-  k_unpack<<<(N + 255) / 256, 256, 0, s>>>(dim, N, npad, planes, x, v, C, F);
+  k_unpack<<<(N + 255) / 256, 256, 0, s>>>(dim, N, npad, planes, x, v, C, F, order);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -82,6 +82,10 @@ struct mpm_scene {
   CtrlPar ctrl{};
   BatchDev b{};              // private batch of one scene; b.scenes = cur
   std::vector<void*> allocs; // everything allocated at creation
+  // storage order: slot p of every per-particle array holds the caller's particle order[p]
+  // (fixed at creation from the initial positions; every entry point maps through it)
+  int* d_order = nullptr;
+  std::vector<int> h_order;
   float4* state = nullptr;   // current state planes
   float4* adj[2] = {nullptr, nullptr};
   int* d_step = nullptr;     // forward step counter (controller time)
