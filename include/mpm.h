@@ -117,7 +117,11 @@ typedef struct {
 } mpm_scene_desc;
 
 /* Creates a scene (Section III state: x, v, C, F per particle; grid per desc) at step 0.  Copies
- * every input; the library owns the scene's device buffers until mpm_scene_destroy. */
+ * every input; the library owns the scene's device buffers until mpm_scene_destroy.
+ * The tiled form stores the particles in an order of its own (by tile, cell and position of the
+ * initial state), so its kernels read neighbouring memory whatever order the caller's arrays
+ * have, and the same particles given in another order give the same result bits.  Every
+ * per-particle array passed to or returned by any entry point is in the caller's order. */
 mpm_status mpm_scene_create(mpm_ctx* ctx, const mpm_scene_desc* desc, mpm_scene** out);
 mpm_status mpm_scene_destroy(mpm_scene* scene);
 
