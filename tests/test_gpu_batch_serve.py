@@ -112,6 +112,33 @@ def test_serving_mix_equals_alone_and_reports_latency(M, ctx):
     srv.close()
 
 
+def test_serving_mix_sampled_requests_equal_alone(M, ctx):
+    """60 requests of the seeded serving mix (2D and 3D box clusters, 1e3-2e5 particles, 50-500
+    steps, 60 % with gradients) arrive as a Poisson stream and are served with continuous
+    batching; 20 of them, sampled, run again alone and return the same bits."""
+    from paper_1810_01054_gb300.serve import Server
+    n = 60
+    reqs = [S.serving_request(i, 4) for i in range(n)]
+    rng = np.random.default_rng(0)
+    arrivals = np.cumsum(rng.exponential(0.004, size=n))
+    srv = Server(device=0, mem_fraction=0.3, tick_steps=8)
+    ids = [srv.submit(sp, g, arrival=float(t)) for (sp, g), t in zip(reqs, arrivals)]
+    srv.run()
+    assert all(srv.results[i]["status"] == 0 for i in ids)
+    for i in rng.choice(n, size=20, replace=False):
+        sp, g = reqs[i]
+        r = srv.results[ids[i]]
+        st, grads = _alone(M, ctx, sp, sp.n_steps, g)
+        for a, b in zip((r["x"], r["v"], r["C"], r["F"]), st):
+            assert np.array_equal(a, b), i
+        if g:
+            for a, b in zip(r["grads"], grads):
+                assert np.array_equal(a, b), i
+    p50, p99 = srv.latency_percentiles()
+    assert 0 < p50 <= p99
+    srv.close()
+
+
 def test_admission_waits_for_memory(M, ctx):
     """A batch whose budget holds one request admits the second only after the first leaves."""
     spec = S.blob(2, 32, 200, 9, radius_cells=4.0)
