@@ -474,60 +474,67 @@ def measure(args, spec, rank, world, dev, stream, ctx, *, e2e=True, plain=True):
             "N": N, "T": T, "k": k_eff, "budget": budget, "launch": launch}
 
 
-def measure_replicas(args, dev, stream, sizes=(1, 64, 1024, 4096)):
+def measure_replicas(args, dev, stream, sizes=(1, 64, 1024, 4096), edges=(8, 4)):
     """The smallest workload (walker_square_2d: 1,024 particles, 100 steps, forward + reverse) as B
-    independent replicas advanced together by one batch, B in `sizes`: one such scene leaves the
-    GPU idle (launch and latency bound); a batch fills it.  Each request is a rollout with its
-    reverse pass (loss = mean final x_0); the timed span is admission to the last result (the
-    replicas' states are reset before it, untimed), L2 flushed before it."""
+    independent replicas advanced together by one batch, B in `sizes`, for each tile edge in
+    `edges` (8 x 8-cell tiles are what the library chooses for this sparse scene; 4 x 4 beside
+    it): one such scene leaves the GPU idle (launch and latency bound); a batch fills it.  Each
+    request is a rollout with its reverse pass (loss = mean final x_0); the timed span is
+    admission to the last result (the replicas' states are reset before it, untimed), L2 flushed
+    before it."""
     import torch
     from paper_1810_01054_gb300 import mpm
     from paper_1810_01054_gb300 import scenes as S
-    spec = S.walker_square_2d(0)
-    T, N = spec.n_steps, spec.n_particles
+    base = S.walker_square_2d(0)
+    T, N = base.n_steps, base.n_particles
     ctx = mpm.Context(dev.index, stream=stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    out = {}
-    for B in sizes:
-        scenes = [mpm.Scene(ctx, spec) for _ in range(B)]
-        batch = mpm.Batch(ctx, 2)
+    by_edge = {}
+    for edge in edges:
+        spec = base.copy(tile_edge=edge)
+        out = {}
+        for B in sizes:
+            scenes = [mpm.Scene(ctx, spec) for _ in range(B)]
+            batch = mpm.Batch(ctx, 2)
 
-        def reset():
+            def reset():
+                for sc in scenes:
+                    sc.set_state(spec.x0, spec.v0, spec.C0, spec.F0, step=0)
+
+            def run():
+                slots = [batch.admit(sc, T, True) for sc in scenes]
+                while not all(batch.poll(sl) for sl in slots):
+                    batch.tick(16)
+                bad = [batch.status(sl) for sl in slots if batch.status(sl) != mpm.MPM_OK]
+                for sl in slots:
+                    batch.release(sl)
+                if bad:
+                    raise RuntimeError(f"replica requests failed: {bad[:4]}")
+
+            for _ in range(max(1, args.warmup)):
+                reset()
+                run()
+            ms = []
+            for _ in range(max(1, min(args.steps, 3))):
+                reset()
+                flush.zero_()
+                torch.cuda.synchronize(dev)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                run()
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                ms.append(e0.elapsed_time(e1))
+            batch.close()
             for sc in scenes:
-                sc.set_state(spec.x0, spec.v0, spec.C0, spec.F0, step=0)
-
-        def run():
-            slots = [batch.admit(sc, T, True) for sc in scenes]
-            while not all(batch.poll(sl) for sl in slots):
-                batch.tick(16)
-            bad = [batch.status(sl) for sl in slots if batch.status(sl) != mpm.MPM_OK]
-            for sl in slots:
-                batch.release(sl)
-            if bad:
-                raise RuntimeError(f"replica requests failed: {bad[:4]}")
-
-        for _ in range(max(1, args.warmup)):
-            reset()
-            run()
-        ms = []
-        for _ in range(max(1, min(args.steps, 3))):
-            reset()
-            flush.zero_()
-            torch.cuda.synchronize(dev)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            run()
-            e1.record(stream)
-            torch.cuda.synchronize(dev)
-            ms.append(e0.elapsed_time(e1))
-        batch.close()
-        for sc in scenes:
-            sc.close()
-        best = float(np.median(ms))
-        out[str(B)] = {"value": B * N * T / (best / 1e3), "ms": best}
+                sc.close()
+            best = float(np.median(ms))
+            out[str(B)] = {"value": B * N * T / (best / 1e3), "ms": best}
+        by_edge[str(edge)] = out
     ctx.close()
     return {"workload": spec.name, "particles_per_replica": N, "sim_steps": T, "unit": UNIT,
-            "pass": "forward+reverse per replica, one batch", "by_replicas": out}
+            "pass": "forward+reverse per replica, one batch", "tile_edge_chosen": edges[0],
+            "by_replicas": by_edge[str(edges[0])], "by_tile_edge": by_edge}
 
 
 def measure_budget_sweep(args, dev, stream, budgets_gib=(32, 4, 1)):

@@ -114,6 +114,10 @@ typedef struct {
   const float* ctrl_params;
   int impl;            /* MPM_IMPL_TILED (sorted, deterministic) or MPM_IMPL_PLAIN (atomics baseline) */
   int mem_space;       /* where every pointer of this descriptor lives */
+  int tile_edge;       /* cells per tile edge of the tiled form: 4; 8 (2D only: sparse scenes, a tile
+                          then holds the particles of four 4 x 4 tiles); 0 = chosen at creation
+                          (8 x 8 for a 2D scene averaging under 96 particles per occupied 4 x 4
+                          tile, else 4 x 4) */
 } mpm_scene_desc;
 
 /* Creates a scene (Section III state: x, v, C, F per particle; grid per desc) at step 0.  Copies
@@ -124,6 +128,8 @@ typedef struct {
  * per-particle array passed to or returned by any entry point is in the caller's order. */
 mpm_status mpm_scene_create(mpm_ctx* ctx, const mpm_scene_desc* desc, mpm_scene** out);
 mpm_status mpm_scene_destroy(mpm_scene* scene);
+/* Cells per tile edge the scene was created with (4 or 8). */
+mpm_status mpm_scene_tile_edge(const mpm_scene* scene, int* edge);
 
 /* Advances the current state by n_steps steps (Eqs. 3-10 with the controller's actuation),
  * asynchronously on the context stream.  Keeps no history. */
@@ -209,7 +215,10 @@ mpm_status mpm_scene_info(const mpm_scene* scene, int* n_particles, int* n_group
  *  mpm_batch_create   empty batch of dimension dim on ctx, admitting scenes while their device
  *                     memory fits mem_budget (0 = no limit)
  *  mpm_batch_admit    adds a scene that will run n_steps more steps (and, with want_grad, its
- *                     reverse pass, seeded by loss = mean of final x_0); *slot = -1 if full
+ *                     reverse pass, seeded by loss = mean of final x_0); *slot = -1 if full.
+ *                     The scenes of a batch share one tile edge: the first admitted scene sets
+ *                     it until the batch is empty again; a scene of another edge is refused
+ *                     with MPM_ERR_ARG (keep a batch per dimension and tile edge)
  *  mpm_batch_tick     advances every admitted scene by up to max_steps steps
  *  mpm_batch_poll     *done = 1 when the slot's work is finished (results stay in the scene);
  *                     a request that stopped on a device error (a particle left the grid, a

@@ -68,8 +68,49 @@ mpm_status dalloc(T** p, size_t count, std::vector<void*>& list) {
 }
 
 int planes_of(int dim) { return dim == 2 ? Cfg<2>::PLANES : Cfg<3>::PLANES; }
-int tile_edge(int dim) { return dim == 2 ? Cfg<2>::B : Cfg<3>::B; }
-int block_nodes(int dim) { return dim == 2 ? Cfg<2>::BLOCK_NODES : Cfg<3>::BLOCK_NODES; }
+// Nodes of a tile's node block ((edge + 2)^dim).
+int block_nodes(int dim, int edge) {
+  const int bn = edge + 2;
+  return dim == 2 ? bn * bn : bn * bn * bn;
+}
+
+// Tile edge of a new scene: the descriptor's, or (0) 8 for a 2D tiled scene whose particles
+// average under 96 per occupied 4 x 4 tile (sparse scenes: fewer, fuller tiles), else 4.
+constexpr int kWideTileMean = 96;
+mpm_status choose_tile_edge(const mpm_scene_desc* d, int dim, int* edge) {
+  if (d->tile_edge != 0) {
+    if (d->tile_edge != 4 && !(d->tile_edge == 8 && dim == 2)) return MPM_ERR_ARG;
+    *edge = d->tile_edge;
+    return MPM_OK;
+  }
+  *edge = 4;
+  const int N = d->n_particles;
+  if (dim != 2 || d->impl != MPM_IMPL_TILED || N == 0) return MPM_OK;
+  std::vector<float> hx(size_t(N) * 2);
+  CK(cudaMemcpy(hx.data(), d->x0, sizeof(float) * hx.size(),
+                d->mem_space == 1 ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+  const int nt0 = (d->n_grid[0] + 3) / 4, nt1 = (d->n_grid[1] + 3) / 4;
+  std::vector<char> seen(size_t(nt0) * nt1, 0);
+  long long occupied = 0;
+  for (int i = 0; i < N; ++i) {
+    int t[2];
+    bool ok = true;
+    for (int a = 0; a < 2; ++a) {
+      const double u = double(hx[size_t(i) * 2 + a]) / double(d->dx) - 0.5;
+      ok = ok && std::isfinite(u);
+      const int b = ok ? int(std::floor(std::min(std::max(u, 0.0), double(d->n_grid[a] - 1)))) : 0;
+      t[a] = b / 4;
+    }
+    if (!ok) continue;
+    char& f = seen[size_t(t[0]) * nt1 + t[1]];
+    if (!f) {
+      f = 1;
+      ++occupied;
+    }
+  }
+  if (occupied > 0 && double(N) / double(occupied) < kWideTileMean) *edge = 8;
+  return MPM_OK;
+}
 
 int ctrl_param_count(int type, int G, int dim, int H) {
   if (type == MPM_CTRL_SIN) return G;
@@ -102,7 +143,7 @@ mpm_status storage_order(mpm_scene* s, const mpm_scene_desc* d, int dim) {
   CK(cudaMemcpy(hx.data(), d->x0, sizeof(float) * hx.size(),
                 d->mem_space == 1 ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
   const ScenePar& p = s->hp;
-  constexpr int B = 4;
+  const int B = s->b.tile_edge;
   const int cells = dim == 2 ? B * B : B * B * B;
   std::vector<int> tile(N), cell(N);
   for (int i = 0; i < N; ++i) {
@@ -616,7 +657,7 @@ mpm_status ensure_ws2(mpm_scene* s) {
 mpm_status ensure_ws2_parts(mpm_scene* s) {
   BatchDev& b = s->b2;
   b = s->b;  // scene tables, offsets and launch shapes; the tile arrays below are its own
-  const int nt = s->hp.n_tiles, NB = block_nodes(s->dim);
+  const int nt = s->hp.n_tiles, NB = block_nodes(s->dim, s->b.tile_edge);
   std::vector<void*>& L = s->ws2_allocs;
   CKS(dalloc(&s->cur2, 1, L));
   CKS(dalloc(&s->key2, s->npad, L));
@@ -1413,7 +1454,14 @@ mpm_status mpm_scene_create(mpm_ctx* c, const mpm_scene_desc* d, mpm_scene** out
   const double rho = double(d->p_mass) / double(d->p_vol);
   if (double(d->dt) > double(d->dx) * std::sqrt(rho / double(d->E)) * (1.0 + 1e-6)) return MPM_ERR_ARG;
 
+  if (d->tile_edge != 0 && d->tile_edge != 4 && !(d->tile_edge == 8 && dim == 2)) return MPM_ERR_ARG;
+
   CK(cudaSetDevice(c->device));
+  int edge = 4;
+  {
+    const mpm_status est = choose_tile_edge(d, dim, &edge);
+    if (est != MPM_OK) return est;
+  }
   mpm_scene* s = new (std::nothrow) mpm_scene();
   if (!s) return MPM_ERR_OOM;
   s->ctx = c;
@@ -1432,7 +1480,8 @@ mpm_status mpm_scene_create(mpm_ctx* c, const mpm_scene_desc* d, mpm_scene** out
   ScenePar& p = s->hp;
   std::memset(&p, 0, sizeof(p));
   p.dim = dim;
-  const int B = tile_edge(dim);
+  const int B = edge;
+  s->b.tile_edge = edge;
   p.n_tiles = 1;
   for (int a = 0; a < 3; ++a) {
     p.n[a] = a < dim ? d->n_grid[a] : 1;
@@ -1540,7 +1589,7 @@ mpm_status mpm_scene_create(mpm_ctx* c, const mpm_scene_desc* d, mpm_scene** out
   b.n_scenes = 1;
   b.total_particles = s->N;
   b.total_tiles = p.n_tiles;
-  const int NB = block_nodes(dim);
+  const int NB = block_nodes(dim, edge);
   int* pbase;
   ALLOC(pbase, 2);
   int* tile_scene;
@@ -1679,6 +1728,12 @@ mpm_status mpm_scene_info(const mpm_scene* s, int* n_particles, int* n_groups, i
   if (n_ctrl_params) *n_ctrl_params = s->nparams;
   if (step) *step = s->step;
   if (state_bytes) *state_bytes = s->state_bytes;
+  return MPM_OK;
+}
+
+mpm_status mpm_scene_tile_edge(const mpm_scene* s, int* edge) {
+  if (!s || !edge) return MPM_ERR_ARG;
+  *edge = s->b.tile_edge;
   return MPM_OK;
 }
 

@@ -49,6 +49,7 @@ struct SubBatch {
   long long key_particles = -1, key_tiles = -1;
   int trial_wait = 0;  // steps of this key left before its trials start (0: none pending)
   float4 *partial = nullptr, *partial_b = nullptr;  // node blocks (each half its own: they run at once)
+  int cap_edge = 0;  // tile edge the node-block arrays are sized for
 };
 
 // Steps a composition key must run before its launch-shape trials start: a serving mix changes
@@ -94,13 +95,18 @@ void free_sub(SubBatch& sb) {
   sb.cap_scenes = sb.cap_tiles = sb.cap_particles = 0;
 }
 
-int block_nodes(int dim) { return dim == 2 ? Cfg<2>::BLOCK_NODES : Cfg<3>::BLOCK_NODES; }
+// Nodes of a tile's node block ((edge + 2)^dim).
+int block_nodes(int dim, int edge) {
+  const int bn = edge + 2;
+  return dim == 2 ? bn * bn : bn * bn * bn;
+}
 
 }  // namespace
 
 struct mpm_batch {
   mpm_ctx* ctx = nullptr;
   int dim = 0;
+  int edge = 0;  // tile edge of the admitted scenes (set by the first admission into an empty batch)
   size_t budget = 0, used = 0;
   std::vector<Slot> slots;
   SubBatch fwd, rev;
@@ -118,7 +124,8 @@ namespace {
 
 mpm_status grow(mpm_batch* B, SubBatch& sb, int n_scenes, int tiles, int particles) {
   const int sc = std::max(1, n_scenes), tl = std::max(1, tiles), pc = std::max(64, particles);
-  if (sc <= sb.cap_scenes && tl <= sb.cap_tiles && pc <= sb.cap_particles) return MPM_OK;
+  if (sc <= sb.cap_scenes && tl <= sb.cap_tiles && pc <= sb.cap_particles && sb.cap_edge == B->edge)
+    return MPM_OK;
   CK(cudaStreamSynchronize(B->ctx->stream));
   free_sub(sb);
   CK(cudaMalloc(&sb.dsel, sizeof(SelectPar) * sc));
@@ -140,8 +147,9 @@ mpm_status grow(mpm_batch* B, SubBatch& sb, int n_scenes, int tiles, int particl
   sb.cap_scenes = sc;
   sb.cap_tiles = tl;
   sb.cap_particles = pc;
-  CK(cudaMalloc(&sb.partial, sizeof(float4) * size_t(tl) * block_nodes(B->dim)));
-  CK(cudaMalloc(&sb.partial_b, sizeof(float4) * size_t(tl) * block_nodes(B->dim)));
+  CK(cudaMalloc(&sb.partial, sizeof(float4) * size_t(tl) * block_nodes(B->dim, B->edge)));
+  CK(cudaMalloc(&sb.partial_b, sizeof(float4) * size_t(tl) * block_nodes(B->dim, B->edge)));
+  sb.cap_edge = B->edge;
   return MPM_OK;
 }
 
@@ -194,6 +202,7 @@ mpm_status compose(mpm_batch* B, SubBatch& sb) {
   CK(cudaMemcpy(sb.pbase, pb.data(), sizeof(int) * pb.size(), cudaMemcpyHostToDevice));
   if (tiles > 0) CK(cudaMemcpy(sb.b.tile_scene, tscene.data(), sizeof(int) * tiles, cudaMemcpyHostToDevice));
   sb.b.scenes = sb.cur;
+  sb.b.tile_edge = B->edge;
   sb.b.n_scenes = int(sb.members.size());
   sb.b.scene_pbase = sb.pbase;
   sb.b.total_particles = particles;
@@ -452,8 +461,13 @@ mpm_status mpm_batch_admit(mpm_batch* B, mpm_scene* s, int n_steps, int want_gra
   if (!B || !s || !slot || n_steps < 1) return MPM_ERR_ARG;
   *slot = -1;
   if (s->dim != B->dim || s->impl != MPM_IMPL_TILED || s->ctx != B->ctx) return MPM_ERR_ARG;
-  for (const Slot& sl : B->slots)
+  bool empty = true;
+  for (const Slot& sl : B->slots) {
     if (sl.s == s && sl.state != S_FREE) return MPM_ERR_STATE;  // a scene runs in one slot at a time
+    empty = empty && sl.state == S_FREE;
+  }
+  // one tile edge per batch: the tile kernels of a launch are instantiated for one edge
+  if (!empty && s->b.tile_edge != B->edge) return MPM_ERR_ARG;
   const size_t need = request_bytes(s, n_steps);
   if (B->budget != 0 && B->used + need > B->budget) return MPM_OK;  // no room now: *slot stays -1
   int idx = -1;
@@ -471,6 +485,7 @@ mpm_status mpm_batch_admit(mpm_batch* B, mpm_scene* s, int n_steps, int want_gra
   if (st != MPM_OK) return st;
   Slot& sl = B->slots[idx];
   sl = Slot();
+  if (empty) B->edge = s->b.tile_edge;
   sl.s = s;
   sl.state = S_FWD;
   sl.T = n_steps;

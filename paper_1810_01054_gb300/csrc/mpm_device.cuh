@@ -43,6 +43,20 @@ struct Cfg<3> {
   static constexpr int STENCIL = 27;
 };
 
+// Tile shape of the tiled form: TB^D cells per tile (TB = 4; 2D also 8 for sparse scenes, where a
+// tile then holds four times the particles of a 4 x 4 tile), its node block (TB + 2)^D, and the
+// most particles a tile's kernels stage.  The bin key holds the cell within the tile in 6 bits.
+template <int D, int TB>
+struct Tile {
+  static constexpr int B = TB;
+  static constexpr int CELLS = D == 2 ? TB * TB : TB * TB * TB;
+  static constexpr int BN = TB + 2;
+  static constexpr int BLOCK_NODES = D == 2 ? BN * BN : BN * BN * BN;
+  static constexpr int SORT_CAP = D == 2 && TB == 4 ? 2048 : 4096;
+  static_assert(CELLS <= 64, "the bin key holds the cell in 6 bits");
+  static_assert(TB == 4 || (D == 2 && TB == 8), "tile edges: 4, and 8 in 2D");
+};
+
 // Status codes written to the per-scene device status word (first error wins).
 enum : int {
   ST_OK = 0,

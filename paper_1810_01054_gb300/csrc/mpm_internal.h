@@ -148,6 +148,7 @@ struct BatchDev {
   float4* partial;      // [total_tiles * BLOCK_NODES] node blocks of P2G
   float4* partial_b;    // [total_tiles * BLOCK_NODES] node blocks of the adjoint scatter
   float* gpartial;      // [total_tiles * MAX_GROUPS] per active tile group sums of dL/da
+  int tile_edge;                // cells per tile edge of every scene in the batch (0 or 4; 8: 2D)
   int has_material;             // some scene has per-particle material (gmat): material gradients
   int sm_count;                 // SMs of the device
   TileLaunch launch[TK_COUNT];  // launch shape of each tile kernel

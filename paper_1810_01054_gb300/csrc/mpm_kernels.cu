@@ -77,19 +77,19 @@ __device__ __forceinline__ void unlin(int l, const int* n, int* c) {
   }
 }
 
-template <int D>
+template <int D, int TB>
 __device__ __forceinline__ int cell_lin(const int* c) {
-  constexpr int B = Cfg<D>::B;
+  constexpr int B = Tile<D, TB>::B;
   int l = 0;
 #pragma unroll
   for (int a = 0; a < D; ++a) l = l * B + c[a];
   return l;
 }
 
-// Bin key of a particle at x: (scene-local tile << 6) | cell within the tile.
-template <int D>
+// Bin key of a particle at x: (scene-local tile << 6) | cell within the tile (TB^D-cell tiles).
+template <int D, int TB>
 __device__ __forceinline__ uint32_t bin_key(const float* x, const ScenePar& sp) {
-  constexpr int B = Cfg<D>::B;
+  constexpr int B = Tile<D, TB>::B;
   int base[D];
   float f[D];
   if (!stencil_base<D>(x, sp.inv_dx, sp.n, base, f)) {
@@ -102,7 +102,7 @@ __device__ __forceinline__ uint32_t bin_key(const float* x, const ScenePar& sp) 
     t[a] = base[a] / B;
     c[a] = base[a] - t[a] * B;
   }
-  return (uint32_t(lin3<D>(t, sp.nt)) << 6) | uint32_t(cell_lin<D>(c));
+  return (uint32_t(lin3<D>(t, sp.nt)) << 6) | uint32_t(cell_lin<D, TB>(c));
 }
 
 // Actuation group of particle id (-1: none).
@@ -202,7 +202,7 @@ __device__ __forceinline__ void select_publish(const SelectPar& q, ScenePar* cur
 // With SEL (a single scene) the kernel also makes the step's selection: every CTA copies the
 // selected record to shared memory for its own use and CTA 0 publishes it (and the actuation) for
 // the kernels that follow, which replaces the selection launch.
-template <int D, bool SEL>
+template <int D, int TB, bool SEL>
 __global__ void k_keys(BatchDev b, const SelectPar* __restrict__ sel) {
   pdl_enter();
   __shared__ __align__(16) ScenePar srec[1];
@@ -218,7 +218,7 @@ __global__ void k_keys(BatchDev b, const SelectPar* __restrict__ sel) {
   int p = gp - sp.pbase;
   float4 q = sp.planes[p];
   float x[3] = {q.x, q.y, q.z};
-  const uint32_t k = bin_key<D>(x, sp);
+  const uint32_t k = bin_key<D, TB>(x, sp);
   sp.key[p] = k;
   warp_aggregated_inc(b.tile_count, k != KEY_INVALID ? int(sp.tile_base + (k >> 6)) : -1);
 }
@@ -534,7 +534,7 @@ template cudaError_t launch_load_sort<3>(const BatchDev&, const SelectPar*, cuda
 // Phase C  work item = (cell, part): 2D one stencil node, 3D one x-slab of 9 nodes; a thread
 //          accumulates its item over the cell's particles in registers (fixed particle order).
 // Phase D  node block = fixed-order sum of the cell stencils covering each node -> global.
-template <int D, bool ADJ, int T = 256>
+template <int D, int TB, bool ADJ, int T = 256>
 struct P2GCfg {
   static constexpr int RF = 2 * D + D * D + 1;             // f, a, M, mass
   static constexpr int RA = ADJ ? D + D * D : 0;           // a', M'
@@ -545,18 +545,18 @@ struct P2GCfg {
   static constexpr int PARTS = D == 2 ? 9 : 3;             // work items per cell
   static constexpr int NK = D == 2 ? 1 : 9;                // stencil nodes per work item
   static constexpr int THREADS = T;
-  static constexpr int ITEMS = Cfg<D>::CELLS * PARTS;      // 2D 144, 3D 192
+  static constexpr int ITEMS = Tile<D, TB>::CELLS * PARTS;  // 2D 144 (576 with 8 x 8 tiles), 3D 192
   static constexpr int IPT = (ITEMS + T - 1) / T;          // work items per thread
   static constexpr int REC_CAP = D == 2 ? 1024 : 512;      // records staged at once
-  static constexpr int CAP = Cfg<D>::SORT_CAP;
+  static constexpr int CAP = Tile<D, TB>::SORT_CAP;
   static constexpr size_t REC_BYTES = size_t(REC_CAP) * RW * 4;
-  static constexpr size_t ACC_BYTES = size_t(Cfg<D>::CELLS) * Cfg<D>::STENCIL * CH * 4;
+  static constexpr size_t ACC_BYTES = size_t(Tile<D, TB>::CELLS) * Cfg<D>::STENCIL * CH * 4;
   static constexpr size_t IDS_BYTES = size_t(CAP) * 4;
   static constexpr size_t U1 = REC_BYTES > ACC_BYTES ? REC_BYTES : ACC_BYTES;
   static constexpr size_t U_BYTES = U1 > IDS_BYTES ? U1 : IDS_BYTES;
   static constexpr size_t SMEM = IDS_BYTES + U_BYTES;
   static_assert(D == 2 || IPT == 1, "a 3D work item holds 9 nodes: one item per thread");
-  static_assert(Cfg<D>::BLOCK_NODES <= THREADS, "one node per thread in phase D");
+  static_assert(Tile<D, TB>::BLOCK_NODES <= THREADS, "one node per thread in phase D");
 };
 
 // T threads per CTA (256; 128 in 2D, where a thread then owns up to two of the 144 work items):
@@ -564,11 +564,12 @@ struct P2GCfg {
 // Resident CTAs: the 3D forward P2G keeps 3 of 256 threads per SM (85 registers, a few spills in
 // its record phase; 4 % faster on the 1M-particle cluster than 2 at 126 registers); the adjoint
 // scatter holds 63 accumulators and keeps 2.
-template <int D, bool ADJ, int T>
+template <int D, int TB, bool ADJ, int T>
 __global__ void __launch_bounds__(T, T == 256 ? (D == 3 && !ADJ ? 3 : 2) : 4) k_p2g(BatchDev b) {
   pdl_enter();
-  using K = P2GCfg<D, ADJ, T>;
-  constexpr int B = Cfg<D>::B, CELLS = Cfg<D>::CELLS, NB = Cfg<D>::BLOCK_NODES, BN = Cfg<D>::BN;
+  using K = P2GCfg<D, TB, ADJ, T>;
+  constexpr int B = Tile<D, TB>::B, CELLS = Tile<D, TB>::CELLS, NB = Tile<D, TB>::BLOCK_NODES,
+                BN = Tile<D, TB>::BN;
   constexpr int ST = Cfg<D>::STENCIL;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   uint32_t* ids = reinterpret_cast<uint32_t*>(smem_raw);
@@ -956,10 +957,10 @@ __global__ void __launch_bounds__(T, T == 256 ? (D == 3 && !ADJ ? 3 : 2) : 4) k_
 // blocks of the <= 2^D tiles whose blocks contain it.  With ADJ the adjoint-scatter blocks give
 // vbar*, and (L), (D), (E) give pbar and mbar.  Nodes a tile owns (its B^D corner) are also
 // written to the dense grid for inspection.
-template <int D, bool ADJ>
+template <int D, int TB, bool ADJ>
 __device__ __forceinline__ void build_node_block(const BatchDev& b, const ScenePar& sp, const int* t, float4* sv,
                                                  float4* sb) {
-  constexpr int B = Cfg<D>::B, NB = Cfg<D>::BLOCK_NODES, BN = Cfg<D>::BN;
+  constexpr int B = Tile<D, TB>::B, NB = Tile<D, TB>::BLOCK_NODES, BN = Tile<D, TB>::BN;
   constexpr int NN = D == 2 ? 9 : 27;  // tiles t + o, o in {-1, 0, 1}^D
   __shared__ int nslot[NN];
   if (threadIdx.x < NN) {
@@ -1172,11 +1173,11 @@ struct G2PCfg {
   static constexpr int NP = Cfg<D>::XF_PLANES;
 };
 
-template <int D, int T>
+template <int D, int TB, int T>
 __global__ void __launch_bounds__(T, 768 / T) k_g2p(BatchDev b) {
   pdl_enter();
   using K = G2PCfg<D>;
-  constexpr int B = Cfg<D>::B, NB = Cfg<D>::BLOCK_NODES, BN = Cfg<D>::BN;
+  constexpr int B = Tile<D, TB>::B, NB = Tile<D, TB>::BLOCK_NODES, BN = Tile<D, TB>::BN;
   __shared__ float4 sv[NB];
   __shared__ float4 stage[K::NP][K::STAGE];
   const int tid = threadIdx.x;
@@ -1193,7 +1194,7 @@ __global__ void __launch_bounds__(T, 768 / T) k_g2p(BatchDev b) {
     const int cnt = int(b.tile_start[gt + 1] - st);
     // a tile over P2G's capacity was skipped there (the step reports it): its list still holds
     // the scatter's cell-tagged entries, so it is skipped here too
-    if (cnt > Cfg<D>::SORT_CAP) {  // uniform across the CTA
+    if (cnt > Tile<D, TB>::SORT_CAP) {  // uniform across the CTA
       // its particles are not advanced: their keys go invalid so the next step's histogram and
       // scatter (which count keys) stay consistent; the step has already reported the error
       for (int e = tid; e < cnt; e += blockDim.x) sp.key[b.sorted[st + e] & 0x3ffffffu] = KEY_INVALID;
@@ -1207,7 +1208,7 @@ __global__ void __launch_bounds__(T, 768 / T) k_g2p(BatchDev b) {
       for (int j = 0; j < K::NP; ++j) cp_async16(&stage[j][e], sp.planes + size_t(j) * sp.npad + id);
     }
     cp_async_commit();
-    build_node_block<D, false>(b, sp, t, sv, nullptr);
+    build_node_block<D, TB, false>(b, sp, t, sv, nullptr);
     cp_async_wait_all();
     __syncthreads();
     for (int e = tid; e < cnt; e += blockDim.x) {
@@ -1250,7 +1251,7 @@ __global__ void __launch_bounds__(T, 768 / T) k_g2p(BatchDev b) {
       float ro[Cfg<D>::S];
       pack<D>(q, ro);
       store_planes<D, Cfg<D>::PLANES>(sp.planes_out, sp.npad, id, ro);
-      const uint32_t nk = bin_key<D>(q.x, sp);  // bin of state n+1 and its histogram
+      const uint32_t nk = bin_key<D, TB>(q.x, sp);  // bin of state n+1 and its histogram
       sp.key[id] = nk;
       warp_aggregated_inc(b.tile_count, nk != KEY_INVALID ? int(sp.tile_base + (nk >> 6)) : -1);
     }
@@ -1495,10 +1496,10 @@ __device__ __forceinline__ float adj_core(Part<D>& q, Part<D>& g1, const float* 
 template <int D>
 constexpr int kAdjThreads = D == 3 ? 128 : 256;
 
-template <int D, bool MAT>
+template <int D, int TB, bool MAT>
 __global__ void __launch_bounds__(kAdjThreads<D>, 512 / kAdjThreads<D>) k_adj_gather(BatchDev b) {
   pdl_enter();
-  constexpr int B = Cfg<D>::B, NB = Cfg<D>::BLOCK_NODES, BN = Cfg<D>::BN;
+  constexpr int B = Tile<D, TB>::B, NB = Tile<D, TB>::BLOCK_NODES, BN = Tile<D, TB>::BN;
   __shared__ float4 sv[NB], sb[NB];
   __shared__ float wpart[8][MAX_GROUPS];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1514,7 +1515,7 @@ __global__ void __launch_bounds__(kAdjThreads<D>, 512 / kAdjThreads<D>) k_adj_ga
     unlin<D>(gt - sp.tile_base, sp.nt, t);
     const uint32_t st = b.tile_start[gt];
     const int cnt = int(b.tile_start[gt + 1] - st);
-    if (cnt > Cfg<D>::SORT_CAP) {  // skipped by the adjoint scatter (the step reports it)
+    if (cnt > Tile<D, TB>::SORT_CAP) {  // skipped by the adjoint scatter (the step reports it)
       if (tid < MAX_GROUPS) b.gpartial[size_t(slot) * MAX_GROUPS + tid] = 0.0f;
       continue;  // uniform across the CTA
     }
@@ -1522,7 +1523,7 @@ __global__ void __launch_bounds__(kAdjThreads<D>, 512 / kAdjThreads<D>) k_adj_ga
     // (requesting its adjoint too, or staging the second particle in shared memory, measured slower)
     float r[Cfg<D>::S];
     if (tid < cnt) load_planes<D, Cfg<D>::PLANES>(sp.planes, sp.npad, int(b.sorted[st + tid] & 0x3ffffffu), r);
-    build_node_block<D, true>(b, sp, t, sv, sb);
+    build_node_block<D, TB, true>(b, sp, t, sv, sb);
     __syncthreads();
     float lo = 0.0f, hi = 0.0f;  // per-warp group sums of (K), lane-owned
     for (int e0 = 0; e0 < cnt; e0 += blockDim.x) {
@@ -1616,20 +1617,34 @@ __global__ void __launch_bounds__(kAdjThreads<D>, 512 / kAdjThreads<D>) k_adj_ga
 }
 
 // ============================================================================ launchers (tiled)
+// Every tiled launcher picks the instantiation of the batch's tile edge: 4, or 8 for 2D scenes
+// created with 8 x 8-cell tiles.
 template <int D>
-cudaError_t launch_keys(const BatchDev& b, cudaStream_t s, const SelectPar* sel) {
-  cudaError_t e = cudaMemsetAsync(b.tile_count, 0, sizeof(uint32_t) * size_t(b.total_tiles), s);
-  if (e != cudaSuccess) return e;
+static bool wide_tiles(const BatchDev& b) {
+  return D == 2 && b.tile_edge == 8;
+}
+
+template <int D, int TB>
+static cudaError_t keys_impl(const BatchDev& b, cudaStream_t s, const SelectPar* sel) {
   if (sel) {  // at least one CTA: the selection is published even without particles
     const int nblk = b.total_particles > 0 ? (b.total_particles + 255) / 256 : 1;
-    launch_pdl(k_keys<D, true>, dim3(nblk), dim3(256), 0, s, b, sel);
+    launch_pdl(k_keys<D, TB, true>, dim3(nblk), dim3(256), 0, s, b, sel);
     count_launches(1);
     return cudaGetLastError();
   }
   if (b.total_particles == 0) return cudaSuccess;
-  launch_pdl(k_keys<D, false>, dim3((b.total_particles + 255) / 256), dim3(256), 0, s, b, sel);
+  launch_pdl(k_keys<D, TB, false>, dim3((b.total_particles + 255) / 256), dim3(256), 0, s, b, sel);
   count_launches(1);
   return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t launch_keys(const BatchDev& b, cudaStream_t s, const SelectPar* sel) {
+  cudaError_t e = cudaMemsetAsync(b.tile_count, 0, sizeof(uint32_t) * size_t(b.total_tiles), s);
+  if (e != cudaSuccess) return e;
+  if constexpr (D == 2)
+    if (wide_tiles<D>(b)) return keys_impl<D, 8>(b, s, sel);
+  return keys_impl<D, 4>(b, s, sel);
 }
 
 template <int D>
@@ -1657,24 +1672,26 @@ cudaError_t launch_sort(const BatchDev& b, cudaStream_t s, const SelectPar* sel)
   return cudaGetLastError();
 }
 
-template <int D, bool ADJ>
+template <int D, int TB, bool ADJ>
 static cudaError_t p2g_configure() {
-  cudaError_t e = cudaFuncSetAttribute(k_p2g<D, ADJ, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       int(P2GCfg<D, ADJ, 256>::SMEM));
+  cudaError_t e = cudaFuncSetAttribute(k_p2g<D, TB, ADJ, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(P2GCfg<D, TB, ADJ, 256>::SMEM));
   if constexpr (D == 2) {
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_p2g<D, ADJ, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               int(P2GCfg<D, ADJ, 128>::SMEM));
+      e = cudaFuncSetAttribute(k_p2g<D, TB, ADJ, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               int(P2GCfg<D, TB, ADJ, 128>::SMEM));
   }
   return e;
 }
 
 cudaError_t configure_kernels() {
   cudaError_t e;
-  if ((e = p2g_configure<2, false>()) != cudaSuccess) return e;
-  if ((e = p2g_configure<2, true>()) != cudaSuccess) return e;
-  if ((e = p2g_configure<3, false>()) != cudaSuccess) return e;
-  return p2g_configure<3, true>();
+  if ((e = p2g_configure<2, 4, false>()) != cudaSuccess) return e;
+  if ((e = p2g_configure<2, 4, true>()) != cudaSuccess) return e;
+  if ((e = p2g_configure<2, 8, false>()) != cudaSuccess) return e;
+  if ((e = p2g_configure<2, 8, true>()) != cudaSuccess) return e;
+  if ((e = p2g_configure<3, 4, false>()) != cudaSuccess) return e;
+  return p2g_configure<3, 4, true>();
 }
 
 // Persistent-grid size of tile kernel k: its CTAs per SM times the SMs, at most one per tile.
@@ -1684,45 +1701,62 @@ static int tile_grid(const BatchDev& b, int k) {
   return grid < 1 ? 1 : grid;
 }
 
-template <int D, bool ADJ>
+template <int D, int TB, bool ADJ>
 static cudaError_t p2g_impl(const BatchDev& b, cudaStream_t s) {
   const int k = ADJ ? TK_P2G_ADJ : TK_P2G;
   const int grid = tile_grid(b, k);
   bool small = false;  // 128-thread CTAs (2D only)
   if constexpr (D == 2) small = b.launch[k].threads == 128;
   if constexpr (D == 2) {
-    if (small) launch_pdl(k_p2g<D, ADJ, 128>, dim3(grid), dim3(128), P2GCfg<D, ADJ, 128>::SMEM, s, b);
+    if (small)
+      launch_pdl(k_p2g<D, TB, ADJ, 128>, dim3(grid), dim3(128), P2GCfg<D, TB, ADJ, 128>::SMEM, s, b);
   }
-  if (!small) launch_pdl(k_p2g<D, ADJ, 256>, dim3(grid), dim3(256), P2GCfg<D, ADJ, 256>::SMEM, s, b);
+  if (!small) launch_pdl(k_p2g<D, TB, ADJ, 256>, dim3(grid), dim3(256), P2GCfg<D, TB, ADJ, 256>::SMEM, s, b);
   count_launches(1);
   return cudaGetLastError();
 }
 
 template <int D>
 cudaError_t launch_p2g(const BatchDev& b, bool with_adjoint, cudaStream_t s) {
-  return with_adjoint ? p2g_impl<D, true>(b, s) : p2g_impl<D, false>(b, s);
+  if constexpr (D == 2)
+    if (wide_tiles<D>(b)) return with_adjoint ? p2g_impl<D, 8, true>(b, s) : p2g_impl<D, 8, false>(b, s);
+  return with_adjoint ? p2g_impl<D, 4, true>(b, s) : p2g_impl<D, 4, false>(b, s);
+}
+
+template <int D, int TB>
+static cudaError_t g2p_impl(const BatchDev& b, cudaStream_t s) {
+  const int grid = tile_grid(b, TK_G2P);
+  if (b.launch[TK_G2P].threads == 128)
+    launch_pdl(k_g2p<D, TB, 128>, dim3(grid), dim3(128), 0, s, b);
+  else
+    launch_pdl(k_g2p<D, TB, 256>, dim3(grid), dim3(256), 0, s, b);
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 template <int D>
 cudaError_t launch_g2p(const BatchDev& b, cudaStream_t s) {
-  const int grid = tile_grid(b, TK_G2P);
-  if (b.launch[TK_G2P].threads == 128)
-    launch_pdl(k_g2p<D, 128>, dim3(grid), dim3(128), 0, s, b);
+  if constexpr (D == 2)
+    if (wide_tiles<D>(b)) return g2p_impl<D, 8>(b, s);
+  return g2p_impl<D, 4>(b, s);
+}
+
+template <int D, int TB>
+static cudaError_t adj_gather_impl(const BatchDev& b, cudaStream_t s) {
+  const int grid = tile_grid(b, TK_ADJ_GATHER);
+  if (b.has_material)
+    launch_pdl(k_adj_gather<D, TB, true>, dim3(grid), dim3(kAdjThreads<D>), 0, s, b);
   else
-    launch_pdl(k_g2p<D, 256>, dim3(grid), dim3(256), 0, s, b);
+    launch_pdl(k_adj_gather<D, TB, false>, dim3(grid), dim3(kAdjThreads<D>), 0, s, b);
   count_launches(1);
   return cudaGetLastError();
 }
 
 template <int D>
 cudaError_t launch_adj_gather(const BatchDev& b, cudaStream_t s) {
-  const int grid = tile_grid(b, TK_ADJ_GATHER);
-  if (b.has_material)
-    launch_pdl(k_adj_gather<D, true>, dim3(grid), dim3(kAdjThreads<D>), 0, s, b);
-  else
-    launch_pdl(k_adj_gather<D, false>, dim3(grid), dim3(kAdjThreads<D>), 0, s, b);
-  count_launches(1);
-  return cudaGetLastError();
+  if constexpr (D == 2)
+    if (wide_tiles<D>(b)) return adj_gather_impl<D, 8>(b, s);
+  return adj_gather_impl<D, 4>(b, s);
 }
 
 template cudaError_t launch_keys<2>(const BatchDev&, cudaStream_t, const SelectPar*);

@@ -62,6 +62,7 @@ class SceneDesc(C.Structure):
         ("ctrl_params", C.c_void_p),
         ("impl", C.c_int),
         ("mem_space", C.c_int),
+        ("tile_edge", C.c_int),
     ]
 
 
@@ -136,6 +137,7 @@ _SIGS = {
     "mpm_status_str": [C.c_int],
     "mpm_scene_create": [C.c_void_p, C.POINTER(SceneDesc), C.POINTER(C.c_void_p)],
     "mpm_scene_destroy": [C.c_void_p],
+    "mpm_scene_tile_edge": [C.c_void_p, C.POINTER(C.c_int)],
     "mpm_step": [C.c_void_p, C.c_int],
     "mpm_rollout": [C.c_void_p, C.c_int, C.c_int, C.c_size_t],
     "mpm_backward": [C.c_void_p] + [C.c_void_p] * 9 + [C.c_int],
@@ -379,6 +381,7 @@ class Scene:
         desc.ctrl_params = _ptr(params_t)
         desc.impl = int(impl)
         desc.mem_space = 1 if dev else 0
+        desc.tile_edge = int(getattr(spec, "tile_edge", 0) or 0)
         h = C.c_void_p()
         _check(lib().mpm_scene_create(ctx.handle, C.byref(desc), C.byref(h)), "mpm_scene_create")
         self.handle = h
@@ -399,6 +402,13 @@ class Scene:
 
     def _touch(self):
         self.generation += 1
+
+    @property
+    def tile_edge(self) -> int:
+        """Cells per tile edge the library uses for this scene (4, or 8 for sparse 2D scenes)."""
+        e = C.c_int()
+        _check(lib().mpm_scene_tile_edge(self.handle, C.byref(e)), "mpm_scene_tile_edge")
+        return e.value
 
     # ------------------------------------------------------------------ forward
     def step(self, n: int = 1):

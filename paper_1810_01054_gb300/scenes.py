@@ -82,6 +82,7 @@ class SceneSpec:
     # per wall w = 2 axis + side (low side first): 0 sticky, 1 slip with friction wall_c[w], 2 open
     wall_kind: Optional[np.ndarray] = None  # [2 dim] int32 (None: bc_type on every wall)
     wall_c: Optional[np.ndarray] = None     # [2 dim] (None: friction_c on every wall)
+    tile_edge: int = 0  # cells per tile edge of the tiled form (0: the library chooses; 4; 8 in 2D)
 
     @property
     def n_particles(self) -> int:

@@ -3,7 +3,7 @@
 Requests (a scene, a horizon, forward-only or forward+gradient) arrive over time.  The server
 admits a request as soon as its batch has a slot and device memory for its checkpoints, keeps
 its state resident on the GPU, and advances every admitted request step-synchronously in the
-same launches (one batch per dimension, libgbmpm mpm_batch_*).  Requests that arrive while others
+same launches (one batch per dimension and tile edge, libgbmpm mpm_batch_*).  Requests that arrive while others
 run join at the next tick; finished ones leave and free their memory.  Latency is measured on the
 host from arrival to the moment the result (final state, and gradients when asked) is ready.
 
@@ -37,6 +37,7 @@ class Request:
     scene: Optional[object] = None
     slot: int = -1
     dim: int = 2
+    key: tuple = ()  # (dimension, tile edge): the batch that runs it
     admitted: float = 0.0
     done: float = 0.0
 
@@ -56,7 +57,8 @@ class Server:
         self.ctx = mpm.Context(device, stream=stream)
         free, _total = torch.cuda.mem_get_info(device)
         self.budget = int(free * mem_fraction)
-        self.batches = {2: mpm.Batch(self.ctx, 2, self.budget), 3: mpm.Batch(self.ctx, 3, self.budget)}
+        # one batch per (dimension, tile edge), made when its first request arrives
+        self.batches = {}
         self.tick_steps = tick_steps
         self.pending = collections.deque()
         self.active = {}
@@ -87,19 +89,22 @@ class Server:
                 continue
             if req.scene is None:
                 req.scene = mpm.Scene(self.ctx, req.spec)
-            slot = self.batches[req.dim].admit(req.scene, req.n_steps, req.want_grad)
+                req.key = (req.dim, req.scene.tile_edge)
+            if req.key not in self.batches:
+                self.batches[req.key] = mpm.Batch(self.ctx, req.dim, self.budget)
+            slot = self.batches[req.key].admit(req.scene, req.n_steps, req.want_grad)
             if slot < 0:  # no memory for it now; it waits for a finished request to leave
                 waiting.append(req)
                 continue
             req.slot = slot
             req.admitted = now
-            self.active[(req.dim, slot)] = req
+            self.active[(req.key, slot)] = req
         self.pending = waiting
 
     def _complete(self):
         for key in list(self.active):
             req = self.active[key]
-            batch = self.batches[req.dim]
+            batch = self.batches[req.key]
             if not batch.poll(req.slot):
                 continue
             status = batch.status(req.slot)
@@ -124,8 +129,8 @@ class Server:
     def step(self):
         """One scheduling round: admit arrived requests, advance every batch, collect results."""
         self._admit()
-        for dim, batch in self.batches.items():
-            if any(k[0] == dim for k in self.active):
+        for key, batch in self.batches.items():
+            if any(k[0] == key for k in self.active):
                 batch.tick(self.tick_steps)
         self._complete()
 

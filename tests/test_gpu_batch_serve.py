@@ -139,6 +139,28 @@ def test_serving_mix_sampled_requests_equal_alone(M, ctx):
     srv.close()
 
 
+def test_a_batch_keeps_one_tile_edge(M, ctx):
+    """The tile kernels of a launch are instantiated for one tile edge: a batch holding scenes of
+    one edge refuses another (MPM_ERR_ARG) and takes it once empty again."""
+    wide = M.Scene(ctx, S.walker_square_2d(0).copy(tile_edge=8))
+    narrow = M.Scene(ctx, S.walker_square_2d(0).copy(tile_edge=4))
+    batch = M.Batch(ctx, 2)
+    s0 = batch.admit(wide, 5, False)
+    assert s0 >= 0
+    with pytest.raises(M.MPMError) as e:
+        batch.admit(narrow, 5, False)
+    assert e.value.status == -1
+    while not batch.poll(s0):
+        batch.tick(8)
+    batch.release(s0)
+    s1 = batch.admit(narrow, 5, False)
+    assert s1 >= 0
+    while not batch.poll(s1):
+        batch.tick(8)
+    batch.release(s1)
+    batch.close()
+
+
 def test_admission_waits_for_memory(M, ctx):
     """A batch whose budget holds one request admits the second only after the first leaves."""
     spec = S.blob(2, 32, 200, 9, radius_cells=4.0)

@@ -470,3 +470,45 @@ def test_caller_particle_order_changes_no_bit(M, ctx, case):
             assert np.array_equal(a, b)
         else:
             assert np.array_equal(a[pr], b), i
+
+
+# ----------------------------------------------------------------------------- tile edge
+@pytest.mark.parametrize("edge", [4, 8])
+@pytest.mark.parametrize("name", ["2d_sticky", "2d_slip_friction", "2d_com"])
+def test_both_tile_edges_match_oracle(M, ctx, name, edge):
+    """2D scenes run with 4 x 4- or 8 x 8-cell tiles (the binning, the node blocks and every tile
+    kernel follow the scene's edge): one step and a 12-step rollout's gradients against the
+    oracle for each."""
+    spec = small_scenes()[name].copy(tile_edge=edge)
+    gpu = M.Scene(ctx, spec)
+    assert gpu.tile_edge == edge
+    st0 = O.Scene(spec).initial_state()
+    gpu.set_state(*st0, step=3)
+    gpu.step(1)
+    assert_state_close(gpu.get_state(), oracle_step_from(spec, st0, 3))
+    T = 12
+    osc = O.Scene(spec)
+    traj = osc.rollout(T)
+    rng = np.random.default_rng(4)
+    wx = rng.normal(size=traj[0][T].shape) / osc.N
+    wv = rng.normal(size=traj[1][T].shape) / osc.N
+    ogx, ogv, ogC, ogF, ogp = osc.backward(traj, (wx, wv, None, None))
+    gpu.set_state(*st0, step=0)
+    gpu.rollout(T, 5)
+    gx, gv, gC, gF, gp = gpu.backward(wx, wv)
+    gpu.close()
+    for nm, a, b in (("x0", gx, ogx), ("v0", gv, ogv), ("C0", gC, ogC), ("F0", gF, ogF), ("params", gp, ogp)):
+        assert_grad_close(a, b, f"{name} edge {edge} dL/d{nm}")
+
+
+def test_tile_edge_chosen_from_particle_density(M, ctx):
+    """0 lets the library choose: 8 x 8 tiles for a sparse 2D scene (the 1,024-particle square:
+    ~50 particles per occupied 4 x 4 tile), 4 x 4 for a dense one (the walker at 16 per cell) and
+    for 3D; 8 is refused in 3D."""
+    assert M.Scene(ctx, S.walker_square_2d(0)).tile_edge == 8
+    assert M.Scene(ctx, S.walker_2d(1, n_steps=10)).tile_edge == 4
+    assert M.Scene(ctx, small_scenes()["3d_sticky"]).tile_edge == 4
+    assert M.Scene(ctx, S.walker_square_2d(0).copy(tile_edge=4)).tile_edge == 4
+    with pytest.raises(M.MPMError) as e:
+        M.Scene(ctx, small_scenes()["3d_sticky"].copy(tile_edge=8))
+    assert e.value.status == -1

@@ -63,7 +63,7 @@ def test_p2g_with_128_thread_ctas_is_bitwise_the_default(M, ctx):
     """2D P2G and adjoint scatter with 128-thread CTAs (a thread owns up to two work items) give
     the bits of the 256-thread CTAs: the work items and every sum keep their order."""
     import torch
-    spec = S.blob(2, 48, 3000, 23, radius_cells=9.0, v_scale=0.3, c_scale=0.5, amp=2.0)
+    spec = S.blob(2, 48, 3000, 23, radius_cells=9.0, v_scale=0.3, c_scale=0.5, amp=2.0).copy(tile_edge=4)
     T, k = 24, 6
     st0, g0, _ = _run(M, ctx, spec, T, k, M.TUNE_OFF)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
@@ -87,7 +87,10 @@ def test_a_batch_tunes_its_composition_and_keeps_the_bits(M, ctx):
         st, g, _ = _run(M, ctx, spec, T, int(np.ceil(np.sqrt(T))), M.TUNE_OFF)
         alone.append(st + g)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    key = (2, B * spec.n_particles, B * (40 // 4) ** 2, sms)
+    probe = M.Scene(ctx, spec)
+    edge = probe.tile_edge  # the library's choice for this density (the key counts its tiles)
+    probe.close()
+    key = (2, B * spec.n_particles, B * ((40 + edge - 1) // edge) ** 2, sms)
     assert M.tune_cache_lookup(*key) is None
     batch = M.Batch(ctx, 2)
     scenes = [M.Scene(ctx, spec) for _ in range(B)]
