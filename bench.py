@@ -69,6 +69,7 @@ def parse():
     ap.add_argument("--no-soft", action="store_true")
     ap.add_argument("--no-walker", action="store_true")
     ap.add_argument("--no-permuted", action="store_true")
+    ap.add_argument("--no-paper-cube", action="store_true")
     ap.add_argument("--no-cpu-aggregate", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=1000)
     ap.add_argument("--no-budget-sweep", action="store_true")
@@ -646,6 +647,65 @@ def measure_serving(dev, stream, n_requests=1000, seed=4, loads=(0.25, 0.5, 0.75
             "percentiles": "numpy linear interpolation over each load's requests"}
 
 
+# The paper's speed table (Table II): time per frame of its CUDA implementation on an NVIDIA GTX
+# 1080 Ti for a falling elastic cube, forward (F) and backward (B); the steps per frame are not
+# stated, so these are particle-frames/s, context rather than a like-for-like rate.
+PAPER_TABLE2 = {
+    "falling_cube_3d_8000": {"F_ms_per_frame": 0.392, "B_ms_per_frame": 0.406},
+    "falling_cube_3d_64000": {"F_ms_per_frame": 1.594, "B_ms_per_frame": 1.774},
+    "falling_cube_3d_512000": {"F_ms_per_frame": 10.501, "B_ms_per_frame": 11.594},
+    "falling_cube_2d_6400": {"F_ms_per_frame": 0.10, "B_ms_per_frame": 0.14},
+}
+
+
+def measure_paper_cube(args, dev, stream, sizes=((3, 20), (3, 40), (3, 80), (2, 80)), T=100):
+    """The paper's speed-comparison workload, a falling elastic cube at its particle counts:
+    forward (T-step rollout keeping every state) and backward (the reverse pass alone) timed
+    separately with device events, beside the paper's per-frame times on its GPU."""
+    import torch
+    from paper_1810_01054_gb300 import mpm
+    from paper_1810_01054_gb300 import scenes as S
+    ctx = mpm.Context(dev.index, stream=stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    out = {}
+    for dim, side in sizes:
+        spec = S.falling_cube(dim, side, n_steps=T)
+        N = spec.n_particles
+        sc = mpm.Scene(ctx, spec)
+        seed = torch.zeros((N, dim), dtype=torch.float32, device=dev)
+        seed[:, 0] = 1.0 / N
+        outs = [torch.empty((N, dim), device=dev), torch.empty((N, dim), device=dev),
+                torch.empty((N, dim, dim), device=dev), torch.empty((N, dim, dim), device=dev),
+                torch.empty((1,), device=dev)]
+        fwd, bwd = [], []
+        for i in range(max(1, args.warmup) + 3):
+            sc.set_state(spec.x0, spec.v0, spec.C0, spec.F0, step=0)
+            flush.zero_()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(stream)
+            sc.rollout(T, 1)
+            ev[1].record(stream)
+            sc.backward(seed, out=outs)
+            ev[2].record(stream)
+            torch.cuda.synchronize(dev)
+            if i >= max(1, args.warmup):
+                fwd.append(ev[0].elapsed_time(ev[1]))
+                bwd.append(ev[1].elapsed_time(ev[2]))
+        sc.close()
+        f_ms, b_ms = float(np.median(fwd)) / T, float(np.median(bwd)) / T
+        paper = PAPER_TABLE2.get(spec.name, {})
+        out[spec.name] = {"particles": N, "grid": "x".join(map(str, spec.n_grid)), "sim_steps": T,
+                          "F_us_per_step": 1e3 * f_ms, "B_us_per_step": 1e3 * b_ms,
+                          "F_particle_steps_per_s": N / (f_ms / 1e3), "B_particle_steps_per_s": N / (b_ms / 1e3),
+                          "paper_gtx1080ti": {**paper,
+                                              "F_particle_frames_per_s": N / (paper["F_ms_per_frame"] / 1e3),
+                                              "B_particle_frames_per_s": N / (paper["B_ms_per_frame"] / 1e3)}}
+    ctx.close()
+    return {"workload": "falling elastic cube (Table II's scene; grid and material are this build's choice)",
+            "unit": UNIT, "by_size": out,
+            "paper_note": "the paper times frames of unstated step count on a GTX 1080 Ti: context only"}
+
+
 # FP64 roofline: GB300 SMs issue 2 FP64 thread-ops per clock (the nominal 1.25 TFLOP/s FP64 rate:
 # 152 SMs x 2 DFMA x 2 flops x 2.07 GHz); no measured FP64 peak exists for this pool.
 F64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
@@ -847,6 +907,9 @@ def run_ours(args, rank, world, local_rank):
                     "ms_per_step": mr["tot_ms"] / args.steps, "roofline": mr["roofline"],
                     "kernel_share_of_profiled_step": mr["share"],
                     "gradients": "dL/dx0, v0, C0, F0, controller parameters, E_p, m_p"}
+    paper_cube = None
+    if rank == 0 and not args.no_paper_cube:
+        paper_cube = measure_paper_cube(args, dev, stream)
     serving = None
     if rank == 0 and not args.no_serve:
         serving = measure_serving(dev, stream, n_requests=args.serve_requests)
@@ -873,7 +936,7 @@ def run_ours(args, rank, world, local_rank):
         "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": r["gpu_launches"], "clocks": r["clocks"],
         "plain_form": r["plain"], "walker": walker, "large_scene": large, "material": material,
         "serving": serving, "fp64": fp64, "large_scene_budgets": sweep, "small_scene_replicas": replicas,
-        "soft_body": soft, "permuted_order": permuted,
+        "soft_body": soft, "permuted_order": permuted, "paper_workload": paper_cube,
     }
     print(json.dumps(line), flush=True)
 

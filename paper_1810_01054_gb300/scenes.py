@@ -197,6 +197,30 @@ def walker_square_2d(seed: int = 0, *, lift_cells: float = 0.0, n_steps: int = 1
                    [4.0, -2.0], rng, 0.1 * dx, freq=1.0, n_steps=n_steps)
 
 
+def falling_cube(dim: int, side: int, seed: int = 6, *, n_steps: int = 100) -> SceneSpec:
+    """The falling elastic cube of Section IV's speed comparison (Table II): side^dim particles on
+    a lattice of spacing dx/2 (side 20, 40, 80 in 3D give the table's 8,000, 64,000 and 512,000
+    particles; 80 in 2D its 6,400), jitter +-0.1 dx, released from rest with its bottom 2 dx above
+    the 3-cell sticky floor band, centred in x (and z), on a grid with a quarter of the cube's width
+    of margin around it (at least 32 cells); E = 20, nu = 0.3, gravity, no actuation (one group,
+    zero amplitude), dt at half the explicit-integration limit.  The paper gives neither grid nor
+    material for this scene."""
+    rng = np.random.default_rng(seed)
+    cells = side // 2  # the cube's width in cells
+    n = max(32, int(math.ceil(1.5 * cells)) + 8)
+    dx = 1.0 / n
+    s = dx / 2
+    E = 20.0
+    dt = 0.5 * dx * math.sqrt(1.0 / E)
+    idx = np.stack(np.meshgrid(*([np.arange(side)] * dim), indexing="ij"), axis=-1).reshape(-1, dim)
+    lo = np.full(dim, 0.5 * (n - cells) * dx)
+    lo[1] = 5 * dx
+    pos = lo + (idx + 0.5) * s
+    group = np.zeros(pos.shape[0], np.int32)
+    return _finish(f"falling_cube_{dim}d_{side ** dim}", dim, n, dx, dt, E, s, pos, group, _up(dim, 1),
+                   CTRL_SIN, [0.0], rng, 0.1 * dx, n_steps=n_steps)
+
+
 def walker_2d(seed: int = 1, *, n_steps: int = 1000) -> SceneSpec:
     """2D soft walker: 128^2 grid, dx = 1/128, body 0.5 x 0.1 on 4 legs 0.08 x 0.2 (each size
     +-10 % seeded), legs standing on the 3-cell sticky floor band, lattice spacing dx/4 (16

@@ -512,3 +512,29 @@ def test_tile_edge_chosen_from_particle_density(M, ctx):
     with pytest.raises(M.MPMError) as e:
         M.Scene(ctx, small_scenes()["3d_sticky"].copy(tile_edge=8))
     assert e.value.status == -1
+
+
+@pytest.mark.parametrize("dim,side", [(3, 20), (2, 80)])
+def test_falling_cube_matches_oracle(M, ctx, dim, side):
+    """The paper's speed-comparison scene (a falling elastic cube at Table II's particle counts):
+    10-step windows of a 30-step fall onto the sticky floor, and the gradient of a 30-step rollout
+    keeping every state, as the bench times it."""
+    spec = S.falling_cube(dim, side, n_steps=30)
+    osc = O.Scene(spec)
+    traj = osc.rollout(30)
+    gpu = M.Scene(ctx, spec)
+    for w in range(3):
+        n0 = 10 * w
+        gpu.set_state(traj[0][n0], traj[1][n0], traj[2][n0], traj[3][n0], step=n0)
+        gpu.step(10)
+        assert_state_close(gpu.get_state(), tuple(t[n0 + 10] for t in traj[:4]))
+    rng = np.random.default_rng(8)
+    wx = rng.normal(size=traj[0][30].shape) / osc.N
+    wv = rng.normal(size=traj[1][30].shape) / osc.N
+    ogx, ogv, ogC, ogF, _ = osc.backward(traj, (wx, wv, None, None))
+    gpu.set_state(*osc.initial_state(), step=0)
+    gpu.rollout(30, 1)
+    gx, gv, gC, gF, _ = gpu.backward(wx, wv)
+    gpu.close()
+    for nm, a, b in (("x0", gx, ogx), ("v0", gv, ogv), ("C0", gC, ogC), ("F0", gF, ogF)):
+        assert_grad_close(a, b, f"cube {dim}d dL/d{nm}")
