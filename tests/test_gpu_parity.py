@@ -527,7 +527,13 @@ def test_falling_cube_matches_oracle(M, ctx, dim, side):
         n0 = 10 * w
         gpu.set_state(traj[0][n0], traj[1][n0], traj[2][n0], traj[3][n0], step=n0)
         gpu.step(10)
-        assert_state_close(gpu.get_state(), tuple(t[n0 + 10] for t in traj[:4]))
+        x, v, Cm, F = gpu.get_state()
+        ref = tuple(t[n0 + 10] for t in traj[:4])
+        assert_state_close((x, v, F), (ref[0], ref[1], ref[3]), names=("x", "v", "F"))
+        # C is exactly zero while the cube falls as a rigid body (the oracle's is ~1e-16): its error
+        # is measured against its natural size |v| / dx
+        scale = max(np.linalg.norm(ref[2]), np.linalg.norm(ref[1]) / spec.dx)
+        assert np.linalg.norm(Cm - ref[2]) / scale <= FWD_TOL
     rng = np.random.default_rng(8)
     wx = rng.normal(size=traj[0][30].shape) / osc.N
     wv = rng.normal(size=traj[1][30].shape) / osc.N
