@@ -297,26 +297,7 @@ __global__ void k_scan_reduce(BatchDev b, const SelectPar* __restrict__ sel) {
   }
 }
 
-// Phase 2: exclusive scan of the block totals (one CTA).
-__global__ void k_scan_top(BatchDev b, int n_blocks) {
-  pdl_enter();
-  uint32_t carry_s = 0, carry_c = 0;
-  for (int base = 0; base < n_blocks; base += blockDim.x) {
-    int i = base + threadIdx.x;
-    uint32_t s = i < n_blocks ? b.block_sums[2 * i] : 0u, c = i < n_blocks ? b.block_sums[2 * i + 1] : 0u;
-    uint32_t ts, tc;
-    block_scan2(s, c, ts, tc);
-    if (i < n_blocks) {
-      b.block_sums[2 * i] = s + carry_s;
-      b.block_sums[2 * i + 1] = c + carry_c;
-    }
-    carry_s += ts;
-    carry_c += tc;
-    __syncthreads();
-  }
-}
-
-// Phase 3: tile_start, tile_slot, active list, n_active; resets the per-step counters for the
+// Phase 2: tile_start, tile_slot, active list, n_active; resets the per-step counters for the
 // next step.
 __global__ void k_scan_down(BatchDev b) {
   pdl_enter();
@@ -330,12 +311,28 @@ __global__ void k_scan_down(BatchDev b) {
     s += cnt[i];
     c += cnt[i] > 0;
   }
+  // this block's offsets: the totals of the blocks before it (one warp; a few dozen at most)
+  __shared__ uint32_t boff[2];
+  if (threadIdx.x < 32) {
+    uint32_t a = 0, n = 0;
+    for (int i = threadIdx.x; i < int(blockIdx.x); i += 32) {
+      a += b.block_sums[2 * i];
+      n += b.block_sums[2 * i + 1];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      n += __shfl_xor_sync(0xffffffffu, n, o);
+    }
+    if (threadIdx.x == 0) {
+      boff[0] = a;
+      boff[1] = n;
+    }
+  }
   uint32_t ts, tc;
-  block_scan2(s, c, ts, tc);
-  uint32_t off_s = b.block_sums[2 * blockIdx.x];
-  uint32_t off_c = b.block_sums[2 * blockIdx.x + 1];
-  s += off_s;
-  c += off_c;
+  block_scan2(s, c, ts, tc);  // its barriers publish boff
+  s += boff[0];
+  c += boff[1];
 #pragma unroll
   for (int i = 0; i < SCAN_PER_THREAD; ++i) {
     int t = base + i;
@@ -576,6 +573,9 @@ __global__ void __launch_bounds__(T, T == 256 ? (D == 3 && !ADJ ? 3 : 2) : 4) k_
   float* U = reinterpret_cast<float*>(smem_raw + K::IDS_BYTES);
   __shared__ int cstart[CELLS + 1], cfill[CELLS];
   const int tid = threadIdx.x;
+  // the CTA's first active tile is requested together with the count (the entry is in bounds
+  // whatever the count; it is used only when the slot is below it)
+  const int first_gt = b.total_tiles > 0 ? b.active[int(blockIdx.x) < b.total_tiles ? blockIdx.x : 0] : 0;
   const int n_active = *b.n_active;
   // the per-step counters are cleared here whichever scan ran (the fused one leaves them set, the
   // separate one leaves the scatter's fill counts): every step then starts from zero, also when a
@@ -586,8 +586,8 @@ __global__ void __launch_bounds__(T, T == 256 ? (D == 3 && !ADJ ? 3 : 2) : 4) k_
   }
 
   for (int slot = blockIdx.x; slot < n_active; slot += gridDim.x) {
-    const int gt = b.active[slot];
-    const ScenePar& sp = b.scenes[b.tile_scene[gt]];
+    const int gt = slot == int(blockIdx.x) ? first_gt : b.active[slot];
+    const ScenePar& sp = b.scenes[b.n_scenes == 1 ? 0 : b.tile_scene[gt]];
     const uint32_t st = b.tile_start[gt];
     const int cnt = int(b.tile_start[gt + 1] - st);
     if (cnt > K::CAP) {  // the step fails (status); the tile adds nothing to the grid
@@ -1112,6 +1112,8 @@ __device__ __forceinline__ void warp_group_add(int g, float c, float& lo, float&
 template <int D, class Fetch>
 __device__ __forceinline__ void g2p_core(Part<D>& q, const float* f, const float (&w)[D][3], float dt, float inv_dx,
                                          Fetch fetch) {
+  // sum_i N v and sum_i N v k^T (k the integer node offset; the f part is taken once below),
+  // formed as nested weighted sums: over z within a row, over y within an x-slab, then over x
   float vn[D], Cn[D][D];
 #pragma unroll
   for (int a = 0; a < D; ++a) {
@@ -1120,26 +1122,47 @@ __device__ __forceinline__ void g2p_core(Part<D>& q, const float* f, const float
     for (int c = 0; c < D; ++c) Cn[a][c] = 0.0f;
   }
 #pragma unroll
-  for (int kx = 0; kx < 3; ++kx)
+  for (int kx = 0; kx < 3; ++kx) {
+    float sv[D], sy[D], sz[D];  // slab sums of wy wz v, ky wy wz v, kz wy wz v
 #pragma unroll
-    for (int ky = 0; ky < 3; ++ky)
+    for (int ky = 0; ky < 3; ++ky) {
+      float r[D], rz[D];  // row sums of wz v and kz wz v (2D: the node's v)
+      if constexpr (D == 3) {
 #pragma unroll
-      for (int kz = 0; kz < (D == 3 ? 3 : 1); ++kz) {
-        float N = w[0][kx] * w[1][ky];
-        if constexpr (D == 3) N *= w[D == 3 ? 2 : 0][kz];
-        const float4 g = fetch(kx, ky, kz);
-        const float vv[3] = {g.x, g.y, g.z};
-        const int k[3] = {kx, ky, kz};
-        // Cn accumulates sum N v k^T here (k the integer node offset); the f part is taken once below
+        for (int kz = 0; kz < 3; ++kz) {
+          const float4 g = fetch(kx, ky, kz);
+          const float vv[3] = {g.x, g.y, g.z};
+          const float wz = w[D == 3 ? 2 : 0][kz];
 #pragma unroll
-        for (int a = 0; a < D; ++a) {
-          const float Nv = N * vv[a];
-          vn[a] += Nv;
-#pragma unroll
-          for (int c = 0; c < D; ++c)
-            if (k[c] > 0) Cn[a][c] += float(k[c]) * Nv;
+          for (int a = 0; a < D; ++a) {
+            r[a] = kz == 0 ? wz * vv[a] : r[a] + wz * vv[a];
+            if (kz == 1) rz[a] = wz * vv[a];
+            if (kz == 2) rz[a] += (2.0f * wz) * vv[a];
+          }
         }
+      } else {
+        const float4 g = fetch(kx, ky, 0);
+        r[0] = g.x;
+        r[1] = g.y;
       }
+      const float wy = w[1][ky];
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        sv[a] = ky == 0 ? wy * r[a] : sv[a] + wy * r[a];
+        if (ky == 1) sy[a] = wy * r[a];
+        if (ky == 2) sy[a] += (2.0f * wy) * r[a];
+        if constexpr (D == 3) sz[a] = ky == 0 ? wy * rz[a] : sz[a] + wy * rz[a];
+      }
+    }
+    const float wx = w[0][kx];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      vn[a] += wx * sv[a];
+      if (kx > 0) Cn[a][0] += (float(kx) * wx) * sv[a];
+      Cn[a][1] += wx * sy[a];
+      if constexpr (D == 3) Cn[a][D - 1] += wx * sz[a];
+    }
+  }
   const float s = 4.0f * inv_dx;  // (4/dx^2) * dx, since x_i - x_p = dx (k - f)
   float Fo[D][D];
 #pragma unroll
@@ -1181,13 +1204,16 @@ __global__ void __launch_bounds__(T, 768 / T) k_g2p(BatchDev b) {
   __shared__ float4 sv[NB];
   __shared__ float4 stage[K::NP][K::STAGE];
   const int tid = threadIdx.x;
+  // the CTA's first active tile is requested together with the count (the entry is in bounds
+  // whatever the count; it is used only when the slot is below it)
+  const int first_gt = b.total_tiles > 0 ? b.active[int(blockIdx.x) < b.total_tiles ? blockIdx.x : 0] : 0;
   const int n_active = *b.n_active;
   if (blockIdx.x == 0)  // this step's counters move on (every reader of them ran before)
     for (int s = tid; s < b.n_scenes; s += blockDim.x)
       if (b.scenes[s].step_ctr) *b.scenes[s].step_ctr += 1;
   for (int slot = blockIdx.x; slot < n_active; slot += gridDim.x) {
-    const int gt = b.active[slot];
-    const ScenePar& sp = b.scenes[b.tile_scene[gt]];
+    const int gt = slot == int(blockIdx.x) ? first_gt : b.active[slot];
+    const ScenePar& sp = b.scenes[b.n_scenes == 1 ? 0 : b.tile_scene[gt]];
     int t[D];
     unlin<D>(gt - sp.tile_base, sp.nt, t);
     const uint32_t st = b.tile_start[gt];
@@ -1503,14 +1529,17 @@ __global__ void __launch_bounds__(kAdjThreads<D>, 512 / kAdjThreads<D>) k_adj_ga
   __shared__ float4 sv[NB], sb[NB];
   __shared__ float wpart[8][MAX_GROUPS];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // the CTA's first active tile is requested together with the count (the entry is in bounds
+  // whatever the count; it is used only when the slot is below it)
+  const int first_gt = b.total_tiles > 0 ? b.active[int(blockIdx.x) < b.total_tiles ? blockIdx.x : 0] : 0;
   const int n_active = *b.n_active;
   if (b.rewind_ctr && blockIdx.x == 0 && tid == 0) {
     *b.rewind_rows = n_active;
     *b.rewind_ctr -= 1;
   }
   for (int slot = blockIdx.x; slot < n_active; slot += gridDim.x) {
-    const int gt = b.active[slot];
-    const ScenePar& sp = b.scenes[b.tile_scene[gt]];
+    const int gt = slot == int(blockIdx.x) ? first_gt : b.active[slot];
+    const ScenePar& sp = b.scenes[b.n_scenes == 1 ? 0 : b.tile_scene[gt]];
     int t[D];
     unlin<D>(gt - sp.tile_base, sp.nt, t);
     const uint32_t st = b.tile_start[gt];
@@ -1663,12 +1692,11 @@ cudaError_t launch_sort(const BatchDev& b, cudaStream_t s, const SelectPar* sel)
     launch_pdl(k_scan_reduce<true>, dim3(nblk + 1), dim3(SCAN_THREADS), 0, s, b, sel);
   else
     launch_pdl(k_scan_reduce<false>, dim3(nblk), dim3(SCAN_THREADS), 0, s, b, sel);
-  launch_pdl(k_scan_top, dim3(1), dim3(SCAN_THREADS), 0, s, b, nblk);
   launch_pdl(k_scan_down, dim3(nblk), dim3(SCAN_THREADS), 0, s, b);
   if (b.total_particles > 0)
     launch_pdl(k_scatter<D, false, false>, dim3((b.total_particles + 255) / 256), dim3(256), 0, s, b,
                static_cast<const SelectPar*>(nullptr));
-  count_launches((b.total_particles > 0 ? 1 : 0) + 3);
+  count_launches((b.total_particles > 0 ? 1 : 0) + 2);
   return cudaGetLastError();
 }
 
