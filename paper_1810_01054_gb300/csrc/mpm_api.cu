@@ -670,6 +670,8 @@ mpm_status ensure_ws2_parts(mpm_scene* s) {
   CKS(dalloc(&b.active, nt, L));
   CKS(dalloc(&b.n_active, 1, L));
   CKS(dalloc(&b.block_sums, 2 * ((nt + 2047) / 2048) + 2, L));
+  CKS(dalloc(&b.work, 4, L));
+  CK(cudaMemsetAsync(b.work, 0, sizeof(uint32_t) * 4, s->ctx->stream));
   CKS(dalloc(&b.sorted, s->npad, L));
   CKS(dalloc(&b.partial, size_t(nt) * NB, L));
   CKS(dalloc(&b.partial_b, size_t(nt) * NB, L));
@@ -1601,6 +1603,7 @@ mpm_status mpm_scene_create(mpm_ctx* c, const mpm_scene_desc* d, mpm_scene** out
   ALLOC(b.active, p.n_tiles);
   ALLOC(b.n_active, 1);
   ALLOC(b.block_sums, 2 * ((p.n_tiles + 2047) / 2048) + 2);
+  ALLOC(b.work, 4);
   ALLOC(b.sorted, s->npad);
   if (s->impl == MPM_IMPL_TILED) {
     ALLOC(b.partial, size_t(p.n_tiles) * NB);
@@ -1626,6 +1629,7 @@ mpm_status mpm_scene_create(mpm_ctx* c, const mpm_scene_desc* d, mpm_scene** out
   cudaStream_t stream = c->stream;
   TRY(cuda_fail(cudaMemsetAsync(b.tile_count, 0, sizeof(uint32_t) * p.n_tiles, stream)));
   TRY(cuda_fail(cudaMemsetAsync(b.tile_fill, 0, sizeof(uint32_t) * p.n_tiles, stream)));
+  TRY(cuda_fail(cudaMemsetAsync(b.work, 0, sizeof(uint32_t) * 4, stream)));
   TRY(cuda_fail(cudaMemsetAsync(tile_scene, 0, sizeof(int) * p.n_tiles, stream)));
   TRY(cuda_fail(cudaMemsetAsync(s->d_status, 0, sizeof(int), stream)));
   TRY(cuda_fail(cudaMemsetAsync(s->d_step, 0, sizeof(int), stream)));

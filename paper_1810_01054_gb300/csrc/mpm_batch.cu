@@ -88,6 +88,7 @@ void free_sub(SubBatch& sb) {
   dfree(sb.b.active);
   dfree(sb.b.n_active);
   dfree(sb.b.block_sums);
+  dfree(sb.b.work);
   dfree(sb.b.sorted);
   dfree(sb.b.gpartial);
   dfree(sb.partial);
@@ -140,6 +141,8 @@ mpm_status grow(mpm_batch* B, SubBatch& sb, int n_scenes, int tiles, int particl
   CK(cudaMalloc(&sb.b.active, sizeof(int) * tl));
   CK(cudaMalloc(&sb.b.n_active, sizeof(int)));
   CK(cudaMalloc(&sb.b.block_sums, sizeof(uint32_t) * (2 * ((tl + 2047) / 2048) + 2)));
+  CK(cudaMalloc(&sb.b.work, sizeof(uint32_t) * 4));
+  CK(cudaMemsetAsync(sb.b.work, 0, sizeof(uint32_t) * 4, B->ctx->stream));
   CK(cudaMalloc(&sb.b.sorted, sizeof(uint32_t) * pc));
   CK(cudaMalloc(&sb.b.gpartial, sizeof(float) * size_t(tl) * MAX_GROUPS));
   CK(cudaMemsetAsync(sb.b.tile_count, 0, sizeof(uint32_t) * tl, B->ctx->stream));

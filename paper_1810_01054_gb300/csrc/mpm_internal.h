@@ -144,6 +144,8 @@ struct BatchDev {
   int* active;          // [total_tiles] batch tile id of every active slot
   int* n_active;        // [1]
   uint32_t* block_sums; // scan scratch
+  uint32_t* work;       // [4] tile counters of the dynamically scheduled P2G and adjoint gather and
+                        // their CTAs-done tickets; zero between launches
   uint32_t* sorted;     // [total_particles] scene-local particle ids, tile-major, canonical
   float4* partial;      // [total_tiles * BLOCK_NODES] node blocks of P2G
   float4* partial_b;    // [total_tiles * BLOCK_NODES] node blocks of the adjoint scatter

@@ -523,6 +523,29 @@ template cudaError_t launch_store_sort<3>(const BatchDev&, uint32_t*, cudaStream
 template cudaError_t launch_load_sort<2>(const BatchDev&, const SelectPar*, cudaStream_t, int, int*);
 template cudaError_t launch_load_sort<3>(const BatchDev&, const SelectPar*, cudaStream_t, int, int*);
 
+// Dynamic tile scheduling (the forward P2G and the adjoint gather, when a launch has more than two
+// active tiles per CTA; fewer, and the other tile kernels, measured faster with the fixed stride):
+// a CTA takes its first active slot by its index and every later one from the kernel's counter
+// work[w], so CTAs that finish early take more tiles.  Which CTA computes a tile changes no bit of
+// it.  The last CTA to finish (its ticket in work[w + 2]) puts both words back to zero for the next
+// launch.
+__device__ __forceinline__ void claim_next(const BatchDev& b, int w, int* s_next, int it) {
+  if (threadIdx.x == 0) s_next[it & 1] = int(gridDim.x) + int(atomicAdd(b.work + w, 1u));
+}
+__device__ __forceinline__ int take_next(const int* s_next, int it) {
+  __syncthreads();  // the claim of this iteration is visible (and the one before it consumed)
+  return s_next[it & 1];
+}
+__device__ __forceinline__ void release_work(const BatchDev& b, int w) {
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(b.work + w + 2, 1u) == gridDim.x - 1) {
+      b.work[w] = 0u;
+      b.work[w + 2] = 0u;
+    }
+  }
+}
+
 // ============================================================================ P2G (tiled)
 // Phase A  canonical order of the tile's particles: by cell, then by particle id (counting sort
 //          over the tile's cells, insertion sort inside each cell) -- fixes every later sum order.
@@ -585,7 +608,11 @@ __global__ void __launch_bounds__(T, T == 256 ? (D == 3 && !ADJ ? 3 : 2) : 4) k_
     b.tile_fill[i] = 0u;
   }
 
-  for (int slot = blockIdx.x; slot < n_active; slot += gridDim.x) {
+  __shared__ int s_next[2];
+  const bool dyn = !ADJ && n_active > 2 * int(gridDim.x);  // uniform across the grid
+  int it = 0;
+  for (int slot = blockIdx.x; slot < n_active; slot = dyn ? take_next(s_next, it++) : slot + int(gridDim.x)) {
+    if (dyn) claim_next(b, 0, s_next, it);
     const int gt = slot == int(blockIdx.x) ? first_gt : b.active[slot];
     const ScenePar& sp = b.scenes[b.n_scenes == 1 ? 0 : b.tile_scene[gt]];
     const uint32_t st = b.tile_start[gt];
@@ -949,6 +976,7 @@ __global__ void __launch_bounds__(T, T == 256 ? (D == 3 && !ADJ ? 3 : 2) : 4) k_
     }
     __syncthreads();
   }
+  if (dyn) release_work(b, 0);
 }
 
 // ============================================================================ grid
@@ -1537,7 +1565,11 @@ __global__ void __launch_bounds__(kAdjThreads<D>, 512 / kAdjThreads<D>) k_adj_ga
     *b.rewind_rows = n_active;
     *b.rewind_ctr -= 1;
   }
-  for (int slot = blockIdx.x; slot < n_active; slot += gridDim.x) {
+  __shared__ int s_next[2];
+  const bool dyn = n_active > 2 * int(gridDim.x);  // uniform across the grid
+  int it = 0;
+  for (int slot = blockIdx.x; slot < n_active; slot = dyn ? take_next(s_next, it++) : slot + int(gridDim.x)) {
+    if (dyn) claim_next(b, 1, s_next, it);
     const int gt = slot == int(blockIdx.x) ? first_gt : b.active[slot];
     const ScenePar& sp = b.scenes[b.n_scenes == 1 ? 0 : b.tile_scene[gt]];
     int t[D];
@@ -1643,6 +1675,7 @@ __global__ void __launch_bounds__(kAdjThreads<D>, 512 / kAdjThreads<D>) k_adj_ga
     }
     __syncthreads();
   }
+  if (dyn) release_work(b, 1);
 }
 
 // ============================================================================ launchers (tiled)

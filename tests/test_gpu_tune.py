@@ -105,3 +105,29 @@ def test_a_batch_tunes_its_composition_and_keeps_the_bits(M, ctx):
         sc.close()
     shapes = M.tune_cache_lookup(*key)
     assert shapes is not None and shapes[M.TK_ADJ_GATHER][1] == 256
+
+
+def test_dynamic_tile_scheduling_keeps_the_bits(M, ctx):
+    """With more than two active tiles per CTA the forward P2G and the adjoint gather hand out
+    tiles from a counter (the CTA that computes a tile varies from run to run); with fewer they
+    use the fixed stride.  A 3D scene of ~1500 active tiles run under 2 CTAs per SM (counter: more
+    than 4 tiles per SM) and under 8 (fixed stride) gives the same bits, over a rollout whose
+    segments are recomputed (the recompute's workspace has counters of its own) and its reverse
+    pass, twice in a row (the counters are back to zero after every launch)."""
+    import torch
+    spec = S.blob(3, 64, 150000, 31, radius_cells=26.0, v_scale=0.3, amp=2.0, bc_width=3)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    x = np.asarray(spec.x0)
+    t = np.floor(x / spec.dx - 0.5).astype(int) // 4
+    n_active = len(np.unique((t[:, 0] * 16 + t[:, 1]) * 16 + t[:, 2]))
+    assert 2 * 2 * sms < n_active <= 2 * 8 * sms
+    T, k = 12, 4
+    res = []
+    for ctas in (8, 2, 2):
+        M.tune_cache_store(3, spec.n_particles, 16 ** 3, sms, [(ctas, 256), (4, 256), (4, 256), (ctas, 256)])
+        st, g, sh = _run(M, ctx, spec, T, k, M.TUNE_AUTO)
+        assert sh[M.TK_P2G][0] == ctas and sh[M.TK_ADJ_GATHER][0] == ctas
+        res.append(st + g)
+    for r in res[1:]:
+        for a, b in zip(res[0], r):
+            assert np.array_equal(a, b)
