@@ -609,6 +609,9 @@ __global__ void __launch_bounds__(T, T == 256 ? (D == 3 && !ADJ ? 3 : 2) : 4) k_
   }
 
   __shared__ int s_next[2];
+  // the per-cell counters are zero whenever a tile starts: here, and again at the end of every tile
+  if (tid < CELLS) cfill[tid] = 0;
+  __syncthreads();
   const bool dyn = !ADJ && n_active > 2 * int(gridDim.x);  // uniform across the grid
   int it = 0;
   for (int slot = blockIdx.x; slot < n_active; slot = dyn ? take_next(s_next, it++) : slot + int(gridDim.x)) {
@@ -630,7 +633,16 @@ __global__ void __launch_bounds__(T, T == 256 ? (D == 3 && !ADJ ? 3 : 2) : 4) k_
     // this thread's work items tid + j T: (cell, stencil part)
     bool item_thread[K::IPT];
     int my_cell[K::IPT], my_part[K::IPT], ikx[K::IPT], iky[K::IPT];
-    float acc[K::IPT][K::NK][K::CH];
+    float acc[K::IPT][K::NK][K::CH];  // 2D
+    // 3D (one item per thread): the channels in pairs for the packed FP32 FMA, whose halves round
+    // exactly as two fmaf: (p_x, p_y), (p_z, m), and in the reverse pass (vbar*_x, vbar*_y), vbar*_z
+    float2 aP01[K::NK], aP2m[K::NK], aQ01[K::NK];
+    float aQ2[K::NK];
+#pragma unroll
+    for (int k = 0; k < K::NK; ++k) {
+      aP01[k] = aP2m[k] = aQ01[k] = make_float2(0.0f, 0.0f);
+      aQ2[k] = 0.0f;
+    }
 #pragma unroll
     for (int j = 0; j < K::IPT; ++j) {
       const int it = tid + j * T;
@@ -750,39 +762,81 @@ __global__ void __launch_bounds__(T, T == 256 ? (D == 3 && !ADJ ? 3 : 2) : 4) k_
               acc[j][0][K::CHF + a] += N * (aa[a] + Ma[a * D] * float(ikx[j]) + Ma[a * D + 1] * float(iky[j]));
           }
         } else {
-          float u[D], ua[D];
-#pragma unroll
-          for (int a = 0; a < D; ++a) u[a] = av[a] + Mv[a * D] * float(ikx[j]);
+          // u = a + M[:,0] kx, then per row + M[:,1] ky and per node + M[:,2] kz (M row-major)
+          const float kxf = float(ikx[j]);
+          const float2 u01 = __ffma2_rn(make_float2(Mv[0], Mv[3]), make_float2(kxf, kxf), make_float2(av[0], av[1]));
+          const float u2s = fmaf(Mv[6], kxf, av[2]);
+          float2 q01 = make_float2(0.0f, 0.0f);
+          float q2s = 0.0f;
           if constexpr (ADJ) {
-#pragma unroll
-            for (int a = 0; a < D; ++a) ua[a] = rec[K::RF + a] + rec[K::RF + D + a * D] * float(ikx[j]);
+            const float* aa = rec + K::RF;
+            const float* Ma = aa + D;
+            q01 = __ffma2_rn(make_float2(Ma[0], Ma[3]), make_float2(kxf, kxf), make_float2(aa[0], aa[1]));
+            q2s = fmaf(Ma[6], kxf, aa[2]);
           }
 #pragma unroll
           for (int ky = 0; ky < 3; ++ky) {
             const float wxy = wx * w[1][ky];
-            float u2[D], ua2[D];
-#pragma unroll
-            for (int a = 0; a < D; ++a) u2[a] = u[a] + Mv[a * D + 1] * float(ky);
+            const float kyf = float(ky);
+            const float2 v01 = __ffma2_rn(make_float2(Mv[1], Mv[4]), make_float2(kyf, kyf), u01);
+            const float v2 = fmaf(Mv[7], kyf, u2s);
+            float2 r01 = make_float2(0.0f, 0.0f);
+            float r2 = 0.0f;
             if constexpr (ADJ) {
-#pragma unroll
-              for (int a = 0; a < D; ++a) ua2[a] = ua[a] + rec[K::RF + D + a * D + 1] * float(ky);
+              const float* Ma = rec + K::RF + D;
+              r01 = __ffma2_rn(make_float2(Ma[1], Ma[4]), make_float2(kyf, kyf), q01);
+              r2 = fmaf(Ma[7], kyf, q2s);
             }
 #pragma unroll
             for (int kz = 0; kz < 3; ++kz) {
-              const float N = wxy * w[D == 3 ? 2 : 0][kz];
+              const float N = wxy * w[2][kz];
+              const float kzf = float(kz);
               const int k = ky * 3 + kz;
-#pragma unroll
-              for (int a = 0; a < D; ++a) acc[j][k][a] += N * (u2[a] + Mv[a * D + D - 1] * float(kz));
-              acc[j][k][D] += N * mass;
+              const float2 NN = make_float2(N, N);
+              const float2 t01 = __ffma2_rn(make_float2(Mv[2], Mv[5]), make_float2(kzf, kzf), v01);
+              const float t2 = fmaf(Mv[8], kzf, v2);
+              aP01[k] = __ffma2_rn(NN, t01, aP01[k]);
+              aP2m[k] = __ffma2_rn(NN, make_float2(t2, mass), aP2m[k]);
               if constexpr (ADJ) {
-#pragma unroll
-                for (int a = 0; a < D; ++a)
-                  acc[j][k][K::CHF + a] += N * (ua2[a] + rec[K::RF + D + a * D + D - 1] * float(kz));
+                const float* Ma = rec + K::RF + D;
+                const float2 s01 = __ffma2_rn(make_float2(Ma[2], Ma[5]), make_float2(kzf, kzf), r01);
+                const float s2 = fmaf(Ma[8], kzf, r2);
+                aQ01[k] = __ffma2_rn(NN, s01, aQ01[k]);
+                aQ2[k] = fmaf(N, s2, aQ2[k]);
               }
             }
           }
         }
       }
+    };
+
+    // Exclusive starts of cells lane and lane + 32 from the counts in cfill, formed by every warp
+    // that calls it (all 32 lanes); warp 0 also writes them, and the total, to cstart.
+    auto warp_scan_cells = [&](int& e0, int& e1) {
+      const int lane = tid & 31;
+      const int v0 = lane < CELLS ? cfill[lane] : 0, v1 = lane + 32 < CELLS ? cfill[lane + 32] : 0;
+      int i0 = v0, i1 = v1;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int a0 = __shfl_up_sync(0xffffffffu, i0, o), a1 = __shfl_up_sync(0xffffffffu, i1, o);
+        if (lane >= o) {
+          i0 += a0;
+          i1 += a1;
+        }
+      }
+      const int tot0 = __shfl_sync(0xffffffffu, i0, 31);
+      e0 = i0 - v0;
+      e1 = tot0 + i1 - v1;
+      if (tid < 32) {
+        if (lane < CELLS) cstart[lane] = e0;
+        if (lane + 32 < CELLS) cstart[lane + 32] = e1;
+        if (lane == 31) cstart[CELLS] = tot0 + (CELLS > 32 ? i1 : 0);
+      }
+    };
+    // start of cell c from the lane-held starts of warp_scan_cells (all 32 lanes call it)
+    auto cell_start_of = [&](int e0, int e1, int c) {
+      const int lo = __shfl_sync(0xffffffffu, e0, c & 31), hi = __shfl_sync(0xffffffffu, e1, c & 31);
+      return c < 32 ? lo : hi;
     };
 
     // scan of the per-cell counts in cfill into cstart (one warp; CELLS <= 64)
@@ -811,7 +865,6 @@ __global__ void __launch_bounds__(T, T == 256 ? (D == 3 && !ADJ ? 3 : 2) : 4) k_
       // Its first particle's state is requested at once and arrives while the tile is being
       // bucketed; its canonical position is the cell start plus the number of smaller ids in its
       // cell (order: cell, then particle id), and its record is written straight there.
-      if (tid < CELLS) cfill[tid] = 0;
       const uint32_t r0 = tid < cnt ? b.sorted[st + tid] : 0xffffffffu;
       const uint32_t r1 = tid + K::THREADS < cnt ? b.sorted[st + tid + K::THREADS] : 0xffffffffu;
       float pre[Cfg<D>::S];
@@ -821,16 +874,20 @@ __global__ void __launch_bounds__(T, T == 256 ? (D == 3 && !ADJ ? 3 : 2) : 4) k_
         g0 = group_of(sp, int(r0 & 0x3ffffffu));
       }
       if (r1 != 0xffffffffu) g1 = group_of(sp, int(r1 & 0x3ffffffu));
+      // the counting atomics also give each entry its place among its cell's entries
+      const int k0 = r0 != 0xffffffffu ? atomicAdd(&cfill[r0 >> 26], 1) : 0;
+      const int k1 = r1 != 0xffffffffu ? atomicAdd(&cfill[r1 >> 26], 1) : 0;
       __syncthreads();
-      if (r0 != 0xffffffffu) atomicAdd(&cfill[r0 >> 26], 1);
-      if (r1 != 0xffffffffu) atomicAdd(&cfill[r1 >> 26], 1);
-      __syncthreads();
-      scan_cells();
-      __syncthreads();
-      if (tid < CELLS) cfill[tid] = 0;
-      __syncthreads();
-      if (r0 != 0xffffffffu) ids[cstart[r0 >> 26] + atomicAdd(&cfill[r0 >> 26], 1)] = r0 & 0x3ffffffu;
-      if (r1 != 0xffffffffu) ids[cstart[r1 >> 26] + atomicAdd(&cfill[r1 >> 26], 1)] = r1 & 0x3ffffffu;
+      {
+        // every warp scans the cell counts itself (warp 0 also publishes cstart for the phases
+        // below), so the entries are placed without another barrier
+        int e0, e1;
+        warp_scan_cells(e0, e1);
+        const uint32_t c0 = r0 != 0xffffffffu ? r0 >> 26 : 0u, c1 = r1 != 0xffffffffu ? r1 >> 26 : 0u;
+        const int s0 = cell_start_of(e0, e1, int(c0)), s1 = cell_start_of(e0, e1, int(c1));
+        if (r0 != 0xffffffffu) ids[s0 + k0] = r0 & 0x3ffffffu;
+        if (r1 != 0xffffffffu) ids[s1 + k1] = r1 & 0x3ffffffu;
+      }
       __syncthreads();
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
@@ -914,9 +971,23 @@ __global__ void __launch_bounds__(T, T == 256 ? (D == 3 && !ADJ ? 3 : 2) : 4) k_
       if (!item_thread[j]) continue;
       float* ca = U + size_t(my_cell[j]) * ST * K::CH;
 #pragma unroll
-      for (int k = 0; k < K::NK; ++k)
+      for (int k = 0; k < K::NK; ++k) {
+        float* e = ca + (my_part[j] * K::NK + k) * K::CH;
+        if constexpr (D == 3) {
+          e[0] = aP01[k].x;
+          e[1] = aP01[k].y;
+          e[2] = aP2m[k].x;
+          e[3] = aP2m[k].y;
+          if constexpr (ADJ) {
+            e[4] = aQ01[k].x;
+            e[5] = aQ01[k].y;
+            e[6] = aQ2[k];
+          }
+        } else {
 #pragma unroll
-        for (int c = 0; c < K::CH; ++c) ca[(my_part[j] * K::NK + k) * K::CH + c] = acc[j][k][c];
+          for (int c = 0; c < K::CH; ++c) e[c] = acc[j][k][c];
+        }
+      }
     }
     __syncthreads();
     // ---- phase D: node block = fixed-order sum over the cells whose stencil covers it -----
@@ -974,6 +1045,7 @@ __global__ void __launch_bounds__(T, T == 256 ? (D == 3 && !ADJ ? 3 : 2) : 4) k_
         b.partial_b[size_t(slot) * NB + tid] = oa;
       }
     }
+    if (tid < CELLS) cfill[tid] = 0;  // for the next tile (nothing reads the counts after placement)
     __syncthreads();
   }
   if (dyn) release_work(b, 0);
@@ -1256,10 +1328,20 @@ __global__ void __launch_bounds__(T, 768 / T) k_g2p(BatchDev b) {
     }
     const int staged = cnt < K::STAGE ? cnt : K::STAGE;
     // request the x, F planes of the tile's particles; they arrive while the node block is built
-    for (int e = tid; e < staged; e += blockDim.x) {
-      const int id = int(b.sorted[st + e] & 0x3ffffffu);
+    // (the thread's list entries are read first, all at once, then the copies are issued)
+    {
+      constexpr int SPT = (K::STAGE + T - 1) / T;
+      uint32_t ent[SPT];
 #pragma unroll
-      for (int j = 0; j < K::NP; ++j) cp_async16(&stage[j][e], sp.planes + size_t(j) * sp.npad + id);
+      for (int u = 0; u < SPT; ++u) ent[u] = tid + u * T < staged ? b.sorted[st + tid + u * T] : 0u;
+#pragma unroll
+      for (int u = 0; u < SPT; ++u) {
+        const int e = tid + u * T;
+        if (e >= staged) break;
+        const int id = int(ent[u] & 0x3ffffffu);
+#pragma unroll
+        for (int j = 0; j < K::NP; ++j) cp_async16(&stage[j][e], sp.planes + size_t(j) * sp.npad + id);
+      }
     }
     cp_async_commit();
     build_node_block<D, TB, false>(b, sp, t, sv, nullptr);
