@@ -562,6 +562,9 @@ struct P2GCfg {
   static constexpr int CHF = D + 1;                        // momentum + mass
   static constexpr int CHA = ADJ ? D : 0;                  // vbar*
   static constexpr int CH = CHF + CHA;
+  // floats per accumulator entry in shared memory: 3D entries are whole float4s (4, or 8 in the
+  // reverse pass), read and summed as float4 in phase D
+  static constexpr int CHS = D == 3 ? (CH + 3) / 4 * 4 : CH;
   static constexpr int PARTS = D == 2 ? 9 : 3;             // work items per cell
   static constexpr int NK = D == 2 ? 1 : 9;                // stencil nodes per work item
   static constexpr int THREADS = T;
@@ -570,7 +573,7 @@ struct P2GCfg {
   static constexpr int REC_CAP = D == 2 ? 1024 : 512;      // records staged at once
   static constexpr int CAP = Tile<D, TB>::SORT_CAP;
   static constexpr size_t REC_BYTES = size_t(REC_CAP) * RW * 4;
-  static constexpr size_t ACC_BYTES = size_t(Tile<D, TB>::CELLS) * Cfg<D>::STENCIL * CH * 4;
+  static constexpr size_t ACC_BYTES = size_t(Tile<D, TB>::CELLS) * Cfg<D>::STENCIL * CHS * 4;
   static constexpr size_t IDS_BYTES = size_t(CAP) * 4;
   static constexpr size_t U1 = REC_BYTES > ACC_BYTES ? REC_BYTES : ACC_BYTES;
   static constexpr size_t U_BYTES = U1 > IDS_BYTES ? U1 : IDS_BYTES;
@@ -969,20 +972,14 @@ __global__ void __launch_bounds__(T, T == 256 ? (D == 3 && !ADJ ? 3 : 2) : 4) k_
 #pragma unroll
     for (int j = 0; j < K::IPT; ++j) {
       if (!item_thread[j]) continue;
-      float* ca = U + size_t(my_cell[j]) * ST * K::CH;
+      float* ca = U + size_t(my_cell[j]) * ST * K::CHS;
 #pragma unroll
       for (int k = 0; k < K::NK; ++k) {
-        float* e = ca + (my_part[j] * K::NK + k) * K::CH;
+        float* e = ca + (my_part[j] * K::NK + k) * K::CHS;
         if constexpr (D == 3) {
-          e[0] = aP01[k].x;
-          e[1] = aP01[k].y;
-          e[2] = aP2m[k].x;
-          e[3] = aP2m[k].y;
-          if constexpr (ADJ) {
-            e[4] = aQ01[k].x;
-            e[5] = aQ01[k].y;
-            e[6] = aQ2[k];
-          }
+          float4* e4 = reinterpret_cast<float4*>(e);
+          e4[0] = make_float4(aP01[k].x, aP01[k].y, aP2m[k].x, aP2m[k].y);
+          if constexpr (ADJ) e4[1] = make_float4(aQ01[k].x, aQ01[k].y, aQ2[k], 0.0f);
         } else {
 #pragma unroll
           for (int c = 0; c < K::CH; ++c) e[c] = acc[j][k][c];
@@ -1004,6 +1001,8 @@ __global__ void __launch_bounds__(T, T == 256 ? (D == 3 && !ADJ ? 3 : 2) : 4) k_
       float s[K::CH];
 #pragma unroll
       for (int c = 0; c < K::CH; ++c) s[c] = 0.0f;
+      float2 s01 = make_float2(0.0f, 0.0f), s23 = s01, s45 = s01;  // 3D
+      float s6 = 0.0f;
 #pragma unroll
       for (int kx = 0; kx < 3; ++kx) {
         const int cx = nl[0] - kx;
@@ -1023,9 +1022,16 @@ __global__ void __launch_bounds__(T, T == 256 ? (D == 3 && !ADJ ? 3 : 2) : 4) k_
               const int cz = nl[2] - kz;
               if (cz < 0 || cz >= B) continue;
               const int cell = (cx * B + cy) * B + cz;
-              const float* ca = U + (size_t(cell) * ST + kx * 9 + ky * 3 + kz) * K::CH;
-#pragma unroll
-              for (int c = 0; c < K::CH; ++c) s[c] += ca[c];
+              const float4* ca = reinterpret_cast<const float4*>(U + (size_t(cell) * ST + kx * 9 + ky * 3 + kz) * K::CHS);
+              // the same per-channel sums in the same order, two channels per packed add
+              const float4 e = ca[0];
+              s01 = __fadd2_rn(s01, make_float2(e.x, e.y));
+              s23 = __fadd2_rn(s23, make_float2(e.z, e.w));
+              if constexpr (ADJ) {
+                const float4 e2 = ca[1];
+                s45 = __fadd2_rn(s45, make_float2(e2.x, e2.y));
+                s6 += e2.z;
+              }
             }
           }
         }
@@ -1034,14 +1040,14 @@ __global__ void __launch_bounds__(T, T == 256 ? (D == 3 && !ADJ ? 3 : 2) : 4) k_
       if constexpr (D == 2)
         o = make_float4(s[0], s[1], s[2], 0.0f);
       else
-        o = make_float4(s[0], s[1], s[2], s[3]);
+        o = make_float4(s01.x, s01.y, s23.x, s23.y);
       b.partial[size_t(slot) * NB + tid] = o;
       if constexpr (ADJ) {
         float4 oa;
         if constexpr (D == 2)
           oa = make_float4(s[K::CHF], s[K::CHF + 1], 0.0f, 0.0f);
         else
-          oa = make_float4(s[K::CHF], s[K::CHF + 1], s[K::CHF + 2], 0.0f);
+          oa = make_float4(s45.x, s45.y, s6, 0.0f);
         b.partial_b[size_t(slot) * NB + tid] = oa;
       }
     }
@@ -1454,6 +1460,126 @@ __device__ __forceinline__ float adj_core(Part<D>& q, Part<D>& g1, const float* 
   // by the y (and z) node offset; Rv/Rp = running totals of sv/spb at each x-slab end, from which the
   // x-offset-weighted sums follow (sum kx S_kx = 3 S - R for kx = 0, 1, 2)
   float gxs[D], sv[D], spb[D], Tv[D][D - 1], Tp[D][D - 1], Rv[D], Rp[D], smb = 0.0f;  // smb = sum N mbar
+  if constexpr (D == 3) {
+    // the x and y components of every 3-vector in pairs for the packed FP32 operations (each half
+    // rounds as its own fmaf / fmul / fadd), the z component alone: the same operations in the same
+    // order as the loop below
+    float2 A01[3], B01[3];
+    float A2[3], B2[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      A01[c] = make_float2(Ac[c][0], Ac[c][1]);
+      A2[c] = Ac[c][2];
+      B01[c] = make_float2(Bc[c][0], Bc[c][1]);
+      B2[c] = Bc[c][2];
+    }
+    float2 al01 = make_float2(al[0], al[1]), be01 = make_float2(be[0], be[1]);
+    float al2 = al[2], be2 = be[2];
+    const float2 z2 = make_float2(0.0f, 0.0f);
+    float2 gx01 = z2, sv01 = z2, sp01 = z2, tvy01 = z2, tvz01 = z2, tpy01 = z2, tpz01 = z2, rv01 = z2, rp01 = z2;
+    float gx2 = 0.0f, sv2 = 0.0f, sp2 = 0.0f, tvy2 = 0.0f, tvz2 = 0.0f, tpy2 = 0.0f, tpz2 = 0.0f, rv2 = 0.0f,
+          rp2 = 0.0f;
+#pragma unroll 1
+    for (int kx = 0; kx < 3; ++kx) {
+      const float wx = kx == 0 ? w[0][0] : (kx == 1 ? w[0][1] : w[0][2]);
+      const float dwx = kx == 0 ? dw[0][0] : (kx == 1 ? dw[0][1] : dw[0][2]);
+#pragma unroll
+      for (int ky = 0; ky < 3; ++ky) {
+        const float wxy = wx * w[1][ky], dwxy = dwx * w[1][ky], wxdy = wx * dw[1][ky];
+        const float kyf = float(ky);
+        const float2 ky2 = make_float2(kyf, kyf);
+        float2 ar01 = al01, br01 = be01;
+        float ar2 = al2, br2 = be2;
+        if (ky > 0) {
+          ar01 = __ffma2_rn(ky2, A01[1], al01);
+          ar2 = fmaf(kyf, A2[1], al2);
+          br01 = __ffma2_rn(ky2, B01[1], be01);
+          br2 = fmaf(kyf, B2[1], be2);
+        }
+#pragma unroll
+        for (int kz = 0; kz < 3; ++kz) {
+          const float wz = w[2][kz];
+          const float N = wxy * wz;
+          const float2 dN01 = __fmul2_rn(make_float2(dwxy, wxdy), make_float2(wz, wz));
+          const float dN2 = wxy * dw[2][kz];
+          const float kzf = float(kz);
+          const float2 kz2 = make_float2(kzf, kzf);
+          float2 alpha01 = ar01, beta01 = br01;
+          float alpha2 = ar2, beta2 = br2;
+          if (kz > 0) {
+            alpha01 = __ffma2_rn(kz2, A01[2], ar01);
+            alpha2 = fmaf(kzf, A2[2], ar2);
+            beta01 = __ffma2_rn(kz2, B01[2], br01);
+            beta2 = fmaf(kzf, B2[2], br2);
+          }
+          float4 v4, p4;
+          fetch(kx, ky, kz, v4, p4);
+          const float mb = p4.w;
+          float si = mass * mb;
+          if constexpr (MAT) smb += N * mb;
+          si += v4.x * alpha01.x + p4.x * beta01.x;
+          si += v4.y * alpha01.y + p4.y * beta01.y;
+          si += v4.z * alpha2 + p4.z * beta2;
+          gx01 = __ffma2_rn(dN01, make_float2(si, si), gx01);
+          gx2 = fmaf(dN2, si, gx2);
+          const float2 NN = make_float2(N, N);
+          const float2 qv01 = __fmul2_rn(NN, make_float2(v4.x, v4.y)), qp01 = __fmul2_rn(NN, make_float2(p4.x, p4.y));
+          const float qv2 = N * v4.z, qp2 = N * p4.z;
+          sv01 = __fadd2_rn(sv01, qv01);
+          sv2 += qv2;
+          sp01 = __fadd2_rn(sp01, qp01);
+          sp2 += qp2;
+          if (ky > 0) {
+            tvy01 = __ffma2_rn(ky2, qv01, tvy01);
+            tvy2 = fmaf(kyf, qv2, tvy2);
+            tpy01 = __ffma2_rn(ky2, qp01, tpy01);
+            tpy2 = fmaf(kyf, qp2, tpy2);
+          }
+          if (kz > 0) {
+            tvz01 = __ffma2_rn(kz2, qv01, tvz01);
+            tvz2 = fmaf(kzf, qv2, tvz2);
+            tpz01 = __ffma2_rn(kz2, qp01, tpz01);
+            tpz2 = fmaf(kzf, qp2, tpz2);
+          }
+        }
+      }
+      rv01 = __fadd2_rn(rv01, sv01);
+      rv2 += sv2;
+      rp01 = __fadd2_rn(rp01, sp01);
+      rp2 += sp2;
+      al01 = __fadd2_rn(al01, A01[0]);
+      al2 += A2[0];
+      be01 = __fadd2_rn(be01, B01[0]);
+      be2 += B2[0];
+    }
+    gxs[0] = gx01.x;
+    gxs[1] = gx01.y;
+    gxs[2] = gx2;
+    sv[0] = sv01.x;
+    sv[1] = sv01.y;
+    sv[2] = sv2;
+    spb[0] = sp01.x;
+    spb[1] = sp01.y;
+    spb[2] = sp2;
+    Tv[0][0] = tvy01.x;
+    Tv[1][0] = tvy01.y;
+    Tv[2][0] = tvy2;
+    Tv[0][D - 2] = tvz01.x;
+    Tv[1][D - 2] = tvz01.y;
+    Tv[2][D - 2] = tvz2;
+    Tp[0][0] = tpy01.x;
+    Tp[1][0] = tpy01.y;
+    Tp[2][0] = tpy2;
+    Tp[0][D - 2] = tpz01.x;
+    Tp[1][D - 2] = tpz01.y;
+    Tp[2][D - 2] = tpz2;
+    Rv[0] = rv01.x;
+    Rv[1] = rv01.y;
+    Rv[2] = rv2;
+    Rp[0] = rp01.x;
+    Rp[1] = rp01.y;
+    Rp[2] = rp2;
+  } else {
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     gxs[a] = sv[a] = spb[a] = Rv[a] = Rp[a] = 0.0f;
@@ -1533,6 +1659,7 @@ __device__ __forceinline__ float adj_core(Part<D>& q, Part<D>& g1, const float* 
       al[a] += Ac[0][a];
       be[a] += Bc[0][a];
     }
+  }
   }
   // the epilogue's inputs read again (same bits): not kept in registers through the stencil loop
   reload(q, g1);
