@@ -532,10 +532,16 @@ def measure_replicas(args, dev, stream, sizes=(1, 64, 1024, 4096), edges=(8, 4))
             best = float(np.median(ms))
             out[str(B)] = {"value": B * N * T / (best / 1e3), "ms": best}
         by_edge[str(edge)] = out
+    # the tile-edge autotuner on one such scene and on the 2D walker: each edge's pass of 64
+    # forward steps and their reverse pass, after two untimed ones
+    tuned = {}
+    for tspec in (base, workload("walker_2d")):
+        e, ms4, ms8 = mpm.tune_tile_edge(ctx, tspec, steps=64)
+        tuned[tspec.name] = {"edge": e, "ms_per_step_4x4": ms4, "ms_per_step_8x8": ms8}
     ctx.close()
     return {"workload": spec.name, "particles_per_replica": N, "sim_steps": T, "unit": UNIT,
             "pass": "forward+reverse per replica, one batch", "tile_edge_chosen": edges[0],
-            "by_replicas": by_edge[str(edges[0])], "by_tile_edge": by_edge}
+            "by_replicas": by_edge[str(edges[0])], "by_tile_edge": by_edge, "tile_edge_tuning": tuned}
 
 
 def measure_budget_sweep(args, dev, stream, budgets_gib=(32, 4, 1)):

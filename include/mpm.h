@@ -116,8 +116,9 @@ typedef struct {
   int mem_space;       /* where every pointer of this descriptor lives */
   int tile_edge;       /* cells per tile edge of the tiled form: 4; 8 (2D only: sparse scenes, a tile
                           then holds the particles of four 4 x 4 tiles); 0 = chosen at creation
-                          (8 x 8 for a 2D scene averaging under 96 particles per occupied 4 x 4
-                          tile, else 4 x 4) */
+                          (2D: the edge mpm_tune_tile_edge cached for the workload, else 8 x 8 for
+                          a scene averaging under 96 particles per occupied 4 x 4 tile, else
+                          4 x 4) */
 } mpm_scene_desc;
 
 /* Creates a scene (Section III state: x, v, C, F per particle; grid per desc) at step 0.  Copies
@@ -352,6 +353,20 @@ mpm_status mpm_tune_cache_lookup(int dim, long long particles, long long grid_ti
 mpm_status mpm_tune_cache_store(int dim, long long particles, long long grid_tiles, int sm_count, const int* shape);
 mpm_status mpm_tune_cache_save(const char* path);
 mpm_status mpm_tune_cache_load(const char* path);
+/* Tile-edge autotuning (particles per tile; no counterpart in the paper).  For a 2D tiled scene
+ * described by `desc` it creates the scene with 4 x 4-cell and with 8 x 8-cell tiles in turn, runs
+ * each through two untimed and one timed pass of `steps` forward steps (every state kept) and
+ * their reverse pass, destroys it, and returns the edge whose pass took less GPU time in *edge and
+ * the two passes' milliseconds per step in ms[0] (4 x 4) and ms[1] (8 x 8) (ms may be NULL).  The
+ * choice goes into the process-wide cache under the workload's key (dimension, log2 buckets of its
+ * particle and grid-node counts, SM count; saved with the launch shapes, as lines
+ * "edge dim log2_particles log2_nodes sms tile_edge"), and mpm_scene_create with tile_edge = 0 takes
+ * the cached edge for that key before the density rule.  3D scenes and the plain form have one
+ * tile shape: *edge = 4 and nothing runs.  The descriptor's pointers are read as for
+ * mpm_scene_create; the context stream is used and synchronised.  Errors: MPM_ERR_ARG for a NULL
+ * argument, steps < 1 or a descriptor mpm_scene_create refuses; whatever creating, stepping or
+ * reversing the trial scenes returns (the cache is then unchanged). */
+mpm_status mpm_tune_tile_edge(mpm_ctx* ctx, const mpm_scene_desc* desc, int steps, int* edge, float* ms);
 
 /* Allocation-free forward step (no counterpart in the paper; an addition for callers that must
  * not allocate device memory: a control loop with a hard latency budget, where cudaMalloc may

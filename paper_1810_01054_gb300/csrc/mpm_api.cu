@@ -77,7 +77,15 @@ int block_nodes(int dim, int edge) {
 // Tile edge of a new scene: the descriptor's, or (0) 8 for a 2D tiled scene whose particles
 // average under 96 per occupied 4 x 4 tile (sparse scenes: fewer, fuller tiles), else 4.
 constexpr int kWideTileMean = 96;
-mpm_status choose_tile_edge(const mpm_scene_desc* d, int dim, int* edge) {
+long long grid_nodes_of(const mpm_scene_desc* d, int dim) {
+  long long n = 1;
+  for (int a = 0; a < dim; ++a) n *= d->n_grid[a];
+  return n;
+}
+
+// Tile edge of a new scene: the descriptor's; else, for a 2D tiled scene, the one
+// mpm_tune_tile_edge measured fastest for its workload key; else the density rule.
+mpm_status choose_tile_edge(const mpm_scene_desc* d, int dim, int sm_count, int* edge) {
   if (d->tile_edge != 0) {
     if (d->tile_edge != 4 && !(d->tile_edge == 8 && dim == 2)) return MPM_ERR_ARG;
     *edge = d->tile_edge;
@@ -86,6 +94,7 @@ mpm_status choose_tile_edge(const mpm_scene_desc* d, int dim, int* edge) {
   *edge = 4;
   const int N = d->n_particles;
   if (dim != 2 || d->impl != MPM_IMPL_TILED || N == 0) return MPM_OK;
+  if (tune_edge_lookup(dim, N, grid_nodes_of(d, dim), sm_count, edge)) return MPM_OK;
   std::vector<float> hx(size_t(N) * 2);
   CK(cudaMemcpy(hx.data(), d->x0, sizeof(float) * hx.size(),
                 d->mem_space == 1 ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
@@ -1461,7 +1470,7 @@ mpm_status mpm_scene_create(mpm_ctx* c, const mpm_scene_desc* d, mpm_scene** out
   CK(cudaSetDevice(c->device));
   int edge = 4;
   {
-    const mpm_status est = choose_tile_edge(d, dim, &edge);
+    const mpm_status est = choose_tile_edge(d, dim, c->sm_count, &edge);
     if (est != MPM_OK) return est;
   }
   mpm_scene* s = new (std::nothrow) mpm_scene();
@@ -1798,6 +1807,55 @@ mpm_status mpm_plan_checkpoints(int T, long long budget_states, long long* forwa
   if (forward_steps) *forward_steps = fwd;
   if (states_used) *states_used = used;
   if (multi_level) *multi_level = multi;
+  return MPM_OK;
+}
+
+mpm_status mpm_tune_tile_edge(mpm_ctx* c, const mpm_scene_desc* d, int steps, int* edge, float* ms) {
+  if (!c || !d || !edge || steps < 1) return MPM_ERR_ARG;
+  const int dim = d->dim;
+  if (dim != 2 && dim != 3) return MPM_ERR_ARG;
+  if (ms) ms[0] = ms[1] = 0.0f;
+  *edge = 4;
+  if (dim != 2 || d->impl != MPM_IMPL_TILED || d->n_particles == 0) return MPM_OK;  // one candidate
+  CK(cudaSetDevice(c->device));
+  const int edges[2] = {4, 8};
+  float t[2] = {0.0f, 0.0f};
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  mpm_status st = MPM_OK;
+  for (int i = 0; i < 2 && st == MPM_OK; ++i)
+    if (cudaEventCreate(&ev[i]) != cudaSuccess) st = MPM_ERR_CUDA;
+  for (int i = 0; i < 2 && st == MPM_OK; ++i) {
+    mpm_scene_desc de = *d;
+    de.tile_edge = edges[i];
+    mpm_scene* s = nullptr;
+    st = mpm_scene_create(c, &de, &s);
+    if (st != MPM_OK) break;
+    // two untimed passes (the launch-shape trials finish and the step graphs are captured), then
+    // one timed pass: `steps` forward steps keeping every state, and their reverse pass
+    for (int pass = 0; pass < 3 && st == MPM_OK; ++pass) {
+      st = mpm_set_state(s, d->x0, d->v0, d->C0, d->F0, 0, d->mem_space);
+      if (st == MPM_OK && pass == 2 && cudaEventRecord(ev[0], c->stream) != cudaSuccess) st = MPM_ERR_CUDA;
+      if (st == MPM_OK) st = mpm_rollout(s, steps, 1, 0);
+      if (st == MPM_OK)
+        st = mpm_backward(s, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0);
+      if (st == MPM_OK && pass == 2) {
+        if (cudaEventRecord(ev[1], c->stream) != cudaSuccess || cudaEventSynchronize(ev[1]) != cudaSuccess ||
+            cudaEventElapsedTime(&t[i], ev[0], ev[1]) != cudaSuccess)
+          st = MPM_ERR_CUDA;
+      }
+    }
+    const mpm_status ds = mpm_scene_destroy(s);
+    if (st == MPM_OK) st = ds;
+  }
+  for (cudaEvent_t e : ev)
+    if (e) cudaEventDestroy(e);
+  if (st != MPM_OK) return st;
+  *edge = t[1] < t[0] ? 8 : 4;
+  if (ms) {
+    ms[0] = t[0] / float(steps);
+    ms[1] = t[1] / float(steps);
+  }
+  tune_edge_store(dim, d->n_particles, grid_nodes_of(d, dim), c->sm_count, *edge);
   return MPM_OK;
 }
 

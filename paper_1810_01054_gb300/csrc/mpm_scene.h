@@ -237,6 +237,10 @@ void tune_release(mpm_scene* s);
 bool tune_wants(const mpm_scene* s, int ph);
 // One directly-launched step of phase ph with the candidate shapes under trial, timed.
 mpm_status tune_step(mpm_scene* s, int ph);
+// Tile edge that mpm_tune_tile_edge chose for a workload (dim, particles, grid nodes, SMs), and
+// storing one (rewrites the cache file named by GBMPM_TUNE_CACHE, if any).
+bool tune_edge_lookup(int dim, long long particles, long long nodes, int sms, int* edge);
+void tune_edge_store(int dim, long long particles, long long nodes, int sms, int edge);
 // Batches (mpm_batch.cu): a sub-batch composition's shapes come from the cache; on a miss the
 // kernels it runs are tried the way a scene's are, during its ordinary steps.
 //  batch_tune_init   cache shapes of the composition's key, or trials armed for `kernels` (mask)

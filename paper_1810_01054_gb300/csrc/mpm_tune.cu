@@ -1,5 +1,6 @@
 // Launch-shape autotuner of the tile kernels: candidate tables, the process-wide cache (with its
-// optional text file), per-scene trials, and the C-ABI entry points.
+// optional text file), per-scene trials, and the C-ABI entry points; the cache also keeps the tile
+// edge that mpm_tune_tile_edge measured fastest for a 2D workload.
 //
 // A trial step is an ordinary simulation step: the tile kernels process every tile whole inside
 // one CTA, so neither the number of CTAs nor (for G2P, whose outputs are per particle) the CTA
@@ -83,6 +84,8 @@ std::map<Key, Entry> g_cache;
 // (absent: every kernel of the entry is tuned)
 std::map<Key, unsigned> g_partial;
 bool g_env_loaded = false;
+// tile edge per workload key (dim, log2 particles, log2 grid nodes, SMs), from mpm_tune_tile_edge
+std::map<Key, int> g_edge;
 
 Key make_key(int dim, long long particles, long long tiles, int sms) {
   return Key(dim, log2_bucket(particles < 1 ? 1 : particles), log2_bucket(tiles < 1 ? 1 : tiles), sms);
@@ -99,11 +102,25 @@ mpm_status load_locked(const char* path) {
     return MPM_ERR_ARG;
   }
   std::map<Key, Entry> add;
+  std::map<Key, int> add_edge;
   char line[512];
   bool bad = false;
   while (!bad && std::fgets(line, sizeof(line), f)) {
     int v[4 + 2 * TK_COUNT], used = 0, n = 0;
     const char* q = line;
+    if (std::string(line).rfind("edge ", 0) == 0) {  // edge dim log2_particles log2_nodes sms tile_edge
+      int e[5], u = 0, m = 0;
+      q = line + 5;
+      while (m < 5 && std::sscanf(q, "%d%n", &e[m], &u) == 1) {
+        q += u;
+        ++m;
+      }
+      for (const char* c = q; *c; ++c) bad = bad || !(*c == ' ' || *c == '\t' || *c == '\n' || *c == '\r');
+      bad = bad || m != 5 || !(e[0] == 2 || e[0] == 3) || e[1] < 0 || e[2] < 0 || e[3] < 1 ||
+            !(e[4] == 4 || (e[4] == 8 && e[0] == 2));
+      if (!bad) add_edge[Key(e[0], e[1], e[2], e[3])] = e[4];
+      continue;
+    }
     while (n < 4 + 2 * TK_COUNT && std::sscanf(q, "%d%n", &v[n], &used) == 1) {
       q += used;
       ++n;
@@ -127,6 +144,7 @@ mpm_status load_locked(const char* path) {
   }
   std::fclose(f);
   for (auto& kv : add) g_cache[kv.first] = kv.second;
+  for (auto& kv : add_edge) g_edge[kv.first] = kv.second;
   return MPM_OK;
 }
 
@@ -144,6 +162,9 @@ mpm_status save_locked(const char* path) {
     for (int k = 0; k < TK_COUNT; ++k) std::fprintf(f, " %d %d", kv.second.l[k].ctas_per_sm, kv.second.l[k].threads);
     std::fprintf(f, "\n");
   }
+  for (auto& kv : g_edge)
+    std::fprintf(f, "edge %d %d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
+                 std::get<3>(kv.first), kv.second);
   const bool ok = std::fclose(f) == 0;
   if (!ok || std::rename(tmp.c_str(), path) != 0) return MPM_ERR_ARG;
   return MPM_OK;
@@ -176,6 +197,27 @@ void store(const Key& key, const Entry& e) {
 }
 
 Key scene_key(const mpm_scene* s) { return make_key(s->dim, s->N, s->hp.n_tiles, s->ctx->sm_count); }
+
+}  // namespace
+
+bool tune_edge_lookup(int dim, long long particles, long long nodes, int sms, int* edge) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  env_load_locked();
+  auto it = g_edge.find(make_key(dim, particles, nodes, sms));
+  if (it == g_edge.end()) return false;
+  *edge = it->second;
+  return true;
+}
+
+void tune_edge_store(int dim, long long particles, long long nodes, int sms, int edge) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  env_load_locked();
+  g_edge[make_key(dim, particles, nodes, sms)] = edge;
+  const char* p = std::getenv("GBMPM_TUNE_CACHE");
+  if (p && *p) save_locked(p);
+}
+
+namespace {
 
 bool phase_runs(int ph, int k) {
   if (ph == PH_REV) return k == TK_P2G_ADJ || k == TK_ADJ_GATHER;

@@ -168,6 +168,7 @@ _SIGS = {
     "mpm_tune_cache_store": [C.c_int, C.c_longlong, C.c_longlong, C.c_int, C.POINTER(C.c_int)],
     "mpm_tune_cache_save": [C.c_char_p],
     "mpm_tune_cache_load": [C.c_char_p],
+    "mpm_tune_tile_edge": [C.c_void_p, C.POINTER(SceneDesc), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)],
     "mpm64_create": [C.c_void_p, C.POINTER(SceneDesc64), C.POINTER(C.c_void_p)],
     "mpm64_destroy": [C.c_void_p],
     "mpm64_set_state": [C.c_void_p] + [C.c_void_p] * 4,
@@ -214,6 +215,19 @@ def tune_cache_store(dim: int, particles: int, grid_tiles: int, sm_count: int, s
     flat = (C.c_int * 8)(*[int(v) for sh in shapes for v in sh])
     _check(lib().mpm_tune_cache_store(int(dim), int(particles), int(grid_tiles), int(sm_count), flat),
            "mpm_tune_cache_store")
+
+
+def tune_tile_edge(ctx, spec, steps: int = 64):
+    """Times ``steps`` forward steps and their reverse pass of ``spec`` with 4 x 4- and with
+    8 x 8-cell tiles (2D tiled scenes; 3D has one tile shape) and caches the faster edge for the
+    workload, which scenes created afterwards with tile_edge 0 take.  Returns (edge, ms per step
+    with 4 x 4, ms per step with 8 x 8); the times are 0 where nothing ran."""
+    desc, keep, _, _ = _scene_desc(spec)
+    edge = C.c_int()
+    ms = (C.c_float * 2)()
+    _check(lib().mpm_tune_tile_edge(ctx.handle, C.byref(desc), int(steps), C.byref(edge), ms), "mpm_tune_tile_edge")
+    del keep
+    return int(edge.value), float(ms[0]), float(ms[1])
 
 
 def tune_cache_save(path: str):
@@ -323,6 +337,65 @@ class Context:
             pass
 
 
+def _scene_desc(spec, impl=None, params=None):
+    """SceneDesc of ``spec`` with the arrays it points to (kept alive by the caller), the controller
+    parameter count and the number of actuation groups."""
+    impl = IMPL_TILED if impl is None else impl
+    d = int(spec.dim)
+    N = int(np.asarray(spec.x0).shape[0]) if not _is_torch(spec.x0) else int(spec.x0.shape[0])
+    G = int(np.asarray(spec.act_dir).shape[0])
+    keep = []
+    dev = _is_torch(spec.x0) and spec.x0.is_cuda
+
+    def arr(a, shape):
+        t = _f32(a, shape)
+        keep.append(t)
+        return t
+
+    desc = SceneDesc()
+    desc.dim = d
+    ng = list(spec.n_grid) + [1] * (3 - len(spec.n_grid))
+    for a in range(3):
+        desc.n_grid[a] = int(ng[a])
+    desc.dx, desc.dt = float(spec.dx), float(spec.dt)
+    g = list(spec.gravity) + [0.0] * (3 - len(spec.gravity))
+    for a in range(3):
+        desc.gravity[a] = float(g[a])
+    desc.E, desc.nu = float(spec.E), float(spec.nu)
+    desc.p_mass, desc.p_vol = float(spec.p_mass), float(spec.p_vol)
+    desc.bc_type, desc.bc_width, desc.friction_c = int(spec.bc_type), int(spec.bc_width), float(spec.friction_c)
+    desc.n_particles = N
+    desc.x0 = _ptr(arr(spec.x0, (N, d)))
+    desc.v0 = _ptr(arr(spec.v0, (N, d))) if spec.v0 is not None else None
+    desc.C0 = _ptr(arr(spec.C0, (N, d, d))) if spec.C0 is not None else None
+    desc.F0 = _ptr(arr(spec.F0, (N, d, d))) if spec.F0 is not None else None
+    if dev:
+        import torch
+        grp = torch.as_tensor(spec.group, dtype=torch.int32, device=spec.x0.device).contiguous()
+        params_t = torch.as_tensor(spec.ctrl_params if params is None else params, dtype=torch.float32,
+                                   device=spec.x0.device).contiguous()
+        dirs = torch.as_tensor(spec.act_dir, dtype=torch.float32, device=spec.x0.device).contiguous()
+    else:
+        grp = np.ascontiguousarray(np.asarray(spec.group, dtype=np.int32))
+        params_t = np.ascontiguousarray(np.asarray(spec.ctrl_params if params is None else params,
+                                                   dtype=np.float32).ravel())
+        dirs = np.ascontiguousarray(np.asarray(spec.act_dir, dtype=np.float32).reshape(G, d) if G else
+                                    np.zeros((1, d), np.float32))
+    keep += [grp, params_t, dirs]
+    desc.group = _ptr(grp)
+    desc.n_groups = G
+    desc.act_dir = _ptr(dirs)
+    desc.ctrl_type, desc.ctrl_hidden = int(spec.ctrl_type), int(spec.ctrl_hidden)
+    desc.ctrl_freq, desc.ctrl_scale = float(spec.ctrl_freq), float(spec.ctrl_scale)
+    n_params = int(params_t.numel() if _is_torch(params_t) else params_t.size)
+    desc.n_ctrl_params = n_params
+    desc.ctrl_params = _ptr(params_t)
+    desc.impl = int(impl)
+    desc.mem_space = 1 if dev else 0
+    desc.tile_edge = int(getattr(spec, "tile_edge", 0) or 0)
+    return desc, keep, n_params, G
+
+
 class Scene:
     """One simulation (state, grid, controller) living on the GPU."""
 
@@ -332,56 +405,7 @@ class Scene:
         self.spec = spec
         N = int(np.asarray(spec.x0).shape[0]) if not _is_torch(spec.x0) else int(spec.x0.shape[0])
         self.N = N
-        G = int(np.asarray(spec.act_dir).shape[0])
-        keep = []
-        dev = _is_torch(spec.x0) and spec.x0.is_cuda
-
-        def arr(a, shape):
-            t = _f32(a, shape)
-            keep.append(t)
-            return t
-
-        desc = SceneDesc()
-        desc.dim = d
-        ng = list(spec.n_grid) + [1] * (3 - len(spec.n_grid))
-        for a in range(3):
-            desc.n_grid[a] = int(ng[a])
-        desc.dx, desc.dt = float(spec.dx), float(spec.dt)
-        g = list(spec.gravity) + [0.0] * (3 - len(spec.gravity))
-        for a in range(3):
-            desc.gravity[a] = float(g[a])
-        desc.E, desc.nu = float(spec.E), float(spec.nu)
-        desc.p_mass, desc.p_vol = float(spec.p_mass), float(spec.p_vol)
-        desc.bc_type, desc.bc_width, desc.friction_c = int(spec.bc_type), int(spec.bc_width), float(spec.friction_c)
-        desc.n_particles = N
-        desc.x0 = _ptr(arr(spec.x0, (N, d)))
-        desc.v0 = _ptr(arr(spec.v0, (N, d))) if spec.v0 is not None else None
-        desc.C0 = _ptr(arr(spec.C0, (N, d, d))) if spec.C0 is not None else None
-        desc.F0 = _ptr(arr(spec.F0, (N, d, d))) if spec.F0 is not None else None
-        if dev:
-            import torch
-            grp = torch.as_tensor(spec.group, dtype=torch.int32, device=spec.x0.device).contiguous()
-            params_t = torch.as_tensor(spec.ctrl_params if params is None else params, dtype=torch.float32,
-                                       device=spec.x0.device).contiguous()
-            dirs = torch.as_tensor(spec.act_dir, dtype=torch.float32, device=spec.x0.device).contiguous()
-        else:
-            grp = np.ascontiguousarray(np.asarray(spec.group, dtype=np.int32))
-            params_t = np.ascontiguousarray(np.asarray(spec.ctrl_params if params is None else params,
-                                                       dtype=np.float32).ravel())
-            dirs = np.ascontiguousarray(np.asarray(spec.act_dir, dtype=np.float32).reshape(G, d) if G else
-                                        np.zeros((1, d), np.float32))
-        keep += [grp, params_t, dirs]
-        desc.group = _ptr(grp)
-        desc.n_groups = G
-        desc.act_dir = _ptr(dirs)
-        desc.ctrl_type, desc.ctrl_hidden = int(spec.ctrl_type), int(spec.ctrl_hidden)
-        desc.ctrl_freq, desc.ctrl_scale = float(spec.ctrl_freq), float(spec.ctrl_scale)
-        self.n_params = int(params_t.numel() if _is_torch(params_t) else params_t.size)
-        desc.n_ctrl_params = self.n_params
-        desc.ctrl_params = _ptr(params_t)
-        desc.impl = int(impl)
-        desc.mem_space = 1 if dev else 0
-        desc.tile_edge = int(getattr(spec, "tile_edge", 0) or 0)
+        desc, keep, self.n_params, G = _scene_desc(spec, impl, params)
         h = C.c_void_p()
         _check(lib().mpm_scene_create(ctx.handle, C.byref(desc), C.byref(h)), "mpm_scene_create")
         self.handle = h

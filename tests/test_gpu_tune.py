@@ -131,3 +131,20 @@ def test_dynamic_tile_scheduling_keeps_the_bits(M, ctx):
     for r in res[1:]:
         for a, b in zip(res[0], r):
             assert np.array_equal(a, b)
+
+
+def test_tile_edge_tuning_keeps_the_faster_edge_for_new_scenes(M, ctx):
+    """mpm_tune_tile_edge times a 2D workload with 4 x 4- and with 8 x 8-cell tiles, returns the
+    edge of the shorter pass and caches it: a scene of that workload created afterwards with
+    tile_edge 0 takes it.  A 3D workload has one tile shape (nothing runs).  The workload's key
+    (6,000 particles, 96^2 grid) is one no other test uses, so the cached edge changes no other
+    scene of this process."""
+    spec = S.blob(2, 96, 6000, 41, radius_cells=20.0, v_scale=0.3, amp=2.0)
+    edge, ms4, ms8 = M.tune_tile_edge(ctx, spec, steps=32)
+    print(f"\ntile edge 4: {ms4:.4f} ms/step, 8: {ms8:.4f} ms/step -> {edge}")
+    assert ms4 > 0 and ms8 > 0
+    assert edge == (8 if ms8 < ms4 else 4)
+    sc = M.Scene(ctx, spec)
+    assert sc.tile_edge == edge
+    sc.close()
+    assert M.tune_tile_edge(ctx, S.blob(3, 16, 200, 42, radius_cells=3.0), steps=4) == (4, 0.0, 0.0)

@@ -80,3 +80,30 @@ def test_malformed_files_are_refused_whole(tmp_path, body):
 def test_missing_file_is_an_argument_error(tmp_path):
     with pytest.raises(mpm.MPMError):
         mpm.tune_cache_load(str(tmp_path / "none.txt"))
+
+
+def test_tile_edge_lines_round_trip(tmp_path):
+    """Tile-edge entries (from mpm_tune_tile_edge) are kept in the same file as lines
+    "edge dim log2_particles log2_nodes sms tile_edge" and survive a save and a load."""
+    f = tmp_path / "edge.txt"
+    f.write_text("gbmpm-tune 1\nedge 2 10 14 132 8\nedge 2 14 14 132 4\n")
+    mpm.tune_cache_load(str(f))
+    g = tmp_path / "edge_out.txt"
+    mpm.tune_cache_save(str(g))
+    lines = g.read_text().splitlines()
+    assert "edge 2 10 14 132 8" in lines and "edge 2 14 14 132 4" in lines
+
+
+@pytest.mark.parametrize("line", [
+    "edge 3 10 14 132 8",      # 3D has one tile shape
+    "edge 2 10 14 132 6",      # not an edge
+    "edge 2 10 14 132",        # short
+    "edge 2 10 14 0 4",        # no SMs
+    "edge 2 10 14 132 8 x",    # trailing text
+])
+def test_malformed_tile_edge_lines_are_refused_whole(tmp_path, line):
+    f = tmp_path / "bad_edge.txt"
+    f.write_text("gbmpm-tune 1\n" + line + "\n2 12 7 98 2 256 2 256 2 256 2 256\n")
+    with pytest.raises(mpm.MPMError):
+        mpm.tune_cache_load(str(f))
+    assert mpm.tune_cache_lookup(2, 4096, 128, 98) is None
