@@ -20,7 +20,6 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -98,7 +97,8 @@ def ckpt_of(spec):
 
 
 # Device-memory budget of the checkpoint store per workload (0 = no limit): the 1M-particle cluster
-# keeps its checkpoints within 4 GiB, which sets the interval to ceil(sqrt(200)) = 15 states.
+# keeps its checkpoints within 4 GiB, where the library takes a checkpoint every 8 steps (the
+# smallest whole-graph interval whose store, with the overlapped recompute's, fits).
 BUDGET = {"box_cluster_3d": 4 << 30}
 
 
@@ -337,10 +337,7 @@ def measure(args, spec, rank, world, dev, stream, ctx, *, e2e=True, plain=True):
     T, k, budget = spec.n_steps, ckpt_of(spec), budget_of(spec)
     N, d = spec.n_particles, spec.dim
     scene = mpm.Scene(ctx, spec)
-    S_bytes = scene.info()["state_bytes"]
-    # the interval the library takes: the given one, else every state when they fit the budget,
-    # else ceil(sqrt(T))
-    k_eff = k if k else (1 if budget == 0 or T * S_bytes <= budget else int(math.ceil(math.sqrt(T))))
+    k_eff = scene.plan_rollout(T, k, budget)[0]  # the interval the library takes (0: multi-level)
     x0 = torch.tensor(spec.x0, dtype=torch.float32, device=dev)
     v0 = torch.tensor(spec.v0, dtype=torch.float32, device=dev)
     C0 = torch.tensor(spec.C0, dtype=torch.float32, device=dev)
@@ -546,8 +543,8 @@ def measure_replicas(args, dev, stream, sizes=(1, 64, 1024, 4096), edges=(8, 4))
 
 def measure_budget_sweep(args, dev, stream, budgets_gib=(32, 4, 1)):
     """Full-horizon gradient of the 1M-particle cluster (200 steps) under device-memory budgets for
-    the checkpoint store: every state when they fit (k = 1); else every ceil(sqrt(T))-th state with
-    the segments recomputed (the recompute beside the reverse steps when the budget leaves room);
+    the checkpoint store: every state when they fit (k = 1); else every k-th state with the segments
+    recomputed beside the reverse steps (k the smallest whole-graph interval whose store fits);
     below that the multi-level store (a recursive schedule planned for the fewest recomputed steps).
     Each budget's final state and gradients are compared bit for bit with the first budget's."""
     import torch
@@ -569,11 +566,18 @@ def measure_budget_sweep(args, dev, stream, budgets_gib=(32, 4, 1)):
     res, ref = {}, None
     for gib in budgets_gib:
         budget = gib << 30
-        fwd_steps, stored, multi = mpm.plan_checkpoints(T, budget // S)
+        try:
+            kk, fwd_steps, multi = sc.plan_rollout(T, 0, budget)
+        except mpm.MPMError as e:
+            res[f"{gib}GiB"] = {"status": e.status}
+            continue
+        # states stored at most: the multi-level plan's; the checkpoints and the two sets of recompute
+        # buffers of the overlapped reverse pass
+        stored = mpm.plan_checkpoints(T, budget // S)[1] if multi else (T + kk - 1) // kk + 2 * (kk - 1)
         rec = {"store": "multi-level" if multi else "single-level", "stored_states": stored,
                "store_gb": stored * S / 1e9, "forward_steps": fwd_steps}
         if not multi:
-            rec["ckpt_interval"] = 1 if T * S <= budget else int(np.ceil(np.sqrt(T)))
+            rec["ckpt_interval"] = kk
 
         def one():
             sc.set_state(x0, v0, C0, F0, step=0)

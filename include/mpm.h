@@ -139,8 +139,12 @@ mpm_status mpm_step(mpm_scene* scene, int n_steps);
 /* Rollout for differentiation (Section III "memo"): n_steps steps from the current state,
  * asynchronously; the checkpoint buffers are kept for the next rollout of the same shape.
  * storing the state every ckpt_interval steps (0 = choose from mem_budget_bytes: every step if
- * all states fit, else about sqrt(n_steps)); the states in between are recomputed by
- * mpm_backward.  mem_budget_bytes = 0 means no limit.
+ * all states fit; else, in the tiled form, the smallest multiple of 8 steps (the length of the
+ * reverse pass's step graphs) whose checkpoints, two sets of recompute buffers and the sorts an
+ * overlapped reverse pass keeps all fit, so that the fewest steps are recomputed and the recompute
+ * runs beside the reverse steps; else about sqrt(n_steps); mpm_scene_plan_rollout reports the
+ * choice); the states in between are recomputed by mpm_backward.  mem_budget_bytes = 0 means no
+ * limit.
  * With ckpt_interval = 0 and a budget below that single-level store ((ceil(T/k) + k - 1) states),
  * the rollout keeps a multi-level store instead: a recursive schedule (store a state, reverse the
  * later part, release it, reverse the earlier part) planned for the fewest recomputed steps within
@@ -150,13 +154,23 @@ mpm_status mpm_step(mpm_scene* scene, int n_steps);
  * of a stored step returns MPM_ERR_STATE.  MPM_ERR_OOM when neither store fits the budget. */
 mpm_status mpm_rollout(mpm_scene* scene, int n_steps, int ckpt_interval, size_t mem_budget_bytes);
 
-/* The schedule mpm_rollout(scene, n_steps, 0, budget) takes, for a budget of budget_states whole
- * states (budget / state size; 0 = no limit): forward steps it runs over the rollout and its
- * reverse pass together (n_steps when every state is kept; the reverse steps themselves are
- * n_steps in every schedule), the number of states it stores at most, and whether the multi-level
- * store is used (NULL outputs are skipped).  MPM_ERR_OOM when no schedule fits.  Host only. */
+/* The schedule of a budget counted in whole states only (budget_states = budget / state size; 0 =
+ * no limit): every state when they fit, else the single-level store at about sqrt(n_steps), else
+ * the multi-level store.  Reports the forward steps run over the rollout and its reverse pass
+ * together (n_steps when every state is kept; the reverse steps themselves are n_steps in every
+ * schedule), the number of states stored at most, and whether the multi-level store is used (NULL
+ * outputs are skipped).  MPM_ERR_OOM when no schedule fits.  Host only.  This is the schedule of
+ * mpm_rollout with ckpt_interval 0 for the multi-level store and for the plain form; a tiled
+ * scene's single-level interval also counts the overlap's stores: mpm_scene_plan_rollout. */
 mpm_status mpm_plan_checkpoints(int n_steps, long long budget_states, long long* forward_steps, int* states_used,
                                 int* multi_level);
+/* What mpm_rollout(scene, n_steps, ckpt_interval, mem_budget_bytes) would do: *k_out the interval
+ * of its single-level store (0 with the multi-level store), *forward_steps the forward steps of
+ * the rollout and its reverse pass together, *multi_level 1 for the multi-level store (NULL
+ * outputs are skipped).  MPM_ERR_OOM when the given interval's store, or every store, exceeds
+ * the budget; MPM_ERR_ARG for n_steps < 1 or ckpt_interval < 0.  Host only (no GPU work). */
+mpm_status mpm_scene_plan_rollout(const mpm_scene* scene, int n_steps, int ckpt_interval, size_t mem_budget_bytes,
+                                  int* k_out, long long* forward_steps, int* multi_level);
 
 /* Reverse pass of the last rollout (Supplement S2-S5 at every step, chained to the first state
  * and to the controller parameters used at every step).  Seeds are dL/d(final x, v, C, F)

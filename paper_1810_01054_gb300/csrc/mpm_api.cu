@@ -793,11 +793,33 @@ mpm_status read_status(mpm_scene* s) {
 // per-step record map, the forward counter, and checkpoint 0 = the current state.
 mpm_status rollout_records(mpm_scene* s, int T, int k, size_t budget, bool copy_start);
 
-// Interval the single-level store takes for T steps under a budget (0 = every state when they
-// fit or there is no budget, else ceil(sqrt(T))), and whether its states fit.
+// Bytes of the stores a single scene's reverse pass keeps when it recomputes beside the reverse
+// steps with interval k: the sort of every recomputed state (2k slots) and, for controllers that
+// read the state, their inputs.
+size_t overlap_store_bytes(const mpm_scene* s, int k) {
+  const size_t ctrl = ctrl_reads_state(s->ctrl) ? 2 * size_t(k) * CTRL_SLOT_FLOATS * sizeof(float) : 0;
+  return 2 * size_t(k) * sort_slot_words(s->npad, s->hp.n_tiles) * sizeof(uint32_t) + ctrl;
+}
+
+// Interval the single-level store takes for T steps under a budget (k = 0: chosen), and whether
+// its states fit.  Chosen: every state when they fit or there is no budget; else, in the tiled
+// form, the smallest multiple of the reverse graph length (GRAPH_STEPS) whose checkpoints, two
+// sets of recompute buffers and the overlap's stores fit, so that the fewest steps are recomputed,
+// beside the reverse steps, and a segment's reverse steps run as whole graphs; else ceil(sqrt(T)).
 int auto_interval(const mpm_scene* s, int T, int k, size_t budget, bool* fits) {
   const size_t S = s->state_bytes;
-  if (k == 0) k = (budget == 0 || size_t(T) * S <= budget) ? 1 : int(std::ceil(std::sqrt(double(T))));
+  if (k == 0) {
+    if (budget == 0 || size_t(T) * S <= budget) {
+      k = 1;
+    } else {
+      if (s->impl == MPM_IMPL_TILED)
+        for (int c = GRAPH_STEPS; c < T && k == 0; c += GRAPH_STEPS) {
+          const size_t nseg = size_t((T + c - 1) / c);
+          if (nseg > 1 && (nseg + 2 * size_t(c - 1)) * S + overlap_store_bytes(s, c) <= budget) k = c;
+        }
+      if (k == 0) k = int(std::ceil(std::sqrt(double(T))));
+    }
+  }
   k = std::min(k, T);
   const int nseg = (T + k - 1) / k;
   *fits = budget == 0 || (size_t(nseg) + size_t(k - 1)) * S <= budget;
@@ -922,8 +944,7 @@ mpm_status prepare_backward(mpm_scene* s, const float* gxT, const float* gvT, co
   const size_t S = s->state_bytes;
   const bool keep_ctrl = ctrl_reads_state(s->ctrl);  // controller inputs kept beside the sorts
   const size_t ctrl_bytes = keep_ctrl ? 2 * size_t(k) * CTRL_SLOT_FLOATS * sizeof(float) : 0;
-  const size_t store_bytes =
-      2 * size_t(k) * sort_slot_words(s->npad, s->hp.n_tiles) * sizeof(uint32_t) + ctrl_bytes;
+  const size_t store_bytes = overlap_store_bytes(s, k);
   const bool overlap = !mean_x0_seed && !(flags & BW_NO_OVERLAP) && s->impl == MPM_IMPL_TILED && k > 1 && nseg > 1 &&
                        (s->roll_budget == 0 ||
                         (size_t(nseg) + 2 * size_t(k - 1)) * S + store_bytes <= s->roll_budget);
@@ -1856,6 +1877,29 @@ mpm_status mpm_tune_tile_edge(mpm_ctx* c, const mpm_scene_desc* d, int steps, in
     ms[1] = t[1] / float(steps);
   }
   tune_edge_store(dim, d->n_particles, grid_nodes_of(d, dim), c->sm_count, *edge);
+  return MPM_OK;
+}
+
+mpm_status mpm_scene_plan_rollout(const mpm_scene* s, int T, int k, size_t budget, int* k_out,
+                                  long long* forward_steps, int* multi_level) {
+  if (!s || T < 1 || k < 0) return MPM_ERR_ARG;
+  bool fits = false;
+  const int kk = auto_interval(s, T, k, budget, &fits);
+  int kout = kk, multi = 0;
+  long long fwd = 0;
+  if (fits) {
+    fwd = 2LL * T - (T + kk - 1) / kk;  // the rollout, then the recompute of every segment
+  } else if (k == 0) {  // the multi-level store, planned in states of this scene
+    const long long states = s->state_bytes ? (long long)(budget / s->state_bytes) : 0;
+    int used = 0;
+    CKS(mpm_plan_checkpoints(T, states, &fwd, &used, &multi));
+    kout = 0;
+  } else {
+    return MPM_ERR_OOM;  // the given interval's states do not fit
+  }
+  if (k_out) *k_out = kout;
+  if (forward_steps) *forward_steps = fwd;
+  if (multi_level) *multi_level = multi;
   return MPM_OK;
 }
 

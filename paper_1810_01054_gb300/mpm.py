@@ -158,6 +158,8 @@ _SIGS = {
     "mpm_launch_count": [C.POINTER(C.c_longlong)],
     "mpm_plan_checkpoints": [C.c_int, C.c_longlong, C.POINTER(C.c_longlong), C.POINTER(C.c_int),
                              C.POINTER(C.c_int)],
+    "mpm_scene_plan_rollout": [C.c_void_p, C.c_int, C.c_int, C.c_size_t, C.POINTER(C.c_int),
+                               C.POINTER(C.c_longlong), C.POINTER(C.c_int)],
     "mpm_step_noalloc": [C.POINTER(NoAllocStep), C.c_void_p],
     "mpm_scene_set_tuning": [C.c_void_p, C.c_int],
     "mpm_scene_set_material": [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int],
@@ -492,6 +494,14 @@ class Scene:
         v = np.empty((n, self.dim), np.float32)
         _check(lib().mpm_get_grid(self.handle, _ptr(m), _ptr(v), 0), "mpm_get_grid")
         return m, v
+
+    def plan_rollout(self, n_steps: int, k: int = 0, budget: int = 0):
+        """(interval, forward steps of the rollout and its reverse pass, multi-level?) of
+        ``rollout(n_steps, k, budget)``; the interval is 0 with the multi-level store."""
+        kk, f, m = C.c_int(), C.c_longlong(), C.c_int()
+        _check(lib().mpm_scene_plan_rollout(self.handle, int(n_steps), int(k), int(budget), C.byref(kk), C.byref(f),
+                                            C.byref(m)), "mpm_scene_plan_rollout")
+        return int(kk.value), int(f.value), bool(m.value)
 
     def info(self):
         a, b, c, s = C.c_int(), C.c_int(), C.c_int(), C.c_int()
