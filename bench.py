@@ -97,8 +97,8 @@ def ckpt_of(spec):
 
 
 # Device-memory budget of the checkpoint store per workload (0 = no limit): the 1M-particle cluster
-# keeps its checkpoints within 4 GiB, where the library takes a checkpoint every 8 steps (the
-# smallest whole-graph interval whose store, with the overlapped recompute's, fits).
+# keeps its checkpoints within 4 GiB, where the library takes a checkpoint every 7 steps (the
+# smallest interval whose store, with the overlapped recompute's, fits).
 BUDGET = {"box_cluster_3d": 4 << 30}
 
 
@@ -544,7 +544,7 @@ def measure_replicas(args, dev, stream, sizes=(1, 64, 1024, 4096), edges=(8, 4))
 def measure_budget_sweep(args, dev, stream, budgets_gib=(32, 4, 1)):
     """Full-horizon gradient of the 1M-particle cluster (200 steps) under device-memory budgets for
     the checkpoint store: every state when they fit (k = 1); else every k-th state with the segments
-    recomputed beside the reverse steps (k the smallest whole-graph interval whose store fits);
+    recomputed beside the reverse steps (k the smallest interval whose store fits);
     below that the multi-level store (a recursive schedule planned for the fewest recomputed steps).
     Each budget's final state and gradients are compared bit for bit with the first budget's."""
     import torch

@@ -139,11 +139,11 @@ mpm_status mpm_step(mpm_scene* scene, int n_steps);
 /* Rollout for differentiation (Section III "memo"): n_steps steps from the current state,
  * asynchronously; the checkpoint buffers are kept for the next rollout of the same shape.
  * storing the state every ckpt_interval steps (0 = choose from mem_budget_bytes: every step if
- * all states fit; else, in the tiled form, the smallest multiple of 8 steps (the length of the
- * reverse pass's step graphs) whose checkpoints, two sets of recompute buffers and the sorts an
- * overlapped reverse pass keeps all fit, so that the fewest steps are recomputed and the recompute
- * runs beside the reverse steps; else about sqrt(n_steps); mpm_scene_plan_rollout reports the
- * choice); the states in between are recomputed by mpm_backward.  mem_budget_bytes = 0 means no
+ * all states fit; else, in the tiled form, the smallest interval whose checkpoints, two sets of
+ * recompute buffers and the sorts an overlapped reverse pass keeps all fit, so that the fewest
+ * steps are recomputed and the recompute runs beside the reverse steps; else about sqrt(n_steps);
+ * mpm_scene_plan_rollout reports the choice); the states in between are recomputed by
+ * mpm_backward.  mem_budget_bytes = 0 means no
  * limit.
  * With ckpt_interval = 0 and a budget below that single-level store ((ceil(T/k) + k - 1) states),
  * the rollout keeps a multi-level store instead: a recursive schedule (store a state, reverse the

@@ -4,8 +4,8 @@
 // Every step of a phase (plain stepping, rollout, segment recompute, reverse pass) is the same
 // launch sequence: a selection kernel first copies the scene record of step n (which buffers to
 // read and write) from a device table indexed by the scene's device-resident step counter, then
-// the step's kernels run on that record.  The sequences are captured once as CUDA graphs (one
-// step and GRAPH_STEPS steps per phase) and replayed.
+// the step's kernels run on that record.  The sequences are captured once as CUDA graphs (per
+// phase, one graph of each length from 1 to GRAPH_STEPS steps that a run needs) and replayed.
 //
 // Checkpointing: a rollout of T steps stores the state every k steps.  The stored states are
 // written by the step itself (G2P writes out of place at segment boundaries), so storing costs no
@@ -608,16 +608,19 @@ mpm_status run_phase(mpm_scene* s, int ph, int count, cudaStream_t graph_stream 
     for (int i = 0; i < count; ++i) CKS(enqueue_phase(s, ph, c->stream));
     return MPM_OK;
   }
+  // whole GRAPH_STEPS-step graphs, then one graph of the remaining steps (each length captured once)
   const int big = count / GRAPH_STEPS, small = count % GRAPH_STEPS;
-  if (big > 0 && !s->graphs[ph][1].exec) CKS(capture(s, ph, GRAPH_STEPS, &s->graphs[ph][1]));
-  if (small > 0 && !s->graphs[ph][0].exec) CKS(capture(s, ph, 1, &s->graphs[ph][0]));
+  Graph& gb = s->graphs[ph][GRAPH_STEPS];
+  if (big > 0 && !gb.exec) CKS(capture(s, ph, GRAPH_STEPS, &gb));
   for (int i = 0; i < big; ++i) {
-    CK(cudaGraphLaunch(s->graphs[ph][1].exec, gs));
-    count_launches(int(s->graphs[ph][1].kernels));
+    CK(cudaGraphLaunch(gb.exec, gs));
+    count_launches(int(gb.kernels));
   }
-  for (int i = 0; i < small; ++i) {
-    CK(cudaGraphLaunch(s->graphs[ph][0].exec, gs));
-    count_launches(int(s->graphs[ph][0].kernels));
+  if (small > 0) {
+    Graph& g = s->graphs[ph][small];
+    if (!g.exec) CKS(capture(s, ph, small, &g));
+    CK(cudaGraphLaunch(g.exec, gs));
+    count_launches(int(g.kernels));
   }
   return MPM_OK;
 }
@@ -803,9 +806,9 @@ size_t overlap_store_bytes(const mpm_scene* s, int k) {
 
 // Interval the single-level store takes for T steps under a budget (k = 0: chosen), and whether
 // its states fit.  Chosen: every state when they fit or there is no budget; else, in the tiled
-// form, the smallest multiple of the reverse graph length (GRAPH_STEPS) whose checkpoints, two
-// sets of recompute buffers and the overlap's stores fit, so that the fewest steps are recomputed,
-// beside the reverse steps, and a segment's reverse steps run as whole graphs; else ceil(sqrt(T)).
+// form, the smallest interval whose checkpoints, two sets of recompute buffers and the overlap's
+// stores fit, so that the fewest steps are recomputed, beside the reverse steps; else
+// ceil(sqrt(T)).
 int auto_interval(const mpm_scene* s, int T, int k, size_t budget, bool* fits) {
   const size_t S = s->state_bytes;
   if (k == 0) {
@@ -813,7 +816,7 @@ int auto_interval(const mpm_scene* s, int T, int k, size_t budget, bool* fits) {
       k = 1;
     } else {
       if (s->impl == MPM_IMPL_TILED)
-        for (int c = GRAPH_STEPS; c < T && k == 0; c += GRAPH_STEPS) {
+        for (int c = 2; c < T && k == 0; ++c) {
           const size_t nseg = size_t((T + c - 1) / c);
           if (nseg > 1 && (nseg + 2 * size_t(c - 1)) * S + overlap_store_bytes(s, c) <= budget) k = c;
         }

@@ -110,7 +110,7 @@ struct mpm_scene {
     int cap = 0;
     std::vector<int> host;
   } maps[3];                 // record index per step: rollout, recompute, reverse
-  Graph graphs[gbmpm::PH_COUNT][2]; // [phase][single step, GRAPH_STEPS steps]
+  Graph graphs[gbmpm::PH_COUNT][gbmpm::GRAPH_STEPS + 1];  // [phase][steps in the graph, 1..GRAPH_STEPS]
   // rollout record
   bool have_rollout = false;
   bool have_grad = false;    // adjoint buffers hold a finished reverse pass

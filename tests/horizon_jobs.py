@@ -9,7 +9,7 @@ Jobs (all on the seeded workloads the benchmark times):
   soft        3D soft body, 95,123 particles, MLP controller, the whole 500-step rollout: every 10th
               state and the full-horizon gradient of the same loss.
   cluster_fwd 1M-particle 3D cluster, the first 50 of its 200 steps: every 10th state.
-  cluster_seg 1M-particle 3D cluster, one checkpoint segment (8 steps from the initial state): the
+  cluster_seg 1M-particle 3D cluster, one checkpoint segment (7 steps from the initial state): the
               gradient of L = <w, x_15> + <u, v_15> with seeded weights w, u.
 """
 from __future__ import annotations
@@ -20,7 +20,7 @@ import numpy as np
 
 EVERY = 10
 CLUSTER_WINDOW_STEPS = 50
-CLUSTER_SEGMENT = 8
+CLUSTER_SEGMENT = 7
 
 
 def _spec(name):

@@ -2,7 +2,7 @@
 ~15-25 minutes of one host core and ~40 GB of host memory for the 1M-particle cluster's 200
 steps, so the test runs only with GBMPM_FULL_HORIZON=1 in the environment).
 
-1M-particle 3D cluster, 200 steps, the checkpoint store limited to 4 GiB (every 8th state kept,
+1M-particle 3D cluster, 200 steps, the checkpoint store limited to 4 GiB (every 7th state kept,
 segments recomputed beside the reverse steps), loss = mean final x_0, exactly as the benchmark
 times it: the final state and dL/d{x0, v0, C0, F0, controller parameters} against the oracle's
 whole rollout and reverse pass, at the stated gradient tolerance (relative 1e-3, cosine >= 0.999,

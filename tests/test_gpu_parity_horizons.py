@@ -8,7 +8,7 @@ re-synced to the oracle, gradients relative 1e-3 with cosine >= 0.999 and an ele
   3D soft body (95,123 particles, MLP controller): every 10-step window of the 500-step rollout, and
       the full-horizon gradient with a checkpoint every 23 steps, as benchmarked.
   1M-particle 3D cluster: the 10-step windows of the first 50 of its 200 steps, and the gradient of
-      one checkpoint segment (8 steps: the interval its 4 GiB budget gives), recomputed from its
+      one checkpoint segment (7 steps: the interval its 4 GiB budget gives), recomputed from its
       checkpoint as in the benchmarked reverse pass.
 
 The oracle runs in four spawned processes (tests/horizon_jobs.py) started when the module begins,
@@ -138,19 +138,19 @@ def test_cluster_one_checkpoint_segment_gradient(M, ctx, jobs):
 
 def test_cluster_plan_under_its_budgets(M, ctx):
     """The intervals mpm_rollout takes for the 1M-particle cluster's 200 steps by budget: every
-    state in 32 GiB; in 4 GiB the smallest whole-graph interval whose store (checkpoints, two sets
-    of recompute buffers, the overlap's sorts) fits, 8 steps (25 checkpoints, 175 steps
-    recomputed); in 1 GiB the multi-level store."""
+    state in 32 GiB; in 4 GiB the smallest interval whose store (checkpoints, two sets of recompute
+    buffers, the overlap's sorts) fits, 7 steps (29 checkpoints, 171 steps recomputed); in 1 GiB the
+    multi-level store."""
     spec = S.box_cluster_3d(3)
     sc = M.Scene(ctx, spec)
     S_ = sc.info()["state_bytes"]
     T = spec.n_steps
     assert sc.plan_rollout(T, 0, 32 << 30) == (1, T, False)
     k, fwd, multi = sc.plan_rollout(T, 0, 4 << 30)
-    assert (k, fwd, multi) == (8, 2 * T - T // 8, False)
-    assert (T // 8 + 2 * (k - 1)) * S_ <= 4 << 30
+    nseg = -(-T // 7)
+    assert (k, fwd, multi) == (7, 2 * T - nseg, False)
+    assert (nseg + 2 * (k - 1)) * S_ <= 4 << 30
     k1, fwd1, multi1 = sc.plan_rollout(T, 0, 1 << 30)
-    assert k1 == 0 and multi1 and fwd1 > 2 * T - T // 8
+    assert k1 == 0 and multi1 and fwd1 > 2 * T - nseg
     assert sc.plan_rollout(T, 15, 4 << 30)[:2] == (15, 2 * T - (-(-T // 15)))  # a given interval stays
     sc.close()
-
