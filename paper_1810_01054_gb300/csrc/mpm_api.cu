@@ -74,9 +74,10 @@ int block_nodes(int dim, int edge) {
   return dim == 2 ? bn * bn : bn * bn * bn;
 }
 
-// Tile edge of a new scene: the descriptor's, or (0) 8 for a 2D tiled scene whose particles
-// average under 96 per occupied 4 x 4 tile (sparse scenes: fewer, fuller tiles), else 4.
+// Density rule of the tile edge: a 2D tiled scene whose particles average under this many per
+// occupied 4 x 4 tile takes 8 x 8-cell tiles (sparse scenes: fewer, fuller tiles), else 4 x 4.
 constexpr int kWideTileMean = 96;
+
 long long grid_nodes_of(const mpm_scene_desc* d, int dim) {
   long long n = 1;
   for (int a = 0; a < dim; ++a) n *= d->n_grid[a];
